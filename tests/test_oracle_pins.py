@@ -1,0 +1,367 @@
+"""Pins of the CPU oracle against facts the paper and the mathematics fix.
+
+None of these compare the oracle with itself: each checks it against a closed
+form, a dense / sparse direct solve, an algebraic identity, a geometric
+definition evaluated by brute force, or values the paper prints (tests/golden).
+"""
+
+import math
+import os
+
+import numpy as np
+import pytest
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+import hhg_inputs as I
+import oracle as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+SHEAR = np.array([[1.0, 0.3, -0.2], [0.1, 0.9, 0.25], [-0.15, 0.2, 1.1]])
+
+
+def _rand_coeff(n, seed=5):
+    return np.exp(np.random.default_rng(seed).standard_normal(n))
+
+
+# --------------------------------------------------------------------------
+# operator (§2.1 Eq. (2))
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("sub,r,affine", [((1, 1, 1), 2, None), ((2, 1, 1), 2, SHEAR), ((1, 2, 2), 1 + 1, SHEAR)])
+def test_dia_equals_per_element_assembly(sub, r, affine):
+    m_coeff = _rand_coeff(6 * sub[0] * sub[1] * sub[2])
+    lv = O.Level(sub, r, m_coeff, affine)
+    A_dia = O.dia_to_csr(lv)
+    A_coo = O.assemble_coo(lv, m_coeff)
+    assert abs(A_dia - A_coo).max() <= 1e-14 * abs(A_coo).max()
+
+
+def test_element_macro_map_geometric():
+    """Each fine tetrahedron's centroid lies inside the macro-tetrahedron the
+    oracle assigns it to (barycentric coordinates all positive), the macro
+    being spanned by 0, e_pi0, e_pi0+e_pi1, (1,1,1) in its sub-cube."""
+    sub, r = (2, 1, 2), 2
+    lv = O.Level(sub, r, np.ones(24))
+    N = lv.N
+    nx, ny, nz = lv.n
+    for s, sigma in enumerate(O.PERMS):
+        offs = O.hhg_oracle._kuhn_offsets(sigma)
+        for cz in range(nz):
+            for cy in range(ny):
+                for cx in range(nx):
+                    cen = np.array([cx, cy, cz], float) + np.mean(np.array(offs, float), axis=0)
+                    mid = int(lv.emacro[s][cz, cy, cx])
+                    sl, p = divmod(mid, 6)
+                    a, rest = sl % sub[0], sl // sub[0]
+                    b, c = rest % sub[1], rest // sub[1]
+                    pi = O.PERMS[p]
+                    v0 = np.array([a, b, c], float) * N
+                    e = np.eye(3) * N
+                    V = np.array([v0, v0 + e[pi[0]], v0 + e[pi[0]] + e[pi[1]], v0 + N])
+                    lam = np.linalg.solve(np.vstack([V.T, np.ones(4)]), np.append(cen, 1.0))
+                    assert np.all(lam > 0), (s, cx, cy, cz, mid, lam)
+
+
+def test_cube_stencil_is_scaled_seven_point():
+    """On the un-sheared cube with k = 2.5 the Kuhn P1 matrix is k*h times the
+    7-point Laplacian at interior nodes (h = mesh width)."""
+    lv = O.Level((2, 2, 2), 3, np.full(48, 2.5))
+    rng = np.random.default_rng(0)
+    u = rng.standard_normal(lv.pshape)
+    Au = O.apply_A(lv, u)
+    h = 1.0 / lv.n[0]
+    c = O.interior(u)
+    s = np.zeros_like(c)
+    s[1:-1, 1:-1, 1:-1] = (6 * c[1:-1, 1:-1, 1:-1] - c[2:, 1:-1, 1:-1] - c[:-2, 1:-1, 1:-1]
+                           - c[1:-1, 2:, 1:-1] - c[1:-1, :-2, 1:-1] - c[1:-1, 1:-1, 2:] - c[1:-1, 1:-1, :-2])
+    assert np.allclose(Au[1:-1, 1:-1, 1:-1], 2.5 * h * s[1:-1, 1:-1, 1:-1], rtol=1e-13, atol=1e-13)
+    assert sorted(d for d in lv.A if d != (0, 0, 0)) == sorted(
+        [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)])
+
+
+def test_sheared_mesh_uses_all_fifteen_offsets():
+    lv = O.Level((1, 1, 1), 3, np.ones(6), SHEAR)
+    assert len(lv.A) == 15
+
+
+def test_symmetry_and_constants():
+    lv = O.Level((2, 1, 1), 3, _rand_coeff(12), SHEAR)
+    rng = np.random.default_rng(1)
+    u, v = rng.standard_normal(lv.shape), rng.standard_normal(lv.shape)
+    uAv = np.sum(u * O.apply_A(lv, O.pad(v)))
+    vAu = np.sum(v * O.apply_A(lv, O.pad(u)))
+    assert abs(uAv - vAu) <= 1e-12 * abs(uAv)
+    ones = O.pad(np.ones(lv.shape))
+    assert np.abs(O.apply_A(lv, ones)).max() <= 1e-13 * np.abs(lv.A[(0, 0, 0)]).max()
+
+
+def test_colouring_is_proper():
+    lv = O.Level((1, 1, 1), 3, np.ones(6), SHEAR)
+    col = O.pad(lv.colour.astype(float) + 1.0)     # 0 in the padding
+    for d, a in lv.A.items():
+        if d == (0, 0, 0):
+            continue
+        nb = O.hhg_oracle._shift(col, d, lv)
+        coupled = O.interior(a) != 0
+        assert not np.any(coupled & (nb == O.interior(col)))
+
+
+# --------------------------------------------------------------------------
+# transfers (§2.1)
+# --------------------------------------------------------------------------
+
+def _prolong_matrix(lc):
+    nz, ny, nx = lc.shape
+    cols = []
+    for i in range(nz * ny * nx):
+        e = np.zeros(nz * ny * nx)
+        e[i] = 1.0
+        cols.append(O.prolong(e.reshape(lc.shape)).ravel())
+    return sp.csr_matrix(np.array(cols).T)
+
+
+def test_galerkin_identity():
+    """P^T A_l P = A_{l-1} for nested P1 spaces with per-macro constant k."""
+    coeff = _rand_coeff(12, 3)
+    lc = O.Level((1, 2, 1), 2, coeff, SHEAR)
+    lf = O.Level((1, 2, 1), 3, coeff, SHEAR)
+    P = _prolong_matrix(lc)
+    G = (P.T @ O.dia_to_csr(lf) @ P).toarray()
+    Ac = O.dia_to_csr(lc).toarray()
+    assert np.abs(G - Ac).max() <= 1e-13 * np.abs(Ac).max()
+
+
+def test_prolongation_reproduces_linear_functions():
+    lc = O.Level((2, 1, 1), 2, np.ones(12))
+    z, y, x = np.indices(lc.shape).astype(float)
+    lin = lambda x, y, z: 0.3 + 1.7 * x - 0.4 * y + 2.2 * z
+    zf, yf, xf = np.indices(tuple(2 * s - 1 for s in lc.shape)).astype(float)
+    assert np.allclose(O.prolong(lin(x, y, z)), lin(xf / 2, yf / 2, zf / 2), rtol=0, atol=1e-13)
+
+
+def test_restriction_is_adjoint_of_prolongation():
+    rng = np.random.default_rng(2)
+    ec = rng.standard_normal((5, 9, 5))
+    rf = rng.standard_normal((9, 17, 9))
+    assert abs(np.sum(O.prolong(ec) * rf) - np.sum(ec * O.restrict(rf))) < 1e-12
+
+
+# --------------------------------------------------------------------------
+# solvers against direct solves (§2.1)
+# --------------------------------------------------------------------------
+
+def _direct(lv, u_full, f_full, free):
+    A = O.dia_to_csr(lv)
+    fr = free.ravel()
+    ub = u_full.ravel().copy()
+    rhs = f_full.ravel()[fr] - A[fr][:, ~fr] @ ub[~fr]
+    ub[fr] = spla.spsolve(A[fr][:, fr].tocsc(), rhs)
+    return ub.reshape(lv.shape)
+
+
+def test_cg_matches_direct_solve():
+    lv = O.Level((2, 2, 2), 2, _rand_coeff(48, 4))
+    free = ~lv.boundary
+    b = O.pad(np.random.default_rng(3).standard_normal(lv.shape))
+    x, it = O.cg(lv, b, free, rtol=1e-14)
+    ref = _direct(lv, np.zeros(lv.shape), O.interior(b), free)
+    assert np.abs(O.interior(x) - ref).max() <= 1e-11 * np.abs(ref).max()
+    assert 0 < it <= free.sum()
+
+
+@pytest.mark.parametrize("coeff_seed,affine", [(None, None), (7, SHEAR)])
+def test_vcycles_converge_to_direct_solve(coeff_seed, affine):
+    sub, R = (2, 2, 2), 4
+    coeff = None if coeff_seed is None else _rand_coeff(48, coeff_seed)
+    m = O.Mesh(sub, R, coeff=coeff, affine=affine)
+    g = I.harmonic_boundary(sub, R)
+    u = O.pad(I.initial_guess(sub, R, g))
+    f = O.pad(I.random_load(sub, R, seed=0) * 1e-3)
+    res = O.solve(m, u, f, rtol=1e-13, max_cycles=40)
+    ref = _direct(m.fine, I.initial_guess(sub, R, g), O.interior(f), ~m.fine.boundary)
+    assert np.abs(O.interior(u) - ref).max() <= 1e-10 * np.abs(ref).max()
+    assert res["hist"][-1] <= 1e-13
+
+
+def test_discretisation_error_is_second_order():
+    """Harmonic u* = exp(pi x) sin(pi y): max-norm error drops ~4x per refinement."""
+    errs = []
+    for R in (3, 4, 5):
+        sub = (1, 1, 1)
+        m = O.Mesh(sub, R)
+        g = I.harmonic_boundary(sub, R)
+        u = O.pad(I.initial_guess(sub, R, g))
+        O.solve(m, u, np.zeros(m.fine.pshape), rtol=1e-12, max_cycles=40)
+        errs.append(np.abs(O.interior(u) - g).max())
+    ratios = [errs[i] / errs[i + 1] for i in range(2)]
+    assert all(3.4 < q < 4.6 for q in ratios), ratios
+
+
+def test_vcycle_factor_is_h_independent():
+    """Textbook V(3,3) Gauss-Seidel on P1 Poisson: per-cycle residual factor
+    well below 0.2 and essentially independent of the mesh size."""
+    worst = []
+    for R in (3, 4, 5, 6):
+        sub = (2, 2, 2)
+        m = O.Mesh(sub, R)
+        u = O.pad(np.zeros(m.fine.shape))
+        f = O.pad(I.random_load(sub, R, seed=1))
+        res = O.solve(m, u, f, rtol=1e-30, max_cycles=8)
+        h = res["hist"]
+        worst.append(max(h[i + 1] / h[i] for i in range(2, 8)))
+    assert max(worst) < 0.2, worst
+    assert max(worst) / min(worst) < 2.0, worst
+
+
+def test_residual_history_matches_paper_band():
+    """Fault-free history of Fig. 2: every per-cycle factor of the oracle's
+    V(3,3) on the 2x2x2x6 cube lies within 2x of the paper's printed factor."""
+    data = np.loadtxt(os.path.join(GOLDEN, "fig2_residual_history.txt"))
+    paper = data[:, 1]
+    pf = paper[1:10] / paper[0:9]
+    sub, R = (2, 2, 2), 5
+    m = O.Mesh(sub, R)
+    g = I.harmonic_boundary(sub, R)
+    u = O.pad(I.initial_guess(sub, R, g))
+    res = O.solve(m, u, np.zeros(m.fine.pshape), rtol=1e-30, max_cycles=9)
+    h = res["hist"]
+    of = h[1:10] / h[0:9]
+    assert np.all(of < 2 * pf) and np.all(of > 0.5 * pf), (of, pf)
+
+
+# --------------------------------------------------------------------------
+# fault model and recovery (§2.2, §4.1, §4.2 Algorithm 1, Eq. (3))
+# --------------------------------------------------------------------------
+
+def test_fault_sets_integer_facts():
+    m = O.Mesh((2, 2, 2), 4)
+    # one macro-tetrahedron: its coarsest level (r = 2) has exactly one inner
+    # node (§2.1 / §4.1); at r = 4 it has 15*14*13/6 = 455 inner nodes.
+    masks = m.fault_masks([13])
+    assert masks[0][0].sum() == 1
+    assert masks[-1][0].sum() == 15 * 14 * 13 // 6
+    # a whole interior sub-cube: (N-1)^3 inner nodes on each level
+    sub = I.subcube_macros((2, 2, 2), 1, 1, 1)
+    for lv, (o, c) in zip(m.levels, m.fault_masks(sub)):
+        assert o.sum() == (lv.N - 1) ** 3
+        assert c.sum() == (lv.N + 1) ** 3
+    # fine-grid DoF of the whole problem = (2N - 1)^3
+    assert (~m.fine.boundary).sum() == 31 ** 3
+
+
+def _local_direct(m, u, f, ids, healthy=False):
+    o, c = m.fault_masks(ids)[-1]
+    free = (~m.fine.boundary & ~c) if healthy else o
+    return _direct(m.fine, O.interior(u).copy(), O.interior(f), free), free
+
+
+@pytest.mark.parametrize("healthy", [False, True])
+def test_recovery_subproblems_converge_to_direct_solve(healthy):
+    """Algorithm 1: step a solves A_FF u_F = f_F - A_FG u_G, step b solves
+    A_II u_I = f_I - A_IG u_G with the interface G frozen."""
+    sub, R = (2, 2, 2), 4
+    m = O.Mesh(sub, R, coeff=_rand_coeff(48, 9))
+    rng = np.random.default_rng(4)
+    u = O.pad(I.initial_guess(sub, R))
+    O.interior(u)[~m.fine.boundary] = rng.standard_normal((~m.fine.boundary).sum())
+    f = O.pad(I.random_load(sub, R, seed=2))
+    ids = I.subcube_macros(sub, 0, 0, 0) if healthy else [13]
+    prob = m.healthy_problem(ids) if healthy else m.local_problem(ids)
+    ref, free = _local_direct(m, u, f, ids, healthy)
+    for _ in range(30):
+        O.vcycle(m, prob, len(m.levels) - 1, u, f)
+    assert np.abs(O.interior(u) - ref).max() <= 1e-10 * np.abs(ref).max()
+    # frozen nodes untouched
+    assert np.array_equal(O.interior(u)[~free], ref[~free])
+
+
+def _run(m, f, rtol, **kw):
+    u = O.pad(np.zeros(m.fine.shape))
+    return O.solve(m, u, f, rtol=rtol, max_cycles=60, **kw)
+
+
+def test_do_nothing_costs_about_kF_minus_one_cycles():
+    """§2.2 / Fig. 2: after a fault at k_F = 5 the do-nothing job needs about
+    k_F - 1 extra cycles; kappa close to the Tab. 1 do-nothing row."""
+    sub, R = (2, 2, 2), 5
+    m = O.Mesh(sub, R)
+    f = O.pad(I.random_load(sub, R, seed=0))
+    free = _run(m, f, 1e-10)
+    dn = _run(m, f, 1e-10, fault_cycle=5, fault_ids=[13])
+    extra = dn["k_faulty"] - free["cycles"]
+    assert 3 <= extra <= 5, extra
+    tab = np.loadtxt(os.path.join(GOLDEN, "tab1_kappa_do_nothing.txt"))
+    k_dn = O.kappa(dn["k_faulty"], free["cycles"], 5)
+    assert tab[0, 1] - 0.01 <= k_dn <= 1.0
+    # the fault makes the residual jump by orders of magnitude (Fig. 2)
+    assert dn["hist"][6] > 1e3 * dn["hist"][5]
+
+
+def test_recovery_beats_do_nothing():
+    sub, R = (2, 2, 2), 5
+    m = O.Mesh(sub, R)
+    f = O.pad(I.random_load(sub, R, seed=0))
+    ids = I.subcube_macros(sub, 0, 0, 0)
+    free = _run(m, f, 1e-10)["cycles"]
+    dn = _run(m, f, 1e-10, fault_cycle=5, fault_ids=ids)["k_faulty"]
+    lr = _run(m, f, 1e-10, fault_cycle=5, fault_ids=ids, recovery=O.LR, n_local=6)["k_faulty"]
+    dd = _run(m, f, 1e-10, fault_cycle=5, fault_ids=ids, recovery=O.DD, n_global=2, eta=4.0)
+    assert dd["n_F"] == 8
+    kd = O.kappa(dn, free, 5)
+    assert O.kappa(lr, free, 5) < kd
+    assert O.kappa(dd["k_faulty"], free, 5) < kd
+
+
+def test_dd_with_zero_healthy_cycles_is_do_nothing():
+    sub, R = (2, 2, 2), 4
+    m = O.Mesh(sub, R)
+    f = O.pad(I.random_load(sub, R, seed=0))
+    a = _run(m, f, 1e-10, fault_cycle=4, fault_ids=[13])
+    b = _run(m, f, 1e-10, fault_cycle=4, fault_ids=[13], recovery=O.DD, n_global=0, eta=4.0)
+    assert np.array_equal(a["hist"], b["hist"])
+
+
+# --------------------------------------------------------------------------
+# adjoint gradient
+# --------------------------------------------------------------------------
+
+def test_coefficient_gradient_matches_finite_differences():
+    sub, R = (1, 1, 1), 3
+    k0 = _rand_coeff(6, 11)
+    f = I.random_load(sub, R, seed=3)
+    tgt = I.smooth_target(sub, R)
+
+    def fwd(k):
+        lv = O.Level(sub, R, k)
+        return _direct(lv, np.zeros(lv.shape), f, ~lv.boundary), lv
+
+    u, lv = fwd(k0)
+    lam = _direct(lv, np.zeros(lv.shape), u - tgt, ~lv.boundary)
+    m = O.Mesh(sub, R, coeff=k0)
+    g = O.grad_coeff(m, O.pad(u), O.pad(lam))
+    L = lambda k: 0.5 * np.sum((fwd(k)[0] - tgt)[~lv.boundary] ** 2)
+    for i in range(6):
+        e = np.zeros(6)
+        e[i] = 1e-6
+        fd = (L(k0 + e) - L(k0 - e)) / 2e-6
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(g[i])), (i, fd, g[i])
+
+
+# --------------------------------------------------------------------------
+# planted mistakes: each must be caught by one of the pins above
+# --------------------------------------------------------------------------
+
+def test_planted_restriction_mistake_is_caught(monkeypatch):
+    orig = O.hhg_oracle.FREUDENTHAL
+    monkeypatch.setattr(O.hhg_oracle, "FREUDENTHAL", orig[:-1])   # drop one term
+    with pytest.raises(AssertionError):
+        test_galerkin_identity()
+
+
+def test_planted_stiffness_mistake_is_caught(monkeypatch):
+    orig = O.hhg_oracle.element_stiffness
+    monkeypatch.setattr(O.hhg_oracle, "element_stiffness", lambda X: orig(X).T * np.array([1, 1, 1, 1.01]))
+    with pytest.raises(AssertionError):
+        test_cube_stencil_is_scaled_seven_point()
