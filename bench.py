@@ -1,0 +1,375 @@
+#!/usr/bin/env python
+"""Benchmark of the resilient HHG multigrid path on GB300.
+
+Workload: the unit cube split into 2x2x2 sub-cubes x 6 Kuhn macro-tetrahedra
+(48 macros), refined 8 times (512 intervals per cube edge, 1.334e8 fine
+unknowns), P1 Poisson with a load vector of i.i.d. uniform[-1, 1] entries
+(Philox seed 0), homogeneous Dirichlet data, zero initial guess, FP64
+V(3,3) cycles with 4-colour Gauss-Seidel and coarse CG.  After global cycle
+5 a fault erases the volume unknowns of sub-cube (0,0,0) (six macros); the
+Dirichlet-Dirichlet recovery runs n_F = 12 local cycles on the lost sub-cube
+concurrently with n_I = 3 cycles on the healthy part (eta = 4); the global
+iteration then continues to a relative residual of 1e-8.
+
+One step = one such solve (every stage of the path: V-cycles, residual norms,
+fault injection, interface restore, local and healthy-side recovery cycles,
+recoupling).  value = fine-grid DoF x global V-cycles / second.  Inputs are
+resident in HBM before the timed region and larger than L2.
+
+--impl reference runs the CPU oracle (FP64 numpy) on the host cores on a
+bounded sample of the same workload: one V-cycle of the same cube refined 7
+times per step.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "fine-grid DoF/s per V-cycle (% HBM roofline); time to 1e-8 rel. residual w/ fault"
+UNIT = "DoF/s"
+SUB, R = (2, 2, 2), 8
+R_CPU = 7
+SEED = 0
+FAULT_CYCLE = 5
+ETA, N_I = 4.0, 3
+RTOL = 1e-8
+MAX_CYCLES = 40
+WORKLOAD = ("cube 2x2x2x6 macro-tets refined 8 levels (1.334e8 DoF), FP64 V(3,3) 4-colour GS + coarse CG, "
+            "random load seed 0, fault after cycle 5 erases sub-cube (0,0,0), DD recovery eta=4 n_I=3 n_F=12, "
+            "solve to 1e-8 relative residual")
+# FP64 peak of the GB300 derived from its unit counts and clock: 152 SMs x
+# 2 DFMA / clock / SM (ncu: sm__sass_thread_inst_executed_op_dfma_pred_on
+# peak_sustained) x 2 flop x 2070 MHz.
+FP64_PEAK_TFLOPS = 152 * 2 * 2 * 2.070e9 / 1e12
+FALLBACK_HBM_GBS = 6800.0
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ["index", "clocks.sm", "clocks.max.sm", "power.draw", "clocks_event_reasons.active",
+              "clocks_event_reasons.hw_slowdown", "clocks_event_reasons.hw_thermal_slowdown",
+              "clocks_event_reasons.sw_thermal_slowdown", "clocks_event_reasons.sw_power_cap"]
+
+    def __init__(self, gpu_id):
+        self.gpu_id = gpu_id
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu_id), "--query-gpu=" + ",".join(self.FIELDS),
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+
+        def rd():
+            for line in self.proc.stdout:
+                self.lines.append(line.strip())
+        self.thread = threading.Thread(target=rd, daemon=True)
+        self.thread.start()
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _kernel_hash():
+    with open(os.path.join(ROOT, "paper_1506_06185_gb300", "csrc", "kernels.cu"), "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def _traffic(kind):
+    """DRAM bytes per launch of the dominant kernel from a committed ncu
+    summary, if it was taken on the current kernel source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            d = json.load(fh)
+        e = d.get(kind)
+        if e and e.get("kernel_hash") == _kernel_hash():
+            return e.get("bytes_per_launch_full_size")
+    except Exception:
+        pass
+    return None
+
+
+def cpu_oracle_sample(steps=1):
+    """The CPU oracle as it stands: V-cycles on the cube refined R_CPU times."""
+    import numpy as np
+    import hhg_inputs as I
+    import oracle as O
+    m = O.Mesh(SUB, R_CPU)
+    f = O.pad(I.random_load(SUB, R_CPU, SEED))
+    u = O.pad(np.zeros(m.fine.shape))
+    top = len(m.levels) - 1
+    dof = (2 ** (R_CPU + 1) - 1) ** 3
+    times = []
+    for _ in range(steps):
+        t = time.perf_counter()
+        O.vcycle(m, m.global_problem, top, u, f)
+        times.append(time.perf_counter() - t)
+    return dof, times
+
+
+def _dist():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args):
+    rank, world, _ = _dist()
+    if rank != 0:
+        return 0
+    import numpy as np  # noqa: F401
+    dof, times = cpu_oracle_sample(args.warmup + args.steps)
+    timed = times[args.warmup:]
+    t = sum(timed)
+    value = dof * len(timed) / t
+    sample = (f"{len(timed)} V-cycles (one per step) of the CPU oracle on the same cube refined {R_CPU} levels "
+              f"({dof} DoF), FP64 numpy, single thread")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / len(timed), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": WORKLOAD, "sample": sample, "parallelism": "none (host)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    import hhg_inputs as I
+    from paper_1506_06185_gb300 import build
+    from paper_1506_06185_gb300 import hhg
+
+    rank, world, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    build()
+    dev = torch.device("cuda", local)
+    M = hhg.Mesh(SUB, R, precision=32)
+    fault = I.subcube_macros(SUB, 0, 0, 0)
+    f_np = I.random_load(SUB, R, SEED)
+    f_dev = torch.from_numpy(f_np).to(dev)
+    u0_dev = torch.zeros_like(f_dev)
+    M.set_problem(f_dev, u0_dev)
+    torch.cuda.synchronize()
+    solve_kw = dict(rtol=RTOL, max_cycles=MAX_CYCLES, fault_cycle=FAULT_CYCLE, fault_ids=fault,
+                    recovery=hhg.HHG_RECOVERY_DD, n_global=N_I, eta=ETA)
+    stream = torch.cuda.current_stream()
+
+    def step(**over):
+        kw = dict(solve_kw)
+        kw.update(over)
+        M.set_problem(None, u0_dev)
+        hist, cyc, _ = M.solve(**kw)
+        return hist, cyc
+
+    for _ in range(args.warmup):
+        hist, cycles = step()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    visible = os.environ.get("CUDA_VISIBLE_DEVICES")
+    sampler = ClockSampler(visible.split(",")[local] if visible else local)
+    sampler.start()
+    hhg.hhg_profile_enable(M.h, True)
+    l0 = hhg.hhg_launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    cyc_list = []
+    for _ in range(args.steps):
+        hist, cycles = step()
+        cyc_list.append(cycles)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    l1 = hhg.hhg_launch_count()
+    n_prof, prof_ms = hhg.hhg_profile_read(M.h)
+    hhg.hhg_profile_enable(M.h, False)
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        dist.barrier()
+    dof = M.n_dof
+    value = world * dof * sum(cyc_list) / (ms * 1e-3)
+
+    # dominant kernel: finest-level FP64 Gauss-Seidel volume kernel (one colour per launch)
+    n_vol, seven = hhg.hhg_profile_info(M.h)
+    avg_s = prof_ms / max(n_prof, 1) * 1e-3
+    ops = 6 if seven else 14
+    flops_per_node = 2 * ops + 1          # DFMA per neighbour + one DMUL
+    flops = flops_per_node * n_vol / 4.0
+    achieved_tflops = flops / avg_s / 1e12
+    hbm_peak, hbm_src = _peaks()
+    alg_bytes = 24.0 * n_vol / 4.0        # read u, read f, write u per node update
+    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": _traffic("gs_vol_f64"),
+                "kernel": "k_gs_vol<double> finest level, one colour", "launches": n_prof,
+                "avg_launch_ms": avg_s * 1e3,
+                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64)",
+                "hbm_achieved_gbs": alg_bytes / avg_s / 1e9, "hbm_peak_gbs": hbm_peak,
+                "hbm_frac": alg_bytes / avg_s / 1e9 / hbm_peak, "hbm_peak_source": hbm_src}
+
+    # end to end through the C ABI with pinned host buffers
+    f_pin = torch.from_numpy(f_np).pin_memory()
+    u0_pin = torch.zeros_like(f_pin).pin_memory()
+    u_pin = torch.zeros_like(f_pin).pin_memory()
+    torch.cuda.synchronize()
+    k_e2e = max(1, min(args.steps, 3))
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    e2e_cycles = 0
+    for _ in range(k_e2e):
+        M.set_problem(f_pin.numpy(), u0_pin.numpy())
+        hist_e, cyc_e, _ = M.solve(**solve_kw)
+        M.get_solution(u_pin.numpy())
+        e2e_cycles += cyc_e
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([t_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_e2e = float(t.item())
+    nbytes = f_np.nbytes
+    e2e = {"value": world * dof * e2e_cycles / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * nbytes,
+           "d2h_bytes_per_step": nbytes, "ms_per_step": 1e3 * t_e2e / k_e2e}
+    M.set_problem(f_dev, None)
+
+    # variants on the same GPU: fault-free, do-nothing, LR, and mixed precision
+    variants = {}
+    if not args.quick:
+        def timed(**over):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            h, c = step(**over)
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b), h, c
+        ms_free, h_free, c_free = timed(fault_cycle=0)
+        ms_dn, h_dn, c_dn = timed(recovery=hhg.HHG_RECOVERY_NONE)
+        ms_lr, h_lr, c_lr = timed(recovery=hhg.HHG_RECOVERY_LR, n_local=3)
+        ms_dd, h_dd, c_dd = timed()
+        u_fp64 = torch.zeros_like(f_dev)
+        M.get_solution(u_fp64)
+        ms_mx, h_mx, c_mx = timed(mixed_precision=True)
+        u_mx = torch.zeros_like(f_dev)
+        M.get_solution(u_mx)
+        ms_mx_free, h_mx_free, c_mx_free = timed(mixed_precision=True, fault_cycle=0)
+        diff = float((u_mx - u_fp64).abs().max().item())
+        scale = float(u_fp64.abs().max().item())
+        kappa = lambda kf, n_extra=0: (kf + n_extra - c_free) / FAULT_CYCLE
+        variants = {
+            "fault_free_fp64": {"ms": ms_free, "cycles": c_free, "final_rel_res": float(h_free[-1])},
+            "do_nothing_fp64": {"ms": ms_dn, "cycles": c_dn, "kappa": kappa(c_dn)},
+            "local_recovery_fp64_nF3": {"ms": ms_lr, "cycles": c_lr, "kappa": kappa(c_lr)},
+            "dd_fp64_eta4_nI3": {"ms": ms_dd, "cycles": c_dd, "kappa": kappa(c_dd, N_I)},
+            "dd_mixed_fp32_in_fp64_ir": {"ms": ms_mx, "cycles": c_mx, "final_rel_res": float(h_mx[-1]),
+                                         "max_abs_diff_vs_fp64_solution": diff, "fp64_solution_max": scale},
+            "fault_free_mixed": {"ms": ms_mx_free, "cycles": c_mx_free},
+        }
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "dof": dof, "cycles_per_step": cyc_list,
+                       "time_to_1e-8_with_fault_ms": ms / args.steps, "l2": "inputs larger than L2 (no flush)",
+                       "parallelism": "replicas" if world > 1 else "single GPU"},
+            "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": l1 - l0,
+            "final_rel_residual": float(hist[-1]), "variants": variants}
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cdof, ctimes = cpu_oracle_sample(1)
+        line["cpu_baseline"] = {"value": cdof / ctimes[0], "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": f"1 V-cycle of the CPU oracle (FP64 numpy, one thread) on the same cube "
+                                          f"refined {R_CPU} levels ({cdof} DoF), {ctimes[0]:.1f} s"}
+    M.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--quick", action="store_true", help="skip the variant timings")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        print("warning: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,185 @@
+/*
+ * hhg.h - C ABI of the GB300 resilient hierarchical-hybrid multigrid library.
+ *
+ * Method: Huber, Gmeiner, Ruede, Wohlmuth, "Resilience for Multigrid Software
+ * at the Extreme Scale".  The library solves the P1 finite-element Poisson
+ * problem of §2.1 (Eq. (1), discretised as Eq. (2)) on the unit cube split
+ * into sub-cubes of six Kuhn macro-tetrahedra (the base mesh T_-2, §2.1),
+ * refined uniformly, with matrix-free multigrid V-cycles (linear
+ * interpolation, its adjoint, multicolour Gauss-Seidel smoothing, CG on the
+ * coarsest level; §2.1), and recovers from the loss of the volume unknowns
+ * of some macro-tetrahedra (the fault model of §2.2) with local Dirichlet
+ * multigrid cycles (local recovery LR, §4.4) running, for the
+ * Dirichlet-Dirichlet strategy (§4.2, Algorithm 1), concurrently with
+ * global cycles on the healthy sub-domain.
+ *
+ * Conventions shared by every entry point
+ * ----------------------------------------
+ * - Every call returns an int status (HHG_OK on success).  Nothing throws
+ *   across the ABI.  hhg_last_error() gives a message for the last failure
+ *   of the calling thread.
+ * - A mesh handle owns all device storage it allocates; the caller owns the
+ *   vectors it passes in.  Handles are not thread-safe: one thread at a time.
+ * - Global vectors (right-hand side, solution) are laid out over the global
+ *   node grid, x fastest: node (x, y, z) of a grid with nx, ny, nz intervals
+ *   has index (z * (ny + 1) + y) * (nx + 1) + x, nx = subcubes[0] * 2^levels
+ *   etc.; there are (nx + 1)(ny + 1)(nz + 1) entries.  A vector pointer may
+ *   be host memory (pageable or pinned) or device memory of the current
+ *   device; the library tells them apart itself.
+ * - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *   stream).  Calls that return values to the host synchronise that stream.
+ * - The right-hand side is the algebraic load vector f_l of Eq. (2) (one
+ *   value per node); its Dirichlet-node entries are ignored.  The solution
+ *   vector carries the Dirichlet values g on the boundary nodes.
+ */
+#ifndef HHG_H
+#define HHG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  HHG_OK = 0,
+  HHG_ERR_ARG = 1,            /* invalid argument (sizes, ids, null pointer) */
+  HHG_ERR_CUDA = 2,           /* a CUDA runtime call failed */
+  HHG_ERR_OOM = 3,            /* device or host allocation failed */
+  HHG_ERR_TIMEOUT = 4,        /* a bounded device-side wait ran out */
+  HHG_ERR_NOT_CONVERGED = 5,  /* hhg_solve stopped at max_cycles above rtol */
+  HHG_ERR_STATE = 6           /* call not valid in the mesh's current state */
+};
+
+/* Recovery strategies after a fault (§2.2 job classes, §4). */
+enum {
+  HHG_RECOVERY_NONE = 0,      /* do-nothing: zero re-initialisation only */
+  HHG_RECOVERY_LR = 1,        /* n_F local cycles on Omega_F, Omega_I idle */
+  HHG_RECOVERY_DD = 2         /* Algorithm 1: n_F local cycles on Omega_F and,
+                                 concurrently, n_I cycles on Omega_I with the
+                                 interface frozen */
+};
+
+typedef struct hhg_mesh hhg_mesh;
+
+typedef struct {
+  int subcubes[3];        /* sub-cubes per axis; 6 macro-tetrahedra each */
+  int levels;             /* finest refinement R: 2^R intervals per macro edge */
+  int coarsest;           /* coarsest refinement r0 (>= 2, < levels; 0 = 2) */
+  int precision;          /* 64: FP64 cycles; 32: also allocate the FP32
+                             inner-cycle arrays used by mixed-precision
+                             iterative refinement (hhg_solve_opts) */
+  const double* coeff;    /* host, one diffusion coefficient k_T per macro
+                             (macro id = 6 * subcube + Kuhn type, sub-cubes x
+                             fastest, Kuhn types in lexicographic axis order);
+                             NULL = all ones */
+  const double* affine;   /* host, 3x3 row-major linear map applied to the
+                             unit cube's node positions; NULL = identity */
+} hhg_mesh_desc;
+
+/* Build the macro mesh, all levels coarsest..levels, the per-macro stencils
+ * (15 weights per node class, interface sub-stencils summed per node, §3.2
+ * Fig. 4) and the device storage (per-macro blocks with a ghost shell and
+ * face/edge/vertex interface containers, §3.1).  *out receives the handle. */
+int hhg_mesh_create(const hhg_mesh_desc* desc, hhg_mesh** out);
+int hhg_mesh_destroy(hhg_mesh* mesh);
+
+/* n_nodes: entries of a global vector; n_dof: non-Dirichlet fine nodes;
+ * n_macro: macro-tetrahedra.  Any output pointer may be NULL. */
+int hhg_mesh_info(const hhg_mesh* mesh, int64_t* n_nodes, int64_t* n_dof, int* n_macro);
+
+/* Device bytes held by the mesh (all levels, interface tables, scratch). */
+int hhg_mesh_bytes(const hhg_mesh* mesh, int64_t* bytes);
+
+/* Load the right-hand side f (may be NULL: keep the current one, initially
+ * zero) and the initial guess u0 including Dirichlet values (may be NULL:
+ * keep the current iterate, initially zero) from global vectors. */
+int hhg_set_problem(hhg_mesh* mesh, const double* f, const double* u0, void* stream);
+
+/* Write the current fine-level iterate into the global vector u. */
+int hhg_get_solution(hhg_mesh* mesh, double* u, void* stream);
+
+/* One global V(pre, post) cycle (§2.1) on the current iterate.  If resid_out
+ * is not NULL it receives ||f - A u||_2 over the non-Dirichlet fine nodes
+ * after the cycle (synchronises the stream). */
+int hhg_vcycle(hhg_mesh* mesh, int pre, int post, double* resid_out, void* stream);
+
+/* ||f - A u||_2 over the non-Dirichlet fine nodes (synchronises). */
+int hhg_residual_norm(hhg_mesh* mesh, double* out, void* stream);
+
+/* Fault model of §2.2: the macro-tetrahedra macro_ids[0..n_ids) lose their
+ * volume storage (block and ghost shell) and every unknown strictly inside
+ * their union Omega_F is re-initialised with zero.  The interface values on
+ * Gamma survive in the face/edge/vertex containers and are written back into
+ * the ghost shells of the lost blocks (Eq. (4), row 4; Algorithm 1 step 4).
+ * Ids must be distinct and in [0, n_macro). */
+int hhg_inject_fault(hhg_mesh* mesh, const int* macro_ids, int n_ids, void* stream);
+
+/* Recovery after hhg_inject_fault on the same ids.  n_local V-cycles of the
+ * Dirichlet problem A_FF u_F = f_F - A_FG u_G on Omega_F (Algorithm 1 step
+ * a).  n_global = 0: local recovery (LR), Omega_I idles.  n_global > 0:
+ * Dirichlet-Dirichlet recovery, n_global V-cycles of A_II u_I = f_I -
+ * A_IG u_G on Omega_I with the interface frozen (step b) run concurrently on
+ * a second stream.  If seconds_local / seconds_global are not NULL they
+ * receive the device time of the two cycle sequences (synchronises). */
+int hhg_recover_local(hhg_mesh* mesh, const int* macro_ids, int n_ids, int n_local,
+                      int n_global, double* seconds_local, double* seconds_global,
+                      void* stream);
+
+typedef struct {
+  double rtol;            /* stop when ||r_k|| <= rtol ||r_0|| (r_0 of the
+                             initial iterate) */
+  int max_cycles;         /* global V-cycles at most */
+  int pre, post;          /* smoothing steps (0 = 3 each) */
+  int fault_cycle;        /* inject the fault after this global cycle; <= 0:
+                             no fault */
+  const int* fault_ids;   /* host, macro ids of Omega_F */
+  int n_fault_ids;
+  int recovery;           /* HHG_RECOVERY_* */
+  int n_local;            /* n_F; 0 with DD: ceil(eta * n_global) */
+  int n_global;           /* n_I (DD only) */
+  double eta;             /* superman factor for n_F = ceil(eta * n_I) */
+  int mixed_precision;    /* 1: FP32 cycles inside FP64 iterative refinement
+                             (needs a precision-32 mesh) */
+  double coarse_rtol;     /* coarse CG relative tolerance (0 = 1e-12) */
+  int coarse_maxit;       /* coarse CG iteration cap (0 = 1000) */
+} hhg_solve_opts;
+
+/* Iterate global V-cycles from the current iterate until rtol or
+ * max_cycles, injecting the fault and running the recovery of opts.
+ * hist (host, at least max_cycles + 2 doubles, may be NULL) receives the
+ * relative residuals: hist[0] = 1, one entry per global cycle and, for a
+ * faulty run, one extra entry right after the fault and its recovery.
+ * *n_hist receives the entries written, *cycles the global V-cycles run.
+ * Returns HHG_ERR_NOT_CONVERGED (after writing the outputs) if rtol was not
+ * reached. */
+int hhg_solve(hhg_mesh* mesh, const hhg_solve_opts* opts, double* hist, int* n_hist,
+              int* cycles, void* stream);
+
+/* Measurement support (not part of the method).
+ * hhg_profile_enable: while enabled, every launch of the dominant kernel -- the
+ * finest-level Gauss-Seidel volume kernel of the global problem (one colour of
+ * the smoother of §2.1 on all macro interiors) -- is bracketed by CUDA events on
+ * the stream it runs on.  Enabling clears the record.
+ * hhg_profile_read: synchronises the device and returns the number of
+ * recorded launches and their summed device time in milliseconds; clears the
+ * record.
+ * hhg_profile_info: volume-interior nodes of the finest level (the nodes one
+ * sweep of all four colours of that kernel updates) and whether the stencil
+ * has the 7-point structure (only the six axis neighbours non-zero).
+ * hhg_launch_count: kernel launches issued by the library in this process. */
+int hhg_profile_enable(hhg_mesh* mesh, int enable);
+int hhg_profile_read(hhg_mesh* mesh, int64_t* launches, double* total_ms);
+int hhg_profile_info(const hhg_mesh* mesh, int64_t* volume_nodes, int* seven_point);
+int hhg_launch_count(int64_t* count);
+
+/* Copy the message of the calling thread's last failure into buf (always
+ * NUL-terminated if len > 0).  Returns the status of that failure. */
+int hhg_last_error(char* buf, size_t len);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HHG_H */

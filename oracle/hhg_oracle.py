@@ -45,7 +45,7 @@ __all__ = [
     "element_stiffness", "assemble_coo", "dia_to_csr", "apply_A",
     "gs_step", "residual", "restrict", "prolong", "cg", "vcycle",
     "resnorm", "inject_fault", "solve", "kappa", "grad_coeff",
-    "interior", "pad", "node_coords", "NONE", "LR", "DD",
+    "interior", "pad", "node_coords", "NONE", "LR", "DD", "local_residual",
 ]
 
 # Lexicographic permutations of the axes (x=0, y=1, z=2).  Kuhn tetrahedron
@@ -539,3 +539,36 @@ def grad_coeff(mesh, u, lam):
                 acc += K[a, b] * la * u[lv._cell_slice(offs[b])]
         g += np.bincount(lv.emacro[s].ravel(), weights=acc.ravel(), minlength=mesh.n_macro)
     return -g
+
+
+def local_residual(sub, R, coeff, affine, u, f, nodes):
+    """f_p - (A u)_p at selected nodes p of the finest grid, each row assembled
+    on the spot from the fine tetrahedra around p (§2.1 Eq. (2)); for checks on
+    meshes too large for a full assembly.  ``u`` and ``f`` are grid arrays
+    (unpadded), ``nodes`` an (n, 3) array of (x, y, z) interior node indices."""
+    sx, sy, sz = sub
+    N = 1 << R
+    nx, ny, nz = sx * N, sy * N, sz * N
+    G = np.eye(3) if affine is None else np.asarray(affine, dtype=np.float64)[:, :3]
+    h = np.array([1.0 / nx, 1.0 / ny, 1.0 / nz])
+    Kel = [element_stiffness(np.array([G @ (np.array(o) * h) for o in _kuhn_offsets(s)])) for s in PERMS]
+    coeff = np.asarray(coeff, dtype=np.float64)
+    out = np.zeros(len(nodes))
+    for q, (x, y, z) in enumerate(np.asarray(nodes, dtype=np.int64)):
+        acc = 0.0
+        for s, sigma in enumerate(PERMS):
+            offs = _kuhn_offsets(sigma)
+            for a, oa in enumerate(offs):
+                c = (x - oa[0], y - oa[1], z - oa[2])
+                if not (0 <= c[0] < nx and 0 <= c[1] < ny and 0 <= c[2] < nz):
+                    continue
+                # macro of this fine tetrahedron: sort the centroid's sub-cube-local coordinates
+                cen = [c[i] + (3 - sigma.index(i)) / 4.0 for i in range(3)]
+                sc = [int(cen[i] // N) for i in range(3)]
+                loc = [cen[i] - sc[i] * N for i in range(3)]
+                pi = tuple(sorted(range(3), key=lambda i: -loc[i]))
+                mid = ((sc[2] * sy + sc[1]) * sx + sc[0]) * 6 + PERMS.index(pi)
+                for b, ob in enumerate(offs):
+                    acc += coeff[mid] * Kel[s][a, b] * u[c[2] + ob[2], c[1] + ob[1], c[0] + ob[0]]
+        out[q] = f[z, y, x] - acc
+    return out

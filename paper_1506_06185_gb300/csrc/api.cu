@@ -1,0 +1,738 @@
+// C ABI of the HHG library (include/hhg.h): device storage, the V-cycle
+// driver, the fault / recovery paths and the solve loop.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/hhg.h"
+#include "hhg_kernels.h"
+
+using namespace hhg;
+
+namespace {
+
+thread_local std::string g_err;
+thread_local int g_err_code = HHG_OK;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  g_err_code = code;
+  return code;
+}
+
+#define HHG_CUDA(call)                                                                 \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return fail(e_ == cudaErrorMemoryAllocation ? HHG_ERR_OOM : HHG_ERR_CUDA,        \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                 \
+  } while (0)
+
+#define HHG_TRY(expr)            \
+  do {                           \
+    int rc_ = (expr);            \
+    if (rc_ != HHG_OK) return rc_; \
+  } while (0)
+
+template <class T>
+struct Prec {
+  std::vector<DevLevel<T>> lv;
+  std::vector<T*> Winv;
+};
+
+}  // namespace
+
+struct hhg_mesh {
+  HostMesh host;
+  int device = 0;
+  int precision = 64;
+  std::vector<DevLevelTables> tab;
+  Prec<double> d64;
+  Prec<float> d32;
+  MacroGeo* geo = nullptr;
+  DevProblem global, faulty, healthy;
+  std::vector<unsigned char> fault_set;
+  bool has_fault = false;
+  // fault bookkeeping on the finest level
+  int* fault_zero_ids = nullptr;
+  int n_fault_zero = 0;
+  int64_t* fault_restore_off = nullptr;
+  int* fault_restore_master = nullptr;
+  int n_fault_restore = 0;
+  double* staging = nullptr;
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  double* host_scalar = nullptr;   // pinned
+  // profiling of the finest-level Gauss-Seidel volume kernel of the global problem
+  bool prof_on = false;
+  std::vector<cudaEvent_t> prof_ev;
+  size_t prof_used = 0;
+};
+
+namespace {
+
+template <class T>
+int dalloc(hhg_mesh* m, T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) return HHG_OK;
+  void* q = nullptr;
+  cudaError_t e = cudaMalloc(&q, n * sizeof(T));
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(HHG_ERR_OOM, "cudaMalloc of " + std::to_string(n * sizeof(T)) + " bytes failed: " +
+                                 cudaGetErrorString(e));
+  }
+  m->allocs.push_back(q);
+  m->bytes += (int64_t)(n * sizeof(T));
+  *p = static_cast<T*>(q);
+  return HHG_OK;
+}
+
+template <class T>
+int upload(hhg_mesh* m, T** p, const std::vector<T>& v) {
+  HHG_TRY(dalloc(m, p, v.size()));
+  if (!v.empty()) HHG_CUDA(cudaMemcpy(*p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+  return HHG_OK;
+}
+
+void free_all(hhg_mesh* m) {
+  for (void* p : m->allocs) cudaFree(p);
+  m->allocs.clear();
+}
+
+LevelArgs largs(const hhg_mesh* m, int l) {
+  const HostLevel& H = m->host.lv[l];
+  const DevLevelTables& t = m->tab[l];
+  LevelArgs a;
+  a.N = H.N;
+  a.P = H.P;
+  a.block = H.block;
+  a.if_gid = t.if_gid;
+  a.cptr = t.if_cptr;
+  a.cps = t.if_copy;
+  a.tiles_int = t.tiles_int;
+  a.n_tiles_int = t.n_tiles_int;
+  a.tiles_all = t.tiles_all;
+  a.n_tiles_all = t.n_tiles_all;
+  return a;
+}
+
+ProbArgs pargs(const DevProblem& p, int l) {
+  ProbArgs a;
+  a.act = p.act;
+  a.n_act = p.n_act;
+  const DevProblemLevel& q = p.lv[l];
+  a.free_if = q.free_if;
+  for (int c = 0; c < 5; ++c) a.col_off[c] = q.col_off[c];
+  a.zero_off = q.zero_off;
+  a.n_zero = q.n_zero;
+  a.gather = q.gather;
+  return a;
+}
+
+int upload_problem(hhg_mesh* m, const HostProblem& h, DevProblem& d) {
+  d.kind = h.kind;
+  d.act_host = h.act;
+  d.n_act = (int)h.act.size();
+  HHG_TRY(upload(m, &d.act, h.act));
+  d.lv.assign(h.lv.size(), DevProblemLevel());
+  for (size_t l = 0; l < h.lv.size(); ++l) {
+    HHG_TRY(upload(m, &d.lv[l].free_if, h.lv[l].free_if));
+    for (int c = 0; c < 5; ++c) d.lv[l].col_off[c] = h.lv[l].col_off[c];
+    HHG_TRY(upload(m, &d.lv[l].zero_off, h.lv[l].zero_off));
+    d.lv[l].n_zero = (int)h.lv[l].zero_off.size();
+    HHG_TRY(upload(m, &d.lv[l].gather, h.lv[l].gather));
+  }
+  d.n_cg = h.n_cg;
+  HHG_TRY(upload(m, &d.rowptr, h.rowptr));
+  HHG_TRY(upload(m, &d.col, h.col));
+  HHG_TRY(upload(m, &d.val, h.val));
+  HHG_TRY(upload(m, &d.fsrc, h.fsrc));
+  HHG_TRY(upload(m, &d.uptr, h.uptr));
+  HHG_TRY(upload(m, &d.udst, h.udst));
+  HHG_TRY(upload(m, &d.umaster, h.umaster));
+  HHG_TRY(dalloc(m, &d.cg_work, (size_t)4 * std::max(1, h.n_cg)));
+  const int L = (int)m->host.lv.size() - 1;
+  d.n_partial = m->tab[L].n_tiles_int * std::max(1, d.n_act) + (m->host.lv[L].n_if + 127) / 128 + 64;
+  HHG_TRY(dalloc(m, &d.partial, (size_t)d.n_partial));
+  HHG_TRY(dalloc(m, &d.scalar, 8));
+  HHG_TRY(dalloc(m, &d.cg_iters, 4));
+  return HHG_OK;
+}
+
+template <class T>
+int alloc_levels(hhg_mesh* m, Prec<T>& P, bool with_r_on_finest) {
+  const int nl = (int)m->host.lv.size();
+  P.lv.assign(nl, DevLevel<T>());
+  P.Winv.assign(nl, nullptr);
+  for (int l = 0; l < nl; ++l) {
+    const HostLevel& H = m->host.lv[l];
+    DevLevel<T>& D = P.lv[l];
+    D.N = H.N;
+    D.P = H.P;
+    D.block = H.block;
+    D.n_if = H.n_if;
+    const size_t nb = (size_t)m->host.n_macro * H.block;
+    HHG_TRY(dalloc(m, &D.u, nb));
+    HHG_TRY(dalloc(m, &D.f, nb));
+    if (l < nl - 1 || with_r_on_finest) HHG_TRY(dalloc(m, &D.r, nb));
+    HHG_TRY(dalloc(m, &D.uI, (size_t)std::max(1, H.n_if)));
+    HHG_TRY(dalloc(m, &D.fI, (size_t)std::max(1, H.n_if)));
+    HHG_CUDA(cudaMemset(D.u, 0, nb * sizeof(T)));
+    HHG_CUDA(cudaMemset(D.f, 0, nb * sizeof(T)));
+    if (D.r) HHG_CUDA(cudaMemset(D.r, 0, nb * sizeof(T)));
+    HHG_CUDA(cudaMemset(D.uI, 0, std::max(1, H.n_if) * sizeof(T)));
+    HHG_CUDA(cudaMemset(D.fI, 0, std::max(1, H.n_if) * sizeof(T)));
+    std::vector<T> w(H.W.size()), winv(m->host.n_macro);
+    for (size_t q = 0; q < w.size(); ++q) w[q] = (T)H.W[q];
+    for (int t = 0; t < m->host.n_macro; ++t) winv[t] = (T)(1.0 / H.W[(size_t)t * 16 * NDIR]);
+    HHG_TRY(upload(m, &D.W, w));
+    HHG_TRY(upload(m, &P.Winv[l], winv));
+  }
+  return HHG_OK;
+}
+
+// One V(pre, post) cycle of problem p on the arrays of precision T.
+// A pair of events bracketing the next profiled launch (none when profiling
+// is off).
+int prof_pair(hhg_mesh* m, cudaEvent_t* b, cudaEvent_t* e) {
+  *b = *e = nullptr;
+  if (!m->prof_on) return HHG_OK;
+  while (m->prof_ev.size() < m->prof_used + 2) {
+    cudaEvent_t ev;
+    HHG_CUDA(cudaEventCreate(&ev));
+    m->prof_ev.push_back(ev);
+  }
+  *b = m->prof_ev[m->prof_used];
+  *e = m->prof_ev[m->prof_used + 1];
+  m->prof_used += 2;
+  return HHG_OK;
+}
+
+template <class T>
+int smooth(hhg_mesh* m, Prec<T>& P, DevProblem& p, int l, int steps, cudaStream_t s) {
+  const int L = (int)P.lv.size() - 1;
+  DevLevel<T>& D = P.lv[l];
+  const LevelArgs a = largs(m, l);
+  const ProbArgs q = pargs(p, l);
+  const bool prof = l == L && p.kind == 0;
+  for (int it = 0; it < steps; ++it)
+    for (int c = 0; c < 4; ++c) {
+      cudaEvent_t b = nullptr, e = nullptr;
+      if (prof) HHG_TRY(prof_pair(m, &b, &e));
+      HHG_CUDA(gs_colour<T>(a, q, D.u, D.uI, D.f, D.fI, D.W, P.Winv[l], c, m->host.seven_point, s, b, e));
+    }
+  return HHG_OK;
+}
+
+template <class T>
+int vcycle_T(hhg_mesh* m, Prec<T>& P, DevProblem& p, int pre, int post, double cg_rtol, int cg_maxit,
+             cudaStream_t s) {
+  const int L = (int)P.lv.size() - 1;
+  const bool s7 = m->host.seven_point;
+  for (int l = L; l >= 1; --l) {
+    DevLevel<T>& D = P.lv[l];
+    const LevelArgs a = largs(m, l);
+    const ProbArgs q = pargs(p, l);
+    HHG_TRY(smooth<T>(m, P, p, l, pre, s));
+    HHG_CUDA(residual<T>(a, q, D.u, D.uI, D.f, D.fI, D.r, D.W, s7, true, nullptr, nullptr, s));
+    DevLevel<T>& C = P.lv[l - 1];
+    HHG_CUDA(restrict_to<T>(largs(m, l - 1), a, pargs(p, l - 1), D.r, C.f, C.fI, C.u, C.uI, s));
+  }
+  HHG_CUDA(coarse_cg<T>(p, P.lv[0].f, P.lv[0].fI, P.lv[0].u, P.lv[0].uI, cg_rtol, cg_maxit, s));
+  for (int l = 1; l <= L; ++l) {
+    DevLevel<T>& D = P.lv[l];
+    const LevelArgs a = largs(m, l);
+    const ProbArgs q = pargs(p, l);
+    HHG_CUDA(prolong_add<T>(a, largs(m, l - 1), q, D.u, D.uI, P.lv[l - 1].u, s));
+    HHG_TRY(smooth<T>(m, P, p, l, post, s));
+  }
+  return HHG_OK;
+}
+
+// ||f - A u||^2 of problem p on the finest FP64 level, left in p.scalar[0].
+int norm2_async(hhg_mesh* m, DevProblem& p, cudaStream_t s) {
+  const int L = (int)m->d64.lv.size() - 1;
+  DevLevel<double>& D = m->d64.lv[L];
+  int np = 0;
+  HHG_CUDA(residual<double>(largs(m, L), pargs(p, L), D.u, D.uI, D.f, D.fI, nullptr, D.W, m->host.seven_point, false,
+                            p.partial, &np, s));
+  HHG_CUDA(reduce_partials(p.partial, np, p.scalar, s));
+  return HHG_OK;
+}
+
+int read_scalar(hhg_mesh* m, const double* dev, double* out, cudaStream_t s) {
+  HHG_CUDA(cudaMemcpyAsync(m->host_scalar, dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  HHG_CUDA(cudaStreamSynchronize(s));
+  *out = *m->host_scalar;
+  return HHG_OK;
+}
+
+int resnorm(hhg_mesh* m, double* out, cudaStream_t s) {
+  HHG_TRY(norm2_async(m, m->global, s));
+  double v = 0.0;
+  HHG_TRY(read_scalar(m, m->global.scalar, &v, s));
+  *out = std::sqrt(v);
+  return HHG_OK;
+}
+
+// Mixed precision: one FP64 iterative-refinement step of problem p with an
+// FP32 inner V-cycle.  The FP64 residual r = f - A u is formed on the finest
+// level and handed to the FP32 cycle as its right-hand side (its squared norm
+// is left in p.scalar[0]); the FP32 correction e (zero initial guess) is then
+// added to u in FP64.
+int ir_residual(hhg_mesh* m, DevProblem& p, cudaStream_t s) {
+  const int L = (int)m->d64.lv.size() - 1;
+  DevLevel<double>& D = m->d64.lv[L];
+  DevLevel<float>& E = m->d32.lv[L];
+  int np = 0;
+  HHG_CUDA(residual_to_f32(largs(m, L), pargs(p, L), D.u, D.uI, D.f, D.fI, E.f, E.fI, D.W, m->host.seven_point,
+                           p.partial, &np, s));
+  HHG_CUDA(reduce_partials(p.partial, np, p.scalar, s));
+  return HHG_OK;
+}
+
+int ir_cycle(hhg_mesh* m, DevProblem& p, int pre, int post, double cg_rtol, int cg_maxit, cudaStream_t s) {
+  const int L = (int)m->d64.lv.size() - 1;
+  DevLevel<float>& E = m->d32.lv[L];
+  HHG_TRY(ir_residual(m, p, s));
+  HHG_CUDA(zero_problem_blocks<float>(largs(m, L), pargs(p, L), E.u, E.uI, s));
+  HHG_TRY(vcycle_T<float>(m, m->d32, p, pre, post, cg_rtol, cg_maxit, s));
+  DevLevel<double>& D = m->d64.lv[L];
+  HHG_CUDA(add_correction(largs(m, L), pargs(p, L), D.u, D.uI, E.u, E.uI, s));
+  return HHG_OK;
+}
+
+int cycle(hhg_mesh* m, DevProblem& p, bool mixed, int pre, int post, double cg_rtol, int cg_maxit, cudaStream_t s) {
+  if (mixed) return ir_cycle(m, p, pre, post, cg_rtol, cg_maxit, s);
+  return vcycle_T<double>(m, m->d64, p, pre, post, cg_rtol, cg_maxit, s);
+}
+
+const double* stage_in(hhg_mesh* m, const double* g, cudaStream_t s, int* rc) {
+  *rc = HHG_OK;
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, g);
+  if (e != cudaSuccess) cudaGetLastError();
+  if (e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) return g;
+  const int64_t n = (m->host.nx + 1) * (m->host.ny + 1) * (m->host.nz + 1);
+  if (!m->staging) {
+    *rc = dalloc(m, &m->staging, (size_t)n);
+    if (*rc != HHG_OK) return nullptr;
+  }
+  e = cudaMemcpyAsync(m->staging, g, (size_t)n * sizeof(double), cudaMemcpyDefault, s);
+  if (e != cudaSuccess) {
+    *rc = fail(HHG_ERR_CUDA, std::string("copy of a global vector to the device: ") + cudaGetErrorString(e));
+    return nullptr;
+  }
+  return m->staging;
+}
+
+int check_ids(const hhg_mesh* m, const int* ids, int n, std::vector<unsigned char>& set) {
+  if (n <= 0 || !ids) return fail(HHG_ERR_ARG, "empty macro id list");
+  set.assign(m->host.n_macro, 0);
+  for (int q = 0; q < n; ++q) {
+    if (ids[q] < 0 || ids[q] >= m->host.n_macro) return fail(HHG_ERR_ARG, "macro id out of range");
+    if (set[ids[q]]) return fail(HHG_ERR_ARG, "duplicate macro id");
+    set[ids[q]] = 1;
+  }
+  return HHG_OK;
+}
+
+int setup_fault(hhg_mesh* m, const std::vector<unsigned char>& set) {
+  if (m->has_fault && set == m->fault_set) return HHG_OK;
+  HostProblem hf, hh;
+  try {
+    build_problem(m->host, 1, set, hf);
+    build_problem(m->host, 2, set, hh);
+  } catch (const std::exception& e) {
+    return fail(HHG_ERR_ARG, std::string("fault set: ") + e.what());
+  }
+  HHG_TRY(upload_problem(m, hf, m->faulty));
+  HHG_TRY(upload_problem(m, hh, m->healthy));
+  // finest-level fault bookkeeping: masters inside Omega_F are erased; every
+  // interface copy inside a lost block is restored from its master
+  const int L = (int)m->host.lv.size() - 1;
+  const HostLevel& H = m->host.lv[L];
+  std::vector<int> zero_ids(hf.lv[L].free_if);
+  std::vector<int64_t> off;
+  std::vector<int> mst;
+  for (int n = 0; n < H.n_if; ++n)
+    for (int c = H.if_cptr[n]; c < H.if_cptr[n + 1]; ++c) {
+      const Copy& cp = H.if_copy[c];
+      if (!set[cp.macro]) continue;
+      off.push_back((int64_t)cp.macro * H.block + lidx(H.N, H.P, cp.i, cp.j, cp.k));
+      mst.push_back(n);
+    }
+  HHG_TRY(upload(m, &m->fault_zero_ids, zero_ids));
+  m->n_fault_zero = (int)zero_ids.size();
+  HHG_TRY(upload(m, &m->fault_restore_off, off));
+  HHG_TRY(upload(m, &m->fault_restore_master, mst));
+  m->n_fault_restore = (int)off.size();
+  m->fault_set = set;
+  m->has_fault = true;
+  return HHG_OK;
+}
+
+int inject(hhg_mesh* m, cudaStream_t s) {
+  const int L = (int)m->host.lv.size() - 1;
+  DevLevel<double>& D = m->d64.lv[L];
+  for (int t = 0; t < m->host.n_macro; ++t)
+    if (m->fault_set[t]) HHG_CUDA(cudaMemsetAsync(D.u + (size_t)t * D.block, 0, D.block * sizeof(double), s));
+  HHG_CUDA(set_masters_zero(D.uI, m->fault_zero_ids, m->n_fault_zero, s));
+  HHG_CUDA(restore_copies(D.u, D.uI, m->fault_restore_off, m->fault_restore_master, m->n_fault_restore, s));
+  return HHG_OK;
+}
+
+int recover(hhg_mesh* m, int n_local, int n_global, bool mixed, int pre, int post, double cg_rtol, int cg_maxit,
+            double* t_local, double* t_global, cudaStream_t s) {
+  cudaEvent_t a0, a1, b0, b1;
+  const bool timed = t_local || t_global;
+  if (timed) {
+    HHG_CUDA(cudaEventCreate(&a0));
+    HHG_CUDA(cudaEventCreate(&a1));
+    HHG_CUDA(cudaEventCreate(&b0));
+    HHG_CUDA(cudaEventCreate(&b1));
+  }
+  if (n_global > 0) {
+    HHG_CUDA(cudaEventRecord(m->ev_fork, s));
+    HHG_CUDA(cudaStreamWaitEvent(m->side, m->ev_fork, 0));
+  }
+  if (timed) HHG_CUDA(cudaEventRecord(a0, s));
+  for (int c = 0; c < n_local; ++c) HHG_TRY(cycle(m, m->faulty, mixed, pre, post, cg_rtol, cg_maxit, s));
+  if (timed) HHG_CUDA(cudaEventRecord(a1, s));
+  if (n_global > 0) {
+    if (timed) HHG_CUDA(cudaEventRecord(b0, m->side));
+    for (int c = 0; c < n_global; ++c) HHG_TRY(cycle(m, m->healthy, mixed, pre, post, cg_rtol, cg_maxit, m->side));
+    if (timed) HHG_CUDA(cudaEventRecord(b1, m->side));
+    HHG_CUDA(cudaEventRecord(m->ev_join, m->side));
+    HHG_CUDA(cudaStreamWaitEvent(s, m->ev_join, 0));
+  }
+  if (timed) {
+    HHG_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    HHG_CUDA(cudaEventElapsedTime(&ms, a0, a1));
+    if (t_local) *t_local = ms * 1e-3;
+    if (t_global) {
+      *t_global = 0.0;
+      if (n_global > 0) {
+        HHG_CUDA(cudaEventElapsedTime(&ms, b0, b1));
+        *t_global = ms * 1e-3;
+      }
+    }
+    cudaEventDestroy(a0);
+    cudaEventDestroy(a1);
+    cudaEventDestroy(b0);
+    cudaEventDestroy(b1);
+  }
+  return HHG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hhg_last_error(char* buf, size_t len) {
+  if (buf && len > 0) {
+    size_t n = std::min(len - 1, g_err.size());
+    std::memcpy(buf, g_err.data(), n);
+    buf[n] = '\0';
+  }
+  return g_err_code;
+}
+
+int hhg_mesh_create(const hhg_mesh_desc* desc, hhg_mesh** out) {
+  if (!desc || !out) return fail(HHG_ERR_ARG, "null argument");
+  *out = nullptr;
+  const int r0 = desc->coarsest > 0 ? desc->coarsest : 2;
+  for (int a = 0; a < 3; ++a)
+    if (desc->subcubes[a] < 1 || desc->subcubes[a] > 64) return fail(HHG_ERR_ARG, "subcubes must be in [1, 64]");
+  if (r0 < 2) return fail(HHG_ERR_ARG, "coarsest refinement must be >= 2");
+  if (desc->levels <= r0 || desc->levels > 10) return fail(HHG_ERR_ARG, "levels must be in (coarsest, 10]");
+  if (desc->precision != 64 && desc->precision != 32) return fail(HHG_ERR_ARG, "precision must be 64 or 32");
+  if (desc->coeff)
+    for (int t = 0; t < 6 * desc->subcubes[0] * desc->subcubes[1] * desc->subcubes[2]; ++t)
+      if (!(desc->coeff[t] > 0.0)) return fail(HHG_ERR_ARG, "coefficients must be positive");
+  std::unique_ptr<hhg_mesh> m(new (std::nothrow) hhg_mesh());
+  if (!m) return fail(HHG_ERR_OOM, "host allocation failed");
+  try {
+    build_host_mesh(m->host, desc->subcubes, desc->levels, r0, desc->coeff, desc->affine);
+  } catch (const std::bad_alloc&) {
+    return fail(HHG_ERR_OOM, "host allocation failed while building the mesh");
+  } catch (const std::exception& e) {
+    return fail(HHG_ERR_ARG, std::string("mesh: ") + e.what());
+  }
+  m->precision = desc->precision;
+  int rc = HHG_OK;
+  auto cleanup = [&](int code) {
+    free_all(m.get());
+    return code;
+  };
+  if (cudaGetDevice(&m->device) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(HHG_ERR_CUDA, "no CUDA device");
+  }
+  const int nl = (int)m->host.lv.size();
+  m->tab.assign(nl, DevLevelTables());
+  for (int l = 0; l < nl && rc == HHG_OK; ++l) {
+    const HostLevel& H = m->host.lv[l];
+    DevLevelTables& t = m->tab[l];
+    if ((rc = upload(m.get(), &t.if_gid, H.if_gid)) != HHG_OK) break;
+    if ((rc = upload(m.get(), &t.if_cptr, H.if_cptr)) != HHG_OK) break;
+    if ((rc = upload(m.get(), &t.if_copy, H.if_copy)) != HHG_OK) break;
+    if ((rc = upload(m.get(), &t.tiles_int, H.tiles_int)) != HHG_OK) break;
+    if ((rc = upload(m.get(), &t.tiles_all, H.tiles_all)) != HHG_OK) break;
+    t.n_tiles_int = (int)H.tiles_int.size();
+    t.n_tiles_all = (int)H.tiles_all.size();
+  }
+  if (rc == HHG_OK) rc = upload(m.get(), &m->geo, m->host.geo);
+  if (rc == HHG_OK) rc = alloc_levels<double>(m.get(), m->d64, true);
+  if (rc == HHG_OK && m->precision == 32) rc = alloc_levels<float>(m.get(), m->d32, true);
+  if (rc == HHG_OK) {
+    HostProblem hg;
+    try {
+      build_problem(m->host, 0, std::vector<unsigned char>(m->host.n_macro, 0), hg);
+    } catch (const std::exception& e) {
+      rc = fail(HHG_ERR_ARG, std::string("problem: ") + e.what());
+    }
+    if (rc == HHG_OK) rc = upload_problem(m.get(), hg, m->global);
+  }
+  if (rc != HHG_OK) return cleanup(rc);
+  if (cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMallocHost(&m->host_scalar, sizeof(double) * 8) != cudaSuccess) {
+    cudaGetLastError();
+    return cleanup(fail(HHG_ERR_CUDA, "stream / event creation failed"));
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) return cleanup(fail(HHG_ERR_CUDA, "device error during setup"));
+  *out = m.release();
+  return HHG_OK;
+}
+
+int hhg_mesh_destroy(hhg_mesh* m) {
+  if (!m) return HHG_OK;
+  cudaDeviceSynchronize();
+  free_all(m);
+  if (m->side) cudaStreamDestroy(m->side);
+  if (m->ev_fork) cudaEventDestroy(m->ev_fork);
+  if (m->ev_join) cudaEventDestroy(m->ev_join);
+  if (m->host_scalar) cudaFreeHost(m->host_scalar);
+  for (cudaEvent_t ev : m->prof_ev) cudaEventDestroy(ev);
+  delete m;
+  return HHG_OK;
+}
+
+int hhg_mesh_info(const hhg_mesh* m, int64_t* n_nodes, int64_t* n_dof, int* n_macro) {
+  if (!m) return fail(HHG_ERR_ARG, "null mesh");
+  if (n_nodes) *n_nodes = (m->host.nx + 1) * (m->host.ny + 1) * (m->host.nz + 1);
+  if (n_dof) *n_dof = (m->host.nx - 1) * (m->host.ny - 1) * (m->host.nz - 1);
+  if (n_macro) *n_macro = m->host.n_macro;
+  return HHG_OK;
+}
+
+int hhg_mesh_bytes(const hhg_mesh* m, int64_t* bytes) {
+  if (!m || !bytes) return fail(HHG_ERR_ARG, "null argument");
+  *bytes = m->bytes;
+  return HHG_OK;
+}
+
+int hhg_set_problem(hhg_mesh* m, const double* f, const double* u0, void* stream) {
+  if (!m) return fail(HHG_ERR_ARG, "null mesh");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int L = (int)m->host.lv.size() - 1;
+  const LevelArgs a = largs(m, L);
+  DevLevel<double>& D = m->d64.lv[L];
+  int rc;
+  if (f) {
+    const double* g = stage_in(m, f, s, &rc);
+    if (!g) return rc;
+    HHG_CUDA(import_vec<double>(a, m->geo, m->host.n_macro, m->host.nx, m->host.ny, g, D.f, D.fI, false, s));
+    HHG_CUDA(import_masters<double>(a.if_gid, m->host.lv[L].n_if, g, D.fI, s));
+  }
+  if (u0) {
+    const double* g = stage_in(m, u0, s, &rc);
+    if (!g) return rc;
+    HHG_CUDA(import_vec<double>(a, m->geo, m->host.n_macro, m->host.nx, m->host.ny, g, D.u, D.uI, true, s));
+    HHG_CUDA(import_masters<double>(a.if_gid, m->host.lv[L].n_if, g, D.uI, s));
+  }
+  return HHG_OK;
+}
+
+int hhg_get_solution(hhg_mesh* m, double* u, void* stream) {
+  if (!m || !u) return fail(HHG_ERR_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int L = (int)m->host.lv.size() - 1;
+  const LevelArgs a = largs(m, L);
+  DevLevel<double>& D = m->d64.lv[L];
+  cudaPointerAttributes at;
+  cudaError_t e = cudaPointerGetAttributes(&at, u);
+  if (e != cudaSuccess) cudaGetLastError();
+  const bool dev = e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+  double* g = u;
+  const int64_t n = (m->host.nx + 1) * (m->host.ny + 1) * (m->host.nz + 1);
+  if (!dev) {
+    if (!m->staging) HHG_TRY(dalloc(m, &m->staging, (size_t)n));
+    g = m->staging;
+  }
+  HHG_CUDA(export_vec<double>(a, m->geo, m->host.n_macro, m->host.nx, m->host.ny, D.u, D.uI, g, s));
+  HHG_CUDA(export_masters<double>(a.if_gid, m->host.lv[L].n_if, D.uI, g, s));
+  if (!dev) {
+    HHG_CUDA(cudaMemcpyAsync(u, g, (size_t)n * sizeof(double), cudaMemcpyDefault, s));
+    HHG_CUDA(cudaStreamSynchronize(s));
+  }
+  return HHG_OK;
+}
+
+int hhg_vcycle(hhg_mesh* m, int pre, int post, double* resid_out, void* stream) {
+  if (!m || pre < 0 || post < 0) return fail(HHG_ERR_ARG, "invalid argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  HHG_TRY(vcycle_T<double>(m, m->d64, m->global, pre, post, 1e-12, 1000, s));
+  if (resid_out) HHG_TRY(resnorm(m, resid_out, s));
+  return HHG_OK;
+}
+
+int hhg_residual_norm(hhg_mesh* m, double* out, void* stream) {
+  if (!m || !out) return fail(HHG_ERR_ARG, "null argument");
+  return resnorm(m, out, (cudaStream_t)stream);
+}
+
+int hhg_inject_fault(hhg_mesh* m, const int* ids, int n, void* stream) {
+  if (!m) return fail(HHG_ERR_ARG, "null mesh");
+  std::vector<unsigned char> set;
+  HHG_TRY(check_ids(m, ids, n, set));
+  HHG_TRY(setup_fault(m, set));
+  return inject(m, (cudaStream_t)stream);
+}
+
+int hhg_recover_local(hhg_mesh* m, const int* ids, int n, int n_local, int n_global, double* seconds_local,
+                      double* seconds_global, void* stream) {
+  if (!m || n_local < 0 || n_global < 0) return fail(HHG_ERR_ARG, "invalid argument");
+  std::vector<unsigned char> set;
+  HHG_TRY(check_ids(m, ids, n, set));
+  HHG_TRY(setup_fault(m, set));
+  return recover(m, n_local, n_global, false, 3, 3, 1e-12, 1000, seconds_local, seconds_global,
+                 (cudaStream_t)stream);
+}
+
+int hhg_profile_enable(hhg_mesh* m, int enable) {
+  if (!m) return fail(HHG_ERR_ARG, "null mesh");
+  m->prof_on = enable != 0;
+  m->prof_used = 0;
+  return HHG_OK;
+}
+
+int hhg_profile_read(hhg_mesh* m, int64_t* launches, double* total_ms) {
+  if (!m) return fail(HHG_ERR_ARG, "null mesh");
+  HHG_CUDA(cudaDeviceSynchronize());
+  double t = 0.0;
+  for (size_t q = 0; q + 1 < m->prof_used; q += 2) {
+    float ms = 0.f;
+    HHG_CUDA(cudaEventElapsedTime(&ms, m->prof_ev[q], m->prof_ev[q + 1]));
+    t += ms;
+  }
+  if (launches) *launches = (int64_t)(m->prof_used / 2);
+  if (total_ms) *total_ms = t;
+  m->prof_used = 0;
+  return HHG_OK;
+}
+
+int hhg_profile_info(const hhg_mesh* m, int64_t* volume_nodes, int* seven_point) {
+  if (!m) return fail(HHG_ERR_ARG, "null mesh");
+  const int N = m->host.lv.back().N;
+  if (volume_nodes) *volume_nodes = (int64_t)m->host.n_macro * (N - 1) * (N - 2) * (N - 3) / 6;
+  if (seven_point) *seven_point = m->host.seven_point ? 1 : 0;
+  return HHG_OK;
+}
+
+int hhg_launch_count(int64_t* count) {
+  if (!count) return fail(HHG_ERR_ARG, "null argument");
+  *count = (int64_t)g_kernel_launches.load();
+  return HHG_OK;
+}
+
+int hhg_solve(hhg_mesh* m, const hhg_solve_opts* o, double* hist, int* n_hist, int* cycles, void* stream) {
+  if (!m || !o) return fail(HHG_ERR_ARG, "null argument");
+  if (o->max_cycles < 0 || !(o->rtol >= 0.0)) return fail(HHG_ERR_ARG, "invalid rtol / max_cycles");
+  const bool mixed = o->mixed_precision != 0;
+  if (mixed && m->precision != 32) return fail(HHG_ERR_STATE, "mixed precision needs a precision-32 mesh");
+  const int pre = o->pre > 0 ? o->pre : 3, post = o->post > 0 ? o->post : 3;
+  const double cg_rtol = o->coarse_rtol > 0 ? o->coarse_rtol : 1e-12;
+  const int cg_maxit = o->coarse_maxit > 0 ? o->coarse_maxit : 1000;
+  const bool faulty = o->fault_cycle > 0;
+  if (faulty) {
+    std::vector<unsigned char> set;
+    HHG_TRY(check_ids(m, o->fault_ids, o->n_fault_ids, set));
+    HHG_TRY(setup_fault(m, set));
+    if (o->recovery < HHG_RECOVERY_NONE || o->recovery > HHG_RECOVERY_DD)
+      return fail(HHG_ERR_ARG, "unknown recovery strategy");
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  int nh = 0;
+  auto push = [&](double v) {
+    if (hist) hist[nh] = v;
+    ++nh;
+  };
+  // residual norm of the current iterate
+  double r0 = 0.0, v = 0.0;
+  if (mixed) {
+    HHG_TRY(ir_residual(m, m->global, s));
+    HHG_TRY(read_scalar(m, m->global.scalar, &v, s));
+    r0 = std::sqrt(v);
+  } else {
+    HHG_TRY(resnorm(m, &r0, s));
+  }
+  push(1.0);
+  int k = 0;
+  double rel = 1.0;
+  while (k < o->max_cycles) {
+    if (mixed) {
+      // the residual of the current iterate is already the FP32 right-hand side
+      const int L = (int)m->d64.lv.size() - 1;
+      DevLevel<float>& E = m->d32.lv[L];
+      HHG_CUDA(zero_problem_blocks<float>(largs(m, L), pargs(m->global, L), E.u, E.uI, s));
+      HHG_TRY(vcycle_T<float>(m, m->d32, m->global, pre, post, cg_rtol, cg_maxit, s));
+      DevLevel<double>& D = m->d64.lv[L];
+      HHG_CUDA(add_correction(largs(m, L), pargs(m->global, L), D.u, D.uI, E.u, E.uI, s));
+      HHG_TRY(ir_residual(m, m->global, s));
+      HHG_TRY(read_scalar(m, m->global.scalar, &v, s));
+    } else {
+      HHG_TRY(vcycle_T<double>(m, m->d64, m->global, pre, post, cg_rtol, cg_maxit, s));
+      HHG_TRY(norm2_async(m, m->global, s));
+      HHG_TRY(read_scalar(m, m->global.scalar, &v, s));
+    }
+    ++k;
+    rel = r0 > 0 ? std::sqrt(v) / r0 : 0.0;
+    push(rel);
+    if (faulty && k == o->fault_cycle) {
+      HHG_TRY(inject(m, s));
+      if (o->recovery != HHG_RECOVERY_NONE) {
+        const int n_global = o->recovery == HHG_RECOVERY_DD ? o->n_global : 0;
+        int n_local = o->n_local;
+        if (n_local <= 0 && o->recovery == HHG_RECOVERY_DD) n_local = (int)std::ceil(o->eta * o->n_global);
+        HHG_TRY(recover(m, n_local, n_global, mixed, pre, post, cg_rtol, cg_maxit, nullptr, nullptr, s));
+      }
+      if (mixed) HHG_TRY(ir_residual(m, m->global, s));
+      else HHG_TRY(norm2_async(m, m->global, s));
+      HHG_TRY(read_scalar(m, m->global.scalar, &v, s));
+      rel = r0 > 0 ? std::sqrt(v) / r0 : 0.0;
+      push(rel);
+    }
+    if (rel <= o->rtol) break;
+  }
+  if (n_hist) *n_hist = nh;
+  if (cycles) *cycles = k;
+  if (rel > o->rtol) return fail(HHG_ERR_NOT_CONVERGED, "rtol not reached within max_cycles");
+  return HHG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,225 @@
+// Internal structures of the HHG library: the blocked per-macro layout, the
+// interface (face / edge / vertex) containers, per-problem work lists, and the
+// declarations shared by the host mesh builder and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <atomic>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace hhg {
+
+// Kernel launches issued by the library (all meshes, all streams).
+extern std::atomic<long long> g_kernel_launches;
+
+// ---------------------------------------------------------------------------
+// 15-point stencil directions in a macro-tetrahedron's local lattice.
+//
+// Local node (i, j, k), i, j, k >= 0, i + j + k <= N, sits at
+// V0 + (i (V1 - V0) + j (V2 - V0) + k (V3 - V0)) / N.  In "chain" coordinates
+// (a, b, c) = (i + j + k, j + k, k) the macro is the Kuhn simplex
+// N >= a >= b >= c >= 0 and its uniform (Bey) refinement is the Freudenthal
+// triangulation of the chain lattice, whose edges are the 7 non-zero 0/1
+// chain vectors.  Index 0 is the centre, 1..7 those chain vectors mapped to
+// (di, dj, dk) = (da - db, db - dc, dc), 8..14 their negatives.
+// ---------------------------------------------------------------------------
+constexpr int NDIR = 15;
+
+__host__ __device__ __forceinline__ void dir_ijk(int d, int& di, int& dj, int& dk) {
+  // chain (1,0,0) (0,1,0) (0,0,1) (1,1,0) (0,1,1) (1,0,1) (1,1,1)
+  int s = 1;
+  if (d > 7) { s = -1; d -= 7; }
+  switch (d) {
+    case 1: di = 1;  dj = 0;  dk = 0; break;
+    case 2: di = -1; dj = 1;  dk = 0; break;
+    case 3: di = 0;  dj = -1; dk = 1; break;
+    case 4: di = 0;  dj = 1;  dk = 0; break;
+    case 5: di = -1; dj = 0;  dk = 1; break;
+    case 6: di = 1;  dj = -1; dk = 1; break;
+    case 7: di = 0;  dj = 0;  dk = 1; break;
+    default: di = 0; dj = 0; dk = 0; s = 1; break;
+  }
+  di *= s; dj *= s; dk *= s;
+}
+
+// Node class of a local lattice node: bit 0: k == 0, bit 1: j == 0,
+// bit 2: i == 0, bit 3: i + j + k == N (the four faces of the macro).
+// 0 = volume interior, one bit = face, two = edge, three = vertex.
+__host__ __device__ __forceinline__ int node_class(int i, int j, int k, int N) {
+  return (k == 0) | ((j == 0) << 1) | ((i == 0) << 2) | ((i + j + k == N) << 3);
+}
+
+__host__ __device__ __forceinline__ bool in_lattice(int i, int j, int k, int N) {
+  return i >= 0 && j >= 0 && k >= 0 && i + j + k <= N;
+}
+
+// ---------------------------------------------------------------------------
+// Blocked colour-split layout of one macro's closed lattice at refinement N.
+// The colour of node (i, j, k) is (i + 2j + 3k) mod 4, equal to (x + y + z)
+// mod 4 of its global grid coordinates.  Slice k holds rows j = 0..N-k; each
+// row is stored as four colour segments of P slots; node i of colour c sits
+// in slot i >> 2 of segment c.  A multicolour sweep of one colour therefore
+// reads and writes contiguous slots.
+// ---------------------------------------------------------------------------
+__host__ __device__ __forceinline__ int slots_per_row(int N) {
+  int p = (N + 1 + 3) / 4;
+  return (p + 7) & ~7;
+}
+
+__host__ __device__ __forceinline__ int64_t slice_off(int N, int P, int k) {
+  return 4LL * P * ((int64_t)k * (N + 1) - (int64_t)k * (k - 1) / 2);
+}
+
+__host__ __device__ __forceinline__ int64_t lidx(int N, int P, int i, int j, int k) {
+  int c = (i + 2 * j + 3 * k) & 3;
+  return slice_off(N, P, k) + (int64_t)(4 * j + c) * P + (i >> 2);
+}
+
+inline int64_t block_elems(int N) {
+  int P = slots_per_row(N);
+  int64_t n = slice_off(N, P, N + 1);
+  return (n + 63) & ~int64_t(63);
+}
+
+// Work tile of the volume kernels: 8 rows (j0..j0+7) x 32 slots (m0..m0+31)
+// of slice k.
+struct Tile {
+  int k, j0, m0, pad;
+};
+constexpr int TILE_ROWS = 8;
+constexpr int TILE_SLOTS = 32;
+
+// A copy of an interface node inside one macro block.
+struct Copy {
+  int macro, i, j, k;
+};
+
+// Macro geometry used by device kernels: global fine coordinates of local
+// node (i, j, k) at refinement N are N * v0 + i * e1 + j * e2 + k * e3.
+struct MacroGeo {
+  int v0[3], e1[3], e2[3], e3[3];
+};
+
+// ---------------------------------------------------------------------------
+// Host-side mesh description (built by mesh.cpp).
+// ---------------------------------------------------------------------------
+struct HostLevel {
+  int r = 0, N = 0, P = 0;
+  int64_t block = 0;
+  int n_if = 0;
+  std::vector<int64_t> if_gid;        // global grid id of each interface node
+  std::vector<int> if_cptr;           // copies CSR
+  std::vector<Copy> if_copy;
+  std::vector<unsigned char> if_colour, if_dirichlet;
+  std::vector<double> W;              // [n_macro][16][15] stencil weights
+  std::vector<Tile> tiles_int;        // tiles covering the volume interior
+  std::vector<Tile> tiles_all;        // tiles covering the closed lattice
+};
+
+struct HostMesh {
+  int sub[3] = {0, 0, 0};
+  int R = 0, r0 = 2;
+  int n_macro = 0;
+  int64_t nx = 0, ny = 0, nz = 0;     // finest-level intervals per axis
+  std::vector<MacroGeo> geo;
+  std::vector<double> coeff;
+  double G[9];
+  std::vector<HostLevel> lv;          // index 0 = coarsest (r0)
+  std::vector<std::vector<int>> node_macros;   // not used on device
+  bool seven_point = false;           // all volume stencils have only the 6
+                                      // chain-axis neighbours non-zero
+};
+
+// Problem: which nodes are unknowns.  kind 0 = global, 1 = faulty sub-domain,
+// 2 = healthy sub-domain (interface frozen).
+struct HostProblemLevel {
+  std::vector<int> free_if;           // free interface nodes grouped by colour
+  int col_off[5] = {0, 0, 0, 0, 0};
+  std::vector<int64_t> zero_off;      // frozen copies in active blocks
+  std::vector<int64_t> gather;        // [free_if.size()][15] fine offsets of the
+                                      // restriction onto this level (-1 = none)
+};
+
+struct HostProblem {
+  int kind = 0;
+  std::vector<int> act;               // active macros
+  std::vector<unsigned char> macro_active;
+  std::vector<HostProblemLevel> lv;
+  // coarse CG (level 0): compact free nodes
+  int n_cg = 0;
+  std::vector<int> rowptr, col;
+  std::vector<double> val;
+  std::vector<int64_t> fsrc;          // >= 0: block offset of f; < 0: -1 - master
+  std::vector<int> uptr;              // scatter CSR
+  std::vector<int64_t> udst;          // block offsets to write
+  std::vector<int> umaster;           // master index or -1
+};
+
+void build_host_mesh(HostMesh& m, const int sub[3], int R, int r0, const double* coeff,
+                     const double* affine);
+// open: all adjacent macros faulty (and not Dirichlet); closed: any faulty.
+void build_problem(const HostMesh& m, int kind, const std::vector<unsigned char>& faulty,
+                   HostProblem& p);
+bool macro_in_set(const std::vector<unsigned char>& s, int m);
+
+// ---------------------------------------------------------------------------
+// Device-side structures.
+// ---------------------------------------------------------------------------
+template <class T>
+struct DevLevel {
+  int N = 0, P = 0;
+  int64_t block = 0;
+  int n_if = 0;
+  T* u = nullptr;   // blocks [n_macro * block]
+  T* f = nullptr;
+  T* r = nullptr;
+  T* uI = nullptr;  // interface masters [n_if]
+  T* fI = nullptr;
+  T* W = nullptr;   // [n_macro][16][15]
+};
+
+struct DevLevelTables {
+  int64_t* if_gid = nullptr;
+  int* if_cptr = nullptr;
+  Copy* if_copy = nullptr;
+  Tile* tiles_int = nullptr;
+  int n_tiles_int = 0;
+  Tile* tiles_all = nullptr;
+  int n_tiles_all = 0;
+};
+
+struct DevProblemLevel {
+  int* free_if = nullptr;
+  int col_off[5] = {0, 0, 0, 0, 0};
+  int64_t* zero_off = nullptr;
+  int n_zero = 0;
+  int64_t* gather = nullptr;
+};
+
+struct DevProblem {
+  int kind = 0;
+  int* act = nullptr;
+  int n_act = 0;
+  std::vector<int> act_host;
+  std::vector<DevProblemLevel> lv;
+  int n_cg = 0;
+  int* rowptr = nullptr;
+  int* col = nullptr;
+  double* val = nullptr;
+  int64_t* fsrc = nullptr;
+  int* uptr = nullptr;
+  int64_t* udst = nullptr;
+  int* umaster = nullptr;
+  double* cg_work = nullptr;        // 4 * n_cg scratch
+  double* partial = nullptr;        // per-CTA partial sums of the norm
+  int n_partial = 0;
+  double* scalar = nullptr;         // [4]: norm^2 result, cg info
+  int* cg_iters = nullptr;
+  cudaStream_t stream = nullptr;    // stream owned by the problem (DD half)
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+};
+
+}  // namespace hhg

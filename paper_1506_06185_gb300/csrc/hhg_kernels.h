@@ -1,0 +1,98 @@
+// Launchers of the HHG CUDA kernels (kernels.cu).  T is the arithmetic type of
+// the cycle (double, or float for the inner cycles of mixed-precision
+// iterative refinement).
+#pragma once
+
+#include "hhg_internal.h"
+
+namespace hhg {
+
+struct LevelArgs {
+  int N, P;
+  int64_t block;
+  const int64_t* if_gid;
+  const int* cptr;
+  const Copy* cps;
+  const Tile* tiles_int;
+  int n_tiles_int;
+  const Tile* tiles_all;
+  int n_tiles_all;
+};
+
+struct ProbArgs {
+  const int* act;
+  int n_act;
+  const int* free_if;
+  int col_off[5];
+  const int64_t* zero_off;
+  int n_zero;
+  const int64_t* gather;
+};
+
+// One colour of multicolour Gauss-Seidel on the volume interiors and the free
+// interface nodes of a problem.
+// If ev_begin / ev_end are not null they are recorded on s right before and
+// after the volume kernel (profiling of the dominant kernel).
+template <class T>
+cudaError_t gs_colour(const LevelArgs& L, const ProbArgs& p, T* u, T* uI, const T* f, const T* fI,
+                      const T* W, const T* Winv, int colour, bool seven_point, cudaStream_t s,
+                      cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
+
+// r = f - A u on the free nodes (written to the blocks' r), zero at the
+// problem's frozen copies.  If partial != NULL each CTA also writes its
+// partial sum of r^2 (volume CTAs first, then interface CTAs) and write_r may
+// be false (norm only).  Returns the number of partials written in *n_part.
+template <class T>
+cudaError_t residual(const LevelArgs& L, const ProbArgs& p, const T* u, const T* uI, const T* f,
+                     const T* fI, T* r, const T* W, bool seven_point, bool write_r, double* partial,
+                     int* n_part, cudaStream_t s);
+
+// Coarse right-hand side f_c = P^T r_f on the free coarse nodes; the coarse
+// correction u_c is set to zero on the problem's nodes of the coarse level.
+template <class T>
+cudaError_t restrict_to(const LevelArgs& C, const LevelArgs& F, const ProbArgs& pc, const T* rf, T* fc,
+                        T* fIc, T* uc, T* uIc, cudaStream_t s);
+
+// u_f += P u_c on the free fine nodes.
+template <class T>
+cudaError_t prolong_add(const LevelArgs& F, const LevelArgs& C, const ProbArgs& pf, T* uf, T* uIf,
+                        const T* uc, cudaStream_t s);
+
+// Coarse CG (FP64) on the compact free nodes of level 0; reads the level's
+// right-hand side (type T), writes the solution into u / uI.
+template <class T>
+cudaError_t coarse_cg(const DevProblem& p, const T* f, const T* fI, T* u, T* uI, double rtol, int maxit,
+                      cudaStream_t s);
+
+cudaError_t reduce_partials(const double* partial, int n, double* out, cudaStream_t s);
+
+// Global vector <-> blocked storage of one level.
+template <class T>
+cudaError_t import_vec(const LevelArgs& L, const MacroGeo* geo, int n_macro, int64_t nx, int64_t ny,
+                       const double* g, T* blocks, T* masters, bool closed, cudaStream_t s);
+template <class T>
+cudaError_t export_vec(const LevelArgs& L, const MacroGeo* geo, int n_macro, int64_t nx, int64_t ny,
+                       const T* blocks, const T* masters, double* g, cudaStream_t s);
+
+template <class T>
+cudaError_t import_masters(const int64_t* gid, int n, const double* g, T* m, cudaStream_t s);
+template <class T>
+cudaError_t export_masters(const int64_t* gid, int n, const T* m, double* g, cudaStream_t s);
+
+// Fault support.
+cudaError_t set_masters_zero(double* uI, const int* ids, int n, cudaStream_t s);
+cudaError_t restore_copies(double* u, const double* uI, const int64_t* off, const int* master, int n,
+                           cudaStream_t s);
+
+// Mixed precision: fine FP64 residual written as the FP32 right-hand side of
+// the correction problem (blocks and masters), with its norm partials.
+cudaError_t residual_to_f32(const LevelArgs& L, const ProbArgs& p, const double* u, const double* uI,
+                            const double* f, const double* fI, float* f32, float* fI32, const double* W,
+                            bool seven_point, double* partial, int* n_part, cudaStream_t s);
+// u64 += e32 on the free nodes (volume interiors and interface masters + copies).
+cudaError_t add_correction(const LevelArgs& L, const ProbArgs& p, double* u, double* uI, const float* e,
+                           const float* eI, cudaStream_t s);
+template <class T>
+cudaError_t zero_problem_blocks(const LevelArgs& L, const ProbArgs& p, T* u, T* uI, cudaStream_t s);
+
+}  // namespace hhg

@@ -1,0 +1,449 @@
+// Host-side construction of the macro mesh, its refinement levels, the
+// per-macro stencils and the interface containers (§2.1 base mesh and
+// uniform refinement; §3.1 volume / face / edge / vertex containers; §3.2 and
+// Fig. 4: a node on a macro face, edge or vertex gets its stencil as the sum
+// of the sub-stencils of the macros around it).
+#include <algorithm>
+#include <array>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <stdexcept>
+#include <unordered_map>
+
+#include "hhg_internal.h"
+
+namespace hhg {
+
+namespace {
+
+const int PERM[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+
+struct Prim {
+  int type = 0;                         // 0 vertex, 1 edge, 2 face
+  std::vector<int> gv;                  // sorted global vertex ids
+  std::vector<std::array<int, 3>> X;    // their integer sub-cube coordinates
+  std::vector<std::pair<int, std::array<int, 3>>> adj;  // (macro, local vertex of gv[t])
+  bool boundary = false;
+};
+
+int64_t grid_gid(const HostMesh& m, int N, int64_t x, int64_t y, int64_t z) {
+  int64_t nx = (int64_t)m.sub[0] * N, ny = (int64_t)m.sub[1] * N;
+  return (z * (ny + 1) + y) * (nx + 1) + x;
+}
+
+void local_to_fine(const MacroGeo& g, int N, int i, int j, int k, int64_t X[3]) {
+  for (int a = 0; a < 3; ++a)
+    X[a] = (int64_t)N * g.v0[a] + (int64_t)i * g.e1[a] + (int64_t)j * g.e2[a] + (int64_t)k * g.e3[a];
+}
+
+int64_t node_gid(const HostMesh& m, int macro, int N, int i, int j, int k) {
+  int64_t X[3];
+  local_to_fine(m.geo[macro], N, i, j, k, X);
+  return grid_gid(m, N, X[0], X[1], X[2]);
+}
+
+// Physical position of a local lattice node of a macro at refinement N.
+void position(const HostMesh& m, int macro, int N, int i, int j, int k, double out[3]) {
+  int64_t X[3];
+  local_to_fine(m.geo[macro], N, i, j, k, X);
+  double p[3] = {double(X[0]) / (double(m.sub[0]) * N), double(X[1]) / (double(m.sub[1]) * N),
+                 double(X[2]) / (double(m.sub[2]) * N)};
+  for (int a = 0; a < 3; ++a) out[a] = m.G[3 * a] * p[0] + m.G[3 * a + 1] * p[1] + m.G[3 * a + 2] * p[2];
+}
+
+// P1 stiffness of one tetrahedron with unit coefficient: gradients of the
+// barycentric coordinates from the inverse edge matrix, times the volume.
+void tet_stiffness(const double X[4][3], double K[4][4]) {
+  double E[3][3];
+  for (int q = 0; q < 3; ++q)
+    for (int a = 0; a < 3; ++a) E[a][q] = X[q + 1][a] - X[0][a];
+  double det = E[0][0] * (E[1][1] * E[2][2] - E[1][2] * E[2][1]) -
+               E[0][1] * (E[1][0] * E[2][2] - E[1][2] * E[2][0]) +
+               E[0][2] * (E[1][0] * E[2][1] - E[1][1] * E[2][0]);
+  double inv[3][3];
+  inv[0][0] = (E[1][1] * E[2][2] - E[1][2] * E[2][1]) / det;
+  inv[0][1] = (E[0][2] * E[2][1] - E[0][1] * E[2][2]) / det;
+  inv[0][2] = (E[0][1] * E[1][2] - E[0][2] * E[1][1]) / det;
+  inv[1][0] = (E[1][2] * E[2][0] - E[1][0] * E[2][2]) / det;
+  inv[1][1] = (E[0][0] * E[2][2] - E[0][2] * E[2][0]) / det;
+  inv[1][2] = (E[0][2] * E[1][0] - E[0][0] * E[1][2]) / det;
+  inv[2][0] = (E[1][0] * E[2][1] - E[1][1] * E[2][0]) / det;
+  inv[2][1] = (E[0][1] * E[2][0] - E[0][0] * E[2][1]) / det;
+  inv[2][2] = (E[0][0] * E[1][1] - E[0][1] * E[1][0]) / det;
+  double D[4][3];
+  for (int a = 0; a < 3; ++a) {
+    D[1][a] = inv[0][a];
+    D[2][a] = inv[1][a];
+    D[3][a] = inv[2][a];
+    D[0][a] = -(inv[0][a] + inv[1][a] + inv[2][a]);
+  }
+  double vol = std::fabs(det) / 6.0;
+  for (int p = 0; p < 4; ++p)
+    for (int q = 0; q < 4; ++q) K[p][q] = vol * (D[p][0] * D[q][0] + D[p][1] * D[q][1] + D[p][2] * D[q][2]);
+}
+
+int dir_index(int di, int dj, int dk) {
+  for (int d = 0; d < NDIR; ++d) {
+    int a, b, c;
+    dir_ijk(d, a, b, c);
+    if (a == di && b == dj && c == dk) return d;
+  }
+  return -1;
+}
+
+// Representative local node of a node class at refinement N (N >= 4).
+bool class_representative(int mask, int N, int& i, int& j, int& k) {
+  bool k0 = mask & 1, j0 = mask & 2, i0 = mask & 4, top = mask & 8;
+  if (mask == 15) return false;
+  i = i0 ? 0 : 1;
+  j = j0 ? 0 : 1;
+  k = k0 ? 0 : 1;
+  if (top) {
+    if (!i0) i = N - j - k;
+    else if (!j0) j = N - k;
+    else if (!k0) k = N;
+    else return false;
+  }
+  if (!in_lattice(i, j, k, N) || node_class(i, j, k, N) != mask) return false;
+  return true;
+}
+
+// Sub-stencil of macro `macro` at a node of class `mask`: the sum over the
+// fine tetrahedra of the macro that contain the node (Kuhn simplices of the
+// chain lattice inside N >= a >= b >= c >= 0) of their element stiffness row.
+void class_weights(const HostMesh& m, int macro, int N, int mask, double w[NDIR]) {
+  for (int d = 0; d < NDIR; ++d) w[d] = 0.0;
+  int i, j, k;
+  if (!class_representative(mask, N, i, j, k)) return;
+  const int pa = i + j + k, pb = j + k, pc = k;
+  const double kT = m.coeff[macro];
+  for (int o = 0; o < 8; ++o) {
+    const int oa = o & 1, ob = (o >> 1) & 1, oc = (o >> 2) & 1;
+    const int ca = pa - oa, cb = pb - ob, cc = pc - oc;
+    for (int s = 0; s < 6; ++s) {
+      int V[4][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}, {1, 1, 1}};
+      V[1][PERM[s][0]] = 1;
+      V[2][PERM[s][0]] = 1;
+      V[2][PERM[s][1]] = 1;
+      int self = -1;
+      for (int q = 0; q < 4; ++q)
+        if (V[q][0] == oa && V[q][1] == ob && V[q][2] == oc) self = q;
+      if (self < 0) continue;
+      bool inside = true;
+      double X[4][3];
+      int L[4][3];
+      for (int q = 0; q < 4; ++q) {
+        int a = ca + V[q][0], b = cb + V[q][1], c = cc + V[q][2];
+        if (!(N >= a && a >= b && b >= c && c >= 0)) { inside = false; break; }
+        L[q][0] = a - b;
+        L[q][1] = b - c;
+        L[q][2] = c;
+        position(m, macro, N, L[q][0], L[q][1], L[q][2], X[q]);
+      }
+      if (!inside) continue;
+      double K[4][4];
+      tet_stiffness(X, K);
+      for (int q = 0; q < 4; ++q) {
+        int d = dir_index(L[q][0] - i, L[q][1] - j, L[q][2] - k);
+        if (d < 0) throw std::runtime_error("stencil direction outside the 15-point set");
+        w[d] += kT * K[self][q];
+      }
+    }
+  }
+}
+
+void build_tiles(int N, bool interior, std::vector<Tile>& out) {
+  out.clear();
+  const int lo = interior ? 1 : 0;
+  const int top = interior ? N - 1 : N;     // i + j + k <= top
+  for (int k = lo; k <= top; ++k) {
+    int jmax = top - k - lo;                // need i >= lo
+    for (int j0 = lo; j0 <= jmax; j0 += TILE_ROWS) {
+      int imax = top - j0 - k;
+      int mmax = imax >> 2;
+      for (int m0 = 0; m0 <= mmax; m0 += TILE_SLOTS) out.push_back(Tile{k, j0, m0, 0});
+    }
+  }
+}
+
+}  // namespace
+
+bool macro_in_set(const std::vector<unsigned char>& s, int m) { return m >= 0 && m < (int)s.size() && s[m]; }
+
+void build_host_mesh(HostMesh& m, const int sub[3], int R, int r0, const double* coeff,
+                     const double* affine) {
+  for (int a = 0; a < 3; ++a) m.sub[a] = sub[a];
+  m.R = R;
+  m.r0 = r0;
+  m.n_macro = 6 * sub[0] * sub[1] * sub[2];
+  const int N_f = 1 << R;
+  m.nx = (int64_t)sub[0] * N_f;
+  m.ny = (int64_t)sub[1] * N_f;
+  m.nz = (int64_t)sub[2] * N_f;
+  for (int a = 0; a < 9; ++a) m.G[a] = affine ? affine[a] : (a % 4 == 0 ? 1.0 : 0.0);
+  m.coeff.assign(m.n_macro, 1.0);
+  if (coeff)
+    for (int t = 0; t < m.n_macro; ++t) m.coeff[t] = coeff[t];
+
+  // macro-tetrahedra: sub-cube (a, b, c), x fastest, six Kuhn types each
+  m.geo.resize(m.n_macro);
+  std::vector<std::array<std::array<int, 3>, 4>> V(m.n_macro);
+  for (int c = 0; c < sub[2]; ++c)
+    for (int b = 0; b < sub[1]; ++b)
+      for (int a = 0; a < sub[0]; ++a)
+        for (int p = 0; p < 6; ++p) {
+          int t = ((c * sub[1] + b) * sub[0] + a) * 6 + p;
+          std::array<int, 3> v0 = {a, b, c}, v1 = v0, v2, v3 = {a + 1, b + 1, c + 1};
+          v1[PERM[p][0]] += 1;
+          v2 = v1;
+          v2[PERM[p][1]] += 1;
+          V[t] = {v0, v1, v2, v3};
+          for (int q = 0; q < 3; ++q) {
+            m.geo[t].v0[q] = v0[q];
+            m.geo[t].e1[q] = v1[q] - v0[q];
+            m.geo[t].e2[q] = v2[q] - v0[q];
+            m.geo[t].e3[q] = v3[q] - v0[q];
+          }
+        }
+  auto vid = [&](const std::array<int, 3>& x) { return (x[2] * (sub[1] + 1) + x[1]) * (sub[0] + 1) + x[0]; };
+
+  // interface primitives (faces, edges, vertices) with their adjacent macros
+  std::map<std::vector<int>, int> key;
+  std::vector<Prim> prims;
+  auto add = [&](int t, const std::vector<int>& loc) {
+    std::vector<std::pair<int, int>> gl;
+    for (int l : loc) gl.push_back({vid(V[t][l]), l});
+    std::sort(gl.begin(), gl.end());
+    std::vector<int> g;
+    for (auto& x : gl) g.push_back(x.first);
+    auto it = key.find(g);
+    int id;
+    if (it == key.end()) {
+      id = (int)prims.size();
+      key[g] = id;
+      Prim pr;
+      pr.type = (int)loc.size() - 1;
+      pr.gv = g;
+      for (auto& x : gl) pr.X.push_back(V[t][x.second]);
+      prims.push_back(pr);
+    } else {
+      id = it->second;
+    }
+    std::array<int, 3> lv = {-1, -1, -1};
+    for (size_t q = 0; q < gl.size(); ++q) lv[q] = gl[q].second;
+    prims[id].adj.push_back({t, lv});
+  };
+  for (int t = 0; t < m.n_macro; ++t) {
+    for (int q = 0; q < 4; ++q) add(t, {q});
+    for (int q = 0; q < 4; ++q)
+      for (int s = q + 1; s < 4; ++s) add(t, {q, s});
+    for (int o = 0; o < 4; ++o) {
+      std::vector<int> loc;
+      for (int q = 0; q < 4; ++q)
+        if (q != o) loc.push_back(q);
+      add(t, loc);
+    }
+  }
+  for (auto& pr : prims) {
+    for (int a = 0; a < 3 && !pr.boundary; ++a)
+      for (int side : {0, sub[a]}) {
+        bool all = true;
+        for (auto& x : pr.X) all = all && (x[a] == side);
+        if (all) pr.boundary = true;
+      }
+  }
+  std::vector<int> order(prims.size());
+  for (size_t q = 0; q < prims.size(); ++q) order[q] = (int)q;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return prims[a].type < prims[b].type; });
+
+  m.lv.clear();
+  m.seven_point = true;
+  for (int r = r0; r <= R; ++r) {
+    HostLevel L;
+    L.r = r;
+    L.N = 1 << r;
+    L.P = slots_per_row(L.N);
+    L.block = block_elems(L.N);
+    const int N = L.N;
+    // stencils
+    L.W.assign((size_t)m.n_macro * 16 * NDIR, 0.0);
+    for (int t = 0; t < m.n_macro; ++t)
+      for (int mask = 0; mask < 15; ++mask) class_weights(m, t, N, mask, &L.W[((size_t)t * 16 + mask) * NDIR]);
+    for (int t = 0; t < m.n_macro; ++t) {
+      const double* w = &L.W[(size_t)t * 16 * NDIR];
+      for (int d = 1; d < NDIR; ++d) {
+        int dd = d > 7 ? d - 7 : d;
+        if (dd > 3 && w[d] != 0.0) m.seven_point = false;
+      }
+    }
+    // interface nodes: vertices, edges, faces
+    L.if_cptr.push_back(0);
+    for (int id : order) {
+      const Prim& pr = prims[id];
+      const int nv = (int)pr.gv.size();
+      std::vector<std::array<int, 3>> alphas;
+      if (nv == 1) alphas.push_back({N, 0, 0});
+      if (nv == 2)
+        for (int a = 1; a <= N - 1; ++a) alphas.push_back({a, N - a, 0});
+      if (nv == 3)
+        for (int a = 1; a <= N - 2; ++a)
+          for (int b = 1; a + b <= N - 1; ++b) alphas.push_back({a, b, N - a - b});
+      for (auto& al : alphas) {
+        int64_t X[3] = {0, 0, 0};
+        for (int q = 0; q < nv; ++q)
+          for (int a = 0; a < 3; ++a) X[a] += (int64_t)al[q] * pr.X[q][a];
+        L.if_gid.push_back(grid_gid(m, N, X[0], X[1], X[2]));
+        L.if_colour.push_back((unsigned char)((X[0] + X[1] + X[2]) & 3));
+        L.if_dirichlet.push_back(pr.boundary ? 1 : 0);
+        for (auto& ad : pr.adj) {
+          int lam[4] = {0, 0, 0, 0};
+          for (int q = 0; q < nv; ++q) lam[ad.second[q]] = al[q];
+          Copy cp{ad.first, lam[1], lam[2], lam[3]};
+          if (((cp.i + 2 * cp.j + 3 * cp.k) & 3) != L.if_colour.back())
+            throw std::runtime_error("inconsistent colouring across macros");
+          L.if_copy.push_back(cp);
+        }
+        L.if_cptr.push_back((int)L.if_copy.size());
+      }
+    }
+    L.n_if = (int)L.if_gid.size();
+    build_tiles(N, true, L.tiles_int);
+    build_tiles(N, false, L.tiles_all);
+    m.lv.push_back(std::move(L));
+  }
+}
+
+void build_problem(const HostMesh& m, int kind, const std::vector<unsigned char>& faulty, HostProblem& p) {
+  p = HostProblem();
+  p.kind = kind;
+  p.macro_active.assign(m.n_macro, 0);
+  for (int t = 0; t < m.n_macro; ++t) {
+    bool f = macro_in_set(faulty, t);
+    bool a = kind == 0 ? true : (kind == 1 ? f : !f);
+    p.macro_active[t] = a;
+    if (a) p.act.push_back(t);
+  }
+  const int nl = (int)m.lv.size();
+  p.lv.resize(nl);
+  std::vector<std::vector<unsigned char>> is_free(nl);
+  for (int l = 0; l < nl; ++l) {
+    const HostLevel& L = m.lv[l];
+    HostProblemLevel& P = p.lv[l];
+    is_free[l].assign(L.n_if, 0);
+    std::vector<int> bycol[4];
+    for (int n = 0; n < L.n_if; ++n) {
+      bool any_f = false, all_f = true;
+      for (int c = L.if_cptr[n]; c < L.if_cptr[n + 1]; ++c) {
+        bool f = macro_in_set(faulty, L.if_copy[c].macro);
+        any_f = any_f || f;
+        all_f = all_f && f;
+      }
+      bool fr = !L.if_dirichlet[n];
+      if (kind == 1) fr = fr && all_f;
+      if (kind == 2) fr = fr && !any_f;
+      is_free[l][n] = fr;
+      if (fr) {
+        bycol[L.if_colour[n]].push_back(n);
+      } else {
+        for (int c = L.if_cptr[n]; c < L.if_cptr[n + 1]; ++c) {
+          const Copy& cp = L.if_copy[c];
+          if (p.macro_active[cp.macro])
+            P.zero_off.push_back((int64_t)cp.macro * L.block + lidx(L.N, L.P, cp.i, cp.j, cp.k));
+        }
+      }
+    }
+    P.col_off[0] = 0;
+    for (int c = 0; c < 4; ++c) {
+      P.free_if.insert(P.free_if.end(), bycol[c].begin(), bycol[c].end());
+      P.col_off[c + 1] = (int)P.free_if.size();
+    }
+  }
+  // restriction gathers onto every level below the finest
+  for (int l = 0; l + 1 < nl; ++l) {
+    const HostLevel& C = m.lv[l];
+    const HostLevel& F = m.lv[l + 1];
+    HostProblemLevel& P = p.lv[l];
+    P.gather.assign(P.free_if.size() * NDIR, -1);
+    for (size_t q = 0; q < P.free_if.size(); ++q) {
+      int n = P.free_if[q];
+      std::vector<int64_t> seen;
+      int cnt = 0;
+      for (int c = C.if_cptr[n]; c < C.if_cptr[n + 1]; ++c) {
+        const Copy& cp = C.if_copy[c];
+        if (!p.macro_active[cp.macro]) continue;
+        for (int d = 0; d < NDIR; ++d) {
+          int di, dj, dk;
+          dir_ijk(d, di, dj, dk);
+          int fi = 2 * cp.i + di, fj = 2 * cp.j + dj, fk = 2 * cp.k + dk;
+          if (!in_lattice(fi, fj, fk, F.N)) continue;
+          int64_t g = node_gid(m, cp.macro, F.N, fi, fj, fk);
+          if (std::find(seen.begin(), seen.end(), g) != seen.end()) continue;
+          seen.push_back(g);
+          if (cnt >= NDIR) throw std::runtime_error("restriction stencil has more than 15 points");
+          int64_t off = (int64_t)cp.macro * F.block + lidx(F.N, F.P, fi, fj, fk);
+          // the centre (the coarse node itself, weight 1) comes first; the 14
+          // edge midpoints follow (weight 1/2)
+          if (d == 0 && cnt != 0) throw std::runtime_error("restriction centre not first");
+          P.gather[q * NDIR + cnt] = off;
+          ++cnt;
+        }
+      }
+      if (cnt != NDIR) throw std::runtime_error("restriction stencil incomplete");
+    }
+  }
+  // coarse-level CG system on the compact free nodes of level 0
+  {
+    const HostLevel& L = m.lv[0];
+    const int N = L.N;
+    std::unordered_map<int64_t, int> cidx;
+    struct Dof { std::vector<Copy> cps; int master; };
+    std::vector<Dof> dofs;
+    for (int t : p.act)
+      for (int k = 1; k <= N - 3; ++k)
+        for (int j = 1; j + k <= N - 2; ++j)
+          for (int i = 1; i + j + k <= N - 1; ++i) {
+            cidx[node_gid(m, t, N, i, j, k)] = (int)dofs.size();
+            dofs.push_back(Dof{{Copy{t, i, j, k}}, -1});
+          }
+    for (int n : p.lv[0].free_if) {
+      Dof d;
+      d.master = n;
+      for (int c = L.if_cptr[n]; c < L.if_cptr[n + 1]; ++c) d.cps.push_back(L.if_copy[c]);
+      cidx[L.if_gid[n]] = (int)dofs.size();
+      dofs.push_back(d);
+    }
+    p.n_cg = (int)dofs.size();
+    p.rowptr.push_back(0);
+    p.uptr.push_back(0);
+    for (auto& d : dofs) {
+      std::map<int, double> row;
+      for (const Copy& cp : d.cps) {
+        int mask = node_class(cp.i, cp.j, cp.k, N);
+        const double* w = &L.W[((size_t)cp.macro * 16 + mask) * NDIR];
+        for (int e = 0; e < NDIR; ++e) {
+          if (w[e] == 0.0) continue;
+          int di, dj, dk;
+          dir_ijk(e, di, dj, dk);
+          int ni = cp.i + di, nj = cp.j + dj, nk = cp.k + dk;
+          if (!in_lattice(ni, nj, nk, N)) continue;
+          auto it = cidx.find(node_gid(m, cp.macro, N, ni, nj, nk));
+          if (it == cidx.end()) continue;
+          row[it->second] += w[e];
+        }
+        p.udst.push_back((int64_t)cp.macro * L.block + lidx(N, L.P, cp.i, cp.j, cp.k));
+      }
+      for (auto& kv : row) {
+        p.col.push_back(kv.first);
+        p.val.push_back(kv.second);
+      }
+      p.rowptr.push_back((int)p.col.size());
+      p.uptr.push_back((int)p.udst.size());
+      p.umaster.push_back(d.master);
+      if (d.master >= 0) p.fsrc.push_back(-1 - (int64_t)d.master);
+      else p.fsrc.push_back(p.udst.back());
+    }
+  }
+}
+
+}  // namespace hhg

@@ -1,0 +1,292 @@
+"""ctypes binding of the HHG C ABI (include/hhg.h).
+
+Argument marshalling only: every step of the multigrid path runs in the CUDA
+library.  The module-level functions carry the C names (``hhg_mesh_create``,
+``hhg_vcycle``, ...) and take the same arguments; :class:`Mesh` is a thin
+object wrapper over them.  Vectors may be torch tensors (CUDA or CPU) or
+numpy arrays of float64 in the global x-fastest node order.  If the shared
+library is missing the import of this module fails loudly: there is no CPU
+fallback.
+"""
+
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libhhg.so")
+
+HHG_OK, HHG_ERR_ARG, HHG_ERR_CUDA, HHG_ERR_OOM, HHG_ERR_TIMEOUT, HHG_ERR_NOT_CONVERGED, HHG_ERR_STATE = range(7)
+HHG_RECOVERY_NONE, HHG_RECOVERY_LR, HHG_RECOVERY_DD = 0, 1, 2
+
+EXPORTS = ["hhg_mesh_create", "hhg_mesh_destroy", "hhg_mesh_info", "hhg_mesh_bytes", "hhg_set_problem",
+           "hhg_get_solution", "hhg_vcycle", "hhg_residual_norm", "hhg_inject_fault", "hhg_recover_local",
+           "hhg_solve", "hhg_last_error", "hhg_profile_enable", "hhg_profile_read", "hhg_profile_info",
+           "hhg_launch_count"]
+
+
+class hhg_mesh_desc(C.Structure):
+    _fields_ = [("subcubes", C.c_int * 3), ("levels", C.c_int), ("coarsest", C.c_int), ("precision", C.c_int),
+                ("coeff", C.POINTER(C.c_double)), ("affine", C.POINTER(C.c_double))]
+
+
+class hhg_solve_opts(C.Structure):
+    _fields_ = [("rtol", C.c_double), ("max_cycles", C.c_int), ("pre", C.c_int), ("post", C.c_int),
+                ("fault_cycle", C.c_int), ("fault_ids", C.POINTER(C.c_int)), ("n_fault_ids", C.c_int),
+                ("recovery", C.c_int), ("n_local", C.c_int), ("n_global", C.c_int), ("eta", C.c_double),
+                ("mixed_precision", C.c_int), ("coarse_rtol", C.c_double), ("coarse_maxit", C.c_int)]
+
+
+class HHGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"HHG error {code}: {msg}")
+        self.code = code
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build the CUDA library first "
+                           "(python -m paper_1506_06185_gb300.build)")
+    lib = C.CDLL(path)
+    P = C.c_void_p
+    sig = {
+        "hhg_mesh_create": ([C.POINTER(hhg_mesh_desc), C.POINTER(P)], C.c_int),
+        "hhg_mesh_destroy": ([P], C.c_int),
+        "hhg_mesh_info": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int)], C.c_int),
+        "hhg_mesh_bytes": ([P, C.POINTER(C.c_int64)], C.c_int),
+        "hhg_set_problem": ([P, P, P, P], C.c_int),
+        "hhg_get_solution": ([P, P, P], C.c_int),
+        "hhg_vcycle": ([P, C.c_int, C.c_int, C.POINTER(C.c_double), P], C.c_int),
+        "hhg_residual_norm": ([P, C.POINTER(C.c_double), P], C.c_int),
+        "hhg_inject_fault": ([P, C.POINTER(C.c_int), C.c_int, P], C.c_int),
+        "hhg_recover_local": ([P, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
+                               C.POINTER(C.c_double), P], C.c_int),
+        "hhg_solve": ([P, C.POINTER(hhg_solve_opts), C.POINTER(C.c_double), C.POINTER(C.c_int),
+                       C.POINTER(C.c_int), P], C.c_int),
+        "hhg_last_error": ([C.c_char_p, C.c_size_t], C.c_int),
+        "hhg_profile_enable": ([P, C.c_int], C.c_int),
+        "hhg_profile_read": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_double)], C.c_int),
+        "hhg_profile_info": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_int)], C.c_int),
+        "hhg_launch_count": ([C.POINTER(C.c_int64)], C.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    return lib
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def _check(rc, allow=()):
+    if rc != HHG_OK and rc not in allow:
+        buf = C.create_string_buffer(1024)
+        lib().hhg_last_error(buf, 1024)
+        raise HHGError(rc, buf.value.decode(errors="replace"))
+    return rc
+
+
+def _ptr(x):
+    """Raw address of a torch tensor or numpy array (must be contiguous float64)."""
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        if str(x.dtype) != "torch.float64":
+            raise ValueError("tensor must be float64")
+        return C.c_void_p(x.data_ptr())
+    a = np.asarray(x)
+    if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("array must be C-contiguous float64")
+    return C.c_void_p(a.ctypes.data)
+
+
+def _stream(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return C.c_void_p(stream.cuda_stream)
+    return C.c_void_p(int(stream))
+
+
+def _ids(ids):
+    a = (C.c_int * len(ids))(*[int(i) for i in ids])
+    return a, len(ids)
+
+
+# --- C-named wrappers -------------------------------------------------------
+
+def hhg_mesh_create(subcubes, levels, coarsest=2, precision=64, coeff=None, affine=None):
+    d = hhg_mesh_desc()
+    d.subcubes[:] = [int(s) for s in subcubes]
+    d.levels, d.coarsest, d.precision = int(levels), int(coarsest), int(precision)
+    keep = []
+    if coeff is not None:
+        c = np.ascontiguousarray(coeff, dtype=np.float64)
+        keep.append(c)
+        d.coeff = c.ctypes.data_as(C.POINTER(C.c_double))
+    if affine is not None:
+        a = np.ascontiguousarray(np.asarray(affine, dtype=np.float64)[:3, :3])
+        keep.append(a)
+        d.affine = a.ctypes.data_as(C.POINTER(C.c_double))
+    h = C.c_void_p()
+    _check(lib().hhg_mesh_create(C.byref(d), C.byref(h)))
+    return h
+
+
+def hhg_mesh_destroy(h):
+    return _check(lib().hhg_mesh_destroy(h))
+
+
+def hhg_mesh_info(h):
+    a, b, c = C.c_int64(), C.c_int64(), C.c_int()
+    _check(lib().hhg_mesh_info(h, C.byref(a), C.byref(b), C.byref(c)))
+    return a.value, b.value, c.value
+
+
+def hhg_mesh_bytes(h):
+    a = C.c_int64()
+    _check(lib().hhg_mesh_bytes(h, C.byref(a)))
+    return a.value
+
+
+def hhg_set_problem(h, f=None, u0=None, stream=None):
+    return _check(lib().hhg_set_problem(h, _ptr(f), _ptr(u0), _stream(stream)))
+
+
+def hhg_get_solution(h, u, stream=None):
+    return _check(lib().hhg_get_solution(h, _ptr(u), _stream(stream)))
+
+
+def hhg_vcycle(h, pre=3, post=3, want_residual=True, stream=None):
+    r = C.c_double()
+    _check(lib().hhg_vcycle(h, int(pre), int(post), C.byref(r) if want_residual else None, _stream(stream)))
+    return r.value if want_residual else None
+
+
+def hhg_residual_norm(h, stream=None):
+    r = C.c_double()
+    _check(lib().hhg_residual_norm(h, C.byref(r), _stream(stream)))
+    return r.value
+
+
+def hhg_inject_fault(h, ids, stream=None):
+    a, n = _ids(ids)
+    return _check(lib().hhg_inject_fault(h, a, n, _stream(stream)))
+
+
+def hhg_recover_local(h, ids, n_local, n_global=0, timed=False, stream=None):
+    a, n = _ids(ids)
+    tl, tg = C.c_double(), C.c_double()
+    _check(lib().hhg_recover_local(h, a, n, int(n_local), int(n_global), C.byref(tl) if timed else None,
+                                   C.byref(tg) if timed else None, _stream(stream)))
+    return (tl.value, tg.value) if timed else None
+
+
+def hhg_solve(h, rtol=1e-8, max_cycles=50, pre=3, post=3, fault_cycle=0, fault_ids=(), recovery=0, n_local=0,
+              n_global=0, eta=1.0, mixed_precision=False, coarse_rtol=0.0, coarse_maxit=0, stream=None,
+              allow_not_converged=False):
+    o = hhg_solve_opts()
+    o.rtol, o.max_cycles, o.pre, o.post = float(rtol), int(max_cycles), int(pre), int(post)
+    ids, n = _ids(fault_ids) if len(fault_ids) else (None, 0)
+    o.fault_cycle = int(fault_cycle)
+    o.fault_ids = ids
+    o.n_fault_ids = n
+    o.recovery, o.n_local, o.n_global, o.eta = int(recovery), int(n_local), int(n_global), float(eta)
+    o.mixed_precision = 1 if mixed_precision else 0
+    o.coarse_rtol, o.coarse_maxit = float(coarse_rtol), int(coarse_maxit)
+    hist = (C.c_double * (int(max_cycles) + 2))()
+    nh, cyc = C.c_int(), C.c_int()
+    rc = lib().hhg_solve(h, C.byref(o), hist, C.byref(nh), C.byref(cyc), _stream(stream))
+    _check(rc, allow=(HHG_ERR_NOT_CONVERGED,) if allow_not_converged else ())
+    return np.array(hist[:nh.value]), cyc.value, rc
+
+
+def hhg_profile_enable(h, enable=True):
+    return _check(lib().hhg_profile_enable(h, 1 if enable else 0))
+
+
+def hhg_profile_read(h):
+    n, t = C.c_int64(), C.c_double()
+    _check(lib().hhg_profile_read(h, C.byref(n), C.byref(t)))
+    return n.value, t.value
+
+
+def hhg_profile_info(h):
+    n, s = C.c_int64(), C.c_int()
+    _check(lib().hhg_profile_info(h, C.byref(n), C.byref(s)))
+    return n.value, bool(s.value)
+
+
+def hhg_launch_count():
+    n = C.c_int64()
+    _check(lib().hhg_launch_count(C.byref(n)))
+    return n.value
+
+
+class Mesh:
+    """Owning wrapper of an ``hhg_mesh`` handle."""
+
+    def __init__(self, subcubes, levels, coarsest=2, precision=64, coeff=None, affine=None):
+        self.subcubes = tuple(int(s) for s in subcubes)
+        self.levels = int(levels)
+        self.h = hhg_mesh_create(subcubes, levels, coarsest, precision, coeff, affine)
+        self.n_nodes, self.n_dof, self.n_macro = hhg_mesh_info(self.h)
+        N = 1 << self.levels
+        self.shape = (self.subcubes[2] * N + 1, self.subcubes[1] * N + 1, self.subcubes[0] * N + 1)
+
+    def close(self):
+        if self.h is not None:
+            hhg_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def bytes(self):
+        return hhg_mesh_bytes(self.h)
+
+    def set_problem(self, f=None, u0=None, stream=None):
+        hhg_set_problem(self.h, f, u0, stream)
+
+    def get_solution(self, out=None, stream=None):
+        if out is None:
+            out = np.zeros(self.shape)
+        hhg_get_solution(self.h, out, stream)
+        return out
+
+    def vcycle(self, pre=3, post=3, stream=None):
+        return hhg_vcycle(self.h, pre, post, True, stream)
+
+    def residual_norm(self, stream=None):
+        return hhg_residual_norm(self.h, stream)
+
+    def inject_fault(self, ids, stream=None):
+        hhg_inject_fault(self.h, ids, stream)
+
+    def recover_local(self, ids, n_local, n_global=0, timed=False, stream=None):
+        return hhg_recover_local(self.h, ids, n_local, n_global, timed, stream)
+
+    def solve(self, **kw):
+        return hhg_solve(self.h, **kw)
