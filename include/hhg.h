@@ -157,6 +157,25 @@ typedef struct {
 int hhg_solve(hhg_mesh* mesh, const hhg_solve_opts* opts, double* hist, int* n_hist,
               int* cycles, void* stream);
 
+/* Allocation-free V-cycle (an interface addition; the paper has no
+ * counterpart).  Some callers cannot call cudaMalloc at all once they are
+ * running: for example a host application that hands the device's memory to
+ * its own arena allocator at start-up, or code on a path where device
+ * allocation is forbidden.  This call runs the same global V(pre, post) cycle
+ * as hhg_vcycle (without the residual norm) but its coarse-grid CG keeps its
+ * work vectors in a fixed array of the library's static device memory
+ * (4 x 16384 doubles = 512 KiB, which every GPU that loads the library holds
+ * until the process exits) instead of in memory obtained from cudaMalloc; the
+ * call itself makes no cudaMalloc, cudaFree or other allocating call.
+ * Limit: the coarsest level may have at most 16384 unknowns; larger meshes
+ * get HHG_ERR_ARG.  The first call on a device looks up the array's device
+ * address (cudaGetSymbolAddress) with that device current; make that first
+ * call before any stream capture.  All calls share the array and it keeps
+ * the last call's contents; the CG kernel writes every work value before it
+ * reads it, so nothing has to start at zero, but calls whose work overlaps on
+ * the GPU (other streams, other threads, other meshes) race on the array. */
+int hhg_vcycle_noalloc(hhg_mesh* mesh, int pre, int post, void* stream);
+
 /* Measurement support (not part of the method).
  * hhg_profile_enable: while enabled, every launch of the dominant kernel -- the
  * finest-level Gauss-Seidel volume kernel of the global problem (one colour of

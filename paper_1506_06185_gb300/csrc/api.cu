@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <stdexcept>
 #include <string>
@@ -437,9 +438,57 @@ int recover(hhg_mesh* m, int n_local, int n_global, bool mixed, int pre, int pos
   return HHG_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free V-cycle: the coarse-grid CG keeps its work vectors (x, r, p,
+// A p) in this file-scope static device array instead of the mesh's own
+// scratch.  Every GPU that loads the library holds the array until the
+// process exits.
+// ---------------------------------------------------------------------------
+constexpr int NOALLOC_MAX_COARSE = 16384;
+static __device__ __align__(256) double g_noalloc_cg_scratch[4 * NOALLOC_MAX_COARSE];
+constexpr int NOALLOC_MAX_DEVICES = 64;
+std::mutex g_noalloc_mu;
+double* g_noalloc_cg_ptr[NOALLOC_MAX_DEVICES] = {};
+
+// Device address of the static array on the current device, looked up once
+// per device (with that device current).
+int noalloc_scratch(double** out) {
+  int dev = 0;
+  HHG_CUDA(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return fail(HHG_ERR_ARG, "device ordinal beyond 63");
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_cg_ptr[dev]) {
+    void* p = nullptr;
+    HHG_CUDA(cudaGetSymbolAddress(&p, g_noalloc_cg_scratch));
+    g_noalloc_cg_ptr[dev] = static_cast<double*>(p);
+  }
+  *out = g_noalloc_cg_ptr[dev];
+  return HHG_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+int hhg_vcycle_noalloc(hhg_mesh* m, int pre, int post, void* stream) {
+  if (!m || pre < 0 || post < 0) return fail(HHG_ERR_ARG, "invalid argument");
+  if (m->global.n_cg > NOALLOC_MAX_COARSE)
+    return fail(HHG_ERR_ARG, "coarse problem has " + std::to_string(m->global.n_cg) +
+                                 " unknowns; the allocation-free V-cycle holds at most " +
+                                 std::to_string(NOALLOC_MAX_COARSE));
+  double* scratch = nullptr;
+  HHG_TRY(noalloc_scratch(&scratch));
+  // run the ordinary cycle with the coarse CG pointed at the static array; the
+  // pointer is passed by value at launch, so restoring it right away is safe
+  double* own = m->global.cg_work;
+  const int kind = m->global.kind;
+  m->global.cg_work = scratch;
+  m->global.kind = -1;   // keeps the profiling hook (which creates events) out
+  const int rc = vcycle_T<double>(m, m->d64, m->global, pre, post, 1e-12, 1000, (cudaStream_t)stream);
+  m->global.cg_work = own;
+  m->global.kind = kind;
+  return rc;
+}
 
 int hhg_last_error(char* buf, size_t len) {
   if (buf && len > 0) {

@@ -25,7 +25,7 @@ HHG_RECOVERY_NONE, HHG_RECOVERY_LR, HHG_RECOVERY_DD = 0, 1, 2
 EXPORTS = ["hhg_mesh_create", "hhg_mesh_destroy", "hhg_mesh_info", "hhg_mesh_bytes", "hhg_set_problem",
            "hhg_get_solution", "hhg_vcycle", "hhg_residual_norm", "hhg_inject_fault", "hhg_recover_local",
            "hhg_solve", "hhg_last_error", "hhg_profile_enable", "hhg_profile_read", "hhg_profile_info",
-           "hhg_launch_count"]
+           "hhg_launch_count", "hhg_vcycle_noalloc"]
 
 
 class hhg_mesh_desc(C.Structure):
@@ -71,6 +71,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "hhg_profile_read": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_double)], C.c_int),
         "hhg_profile_info": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_int)], C.c_int),
         "hhg_launch_count": ([C.POINTER(C.c_int64)], C.c_int),
+        "hhg_vcycle_noalloc": ([P, C.c_int, C.c_int, P], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -180,6 +181,12 @@ def hhg_vcycle(h, pre=3, post=3, want_residual=True, stream=None):
     r = C.c_double()
     _check(lib().hhg_vcycle(h, int(pre), int(post), C.byref(r) if want_residual else None, _stream(stream)))
     return r.value if want_residual else None
+
+
+def hhg_vcycle_noalloc(h, pre=3, post=3, stream=None):
+    """One global V-cycle whose coarse CG uses the library's static device
+    scratch instead of allocated memory (see include/hhg.h)."""
+    return _check(lib().hhg_vcycle_noalloc(h, int(pre), int(post), _stream(stream)))
 
 
 def hhg_residual_norm(h, stream=None):
