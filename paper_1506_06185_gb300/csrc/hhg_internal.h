@@ -84,8 +84,9 @@ inline int64_t block_elems(int N) {
   return (n + 63) & ~int64_t(63);
 }
 
-// Work tile of the volume kernels: 8 rows (j0..j0+7) x 32 slots (m0..m0+31)
-// of slice k.
+// Work tile of the volume kernels.  Interior tiles: slice k, row pairs
+// j0 .. j0 + m0 - 1 (see build_pair_tiles).  Closed-lattice tiles: 8 rows
+// (j0..j0+7) x 32 slots (m0..m0+31) of slice k.
 struct Tile {
   int k, j0, m0, pad;
 };
@@ -115,7 +116,7 @@ struct HostLevel {
   std::vector<Copy> if_copy;
   std::vector<unsigned char> if_colour, if_dirichlet;
   std::vector<double> W;              // [n_macro][16][15] stencil weights
-  std::vector<Tile> tiles_int;        // tiles covering the volume interior
+  std::vector<Tile> tiles_int;        // row-pair tiles of the volume interior
   std::vector<Tile> tiles_all;        // tiles covering the closed lattice
 };
 

@@ -1,16 +1,31 @@
 // CUDA kernels of the HHG multigrid for sm_103a.
 //
-// Volume kernels run over 8 x 32 tiles of one slice of a macro block (rows j,
-// slots m of the colour-split layout) with one CTA per (tile, active macro);
-// a warp reads 32 consecutive slots of one colour segment, so every stencil
-// neighbour is a contiguous, sector-aligned access.  Interface kernels run one
-// thread per face / edge / vertex node: they sum the sub-stencils of the
-// macros around the node (§3.2, Fig. 4), update the master in the interface
-// container and write the new value into the ghost shell of every adjacent
-// block (the local half of the ghost update of §3.1).
+// Every level-wide operation is one launch of 256-thread CTAs (32 x 8), as many
+// as the GPU holds at once, walking a list of work units with a grid stride:
+// the first units are chunks of free interface (face / edge / vertex) nodes,
+// one node per thread; the rest are row-pair tiles of the volume interiors of
+// the active macros.
+//
+// Volume work: in slice k of a macro's lattice the interior rows are
+// j = 1..J (J = N - 2 - k) and row j holds N - 1 - j - k nodes.  Rows are
+// paired as (1 + p, J - p), whose lengths add up to N - 1 - k, and a tile
+// holds enough pairs for about 512 nodes of one colour; the CTA flattens the
+// nodes (or 4-node slots) of all its pairs into one index range, so lanes stay
+// busy although the rows shrink across the triangle.  On GB300 the FP64 pipe
+// retires 2 DFMA per clock per SM and is charged per warp instruction, so
+// idle lanes cost as much as busy ones.  Consecutive lanes read consecutive
+// slots of one colour segment, so stencil neighbours are contiguous accesses.
+//
+// Interface work: a node's stencil is the sum of the sub-stencils of the
+// macros around it (§3.2, Fig. 4); the kernel updates the master in the
+// interface container and writes the value into the ghost shell of every
+// adjacent block (the local half of the ghost update of §3.1).
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 
 #include "hhg_kernels.h"
 
@@ -20,7 +35,7 @@ std::atomic<long long> g_kernel_launches{0};
 
 namespace {
 
-constexpr int VOL_THREADS = TILE_ROWS * TILE_SLOTS;   // 256
+constexpr int CTA = TILE_ROWS * TILE_SLOTS;   // 256 threads, 32 x 8
 
 // 7-point structure: only the three chain axes (and negatives) are non-zero.
 __host__ __device__ constexpr bool used_dir(int d, bool s7) {
@@ -36,6 +51,9 @@ __device__ __forceinline__ int lidx32(int N, int P, int i, int j, int k) {
   return slice32(N, P, k) + (4 * j + ((i + 2 * j + 3 * k) & 3)) * P + (i >> 2);
 }
 
+__device__ __forceinline__ int tid256() { return threadIdx.y * TILE_SLOTS + threadIdx.x; }
+
+// Sum over the CTA (any shape up to 1024 threads); result valid in thread 0.
 __device__ __forceinline__ double block_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x + threadIdx.y * blockDim.x;
@@ -48,49 +66,118 @@ __device__ __forceinline__ double block_sum(double v, double* sh) {
     s = (lane < (nthreads + 31) / 32) ? sh[lane] : 0.0;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
   }
-  return s;   // valid in thread 0
+  return s;
 }
 
-// ---------------------------------------------------------------------------
-// Gauss-Seidel, one colour
-// ---------------------------------------------------------------------------
-template <class T, bool S7>
-__global__ void __launch_bounds__(VOL_THREADS) k_gs_vol(int N, int P, int64_t block, T* __restrict__ u,
-                                                        const T* __restrict__ f, const T* __restrict__ W,
-                                                        const T* __restrict__ Winv, const Tile* __restrict__ tiles,
-                                                        const int* __restrict__ act, int colour) {
-  const Tile t = tiles[blockIdx.x];
-  const int macro = act[blockIdx.y];
-  const int k = t.k;
-  const int j = t.j0 + threadIdx.y;
-  const int m = t.m0 + threadIdx.x;
-  const int i = 4 * m + ((colour - 2 * j - 3 * k) & 3);
-  if (j < 1 || i < 1 || i + j + k > N - 1) return;
-  T* ub = u + (size_t)macro * block;
-  const T* fb = f + (size_t)macro * block;
-  const T* w = W + (size_t)macro * 16 * NDIR;
-  const int me = lidx32(N, P, i, j, k);
-  T acc = fb[me];
-#pragma unroll
-  for (int d = 1; d < NDIR; ++d) {
-    if (!used_dir(d, S7)) continue;
-    int di, dj, dk;
-    dir_ijk(d, di, dj, dk);
-    acc -= w[d] * ub[lidx32(N, P, i + di, j + dj, k + dk)];
+// Colour-c nodes of interior row j of slice k: slots m = mlo .. mlo + n - 1
+// (i = 4m + ic, 1 <= i <= N - 1 - j - k).
+__device__ __forceinline__ void colour_row(int N, int j, int k, int c, int& ic, int& mlo, int& n) {
+  ic = (c - 2 * j - 3 * k) & 3;
+  const int L = N - 1 - j - k;
+  mlo = ic == 0;
+  n = L >= ic ? ((L - ic) >> 2) - mlo + 1 : 0;
+}
+
+// Work items of interior row j: its colour-c nodes (colour kernels) or its
+// slots of four consecutive nodes (all-colour kernels).
+__device__ __forceinline__ int row_items(int N, int j, int k, int c, bool colour) {
+  if (colour) {
+    int ic, mlo, n;
+    colour_row(N, j, k, c, ic, mlo, n);
+    return n;
   }
-  ub[me] = acc * Winv[macro];
+  return ((N - 1 - j - k) >> 2) + 1;
 }
 
-template <class T>
-__global__ void k_gs_if(int N, int P, int64_t block, T* __restrict__ u, T* __restrict__ uI,
-                        const T* __restrict__ fI, const T* __restrict__ W, const int* __restrict__ cptr,
-                        const Copy* __restrict__ cps, const int* __restrict__ list, int n) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n) return;
-  const int node = list[q];
-  T acc = fI[node];
-  T diag = T(0);
-  const int c0 = cptr[node], c1 = cptr[node + 1];
+// An interior tile holds row pairs p = t.j0 .. t.j0 + t.m0 - 1 of slice t.k,
+// pair p being rows 1 + p and J - p (J = N - 2 - k).  The CTA flattens the
+// items of all its pairs into one range so that every lane has work:
+// s_pre[q] = items of pairs t.j0 .. t.j0 + q - 1 (warp 0 computes it with a
+// warp scan).  Returns the tile's item count.  All threads must call it.
+__device__ __forceinline__ int flat_setup(const Tile& t, int N, int c, bool colour, int* s_pre) {
+  const int k = t.k, J = N - 2 - k;
+  if (threadIdx.y == 0) {
+    const int q = threadIdx.x;
+    int len = 0;
+    if (q < t.m0) {
+      const int j1 = 1 + t.j0 + q, j2 = J - t.j0 - q;
+      if (j1 <= j2) {
+        len = row_items(N, j1, k, c, colour);
+        if (j2 > j1) len += row_items(N, j2, k, c, colour);
+      }
+    }
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, len, o);
+      if (q >= o) len += y;
+    }
+    s_pre[q + 1] = len;
+    if (q == 0) s_pre[0] = 0;
+  }
+  __syncthreads();
+  return s_pre[t.m0];
+}
+
+// Item tt of a flattened tile -> its row j and index v within the row.
+__device__ __forceinline__ void flat_item(const Tile& t, int N, int c, bool colour, const int* s_pre, int tt, int& j,
+                                          int& v) {
+  int lo = 0, hi = t.m0;
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (s_pre[mid] <= tt) lo = mid;
+    else hi = mid;
+  }
+  const int j1 = 1 + t.j0 + lo;
+  const int w = tt - s_pre[lo];
+  const int n1 = row_items(N, j1, t.k, c, colour);
+  if (w < n1) {
+    j = j1;
+    v = w;
+  } else {
+    j = N - 2 - t.k - t.j0 - lo;
+    v = w - n1;
+  }
+}
+
+// Loop over the interior nodes of a tile, four consecutive nodes
+// i = 4m .. 4m + 3 (one per colour segment) per item; the body sees i, j, k.
+#define HHG_TILE_NODES(NN, t, s_pre, ...)                                 \
+  {                                                                       \
+    const int k = (t).k;                                                  \
+    const int total_ = flat_setup((t), (NN), 0, false, (s_pre));          \
+    for (int tt = tid256(); tt < total_; tt += CTA) {                     \
+      int j, m;                                                           \
+      flat_item((t), (NN), 0, false, (s_pre), tt, j, m);                  \
+      const int L = (NN) - 1 - j - k;                                     \
+      _Pragma("unroll") for (int qq = 0; qq < 4; ++qq) {                  \
+        const int i = 4 * m + qq;                                         \
+        if (i < 1 || i > L) continue;                                     \
+        __VA_ARGS__                                                       \
+      }                                                                   \
+    }                                                                     \
+    __syncthreads();                                                      \
+  }
+
+// Work units of a fused launch: units [0, n_if_units) are chunks of 256
+// interface list entries, the rest are (tile, active macro) pairs.  CTAs walk
+// the units with a grid stride, so a launch has a few CTAs per SM whatever the
+// level size.
+#define HHG_UNITS(n_if_units, n_tiles, n_act)                                                     \
+  for (int unit = blockIdx.x, n_units_ = (n_if_units) + (n_tiles) * (n_act); unit < n_units_;     \
+       unit += gridDim.x)
+
+__device__ __forceinline__ void vol_unit(int unit, int n_if_units, int n_tiles, const Tile* __restrict__ tiles,
+                                         const int* __restrict__ act, Tile& t, int& macro) {
+  const int b = unit - n_if_units;
+  t = tiles[b % n_tiles];
+  macro = act[b / n_tiles];
+}
+
+// Off-diagonal part of an interface node's stencil applied to u, and the sum
+// of the diagonal weights, over all copies of the node.
+template <class T, bool S7>
+__device__ __forceinline__ void if_stencil(int N, int P, int64_t block, const T* __restrict__ u,
+                                           const T* __restrict__ W, const Copy* __restrict__ cps, int c0, int c1,
+                                           T& off, T& diag) {
   for (int c = c0; c < c1; ++c) {
     const Copy cp = cps[c];
     const T* w = W + ((size_t)cp.macro * 16 + node_class(cp.i, cp.j, cp.k, N)) * NDIR;
@@ -98,17 +185,21 @@ __global__ void k_gs_if(int N, int P, int64_t block, T* __restrict__ u, T* __res
     diag += w[0];
 #pragma unroll
     for (int d = 1; d < NDIR; ++d) {
+      if (!used_dir(d, S7)) continue;
       const T wd = w[d];
       if (wd == T(0)) continue;
       int di, dj, dk;
       dir_ijk(d, di, dj, dk);
       const int ni = cp.i + di, nj = cp.j + dj, nk = cp.k + dk;
       if (!in_lattice(ni, nj, nk, N)) continue;
-      acc -= wd * ub[lidx32(N, P, ni, nj, nk)];
+      off += wd * ub[lidx32(N, P, ni, nj, nk)];
     }
   }
-  const T val = acc / diag;
-  uI[node] = val;
+}
+
+template <class T>
+__device__ __forceinline__ void write_copies(int N, int P, int64_t block, T* __restrict__ u,
+                                             const Copy* __restrict__ cps, int c0, int c1, T val) {
   for (int c = c0; c < c1; ++c) {
     const Copy cp = cps[c];
     u[(size_t)cp.macro * block + lidx32(N, P, cp.i, cp.j, cp.k)] = val;
@@ -116,32 +207,103 @@ __global__ void k_gs_if(int N, int P, int64_t block, T* __restrict__ u, T* __res
 }
 
 // ---------------------------------------------------------------------------
-// Residual (all colours); optional write and norm partials
+// Gauss-Seidel, one colour (§2.1 smoother)
+// ---------------------------------------------------------------------------
+template <class T, bool S7>
+__global__ void __launch_bounds__(CTA) k_gs(int N, int P, int64_t block, T* __restrict__ u, T* __restrict__ uI,
+                                            const T* __restrict__ f, const T* __restrict__ fI,
+                                            const T* __restrict__ W, const T* __restrict__ Winv,
+                                            const Tile* __restrict__ tiles, int n_tiles, const int* __restrict__ act,
+                                            int n_act, int colour, const int* __restrict__ cptr,
+                                            const Copy* __restrict__ cps, const int* __restrict__ list, int n_list,
+                                            int n_if_units) {
+  __shared__ int s_pre[33];
+  HHG_UNITS(n_if_units, n_tiles, n_act) {
+    if (unit < n_if_units) {
+      const int q = unit * CTA + tid256();
+      if (q < n_list) {
+        const int node = list[q];
+        const int c0 = cptr[node], c1 = cptr[node + 1];
+        T off = T(0), diag = T(0);
+        if_stencil<T, S7>(N, P, block, u, W, cps, c0, c1, off, diag);
+        const T val = (fI[node] - off) / diag;
+        uI[node] = val;
+        write_copies(N, P, block, u, cps, c0, c1, val);
+      }
+      continue;
+    }
+    Tile t;
+    int macro;
+    vol_unit(unit, n_if_units, n_tiles, tiles, act, t, macro);
+    const int k = t.k;
+    T* ub = u + (size_t)macro * block;
+    const T* fb = f + (size_t)macro * block;
+    const T* w = W + (size_t)macro * 16 * NDIR;
+    const T inv = Winv[macro];
+    const int total = flat_setup(t, N, colour, true, s_pre);
+    for (int tt = tid256(); tt < total; tt += CTA) {
+      int j, v, ic, mlo, n;
+      flat_item(t, N, colour, true, s_pre, tt, j, v);
+      colour_row(N, j, k, colour, ic, mlo, n);
+      const int i = 4 * (mlo + v) + ic;
+      const int me = lidx32(N, P, i, j, k);
+      T acc = fb[me];
+#pragma unroll
+      for (int d = 1; d < NDIR; ++d) {
+        if (!used_dir(d, S7)) continue;
+        int di, dj, dk;
+        dir_ijk(d, di, dj, dk);
+        acc -= w[d] * ub[lidx32(N, P, i + di, j + dj, k + dk)];
+      }
+      ub[me] = acc * inv;
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Residual r = f - A u on the free nodes (all colours); optional write of r
+// (zero at the problem's frozen ghost copies) and per-CTA partial sums of r^2
 // ---------------------------------------------------------------------------
 template <class T, bool S7, bool WRITE, bool NORM>
-__global__ void __launch_bounds__(VOL_THREADS) k_res_vol(int N, int P, int64_t block, const T* __restrict__ u,
-                                                         const T* __restrict__ f, T* __restrict__ r,
-                                                         const T* __restrict__ W, const Tile* __restrict__ tiles,
-                                                         const int* __restrict__ act, double* __restrict__ partial) {
+__global__ void __launch_bounds__(CTA) k_res(int N, int P, int64_t block, const T* __restrict__ u,
+                                             const T* __restrict__ uI, const T* __restrict__ f,
+                                             const T* __restrict__ fI, T* __restrict__ r, const T* __restrict__ W,
+                                             const Tile* __restrict__ tiles, int n_tiles, const int* __restrict__ act,
+                                             int n_act, const int* __restrict__ cptr, const Copy* __restrict__ cps,
+                                             const int* __restrict__ list, int n_list,
+                                             const int64_t* __restrict__ zero_off, int n_zero, int n_if_units,
+                                             double* __restrict__ partial) {
+  __shared__ int s_pre[33];
   __shared__ double sh[32];
-  const Tile t = tiles[blockIdx.x];
-  const int macro = act[blockIdx.y];
-  const int k = t.k;
-  const int j = t.j0 + threadIdx.y;
-  const int m = t.m0 + threadIdx.x;
-  const T* ub = u + (size_t)macro * block;
-  const T* fb = f + (size_t)macro * block;
-  T* rb = r + (size_t)macro * block;
-  const T* w = W + (size_t)macro * 16 * NDIR;
   double ss = 0.0;
-  if (j >= 1) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = 4 * m + q;
-      if (i < 1 || i + j + k > N - 1) continue;
+  HHG_UNITS(n_if_units, n_tiles, n_act) {
+    if (unit < n_if_units) {
+      const int q = unit * CTA + tid256();
+      if (q < n_list) {
+        const int node = list[q];
+        const int c0 = cptr[node], c1 = cptr[node + 1];
+        T off = T(0), diag = T(0);
+        if_stencil<T, S7>(N, P, block, u, W, cps, c0, c1, off, diag);
+        const T res = fI[node] - diag * uI[node] - off;
+        if (WRITE) write_copies(N, P, block, r, cps, c0, c1, res);
+        if (NORM) ss += (double)res * (double)res;
+      } else if (WRITE && q < n_list + n_zero) {
+        r[zero_off[q - n_list]] = T(0);
+      }
+      continue;
+    }
+    Tile t;
+    int macro;
+    vol_unit(unit, n_if_units, n_tiles, tiles, act, t, macro);
+    const T* ub = u + (size_t)macro * block;
+    const T* fb = f + (size_t)macro * block;
+    T* rb = r + (size_t)macro * block;
+    const T* w = W + (size_t)macro * 16 * NDIR;
+    HHG_TILE_NODES(N, t, s_pre, {
       const int me = lidx32(N, P, i, j, k);
       T acc = fb[me] - w[0] * ub[me];
-#pragma unroll
+_Pragma("unroll")
       for (int d = 1; d < NDIR; ++d) {
         if (!used_dir(d, S7)) continue;
         int di, dj, dk;
@@ -150,116 +312,67 @@ __global__ void __launch_bounds__(VOL_THREADS) k_res_vol(int N, int P, int64_t b
       }
       if (WRITE) rb[me] = acc;
       if (NORM) ss += (double)acc * (double)acc;
-    }
+    })
   }
   if (NORM) {
-    double s = block_sum(ss, sh);
-    if (threadIdx.x == 0 && threadIdx.y == 0) partial[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
+    const double s = block_sum(ss, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.x] = s;
   }
 }
 
-template <class T, bool WRITE, bool NORM>
-__global__ void k_res_if(int N, int P, int64_t block, const T* __restrict__ u, const T* __restrict__ fI,
-                         T* __restrict__ r, const T* __restrict__ W, const int* __restrict__ cptr,
-                         const Copy* __restrict__ cps, const int* __restrict__ list, int n,
-                         const int64_t* __restrict__ zero_off, int n_zero, double* __restrict__ partial) {
-  __shared__ double sh[32];
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  double ss = 0.0;
-  if (q < n) {
-    const int node = list[q];
-    T acc = fI[node];
-    const int c0 = cptr[node], c1 = cptr[node + 1];
-    for (int c = c0; c < c1; ++c) {
-      const Copy cp = cps[c];
-      const T* w = W + ((size_t)cp.macro * 16 + node_class(cp.i, cp.j, cp.k, N)) * NDIR;
-      const T* ub = u + (size_t)cp.macro * block;
-      acc -= w[0] * ub[lidx32(N, P, cp.i, cp.j, cp.k)];
-#pragma unroll
+// ---------------------------------------------------------------------------
+// Restriction R = P^T onto the coarse level (§2.1); zero the coarse correction
+// ---------------------------------------------------------------------------
+template <class T>
+__global__ void __launch_bounds__(CTA) k_restrict(int Nc, int Pc, int64_t bc, T* __restrict__ fc, T* __restrict__ fIc,
+                                                  T* __restrict__ uc, T* __restrict__ uIc, int Nf, int Pf, int64_t bf,
+                                                  const T* __restrict__ rf, const Tile* __restrict__ tiles, int n_tiles,
+                                                  const int* __restrict__ act, int n_act,
+                                                  const int* __restrict__ cptr, const Copy* __restrict__ cps,
+                                                  const int* __restrict__ list, int n_list,
+                                                  const int64_t* __restrict__ gather,
+                                                  const int64_t* __restrict__ zero_off, int n_zero, int n_if_units) {
+  __shared__ int s_pre[33];
+  HHG_UNITS(n_if_units, n_tiles, n_act) {
+    if (unit < n_if_units) {
+      const int q = unit * CTA + tid256();
+      if (q < n_list) {
+        const int node = list[q];
+        const int64_t* g = gather + (size_t)q * NDIR;
+        T acc = T(0);
+        for (int e = 1; e < NDIR; ++e) acc += rf[g[e]];
+        fIc[node] = rf[g[0]] + T(0.5) * acc;
+        uIc[node] = T(0);
+        write_copies(Nc, Pc, bc, uc, cps, cptr[node], cptr[node + 1], T(0));
+      } else if (q < n_list + n_zero) {
+        uc[zero_off[q - n_list]] = T(0);
+      }
+      continue;
+    }
+    Tile t;
+    int macro;
+    vol_unit(unit, n_if_units, n_tiles, tiles, act, t, macro);
+    const T* rb = rf + (size_t)macro * bf;
+    T* fb = fc + (size_t)macro * bc;
+    T* ub = uc + (size_t)macro * bc;
+    HHG_TILE_NODES(Nc, t, s_pre, {
+      const int fi = 2 * i, fj = 2 * j, fk = 2 * k;
+      T acc = T(0);
+_Pragma("unroll")
       for (int d = 1; d < NDIR; ++d) {
-        const T wd = w[d];
-        if (wd == T(0)) continue;
         int di, dj, dk;
         dir_ijk(d, di, dj, dk);
-        const int ni = cp.i + di, nj = cp.j + dj, nk = cp.k + dk;
-        if (!in_lattice(ni, nj, nk, N)) continue;
-        acc -= wd * ub[lidx32(N, P, ni, nj, nk)];
+        acc += rb[lidx32(Nf, Pf, fi + di, fj + dj, fk + dk)];
       }
-    }
-    if (WRITE)
-      for (int c = c0; c < c1; ++c) {
-        const Copy cp = cps[c];
-        r[(size_t)cp.macro * block + lidx32(N, P, cp.i, cp.j, cp.k)] = acc;
-      }
-    if (NORM) ss = (double)acc * (double)acc;
-  } else if (WRITE && q < n + n_zero) {
-    r[zero_off[q - n]] = T(0);
-  }
-  if (NORM) {
-    double s = block_sum(ss, sh);
-    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+      const int me = lidx32(Nc, Pc, i, j, k);
+      fb[me] = rb[lidx32(Nf, Pf, fi, fj, fk)] + T(0.5) * acc;
+      ub[me] = T(0);
+    })
   }
 }
 
 // ---------------------------------------------------------------------------
-// Restriction R = P^T onto the coarse level; zero the coarse correction
-// ---------------------------------------------------------------------------
-template <class T>
-__global__ void __launch_bounds__(VOL_THREADS) k_restrict_vol(int Nc, int Pc, int64_t bc, T* __restrict__ fc,
-                                                              T* __restrict__ uc, int Nf, int Pf, int64_t bf,
-                                                              const T* __restrict__ rf, const Tile* __restrict__ tiles,
-                                                              const int* __restrict__ act) {
-  const Tile t = tiles[blockIdx.x];
-  const int macro = act[blockIdx.y];
-  const int k = t.k;
-  const int j = t.j0 + threadIdx.y;
-  const int m = t.m0 + threadIdx.x;
-  if (j < 1) return;
-  const T* rb = rf + (size_t)macro * bf;
-  T* fb = fc + (size_t)macro * bc;
-  T* ub = uc + (size_t)macro * bc;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int i = 4 * m + q;
-    if (i < 1 || i + j + k > Nc - 1) continue;
-    const int fi = 2 * i, fj = 2 * j, fk = 2 * k;
-    T acc = T(0);
-#pragma unroll
-    for (int d = 1; d < NDIR; ++d) {
-      int di, dj, dk;
-      dir_ijk(d, di, dj, dk);
-      acc += rb[lidx32(Nf, Pf, fi + di, fj + dj, fk + dk)];
-    }
-    const int me = lidx32(Nc, Pc, i, j, k);
-    fb[me] = rb[lidx32(Nf, Pf, fi, fj, fk)] + T(0.5) * acc;
-    ub[me] = T(0);
-  }
-}
-
-template <class T>
-__global__ void k_restrict_if(int Nc, int Pc, int64_t bc, const T* __restrict__ rf, T* __restrict__ fIc,
-                              T* __restrict__ uc, T* __restrict__ uIc, const int* __restrict__ cptr,
-                              const Copy* __restrict__ cps, const int* __restrict__ list, int n,
-                              const int64_t* __restrict__ gather, const int64_t* __restrict__ zero_off, int n_zero) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q < n) {
-    const int node = list[q];
-    const int64_t* g = gather + (size_t)q * NDIR;
-    T acc = T(0);
-    for (int e = 1; e < NDIR; ++e) acc += rf[g[e]];
-    fIc[node] = rf[g[0]] + T(0.5) * acc;
-    uIc[node] = T(0);
-    for (int c = cptr[node]; c < cptr[node + 1]; ++c) {
-      const Copy cp = cps[c];
-      uc[(size_t)cp.macro * bc + lidx32(Nc, Pc, cp.i, cp.j, cp.k)] = T(0);
-    }
-  } else if (q < n + n_zero) {
-    uc[zero_off[q - n]] = T(0);
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Prolongation u_f += P u_c
+// Prolongation u_f += P u_c (linear interpolation, §2.1)
 // ---------------------------------------------------------------------------
 template <class T>
 __device__ __forceinline__ T interp(const T* __restrict__ cb, int Nc, int Pc, int i, int j, int k) {
@@ -283,42 +396,117 @@ __device__ __forceinline__ T interp(const T* __restrict__ cb, int Nc, int Pc, in
 }
 
 template <class T>
-__global__ void __launch_bounds__(VOL_THREADS) k_prolong_vol(int Nf, int Pf, int64_t bf, T* __restrict__ uf, int Nc,
-                                                             int Pc, int64_t bc, const T* __restrict__ uc,
-                                                             const Tile* __restrict__ tiles,
-                                                             const int* __restrict__ act) {
-  const Tile t = tiles[blockIdx.x];
-  const int macro = act[blockIdx.y];
-  const int k = t.k;
-  const int j = t.j0 + threadIdx.y;
-  const int m = t.m0 + threadIdx.x;
-  if (j < 1) return;
-  T* fb = uf + (size_t)macro * bf;
-  const T* cb = uc + (size_t)macro * bc;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int i = 4 * m + q;
-    if (i < 1 || i + j + k > Nf - 1) continue;
-    const int me = lidx32(Nf, Pf, i, j, k);
-    fb[me] += interp(cb, Nc, Pc, i, j, k);
+__global__ void __launch_bounds__(CTA) k_prolong(int Nf, int Pf, int64_t bf, T* __restrict__ uf, T* __restrict__ uIf,
+                                                 int Nc, int Pc, int64_t bc, const T* __restrict__ uc,
+                                                 const Tile* __restrict__ tiles, int n_tiles,
+                                                 const int* __restrict__ act, int n_act, const int* __restrict__ cptr,
+                                                 const Copy* __restrict__ cps, const int* __restrict__ list,
+                                                 int n_list, int n_if_units) {
+  __shared__ int s_pre[33];
+  HHG_UNITS(n_if_units, n_tiles, n_act) {
+    if (unit < n_if_units) {
+      const int q = unit * CTA + tid256();
+      if (q < n_list) {
+        const int node = list[q];
+        const int c0 = cptr[node], c1 = cptr[node + 1];
+        const Copy cp = cps[c0];
+        const T val = uIf[node] + interp(uc + (size_t)cp.macro * bc, Nc, Pc, cp.i, cp.j, cp.k);
+        uIf[node] = val;
+        write_copies(Nf, Pf, bf, uf, cps, c0, c1, val);
+      }
+      continue;
+    }
+    Tile t;
+    int macro;
+    vol_unit(unit, n_if_units, n_tiles, tiles, act, t, macro);
+    T* fb = uf + (size_t)macro * bf;
+    const T* cb = uc + (size_t)macro * bc;
+    HHG_TILE_NODES(Nf, t, s_pre, { fb[lidx32(Nf, Pf, i, j, k)] += interp(cb, Nc, Pc, i, j, k); })
   }
 }
 
-template <class T>
-__global__ void k_prolong_if(int Nf, int Pf, int64_t bf, T* __restrict__ uf, T* __restrict__ uIf, int Nc, int Pc,
-                             int64_t bc, const T* __restrict__ uc, const int* __restrict__ cptr,
-                             const Copy* __restrict__ cps, const int* __restrict__ list, int n) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n) return;
-  const int node = list[q];
-  const int c0 = cptr[node], c1 = cptr[node + 1];
-  const Copy c0p = cps[c0];
-  const T corr = interp(uc + (size_t)c0p.macro * bc, Nc, Pc, c0p.i, c0p.j, c0p.k);
-  const T val = uIf[node] + corr;
-  uIf[node] = val;
-  for (int c = c0; c < c1; ++c) {
-    const Copy cp = cps[c];
-    uf[(size_t)cp.macro * bf + lidx32(Nf, Pf, cp.i, cp.j, cp.k)] = val;
+// ---------------------------------------------------------------------------
+// Mixed precision: FP64 residual handed to the FP32 cycle as its right-hand
+// side (with partial sums of r^2), and the FP64 update u += e
+// ---------------------------------------------------------------------------
+template <bool S7>
+__global__ void __launch_bounds__(CTA) k_res_f32(int N, int P, int64_t block, const double* __restrict__ u,
+                                                 const double* __restrict__ uI, const double* __restrict__ f,
+                                                 const double* __restrict__ fI, float* __restrict__ f32,
+                                                 float* __restrict__ fI32, const double* __restrict__ W,
+                                                 const Tile* __restrict__ tiles, int n_tiles,
+                                                 const int* __restrict__ act, int n_act,
+                                                 const int* __restrict__ cptr, const Copy* __restrict__ cps,
+                                                 const int* __restrict__ list, int n_list, int n_if_units,
+                                                 double* __restrict__ partial) {
+  __shared__ int s_pre[33];
+  __shared__ double sh[32];
+  double ss = 0.0;
+  HHG_UNITS(n_if_units, n_tiles, n_act) {
+    if (unit < n_if_units) {
+      const int q = unit * CTA + tid256();
+      if (q < n_list) {
+        const int node = list[q];
+        double off = 0.0, diag = 0.0;
+        if_stencil<double, S7>(N, P, block, u, W, cps, cptr[node], cptr[node + 1], off, diag);
+        const double res = fI[node] - diag * uI[node] - off;
+        fI32[node] = (float)res;
+        ss += res * res;
+      }
+      continue;
+    }
+    Tile t;
+    int macro;
+    vol_unit(unit, n_if_units, n_tiles, tiles, act, t, macro);
+    const double* ub = u + (size_t)macro * block;
+    const double* fb = f + (size_t)macro * block;
+    float* ob = f32 + (size_t)macro * block;
+    const double* w = W + (size_t)macro * 16 * NDIR;
+    HHG_TILE_NODES(N, t, s_pre, {
+      const int me = lidx32(N, P, i, j, k);
+      double acc = fb[me] - w[0] * ub[me];
+_Pragma("unroll")
+      for (int d = 1; d < NDIR; ++d) {
+        if (!used_dir(d, S7)) continue;
+        int di, dj, dk;
+        dir_ijk(d, di, dj, dk);
+        acc -= w[d] * ub[lidx32(N, P, i + di, j + dj, k + dk)];
+      }
+      ob[me] = (float)acc;
+      ss += acc * acc;
+    })
+  }
+  const double s = block_sum(ss, sh);
+  if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.x] = s;
+}
+
+__global__ void __launch_bounds__(CTA) k_add_corr(int N, int P, int64_t block, double* __restrict__ u,
+                                                  double* __restrict__ uI, const float* __restrict__ e,
+                                                  const float* __restrict__ eI, const Tile* __restrict__ tiles,
+                                                  int n_tiles, const int* __restrict__ act, int n_act,
+                                                  const int* __restrict__ cptr, const Copy* __restrict__ cps,
+                                                  const int* __restrict__ list, int n_list, int n_if_units) {
+  __shared__ int s_pre[33];
+  HHG_UNITS(n_if_units, n_tiles, n_act) {
+    if (unit < n_if_units) {
+      const int q = unit * CTA + tid256();
+      if (q < n_list) {
+        const int node = list[q];
+        const double val = uI[node] + (double)eI[node];
+        uI[node] = val;
+        write_copies(N, P, block, u, cps, cptr[node], cptr[node + 1], val);
+      }
+      continue;
+    }
+    Tile t;
+    int macro;
+    vol_unit(unit, n_if_units, n_tiles, tiles, act, t, macro);
+    double* ub = u + (size_t)macro * block;
+    const float* eb = e + (size_t)macro * block;
+    HHG_TILE_NODES(N, t, s_pre, {
+      const int me = lidx32(N, P, i, j, k);
+      ub[me] += (double)eb[me];
+    })
   }
 }
 
@@ -407,7 +595,7 @@ __global__ void k_reduce(const double* __restrict__ partial, int n, double* __re
 }
 
 // ---------------------------------------------------------------------------
-// Global vector <-> blocks
+// Global vector <-> blocks (closed-lattice tiles: 8 rows x 32 slots)
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ int64_t dev_gid(const MacroGeo& g, int N, int i, int j, int k, int64_t nx, int64_t ny) {
   const int64_t X = (int64_t)N * g.v0[0] + (int64_t)i * g.e1[0] + (int64_t)j * g.e2[0] + (int64_t)k * g.e3[0];
@@ -417,10 +605,9 @@ __device__ __forceinline__ int64_t dev_gid(const MacroGeo& g, int N, int i, int 
 }
 
 template <class T>
-__global__ void __launch_bounds__(VOL_THREADS) k_import_vol(int N, int P, int64_t block, const MacroGeo* __restrict__ geo,
-                                                            int64_t nx, int64_t ny, const double* __restrict__ g,
-                                                            T* __restrict__ dst, const Tile* __restrict__ tiles,
-                                                            bool closed) {
+__global__ void __launch_bounds__(CTA) k_import_vol(int N, int P, int64_t block, const MacroGeo* __restrict__ geo,
+                                                    int64_t nx, int64_t ny, const double* __restrict__ g,
+                                                    T* __restrict__ dst, const Tile* __restrict__ tiles, bool closed) {
   const Tile t = tiles[blockIdx.x];
   const int macro = blockIdx.y;
   const int k = t.k;
@@ -439,9 +626,9 @@ __global__ void __launch_bounds__(VOL_THREADS) k_import_vol(int N, int P, int64_
 }
 
 template <class T>
-__global__ void __launch_bounds__(VOL_THREADS) k_export_vol(int N, int P, int64_t block, const MacroGeo* __restrict__ geo,
-                                                            int64_t nx, int64_t ny, const T* __restrict__ src,
-                                                            double* __restrict__ g, const Tile* __restrict__ tiles) {
+__global__ void __launch_bounds__(CTA) k_export_vol(int N, int P, int64_t block, const MacroGeo* __restrict__ geo,
+                                                    int64_t nx, int64_t ny, const T* __restrict__ src,
+                                                    double* __restrict__ g, const Tile* __restrict__ tiles) {
   const Tile t = tiles[blockIdx.x];
   const int macro = blockIdx.y;
   const int k = t.k;
@@ -449,7 +636,7 @@ __global__ void __launch_bounds__(VOL_THREADS) k_export_vol(int N, int P, int64_
   const int m = t.m0 + threadIdx.x;
   const MacroGeo gm = geo[macro];
   const T* b = src + (size_t)macro * block;
-  if (j < 1) return;
+  if (j < 1 || k < 1) return;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const int i = 4 * m + q;
@@ -481,113 +668,6 @@ __global__ void k_restore(double* __restrict__ u, const double* __restrict__ uI,
   if (q < n) u[off[q]] = uI[master[q]];
 }
 
-// ---------------------------------------------------------------------------
-// Mixed precision helpers
-// ---------------------------------------------------------------------------
-template <bool S7>
-__global__ void __launch_bounds__(VOL_THREADS) k_res_vol_f32(int N, int P, int64_t block, const double* __restrict__ u,
-                                                             const double* __restrict__ f, float* __restrict__ f32,
-                                                             const double* __restrict__ W, const Tile* __restrict__ tiles,
-                                                             const int* __restrict__ act, double* __restrict__ partial) {
-  __shared__ double sh[32];
-  const Tile t = tiles[blockIdx.x];
-  const int macro = act[blockIdx.y];
-  const int k = t.k;
-  const int j = t.j0 + threadIdx.y;
-  const int m = t.m0 + threadIdx.x;
-  const double* ub = u + (size_t)macro * block;
-  const double* fb = f + (size_t)macro * block;
-  float* ob = f32 + (size_t)macro * block;
-  const double* w = W + (size_t)macro * 16 * NDIR;
-  double ss = 0.0;
-  if (j >= 1) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int i = 4 * m + q;
-      if (i < 1 || i + j + k > N - 1) continue;
-      const int me = lidx32(N, P, i, j, k);
-      double acc = fb[me] - w[0] * ub[me];
-#pragma unroll
-      for (int d = 1; d < NDIR; ++d) {
-        if (!used_dir(d, S7)) continue;
-        int di, dj, dk;
-        dir_ijk(d, di, dj, dk);
-        acc -= w[d] * ub[lidx32(N, P, i + di, j + dj, k + dk)];
-      }
-      ob[me] = (float)acc;
-      ss += acc * acc;
-    }
-  }
-  double s = block_sum(ss, sh);
-  if (threadIdx.x == 0 && threadIdx.y == 0) partial[(size_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
-}
-
-__global__ void k_res_if_f32(int N, int P, int64_t block, const double* __restrict__ u, const double* __restrict__ fI,
-                             float* __restrict__ fI32, const double* __restrict__ W, const int* __restrict__ cptr,
-                             const Copy* __restrict__ cps, const int* __restrict__ list, int n,
-                             double* __restrict__ partial) {
-  __shared__ double sh[32];
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  double ss = 0.0;
-  if (q < n) {
-    const int node = list[q];
-    double acc = fI[node];
-    for (int c = cptr[node]; c < cptr[node + 1]; ++c) {
-      const Copy cp = cps[c];
-      const double* w = W + ((size_t)cp.macro * 16 + node_class(cp.i, cp.j, cp.k, N)) * NDIR;
-      const double* ub = u + (size_t)cp.macro * block;
-      acc -= w[0] * ub[lidx32(N, P, cp.i, cp.j, cp.k)];
-      for (int d = 1; d < NDIR; ++d) {
-        const double wd = w[d];
-        if (wd == 0.0) continue;
-        int di, dj, dk;
-        dir_ijk(d, di, dj, dk);
-        const int ni = cp.i + di, nj = cp.j + dj, nk = cp.k + dk;
-        if (!in_lattice(ni, nj, nk, N)) continue;
-        acc -= wd * ub[lidx32(N, P, ni, nj, nk)];
-      }
-    }
-    fI32[node] = (float)acc;
-    ss = acc * acc;
-  }
-  double s = block_sum(ss, sh);
-  if (threadIdx.x == 0) partial[blockIdx.x] = s;
-}
-
-__global__ void __launch_bounds__(VOL_THREADS) k_add_corr_vol(int N, int P, int64_t block, double* __restrict__ u,
-                                                              const float* __restrict__ e, const Tile* __restrict__ tiles,
-                                                              const int* __restrict__ act) {
-  const Tile t = tiles[blockIdx.x];
-  const int macro = act[blockIdx.y];
-  const int k = t.k;
-  const int j = t.j0 + threadIdx.y;
-  const int m = t.m0 + threadIdx.x;
-  if (j < 1) return;
-  double* ub = u + (size_t)macro * block;
-  const float* eb = e + (size_t)macro * block;
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    const int i = 4 * m + q;
-    if (i < 1 || i + j + k > N - 1) continue;
-    const int me = lidx32(N, P, i, j, k);
-    ub[me] += (double)eb[me];
-  }
-}
-
-__global__ void k_add_corr_if(int N, int P, int64_t block, double* __restrict__ u, double* __restrict__ uI,
-                              const float* __restrict__ eI, const int* __restrict__ cptr, const Copy* __restrict__ cps,
-                              const int* __restrict__ list, int n) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n) return;
-  const int node = list[q];
-  const double val = uI[node] + (double)eI[node];
-  uI[node] = val;
-  for (int c = cptr[node]; c < cptr[node + 1]; ++c) {
-    const Copy cp = cps[c];
-    u[(size_t)cp.macro * block + lidx32(N, P, cp.i, cp.j, cp.k)] = val;
-  }
-}
-
 template <class T>
 __global__ void k_zero_blocks(T* __restrict__ u, int64_t block, const int* __restrict__ act) {
   T* b = u + (size_t)act[blockIdx.y] * block;
@@ -601,9 +681,44 @@ __global__ void k_zero_list(T* __restrict__ uI, const int* __restrict__ list, in
   if (q < n) uI[list[q]] = T(0);
 }
 
-inline dim3 vol_grid(int n_tiles, int n_macro) { return dim3((unsigned)n_tiles, (unsigned)n_macro); }
-inline dim3 vol_block() { return dim3(TILE_SLOTS, TILE_ROWS); }
 inline unsigned lin_grid(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+inline dim3 cta_shape() { return dim3(TILE_SLOTS, TILE_ROWS); }
+
+// Grid of a fused launch: interface units first, then tiles x active macros;
+// at most as many CTAs as the GPU holds at once (occupancy of the kernel
+// times the SM count), each walking the units with a grid stride.
+struct Units {
+  int n_if_units, total;
+};
+inline Units units(int n_if_items, int n_tiles, int n_act) {
+  Units g;
+  g.n_if_units = (int)lin_grid(n_if_items, CTA);
+  g.total = g.n_if_units + (n_act > 0 ? n_tiles * n_act : 0);
+  return g;
+}
+
+std::mutex g_occ_mu;
+std::map<std::pair<const void*, int>, int> g_occ;   // (kernel, device) -> resident CTAs
+
+inline unsigned resident_grid(const void* kernel, int total) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int cap = 0;
+  {
+    std::lock_guard<std::mutex> lock(g_occ_mu);
+    auto it = g_occ.find({kernel, dev});
+    if (it != g_occ.end()) {
+      cap = it->second;
+    } else {
+      int sms = 0, per_sm = 0;
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, CTA, 0);
+      cap = std::max(1, sms * std::max(1, per_sm));
+      g_occ[{kernel, dev}] = cap;
+    }
+  }
+  return (unsigned)std::min(total, cap);
+}
 
 }  // namespace
 
@@ -614,93 +729,67 @@ template <class T>
 cudaError_t gs_colour(const LevelArgs& L, const ProbArgs& p, T* u, T* uI, const T* f, const T* fI, const T* W,
                       const T* Winv, int colour, bool seven_point, cudaStream_t s, cudaEvent_t ev_begin,
                       cudaEvent_t ev_end) {
-  if (p.n_act > 0 && L.n_tiles_int > 0) {
-    if (ev_begin) cudaEventRecord(ev_begin, s);
-    if (seven_point)
-      { ++g_kernel_launches; k_gs_vol<T, true><<<vol_grid(L.n_tiles_int, p.n_act), vol_block(), 0, s>>>(L.N, L.P, L.block, u, f, W, Winv,
-                                                                                  L.tiles_int, p.act, colour); }
-    else
-      { ++g_kernel_launches; k_gs_vol<T, false><<<vol_grid(L.n_tiles_int, p.n_act), vol_block(), 0, s>>>(L.N, L.P, L.block, u, f, W, Winv,
-                                                                                   L.tiles_int, p.act, colour); }
-    if (ev_end) cudaEventRecord(ev_end, s);
-  }
   const int n = p.col_off[colour + 1] - p.col_off[colour];
-  if (n > 0)
-    { ++g_kernel_launches; k_gs_if<T><<<lin_grid(n, 128), 128, 0, s>>>(L.N, L.P, L.block, u, uI, fI, W, L.cptr, L.cps,
-                                                p.free_if + p.col_off[colour], n); }
+  const Units g = units(n, L.n_tiles_int, p.n_act);
+  if (g.total == 0) return cudaSuccess;
+  auto kern = seven_point ? k_gs<T, true> : k_gs<T, false>;
+  const unsigned grid = resident_grid((const void*)kern, g.total);
+  if (ev_begin) cudaEventRecord(ev_begin, s);
+  ++g_kernel_launches;
+  kern<<<grid, cta_shape(), 0, s>>>(L.N, L.P, L.block, u, uI, f, fI, W, Winv, L.tiles_int, L.n_tiles_int, p.act,
+                                    p.n_act, colour, L.cptr, L.cps, p.free_if + p.col_off[colour], n, g.n_if_units);
+  if (ev_end) cudaEventRecord(ev_end, s);
   return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t residual(const LevelArgs& L, const ProbArgs& p, const T* u, const T* uI, const T* f, const T* fI, T* r,
                      const T* W, bool seven_point, bool write_r, double* partial, int* n_part, cudaStream_t s) {
-  (void)uI;
-  int np = 0;
   const bool norm = partial != nullptr;
-  if (p.n_act > 0 && L.n_tiles_int > 0) {
-    dim3 g = vol_grid(L.n_tiles_int, p.n_act);
-#define HHG_RES_VOL(S7, WR, NO)                                                                          \
-  do {                                                                                                    \
-    ++g_kernel_launches;                                                                                  \
-    k_res_vol<T, S7, WR, NO><<<g, vol_block(), 0, s>>>(L.N, L.P, L.block, u, f, r, W, L.tiles_int, p.act, \
-                                                       partial);                                          \
-  } while (0)
-    if (seven_point) {
-      if (write_r && norm) HHG_RES_VOL(true, true, true);
-      else if (write_r) HHG_RES_VOL(true, true, false);
-      else if (norm) HHG_RES_VOL(true, false, true);
-    } else {
-      if (write_r && norm) HHG_RES_VOL(false, true, true);
-      else if (write_r) HHG_RES_VOL(false, true, false);
-      else if (norm) HHG_RES_VOL(false, false, true);
-    }
-#undef HHG_RES_VOL
-    np = (int)(g.x * g.y);
-  }
   const int n = p.col_off[4];
-  const int total = n + (write_r ? p.n_zero : 0);
-  if (total > 0) {
-    const unsigned gb = lin_grid(total, 128);
-    double* pp = norm ? partial + np : nullptr;
-    if (write_r && norm)
-      { ++g_kernel_launches; k_res_if<T, true, true><<<gb, 128, 0, s>>>(L.N, L.P, L.block, u, fI, r, W, L.cptr, L.cps, p.free_if, n,
-                                                 p.zero_off, p.n_zero, pp); }
-    else if (write_r)
-      { ++g_kernel_launches; k_res_if<T, true, false><<<gb, 128, 0, s>>>(L.N, L.P, L.block, u, fI, r, W, L.cptr, L.cps, p.free_if, n,
-                                                  p.zero_off, p.n_zero, pp); }
-    else
-      { ++g_kernel_launches; k_res_if<T, false, true><<<gb, 128, 0, s>>>(L.N, L.P, L.block, u, fI, r, W, L.cptr, L.cps, p.free_if, n,
-                                                  p.zero_off, p.n_zero, pp); }
-    if (norm) np += (int)gb;
-  }
-  if (n_part) *n_part = np;
+  const int n_zero = write_r ? p.n_zero : 0;
+  const Units g = units(n + n_zero, L.n_tiles_int, p.n_act);
+  if (n_part) *n_part = 0;
+  if (g.total == 0) return cudaSuccess;
+  void (*kern)(int, int, int64_t, const T*, const T*, const T*, const T*, T*, const T*, const Tile*, int, const int*,
+               int, const int*, const Copy*, const int*, int, const int64_t*, int, int, double*);
+  if (seven_point)
+    kern = write_r ? (norm ? k_res<T, true, true, true> : k_res<T, true, true, false>) : k_res<T, true, false, true>;
+  else
+    kern = write_r ? (norm ? k_res<T, false, true, true> : k_res<T, false, true, false>) : k_res<T, false, false, true>;
+  const unsigned grid = resident_grid((const void*)kern, g.total);
+  if (n_part && norm) *n_part = (int)grid;
+  ++g_kernel_launches;
+  kern<<<grid, cta_shape(), 0, s>>>(L.N, L.P, L.block, u, uI, f, fI, r, W, L.tiles_int, L.n_tiles_int, p.act,
+                                    p.n_act, L.cptr, L.cps, p.free_if, n, p.zero_off, n_zero, g.n_if_units, partial);
   return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t restrict_to(const LevelArgs& C, const LevelArgs& F, const ProbArgs& pc, const T* rf, T* fc, T* fIc, T* uc,
                         T* uIc, cudaStream_t s) {
-  if (pc.n_act > 0 && C.n_tiles_int > 0)
-    { ++g_kernel_launches; k_restrict_vol<T><<<vol_grid(C.n_tiles_int, pc.n_act), vol_block(), 0, s>>>(C.N, C.P, C.block, fc, uc, F.N, F.P,
-                                                                                 F.block, rf, C.tiles_int, pc.act); }
   const int n = pc.col_off[4];
-  const int total = n + pc.n_zero;
-  if (total > 0)
-    { ++g_kernel_launches; k_restrict_if<T><<<lin_grid(total, 128), 128, 0, s>>>(C.N, C.P, C.block, rf, fIc, uc, uIc, C.cptr, C.cps,
-                                                          pc.free_if, n, pc.gather, pc.zero_off, pc.n_zero); }
+  const Units g = units(n + pc.n_zero, C.n_tiles_int, pc.n_act);
+  if (g.total == 0) return cudaSuccess;
+  const unsigned grid = resident_grid((const void*)k_restrict<T>, g.total);
+  ++g_kernel_launches;
+  k_restrict<T><<<grid, cta_shape(), 0, s>>>(C.N, C.P, C.block, fc, fIc, uc, uIc, F.N, F.P, F.block, rf, C.tiles_int,
+                                             C.n_tiles_int, pc.act, pc.n_act, C.cptr, C.cps, pc.free_if, n, pc.gather,
+                                             pc.zero_off, pc.n_zero, g.n_if_units);
   return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t prolong_add(const LevelArgs& F, const LevelArgs& C, const ProbArgs& pf, T* uf, T* uIf, const T* uc,
                         cudaStream_t s) {
-  if (pf.n_act > 0 && F.n_tiles_int > 0)
-    { ++g_kernel_launches; k_prolong_vol<T><<<vol_grid(F.n_tiles_int, pf.n_act), vol_block(), 0, s>>>(F.N, F.P, F.block, uf, C.N, C.P,
-                                                                                C.block, uc, F.tiles_int, pf.act); }
   const int n = pf.col_off[4];
-  if (n > 0)
-    { ++g_kernel_launches; k_prolong_if<T><<<lin_grid(n, 128), 128, 0, s>>>(F.N, F.P, F.block, uf, uIf, C.N, C.P, C.block, uc, F.cptr,
-                                                     F.cps, pf.free_if, n); }
+  const Units g = units(n, F.n_tiles_int, pf.n_act);
+  if (g.total == 0) return cudaSuccess;
+  const unsigned grid = resident_grid((const void*)k_prolong<T>, g.total);
+  ++g_kernel_launches;
+  k_prolong<T><<<grid, cta_shape(), 0, s>>>(F.N, F.P, F.block, uf, uIf, C.N, C.P, C.block, uc, F.tiles_int,
+                                            F.n_tiles_int, pf.act, pf.n_act, F.cptr, F.cps, pf.free_if, n,
+                                            g.n_if_units);
   return cudaGetLastError();
 }
 
@@ -708,25 +797,29 @@ template <class T>
 cudaError_t coarse_cg(const DevProblem& p, const T* f, const T* fI, T* u, T* uI, double rtol, int maxit,
                       cudaStream_t s) {
   if (p.n_cg == 0) return cudaSuccess;
-  { ++g_kernel_launches; k_cg<T><<<1, CG_THREADS, 0, s>>>(p.n_cg, p.rowptr, p.col, p.val, p.fsrc, f, fI, p.uptr, p.udst, p.umaster, u, uI,
-                                   p.cg_work, rtol, maxit, p.cg_iters); }
+  ++g_kernel_launches;
+  k_cg<T><<<1, CG_THREADS, 0, s>>>(p.n_cg, p.rowptr, p.col, p.val, p.fsrc, f, fI, p.uptr, p.udst, p.umaster, u, uI,
+                                   p.cg_work, rtol, maxit, p.cg_iters);
   return cudaGetLastError();
 }
 
 cudaError_t reduce_partials(const double* partial, int n, double* out, cudaStream_t s) {
-  { ++g_kernel_launches; k_reduce<<<1, 1024, 0, s>>>(partial, n, out); }
+  ++g_kernel_launches;
+  k_reduce<<<1, 1024, 0, s>>>(partial, n, out);
   return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t import_vec(const LevelArgs& L, const MacroGeo* geo, int n_macro, int64_t nx, int64_t ny, const double* g,
                        T* blocks, T* masters, bool closed, cudaStream_t s) {
-  const Tile* tl = closed ? L.tiles_all : L.tiles_int;
-  const int nt = closed ? L.n_tiles_all : L.n_tiles_int;
-  if (nt > 0)
-    { ++g_kernel_launches; k_import_vol<T><<<vol_grid(nt, n_macro), vol_block(), 0, s>>>(L.N, L.P, L.block, geo, nx, ny, g, blocks, tl,
-                                                                   closed); }
   (void)masters;
+  // interior imports also go through the closed-lattice tiles (the kernel
+  // filters to the interior)
+  if (L.n_tiles_all > 0) {
+    ++g_kernel_launches;
+    k_import_vol<T><<<dim3((unsigned)L.n_tiles_all, (unsigned)n_macro), cta_shape(), 0, s>>>(
+        L.N, L.P, L.block, geo, nx, ny, g, blocks, L.tiles_all, closed);
+  }
   return cudaGetLastError();
 }
 
@@ -734,65 +827,73 @@ template <class T>
 cudaError_t export_vec(const LevelArgs& L, const MacroGeo* geo, int n_macro, int64_t nx, int64_t ny, const T* blocks,
                        const T* masters, double* g, cudaStream_t s) {
   (void)masters;
-  if (L.n_tiles_int > 0)
-    { ++g_kernel_launches; k_export_vol<T><<<vol_grid(L.n_tiles_int, n_macro), vol_block(), 0, s>>>(L.N, L.P, L.block, geo, nx, ny, blocks,
-                                                                              g, L.tiles_int); }
+  if (L.n_tiles_all > 0) {
+    ++g_kernel_launches;
+    k_export_vol<T><<<dim3((unsigned)L.n_tiles_all, (unsigned)n_macro), cta_shape(), 0, s>>>(
+        L.N, L.P, L.block, geo, nx, ny, blocks, g, L.tiles_all);
+  }
   return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t import_masters(const int64_t* gid, int n, const double* g, T* m, cudaStream_t s) {
-  if (n > 0) { ++g_kernel_launches; k_import_if<T><<<lin_grid(n, 256), 256, 0, s>>>(gid, n, g, m); }
+  if (n > 0) {
+    ++g_kernel_launches;
+    k_import_if<T><<<lin_grid(n, 256), 256, 0, s>>>(gid, n, g, m);
+  }
   return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t export_masters(const int64_t* gid, int n, const T* m, double* g, cudaStream_t s) {
-  if (n > 0) { ++g_kernel_launches; k_export_if<T><<<lin_grid(n, 256), 256, 0, s>>>(gid, n, m, g); }
+  if (n > 0) {
+    ++g_kernel_launches;
+    k_export_if<T><<<lin_grid(n, 256), 256, 0, s>>>(gid, n, m, g);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t set_masters_zero(double* uI, const int* ids, int n, cudaStream_t s) {
-  if (n > 0) { ++g_kernel_launches; k_set_masters_zero<<<lin_grid(n, 256), 256, 0, s>>>(uI, ids, n); }
+  if (n > 0) {
+    ++g_kernel_launches;
+    k_set_masters_zero<<<lin_grid(n, 256), 256, 0, s>>>(uI, ids, n);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t restore_copies(double* u, const double* uI, const int64_t* off, const int* master, int n, cudaStream_t s) {
-  if (n > 0) { ++g_kernel_launches; k_restore<<<lin_grid(n, 256), 256, 0, s>>>(u, uI, off, master, n); }
+  if (n > 0) {
+    ++g_kernel_launches;
+    k_restore<<<lin_grid(n, 256), 256, 0, s>>>(u, uI, off, master, n);
+  }
   return cudaGetLastError();
 }
 
 cudaError_t residual_to_f32(const LevelArgs& L, const ProbArgs& p, const double* u, const double* uI, const double* f,
                             const double* fI, float* f32, float* fI32, const double* W, bool seven_point,
                             double* partial, int* n_part, cudaStream_t s) {
-  (void)uI;
-  int np = 0;
-  if (p.n_act > 0 && L.n_tiles_int > 0) {
-    dim3 g = vol_grid(L.n_tiles_int, p.n_act);
-    if (seven_point)
-      { ++g_kernel_launches; k_res_vol_f32<true><<<g, vol_block(), 0, s>>>(L.N, L.P, L.block, u, f, f32, W, L.tiles_int, p.act, partial); }
-    else
-      { ++g_kernel_launches; k_res_vol_f32<false><<<g, vol_block(), 0, s>>>(L.N, L.P, L.block, u, f, f32, W, L.tiles_int, p.act, partial); }
-    np = (int)(g.x * g.y);
-  }
   const int n = p.col_off[4];
-  if (n > 0) {
-    const unsigned gb = lin_grid(n, 128);
-    { ++g_kernel_launches; k_res_if_f32<<<gb, 128, 0, s>>>(L.N, L.P, L.block, u, fI, fI32, W, L.cptr, L.cps, p.free_if, n, partial + np); }
-    np += (int)gb;
-  }
-  if (n_part) *n_part = np;
+  const Units g = units(n, L.n_tiles_int, p.n_act);
+  if (n_part) *n_part = 0;
+  if (g.total == 0) return cudaSuccess;
+  auto kern = seven_point ? k_res_f32<true> : k_res_f32<false>;
+  const unsigned grid = resident_grid((const void*)kern, g.total);
+  if (n_part) *n_part = (int)grid;
+  ++g_kernel_launches;
+  kern<<<grid, cta_shape(), 0, s>>>(L.N, L.P, L.block, u, uI, f, fI, f32, fI32, W, L.tiles_int, L.n_tiles_int, p.act,
+                                    p.n_act, L.cptr, L.cps, p.free_if, n, g.n_if_units, partial);
   return cudaGetLastError();
 }
 
 cudaError_t add_correction(const LevelArgs& L, const ProbArgs& p, double* u, double* uI, const float* e,
                            const float* eI, cudaStream_t s) {
-  if (p.n_act > 0 && L.n_tiles_int > 0)
-    { ++g_kernel_launches; k_add_corr_vol<<<vol_grid(L.n_tiles_int, p.n_act), vol_block(), 0, s>>>(L.N, L.P, L.block, u, e, L.tiles_int,
-                                                                             p.act); }
   const int n = p.col_off[4];
-  if (n > 0)
-    { ++g_kernel_launches; k_add_corr_if<<<lin_grid(n, 128), 128, 0, s>>>(L.N, L.P, L.block, u, uI, eI, L.cptr, L.cps, p.free_if, n); }
+  const Units g = units(n, L.n_tiles_int, p.n_act);
+  if (g.total == 0) return cudaSuccess;
+  const unsigned grid = resident_grid((const void*)k_add_corr, g.total);
+  ++g_kernel_launches;
+  k_add_corr<<<grid, cta_shape(), 0, s>>>(L.N, L.P, L.block, u, uI, e, eI, L.tiles_int, L.n_tiles_int, p.act,
+                                          p.n_act, L.cptr, L.cps, p.free_if, n, g.n_if_units);
   return cudaGetLastError();
 }
 
@@ -801,10 +902,14 @@ cudaError_t zero_problem_blocks(const LevelArgs& L, const ProbArgs& p, T* u, T* 
   if (p.n_act > 0) {
     const int64_t per = 256 * 8;
     unsigned gx = (unsigned)std::min<int64_t>((L.block + per - 1) / per, 4096);
-    { ++g_kernel_launches; k_zero_blocks<T><<<dim3(gx, p.n_act), 256, 0, s>>>(u, L.block, p.act); }
+    ++g_kernel_launches;
+    k_zero_blocks<T><<<dim3(gx, p.n_act), 256, 0, s>>>(u, L.block, p.act);
   }
   const int n = p.col_off[4];
-  if (n > 0) { ++g_kernel_launches; k_zero_list<T><<<lin_grid(n, 256), 256, 0, s>>>(uI, p.free_if, n); }
+  if (n > 0) {
+    ++g_kernel_launches;
+    k_zero_list<T><<<lin_grid(n, 256), 256, 0, s>>>(uI, p.free_if, n);
+  }
   return cudaGetLastError();
 }
 

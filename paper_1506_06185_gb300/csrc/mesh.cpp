@@ -167,6 +167,21 @@ void build_tiles(int N, bool interior, std::vector<Tile>& out) {
   }
 }
 
+// Row-pair tiles of the volume interior: in slice k the interior rows are
+// j = 1..J, J = N - 2 - k; pair p joins rows 1 + p and J - p, whose lengths add
+// up to N - 1 - k nodes.  A tile holds np consecutive pairs (j0 = first pair,
+// m0 = np), about 512 nodes of one colour, at most 32 pairs.
+void build_pair_tiles(int N, std::vector<Tile>& out) {
+  out.clear();
+  for (int k = 1; k <= N - 3; ++k) {
+    const int J = N - 2 - k;
+    const int pairs = (J + 1) / 2;
+    const int per_pair = std::max(1, (N - 1 - k) / 4);
+    const int np = std::min(32, std::max(1, (512 + per_pair - 1) / per_pair));
+    for (int p0 = 0; p0 < pairs; p0 += np) out.push_back(Tile{k, p0, std::min(np, pairs - p0), 0});
+  }
+}
+
 }  // namespace
 
 bool macro_in_set(const std::vector<unsigned char>& s, int m) { return m >= 0 && m < (int)s.size() && s[m]; }
@@ -270,12 +285,12 @@ void build_host_mesh(HostMesh& m, const int sub[3], int R, int r0, const double*
     L.W.assign((size_t)m.n_macro * 16 * NDIR, 0.0);
     for (int t = 0; t < m.n_macro; ++t)
       for (int mask = 0; mask < 15; ++mask) class_weights(m, t, N, mask, &L.W[((size_t)t * 16 + mask) * NDIR]);
-    for (int t = 0; t < m.n_macro; ++t) {
-      const double* w = &L.W[(size_t)t * 16 * NDIR];
-      for (int d = 1; d < NDIR; ++d) {
-        int dd = d > 7 ? d - 7 : d;
-        if (dd > 3 && w[d] != 0.0) m.seven_point = false;
-      }
+    // 7-point structure: every class (volume and sub-stencils) of every macro
+    // has zero weights off the three chain axes
+    for (size_t q = 0; q < L.W.size(); ++q) {
+      const int d = (int)(q % NDIR);
+      const int dd = d > 7 ? d - 7 : d;
+      if (dd > 3 && L.W[q] != 0.0) m.seven_point = false;
     }
     // interface nodes: vertices, edges, faces
     L.if_cptr.push_back(0);
@@ -308,7 +323,7 @@ void build_host_mesh(HostMesh& m, const int sub[3], int R, int r0, const double*
       }
     }
     L.n_if = (int)L.if_gid.size();
-    build_tiles(N, true, L.tiles_int);
+    build_pair_tiles(N, L.tiles_int);
     build_tiles(N, false, L.tiles_all);
     m.lv.push_back(std::move(L));
   }

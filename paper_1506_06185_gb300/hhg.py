@@ -17,7 +17,8 @@ import os
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "libhhg.so")
+# HHG_LIB may point at another build of the same library (e.g. a debug build)
+LIB_PATH = os.environ.get("HHG_LIB") or os.path.join(_HERE, "_lib", "libhhg.so")
 
 HHG_OK, HHG_ERR_ARG, HHG_ERR_CUDA, HHG_ERR_OOM, HHG_ERR_TIMEOUT, HHG_ERR_NOT_CONVERGED, HHG_ERR_STATE = range(7)
 HHG_RECOVERY_NONE, HHG_RECOVERY_LR, HHG_RECOVERY_DD = 0, 1, 2
