@@ -116,7 +116,7 @@ LevelArgs largs(const hhg_mesh* m, int l) {
   const DevLevelTables& t = m->tab[l];
   LevelArgs a;
   a.N = H.N;
-  a.P = H.P;
+  a.rs = t.SL;
   a.block = H.block;
   a.if_gid = t.if_gid;
   a.cptr = t.if_cptr;
@@ -180,7 +180,6 @@ int alloc_levels(hhg_mesh* m, Prec<T>& P, bool with_r_on_finest) {
     const HostLevel& H = m->host.lv[l];
     DevLevel<T>& D = P.lv[l];
     D.N = H.N;
-    D.P = H.P;
     D.block = H.block;
     D.n_if = H.n_if;
     const size_t nb = (size_t)m->host.n_macro * H.block;
@@ -371,7 +370,7 @@ int setup_fault(hhg_mesh* m, const std::vector<unsigned char>& set) {
     for (int c = H.if_cptr[n]; c < H.if_cptr[n + 1]; ++c) {
       const Copy& cp = H.if_copy[c];
       if (!set[cp.macro]) continue;
-      off.push_back((int64_t)cp.macro * H.block + lidx(H.N, H.P, cp.i, cp.j, cp.k));
+      off.push_back((int64_t)cp.macro * H.block + lidx(H.SL.data(), H.N, cp.i, cp.j, cp.k));
       mst.push_back(n);
     }
   HHG_TRY(upload(m, &m->fault_zero_ids, zero_ids));
@@ -535,6 +534,7 @@ int hhg_mesh_create(const hhg_mesh_desc* desc, hhg_mesh** out) {
   for (int l = 0; l < nl && rc == HHG_OK; ++l) {
     const HostLevel& H = m->host.lv[l];
     DevLevelTables& t = m->tab[l];
+    if ((rc = upload(m.get(), &t.SL, H.SL)) != HHG_OK) break;
     if ((rc = upload(m.get(), &t.if_gid, H.if_gid)) != HHG_OK) break;
     if ((rc = upload(m.get(), &t.if_cptr, H.if_cptr)) != HHG_OK) break;
     if ((rc = upload(m.get(), &t.if_copy, H.if_copy)) != HHG_OK) break;

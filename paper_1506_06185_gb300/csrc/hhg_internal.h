@@ -59,38 +59,51 @@ __host__ __device__ __forceinline__ bool in_lattice(int i, int j, int k, int N) 
 // ---------------------------------------------------------------------------
 // Blocked colour-split layout of one macro's closed lattice at refinement N.
 // The colour of node (i, j, k) is (i + 2j + 3k) mod 4, equal to (x + y + z)
-// mod 4 of its global grid coordinates.  Slice k holds rows j = 0..N-k; each
-// row is stored as four colour segments of P slots; node i of colour c sits
-// in slot i >> 2 of segment c.  A multicolour sweep of one colour therefore
-// reads and writes contiguous slots.
+// mod 4 of its global grid coordinates.  A block holds four colour arrays of
+// CS slots each (block = 4 CS).  Inside each colour array the rows (j, k)
+// follow each other (k major); row (j, k) has L = N + 1 - j - k nodes and
+// gets ceil(L / 4) slots, node i sitting in slot i >> 2 of the row of its
+// colour.  With S(m) = sum_{l=1..m} ceil(l / 4) = (a + 1)(2a + b) for
+// m = 4a + b, the rows of slice k before row j take S(M) - S(M - j) slots
+// (M = N + 1 - k), and the per-level table SL[k] = sum_{k' < k} S(N + 1 - k')
+// gives the slice starts:
+//   offset(i, j, k) = c CS + SL[k] + S(M) - S(M - j) + (i >> 2).
+// The arrays are dense (at most 3 idle slots per row), and a sweep of one
+// colour streams exactly the arrays it reads and writes.  SL has N + 3
+// entries; SL[N + 2] holds CS.
 // ---------------------------------------------------------------------------
-__host__ __device__ __forceinline__ int slots_per_row(int N) {
-  int p = (N + 1 + 3) / 4;
-  return (p + 7) & ~7;
+__host__ __device__ __forceinline__ int slot_prefix(int m) {
+  const int a = m >> 2, b = m & 3;
+  return (a + 1) * (2 * a + b);
 }
 
-__host__ __device__ __forceinline__ int64_t slice_off(int N, int P, int k) {
-  return 4LL * P * ((int64_t)k * (N + 1) - (int64_t)k * (k - 1) / 2);
+__host__ __device__ __forceinline__ int lidx(const int* SL, int N, int i, int j, int k) {
+  const int M = N + 1 - k;
+  return ((i + 2 * j + 3 * k) & 3) * SL[N + 2] + SL[k] + slot_prefix(M) - slot_prefix(M - j) + (i >> 2);
 }
 
-__host__ __device__ __forceinline__ int64_t lidx(int N, int P, int i, int j, int k) {
-  int c = (i + 2 * j + 3 * k) & 3;
-  return slice_off(N, P, k) + (int64_t)(4 * j + c) * P + (i >> 2);
+// Slice-start table (N + 3 entries, last = CS) and block size (4 CS, CS a
+// multiple of 64) of refinement N.
+inline int64_t build_slice_starts(int N, std::vector<int>& SL) {
+  SL.assign((size_t)N + 3, 0);
+  int64_t off = 0;
+  for (int k = 0; k <= N + 1; ++k) {
+    SL[k] = (int)off;
+    if (k <= N) off += slot_prefix(N + 1 - k);
+  }
+  const int64_t cs = (off + 63) & ~int64_t(63);
+  SL[N + 2] = (int)cs;
+  return 4 * cs;
 }
 
-inline int64_t block_elems(int N) {
-  int P = slots_per_row(N);
-  int64_t n = slice_off(N, P, N + 1);
-  return (n + 63) & ~int64_t(63);
-}
-
-// Work tile of the volume kernels.  Interior tiles: slice k, row pairs
-// j0 .. j0 + m0 - 1 (see build_pair_tiles).  Closed-lattice tiles: 8 rows
-// (j0..j0+7) x 32 slots (m0..m0+31) of slice k.
+// Work tile of the volume kernels.  Interior tiles: slices k .. k + pad - 1,
+// row pairs j0 .. j0 + m0 - 1 (see build_pair_tiles).  Closed-lattice tiles:
+// 8 rows (j0..j0+7) x 32 slots (m0..m0+31) of slice k.
 struct Tile {
   int k, j0, m0, pad;
 };
 constexpr int TILE_ROWS = 8;
+constexpr int TILE_SLABS = 8;
 constexpr int TILE_SLOTS = 32;
 
 // A copy of an interface node inside one macro block.
@@ -108,8 +121,9 @@ struct MacroGeo {
 // Host-side mesh description (built by mesh.cpp).
 // ---------------------------------------------------------------------------
 struct HostLevel {
-  int r = 0, N = 0, P = 0;
+  int r = 0, N = 0;
   int64_t block = 0;
+  std::vector<int> SL;                // slice-start table of the block layout
   int n_if = 0;
   std::vector<int64_t> if_gid;        // global grid id of each interface node
   std::vector<int> if_cptr;           // copies CSR
@@ -171,7 +185,7 @@ bool macro_in_set(const std::vector<unsigned char>& s, int m);
 // ---------------------------------------------------------------------------
 template <class T>
 struct DevLevel {
-  int N = 0, P = 0;
+  int N = 0;
   int64_t block = 0;
   int n_if = 0;
   T* u = nullptr;   // blocks [n_macro * block]
@@ -183,6 +197,7 @@ struct DevLevel {
 };
 
 struct DevLevelTables {
+  int* SL = nullptr;                  // slice-start table of the block layout
   int64_t* if_gid = nullptr;
   int* if_cptr = nullptr;
   Copy* if_copy = nullptr;

@@ -8,7 +8,8 @@
 namespace hhg {
 
 struct LevelArgs {
-  int N, P;
+  int N;
+  const int* rs;   // slice-start table of the block layout (N + 3 entries)
   int64_t block;
   const int64_t* if_gid;
   const int* cptr;

@@ -9,9 +9,11 @@
 // Volume work: in slice k of a macro's lattice the interior rows are
 // j = 1..J (J = N - 2 - k) and row j holds N - 1 - j - k nodes.  Rows are
 // paired as (1 + p, J - p), whose lengths add up to N - 1 - k, and a tile
-// holds enough pairs for about 512 nodes of one colour; the CTA flattens the
-// nodes (or 4-node slots) of all its pairs into one index range, so lanes stay
-// busy although the rows shrink across the triangle.  On GB300 the FP64 pipe
+// holds enough pairs for about 512 nodes of one colour in 8 consecutive
+// slices; per slice the CTA flattens the nodes (or 4-node slots) of all its
+// pairs into one index range, so lanes stay busy although the rows shrink
+// across the triangle, and the rows it loads for one slice are still in L1
+// when it processes the next.  On GB300 the FP64 pipe
 // retires 2 DFMA per clock per SM and is charged per warp instruction, so
 // idle lanes cost as much as busy ones.  Consecutive lanes read consecutive
 // slots of one colour segment, so stencil neighbours are contiguous accesses.
@@ -42,13 +44,56 @@ __host__ __device__ constexpr bool used_dir(int d, bool s7) {
   return !s7 || d == 1 || d == 2 || d == 3 || d == 8 || d == 9 || d == 10;
 }
 
-// 32-bit local index (a block holds fewer than 2^31 slots for N <= 1024);
-// 64-bit integer arithmetic is kept out of the per-node work entirely.
-__device__ __forceinline__ int slice32(int N, int P, int k) {
-  return 4 * P * (k * (N + 1) - ((k * (k - 1)) >> 1));
+// Offset of node (i, j, k) inside a macro block (32-bit: a block holds fewer
+// than 2^31 nodes for N <= 1024); rs is the level's slice-start table.
+__device__ __forceinline__ int lidx32(const int* __restrict__ rs, int N, int i, int j, int k) {
+  const int M = N + 1 - k;
+  return ((i + 2 * j + 3 * k) & 3) * __ldg(rs + N + 2) + __ldg(rs + k) + slot_prefix(M) - slot_prefix(M - j) +
+         (i >> 2);
 }
-__device__ __forceinline__ int lidx32(int N, int P, int i, int j, int k) {
-  return slice32(N, P, k) + (4 * j + ((i + 2 * j + 3 * k) & 3)) * P + (i >> 2);
+
+// Offsets of the 7-point neighbourhood of node (i, j, k), colour c, in one
+// go: the five rows involved are derived from a single slot_prefix(M - j).
+// nb[d] for d in {1, 2, 3, 8, 9, 10}; me = the node itself.
+struct Slice {
+  int N, k, M, CS, SLm, SL0, SLp, SMm, SM0, SMp;
+};
+__device__ __forceinline__ Slice slice_consts(const int* __restrict__ rs, int N, int k) {
+  Slice s;
+  s.N = N;
+  s.k = k;
+  s.M = N + 1 - k;
+  s.CS = __ldg(rs + N + 2);
+  s.SLm = k > 0 ? __ldg(rs + k - 1) : 0;
+  s.SL0 = __ldg(rs + k);
+  s.SLp = __ldg(rs + k + 1);
+  s.SMm = slot_prefix(s.M - 1);
+  s.SM0 = slot_prefix(s.M);
+  s.SMp = slot_prefix(s.M + 1);
+  return s;
+}
+struct Nb7 {
+  int me, nb1, nb8, nb2, nb9, nb3, nb10;
+};
+__device__ __forceinline__ Nb7 nb7(const Slice& s, int i, int j) {
+  const int X = slot_prefix(s.M - j);
+  const int L = s.M - j;
+  const int r0 = s.SL0 + s.SM0 - X;           // row (j, k)
+  const int rjp = r0 + ((L + 3) >> 2);        // row (j + 1, k)
+  const int rjm = r0 - ((L + 4) >> 2);        // row (j - 1, k)
+  const int rkp = s.SLp + s.SMm - X;          // row (j - 1, k + 1)
+  const int rkm = s.SLm + s.SMp - X;          // row (j + 1, k - 1)
+  const int c = (i + 2 * j + 3 * s.k) & 3;
+  const int cp = ((c + 1) & 3) * s.CS, cm = ((c + 3) & 3) * s.CS;
+  Nb7 n;
+  n.me = c * s.CS + r0 + (i >> 2);
+  n.nb1 = cp + r0 + ((i + 1) >> 2);           // ( 1,  0, 0)
+  n.nb8 = cm + r0 + ((i - 1) >> 2);           // (-1,  0, 0)
+  n.nb2 = cp + rjp + ((i - 1) >> 2);          // (-1,  1, 0)
+  n.nb9 = cm + rjm + ((i + 1) >> 2);          // ( 1, -1, 0)
+  n.nb3 = cp + rkp + (i >> 2);                // ( 0, -1, 1)
+  n.nb10 = cm + rkm + (i >> 2);               // ( 0,  1, -1)
+  return n;
 }
 
 __device__ __forceinline__ int tid256() { return threadIdx.y * TILE_SLOTS + threadIdx.x; }
@@ -138,15 +183,17 @@ __device__ __forceinline__ void flat_item(const Tile& t, int N, int c, bool colo
   }
 }
 
-// Loop over the interior nodes of a tile, four consecutive nodes
-// i = 4m .. 4m + 3 (one per colour segment) per item; the body sees i, j, k.
-#define HHG_TILE_NODES(NN, t, s_pre, ...)                                 \
-  {                                                                       \
-    const int k = (t).k;                                                  \
-    const int total_ = flat_setup((t), (NN), 0, false, (s_pre));          \
+// Loop over the interior nodes of a tile, slice by slice, four consecutive
+// nodes i = 4m .. 4m + 3 (one per colour array) per item; the body sees i, j,
+// k and the slice constants sc of the iterated level.
+#define HHG_TILE_NODES(NN, RS, t, s_pre, ...)                             \
+  for (int k = (t).k; k < (t).k + (t).pad; ++k) {                         \
+    const Tile ts_{k, (t).j0, (t).m0, 1};                                 \
+    const int total_ = flat_setup(ts_, (NN), 0, false, (s_pre));          \
+    const Slice sc = slice_consts((RS), (NN), k);                         \
     for (int tt = tid256(); tt < total_; tt += CTA) {                     \
       int j, m;                                                           \
-      flat_item((t), (NN), 0, false, (s_pre), tt, j, m);                  \
+      flat_item(ts_, (NN), 0, false, (s_pre), tt, j, m);                  \
       const int L = (NN) - 1 - j - k;                                     \
       _Pragma("unroll") for (int qq = 0; qq < 4; ++qq) {                  \
         const int i = 4 * m + qq;                                         \
@@ -175,7 +222,7 @@ __device__ __forceinline__ void vol_unit(int unit, int n_if_units, int n_tiles, 
 // Off-diagonal part of an interface node's stencil applied to u, and the sum
 // of the diagonal weights, over all copies of the node.
 template <class T, bool S7>
-__device__ __forceinline__ void if_stencil(int N, int P, int64_t block, const T* __restrict__ u,
+__device__ __forceinline__ void if_stencil(int N, const int* __restrict__ rs, int64_t block, const T* __restrict__ u,
                                            const T* __restrict__ W, const Copy* __restrict__ cps, int c0, int c1,
                                            T& off, T& diag) {
   for (int c = c0; c < c1; ++c) {
@@ -192,17 +239,17 @@ __device__ __forceinline__ void if_stencil(int N, int P, int64_t block, const T*
       dir_ijk(d, di, dj, dk);
       const int ni = cp.i + di, nj = cp.j + dj, nk = cp.k + dk;
       if (!in_lattice(ni, nj, nk, N)) continue;
-      off += wd * ub[lidx32(N, P, ni, nj, nk)];
+      off += wd * ub[lidx32(rs, N, ni, nj, nk)];
     }
   }
 }
 
 template <class T>
-__device__ __forceinline__ void write_copies(int N, int P, int64_t block, T* __restrict__ u,
+__device__ __forceinline__ void write_copies(int N, const int* __restrict__ rs, int64_t block, T* __restrict__ u,
                                              const Copy* __restrict__ cps, int c0, int c1, T val) {
   for (int c = c0; c < c1; ++c) {
     const Copy cp = cps[c];
-    u[(size_t)cp.macro * block + lidx32(N, P, cp.i, cp.j, cp.k)] = val;
+    u[(size_t)cp.macro * block + lidx32(rs, N, cp.i, cp.j, cp.k)] = val;
   }
 }
 
@@ -210,7 +257,7 @@ __device__ __forceinline__ void write_copies(int N, int P, int64_t block, T* __r
 // Gauss-Seidel, one colour (§2.1 smoother)
 // ---------------------------------------------------------------------------
 template <class T, bool S7>
-__global__ void __launch_bounds__(CTA) k_gs(int N, int P, int64_t block, T* __restrict__ u, T* __restrict__ uI,
+__global__ void __launch_bounds__(CTA, sizeof(T) == 8 ? 6 : 5) k_gs(int N, const int* __restrict__ rs, int64_t block, T* __restrict__ u, T* __restrict__ uI,
                                             const T* __restrict__ f, const T* __restrict__ fI,
                                             const T* __restrict__ W, const T* __restrict__ Winv,
                                             const Tile* __restrict__ tiles, int n_tiles, const int* __restrict__ act,
@@ -225,39 +272,53 @@ __global__ void __launch_bounds__(CTA) k_gs(int N, int P, int64_t block, T* __re
         const int node = list[q];
         const int c0 = cptr[node], c1 = cptr[node + 1];
         T off = T(0), diag = T(0);
-        if_stencil<T, S7>(N, P, block, u, W, cps, c0, c1, off, diag);
+        if_stencil<T, S7>(N, rs, block, u, W, cps, c0, c1, off, diag);
         const T val = (fI[node] - off) / diag;
         uI[node] = val;
-        write_copies(N, P, block, u, cps, c0, c1, val);
+        write_copies(N, rs, block, u, cps, c0, c1, val);
       }
       continue;
     }
     Tile t;
     int macro;
     vol_unit(unit, n_if_units, n_tiles, tiles, act, t, macro);
-    const int k = t.k;
     T* ub = u + (size_t)macro * block;
     const T* fb = f + (size_t)macro * block;
     const T* w = W + (size_t)macro * 16 * NDIR;
     const T inv = Winv[macro];
-    const int total = flat_setup(t, N, colour, true, s_pre);
+    for (int k = t.k; k < t.k + t.pad; ++k) {
+    const Tile ts{k, t.j0, t.m0, 1};
+    const int total = flat_setup(ts, N, colour, true, s_pre);
+    const Slice sc = slice_consts(rs, N, k);
     for (int tt = tid256(); tt < total; tt += CTA) {
       int j, v, ic, mlo, n;
-      flat_item(t, N, colour, true, s_pre, tt, j, v);
+      flat_item(ts, N, colour, true, s_pre, tt, j, v);
       colour_row(N, j, k, colour, ic, mlo, n);
       const int i = 4 * (mlo + v) + ic;
-      const int me = lidx32(N, P, i, j, k);
-      T acc = fb[me];
+      if (S7) {
+        const Nb7 q = nb7(sc, i, j);
+        T acc = fb[q.me];
+        acc -= w[1] * ub[q.nb1];
+        acc -= w[2] * ub[q.nb2];
+        acc -= w[3] * ub[q.nb3];
+        acc -= w[8] * ub[q.nb8];
+        acc -= w[9] * ub[q.nb9];
+        acc -= w[10] * ub[q.nb10];
+        ub[q.me] = acc * inv;
+      } else {
+        const int me = lidx32(rs, N, i, j, k);
+        T acc = fb[me];
 #pragma unroll
-      for (int d = 1; d < NDIR; ++d) {
-        if (!used_dir(d, S7)) continue;
-        int di, dj, dk;
-        dir_ijk(d, di, dj, dk);
-        acc -= w[d] * ub[lidx32(N, P, i + di, j + dj, k + dk)];
+        for (int d = 1; d < NDIR; ++d) {
+          int di, dj, dk;
+          dir_ijk(d, di, dj, dk);
+          acc -= w[d] * ub[lidx32(rs, N, i + di, j + dj, k + dk)];
+        }
+        ub[me] = acc * inv;
       }
-      ub[me] = acc * inv;
     }
     __syncthreads();
+    }
   }
 }
 
@@ -266,7 +327,7 @@ __global__ void __launch_bounds__(CTA) k_gs(int N, int P, int64_t block, T* __re
 // (zero at the problem's frozen ghost copies) and per-CTA partial sums of r^2
 // ---------------------------------------------------------------------------
 template <class T, bool S7, bool WRITE, bool NORM>
-__global__ void __launch_bounds__(CTA) k_res(int N, int P, int64_t block, const T* __restrict__ u,
+__global__ void __launch_bounds__(CTA, sizeof(T) == 8 ? 6 : 5) k_res(int N, const int* __restrict__ rs, int64_t block, const T* __restrict__ u,
                                              const T* __restrict__ uI, const T* __restrict__ f,
                                              const T* __restrict__ fI, T* __restrict__ r, const T* __restrict__ W,
                                              const Tile* __restrict__ tiles, int n_tiles, const int* __restrict__ act,
@@ -284,9 +345,9 @@ __global__ void __launch_bounds__(CTA) k_res(int N, int P, int64_t block, const 
         const int node = list[q];
         const int c0 = cptr[node], c1 = cptr[node + 1];
         T off = T(0), diag = T(0);
-        if_stencil<T, S7>(N, P, block, u, W, cps, c0, c1, off, diag);
+        if_stencil<T, S7>(N, rs, block, u, W, cps, c0, c1, off, diag);
         const T res = fI[node] - diag * uI[node] - off;
-        if (WRITE) write_copies(N, P, block, r, cps, c0, c1, res);
+        if (WRITE) write_copies(N, rs, block, r, cps, c0, c1, res);
         if (NORM) ss += (double)res * (double)res;
       } else if (WRITE && q < n_list + n_zero) {
         r[zero_off[q - n_list]] = T(0);
@@ -300,15 +361,28 @@ __global__ void __launch_bounds__(CTA) k_res(int N, int P, int64_t block, const 
     const T* fb = f + (size_t)macro * block;
     T* rb = r + (size_t)macro * block;
     const T* w = W + (size_t)macro * 16 * NDIR;
-    HHG_TILE_NODES(N, t, s_pre, {
-      const int me = lidx32(N, P, i, j, k);
-      T acc = fb[me] - w[0] * ub[me];
+    HHG_TILE_NODES(N, rs, t, s_pre, {
+      int me;
+      T acc;
+      if (S7) {
+        const Nb7 q = nb7(sc, i, j);
+        me = q.me;
+        acc = fb[me] - w[0] * ub[me];
+        acc -= w[1] * ub[q.nb1];
+        acc -= w[2] * ub[q.nb2];
+        acc -= w[3] * ub[q.nb3];
+        acc -= w[8] * ub[q.nb8];
+        acc -= w[9] * ub[q.nb9];
+        acc -= w[10] * ub[q.nb10];
+      } else {
+        me = lidx32(rs, N, i, j, k);
+        acc = fb[me] - w[0] * ub[me];
 _Pragma("unroll")
-      for (int d = 1; d < NDIR; ++d) {
-        if (!used_dir(d, S7)) continue;
-        int di, dj, dk;
-        dir_ijk(d, di, dj, dk);
-        acc -= w[d] * ub[lidx32(N, P, i + di, j + dj, k + dk)];
+        for (int d = 1; d < NDIR; ++d) {
+          int di, dj, dk;
+          dir_ijk(d, di, dj, dk);
+          acc -= w[d] * ub[lidx32(rs, N, i + di, j + dj, k + dk)];
+        }
       }
       if (WRITE) rb[me] = acc;
       if (NORM) ss += (double)acc * (double)acc;
@@ -324,8 +398,8 @@ _Pragma("unroll")
 // Restriction R = P^T onto the coarse level (§2.1); zero the coarse correction
 // ---------------------------------------------------------------------------
 template <class T>
-__global__ void __launch_bounds__(CTA) k_restrict(int Nc, int Pc, int64_t bc, T* __restrict__ fc, T* __restrict__ fIc,
-                                                  T* __restrict__ uc, T* __restrict__ uIc, int Nf, int Pf, int64_t bf,
+__global__ void __launch_bounds__(CTA) k_restrict(int Nc, const int* __restrict__ rsc, int64_t bc, T* __restrict__ fc, T* __restrict__ fIc,
+                                                  T* __restrict__ uc, T* __restrict__ uIc, int Nf, const int* __restrict__ rsf, int64_t bf,
                                                   const T* __restrict__ rf, const Tile* __restrict__ tiles, int n_tiles,
                                                   const int* __restrict__ act, int n_act,
                                                   const int* __restrict__ cptr, const Copy* __restrict__ cps,
@@ -343,7 +417,7 @@ __global__ void __launch_bounds__(CTA) k_restrict(int Nc, int Pc, int64_t bc, T*
         for (int e = 1; e < NDIR; ++e) acc += rf[g[e]];
         fIc[node] = rf[g[0]] + T(0.5) * acc;
         uIc[node] = T(0);
-        write_copies(Nc, Pc, bc, uc, cps, cptr[node], cptr[node + 1], T(0));
+        write_copies(Nc, rsc, bc, uc, cps, cptr[node], cptr[node + 1], T(0));
       } else if (q < n_list + n_zero) {
         uc[zero_off[q - n_list]] = T(0);
       }
@@ -355,17 +429,17 @@ __global__ void __launch_bounds__(CTA) k_restrict(int Nc, int Pc, int64_t bc, T*
     const T* rb = rf + (size_t)macro * bf;
     T* fb = fc + (size_t)macro * bc;
     T* ub = uc + (size_t)macro * bc;
-    HHG_TILE_NODES(Nc, t, s_pre, {
+    HHG_TILE_NODES(Nc, rsc, t, s_pre, {
       const int fi = 2 * i, fj = 2 * j, fk = 2 * k;
       T acc = T(0);
 _Pragma("unroll")
       for (int d = 1; d < NDIR; ++d) {
         int di, dj, dk;
         dir_ijk(d, di, dj, dk);
-        acc += rb[lidx32(Nf, Pf, fi + di, fj + dj, fk + dk)];
+        acc += rb[lidx32(rsf, Nf, fi + di, fj + dj, fk + dk)];
       }
-      const int me = lidx32(Nc, Pc, i, j, k);
-      fb[me] = rb[lidx32(Nf, Pf, fi, fj, fk)] + T(0.5) * acc;
+      const int me = lidx32(rsc, Nc, i, j, k);
+      fb[me] = rb[lidx32(rsf, Nf, fi, fj, fk)] + T(0.5) * acc;
       ub[me] = T(0);
     })
   }
@@ -375,9 +449,9 @@ _Pragma("unroll")
 // Prolongation u_f += P u_c (linear interpolation, §2.1)
 // ---------------------------------------------------------------------------
 template <class T>
-__device__ __forceinline__ T interp(const T* __restrict__ cb, int Nc, int Pc, int i, int j, int k) {
+__device__ __forceinline__ T interp(const T* __restrict__ cb, int Nc, const int* __restrict__ rsc, int i, int j, int k) {
   const int pi = i & 1, pj = j & 1, pk = k & 1;
-  if (!(pi | pj | pk)) return cb[lidx32(Nc, Pc, i >> 1, j >> 1, k >> 1)];
+  if (!(pi | pj | pk)) return cb[lidx32(rsc, Nc, i >> 1, j >> 1, k >> 1)];
   // the coarse edge through a fine midpoint: parity -> local direction
   int di, dj, dk;
   const int code = pi | (pj << 1) | (pk << 2);
@@ -390,14 +464,14 @@ __device__ __forceinline__ T interp(const T* __restrict__ cb, int Nc, int Pc, in
     case 6: di = 0; dj = -1; dk = 1; break;
     default: di = 1; dj = -1; dk = 1; break;
   }
-  const T a = cb[lidx32(Nc, Pc, (i - di) >> 1, (j - dj) >> 1, (k - dk) >> 1)];
-  const T b = cb[lidx32(Nc, Pc, (i + di) >> 1, (j + dj) >> 1, (k + dk) >> 1)];
+  const T a = cb[lidx32(rsc, Nc, (i - di) >> 1, (j - dj) >> 1, (k - dk) >> 1)];
+  const T b = cb[lidx32(rsc, Nc, (i + di) >> 1, (j + dj) >> 1, (k + dk) >> 1)];
   return T(0.5) * (a + b);
 }
 
 template <class T>
-__global__ void __launch_bounds__(CTA) k_prolong(int Nf, int Pf, int64_t bf, T* __restrict__ uf, T* __restrict__ uIf,
-                                                 int Nc, int Pc, int64_t bc, const T* __restrict__ uc,
+__global__ void __launch_bounds__(CTA) k_prolong(int Nf, const int* __restrict__ rsf, int64_t bf, T* __restrict__ uf, T* __restrict__ uIf,
+                                                 int Nc, const int* __restrict__ rsc, int64_t bc, const T* __restrict__ uc,
                                                  const Tile* __restrict__ tiles, int n_tiles,
                                                  const int* __restrict__ act, int n_act, const int* __restrict__ cptr,
                                                  const Copy* __restrict__ cps, const int* __restrict__ list,
@@ -410,9 +484,9 @@ __global__ void __launch_bounds__(CTA) k_prolong(int Nf, int Pf, int64_t bf, T* 
         const int node = list[q];
         const int c0 = cptr[node], c1 = cptr[node + 1];
         const Copy cp = cps[c0];
-        const T val = uIf[node] + interp(uc + (size_t)cp.macro * bc, Nc, Pc, cp.i, cp.j, cp.k);
+        const T val = uIf[node] + interp(uc + (size_t)cp.macro * bc, Nc, rsc, cp.i, cp.j, cp.k);
         uIf[node] = val;
-        write_copies(Nf, Pf, bf, uf, cps, c0, c1, val);
+        write_copies(Nf, rsf, bf, uf, cps, c0, c1, val);
       }
       continue;
     }
@@ -421,7 +495,7 @@ __global__ void __launch_bounds__(CTA) k_prolong(int Nf, int Pf, int64_t bf, T* 
     vol_unit(unit, n_if_units, n_tiles, tiles, act, t, macro);
     T* fb = uf + (size_t)macro * bf;
     const T* cb = uc + (size_t)macro * bc;
-    HHG_TILE_NODES(Nf, t, s_pre, { fb[lidx32(Nf, Pf, i, j, k)] += interp(cb, Nc, Pc, i, j, k); })
+    HHG_TILE_NODES(Nf, rsf, t, s_pre, { fb[lidx32(rsf, Nf, i, j, k)] += interp(cb, Nc, rsc, i, j, k); })
   }
 }
 
@@ -430,7 +504,7 @@ __global__ void __launch_bounds__(CTA) k_prolong(int Nf, int Pf, int64_t bf, T* 
 // side (with partial sums of r^2), and the FP64 update u += e
 // ---------------------------------------------------------------------------
 template <bool S7>
-__global__ void __launch_bounds__(CTA) k_res_f32(int N, int P, int64_t block, const double* __restrict__ u,
+__global__ void __launch_bounds__(CTA) k_res_f32(int N, const int* __restrict__ rs, int64_t block, const double* __restrict__ u,
                                                  const double* __restrict__ uI, const double* __restrict__ f,
                                                  const double* __restrict__ fI, float* __restrict__ f32,
                                                  float* __restrict__ fI32, const double* __restrict__ W,
@@ -448,7 +522,7 @@ __global__ void __launch_bounds__(CTA) k_res_f32(int N, int P, int64_t block, co
       if (q < n_list) {
         const int node = list[q];
         double off = 0.0, diag = 0.0;
-        if_stencil<double, S7>(N, P, block, u, W, cps, cptr[node], cptr[node + 1], off, diag);
+        if_stencil<double, S7>(N, rs, block, u, W, cps, cptr[node], cptr[node + 1], off, diag);
         const double res = fI[node] - diag * uI[node] - off;
         fI32[node] = (float)res;
         ss += res * res;
@@ -462,15 +536,28 @@ __global__ void __launch_bounds__(CTA) k_res_f32(int N, int P, int64_t block, co
     const double* fb = f + (size_t)macro * block;
     float* ob = f32 + (size_t)macro * block;
     const double* w = W + (size_t)macro * 16 * NDIR;
-    HHG_TILE_NODES(N, t, s_pre, {
-      const int me = lidx32(N, P, i, j, k);
-      double acc = fb[me] - w[0] * ub[me];
+    HHG_TILE_NODES(N, rs, t, s_pre, {
+      int me;
+      double acc;
+      if (S7) {
+        const Nb7 q = nb7(sc, i, j);
+        me = q.me;
+        acc = fb[me] - w[0] * ub[me];
+        acc -= w[1] * ub[q.nb1];
+        acc -= w[2] * ub[q.nb2];
+        acc -= w[3] * ub[q.nb3];
+        acc -= w[8] * ub[q.nb8];
+        acc -= w[9] * ub[q.nb9];
+        acc -= w[10] * ub[q.nb10];
+      } else {
+        me = lidx32(rs, N, i, j, k);
+        acc = fb[me] - w[0] * ub[me];
 _Pragma("unroll")
-      for (int d = 1; d < NDIR; ++d) {
-        if (!used_dir(d, S7)) continue;
-        int di, dj, dk;
-        dir_ijk(d, di, dj, dk);
-        acc -= w[d] * ub[lidx32(N, P, i + di, j + dj, k + dk)];
+        for (int d = 1; d < NDIR; ++d) {
+          int di, dj, dk;
+          dir_ijk(d, di, dj, dk);
+          acc -= w[d] * ub[lidx32(rs, N, i + di, j + dj, k + dk)];
+        }
       }
       ob[me] = (float)acc;
       ss += acc * acc;
@@ -480,7 +567,7 @@ _Pragma("unroll")
   if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(CTA) k_add_corr(int N, int P, int64_t block, double* __restrict__ u,
+__global__ void __launch_bounds__(CTA) k_add_corr(int N, const int* __restrict__ rs, int64_t block, double* __restrict__ u,
                                                   double* __restrict__ uI, const float* __restrict__ e,
                                                   const float* __restrict__ eI, const Tile* __restrict__ tiles,
                                                   int n_tiles, const int* __restrict__ act, int n_act,
@@ -494,7 +581,7 @@ __global__ void __launch_bounds__(CTA) k_add_corr(int N, int P, int64_t block, d
         const int node = list[q];
         const double val = uI[node] + (double)eI[node];
         uI[node] = val;
-        write_copies(N, P, block, u, cps, cptr[node], cptr[node + 1], val);
+        write_copies(N, rs, block, u, cps, cptr[node], cptr[node + 1], val);
       }
       continue;
     }
@@ -503,8 +590,8 @@ __global__ void __launch_bounds__(CTA) k_add_corr(int N, int P, int64_t block, d
     vol_unit(unit, n_if_units, n_tiles, tiles, act, t, macro);
     double* ub = u + (size_t)macro * block;
     const float* eb = e + (size_t)macro * block;
-    HHG_TILE_NODES(N, t, s_pre, {
-      const int me = lidx32(N, P, i, j, k);
+    HHG_TILE_NODES(N, rs, t, s_pre, {
+      const int me = lidx32(rs, N, i, j, k);
       ub[me] += (double)eb[me];
     })
   }
@@ -605,7 +692,7 @@ __device__ __forceinline__ int64_t dev_gid(const MacroGeo& g, int N, int i, int 
 }
 
 template <class T>
-__global__ void __launch_bounds__(CTA) k_import_vol(int N, int P, int64_t block, const MacroGeo* __restrict__ geo,
+__global__ void __launch_bounds__(CTA) k_import_vol(int N, const int* __restrict__ rs, int64_t block, const MacroGeo* __restrict__ geo,
                                                     int64_t nx, int64_t ny, const double* __restrict__ g,
                                                     T* __restrict__ dst, const Tile* __restrict__ tiles, bool closed) {
   const Tile t = tiles[blockIdx.x];
@@ -621,12 +708,12 @@ __global__ void __launch_bounds__(CTA) k_import_vol(int N, int P, int64_t block,
   for (int q = 0; q < 4; ++q) {
     const int i = 4 * m + q;
     if (i < lo || i + j + k > top) continue;
-    b[lidx32(N, P, i, j, k)] = (T)g[dev_gid(gm, N, i, j, k, nx, ny)];
+    b[lidx32(rs, N, i, j, k)] = (T)g[dev_gid(gm, N, i, j, k, nx, ny)];
   }
 }
 
 template <class T>
-__global__ void __launch_bounds__(CTA) k_export_vol(int N, int P, int64_t block, const MacroGeo* __restrict__ geo,
+__global__ void __launch_bounds__(CTA) k_export_vol(int N, const int* __restrict__ rs, int64_t block, const MacroGeo* __restrict__ geo,
                                                     int64_t nx, int64_t ny, const T* __restrict__ src,
                                                     double* __restrict__ g, const Tile* __restrict__ tiles) {
   const Tile t = tiles[blockIdx.x];
@@ -641,7 +728,7 @@ __global__ void __launch_bounds__(CTA) k_export_vol(int N, int P, int64_t block,
   for (int q = 0; q < 4; ++q) {
     const int i = 4 * m + q;
     if (i < 1 || i + j + k > N - 1) continue;
-    g[dev_gid(gm, N, i, j, k, nx, ny)] = (double)b[lidx32(N, P, i, j, k)];
+    g[dev_gid(gm, N, i, j, k, nx, ny)] = (double)b[lidx32(rs, N, i, j, k)];
   }
 }
 
@@ -736,7 +823,7 @@ cudaError_t gs_colour(const LevelArgs& L, const ProbArgs& p, T* u, T* uI, const 
   const unsigned grid = resident_grid((const void*)kern, g.total);
   if (ev_begin) cudaEventRecord(ev_begin, s);
   ++g_kernel_launches;
-  kern<<<grid, cta_shape(), 0, s>>>(L.N, L.P, L.block, u, uI, f, fI, W, Winv, L.tiles_int, L.n_tiles_int, p.act,
+  kern<<<grid, cta_shape(), 0, s>>>(L.N, L.rs, L.block, u, uI, f, fI, W, Winv, L.tiles_int, L.n_tiles_int, p.act,
                                     p.n_act, colour, L.cptr, L.cps, p.free_if + p.col_off[colour], n, g.n_if_units);
   if (ev_end) cudaEventRecord(ev_end, s);
   return cudaGetLastError();
@@ -751,7 +838,7 @@ cudaError_t residual(const LevelArgs& L, const ProbArgs& p, const T* u, const T*
   const Units g = units(n + n_zero, L.n_tiles_int, p.n_act);
   if (n_part) *n_part = 0;
   if (g.total == 0) return cudaSuccess;
-  void (*kern)(int, int, int64_t, const T*, const T*, const T*, const T*, T*, const T*, const Tile*, int, const int*,
+  void (*kern)(int, const int*, int64_t, const T*, const T*, const T*, const T*, T*, const T*, const Tile*, int, const int*,
                int, const int*, const Copy*, const int*, int, const int64_t*, int, int, double*);
   if (seven_point)
     kern = write_r ? (norm ? k_res<T, true, true, true> : k_res<T, true, true, false>) : k_res<T, true, false, true>;
@@ -760,7 +847,7 @@ cudaError_t residual(const LevelArgs& L, const ProbArgs& p, const T* u, const T*
   const unsigned grid = resident_grid((const void*)kern, g.total);
   if (n_part && norm) *n_part = (int)grid;
   ++g_kernel_launches;
-  kern<<<grid, cta_shape(), 0, s>>>(L.N, L.P, L.block, u, uI, f, fI, r, W, L.tiles_int, L.n_tiles_int, p.act,
+  kern<<<grid, cta_shape(), 0, s>>>(L.N, L.rs, L.block, u, uI, f, fI, r, W, L.tiles_int, L.n_tiles_int, p.act,
                                     p.n_act, L.cptr, L.cps, p.free_if, n, p.zero_off, n_zero, g.n_if_units, partial);
   return cudaGetLastError();
 }
@@ -773,7 +860,7 @@ cudaError_t restrict_to(const LevelArgs& C, const LevelArgs& F, const ProbArgs& 
   if (g.total == 0) return cudaSuccess;
   const unsigned grid = resident_grid((const void*)k_restrict<T>, g.total);
   ++g_kernel_launches;
-  k_restrict<T><<<grid, cta_shape(), 0, s>>>(C.N, C.P, C.block, fc, fIc, uc, uIc, F.N, F.P, F.block, rf, C.tiles_int,
+  k_restrict<T><<<grid, cta_shape(), 0, s>>>(C.N, C.rs, C.block, fc, fIc, uc, uIc, F.N, F.rs, F.block, rf, C.tiles_int,
                                              C.n_tiles_int, pc.act, pc.n_act, C.cptr, C.cps, pc.free_if, n, pc.gather,
                                              pc.zero_off, pc.n_zero, g.n_if_units);
   return cudaGetLastError();
@@ -787,7 +874,7 @@ cudaError_t prolong_add(const LevelArgs& F, const LevelArgs& C, const ProbArgs& 
   if (g.total == 0) return cudaSuccess;
   const unsigned grid = resident_grid((const void*)k_prolong<T>, g.total);
   ++g_kernel_launches;
-  k_prolong<T><<<grid, cta_shape(), 0, s>>>(F.N, F.P, F.block, uf, uIf, C.N, C.P, C.block, uc, F.tiles_int,
+  k_prolong<T><<<grid, cta_shape(), 0, s>>>(F.N, F.rs, F.block, uf, uIf, C.N, C.rs, C.block, uc, F.tiles_int,
                                             F.n_tiles_int, pf.act, pf.n_act, F.cptr, F.cps, pf.free_if, n,
                                             g.n_if_units);
   return cudaGetLastError();
@@ -818,7 +905,7 @@ cudaError_t import_vec(const LevelArgs& L, const MacroGeo* geo, int n_macro, int
   if (L.n_tiles_all > 0) {
     ++g_kernel_launches;
     k_import_vol<T><<<dim3((unsigned)L.n_tiles_all, (unsigned)n_macro), cta_shape(), 0, s>>>(
-        L.N, L.P, L.block, geo, nx, ny, g, blocks, L.tiles_all, closed);
+        L.N, L.rs, L.block, geo, nx, ny, g, blocks, L.tiles_all, closed);
   }
   return cudaGetLastError();
 }
@@ -830,7 +917,7 @@ cudaError_t export_vec(const LevelArgs& L, const MacroGeo* geo, int n_macro, int
   if (L.n_tiles_all > 0) {
     ++g_kernel_launches;
     k_export_vol<T><<<dim3((unsigned)L.n_tiles_all, (unsigned)n_macro), cta_shape(), 0, s>>>(
-        L.N, L.P, L.block, geo, nx, ny, blocks, g, L.tiles_all);
+        L.N, L.rs, L.block, geo, nx, ny, blocks, g, L.tiles_all);
   }
   return cudaGetLastError();
 }
@@ -880,7 +967,7 @@ cudaError_t residual_to_f32(const LevelArgs& L, const ProbArgs& p, const double*
   const unsigned grid = resident_grid((const void*)kern, g.total);
   if (n_part) *n_part = (int)grid;
   ++g_kernel_launches;
-  kern<<<grid, cta_shape(), 0, s>>>(L.N, L.P, L.block, u, uI, f, fI, f32, fI32, W, L.tiles_int, L.n_tiles_int, p.act,
+  kern<<<grid, cta_shape(), 0, s>>>(L.N, L.rs, L.block, u, uI, f, fI, f32, fI32, W, L.tiles_int, L.n_tiles_int, p.act,
                                     p.n_act, L.cptr, L.cps, p.free_if, n, g.n_if_units, partial);
   return cudaGetLastError();
 }
@@ -892,7 +979,7 @@ cudaError_t add_correction(const LevelArgs& L, const ProbArgs& p, double* u, dou
   if (g.total == 0) return cudaSuccess;
   const unsigned grid = resident_grid((const void*)k_add_corr, g.total);
   ++g_kernel_launches;
-  k_add_corr<<<grid, cta_shape(), 0, s>>>(L.N, L.P, L.block, u, uI, e, eI, L.tiles_int, L.n_tiles_int, p.act,
+  k_add_corr<<<grid, cta_shape(), 0, s>>>(L.N, L.rs, L.block, u, uI, e, eI, L.tiles_int, L.n_tiles_int, p.act,
                                           p.n_act, L.cptr, L.cps, p.free_if, n, g.n_if_units);
   return cudaGetLastError();
 }

@@ -169,16 +169,19 @@ void build_tiles(int N, bool interior, std::vector<Tile>& out) {
 
 // Row-pair tiles of the volume interior: in slice k the interior rows are
 // j = 1..J, J = N - 2 - k; pair p joins rows 1 + p and J - p, whose lengths add
-// up to N - 1 - k nodes.  A tile holds np consecutive pairs (j0 = first pair,
-// m0 = np), about 512 nodes of one colour, at most 32 pairs.
+// up to N - 1 - k nodes.  A tile covers pairs j0 .. j0 + m0 - 1 (about 512
+// nodes of one colour in its first slice, at most 32 pairs) in the TILE_SLABS
+// consecutive slices k .. k + pad - 1, so that the CTA that loads a slice's
+// rows reuses them for the next slice (pairs beyond a slice's count are empty).
 void build_pair_tiles(int N, std::vector<Tile>& out) {
   out.clear();
-  for (int k = 1; k <= N - 3; ++k) {
-    const int J = N - 2 - k;
+  for (int k0 = 1; k0 <= N - 3; k0 += TILE_SLABS) {
+    const int nk = std::min(TILE_SLABS, N - 2 - k0);
+    const int J = N - 2 - k0;
     const int pairs = (J + 1) / 2;
-    const int per_pair = std::max(1, (N - 1 - k) / 4);
+    const int per_pair = std::max(1, (N - 1 - k0) / 4);
     const int np = std::min(32, std::max(1, (512 + per_pair - 1) / per_pair));
-    for (int p0 = 0; p0 < pairs; p0 += np) out.push_back(Tile{k, p0, std::min(np, pairs - p0), 0});
+    for (int p0 = 0; p0 < pairs; p0 += np) out.push_back(Tile{k0, p0, std::min(np, pairs - p0), nk});
   }
 }
 
@@ -278,8 +281,7 @@ void build_host_mesh(HostMesh& m, const int sub[3], int R, int r0, const double*
     HostLevel L;
     L.r = r;
     L.N = 1 << r;
-    L.P = slots_per_row(L.N);
-    L.block = block_elems(L.N);
+    L.block = build_slice_starts(L.N, L.SL);
     const int N = L.N;
     // stencils
     L.W.assign((size_t)m.n_macro * 16 * NDIR, 0.0);
@@ -364,7 +366,7 @@ void build_problem(const HostMesh& m, int kind, const std::vector<unsigned char>
         for (int c = L.if_cptr[n]; c < L.if_cptr[n + 1]; ++c) {
           const Copy& cp = L.if_copy[c];
           if (p.macro_active[cp.macro])
-            P.zero_off.push_back((int64_t)cp.macro * L.block + lidx(L.N, L.P, cp.i, cp.j, cp.k));
+            P.zero_off.push_back((int64_t)cp.macro * L.block + lidx(L.SL.data(), L.N, cp.i, cp.j, cp.k));
         }
       }
     }
@@ -396,7 +398,7 @@ void build_problem(const HostMesh& m, int kind, const std::vector<unsigned char>
           if (std::find(seen.begin(), seen.end(), g) != seen.end()) continue;
           seen.push_back(g);
           if (cnt >= NDIR) throw std::runtime_error("restriction stencil has more than 15 points");
-          int64_t off = (int64_t)cp.macro * F.block + lidx(F.N, F.P, fi, fj, fk);
+          int64_t off = (int64_t)cp.macro * F.block + lidx(F.SL.data(), F.N, fi, fj, fk);
           // the centre (the coarse node itself, weight 1) comes first; the 14
           // edge midpoints follow (weight 1/2)
           if (d == 0 && cnt != 0) throw std::runtime_error("restriction centre not first");
@@ -446,7 +448,7 @@ void build_problem(const HostMesh& m, int kind, const std::vector<unsigned char>
           if (it == cidx.end()) continue;
           row[it->second] += w[e];
         }
-        p.udst.push_back((int64_t)cp.macro * L.block + lidx(N, L.P, cp.i, cp.j, cp.k));
+        p.udst.push_back((int64_t)cp.macro * L.block + lidx(L.SL.data(), N, cp.i, cp.j, cp.k));
       }
       for (auto& kv : row) {
         p.col.push_back(kv.first);
