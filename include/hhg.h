@@ -157,6 +157,18 @@ typedef struct {
 int hhg_solve(hhg_mesh* mesh, const hhg_solve_opts* opts, double* hist, int* n_hist,
               int* cycles, void* stream);
 
+/* Differentiation support (an extension of the method of §2.1 to a
+ * per-macro diffusion coefficient k_T, A = sum_T k_T A_T).
+ * hhg_set_coefficients: replace the coefficients (host, n_macro positive
+ * values) and rebuild every level's stencils and the coarse CG matrices; the
+ * iterate and right-hand side are kept.  Synchronises the stream.
+ * hhg_grad_coeff: with u a solution (global vector with its Dirichlet
+ * values) and lam the adjoint solution of A_FF lam = dL/du_F (zero on the
+ * Dirichlet nodes), write dL/dk_T = -lam^T A_T u for every macro into grad
+ * (host, n_macro).  u becomes the mesh's iterate.  Synchronises the stream. */
+int hhg_set_coefficients(hhg_mesh* mesh, const double* coeff, void* stream);
+int hhg_grad_coeff(hhg_mesh* mesh, const double* u, const double* lam, double* grad, void* stream);
+
 /* Allocation-free V-cycle (an interface addition; the paper has no
  * counterpart).  Some callers cannot call cudaMalloc at all once they are
  * running: for example a host application that hands the device's memory to

@@ -74,6 +74,8 @@ struct hhg_mesh {
   std::vector<void*> allocs;
   int64_t bytes = 0;
   double* host_scalar = nullptr;   // pinned
+  double* grad_partial = nullptr;  // coefficient-gradient partial sums
+  double* grad_out = nullptr;
   // profiling of the finest-level Gauss-Seidel volume kernel of the global problem
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_ev;
@@ -144,6 +146,8 @@ ProbArgs pargs(const DevProblem& p, int l) {
 int upload_problem(hhg_mesh* m, const HostProblem& h, DevProblem& d) {
   d.kind = h.kind;
   d.act_host = h.act;
+  d.macro_active_host = h.macro_active;
+  d.free0_host = h.lv.empty() ? std::vector<int>() : h.lv[0].free_if;
   d.n_act = (int)h.act.size();
   HHG_TRY(upload(m, &d.act, h.act));
   d.lv.assign(h.lv.size(), DevProblemLevel());
@@ -155,6 +159,7 @@ int upload_problem(hhg_mesh* m, const HostProblem& h, DevProblem& d) {
     HHG_TRY(upload(m, &d.lv[l].gather, h.lv[l].gather));
   }
   d.n_cg = h.n_cg;
+  d.nnz = (int64_t)h.val.size();
   HHG_TRY(upload(m, &d.rowptr, h.rowptr));
   HHG_TRY(upload(m, &d.col, h.col));
   HHG_TRY(upload(m, &d.val, h.val));
@@ -437,6 +442,47 @@ int recover(hhg_mesh* m, int n_local, int n_global, bool mixed, int pre, int pos
   return HHG_OK;
 }
 
+// Stencils of all levels and the coarse CG matrices for new coefficients.
+int update_coefficients(hhg_mesh* m, const double* coeff) {
+  try {
+    set_coefficients(m->host, coeff);
+  } catch (const std::exception& e) {
+    return fail(HHG_ERR_ARG, std::string("coefficients: ") + e.what());
+  }
+  const int nl = (int)m->host.lv.size();
+  for (int l = 0; l < nl; ++l) {
+    const HostLevel& H = m->host.lv[l];
+    std::vector<double> winv(m->host.n_macro);
+    for (int t = 0; t < m->host.n_macro; ++t) winv[t] = 1.0 / H.W[(size_t)t * 16 * NDIR];
+    HHG_CUDA(cudaMemcpy(m->d64.lv[l].W, H.W.data(), H.W.size() * sizeof(double), cudaMemcpyHostToDevice));
+    HHG_CUDA(cudaMemcpy(m->d64.Winv[l], winv.data(), winv.size() * sizeof(double), cudaMemcpyHostToDevice));
+    if (m->precision == 32) {
+      std::vector<float> w32(H.W.begin(), H.W.end()), wi32(winv.begin(), winv.end());
+      HHG_CUDA(cudaMemcpy(m->d32.lv[l].W, w32.data(), w32.size() * sizeof(float), cudaMemcpyHostToDevice));
+      HHG_CUDA(cudaMemcpy(m->d32.Winv[l], wi32.data(), wi32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
+  }
+  std::vector<DevProblem*> probs = {&m->global};
+  if (m->has_fault) {
+    probs.push_back(&m->faulty);
+    probs.push_back(&m->healthy);
+  }
+  for (DevProblem* d : probs) {
+    HostProblem h;
+    h.kind = d->kind;
+    h.act = d->act_host;
+    h.macro_active = d->macro_active_host;
+    h.lv.resize(1);
+    h.lv[0].free_if = d->free0_host;
+    assemble_coarse(m->host, h);
+    if ((int64_t)h.val.size() != d->nnz || h.n_cg != d->n_cg)
+      return fail(HHG_ERR_STATE, "coarse system changed shape");
+    if (!h.val.empty())
+      HHG_CUDA(cudaMemcpy(d->val, h.val.data(), h.val.size() * sizeof(double), cudaMemcpyHostToDevice));
+  }
+  return HHG_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Allocation-free V-cycle: the coarse-grid CG keeps its work vectors (x, r, p,
 // A p) in this file-scope static device array instead of the mesh's own
@@ -671,6 +717,42 @@ int hhg_recover_local(hhg_mesh* m, const int* ids, int n, int n_local, int n_glo
   HHG_TRY(setup_fault(m, set));
   return recover(m, n_local, n_global, false, 3, 3, 1e-12, 1000, seconds_local, seconds_global,
                  (cudaStream_t)stream);
+}
+
+int hhg_set_coefficients(hhg_mesh* m, const double* coeff, void* stream) {
+  if (!m || !coeff) return fail(HHG_ERR_ARG, "null argument");
+  for (int t = 0; t < m->host.n_macro; ++t)
+    if (!(coeff[t] > 0.0)) return fail(HHG_ERR_ARG, "coefficients must be positive");
+  HHG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
+  return update_coefficients(m, coeff);
+}
+
+int hhg_grad_coeff(hhg_mesh* m, const double* u, const double* lam, double* grad, void* stream) {
+  if (!m || !u || !lam || !grad) return fail(HHG_ERR_ARG, "null argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int L = (int)m->host.lv.size() - 1;
+  const LevelArgs a = largs(m, L);
+  DevLevel<double>& D = m->d64.lv[L];
+  const int n_macro = m->host.n_macro;
+  if (!m->grad_partial) {
+    HHG_TRY(dalloc(m, &m->grad_partial, (size_t)n_macro * std::max(1, a.n_tiles_all)));
+    HHG_TRY(dalloc(m, &m->grad_out, (size_t)n_macro));
+  }
+  int rc;
+  const double* g = stage_in(m, u, s, &rc);
+  if (!g) return rc;
+  HHG_CUDA(import_vec<double>(a, m->geo, n_macro, m->host.nx, m->host.ny, g, D.u, D.uI, true, s));
+  HHG_CUDA(import_masters<double>(a.if_gid, m->host.lv[L].n_if, g, D.uI, s));
+  const double* gl = stage_in(m, lam, s, &rc);
+  if (!gl) return rc;
+  HHG_CUDA(import_vec<double>(a, m->geo, n_macro, m->host.nx, m->host.ny, gl, D.r, nullptr, true, s));
+  HHG_CUDA(grad_partials(a, n_macro, D.u, D.r, D.W, m->grad_partial, s));
+  HHG_CUDA(reduce_per_macro(m->grad_partial, a.n_tiles_all, n_macro, m->grad_out, s));
+  std::vector<double> out(n_macro);
+  HHG_CUDA(cudaMemcpyAsync(out.data(), m->grad_out, n_macro * sizeof(double), cudaMemcpyDeviceToHost, s));
+  HHG_CUDA(cudaStreamSynchronize(s));
+  for (int t = 0; t < n_macro; ++t) grad[t] = -out[t] / m->host.coeff[t];
+  return HHG_OK;
 }
 
 int hhg_profile_enable(hhg_mesh* m, int enable) {

@@ -179,6 +179,11 @@ void build_host_mesh(HostMesh& m, const int sub[3], int R, int r0, const double*
 void build_problem(const HostMesh& m, int kind, const std::vector<unsigned char>& faulty,
                    HostProblem& p);
 bool macro_in_set(const std::vector<unsigned char>& s, int m);
+// Recompute every level's stencils for new per-macro coefficients.
+void set_coefficients(HostMesh& m, const double* coeff);
+// (Re)assemble a problem's coarse-level CG system from the current stencils
+// (needs p.act, p.macro_active and p.lv[0].free_if).
+void assemble_coarse(const HostMesh& m, HostProblem& p);
 
 // ---------------------------------------------------------------------------
 // Device-side structures.
@@ -220,8 +225,11 @@ struct DevProblem {
   int* act = nullptr;
   int n_act = 0;
   std::vector<int> act_host;
+  std::vector<unsigned char> macro_active_host;
+  std::vector<int> free0_host;        // free interface nodes of level 0
   std::vector<DevProblemLevel> lv;
   int n_cg = 0;
+  int64_t nnz = 0;
   int* rowptr = nullptr;
   int* col = nullptr;
   double* val = nullptr;

@@ -80,6 +80,13 @@ cudaError_t import_masters(const int64_t* gid, int n, const double* g, T* m, cud
 template <class T>
 cudaError_t export_masters(const int64_t* gid, int n, const T* m, double* g, cudaStream_t s);
 
+// Coefficient gradient: partial[macro * n_tiles_all + tile] = sum over the
+// closed-lattice nodes p of the tile of lam_p (sub-stencil of the macro at p
+// applied to u); reduce_per_macro sums them into out[macro].
+cudaError_t grad_partials(const LevelArgs& L, int n_macro, const double* u, const double* lam, const double* W,
+                          double* partial, cudaStream_t s);
+cudaError_t reduce_per_macro(const double* partial, int n_per, int n_macro, double* out, cudaStream_t s);
+
 // Fault support.
 cudaError_t set_masters_zero(double* uI, const int* ids, int n, cudaStream_t s);
 cudaError_t restore_copies(double* u, const double* uI, const int64_t* off, const int* master, int n,

@@ -673,6 +673,55 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg(int n, const int* __restrict_
   if (threadIdx.x == 0 && iters) *iters = it;
 }
 
+// Coefficient gradient (per macro, closed lattice): sum of lam_p times the
+// macro's own sub-stencil at p applied to u, i.e. lam^T (A_T u) up to the
+// factor k_T.
+__global__ void __launch_bounds__(CTA) k_grad(int N, const int* __restrict__ rs, int64_t block,
+                                              const double* __restrict__ u, const double* __restrict__ lam,
+                                              const double* __restrict__ W, const Tile* __restrict__ tiles,
+                                              double* __restrict__ partial) {
+  __shared__ double sh[32];
+  const Tile t = tiles[blockIdx.x];
+  const int macro = blockIdx.y;
+  const int k = t.k;
+  const int j = t.j0 + threadIdx.y;
+  const int m = t.m0 + threadIdx.x;
+  const double* ub = u + (size_t)macro * block;
+  const double* lb = lam + (size_t)macro * block;
+  const double* Wm = W + (size_t)macro * 16 * NDIR;
+  double acc = 0.0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = 4 * m + q;
+    if (i + j + k > N) continue;
+    const int me = lidx32(rs, N, i, j, k);
+    const double l = lb[me];
+    if (l == 0.0) continue;
+    const double* w = Wm + node_class(i, j, k, N) * NDIR;
+    double sv = w[0] * ub[me];
+    for (int d = 1; d < NDIR; ++d) {
+      const double wd = w[d];
+      if (wd == 0.0) continue;
+      int di, dj, dk;
+      dir_ijk(d, di, dj, dk);
+      if (!in_lattice(i + di, j + dj, k + dk, N)) continue;
+      sv += wd * ub[lidx32(rs, N, i + di, j + dj, k + dk)];
+    }
+    acc += l * sv;
+  }
+  const double s = block_sum(acc, sh);
+  if (threadIdx.x == 0 && threadIdx.y == 0) partial[(size_t)macro * gridDim.x + blockIdx.x] = s;
+}
+
+__global__ void k_reduce_per_macro(const double* __restrict__ partial, int n_per, double* __restrict__ out) {
+  __shared__ double sh[33];
+  double s = 0.0;
+  const double* p = partial + (size_t)blockIdx.x * n_per;
+  for (int q = threadIdx.x; q < n_per; q += blockDim.x) s += p[q];
+  s = cta_sum(s, sh);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
 __global__ void k_reduce(const double* __restrict__ partial, int n, double* __restrict__ out) {
   __shared__ double sh[33];
   double s = 0.0;
@@ -936,6 +985,24 @@ cudaError_t export_masters(const int64_t* gid, int n, const T* m, double* g, cud
   if (n > 0) {
     ++g_kernel_launches;
     k_export_if<T><<<lin_grid(n, 256), 256, 0, s>>>(gid, n, m, g);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t grad_partials(const LevelArgs& L, int n_macro, const double* u, const double* lam, const double* W,
+                          double* partial, cudaStream_t s) {
+  if (L.n_tiles_all > 0 && n_macro > 0) {
+    ++g_kernel_launches;
+    k_grad<<<dim3((unsigned)L.n_tiles_all, (unsigned)n_macro), cta_shape(), 0, s>>>(L.N, L.rs, L.block, u, lam, W,
+                                                                                   L.tiles_all, partial);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t reduce_per_macro(const double* partial, int n_per, int n_macro, double* out, cudaStream_t s) {
+  if (n_macro > 0) {
+    ++g_kernel_launches;
+    k_reduce_per_macro<<<n_macro, 256, 0, s>>>(partial, n_per, out);
   }
   return cudaGetLastError();
 }

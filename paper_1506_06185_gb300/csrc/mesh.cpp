@@ -153,6 +153,12 @@ void class_weights(const HostMesh& m, int macro, int N, int mask, double w[NDIR]
   }
 }
 
+void compute_level_weights(const HostMesh& m, HostLevel& L) {
+  L.W.assign((size_t)m.n_macro * 16 * NDIR, 0.0);
+  for (int t = 0; t < m.n_macro; ++t)
+    for (int mask = 0; mask < 15; ++mask) class_weights(m, t, L.N, mask, &L.W[((size_t)t * 16 + mask) * NDIR]);
+}
+
 void build_tiles(int N, bool interior, std::vector<Tile>& out) {
   out.clear();
   const int lo = interior ? 1 : 0;
@@ -186,6 +192,11 @@ void build_pair_tiles(int N, std::vector<Tile>& out) {
 }
 
 }  // namespace
+
+void set_coefficients(HostMesh& m, const double* coeff) {
+  for (int t = 0; t < m.n_macro; ++t) m.coeff[t] = coeff[t];
+  for (auto& L : m.lv) compute_level_weights(m, L);
+}
 
 bool macro_in_set(const std::vector<unsigned char>& s, int m) { return m >= 0 && m < (int)s.size() && s[m]; }
 
@@ -284,9 +295,7 @@ void build_host_mesh(HostMesh& m, const int sub[3], int R, int r0, const double*
     L.block = build_slice_starts(L.N, L.SL);
     const int N = L.N;
     // stencils
-    L.W.assign((size_t)m.n_macro * 16 * NDIR, 0.0);
-    for (int t = 0; t < m.n_macro; ++t)
-      for (int mask = 0; mask < 15; ++mask) class_weights(m, t, N, mask, &L.W[((size_t)t * 16 + mask) * NDIR]);
+    compute_level_weights(m, L);
     // 7-point structure: every class (volume and sub-stencils) of every macro
     // has zero weights off the three chain axes
     for (size_t q = 0; q < L.W.size(); ++q) {
@@ -330,6 +339,71 @@ void build_host_mesh(HostMesh& m, const int sub[3], int R, int r0, const double*
     m.lv.push_back(std::move(L));
   }
 }
+
+// Coarse-level CG system of a problem (level 0): compact numbering of its
+// free nodes (volume interiors of the active macros, then free interface
+// nodes), the matrix assembled from the per-macro sub-stencils, and the maps
+// that gather the right-hand side and scatter the solution.
+void assemble_coarse(const HostMesh& m, HostProblem& p) {
+  p.n_cg = 0;
+  p.rowptr.clear();
+  p.col.clear();
+  p.val.clear();
+  p.fsrc.clear();
+  p.uptr.clear();
+  p.udst.clear();
+  p.umaster.clear();
+
+    const HostLevel& L = m.lv[0];
+    const int N = L.N;
+    std::unordered_map<int64_t, int> cidx;
+    struct Dof { std::vector<Copy> cps; int master; };
+    std::vector<Dof> dofs;
+    for (int t : p.act)
+      for (int k = 1; k <= N - 3; ++k)
+        for (int j = 1; j + k <= N - 2; ++j)
+          for (int i = 1; i + j + k <= N - 1; ++i) {
+            cidx[node_gid(m, t, N, i, j, k)] = (int)dofs.size();
+            dofs.push_back(Dof{{Copy{t, i, j, k}}, -1});
+          }
+    for (int n : p.lv[0].free_if) {
+      Dof d;
+      d.master = n;
+      for (int c = L.if_cptr[n]; c < L.if_cptr[n + 1]; ++c) d.cps.push_back(L.if_copy[c]);
+      cidx[L.if_gid[n]] = (int)dofs.size();
+      dofs.push_back(d);
+    }
+    p.n_cg = (int)dofs.size();
+    p.rowptr.push_back(0);
+    p.uptr.push_back(0);
+    for (auto& d : dofs) {
+      std::map<int, double> row;
+      for (const Copy& cp : d.cps) {
+        int mask = node_class(cp.i, cp.j, cp.k, N);
+        const double* w = &L.W[((size_t)cp.macro * 16 + mask) * NDIR];
+        for (int e = 0; e < NDIR; ++e) {
+          if (w[e] == 0.0) continue;
+          int di, dj, dk;
+          dir_ijk(e, di, dj, dk);
+          int ni = cp.i + di, nj = cp.j + dj, nk = cp.k + dk;
+          if (!in_lattice(ni, nj, nk, N)) continue;
+          auto it = cidx.find(node_gid(m, cp.macro, N, ni, nj, nk));
+          if (it == cidx.end()) continue;
+          row[it->second] += w[e];
+        }
+        p.udst.push_back((int64_t)cp.macro * L.block + lidx(L.SL.data(), N, cp.i, cp.j, cp.k));
+      }
+      for (auto& kv : row) {
+        p.col.push_back(kv.first);
+        p.val.push_back(kv.second);
+      }
+      p.rowptr.push_back((int)p.col.size());
+      p.uptr.push_back((int)p.udst.size());
+      p.umaster.push_back(d.master);
+      if (d.master >= 0) p.fsrc.push_back(-1 - (int64_t)d.master);
+      else p.fsrc.push_back(p.udst.back());
+    }
+  }
 
 void build_problem(const HostMesh& m, int kind, const std::vector<unsigned char>& faulty, HostProblem& p) {
   p = HostProblem();
@@ -409,58 +483,7 @@ void build_problem(const HostMesh& m, int kind, const std::vector<unsigned char>
       if (cnt != NDIR) throw std::runtime_error("restriction stencil incomplete");
     }
   }
-  // coarse-level CG system on the compact free nodes of level 0
-  {
-    const HostLevel& L = m.lv[0];
-    const int N = L.N;
-    std::unordered_map<int64_t, int> cidx;
-    struct Dof { std::vector<Copy> cps; int master; };
-    std::vector<Dof> dofs;
-    for (int t : p.act)
-      for (int k = 1; k <= N - 3; ++k)
-        for (int j = 1; j + k <= N - 2; ++j)
-          for (int i = 1; i + j + k <= N - 1; ++i) {
-            cidx[node_gid(m, t, N, i, j, k)] = (int)dofs.size();
-            dofs.push_back(Dof{{Copy{t, i, j, k}}, -1});
-          }
-    for (int n : p.lv[0].free_if) {
-      Dof d;
-      d.master = n;
-      for (int c = L.if_cptr[n]; c < L.if_cptr[n + 1]; ++c) d.cps.push_back(L.if_copy[c]);
-      cidx[L.if_gid[n]] = (int)dofs.size();
-      dofs.push_back(d);
-    }
-    p.n_cg = (int)dofs.size();
-    p.rowptr.push_back(0);
-    p.uptr.push_back(0);
-    for (auto& d : dofs) {
-      std::map<int, double> row;
-      for (const Copy& cp : d.cps) {
-        int mask = node_class(cp.i, cp.j, cp.k, N);
-        const double* w = &L.W[((size_t)cp.macro * 16 + mask) * NDIR];
-        for (int e = 0; e < NDIR; ++e) {
-          if (w[e] == 0.0) continue;
-          int di, dj, dk;
-          dir_ijk(e, di, dj, dk);
-          int ni = cp.i + di, nj = cp.j + dj, nk = cp.k + dk;
-          if (!in_lattice(ni, nj, nk, N)) continue;
-          auto it = cidx.find(node_gid(m, cp.macro, N, ni, nj, nk));
-          if (it == cidx.end()) continue;
-          row[it->second] += w[e];
-        }
-        p.udst.push_back((int64_t)cp.macro * L.block + lidx(L.SL.data(), N, cp.i, cp.j, cp.k));
-      }
-      for (auto& kv : row) {
-        p.col.push_back(kv.first);
-        p.val.push_back(kv.second);
-      }
-      p.rowptr.push_back((int)p.col.size());
-      p.uptr.push_back((int)p.udst.size());
-      p.umaster.push_back(d.master);
-      if (d.master >= 0) p.fsrc.push_back(-1 - (int64_t)d.master);
-      else p.fsrc.push_back(p.udst.back());
-    }
-  }
+  assemble_coarse(m, p);
 }
 
 }  // namespace hhg

@@ -26,7 +26,7 @@ HHG_RECOVERY_NONE, HHG_RECOVERY_LR, HHG_RECOVERY_DD = 0, 1, 2
 EXPORTS = ["hhg_mesh_create", "hhg_mesh_destroy", "hhg_mesh_info", "hhg_mesh_bytes", "hhg_set_problem",
            "hhg_get_solution", "hhg_vcycle", "hhg_residual_norm", "hhg_inject_fault", "hhg_recover_local",
            "hhg_solve", "hhg_last_error", "hhg_profile_enable", "hhg_profile_read", "hhg_profile_info",
-           "hhg_launch_count", "hhg_vcycle_noalloc"]
+           "hhg_launch_count", "hhg_vcycle_noalloc", "hhg_set_coefficients", "hhg_grad_coeff"]
 
 
 class hhg_mesh_desc(C.Structure):
@@ -73,6 +73,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "hhg_profile_info": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_int)], C.c_int),
         "hhg_launch_count": ([C.POINTER(C.c_int64)], C.c_int),
         "hhg_vcycle_noalloc": ([P, C.c_int, C.c_int, P], C.c_int),
+        "hhg_set_coefficients": ([P, C.POINTER(C.c_double), P], C.c_int),
+        "hhg_grad_coeff": ([P, P, P, C.POINTER(C.c_double), P], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -228,6 +230,17 @@ def hhg_solve(h, rtol=1e-8, max_cycles=50, pre=3, post=3, fault_cycle=0, fault_i
     return np.array(hist[:nh.value]), cyc.value, rc
 
 
+def hhg_set_coefficients(h, coeff, stream=None):
+    c = np.ascontiguousarray(np.asarray(coeff, dtype=np.float64))
+    return _check(lib().hhg_set_coefficients(h, c.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)))
+
+
+def hhg_grad_coeff(h, u, lam, n_macro, stream=None):
+    g = np.zeros(int(n_macro))
+    _check(lib().hhg_grad_coeff(h, _ptr(u), _ptr(lam), g.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)))
+    return g
+
+
 def hhg_profile_enable(h, enable=True):
     return _check(lib().hhg_profile_enable(h, 1 if enable else 0))
 
@@ -298,3 +311,9 @@ class Mesh:
 
     def solve(self, **kw):
         return hhg_solve(self.h, **kw)
+
+    def set_coefficients(self, coeff, stream=None):
+        hhg_set_coefficients(self.h, coeff, stream)
+
+    def grad_coeff(self, u, lam, stream=None):
+        return hhg_grad_coeff(self.h, u, lam, self.n_macro, stream)

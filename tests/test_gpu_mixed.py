@@ -1,0 +1,73 @@
+"""Mixed precision: FP32 smoothing, transfers and recovery cycles inside FP64
+iterative refinement (FP64 fine residual, update and coarse CG).  Parity is on
+the final residual (the same stopping test as FP64); the solution's error
+against the FP64 oracle is bounded and printed."""
+
+import numpy as np
+import pytest
+
+import hhg_inputs as I
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hhg():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1506_06185_gb300 import build
+    from paper_1506_06185_gb300 import hhg as H
+    build()
+    return H
+
+
+def _check(hhg, sub, R, f, u0, coeff=None, **kw):
+    M = hhg.Mesh(sub, R, precision=32, coeff=coeff)
+    M.set_problem(f, u0)
+    hist, cyc, _ = M.solve(mixed_precision=True, **kw)
+    ug = M.get_solution()
+    m = O.Mesh(sub, R, coeff=coeff)
+    uo = O.pad(u0.copy())
+    okw = {k: v for k, v in kw.items() if k in ("rtol", "max_cycles", "fault_cycle", "fault_ids", "recovery",
+                                                  "n_local", "n_global", "eta")}
+    ref = O.solve(m, uo, O.pad(f), **okw)
+    err = np.linalg.norm(ug - O.interior(uo)) / np.linalg.norm(O.interior(uo))
+    print(f"mixed: {cyc} cycles (FP64 oracle {ref['cycles']}), final rel. residual {hist[-1]:.2e}, "
+          f"|u - u_oracle| / |u_oracle| = {err:.2e}")
+    assert hist[-1] <= kw["rtol"]
+    assert abs(cyc - ref["cycles"]) <= 1
+    # the stopping test bounds the algebraic error by cond(A) * rtol; both
+    # solutions sit within that of the exact discrete solution
+    assert err <= 100 * kw["rtol"] * 1e2
+    M.close()
+    return err
+
+
+def test_mixed_config1_fault_lr(hhg):
+    sub, R = (2, 2, 2), 4
+    g = I.harmonic_boundary(sub, R)
+    _check(hhg, sub, R, np.zeros(g.shape), I.initial_guess(sub, R, g), rtol=1e-10, max_cycles=40,
+           fault_cycle=5, fault_ids=[0], recovery=1, n_local=2)
+
+
+def test_mixed_dd_subcube_random_load(hhg):
+    sub, R = (2, 2, 2), 5
+    f = I.random_load(sub, R, seed=0)
+    _check(hhg, sub, R, f, I.initial_guess(sub, R), rtol=1e-10, max_cycles=40, fault_cycle=5,
+           fault_ids=I.subcube_macros(sub), recovery=2, n_global=2, eta=4.0)
+
+
+def test_mixed_coefficients_fault_free(hhg):
+    sub, R = (3, 2, 2), 5
+    coeff = np.exp(np.random.default_rng(4).standard_normal(72))
+    f = I.random_load(sub, R, seed=1)
+    _check(hhg, sub, R, f, I.initial_guess(sub, R), coeff=coeff, rtol=1e-10, max_cycles=40)
+
+
+def test_mixed_needs_precision32_mesh(hhg):
+    M = hhg.Mesh((1, 1, 1), 3)
+    with pytest.raises(hhg.HHGError) as e:
+        M.solve(rtol=1e-6, max_cycles=5, mixed_precision=True)
+    assert e.value.code == hhg.HHG_ERR_STATE
+    M.close()
