@@ -91,3 +91,61 @@ def random_directions(n_macro, count, seed=2):
     rng = np.random.Generator(np.random.Philox(int(seed)))
     d = rng.standard_normal((int(count), int(n_macro)))
     return d / np.linalg.norm(d, axis=1, keepdims=True)
+
+
+def macro_vertices(sub):
+    """Integer sub-cube coordinates of the 4 vertices of every macro (Kuhn
+    tetrahedron p of sub-cube (a, b, c): 0, e_pi0, e_pi0 + e_pi1, (1,1,1))."""
+    import itertools
+    perms = list(itertools.permutations((0, 1, 2)))
+    out = []
+    for c in range(sub[2]):
+        for b in range(sub[1]):
+            for a in range(sub[0]):
+                for p in perms:
+                    v0 = (a, b, c)
+                    v1 = list(v0)
+                    v1[p[0]] += 1
+                    v2 = list(v1)
+                    v2[p[1]] += 1
+                    out.append([v0, tuple(v1), tuple(v2), (a + 1, b + 1, c + 1)])
+    return out
+
+
+def grow_fault_set(sub, size, seed):
+    """A connected set of ``size`` macros grown breadth-first (through shared
+    faces) from a random seed macro, with a random visiting order."""
+    rng = np.random.Generator(np.random.Philox(int(seed)))
+    verts = [frozenset(v) for v in macro_vertices(sub)]
+    n = len(verts)
+    size = int(min(size, n))
+    start = int(rng.integers(n))
+    chosen, frontier = [start], [start]
+    seen = {start}
+    while frontier and len(chosen) < size:
+        cur = frontier.pop(0)
+        nbrs = [t for t in range(n) if t not in seen and len(verts[cur] & verts[t]) == 3]
+        rng.shuffle(nbrs)
+        for t in nbrs:
+            if len(chosen) >= size:
+                break
+            seen.add(t)
+            chosen.append(t)
+            frontier.append(t)
+    return sorted(chosen)
+
+
+def batch_problems(count, seed=3, max_size=27, levels=(5, 6, 7)):
+    """Recovery problems of uneven size: (sub-cubes, refinement, fault macros)
+    with sizes ~ U{1..max_size} and refinements drawn from ``levels``; each
+    problem lives on the smallest cube of sub-cubes that holds its macros."""
+    rng = np.random.Generator(np.random.Philox(int(seed)))
+    out = []
+    for q in range(int(count)):
+        size = int(rng.integers(1, max_size + 1))
+        r = int(levels[int(rng.integers(len(levels)))])
+        for sub in [(1, 1, 1), (2, 1, 1), (2, 2, 1), (2, 2, 2), (3, 2, 2), (3, 3, 2), (3, 3, 3)]:
+            if 6 * sub[0] * sub[1] * sub[2] >= size:
+                break
+        out.append((sub, r, grow_fault_set(sub, size, seed * 1000 + q)))
+    return out

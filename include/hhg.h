@@ -169,6 +169,36 @@ int hhg_solve(hhg_mesh* mesh, const hhg_solve_opts* opts, double* hist, int* n_h
 int hhg_set_coefficients(hhg_mesh* mesh, const double* coeff, void* stream);
 int hhg_grad_coeff(hhg_mesh* mesh, const double* u, const double* lam, double* grad, void* stream);
 
+/* Autotuning of the volume tile shape (an implementation knob, not part of
+ * the method).  For every smoothed level, times `reps` Gauss-Seidel steps of
+ * the global problem with each candidate tile shape (nodes per tile and
+ * slices per tile: 256/4, 512/8, 1024/8, 2048/16) in the mesh's working
+ * precision (FP32 arrays for precision-32 meshes, otherwise the FP64
+ * iterate, which the sweeps smooth) and keeps the fastest for that level.
+ * chosen (may be NULL, one int per level, coarsest first) receives the index
+ * of the chosen candidate (-1 for the coarsest level, which is not smoothed). */
+int hhg_autotune(hhg_mesh* mesh, int reps, int* chosen, void* stream);
+
+/* Batched recovery in one CUDA-graph launch (the concurrency of §4.1's
+ * superman recovery, many sub-domains at once).  A batch holds n_tasks
+ * recovery tasks -- task t: on meshes[t] (each mesh in one task only), the
+ * fault of §2.2 on the macros ids[t][0..n_ids[t]) followed by cycles[t] local
+ * Dirichlet cycles on them (LR) -- and, if global is not NULL, global_cycles
+ * global cycles on the mesh `global` (not one of the task meshes).  Every
+ * task is one branch of a CUDA graph, all branches fork from one start node,
+ * so the tasks run concurrently; mixed = 1 runs every cycle as FP32 cycles in
+ * FP64 iterative refinement (precision-32 meshes).  Creation does the host
+ * set-up, runs the work once without the graph, and captures the graph.
+ * hhg_batch_launch launches the whole batch with one graph launch on stream;
+ * if task_ms is not NULL (n_tasks + 1 doubles, the global task last when
+ * present) it synchronises and receives each task's completion time in ms
+ * after the start of the launch. */
+typedef struct hhg_batch hhg_batch;
+int hhg_batch_create(hhg_mesh* global, int global_cycles, hhg_mesh* const* meshes, const int* const* ids,
+                     const int* n_ids, const int* cycles, int n_tasks, int mixed, hhg_batch** out);
+int hhg_batch_launch(hhg_batch* batch, double* task_ms, void* stream);
+int hhg_batch_destroy(hhg_batch* batch);
+
 /* Allocation-free V-cycle (an interface addition; the paper has no
  * counterpart).  Some callers cannot call cudaMalloc at all once they are
  * running: for example a host application that hands the device's memory to

@@ -82,6 +82,22 @@ struct hhg_mesh {
   size_t prof_used = 0;
 };
 
+struct hhg_batch {
+  struct Task {
+    hhg_mesh* mesh;
+    int cycles;
+    cudaStream_t stream;
+    cudaEvent_t done;       // join dependency inside the capture
+    cudaEvent_t done_time;  // event-record node: completion time of the task
+  };
+  std::vector<Task> tasks;       // recovery tasks, then (optionally) the global one
+  bool mixed = false;
+  cudaStream_t origin = nullptr;
+  cudaEvent_t start = nullptr, fork = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+};
+
 namespace {
 
 template <class T>
@@ -483,6 +499,59 @@ int update_coefficients(hhg_mesh* m, const double* coeff) {
   return HHG_OK;
 }
 
+// Candidate shapes of the interior tiles: (nodes of one colour per tile in its
+// first slice, consecutive slices per tile).
+const int TUNE_CAND[][2] = {{256, 4}, {512, 8}, {1024, 8}, {2048, 16}};
+constexpr int N_TUNE_CAND = 4;
+
+template <class T>
+int tune_level(hhg_mesh* m, Prec<T>& P, int l, int reps, cudaStream_t s, int* best_out) {
+  const HostLevel& H = m->host.lv[l];
+  DevLevelTables& tb = m->tab[l];
+  double best_ms = 1e30;
+  int best = -1;
+  std::vector<Tile*> dev(N_TUNE_CAND, nullptr);
+  std::vector<int> ndev(N_TUNE_CAND, 0);
+  cudaEvent_t a, b;
+  HHG_CUDA(cudaEventCreate(&a));
+  HHG_CUDA(cudaEventCreate(&b));
+  for (int c = 0; c < N_TUNE_CAND; ++c) {
+    std::vector<Tile> tiles;
+    build_pair_tiles(H.N, tiles, TUNE_CAND[c][0], TUNE_CAND[c][1]);
+    HHG_TRY(upload(m, &dev[c], tiles));
+    ndev[c] = (int)tiles.size();
+    tb.tiles_int = dev[c];
+    tb.n_tiles_int = ndev[c];
+    HHG_TRY(smooth<T>(m, P, m->global, l, 1, s));   // warm-up
+    HHG_CUDA(cudaEventRecord(a, s));
+    HHG_TRY(smooth<T>(m, P, m->global, l, reps, s));
+    HHG_CUDA(cudaEventRecord(b, s));
+    HHG_CUDA(cudaEventSynchronize(b));
+    float ms = 0.f;
+    HHG_CUDA(cudaEventElapsedTime(&ms, a, b));
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  tb.tiles_int = dev[best];
+  tb.n_tiles_int = ndev[best];
+  *best_out = best;
+  return HHG_OK;
+}
+
+int capture_task(hhg_mesh* m, int cycles, bool recovery, bool mixed, cudaStream_t s) {
+  if (recovery) {
+    HHG_TRY(inject(m, s));
+    for (int c = 0; c < cycles; ++c) HHG_TRY(cycle(m, m->faulty, mixed, 3, 3, 1e-12, 1000, s));
+  } else {
+    for (int c = 0; c < cycles; ++c) HHG_TRY(cycle(m, m->global, mixed, 3, 3, 1e-12, 1000, s));
+  }
+  return HHG_OK;
+}
+
 // ---------------------------------------------------------------------------
 // Allocation-free V-cycle: the coarse-grid CG keeps its work vectors (x, r, p,
 // A p) in this file-scope static device array instead of the mesh's own
@@ -752,6 +821,141 @@ int hhg_grad_coeff(hhg_mesh* m, const double* u, const double* lam, double* grad
   HHG_CUDA(cudaMemcpyAsync(out.data(), m->grad_out, n_macro * sizeof(double), cudaMemcpyDeviceToHost, s));
   HHG_CUDA(cudaStreamSynchronize(s));
   for (int t = 0; t < n_macro; ++t) grad[t] = -out[t] / m->host.coeff[t];
+  return HHG_OK;
+}
+
+int hhg_autotune(hhg_mesh* m, int reps, int* chosen, void* stream) {
+  if (!m || reps < 1) return fail(HHG_ERR_ARG, "invalid argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nl = (int)m->host.lv.size();
+  for (int l = 1; l < nl; ++l) {
+    int best = 0;
+    if (m->precision == 32) HHG_TRY(tune_level<float>(m, m->d32, l, reps, s, &best));
+    else HHG_TRY(tune_level<double>(m, m->d64, l, reps, s, &best));
+    if (chosen) chosen[l] = best;
+  }
+  if (chosen) chosen[0] = -1;
+  return HHG_OK;
+}
+
+int hhg_batch_create(hhg_mesh* global, int global_cycles, hhg_mesh* const* meshes, const int* const* ids,
+                     const int* n_ids, const int* cycles, int n_tasks, int mixed, hhg_batch** out) {
+  if (!out || n_tasks < 0 || (n_tasks > 0 && (!meshes || !ids || !n_ids || !cycles)) ||
+      (global && global_cycles < 0))
+    return fail(HHG_ERR_ARG, "invalid argument");
+  *out = nullptr;
+  std::unique_ptr<hhg_batch> b(new (std::nothrow) hhg_batch());
+  if (!b) return fail(HHG_ERR_OOM, "host allocation failed");
+  b->mixed = mixed != 0;
+  for (int t = 0; t < n_tasks; ++t) {
+    hhg_mesh* m = meshes[t];
+    if (!m || cycles[t] < 0) return fail(HHG_ERR_ARG, "invalid task");
+    if (b->mixed && m->precision != 32) return fail(HHG_ERR_STATE, "mixed precision needs precision-32 meshes");
+    for (int q = 0; q < t; ++q)
+      if (meshes[q] == m) return fail(HHG_ERR_ARG, "a mesh may appear in one task only");
+    std::vector<unsigned char> set;
+    HHG_TRY(check_ids(m, ids[t], n_ids[t], set));
+    HHG_TRY(setup_fault(m, set));
+    b->tasks.push_back({m, cycles[t], nullptr, nullptr, nullptr});
+  }
+  if (global) {
+    if (b->mixed && global->precision != 32) return fail(HHG_ERR_STATE, "mixed precision needs precision-32 meshes");
+    for (int t = 0; t < n_tasks; ++t)
+      if (meshes[t] == global) return fail(HHG_ERR_ARG, "the global mesh may not also be a task");
+    b->tasks.push_back({global, global_cycles, nullptr, nullptr, nullptr});
+  }
+  auto cleanup = [&](int rc) {
+    for (auto& t : b->tasks) {
+      if (t.stream) cudaStreamDestroy(t.stream);
+      if (t.done) cudaEventDestroy(t.done);
+      if (t.done_time) cudaEventDestroy(t.done_time);
+    }
+    if (b->origin) cudaStreamDestroy(b->origin);
+    if (b->start) cudaEventDestroy(b->start);
+    if (b->fork) cudaEventDestroy(b->fork);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    return rc;
+  };
+  if (cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreate(&b->start) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming) != cudaSuccess)
+    return cleanup(fail(HHG_ERR_CUDA, "stream / event creation failed"));
+  for (auto& t : b->tasks)
+    if (cudaStreamCreateWithFlags(&t.stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&t.done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreate(&t.done_time) != cudaSuccess)
+      return cleanup(fail(HHG_ERR_CUDA, "stream / event creation failed"));
+  // one uncaptured pass (fills the launch-shape caches; same work as the graph)
+  const size_t n_rec = (size_t)n_tasks;
+  for (size_t t = 0; t < b->tasks.size(); ++t) {
+    int rc = capture_task(b->tasks[t].mesh, b->tasks[t].cycles, t < n_rec, b->mixed, b->origin);
+    if (rc != HHG_OK) return cleanup(rc);
+  }
+  if (cudaStreamSynchronize(b->origin) != cudaSuccess) return cleanup(fail(HHG_ERR_CUDA, "warm-up pass failed"));
+  // capture: fork one branch per task from the origin stream, join at the end
+  if (cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return cleanup(fail(HHG_ERR_CUDA, "cudaStreamBeginCapture failed"));
+  int rc = HHG_OK;
+  // timing events are captured as event-record nodes (External); fork and
+  // join events only order the branches
+  if (cudaEventRecordWithFlags(b->start, b->origin, cudaEventRecordExternal) != cudaSuccess ||
+      cudaEventRecord(b->fork, b->origin) != cudaSuccess)
+    rc = fail(HHG_ERR_CUDA, "event record in capture failed");
+  for (size_t t = 0; t < b->tasks.size() && rc == HHG_OK; ++t) {
+    auto& task = b->tasks[t];
+    if (cudaStreamWaitEvent(task.stream, b->fork, 0) != cudaSuccess) {
+      rc = fail(HHG_ERR_CUDA, "fork in capture failed");
+      break;
+    }
+    rc = capture_task(task.mesh, task.cycles, t < n_rec, b->mixed, task.stream);
+    if (rc == HHG_OK && (cudaEventRecordWithFlags(task.done_time, task.stream, cudaEventRecordExternal) != cudaSuccess ||
+                         cudaEventRecord(task.done, task.stream) != cudaSuccess ||
+                         cudaStreamWaitEvent(b->origin, task.done, 0) != cudaSuccess))
+      rc = fail(HHG_ERR_CUDA, "join in capture failed");
+  }
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(b->origin, &g);
+  if (rc != HHG_OK) {
+    if (g) cudaGraphDestroy(g);
+    return cleanup(rc);
+  }
+  if (ec != cudaSuccess) return cleanup(fail(HHG_ERR_CUDA, std::string("capture failed: ") + cudaGetErrorString(ec)));
+  b->graph = g;
+  if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)
+    return cleanup(fail(HHG_ERR_CUDA, "cudaGraphInstantiate failed"));
+  *out = b.release();
+  return HHG_OK;
+}
+
+int hhg_batch_launch(hhg_batch* b, double* task_ms, void* stream) {
+  if (!b) return fail(HHG_ERR_ARG, "null batch");
+  cudaStream_t s = (cudaStream_t)stream;
+  HHG_CUDA(cudaGraphLaunch(b->exec, s));
+  if (task_ms) {
+    HHG_CUDA(cudaStreamSynchronize(s));
+    for (size_t t = 0; t < b->tasks.size(); ++t) {
+      float ms = 0.f;
+      HHG_CUDA(cudaEventElapsedTime(&ms, b->start, b->tasks[t].done_time));
+      task_ms[t] = ms;
+    }
+  }
+  return HHG_OK;
+}
+
+int hhg_batch_destroy(hhg_batch* b) {
+  if (!b) return HHG_OK;
+  cudaDeviceSynchronize();
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  for (auto& t : b->tasks) {
+    if (t.stream) cudaStreamDestroy(t.stream);
+    if (t.done) cudaEventDestroy(t.done);
+    if (t.done_time) cudaEventDestroy(t.done_time);
+  }
+  if (b->origin) cudaStreamDestroy(b->origin);
+  if (b->start) cudaEventDestroy(b->start);
+  if (b->fork) cudaEventDestroy(b->fork);
+  delete b;
   return HHG_OK;
 }
 

@@ -104,6 +104,7 @@ struct Tile {
 };
 constexpr int TILE_ROWS = 8;
 constexpr int TILE_SLABS = 8;
+constexpr int TILE_TARGET_DEFAULT = 512;
 constexpr int TILE_SLOTS = 32;
 
 // A copy of an interface node inside one macro block.
@@ -179,6 +180,8 @@ void build_host_mesh(HostMesh& m, const int sub[3], int R, int r0, const double*
 void build_problem(const HostMesh& m, int kind, const std::vector<unsigned char>& faulty,
                    HostProblem& p);
 bool macro_in_set(const std::vector<unsigned char>& s, int m);
+// Interior row-pair tiles of refinement N (see mesh.cpp).
+void build_pair_tiles(int N, std::vector<Tile>& out, int target, int slabs);
 // Recompute every level's stencils for new per-macro coefficients.
 void set_coefficients(HostMesh& m, const double* coeff);
 // (Re)assemble a problem's coarse-level CG system from the current stencils

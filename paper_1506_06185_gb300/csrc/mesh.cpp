@@ -173,25 +173,26 @@ void build_tiles(int N, bool interior, std::vector<Tile>& out) {
   }
 }
 
+}  // namespace
+
 // Row-pair tiles of the volume interior: in slice k the interior rows are
 // j = 1..J, J = N - 2 - k; pair p joins rows 1 + p and J - p, whose lengths add
-// up to N - 1 - k nodes.  A tile covers pairs j0 .. j0 + m0 - 1 (about 512
-// nodes of one colour in its first slice, at most 32 pairs) in the TILE_SLABS
-// consecutive slices k .. k + pad - 1, so that the CTA that loads a slice's
-// rows reuses them for the next slice (pairs beyond a slice's count are empty).
-void build_pair_tiles(int N, std::vector<Tile>& out) {
+// up to N - 1 - k nodes.  A tile covers pairs j0 .. j0 + m0 - 1 (about
+// `target` nodes of one colour in its first slice, at most 32 pairs) in the
+// `slabs` consecutive slices k .. k + pad - 1, so that the CTA that loads a
+// slice's rows reuses them for the next slice (pairs beyond a slice's count
+// are empty).
+void build_pair_tiles(int N, std::vector<Tile>& out, int target, int slabs) {
   out.clear();
-  for (int k0 = 1; k0 <= N - 3; k0 += TILE_SLABS) {
-    const int nk = std::min(TILE_SLABS, N - 2 - k0);
+  for (int k0 = 1; k0 <= N - 3; k0 += slabs) {
+    const int nk = std::min(slabs, N - 2 - k0);
     const int J = N - 2 - k0;
     const int pairs = (J + 1) / 2;
     const int per_pair = std::max(1, (N - 1 - k0) / 4);
-    const int np = std::min(32, std::max(1, (512 + per_pair - 1) / per_pair));
+    const int np = std::min(32, std::max(1, (target + per_pair - 1) / per_pair));
     for (int p0 = 0; p0 < pairs; p0 += np) out.push_back(Tile{k0, p0, std::min(np, pairs - p0), nk});
   }
 }
-
-}  // namespace
 
 void set_coefficients(HostMesh& m, const double* coeff) {
   for (int t = 0; t < m.n_macro; ++t) m.coeff[t] = coeff[t];
@@ -334,7 +335,7 @@ void build_host_mesh(HostMesh& m, const int sub[3], int R, int r0, const double*
       }
     }
     L.n_if = (int)L.if_gid.size();
-    build_pair_tiles(N, L.tiles_int);
+    build_pair_tiles(N, L.tiles_int, TILE_TARGET_DEFAULT, TILE_SLABS);
     build_tiles(N, false, L.tiles_all);
     m.lv.push_back(std::move(L));
   }

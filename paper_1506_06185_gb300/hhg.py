@@ -26,7 +26,8 @@ HHG_RECOVERY_NONE, HHG_RECOVERY_LR, HHG_RECOVERY_DD = 0, 1, 2
 EXPORTS = ["hhg_mesh_create", "hhg_mesh_destroy", "hhg_mesh_info", "hhg_mesh_bytes", "hhg_set_problem",
            "hhg_get_solution", "hhg_vcycle", "hhg_residual_norm", "hhg_inject_fault", "hhg_recover_local",
            "hhg_solve", "hhg_last_error", "hhg_profile_enable", "hhg_profile_read", "hhg_profile_info",
-           "hhg_launch_count", "hhg_vcycle_noalloc", "hhg_set_coefficients", "hhg_grad_coeff"]
+           "hhg_launch_count", "hhg_vcycle_noalloc", "hhg_set_coefficients", "hhg_grad_coeff",
+           "hhg_autotune", "hhg_batch_create", "hhg_batch_launch", "hhg_batch_destroy"]
 
 
 class hhg_mesh_desc(C.Structure):
@@ -75,6 +76,11 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "hhg_vcycle_noalloc": ([P, C.c_int, C.c_int, P], C.c_int),
         "hhg_set_coefficients": ([P, C.POINTER(C.c_double), P], C.c_int),
         "hhg_grad_coeff": ([P, P, P, C.POINTER(C.c_double), P], C.c_int),
+        "hhg_autotune": ([P, C.c_int, C.POINTER(C.c_int), P], C.c_int),
+        "hhg_batch_create": ([P, C.c_int, C.POINTER(P), C.POINTER(C.POINTER(C.c_int)), C.POINTER(C.c_int),
+                              C.POINTER(C.c_int), C.c_int, C.c_int, C.POINTER(P)], C.c_int),
+        "hhg_batch_launch": ([P, C.POINTER(C.c_double), P], C.c_int),
+        "hhg_batch_destroy": ([P], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -239,6 +245,49 @@ def hhg_grad_coeff(h, u, lam, n_macro, stream=None):
     g = np.zeros(int(n_macro))
     _check(lib().hhg_grad_coeff(h, _ptr(u), _ptr(lam), g.ctypes.data_as(C.POINTER(C.c_double)), _stream(stream)))
     return g
+
+
+def hhg_autotune(h, n_levels, reps=3, stream=None):
+    ch = (C.c_int * int(n_levels))()
+    _check(lib().hhg_autotune(h, int(reps), ch, _stream(stream)))
+    return list(ch)
+
+
+class Batch:
+    """Recovery tasks (and an optional global solve) captured into one CUDA
+    graph; ``launch()`` runs them all with one graph launch."""
+
+    def __init__(self, tasks, global_mesh=None, global_cycles=0, mixed=False):
+        # tasks: list of (Mesh, fault ids, local cycles)
+        self._keep = []
+        n = len(tasks)
+        meshes = (C.c_void_p * max(n, 1))(*[t[0].h for t in tasks])
+        idarrs = [(C.c_int * len(t[1]))(*[int(i) for i in t[1]]) for t in tasks]
+        self._keep += [meshes, idarrs]
+        ids = (C.POINTER(C.c_int) * max(n, 1))(*[C.cast(a, C.POINTER(C.c_int)) for a in idarrs])
+        nids = (C.c_int * max(n, 1))(*[len(t[1]) for t in tasks])
+        cyc = (C.c_int * max(n, 1))(*[int(t[2]) for t in tasks])
+        self._keep += [ids, nids, cyc]
+        self.n = n + (1 if global_mesh is not None else 0)
+        self.h = C.c_void_p()
+        _check(lib().hhg_batch_create(global_mesh.h if global_mesh is not None else None, int(global_cycles),
+                                      meshes, ids, nids, cyc, n, 1 if mixed else 0, C.byref(self.h)))
+
+    def launch(self, timed=True, stream=None):
+        ms = (C.c_double * max(self.n, 1))()
+        _check(lib().hhg_batch_launch(self.h, ms if timed else None, _stream(stream)))
+        return list(ms)[:self.n] if timed else None
+
+    def close(self):
+        if self.h is not None and self.h.value is not None:
+            lib().hhg_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def hhg_profile_enable(h, enable=True):

@@ -1,0 +1,90 @@
+"""Batched recovery in one CUDA-graph launch, and the tile autotuner.
+
+A batch runs its tasks with the same kernels as the one-at-a-time calls, so
+its results must equal those of hhg_inject_fault + hhg_recover_local (and of
+hhg_vcycle for the global task) on twin meshes; the autotuner only changes
+tile shapes, so V-cycles after tuning still match the oracle."""
+
+import numpy as np
+import pytest
+
+import hhg_inputs as I
+import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def hhg():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_1506_06185_gb300 import build
+    from paper_1506_06185_gb300 import hhg as H
+    build()
+    return H
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+def test_batch_matches_sequential_recovery(hhg):
+    specs = [((1, 1, 1), 4, [2], 3), ((2, 1, 1), 5, I.grow_fault_set((2, 1, 1), 5, 7), 2),
+             ((2, 2, 1), 4, I.grow_fault_set((2, 2, 1), 10, 8), 3)]
+    tasks, twins = [], []
+    for q, (sub, R, ids, cyc) in enumerate(specs):
+        f = I.random_load(sub, R, seed=10 + q)
+        u0 = np.random.default_rng(q).standard_normal(f.shape) * (~I.boundary_mask(sub, R))
+        a, b = hhg.Mesh(sub, R), hhg.Mesh(sub, R)
+        a.set_problem(f, u0)
+        b.set_problem(f, u0)
+        tasks.append((a, ids, cyc))
+        twins.append((b, ids, cyc))
+    gsub, gR = (2, 2, 2), 5
+    gf = I.random_load(gsub, gR, seed=20)
+    G, G2 = hhg.Mesh(gsub, gR), hhg.Mesh(gsub, gR)
+    G.set_problem(gf, I.initial_guess(gsub, gR))
+    G2.set_problem(gf, I.initial_guess(gsub, gR))
+    batch = hhg.Batch(tasks, G, 2)
+    ms = batch.launch()
+    assert len(ms) == 4 and all(t > 0 for t in ms)
+    for (a, ids, cyc), (b, _, _) in zip(tasks, twins):
+        b.inject_fault(ids)
+        b.recover_local(ids, cyc)
+        assert _rel(a.get_solution(), b.get_solution()) <= 1e-13
+    for _ in range(4):   # two cycles at creation (the uncaptured pass) and two per launch
+        G2.vcycle()
+    assert _rel(G.get_solution(), G2.get_solution()) <= 1e-13
+    batch.close()
+
+
+def test_batch_mixed_precision_runs(hhg):
+    sub, R = (2, 1, 1), 5
+    f = I.random_load(sub, R, seed=3)
+    M = hhg.Mesh(sub, R, precision=32)
+    M.set_problem(f, I.initial_guess(sub, R))
+    M.solve(rtol=1e-6, max_cycles=20)
+    r_before = M.residual_norm()
+    ids = I.grow_fault_set(sub, 4, 3)
+    batch = hhg.Batch([(M, ids, 6)], mixed=True)
+    ms = batch.launch()
+    assert ms[0] > 0
+    # six local cycles after the fault bring the residual back near its old level
+    assert M.residual_norm() <= 10 * r_before
+    batch.close()
+
+
+def test_autotune_keeps_parity(hhg):
+    sub, R = (2, 2, 2), 5
+    f = I.random_load(sub, R, seed=1)
+    M = hhg.Mesh(sub, R, precision=32)
+    chosen = hhg.hhg_autotune(M.h, R - 1, reps=2)
+    assert chosen[0] == -1 and all(0 <= c < 4 for c in chosen[1:])
+    M.set_problem(f, I.initial_guess(sub, R))
+    m = O.Mesh(sub, R)
+    uo, fo = O.pad(I.initial_guess(sub, R)), O.pad(f)
+    for _ in range(3):
+        M.vcycle()
+        O.vcycle(m, m.global_problem, len(m.levels) - 1, uo, fo)
+    assert _rel(M.get_solution(), O.interior(uo)) <= 1e-12
+    M.close()
