@@ -45,7 +45,7 @@ __all__ = [
     "element_stiffness", "assemble_coo", "dia_to_csr", "apply_A",
     "gs_step", "residual", "restrict", "prolong", "cg", "vcycle",
     "resnorm", "inject_fault", "solve", "kappa", "grad_coeff",
-    "interior", "pad", "node_coords", "NONE", "LR", "DD", "local_residual",
+    "interior", "pad", "node_coords", "NONE", "LR", "DD", "DN", "local_residual", "dn_recover",
 ]
 
 # Lexicographic permutations of the axes (x=0, y=1, z=2).  Kuhn tetrahedron
@@ -55,7 +55,7 @@ PERMS = list(itertools.permutations((0, 1, 2)))
 # written (dx, dy, dz).
 FREUDENTHAL = [d for d in itertools.product((0, 1), repeat=3) if any(d)]
 
-NONE, LR, DD = 0, 1, 2
+NONE, LR, DD, DN = 0, 1, 2, 3
 
 
 def _e(a):
@@ -339,6 +339,55 @@ class Mesh:
         return Problem(self, [(~lv.boundary) & ~c for lv, (_, c) in zip(self.levels, self.fault_masks(ids))])
 
 
+def healthy_mesh(mesh, ids):
+    """The level hierarchy of A_I: the operator assembled from the healthy
+    macros' elements only (coefficients of the faulty macros set to zero),
+    which is the sum of the healthy sub-stencils at interface nodes (§3.2)."""
+    coeff = mesh.coeff.copy()
+    coeff[np.asarray(list(ids), dtype=np.int64)] = 0.0
+    return Mesh(mesh.sub, mesh.R, mesh.r0, coeff=coeff, affine=mesh.affine)
+
+
+def dn_recover(mesh, u, f, ids, n_global, eta, pre=3, post=3, cg_rtol=1e-12, cg_maxit=1000, hmesh=None):
+    """Dirichlet-Neumann recovery, Algorithm 2 (§4.3), after the fault.
+
+    Reading used for the sign of the flux: the healthy sub-domain keeps, on
+    the interface nodes G, the flux its own elements produce at the time of
+    the fault, b_G = (A_I u)_G (A_I: operator of the healthy macros' elements),
+    i.e. the Neumann data -lambda of Eq. (5) with lambda = -(A_I u)_G of
+    Algorithm 2 step 4.  Omega_I then iterates on A_I restricted to
+    Omega_I and G with right-hand side f on Omega_I and b_G on G; Omega_F
+    iterates on its Dirichlet problem with the interface values of the last
+    finished Omega_I cycle (one-way I -> F update): block j of Omega_F cycles
+    (ceil(j eta) - ceil((j - 1) eta) of them) uses the values after Omega_I
+    cycle j - 1.  Returns the number of Omega_F cycles run.
+    """
+    hm = hmesh or healthy_mesh(mesh, ids)
+    fine = mesh.fine
+    masks = mesh.fault_masks(ids)
+    open_f, closed_f = masks[-1]
+    gamma = closed_f & ~open_f & ~fine.boundary
+    # Omega_I Neumann problem: free = interior nodes outside the open faulty set
+    hp = Problem(hm, [(~lv.boundary) & ~o for lv, (o, _) in zip(mesh.levels, masks)])
+    lp = mesh.local_problem(ids)
+    top = len(mesh.levels) - 1
+    fI = f.copy()
+    interior(fI)[gamma] = apply_A(hm.fine, u)[gamma]
+    snap = interior(u)[gamma].copy()
+    n_F = 0
+    for j in range(1, n_global + 1):
+        cyc = int(math.ceil(j * eta)) - int(math.ceil((j - 1) * eta))
+        uf = u.copy()
+        interior(uf)[gamma] = snap
+        for _ in range(cyc):
+            vcycle(mesh, lp, top, uf, f, pre, post, cg_rtol, cg_maxit)
+        n_F += cyc
+        interior(u)[open_f] = interior(uf)[open_f]
+        vcycle(hm, hp, top, u, fI, pre, post, cg_rtol, cg_maxit)
+        snap = interior(u)[gamma].copy()
+    return n_F
+
+
 def gs_step(lv, u, f, lists):
     """One multicolour Gauss-Seidel step (§2.1 smoother): colours 0,1,2,3 in turn,
     u_i <- (f_i - sum_{j != i} a_ij u_j) / a_ii on the free nodes of each colour.
@@ -472,7 +521,8 @@ def solve(mesh, u, f, rtol=1e-8, max_cycles=50, pre=3, post=3, fault_cycle=-1,
     Dirichlet cycles on Omega_F while Omega_I idles (§4.4), DD = Algorithm 1:
     ``n_F`` local cycles on Omega_F and ``n_I`` cycles on Omega_I with the
     interface frozen, then the global iteration resumes.  ``n_F`` is
-    ``n_local`` if positive, else ceil(eta * n_I) (§4.4).
+    ``n_local`` if positive, else ceil(eta * n_I) (§4.4).  DN = Algorithm 2
+    (see ``dn_recover``).
 
     History: ``hist[0] = 1``, one entry per global cycle, and for a faulty run
     one extra entry right after the fault (and recovery).  ``k_faulty`` counts
@@ -495,7 +545,10 @@ def solve(mesh, u, f, rtol=1e-8, max_cycles=50, pre=3, post=3, fault_cycle=-1,
             iterates.append(u.copy())
         if k == fault_cycle:
             inject_fault(mesh, u, fault_ids)
-            if recovery in (LR, DD):
+            if recovery == DN:
+                n_F = dn_recover(mesh, u, f, fault_ids, n_global, eta, pre, post, cg_rtol, cg_maxit)
+                extra = n_global
+            elif recovery in (LR, DD):
                 n_F = n_local if n_local > 0 else int(math.ceil(eta * n_global))
                 lp = mesh.local_problem(fault_ids)
                 for _ in range(n_F):

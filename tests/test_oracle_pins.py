@@ -379,3 +379,58 @@ def test_local_residual_equals_assembled_residual():
     nodes = np.array([[1, 1, 1], [5, 3, 7], [8, 4, 8], [15, 7, 15], [8, 1, 9]])
     got = O.local_residual(sub, R, c, SHEAR, u, f, nodes)
     assert np.abs(got - np.array([r[z, y, x] for x, y, z in nodes])).max() <= 1e-14
+
+
+# --------------------------------------------------------------------------
+# Dirichlet-Neumann recovery (§4.3, Algorithm 2)
+# --------------------------------------------------------------------------
+
+def test_dn_neumann_subproblem_converges_to_direct_solve():
+    """With many cycles, Omega_I solves A_I [u_I; u_G] = [f_I; b_G] (A_I from
+    the healthy macros' elements, b_G = (A_I u)_G at the fault) and Omega_F
+    the Dirichlet problem with the final interface values."""
+    sub, R = (2, 2, 2), 4
+    m = O.Mesh(sub, R, coeff=_rand_coeff(48, 12))
+    rng = np.random.default_rng(5)
+    u = O.pad(I.initial_guess(sub, R))
+    O.interior(u)[~m.fine.boundary] = rng.standard_normal((~m.fine.boundary).sum())
+    f = O.pad(I.random_load(sub, R, seed=4))
+    ids = I.subcube_macros(sub, 1, 0, 0)
+    hm = O.hhg_oracle.healthy_mesh(m, ids)
+    o, c = m.fault_masks(ids)[-1]
+    gamma = c & ~o & ~m.fine.boundary
+    b = O.interior(f).copy()
+    b[gamma] = O.apply_A(hm.fine, u)[gamma]
+    free_i = ~m.fine.boundary & ~o
+    O.inject_fault(m, u, ids)
+    ref_i = _direct(hm.fine, O.interior(u).copy(), b, free_i)
+    O.dn_recover(m, u, f, ids, n_global=30, eta=1.0, hmesh=hm)
+    assert np.abs(O.interior(u)[free_i] - ref_i[free_i]).max() <= 1e-10 * np.abs(ref_i).max()
+    ref_f = _direct(m.fine, O.interior(u).copy(), O.interior(f), o)
+    assert np.abs(O.interior(u)[o] - ref_f[o]).max() <= 1e-9 * np.abs(ref_f).max()
+
+
+def test_dn_recovers_an_exact_solution():
+    """A fault on the exact discrete solution: the frozen flux is the exact one,
+    so Omega_I stays exact and Omega_F is rebuilt to it."""
+    sub, R = (2, 2, 2), 4
+    m = O.Mesh(sub, R)
+    f = O.pad(I.random_load(sub, R, seed=9))
+    ustar = O.pad(_direct(m.fine, np.zeros(m.fine.shape), O.interior(f), ~m.fine.boundary))
+    u = ustar.copy()
+    ids = [13, 14]
+    O.inject_fault(m, u, ids)
+    O.dn_recover(m, u, f, ids, n_global=12, eta=3.0)
+    assert np.abs(O.interior(u) - O.interior(ustar)).max() <= 1e-9 * np.abs(ustar).max()
+
+
+def test_dn_beats_do_nothing():
+    sub, R = (2, 2, 2), 5
+    m = O.Mesh(sub, R)
+    f = O.pad(I.random_load(sub, R, seed=0))
+    ids = I.subcube_macros(sub, 0, 0, 0)
+    free = _run(m, f, 1e-10)["cycles"]
+    dn = _run(m, f, 1e-10, fault_cycle=5, fault_ids=ids)["k_faulty"]
+    r = _run(m, f, 1e-10, fault_cycle=5, fault_ids=ids, recovery=O.DN, n_global=2, eta=4.0)
+    assert r["n_F"] == 8
+    assert O.kappa(r["k_faulty"], free, 5) < O.kappa(dn, free, 5)
