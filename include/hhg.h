@@ -56,9 +56,12 @@ enum {
 enum {
   HHG_RECOVERY_NONE = 0,      /* do-nothing: zero re-initialisation only */
   HHG_RECOVERY_LR = 1,        /* n_F local cycles on Omega_F, Omega_I idle */
-  HHG_RECOVERY_DD = 2         /* Algorithm 1: n_F local cycles on Omega_F and,
+  HHG_RECOVERY_DD = 2,        /* Algorithm 1: n_F local cycles on Omega_F and,
                                  concurrently, n_I cycles on Omega_I with the
                                  interface frozen */
+  HHG_RECOVERY_DN = 3         /* Algorithm 2 (§4.3): n_I cycles of a Neumann
+                                 problem on Omega_I and the interface, with
+                                 Dirichlet cycles on Omega_F interleaved */
 };
 
 typedef struct hhg_mesh hhg_mesh;
@@ -127,6 +130,24 @@ int hhg_recover_local(hhg_mesh* mesh, const int* macro_ids, int n_ids, int n_loc
                       int n_global, double* seconds_local, double* seconds_global,
                       void* stream);
 
+/* Dirichlet-Neumann recovery (§4.3, Algorithm 2) after hhg_inject_fault on
+ * the same ids.  Omega_I together with the interface Gamma iterates on A_I,
+ * the operator of the healthy macros' elements only, with right-hand side f
+ * on Omega_I and, on Gamma, the flux (A_I u)_Gamma of the iterate at the time
+ * of the fault (the Neumann data of Eq. (5)): n_global V-cycles of that
+ * problem run on the caller's stream.  Omega_F runs Dirichlet V-cycles with
+ * the Gamma values of the last finished Omega_I cycle (one-way update):
+ * before Omega_I cycle j, ceil(j eta) - ceil((j - 1) eta) of them start on a
+ * second stream from the values after Omega_I cycle j - 1, so the two sides
+ * run concurrently.  On return the ghost copies of Gamma in the lost blocks
+ * hold the final Gamma values.  *n_local_run (may be NULL) receives the
+ * Omega_F cycles run, ceil(n_global eta).  seconds_local / seconds_global (may
+ * be NULL) receive the device time spans of the two sides (synchronises).
+ * Errors: HHG_ERR_ARG for a NULL mesh, n_global < 0, eta < 0 or NaN, or an
+ * invalid id list; CUDA errors as HHG_ERR_CUDA. */
+int hhg_recover_dn(hhg_mesh* mesh, const int* macro_ids, int n_ids, int n_global, double eta,
+                   int* n_local_run, double* seconds_local, double* seconds_global, void* stream);
+
 typedef struct {
   double rtol;            /* stop when ||r_k|| <= rtol ||r_0|| (r_0 of the
                              initial iterate) */
@@ -137,9 +158,11 @@ typedef struct {
   const int* fault_ids;   /* host, macro ids of Omega_F */
   int n_fault_ids;
   int recovery;           /* HHG_RECOVERY_* */
-  int n_local;            /* n_F; 0 with DD: ceil(eta * n_global) */
-  int n_global;           /* n_I (DD only) */
-  double eta;             /* superman factor for n_F = ceil(eta * n_I) */
+  int n_local;            /* n_F; 0 with DD: ceil(eta * n_global); unused
+                             with DN */
+  int n_global;           /* n_I (DD and DN) */
+  double eta;             /* superman factor: n_F = ceil(eta * n_I) (DD with
+                             n_local = 0; DN always) */
   int mixed_precision;    /* 1: FP32 cycles inside FP64 iterative refinement
                              (needs a precision-32 mesh) */
   double coarse_rtol;     /* coarse CG relative tolerance (0 = 1e-12) */

@@ -68,6 +68,20 @@ struct hhg_mesh {
   int64_t* fault_restore_off = nullptr;
   int* fault_restore_master = nullptr;
   int n_fault_restore = 0;
+  // Dirichlet-Neumann recovery (§4.3, Algorithm 2) on the finest level:
+  // the Omega_I problem (kind 3), its interface right-hand side with the
+  // frozen flux on Gamma, the Gamma masters, the copies of Gamma inside the
+  // faulty blocks, and two snapshots of the masters
+  DevProblem dn;
+  std::vector<unsigned char> dn_set;
+  bool has_dn = false;
+  int* dn_gamma = nullptr;
+  int n_dn_gamma = 0;
+  int64_t* dn_off = nullptr;
+  int* dn_master = nullptr;
+  int n_dn_copy = 0;
+  double* dn_snap[2] = {nullptr, nullptr};
+  cudaEvent_t ev_dn_e = nullptr, ev_dn_r[2] = {nullptr, nullptr};
   double* staging = nullptr;
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -146,6 +160,28 @@ LevelArgs largs(const hhg_mesh* m, int l) {
   return a;
 }
 
+// Level arguments seen by problem p: kind 3 reaches interface nodes through
+// its own (healthy) copies only.
+LevelArgs plargs(const hhg_mesh* m, const DevProblem& p, int l) {
+  LevelArgs a = largs(m, l);
+  if (p.lv[l].cptr) {
+    a.cptr = p.lv[l].cptr;
+    a.cps = p.lv[l].cps;
+  }
+  return a;
+}
+
+// Interface right-hand side of level l (the finest one may be replaced by
+// the problem's own, FP64 only).
+template <class T>
+const T* level_fI(const DevLevel<T>& D, const DevProblem&, bool) {
+  return D.fI;
+}
+template <>
+const double* level_fI<double>(const DevLevel<double>& D, const DevProblem& p, bool top) {
+  return top && p.fI_top ? p.fI_top : D.fI;
+}
+
 ProbArgs pargs(const DevProblem& p, int l) {
   ProbArgs a;
   a.act = p.act;
@@ -173,6 +209,8 @@ int upload_problem(hhg_mesh* m, const HostProblem& h, DevProblem& d) {
     HHG_TRY(upload(m, &d.lv[l].zero_off, h.lv[l].zero_off));
     d.lv[l].n_zero = (int)h.lv[l].zero_off.size();
     HHG_TRY(upload(m, &d.lv[l].gather, h.lv[l].gather));
+    HHG_TRY(upload(m, &d.lv[l].cptr, h.lv[l].cptr));
+    HHG_TRY(upload(m, &d.lv[l].cps, h.lv[l].copies));
   }
   d.n_cg = h.n_cg;
   d.nnz = (int64_t)h.val.size();
@@ -244,14 +282,15 @@ template <class T>
 int smooth(hhg_mesh* m, Prec<T>& P, DevProblem& p, int l, int steps, cudaStream_t s) {
   const int L = (int)P.lv.size() - 1;
   DevLevel<T>& D = P.lv[l];
-  const LevelArgs a = largs(m, l);
+  const LevelArgs a = plargs(m, p, l);
   const ProbArgs q = pargs(p, l);
+  const T* fI = level_fI<T>(D, p, l == L);
   const bool prof = l == L && p.kind == 0;
   for (int it = 0; it < steps; ++it)
     for (int c = 0; c < 4; ++c) {
       cudaEvent_t b = nullptr, e = nullptr;
       if (prof) HHG_TRY(prof_pair(m, &b, &e));
-      HHG_CUDA(gs_colour<T>(a, q, D.u, D.uI, D.f, D.fI, D.W, P.Winv[l], c, m->host.seven_point, s, b, e));
+      HHG_CUDA(gs_colour<T>(a, q, D.u, D.uI, D.f, fI, D.W, P.Winv[l], c, m->host.seven_point, s, b, e));
     }
   return HHG_OK;
 }
@@ -263,19 +302,19 @@ int vcycle_T(hhg_mesh* m, Prec<T>& P, DevProblem& p, int pre, int post, double c
   const bool s7 = m->host.seven_point;
   for (int l = L; l >= 1; --l) {
     DevLevel<T>& D = P.lv[l];
-    const LevelArgs a = largs(m, l);
+    const LevelArgs a = plargs(m, p, l);
     const ProbArgs q = pargs(p, l);
     HHG_TRY(smooth<T>(m, P, p, l, pre, s));
-    HHG_CUDA(residual<T>(a, q, D.u, D.uI, D.f, D.fI, D.r, D.W, s7, true, nullptr, nullptr, s));
+    HHG_CUDA(residual<T>(a, q, D.u, D.uI, D.f, level_fI<T>(D, p, l == L), D.r, D.W, s7, true, nullptr, nullptr, s));
     DevLevel<T>& C = P.lv[l - 1];
-    HHG_CUDA(restrict_to<T>(largs(m, l - 1), a, pargs(p, l - 1), D.r, C.f, C.fI, C.u, C.uI, s));
+    HHG_CUDA(restrict_to<T>(plargs(m, p, l - 1), a, pargs(p, l - 1), D.r, C.f, C.fI, C.u, C.uI, s));
   }
   HHG_CUDA(coarse_cg<T>(p, P.lv[0].f, P.lv[0].fI, P.lv[0].u, P.lv[0].uI, cg_rtol, cg_maxit, s));
   for (int l = 1; l <= L; ++l) {
     DevLevel<T>& D = P.lv[l];
-    const LevelArgs a = largs(m, l);
+    const LevelArgs a = plargs(m, p, l);
     const ProbArgs q = pargs(p, l);
-    HHG_CUDA(prolong_add<T>(a, largs(m, l - 1), q, D.u, D.uI, P.lv[l - 1].u, s));
+    HHG_CUDA(prolong_add<T>(a, plargs(m, p, l - 1), q, D.u, D.uI, P.lv[l - 1].u, s));
     HHG_TRY(smooth<T>(m, P, p, l, post, s));
   }
   return HHG_OK;
@@ -286,8 +325,8 @@ int norm2_async(hhg_mesh* m, DevProblem& p, cudaStream_t s) {
   const int L = (int)m->d64.lv.size() - 1;
   DevLevel<double>& D = m->d64.lv[L];
   int np = 0;
-  HHG_CUDA(residual<double>(largs(m, L), pargs(p, L), D.u, D.uI, D.f, D.fI, nullptr, D.W, m->host.seven_point, false,
-                            p.partial, &np, s));
+  HHG_CUDA(residual<double>(plargs(m, p, L), pargs(p, L), D.u, D.uI, D.f, level_fI<double>(D, p, true), nullptr, D.W,
+                            m->host.seven_point, false, p.partial, &np, s));
   HHG_CUDA(reduce_partials(p.partial, np, p.scalar, s));
   return HHG_OK;
 }
@@ -317,8 +356,8 @@ int ir_residual(hhg_mesh* m, DevProblem& p, cudaStream_t s) {
   DevLevel<double>& D = m->d64.lv[L];
   DevLevel<float>& E = m->d32.lv[L];
   int np = 0;
-  HHG_CUDA(residual_to_f32(largs(m, L), pargs(p, L), D.u, D.uI, D.f, D.fI, E.f, E.fI, D.W, m->host.seven_point,
-                           p.partial, &np, s));
+  HHG_CUDA(residual_to_f32(plargs(m, p, L), pargs(p, L), D.u, D.uI, D.f, level_fI<double>(D, p, true), E.f, E.fI, D.W,
+                           m->host.seven_point, p.partial, &np, s));
   HHG_CUDA(reduce_partials(p.partial, np, p.scalar, s));
   return HHG_OK;
 }
@@ -327,10 +366,10 @@ int ir_cycle(hhg_mesh* m, DevProblem& p, int pre, int post, double cg_rtol, int 
   const int L = (int)m->d64.lv.size() - 1;
   DevLevel<float>& E = m->d32.lv[L];
   HHG_TRY(ir_residual(m, p, s));
-  HHG_CUDA(zero_problem_blocks<float>(largs(m, L), pargs(p, L), E.u, E.uI, s));
+  HHG_CUDA(zero_problem_blocks<float>(plargs(m, p, L), pargs(p, L), E.u, E.uI, s));
   HHG_TRY(vcycle_T<float>(m, m->d32, p, pre, post, cg_rtol, cg_maxit, s));
   DevLevel<double>& D = m->d64.lv[L];
-  HHG_CUDA(add_correction(largs(m, L), pargs(p, L), D.u, D.uI, E.u, E.uI, s));
+  HHG_CUDA(add_correction(plargs(m, p, L), pargs(p, L), D.u, D.uI, E.u, E.uI, s));
   return HHG_OK;
 }
 
@@ -459,6 +498,129 @@ int recover(hhg_mesh* m, int n_local, int n_global, bool mixed, int pre, int pos
 }
 
 // Stencils of all levels and the coarse CG matrices for new coefficients.
+// Dirichlet-Neumann recovery (§4.3, Algorithm 2).  Omega_I (kind 3) frees
+// every node with a healthy copy, Gamma included, under A_I; Omega_F (kind 1)
+// is the Dirichlet problem of the lost nodes.  Gamma is the set of free
+// kind-3 interface nodes that also have a faulty copy.
+int setup_dn(hhg_mesh* m, const std::vector<unsigned char>& set) {
+  HHG_TRY(setup_fault(m, set));
+  if (m->has_dn && set == m->dn_set) return HHG_OK;
+  HostProblem hd;
+  try {
+    build_problem(m->host, 3, set, hd);
+  } catch (const std::exception& e) {
+    return fail(HHG_ERR_ARG, std::string("fault set: ") + e.what());
+  }
+  m->dn = DevProblem();
+  HHG_TRY(upload_problem(m, hd, m->dn));
+  const int L = (int)m->host.lv.size() - 1;
+  const HostLevel& H = m->host.lv[L];
+  std::vector<int> gamma;
+  std::vector<int64_t> off;
+  std::vector<int> mst;
+  for (int n : hd.lv[L].free_if) {
+    bool any_f = false;
+    for (int c = H.if_cptr[n]; c < H.if_cptr[n + 1]; ++c) {
+      const Copy& cp = H.if_copy[c];
+      if (!set[cp.macro]) continue;
+      any_f = true;
+      off.push_back((int64_t)cp.macro * H.block + lidx(H.SL.data(), H.N, cp.i, cp.j, cp.k));
+      mst.push_back(n);
+    }
+    if (any_f) gamma.push_back(n);
+  }
+  HHG_TRY(upload(m, &m->dn_gamma, gamma));
+  m->n_dn_gamma = (int)gamma.size();
+  HHG_TRY(upload(m, &m->dn_off, off));
+  HHG_TRY(upload(m, &m->dn_master, mst));
+  m->n_dn_copy = (int)off.size();
+  const size_t nI = (size_t)std::max(1, H.n_if);
+  HHG_TRY(dalloc(m, &m->dn.fI_top, nI));
+  for (int b = 0; b < 2; ++b)
+    if (!m->dn_snap[b]) HHG_TRY(dalloc(m, &m->dn_snap[b], nI));
+  if (!m->ev_dn_e) {
+    HHG_CUDA(cudaEventCreateWithFlags(&m->ev_dn_e, cudaEventDisableTiming));
+    for (int b = 0; b < 2; ++b) HHG_CUDA(cudaEventCreateWithFlags(&m->ev_dn_r[b], cudaEventDisableTiming));
+  }
+  m->dn_set = set;
+  m->has_dn = true;
+  return HHG_OK;
+}
+
+// n_global cycles on Omega_I; before cycle j, block j of Omega_F cycles
+// (ceil(j eta) - ceil((j - 1) eta) of them) starts on the side stream from the
+// Gamma values left by Omega_I cycle j - 1 (the copies inside the faulty
+// blocks are the Dirichlet data of Omega_F, rewritten from a snapshot of the
+// masters), so Omega_F block j runs concurrently with Omega_I cycle j.  The
+// healthy side keeps, as the right-hand side of its Gamma rows, the flux
+// (A_I u)_Gamma of the iterate at the time of the fault.  Returns the number
+// of Omega_F cycles in *n_f.
+int recover_dn(hhg_mesh* m, int n_global, double eta, bool mixed, int pre, int post, double cg_rtol, int cg_maxit,
+               int* n_f, double* t_local, double* t_global, cudaStream_t s) {
+  const int L = (int)m->host.lv.size() - 1;
+  DevLevel<double>& D = m->d64.lv[L];
+  const size_t nI = (size_t)std::max(1, D.n_if) * sizeof(double);
+  const bool timed = t_local || t_global;
+  cudaEvent_t a0 = nullptr, a1 = nullptr, b0 = nullptr, b1 = nullptr;
+  if (timed) {
+    HHG_CUDA(cudaEventCreate(&a0));
+    HHG_CUDA(cudaEventCreate(&a1));
+    HHG_CUDA(cudaEventCreate(&b0));
+    HHG_CUDA(cudaEventCreate(&b1));
+  }
+  HHG_CUDA(cudaMemcpyAsync(m->dn.fI_top, D.fI, nI, cudaMemcpyDeviceToDevice, s));
+  HHG_CUDA(apply_if_nodes(plargs(m, m->dn, L), D.u, D.uI, D.W, m->host.seven_point, m->dn_gamma, m->n_dn_gamma,
+                          m->dn.fI_top, s));
+  HHG_CUDA(cudaEventRecord(m->ev_dn_e, s));
+  if (timed) HHG_CUDA(cudaEventRecord(b0, s));
+  int total = 0;
+  for (int j = 1; j <= n_global; ++j) {
+    const int cyc = (int)std::ceil(j * eta) - (int)std::ceil((j - 1) * eta);
+    // Omega_F, block j: after Omega_I cycle j - 1 and its snapshot
+    HHG_CUDA(cudaStreamWaitEvent(m->side, m->ev_dn_e, 0));
+    if (j == 1 && timed) HHG_CUDA(cudaEventRecord(a0, m->side));
+    if (j >= 2)
+      HHG_CUDA(restore_copies(D.u, m->dn_snap[(j - 1) & 1], m->dn_off, m->dn_master, m->n_dn_copy, m->side));
+    HHG_CUDA(cudaEventRecord(m->ev_dn_r[j & 1], m->side));
+    for (int c = 0; c < cyc; ++c) HHG_TRY(cycle(m, m->faulty, mixed, pre, post, cg_rtol, cg_maxit, m->side));
+    total += cyc;
+    // Omega_I, cycle j; its snapshot overwrites the one block j - 1 read
+    HHG_TRY(cycle(m, m->dn, mixed, pre, post, cg_rtol, cg_maxit, s));
+    if (j >= 3) HHG_CUDA(cudaStreamWaitEvent(s, m->ev_dn_r[(j - 1) & 1], 0));
+    HHG_CUDA(copy_listed(D.uI, m->dn_snap[j & 1], m->dn_gamma, m->n_dn_gamma, s));
+    HHG_CUDA(cudaEventRecord(m->ev_dn_e, s));
+  }
+  if (timed) {
+    HHG_CUDA(cudaEventRecord(b1, s));
+    HHG_CUDA(cudaEventRecord(a1, m->side));
+  }
+  // join; the copies of Gamma inside the faulty blocks take the final values
+  HHG_CUDA(cudaEventRecord(m->ev_join, m->side));
+  HHG_CUDA(cudaStreamWaitEvent(s, m->ev_join, 0));
+  HHG_CUDA(restore_copies(D.u, D.uI, m->dn_off, m->dn_master, m->n_dn_copy, s));
+  if (n_f) *n_f = total;
+  if (timed) {
+    HHG_CUDA(cudaStreamSynchronize(s));
+    float ms = 0.f;
+    if (t_local) {
+      *t_local = 0.0;
+      if (n_global > 0) {
+        HHG_CUDA(cudaEventElapsedTime(&ms, a0, a1));
+        *t_local = ms * 1e-3;
+      }
+    }
+    if (t_global) {
+      HHG_CUDA(cudaEventElapsedTime(&ms, b0, b1));
+      *t_global = ms * 1e-3;
+    }
+    cudaEventDestroy(a0);
+    cudaEventDestroy(a1);
+    cudaEventDestroy(b0);
+    cudaEventDestroy(b1);
+  }
+  return HHG_OK;
+}
+
 int update_coefficients(hhg_mesh* m, const double* coeff) {
   try {
     set_coefficients(m->host, coeff);
@@ -690,6 +852,9 @@ int hhg_mesh_destroy(hhg_mesh* m) {
   if (m->side) cudaStreamDestroy(m->side);
   if (m->ev_fork) cudaEventDestroy(m->ev_fork);
   if (m->ev_join) cudaEventDestroy(m->ev_join);
+  if (m->ev_dn_e) cudaEventDestroy(m->ev_dn_e);
+  for (int b = 0; b < 2; ++b)
+    if (m->ev_dn_r[b]) cudaEventDestroy(m->ev_dn_r[b]);
   if (m->host_scalar) cudaFreeHost(m->host_scalar);
   for (cudaEvent_t ev : m->prof_ev) cudaEventDestroy(ev);
   delete m;
@@ -786,6 +951,16 @@ int hhg_recover_local(hhg_mesh* m, const int* ids, int n, int n_local, int n_glo
   HHG_TRY(setup_fault(m, set));
   return recover(m, n_local, n_global, false, 3, 3, 1e-12, 1000, seconds_local, seconds_global,
                  (cudaStream_t)stream);
+}
+
+int hhg_recover_dn(hhg_mesh* m, const int* ids, int n, int n_global, double eta, int* n_local_run,
+                   double* seconds_local, double* seconds_global, void* stream) {
+  if (!m || n_global < 0 || !(eta >= 0.0)) return fail(HHG_ERR_ARG, "invalid argument");
+  std::vector<unsigned char> set;
+  HHG_TRY(check_ids(m, ids, n, set));
+  HHG_TRY(setup_dn(m, set));
+  return recover_dn(m, n_global, eta, false, 3, 3, 1e-12, 1000, n_local_run, seconds_local, seconds_global,
+                    (cudaStream_t)stream);
 }
 
 int hhg_set_coefficients(hhg_mesh* m, const double* coeff, void* stream) {
@@ -1007,9 +1182,14 @@ int hhg_solve(hhg_mesh* m, const hhg_solve_opts* o, double* hist, int* n_hist, i
   if (faulty) {
     std::vector<unsigned char> set;
     HHG_TRY(check_ids(m, o->fault_ids, o->n_fault_ids, set));
-    HHG_TRY(setup_fault(m, set));
-    if (o->recovery < HHG_RECOVERY_NONE || o->recovery > HHG_RECOVERY_DD)
+    if (o->recovery < HHG_RECOVERY_NONE || o->recovery > HHG_RECOVERY_DN)
       return fail(HHG_ERR_ARG, "unknown recovery strategy");
+    if (o->recovery == HHG_RECOVERY_DN) {
+      if (o->n_global < 0 || !(o->eta >= 0.0)) return fail(HHG_ERR_ARG, "invalid n_global / eta");
+      HHG_TRY(setup_dn(m, set));
+    } else {
+      HHG_TRY(setup_fault(m, set));
+    }
   }
   cudaStream_t s = (cudaStream_t)stream;
   int nh = 0;
@@ -1050,7 +1230,9 @@ int hhg_solve(hhg_mesh* m, const hhg_solve_opts* o, double* hist, int* n_hist, i
     push(rel);
     if (faulty && k == o->fault_cycle) {
       HHG_TRY(inject(m, s));
-      if (o->recovery != HHG_RECOVERY_NONE) {
+      if (o->recovery == HHG_RECOVERY_DN) {
+        HHG_TRY(recover_dn(m, o->n_global, o->eta, mixed, pre, post, cg_rtol, cg_maxit, nullptr, nullptr, nullptr, s));
+      } else if (o->recovery != HHG_RECOVERY_NONE) {
         const int n_global = o->recovery == HHG_RECOVERY_DD ? o->n_global : 0;
         int n_local = o->n_local;
         if (n_local <= 0 && o->recovery == HHG_RECOVERY_DD) n_local = (int)std::ceil(o->eta * o->n_global);

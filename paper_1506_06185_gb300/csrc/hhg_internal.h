@@ -150,13 +150,20 @@ struct HostMesh {
 };
 
 // Problem: which nodes are unknowns.  kind 0 = global, 1 = faulty sub-domain,
-// 2 = healthy sub-domain (interface frozen).
+// 2 = healthy sub-domain (interface frozen), 3 = healthy sub-domain with the
+// interface free and only the healthy macros' elements in the operator (A_I,
+// the Neumann side of Dirichlet-Neumann recovery, §4.3 Algorithm 2).
 struct HostProblemLevel {
   std::vector<int> free_if;           // free interface nodes grouped by colour
   int col_off[5] = {0, 0, 0, 0, 0};
   std::vector<int64_t> zero_off;      // frozen copies in active blocks
   std::vector<int64_t> gather;        // [free_if.size()][15] fine offsets of the
                                       // restriction onto this level (-1 = none)
+  // Interface copies restricted to the active macros (kind 3 only; empty
+  // otherwise, where every copy of a free node is active): CSR over all
+  // interface nodes of the level.
+  std::vector<int> cptr;
+  std::vector<Copy> copies;
 };
 
 struct HostProblem {
@@ -221,6 +228,8 @@ struct DevProblemLevel {
   int64_t* zero_off = nullptr;
   int n_zero = 0;
   int64_t* gather = nullptr;
+  int* cptr = nullptr;                // active copies (kind 3), else null
+  Copy* cps = nullptr;
 };
 
 struct DevProblem {
@@ -245,6 +254,8 @@ struct DevProblem {
   int n_partial = 0;
   double* scalar = nullptr;         // [4]: norm^2 result, cg info
   int* cg_iters = nullptr;
+  double* fI_top = nullptr;         // finest-level FP64 interface right-hand
+                                    // side replacing the mesh's (kind 3)
   cudaStream_t stream = nullptr;    // stream owned by the problem (DD half)
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
 };

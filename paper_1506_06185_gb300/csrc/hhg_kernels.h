@@ -88,6 +88,12 @@ cudaError_t grad_partials(const LevelArgs& L, int n_macro, const double* u, cons
 cudaError_t reduce_per_macro(const double* partial, int n_per, int n_macro, double* out, cudaStream_t s);
 
 // Fault support.
+// out[list[q]] = (A u) at interface node list[q], summed over the copies that
+// L's copy lists hold for it (FP64, finest level).
+cudaError_t apply_if_nodes(const LevelArgs& L, const double* u, const double* uI, const double* W, bool seven_point,
+                           const int* list, int n, double* out, cudaStream_t s);
+// dst[idx[q]] = src[idx[q]] for q < n.
+cudaError_t copy_listed(const double* src, double* dst, const int* idx, int n, cudaStream_t s);
 cudaError_t set_masters_zero(double* uI, const int* ids, int n, cudaStream_t s);
 cudaError_t restore_copies(double* u, const double* uI, const int64_t* off, const int* master, int n,
                            cudaStream_t s);

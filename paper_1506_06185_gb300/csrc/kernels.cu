@@ -414,7 +414,10 @@ __global__ void __launch_bounds__(CTA) k_restrict(int Nc, const int* __restrict_
         const int node = list[q];
         const int64_t* g = gather + (size_t)q * NDIR;
         T acc = T(0);
-        for (int e = 1; e < NDIR; ++e) acc += rf[g[e]];
+        for (int e = 1; e < NDIR; ++e) {
+          const int64_t o = g[e];
+          if (o >= 0) acc += rf[o];
+        }
         fIc[node] = rf[g[0]] + T(0.5) * acc;
         uIc[node] = T(0);
         write_copies(Nc, rsc, bc, uc, cps, cptr[node], cptr[node + 1], T(0));
@@ -793,6 +796,26 @@ __global__ void k_export_if(const int64_t* __restrict__ gid, int n, const T* __r
   if (q < n) g[gid[q]] = (double)m[q];
 }
 
+// out[node] = (A u)_node over the copies listed for each node (the healthy
+// copies give A_I, the flux of the healthy side at an interface node).
+template <bool S7>
+__global__ void k_if_apply(int N, const int* __restrict__ rs, int64_t block, const double* __restrict__ u,
+                           const double* __restrict__ uI, const double* __restrict__ W, const int* __restrict__ cptr,
+                           const Copy* __restrict__ cps, const int* __restrict__ list, int n, double* __restrict__ out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const int node = list[q];
+  double off = 0.0, diag = 0.0;
+  if_stencil<double, S7>(N, rs, block, u, W, cps, cptr[node], cptr[node + 1], off, diag);
+  out[node] = diag * uI[node] + off;
+}
+
+__global__ void k_copy_listed(const double* __restrict__ src, double* __restrict__ dst, const int* __restrict__ idx,
+                              int n) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) dst[idx[q]] = src[idx[q]];
+}
+
 __global__ void k_set_masters_zero(double* __restrict__ uI, const int* __restrict__ ids, int n) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q < n) uI[ids[q]] = 0.0;
@@ -1003,6 +1026,26 @@ cudaError_t reduce_per_macro(const double* partial, int n_per, int n_macro, doub
   if (n_macro > 0) {
     ++g_kernel_launches;
     k_reduce_per_macro<<<n_macro, 256, 0, s>>>(partial, n_per, out);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t apply_if_nodes(const LevelArgs& L, const double* u, const double* uI, const double* W, bool seven_point,
+                           const int* list, int n, double* out, cudaStream_t s) {
+  if (n > 0) {
+    ++g_kernel_launches;
+    if (seven_point)
+      k_if_apply<true><<<lin_grid(n, 128), 128, 0, s>>>(L.N, L.rs, L.block, u, uI, W, L.cptr, L.cps, list, n, out);
+    else
+      k_if_apply<false><<<lin_grid(n, 128), 128, 0, s>>>(L.N, L.rs, L.block, u, uI, W, L.cptr, L.cps, list, n, out);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t copy_listed(const double* src, double* dst, const int* idx, int n, cudaStream_t s) {
+  if (n > 0) {
+    ++g_kernel_launches;
+    k_copy_listed<<<lin_grid(n, 256), 256, 0, s>>>(src, dst, idx, n);
   }
   return cudaGetLastError();
 }

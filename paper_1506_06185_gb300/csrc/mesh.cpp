@@ -370,7 +370,8 @@ void assemble_coarse(const HostMesh& m, HostProblem& p) {
     for (int n : p.lv[0].free_if) {
       Dof d;
       d.master = n;
-      for (int c = L.if_cptr[n]; c < L.if_cptr[n + 1]; ++c) d.cps.push_back(L.if_copy[c]);
+      for (int c = L.if_cptr[n]; c < L.if_cptr[n + 1]; ++c)
+        if (p.macro_active[L.if_copy[c].macro]) d.cps.push_back(L.if_copy[c]);
       cidx[L.if_gid[n]] = (int)dofs.size();
       dofs.push_back(d);
     }
@@ -434,6 +435,7 @@ void build_problem(const HostMesh& m, int kind, const std::vector<unsigned char>
       bool fr = !L.if_dirichlet[n];
       if (kind == 1) fr = fr && all_f;
       if (kind == 2) fr = fr && !any_f;
+      if (kind == 3) fr = fr && !all_f;
       is_free[l][n] = fr;
       if (fr) {
         bycol[L.if_colour[n]].push_back(n);
@@ -449,6 +451,16 @@ void build_problem(const HostMesh& m, int kind, const std::vector<unsigned char>
     for (int c = 0; c < 4; ++c) {
       P.free_if.insert(P.free_if.end(), bycol[c].begin(), bycol[c].end());
       P.col_off[c + 1] = (int)P.free_if.size();
+    }
+    if (kind == 3) {
+      // only the healthy copies take part: their sub-stencils sum to A_I, and
+      // the copies inside the faulty blocks keep the other side's values
+      P.cptr.assign(1, 0);
+      for (int n = 0; n < L.n_if; ++n) {
+        for (int c = L.if_cptr[n]; c < L.if_cptr[n + 1]; ++c)
+          if (p.macro_active[L.if_copy[c].macro]) P.copies.push_back(L.if_copy[c]);
+        P.cptr.push_back((int)P.copies.size());
+      }
     }
   }
   // restriction gathers onto every level below the finest
@@ -481,7 +493,9 @@ void build_problem(const HostMesh& m, int kind, const std::vector<unsigned char>
           ++cnt;
         }
       }
-      if (cnt != NDIR) throw std::runtime_error("restriction stencil incomplete");
+      // with the interface free next to inactive macros (kind 3) the fine
+      // points inside those macros are not reachable; their residual is zero
+      if (cnt != NDIR && !(kind == 3 && cnt > 0)) throw std::runtime_error("restriction stencil incomplete");
     }
   }
   assemble_coarse(m, p);

@@ -21,13 +21,13 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.environ.get("HHG_LIB") or os.path.join(_HERE, "_lib", "libhhg.so")
 
 HHG_OK, HHG_ERR_ARG, HHG_ERR_CUDA, HHG_ERR_OOM, HHG_ERR_TIMEOUT, HHG_ERR_NOT_CONVERGED, HHG_ERR_STATE = range(7)
-HHG_RECOVERY_NONE, HHG_RECOVERY_LR, HHG_RECOVERY_DD = 0, 1, 2
+HHG_RECOVERY_NONE, HHG_RECOVERY_LR, HHG_RECOVERY_DD, HHG_RECOVERY_DN = 0, 1, 2, 3
 
 EXPORTS = ["hhg_mesh_create", "hhg_mesh_destroy", "hhg_mesh_info", "hhg_mesh_bytes", "hhg_set_problem",
            "hhg_get_solution", "hhg_vcycle", "hhg_residual_norm", "hhg_inject_fault", "hhg_recover_local",
            "hhg_solve", "hhg_last_error", "hhg_profile_enable", "hhg_profile_read", "hhg_profile_info",
            "hhg_launch_count", "hhg_vcycle_noalloc", "hhg_set_coefficients", "hhg_grad_coeff",
-           "hhg_autotune", "hhg_batch_create", "hhg_batch_launch", "hhg_batch_destroy"]
+           "hhg_autotune", "hhg_batch_create", "hhg_batch_launch", "hhg_batch_destroy", "hhg_recover_dn"]
 
 
 class hhg_mesh_desc(C.Structure):
@@ -66,6 +66,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "hhg_inject_fault": ([P, C.POINTER(C.c_int), C.c_int, P], C.c_int),
         "hhg_recover_local": ([P, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int, C.POINTER(C.c_double),
                                C.POINTER(C.c_double), P], C.c_int),
+        "hhg_recover_dn": ([P, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_double, C.POINTER(C.c_int),
+                            C.POINTER(C.c_double), C.POINTER(C.c_double), P], C.c_int),
         "hhg_solve": ([P, C.POINTER(hhg_solve_opts), C.POINTER(C.c_double), C.POINTER(C.c_int),
                        C.POINTER(C.c_int), P], C.c_int),
         "hhg_last_error": ([C.c_char_p, C.c_size_t], C.c_int),
@@ -217,6 +219,17 @@ def hhg_recover_local(h, ids, n_local, n_global=0, timed=False, stream=None):
     return (tl.value, tg.value) if timed else None
 
 
+def hhg_recover_dn(h, ids, n_global, eta, timed=False, stream=None):
+    """Returns the Omega_F cycles run, and with ``timed`` also the device
+    seconds of the two sides."""
+    a, n = _ids(ids)
+    nf = C.c_int()
+    tl, tg = C.c_double(), C.c_double()
+    _check(lib().hhg_recover_dn(h, a, n, int(n_global), float(eta), C.byref(nf), C.byref(tl) if timed else None,
+                                C.byref(tg) if timed else None, _stream(stream)))
+    return (nf.value, tl.value, tg.value) if timed else nf.value
+
+
 def hhg_solve(h, rtol=1e-8, max_cycles=50, pre=3, post=3, fault_cycle=0, fault_ids=(), recovery=0, n_local=0,
               n_global=0, eta=1.0, mixed_precision=False, coarse_rtol=0.0, coarse_maxit=0, stream=None,
               allow_not_converged=False):
@@ -357,6 +370,9 @@ class Mesh:
 
     def recover_local(self, ids, n_local, n_global=0, timed=False, stream=None):
         return hhg_recover_local(self.h, ids, n_local, n_global, timed, stream)
+
+    def recover_dn(self, ids, n_global, eta, timed=False, stream=None):
+        return hhg_recover_dn(self.h, ids, n_global, eta, timed, stream)
 
     def solve(self, **kw):
         return hhg_solve(self.h, **kw)
