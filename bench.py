@@ -300,7 +300,7 @@ def run_ours(args):
            "d2h_bytes_per_step": nbytes, "ms_per_step": 1e3 * t_e2e / k_e2e}
     M.set_problem(f_dev, None)
 
-    # variants on the same GPU: fault-free, do-nothing, LR, and mixed precision
+    # variants on the same GPU: fault-free, do-nothing, LR, DN, and mixed precision
     variants = {}
     if not args.quick:
         def timed(**over):
@@ -315,6 +315,7 @@ def run_ours(args):
         ms_dn, h_dn, c_dn = timed(recovery=hhg.HHG_RECOVERY_NONE)
         ms_lr, h_lr, c_lr = timed(recovery=hhg.HHG_RECOVERY_LR, n_local=3)
         ms_dd, h_dd, c_dd = timed()
+        ms_dnr, h_dnr, c_dnr = timed(recovery=hhg.HHG_RECOVERY_DN)
         u_fp64 = torch.zeros_like(f_dev)
         M.get_solution(u_fp64)
         ms_mx, h_mx, c_mx = timed(mixed_precision=True)
@@ -329,6 +330,7 @@ def run_ours(args):
             "do_nothing_fp64": {"ms": ms_dn, "cycles": c_dn, "kappa": kappa(c_dn)},
             "local_recovery_fp64_nF3": {"ms": ms_lr, "cycles": c_lr, "kappa": kappa(c_lr)},
             "dd_fp64_eta4_nI3": {"ms": ms_dd, "cycles": c_dd, "kappa": kappa(c_dd, N_I)},
+            "dn_fp64_eta4_nI3": {"ms": ms_dnr, "cycles": c_dnr, "kappa": kappa(c_dnr, N_I)},
             "dd_mixed_fp32_in_fp64_ir": {"ms": ms_mx, "cycles": c_mx, "final_rel_res": float(h_mx[-1]),
                                          "max_abs_diff_vs_fp64_solution": diff, "fp64_solution_max": scale},
             "fault_free_mixed": {"ms": ms_mx_free, "cycles": c_mx_free},
@@ -399,6 +401,25 @@ def run_batch(args):
     ms = np.array(runs)
     lat = ms[:, :-1].ravel()
     total = ms[:, -1].max(axis=0) if ms.ndim == 1 else ms.max(axis=1)
+
+    # the plain FP64 form of the same work, one call after the other on one
+    # stream: the global FP64 solve to 1e-8, then every recovery (fault
+    # injection + 4 local FP64 cycles)
+    def plain():
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        G.set_problem(None, gu0)
+        a.record()
+        _, c, _ = G.solve(rtol=RTOL, max_cycles=MAX_CYCLES)
+        for M, ids, cyc in tasks:
+            M.inject_fault(ids)
+            M.recover_local(ids, cyc)
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), c
+    plain()
+    plain_runs = [plain() for _ in range(max(1, min(args.steps, 3)))]
+    plain_ms = float(np.median([r[0] for r in plain_runs]))
     line = {"metric": "batched recovery: total time to 1e-8 (global) and per-problem latency", "impl": "ours",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "f32-in-f64-ir", "data": "synthetic",
             "config": {"workload": "global 4x4x4x6 macros refined 7 levels (1.33e8 DoF) to 1e-8 + 64 recovery "
@@ -406,9 +427,65 @@ def run_batch(args):
                                    "CUDA-graph launch", "global_cycles": g_cycles,
                        "task_dof": [int(t[0].n_dof) for t in tasks]},
             "total_ms_median": float(np.median(total)), "latency_ms_p50": float(np.percentile(lat, 50)),
-            "latency_ms_p99": float(np.percentile(lat, 99)), "setup_s": setup_s}
+            "latency_ms_p99": float(np.percentile(lat, 99)), "setup_s": setup_s,
+            "plain_fp64_sequential_ms": plain_ms, "plain_fp64_global_cycles": plain_runs[0][1]}
     print(json.dumps(line), flush=True)
     batch.close()
+    return 0
+
+
+def run_precision(args):
+    """FP64 against FP32-in-FP64 refinement on the cube refined 9 levels
+    (1.07e9 DoF): fault after cycle 4 on sub-cube (0,0,0), DD recovery
+    (eta = 4, n_I = 3), time to 1e-8, and the difference of the two
+    solutions."""
+    import numpy as np
+    import torch
+
+    import hhg_inputs as I
+    from paper_1506_06185_gb300 import build
+    from paper_1506_06185_gb300 import hhg
+
+    build()
+    torch.cuda.set_device(0)
+    sub, r = SUB, 9
+    t0 = time.perf_counter()
+    M = hhg.Mesh(sub, r, precision=32)
+    setup_s = time.perf_counter() - t0
+    f = torch.from_numpy(I.random_load(sub, r, SEED)).cuda()
+    u0 = torch.zeros_like(f)
+    M.set_problem(f, u0)
+    kw = dict(rtol=RTOL, max_cycles=MAX_CYCLES, fault_cycle=4, fault_ids=I.subcube_macros(sub),
+              recovery=hhg.HHG_RECOVERY_DD, n_global=N_I, eta=ETA)
+    out = {}
+    sols = {}
+    for name, mixed in (("fp64", False), ("mixed_fp32_in_fp64_ir", True)):
+        times = []
+        for it in range(args.warmup + args.steps):
+            M.set_problem(None, u0)
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            hist, cyc, _ = M.solve(mixed_precision=mixed, **kw)
+            b.record()
+            torch.cuda.synchronize()
+            if it >= args.warmup:
+                times.append(a.elapsed_time(b))
+        u = torch.zeros_like(f)
+        M.get_solution(u)
+        sols[name] = u
+        out[name] = {"ms_median": float(np.median(times)), "cycles": cyc, "final_rel_res": float(hist[-1])}
+    d = sols["mixed_fp32_in_fp64_ir"] - sols["fp64"]
+    line = {"metric": "time to 1e-8 rel. residual w/ fault, FP64 vs FP32-in-FP64 IR", "impl": "ours", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+            "config": {"workload": "cube 2x2x2x6 macro-tets refined 9 levels (1.07e9 DoF), random load seed 0, "
+                                   "fault after cycle 4 erases sub-cube (0,0,0), DD eta=4 n_I=3, rtol 1e-8",
+                       "dof": M.n_dof, "mesh_setup_s": setup_s, "device_bytes": M.bytes()},
+            "forms": out, "speedup_mixed": out["fp64"]["ms_median"] / out["mixed_fp32_in_fp64_ir"]["ms_median"],
+            "rel_l2_diff_mixed_vs_fp64": float(d.norm() / sols["fp64"].norm()),
+            "max_abs_diff_mixed_vs_fp64": float(d.abs().max())}
+    M.close()
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -421,6 +498,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the variant timings")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--batch", action="store_true", help="run the batched-recovery workload instead")
+    ap.add_argument("--precision", action="store_true",
+                    help="run FP64 against mixed precision on the cube refined 9 levels instead")
     args = ap.parse_args()
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
@@ -428,6 +507,8 @@ def main():
         return run_reference(args)
     if args.batch:
         return run_batch(args)
+    if args.precision:
+        return run_precision(args)
     return run_ours(args)
 
 
