@@ -315,6 +315,7 @@ def run_ours(args):
         ms_dn, h_dn, c_dn = timed(recovery=hhg.HHG_RECOVERY_NONE)
         ms_lr, h_lr, c_lr = timed(recovery=hhg.HHG_RECOVERY_LR, n_local=3)
         ms_dd, h_dd, c_dd = timed()
+        step(recovery=hhg.HHG_RECOVERY_DN)   # builds the Neumann-side problem once
         ms_dnr, h_dnr, c_dnr = timed(recovery=hhg.HHG_RECOVERY_DN)
         u_fp64 = torch.zeros_like(f_dev)
         M.get_solution(u_fp64)

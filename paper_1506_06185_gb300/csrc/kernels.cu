@@ -611,7 +611,8 @@ __device__ __forceinline__ double cta_sum(double v, double* sh) {
   if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x < 32) {
-    double s = sh[threadIdx.x];
+    // only the first blockDim.x / 32 entries were written
+    double s = threadIdx.x < (blockDim.x + 31) / 32 ? sh[threadIdx.x] : 0.0;
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
     if (threadIdx.x == 0) sh[32] = s;
   }
