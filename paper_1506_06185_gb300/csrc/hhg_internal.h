@@ -61,21 +61,26 @@ __host__ __device__ __forceinline__ bool in_lattice(int i, int j, int k, int N) 
 // The colour of node (i, j, k) is (i + 2j + 3k) mod 4, equal to (x + y + z)
 // mod 4 of its global grid coordinates.  A block holds four colour arrays of
 // CS slots each (block = 4 CS).  Inside each colour array the rows (j, k)
-// follow each other (k major); row (j, k) has L = N + 1 - j - k nodes and
-// gets ceil(L / 4) slots, node i sitting in slot i >> 2 of the row of its
-// colour.  With S(m) = sum_{l=1..m} ceil(l / 4) = (a + 1)(2a + b) for
-// m = 4a + b, the rows of slice k before row j take S(M) - S(M - j) slots
-// (M = N + 1 - k), and the per-level table SL[k] = sum_{k' < k} S(N + 1 - k')
-// gives the slice starts:
+// follow each other (k major); row (j, k) has L = N + 1 - j - k nodes, node i
+// sitting in slot i >> 2 of the row of its colour, and the row gets
+// 4 ceil(L / 16) slots: a multiple of four, so that every row starts on a
+// 16-byte boundary (FP32) and consecutive same-colour nodes of a row can be
+// moved as one vector.  With S(m) = sum_{l=1..m} 4 ceil(l / 16)
+// = 4 (a + 1)(8a + b) for m = 16a + b, the rows of slice k before row j take
+// S(M) - S(M - j) slots (M = N + 1 - k), and the per-level table
+// SL[k] = sum_{k' < k} S(N + 1 - k') gives the slice starts:
 //   offset(i, j, k) = c CS + SL[k] + S(M) - S(M - j) + (i >> 2).
-// The arrays are dense (at most 3 idle slots per row), and a sweep of one
-// colour streams exactly the arrays it reads and writes.  SL has N + 3
-// entries; SL[N + 2] holds CS.
+// The arrays are dense up to at most 3 idle slots per row plus the padding
+// to four, and a sweep of one colour streams exactly the arrays it reads and
+// writes.  SL has N + 3 entries; SL[N + 2] holds CS.
 // ---------------------------------------------------------------------------
 __host__ __device__ __forceinline__ int slot_prefix(int m) {
-  const int a = m >> 2, b = m & 3;
-  return (a + 1) * (2 * a + b);
+  const int a = m >> 4, b = m & 15;
+  return 4 * (a + 1) * (8 * a + b);
 }
+
+// Slots of a row of L nodes (one colour).
+__host__ __device__ __forceinline__ int row_slots(int L) { return 4 * ((L + 15) >> 4); }
 
 __host__ __device__ __forceinline__ int lidx(const int* SL, int N, int i, int j, int k) {
   const int M = N + 1 - k;

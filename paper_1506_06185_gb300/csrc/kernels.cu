@@ -79,8 +79,8 @@ __device__ __forceinline__ Nb7 nb7(const Slice& s, int i, int j) {
   const int X = slot_prefix(s.M - j);
   const int L = s.M - j;
   const int r0 = s.SL0 + s.SM0 - X;           // row (j, k)
-  const int rjp = r0 + ((L + 3) >> 2);        // row (j + 1, k)
-  const int rjm = r0 - ((L + 4) >> 2);        // row (j - 1, k)
+  const int rjp = r0 + row_slots(L);          // row (j + 1, k)
+  const int rjm = r0 - row_slots(L + 1);      // row (j - 1, k)
   const int rkp = s.SLp + s.SMm - X;          // row (j - 1, k + 1)
   const int rkm = s.SLm + s.SMp - X;          // row (j + 1, k - 1)
   const int c = (i + 2 * j + 3 * s.k) & 3;
@@ -123,13 +123,15 @@ __device__ __forceinline__ void colour_row(int N, int j, int k, int c, int& ic, 
   n = L >= ic ? ((L - ic) >> 2) - mlo + 1 : 0;
 }
 
-// Work items of interior row j: its colour-c nodes (colour kernels) or its
-// slots of four consecutive nodes (all-colour kernels).
-__device__ __forceinline__ int row_items(int N, int j, int k, int c, bool colour) {
+// Work items of interior row j: its colour-c nodes (colour kernels; with
+// vw > 1 its groups of vw consecutive slots holding them, slots vw g .. vw g
+// + vw - 1) or its slots of four consecutive nodes (all-colour kernels).
+__device__ __forceinline__ int row_items(int N, int j, int k, int c, bool colour, int vw = 1) {
   if (colour) {
     int ic, mlo, n;
     colour_row(N, j, k, c, ic, mlo, n);
-    return n;
+    if (vw == 1) return n;
+    return n > 0 ? (mlo + n - 1) / vw + 1 : 0;
   }
   return ((N - 1 - j - k) >> 2) + 1;
 }
@@ -139,7 +141,7 @@ __device__ __forceinline__ int row_items(int N, int j, int k, int c, bool colour
 // items of all its pairs into one range so that every lane has work:
 // s_pre[q] = items of pairs t.j0 .. t.j0 + q - 1 (warp 0 computes it with a
 // warp scan).  Returns the tile's item count.  All threads must call it.
-__device__ __forceinline__ int flat_setup(const Tile& t, int N, int c, bool colour, int* s_pre) {
+__device__ __forceinline__ int flat_setup(const Tile& t, int N, int c, bool colour, int* s_pre, int vw = 1) {
   const int k = t.k, J = N - 2 - k;
   if (threadIdx.y == 0) {
     const int q = threadIdx.x;
@@ -147,8 +149,8 @@ __device__ __forceinline__ int flat_setup(const Tile& t, int N, int c, bool colo
     if (q < t.m0) {
       const int j1 = 1 + t.j0 + q, j2 = J - t.j0 - q;
       if (j1 <= j2) {
-        len = row_items(N, j1, k, c, colour);
-        if (j2 > j1) len += row_items(N, j2, k, c, colour);
+        len = row_items(N, j1, k, c, colour, vw);
+        if (j2 > j1) len += row_items(N, j2, k, c, colour, vw);
       }
     }
     for (int o = 1; o < 32; o <<= 1) {
@@ -162,9 +164,49 @@ __device__ __forceinline__ int flat_setup(const Tile& t, int N, int c, bool colo
   return s_pre[t.m0];
 }
 
+// All slices of a tile at once: s_pre[s] is the pair prefix of slice t.k + s
+// (as flat_setup), s_tot[s] the items of slices t.k .. t.k + s - 1.  One CTA
+// barrier for the whole tile, so that the threads stream through the items
+// of all its slices without waiting for each other.  Returns the tile's item
+// count.  All threads must call it.
+constexpr int MAX_SLABS = 16;
+__device__ __forceinline__ int flat_setup_slabs(const Tile& t, int N, int c, bool colour, int vw,
+                                                int (*s_pre)[33], int* s_tot) {
+  const int J0 = N - 2;
+  for (int sl = threadIdx.y; sl < t.pad; sl += TILE_ROWS) {
+    const int k = t.k + sl, J = J0 - k;
+    const int q = threadIdx.x;
+    int len = 0;
+    if (q < t.m0) {
+      const int j1 = 1 + t.j0 + q, j2 = J - t.j0 - q;
+      if (j1 <= j2) {
+        len = row_items(N, j1, k, c, colour, vw);
+        if (j2 > j1) len += row_items(N, j2, k, c, colour, vw);
+      }
+    }
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, len, o);
+      if (q >= o) len += y;
+    }
+    s_pre[sl][q + 1] = len;
+    if (q == 0) s_pre[sl][0] = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    int acc = 0;
+    for (int sl = 0; sl < t.pad; ++sl) {
+      s_tot[sl] = acc;
+      acc += s_pre[sl][t.m0];
+    }
+    s_tot[t.pad] = acc;
+  }
+  __syncthreads();
+  return s_tot[t.pad];
+}
+
 // Item tt of a flattened tile -> its row j and index v within the row.
 __device__ __forceinline__ void flat_item(const Tile& t, int N, int c, bool colour, const int* s_pre, int tt, int& j,
-                                          int& v) {
+                                          int& v, int vw = 1) {
   int lo = 0, hi = t.m0;
   while (hi - lo > 1) {
     const int mid = (lo + hi) >> 1;
@@ -173,7 +215,7 @@ __device__ __forceinline__ void flat_item(const Tile& t, int N, int c, bool colo
   }
   const int j1 = 1 + t.j0 + lo;
   const int w = tt - s_pre[lo];
-  const int n1 = row_items(N, j1, t.k, c, colour);
+  const int n1 = row_items(N, j1, t.k, c, colour, vw);
   if (w < n1) {
     j = j1;
     v = w;
@@ -183,25 +225,31 @@ __device__ __forceinline__ void flat_item(const Tile& t, int N, int c, bool colo
   }
 }
 
-// Loop over the interior nodes of a tile, slice by slice, four consecutive
-// nodes i = 4m .. 4m + 3 (one per colour array) per item; the body sees i, j,
-// k and the slice constants sc of the iterated level.
-#define HHG_TILE_NODES(NN, RS, t, s_pre, ...)                             \
-  for (int k = (t).k; k < (t).k + (t).pad; ++k) {                         \
-    const Tile ts_{k, (t).j0, (t).m0, 1};                                 \
-    const int total_ = flat_setup(ts_, (NN), 0, false, (s_pre));          \
-    const Slice sc = slice_consts((RS), (NN), k);                         \
-    for (int tt = tid256(); tt < total_; tt += CTA) {                     \
-      int j, m;                                                           \
-      flat_item(ts_, (NN), 0, false, (s_pre), tt, j, m);                  \
-      const int L = (NN) - 1 - j - k;                                     \
-      _Pragma("unroll") for (int qq = 0; qq < 4; ++qq) {                  \
-        const int i = 4 * m + qq;                                         \
-        if (i < 1 || i > L) continue;                                     \
-        __VA_ARGS__                                                       \
-      }                                                                   \
-    }                                                                     \
-    __syncthreads();                                                      \
+// Loop over the interior nodes of a tile, four consecutive nodes
+// i = 4m .. 4m + 3 (one per colour array) per item, the items of all the
+// tile's slices in one range (one CTA barrier per tile); the body sees i, j, k
+// and the slice constants sc of the iterated level.  The kernel declares
+// s_pre2[MAX_SLABS][33] and s_pre_tot[MAX_SLABS + 1] in shared memory.
+#define HHG_TILE_NODES(NN, RS, t, s_pre, ...)                                        \
+  {                                                                                  \
+    const int total_ = flat_setup_slabs((t), (NN), 0, false, 1, s_pre##2, s_pre##_tot); \
+    int sl_ = 0;                                                                     \
+    for (int tt = tid256(); tt < total_; tt += CTA) {                                \
+      while (tt >= s_pre##_tot[sl_ + 1]) ++sl_;                                      \
+      const int k = (t).k + sl_;                                                     \
+      const Tile ts_{k, (t).j0, (t).m0, 1};                                          \
+      int j, m;                                                                      \
+      flat_item(ts_, (NN), 0, false, s_pre##2[sl_], tt - s_pre##_tot[sl_], j, m);    \
+      const Slice sc = slice_consts((RS), (NN), k);                                  \
+      (void)sc;                                                                      \
+      const int L = (NN) - 1 - j - k;                                                \
+      _Pragma("unroll") for (int qq = 0; qq < 4; ++qq) {                             \
+        const int i = 4 * m + qq;                                                    \
+        if (i < 1 || i > L) continue;                                                \
+        __VA_ARGS__                                                                  \
+      }                                                                              \
+    }                                                                                \
+    __syncthreads();                                                                 \
   }
 
 // Work units of a fused launch: units [0, n_if_units) are chunks of 256
@@ -234,7 +282,8 @@ __device__ __forceinline__ void if_stencil(int N, const int* __restrict__ rs, in
     for (int d = 1; d < NDIR; ++d) {
       if (!used_dir(d, S7)) continue;
       const T wd = w[d];
-      if (wd == T(0)) continue;
+      // 15-point: skip the many zero weights; 7-point: no load waits on a weight
+      if (!S7 && wd == T(0)) continue;
       int di, dj, dk;
       dir_ijk(d, di, dj, dk);
       const int ni = cp.i + di, nj = cp.j + dj, nk = cp.k + dk;
@@ -256,8 +305,110 @@ __device__ __forceinline__ void write_copies(int N, const int* __restrict__ rs, 
 // ---------------------------------------------------------------------------
 // Gauss-Seidel, one colour (§2.1 smoother)
 // ---------------------------------------------------------------------------
+// 16-byte vectors of a row: 4 FP32 or 2 FP64 consecutive slots.
+template <class T>
+struct Vec;
+// load() goes through the read-only path: a Gauss-Seidel colour kernel reads
+// only arrays it does not write (the other colours and f).
+template <>
+struct Vec<float> {
+  static constexpr int n = 4;
+  __device__ static void load(const float* p, float* v) {
+    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+  }
+  __device__ static void store(float* p, const float* v) {
+    *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+  }
+};
+template <>
+struct Vec<double> {
+  static constexpr int n = 2;
+  __device__ static void load(const double* p, double* v) {
+    const double2 q = __ldg(reinterpret_cast<const double2*>(p));
+    v[0] = q.x;
+    v[1] = q.y;
+  }
+  __device__ static void store(double* p, const double* v) {
+    *reinterpret_cast<double2*>(p) = make_double2(v[0], v[1]);
+  }
+};
+
+// Slots m0 + s .. m0 + s + VW - 1 (s = +1 when up, -1 when dn, else 0) of a
+// row, from the aligned vector at p = &row[m0] and one extra element.
+template <class T>
+__device__ __forceinline__ void load_shifted(const T* __restrict__ p, bool up, bool dn, T* v) {
+  constexpr int VW = Vec<T>::n;
+  Vec<T>::load(p, v);
+  if (up) {
+    const T e = __ldg(p + VW);
+#pragma unroll
+    for (int t = 0; t < VW - 1; ++t) v[t] = v[t + 1];
+    v[VW - 1] = e;
+  } else if (dn) {
+    const T e = __ldg(p - 1);
+#pragma unroll
+    for (int t = VW - 1; t > 0; --t) v[t] = v[t - 1];
+    v[0] = e;
+  }
+}
+
+// 7-point update of the colour-c nodes in slots m0 .. m0 + VW - 1 of interior
+// row j of slice k (one aligned vector per stencil direction, plus one element
+// where the neighbour's slot is shifted by one); only the interior nodes among
+// them are written.
+template <class T>
+__device__ __forceinline__ void gs_group7(const Slice& sc, int N, int j, int g, int c, T* __restrict__ ub,
+                                          const T* __restrict__ fb, const T* __restrict__ w, T inv) {
+  constexpr int VW = Vec<T>::n;
+  int ic, mlo, n;
+  colour_row(N, j, sc.k, c, ic, mlo, n);
+  const int m0 = g * VW;
+  const int X = slot_prefix(sc.M - j);
+  const int L = sc.M - j;
+  const int r0 = sc.SL0 + sc.SM0 - X;           // row (j, k)
+  const int rjp = r0 + row_slots(L);             // row (j + 1, k)
+  const int rjm = r0 - row_slots(L + 1);         // row (j - 1, k)
+  const int rkp = sc.SLp + sc.SMm - X;           // row (j - 1, k + 1)
+  const int rkm = sc.SLm + sc.SMp - X;           // row (j + 1, k - 1)
+  const int cc = c * sc.CS, cp = ((c + 1) & 3) * sc.CS, cm = ((c + 3) & 3) * sc.CS;
+  const bool e1 = ic == 3, e0 = ic == 0;         // slot of i + 1 is m + e1, of i - 1 is m - e0
+  T acc[VW], a[VW];
+  Vec<T>::load(fb + cc + r0 + m0, acc);
+  load_shifted(ub + cp + r0 + m0, e1, false, a);    // ( 1,  0,  0)
+#pragma unroll
+  for (int t = 0; t < VW; ++t) acc[t] -= w[1] * a[t];
+  load_shifted(ub + cp + rjp + m0, false, e0, a);   // (-1,  1,  0)
+#pragma unroll
+  for (int t = 0; t < VW; ++t) acc[t] -= w[2] * a[t];
+  Vec<T>::load(ub + cp + rkp + m0, a);              // ( 0, -1,  1)
+#pragma unroll
+  for (int t = 0; t < VW; ++t) acc[t] -= w[3] * a[t];
+  load_shifted(ub + cm + r0 + m0, false, e0, a);    // (-1,  0,  0)
+#pragma unroll
+  for (int t = 0; t < VW; ++t) acc[t] -= w[8] * a[t];
+  load_shifted(ub + cm + rjm + m0, e1, false, a);   // ( 1, -1,  0)
+#pragma unroll
+  for (int t = 0; t < VW; ++t) acc[t] -= w[9] * a[t];
+  Vec<T>::load(ub + cm + rkm + m0, a);              // ( 0,  1, -1)
+#pragma unroll
+  for (int t = 0; t < VW; ++t) acc[t] = (acc[t] - w[10] * a[t]) * inv;
+  T* out = ub + cc + r0 + m0;
+  const int lo = max(mlo - m0, 0), hi = min(mlo + n - m0, VW);
+  if (lo == 0 && hi == VW) {
+    Vec<T>::store(out, acc);
+  } else {
+#pragma unroll
+    for (int t = 0; t < VW; ++t)
+      if (t >= lo && t < hi) out[t] = acc[t];
+  }
+}
+
 template <class T, bool S7>
-__global__ void __launch_bounds__(CTA, sizeof(T) == 8 ? 6 : 5) k_gs(int N, const int* __restrict__ rs, int64_t block, T* __restrict__ u, T* __restrict__ uI,
+__global__ void __launch_bounds__(CTA, 5) k_gs(int N, const int* __restrict__ rs, int64_t block, T* __restrict__ u, T* __restrict__ uI,
                                             const T* __restrict__ f, const T* __restrict__ fI,
                                             const T* __restrict__ W, const T* __restrict__ Winv,
                                             const Tile* __restrict__ tiles, int n_tiles, const int* __restrict__ act,
@@ -265,6 +416,8 @@ __global__ void __launch_bounds__(CTA, sizeof(T) == 8 ? 6 : 5) k_gs(int N, const
                                             const Copy* __restrict__ cps, const int* __restrict__ list, int n_list,
                                             int n_if_units) {
   __shared__ int s_pre[33];
+  __shared__ int s_pre2[MAX_SLABS][33];
+  __shared__ int s_pre_tot[MAX_SLABS + 1];
   HHG_UNITS(n_if_units, n_tiles, n_act) {
     if (unit < n_if_units) {
       const int q = unit * CTA + tid256();
@@ -286,36 +439,40 @@ __global__ void __launch_bounds__(CTA, sizeof(T) == 8 ? 6 : 5) k_gs(int N, const
     const T* fb = f + (size_t)macro * block;
     const T* w = W + (size_t)macro * 16 * NDIR;
     const T inv = Winv[macro];
+    if (S7) {
+      // groups of VW consecutive same-colour slots per thread
+      constexpr int VW = Vec<T>::n;
+      const T wr[11] = {T(0), w[1], w[2], w[3], T(0), T(0), T(0), T(0), w[8], w[9], w[10]};
+      const int total = flat_setup_slabs(t, N, colour, true, VW, s_pre2, s_pre_tot);
+      int sl = 0;
+      for (int tt = tid256(); tt < total; tt += CTA) {
+        while (tt >= s_pre_tot[sl + 1]) ++sl;    // items only grow: the slice only advances
+        const int k = t.k + sl;
+        const Tile ts{k, t.j0, t.m0, 1};
+        int j, g;
+        flat_item(ts, N, colour, true, s_pre2[sl], tt - s_pre_tot[sl], j, g, VW);
+        gs_group7<T>(slice_consts(rs, N, k), N, j, g, colour, ub, fb, wr, inv);
+      }
+      __syncthreads();
+      continue;
+    }
     for (int k = t.k; k < t.k + t.pad; ++k) {
     const Tile ts{k, t.j0, t.m0, 1};
     const int total = flat_setup(ts, N, colour, true, s_pre);
-    const Slice sc = slice_consts(rs, N, k);
     for (int tt = tid256(); tt < total; tt += CTA) {
       int j, v, ic, mlo, n;
       flat_item(ts, N, colour, true, s_pre, tt, j, v);
       colour_row(N, j, k, colour, ic, mlo, n);
       const int i = 4 * (mlo + v) + ic;
-      if (S7) {
-        const Nb7 q = nb7(sc, i, j);
-        T acc = fb[q.me];
-        acc -= w[1] * ub[q.nb1];
-        acc -= w[2] * ub[q.nb2];
-        acc -= w[3] * ub[q.nb3];
-        acc -= w[8] * ub[q.nb8];
-        acc -= w[9] * ub[q.nb9];
-        acc -= w[10] * ub[q.nb10];
-        ub[q.me] = acc * inv;
-      } else {
-        const int me = lidx32(rs, N, i, j, k);
-        T acc = fb[me];
+      const int me = lidx32(rs, N, i, j, k);
+      T acc = fb[me];
 #pragma unroll
-        for (int d = 1; d < NDIR; ++d) {
-          int di, dj, dk;
-          dir_ijk(d, di, dj, dk);
-          acc -= w[d] * ub[lidx32(rs, N, i + di, j + dj, k + dk)];
-        }
-        ub[me] = acc * inv;
+      for (int d = 1; d < NDIR; ++d) {
+        int di, dj, dk;
+        dir_ijk(d, di, dj, dk);
+        acc -= w[d] * ub[lidx32(rs, N, i + di, j + dj, k + dk)];
       }
+      ub[me] = acc * inv;
     }
     __syncthreads();
     }
@@ -336,6 +493,8 @@ __global__ void __launch_bounds__(CTA, sizeof(T) == 8 ? 6 : 5) k_res(int N, cons
                                              const int64_t* __restrict__ zero_off, int n_zero, int n_if_units,
                                              double* __restrict__ partial) {
   __shared__ int s_pre[33];
+  __shared__ int s_pre2[MAX_SLABS][33];
+  __shared__ int s_pre_tot[MAX_SLABS + 1];
   __shared__ double sh[32];
   double ss = 0.0;
   HHG_UNITS(n_if_units, n_tiles, n_act) {
@@ -407,6 +566,8 @@ __global__ void __launch_bounds__(CTA) k_restrict(int Nc, const int* __restrict_
                                                   const int64_t* __restrict__ gather,
                                                   const int64_t* __restrict__ zero_off, int n_zero, int n_if_units) {
   __shared__ int s_pre[33];
+  __shared__ int s_pre2[MAX_SLABS][33];
+  __shared__ int s_pre_tot[MAX_SLABS + 1];
   HHG_UNITS(n_if_units, n_tiles, n_act) {
     if (unit < n_if_units) {
       const int q = unit * CTA + tid256();
@@ -480,6 +641,8 @@ __global__ void __launch_bounds__(CTA) k_prolong(int Nf, const int* __restrict__
                                                  const Copy* __restrict__ cps, const int* __restrict__ list,
                                                  int n_list, int n_if_units) {
   __shared__ int s_pre[33];
+  __shared__ int s_pre2[MAX_SLABS][33];
+  __shared__ int s_pre_tot[MAX_SLABS + 1];
   HHG_UNITS(n_if_units, n_tiles, n_act) {
     if (unit < n_if_units) {
       const int q = unit * CTA + tid256();
@@ -517,6 +680,8 @@ __global__ void __launch_bounds__(CTA) k_res_f32(int N, const int* __restrict__ 
                                                  const int* __restrict__ list, int n_list, int n_if_units,
                                                  double* __restrict__ partial) {
   __shared__ int s_pre[33];
+  __shared__ int s_pre2[MAX_SLABS][33];
+  __shared__ int s_pre_tot[MAX_SLABS + 1];
   __shared__ double sh[32];
   double ss = 0.0;
   HHG_UNITS(n_if_units, n_tiles, n_act) {
@@ -577,6 +742,8 @@ __global__ void __launch_bounds__(CTA) k_add_corr(int N, const int* __restrict__
                                                   const int* __restrict__ cptr, const Copy* __restrict__ cps,
                                                   const int* __restrict__ list, int n_list, int n_if_units) {
   __shared__ int s_pre[33];
+  __shared__ int s_pre2[MAX_SLABS][33];
+  __shared__ int s_pre_tot[MAX_SLABS + 1];
   HHG_UNITS(n_if_units, n_tiles, n_act) {
     if (unit < n_if_units) {
       const int q = unit * CTA + tid256();
