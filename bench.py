@@ -490,6 +490,66 @@ def run_precision(args):
     return 0
 
 
+def run_kappa(args):
+    """Cycle advantage kappa (Eq. (3)) of LR, DD and DN recovery on the three
+    fault scenarios of §4.4 refined 7 times, superman factors 2 and 5, n_I =
+    0..4 (fault after 5 cycles) and 0..6 (after 11), FP64, next to the values
+    printed in Tab. 1 and 2 (k_faulty = global cycles + n_I)."""
+    import numpy as np
+    import torch
+
+    import hhg_inputs as I
+    from paper_1506_06185_gb300 import build
+    from paper_1506_06185_gb300 import hhg
+
+    build()
+    torch.cuda.set_device(0)
+    paper = np.loadtxt(os.path.join(ROOT, "tests", "golden", "tab12_kappa.txt"))
+    R, rtol = 7, 1e-12
+    recs = [("LR", hhg.HHG_RECOVERY_LR), ("DD", hhg.HHG_RECOVERY_DD), ("DN", hhg.HHG_RECOVERY_DN)]
+    table, diffs = [], []
+    t0 = time.perf_counter()
+    for si, (name, sub, ids) in enumerate(I.kappa_scenarios()):
+        M = hhg.Mesh(sub, R)
+        f = torch.from_numpy(I.random_load(sub, R, SEED)).cuda()
+        u0 = torch.zeros_like(f)
+        M.set_problem(f, u0)
+        _, k_free, _ = M.solve(rtol=rtol, max_cycles=80)
+        for k_F, n_max in ((5, 4), (11, 6)):
+            for eta in (2.0, 5.0):
+                for n_I in range(n_max + 1):
+                    row = {"scenario": name, "k_F": k_F, "eta": eta, "n_I": n_I, "k_free": k_free}
+                    for ri, (rname, rec) in enumerate(recs):
+                        n_F = int(math.ceil(eta * n_I))
+                        kw = dict(rtol=rtol, max_cycles=80, fault_cycle=k_F, fault_ids=ids, recovery=rec)
+                        if rec == hhg.HHG_RECOVERY_LR:
+                            kw["n_local"] = n_F
+                        else:
+                            kw.update(n_global=n_I, eta=eta)
+                        M.set_problem(None, u0)
+                        _, cyc, _ = M.solve(**kw)
+                        kap = (cyc + n_I - k_free) / k_F
+                        row[rname] = round(kap, 4)
+                        hit = paper[(paper[:, 0] == k_F) & (paper[:, 1] == eta) & (paper[:, 2] == n_I)]
+                        if len(hit):
+                            ref = float(hit[0, 3 + 3 * si + ri])
+                            row[rname + "_paper"] = ref
+                            diffs.append(round((kap - ref) * k_F))
+                    table.append(row)
+        M.close()
+    d = np.array(diffs)
+    line = {"metric": "cycle advantage kappa of LR / DD / DN recovery (Eq. 3), scenarios I-III of the study",
+            "impl": "ours", "n_gpus": 1, "data": "synthetic", "dtype": "f64",
+            "config": {"workload": "cube meshes 1x1x1, 2x2x2, 3x3x3 sub-cubes x 6 macros refined 7 levels, random "
+                                   "load seed 0, V(3,3), rtol 1e-12, faults after 5 and 11 cycles", "rtol": rtol},
+            "cells_compared": int(d.size), "cycles_diff_vs_paper": {"exact": int((d == 0).sum()),
+                                                                   "within_1": int((abs(d) <= 1).sum()),
+                                                                   "mean": float(d.mean()), "max_abs": int(abs(d).max())},
+            "seconds": time.perf_counter() - t0, "table": table}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -499,6 +559,8 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the variant timings")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--batch", action="store_true", help="run the batched-recovery workload instead")
+    ap.add_argument("--kappa", action="store_true",
+                    help="run the cycle-advantage study of the recovery strategies instead")
     ap.add_argument("--precision", action="store_true",
                     help="run FP64 against mixed precision on the cube refined 9 levels instead")
     args = ap.parse_args()
@@ -510,6 +572,8 @@ def main():
         return run_batch(args)
     if args.precision:
         return run_precision(args)
+    if args.kappa:
+        return run_kappa(args)
     return run_ours(args)
 
 

@@ -149,3 +149,37 @@ def batch_problems(count, seed=3, max_size=27, levels=(5, 6, 7)):
                 break
         out.append((sub, r, grow_fault_set(sub, size, seed * 1000 + q)))
     return out
+
+
+def boundary_contact(sub, macro):
+    """(faces, edges) of a macro-tetrahedron that lie on the boundary of the
+    unit cube (pure geometry of the macro mesh)."""
+    import itertools
+    V = macro_vertices(sub)[int(macro)]
+    ext = [int(s) for s in sub]
+
+    def on_bnd(pts):
+        for a in range(3):
+            if all(p[a] == 0 for p in pts) or all(p[a] == ext[a] for p in pts):
+                return True
+        return False
+    faces = sum(on_bnd(c) for c in itertools.combinations(V, 3))
+    edges = sum(on_bnd(c) for c in itertools.combinations(V, 2))
+    return faces, edges
+
+
+def kappa_scenarios():
+    """The three fault scenarios of the cycle-advantage study (§4.4): (name,
+    sub-cubes, faulty macro ids).  I: 1x1x1 cube, a tetrahedron with two faces
+    on the boundary; II: 2x2x2, the first tetrahedron touching the boundary
+    along an edge only; III: 3x3x3, a tetrahedron of the centre sub-cube (no
+    boundary contact)."""
+    out = [("I", (1, 1, 1), [0])]
+    sub = (2, 2, 2)
+    for t in range(6 * 8):
+        f, e = boundary_contact(sub, t)
+        if f == 0 and e > 0:
+            out.append(("II", sub, [t]))
+            break
+    out.append(("III", (3, 3, 3), subcube_macros((3, 3, 3), 1, 1, 1)[:1]))
+    return out

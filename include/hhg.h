@@ -148,6 +148,15 @@ int hhg_recover_local(hhg_mesh* mesh, const int* macro_ids, int n_ids, int n_loc
 int hhg_recover_dn(hhg_mesh* mesh, const int* macro_ids, int n_ids, int n_global, double eta,
                    int* n_local_run, double* seconds_local, double* seconds_global, void* stream);
 
+/* A fault of a multi-fault run (§5: a second fault at another location after
+ * the first recovery): after global cycle `cycle` the macros macro_ids[0..
+ * n_ids) are lost. */
+typedef struct {
+  int cycle;
+  const int* macro_ids;   /* host */
+  int n_ids;
+} hhg_fault;
+
 typedef struct {
   double rtol;            /* stop when ||r_k|| <= rtol ||r_0|| (r_0 of the
                              initial iterate) */
@@ -167,13 +176,19 @@ typedef struct {
                              (needs a precision-32 mesh) */
   double coarse_rtol;     /* coarse CG relative tolerance (0 = 1e-12) */
   int coarse_maxit;       /* coarse CG iteration cap (0 = 1000) */
+  const hhg_fault* faults;  /* further faults (host, may be NULL), each handled
+                               like the first with the same recovery */
+  int n_faults;
 } hhg_solve_opts;
 
 /* Iterate global V-cycles from the current iterate until rtol or
- * max_cycles, injecting the fault and running the recovery of opts.
- * hist (host, at least max_cycles + 2 doubles, may be NULL) receives the
- * relative residuals: hist[0] = 1, one entry per global cycle and, for a
- * faulty run, one extra entry right after the fault and its recovery.
+ * max_cycles, injecting the faults and running the recovery of opts after
+ * each (faults of the same cycle in list order, the one of fault_cycle
+ * first).
+ * hist (host, at least max_cycles + 1 + number of faults doubles, may be
+ * NULL) receives the
+ * relative residuals: hist[0] = 1, one entry per global cycle and one extra
+ * entry right after each fault and its recovery.
  * *n_hist receives the entries written, *cycles the global V-cycles run.
  * Returns HHG_ERR_NOT_CONVERGED (after writing the outputs) if rtol was not
  * reached. */

@@ -513,7 +513,7 @@ def inject_fault(mesh, u, ids):
 
 def solve(mesh, u, f, rtol=1e-8, max_cycles=50, pre=3, post=3, fault_cycle=-1,
           fault_ids=(), recovery=NONE, n_local=0, n_global=0, eta=1.0,
-          cg_rtol=1e-12, cg_maxit=1000, record=False):
+          cg_rtol=1e-12, cg_maxit=1000, record=False, faults=()):
     """V-cycle iteration to a relative residual ``rtol`` with an optional fault.
 
     The fault strikes after global cycle ``fault_cycle`` (§2.2).  Recovery:
@@ -524,10 +524,16 @@ def solve(mesh, u, f, rtol=1e-8, max_cycles=50, pre=3, post=3, fault_cycle=-1,
     ``n_local`` if positive, else ceil(eta * n_I) (§4.4).  DN = Algorithm 2
     (see ``dn_recover``).
 
+    ``faults`` lists further faults as (cycle, macro ids) pairs, handled the
+    same way in cycle order (§5: a second fault at another location after
+    the first recovery has finished).
+
     History: ``hist[0] = 1``, one entry per global cycle, and for a faulty run
-    one extra entry right after the fault (and recovery).  ``k_faulty`` counts
-    global cycles plus n_I for DD (§4.4).
+    one extra entry right after each fault (and recovery).  ``k_faulty``
+    counts global cycles plus n_I for DD and DN per fault (§4.4).
     """
+    events = ([(int(fault_cycle), list(fault_ids))] if fault_cycle > 0 else [])
+    events += [(int(c), list(ids)) for c, ids in faults]
     prob = mesh.global_problem
     top = len(mesh.levels) - 1
     r0 = resnorm(mesh, u, f)
@@ -543,21 +549,23 @@ def solve(mesh, u, f, rtol=1e-8, max_cycles=50, pre=3, post=3, fault_cycle=-1,
         hist.append(rel)
         if record:
             iterates.append(u.copy())
-        if k == fault_cycle:
-            inject_fault(mesh, u, fault_ids)
+        for fc, ids in events:
+            if k != fc:
+                continue
+            inject_fault(mesh, u, ids)
             if recovery == DN:
-                n_F = dn_recover(mesh, u, f, fault_ids, n_global, eta, pre, post, cg_rtol, cg_maxit)
-                extra = n_global
+                n_F = dn_recover(mesh, u, f, ids, n_global, eta, pre, post, cg_rtol, cg_maxit)
+                extra += n_global
             elif recovery in (LR, DD):
                 n_F = n_local if n_local > 0 else int(math.ceil(eta * n_global))
-                lp = mesh.local_problem(fault_ids)
+                lp = mesh.local_problem(ids)
                 for _ in range(n_F):
                     vcycle(mesh, lp, top, u, f, pre, post, cg_rtol, cg_maxit)
                 if recovery == DD:
-                    hp = mesh.healthy_problem(fault_ids)
+                    hp = mesh.healthy_problem(ids)
                     for _ in range(n_global):
                         vcycle(mesh, hp, top, u, f, pre, post, cg_rtol, cg_maxit)
-                    extra = n_global
+                    extra += n_global
             rel = resnorm(mesh, u, f) / r0
             hist.append(rel)
             if record:

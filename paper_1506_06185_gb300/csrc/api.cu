@@ -1178,18 +1178,33 @@ int hhg_solve(hhg_mesh* m, const hhg_solve_opts* o, double* hist, int* n_hist, i
   const int pre = o->pre > 0 ? o->pre : 3, post = o->post > 0 ? o->post : 3;
   const double cg_rtol = o->coarse_rtol > 0 ? o->coarse_rtol : 1e-12;
   const int cg_maxit = o->coarse_maxit > 0 ? o->coarse_maxit : 1000;
-  const bool faulty = o->fault_cycle > 0;
-  if (faulty) {
+  // fault events: (cycle, id set) in the order they are handled
+  struct Event {
+    int cycle;
     std::vector<unsigned char> set;
-    HHG_TRY(check_ids(m, o->fault_ids, o->n_fault_ids, set));
+  };
+  std::vector<Event> events;
+  if (o->n_faults < 0 || (o->n_faults > 0 && !o->faults)) return fail(HHG_ERR_ARG, "invalid fault list");
+  for (int q = -1; q < o->n_faults; ++q) {
+    const int cyc = q < 0 ? o->fault_cycle : o->faults[q].cycle;
+    if (cyc <= 0) {
+      if (q < 0) continue;
+      return fail(HHG_ERR_ARG, "fault cycle must be positive");
+    }
+    Event ev;
+    ev.cycle = cyc;
+    if (q < 0) HHG_TRY(check_ids(m, o->fault_ids, o->n_fault_ids, ev.set));
+    else HHG_TRY(check_ids(m, o->faults[q].macro_ids, o->faults[q].n_ids, ev.set));
+    events.push_back(std::move(ev));
+  }
+  if (!events.empty()) {
     if (o->recovery < HHG_RECOVERY_NONE || o->recovery > HHG_RECOVERY_DN)
       return fail(HHG_ERR_ARG, "unknown recovery strategy");
-    if (o->recovery == HHG_RECOVERY_DN) {
-      if (o->n_global < 0 || !(o->eta >= 0.0)) return fail(HHG_ERR_ARG, "invalid n_global / eta");
-      HHG_TRY(setup_dn(m, set));
-    } else {
-      HHG_TRY(setup_fault(m, set));
-    }
+    if (o->recovery == HHG_RECOVERY_DN && (o->n_global < 0 || !(o->eta >= 0.0)))
+      return fail(HHG_ERR_ARG, "invalid n_global / eta");
+    // the first fault's sub-problems are built before the timed iteration
+    if (o->recovery == HHG_RECOVERY_DN) HHG_TRY(setup_dn(m, events[0].set));
+    else HHG_TRY(setup_fault(m, events[0].set));
   }
   cudaStream_t s = (cudaStream_t)stream;
   int nh = 0;
@@ -1228,7 +1243,10 @@ int hhg_solve(hhg_mesh* m, const hhg_solve_opts* o, double* hist, int* n_hist, i
     ++k;
     rel = r0 > 0 ? std::sqrt(v) / r0 : 0.0;
     push(rel);
-    if (faulty && k == o->fault_cycle) {
+    for (const Event& ev : events) {
+      if (ev.cycle != k) continue;
+      if (o->recovery == HHG_RECOVERY_DN) HHG_TRY(setup_dn(m, ev.set));
+      else HHG_TRY(setup_fault(m, ev.set));
       HHG_TRY(inject(m, s));
       if (o->recovery == HHG_RECOVERY_DN) {
         HHG_TRY(recover_dn(m, o->n_global, o->eta, mixed, pre, post, cg_rtol, cg_maxit, nullptr, nullptr, nullptr, s));

@@ -35,11 +35,16 @@ class hhg_mesh_desc(C.Structure):
                 ("coeff", C.POINTER(C.c_double)), ("affine", C.POINTER(C.c_double))]
 
 
+class hhg_fault(C.Structure):
+    _fields_ = [("cycle", C.c_int), ("macro_ids", C.POINTER(C.c_int)), ("n_ids", C.c_int)]
+
+
 class hhg_solve_opts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("max_cycles", C.c_int), ("pre", C.c_int), ("post", C.c_int),
                 ("fault_cycle", C.c_int), ("fault_ids", C.POINTER(C.c_int)), ("n_fault_ids", C.c_int),
                 ("recovery", C.c_int), ("n_local", C.c_int), ("n_global", C.c_int), ("eta", C.c_double),
-                ("mixed_precision", C.c_int), ("coarse_rtol", C.c_double), ("coarse_maxit", C.c_int)]
+                ("mixed_precision", C.c_int), ("coarse_rtol", C.c_double), ("coarse_maxit", C.c_int),
+                ("faults", C.POINTER(hhg_fault)), ("n_faults", C.c_int)]
 
 
 class HHGError(RuntimeError):
@@ -232,7 +237,8 @@ def hhg_recover_dn(h, ids, n_global, eta, timed=False, stream=None):
 
 def hhg_solve(h, rtol=1e-8, max_cycles=50, pre=3, post=3, fault_cycle=0, fault_ids=(), recovery=0, n_local=0,
               n_global=0, eta=1.0, mixed_precision=False, coarse_rtol=0.0, coarse_maxit=0, stream=None,
-              allow_not_converged=False):
+              allow_not_converged=False, faults=()):
+    """``faults``: further (cycle, macro ids) faults, recovered like the first."""
     o = hhg_solve_opts()
     o.rtol, o.max_cycles, o.pre, o.post = float(rtol), int(max_cycles), int(pre), int(post)
     ids, n = _ids(fault_ids) if len(fault_ids) else (None, 0)
@@ -242,7 +248,15 @@ def hhg_solve(h, rtol=1e-8, max_cycles=50, pre=3, post=3, fault_cycle=0, fault_i
     o.recovery, o.n_local, o.n_global, o.eta = int(recovery), int(n_local), int(n_global), float(eta)
     o.mixed_precision = 1 if mixed_precision else 0
     o.coarse_rtol, o.coarse_maxit = float(coarse_rtol), int(coarse_maxit)
-    hist = (C.c_double * (int(max_cycles) + 2))()
+    keep = []
+    if len(faults):
+        arr = (hhg_fault * len(faults))()
+        for q, (cyc_q, ids_q) in enumerate(faults):
+            a, n_q = _ids(ids_q)
+            keep.append(a)
+            arr[q].cycle, arr[q].macro_ids, arr[q].n_ids = int(cyc_q), a, n_q
+        o.faults, o.n_faults = arr, len(faults)
+    hist = (C.c_double * (int(max_cycles) + 2 + len(faults)))()
     nh, cyc = C.c_int(), C.c_int()
     rc = lib().hhg_solve(h, C.byref(o), hist, C.byref(nh), C.byref(cyc), _stream(stream))
     _check(rc, allow=(HHG_ERR_NOT_CONVERGED,) if allow_not_converged else ())

@@ -128,3 +128,26 @@ def test_mixed_precision_dn(hhg):
     assert abs(hist[k] / ref["hist"][k] - 1.0) < 0.05, (hist[k], ref["hist"][k])
     assert _rel(M.get_solution(), O.interior(uo)) <= 1e-8
     M.close()
+
+
+@pytest.mark.parametrize("recovery", [2, 3])
+def test_two_faults_match_oracle(hhg, recovery):
+    """A second fault at another location after the first recovery (§5),
+    DD and DN: same cycle count, residual history and iterate as the oracle."""
+    sub, R = (2, 2, 2), 5
+    f = I.random_load(sub, R, seed=8)
+    kw = dict(rtol=1e-10, max_cycles=40, fault_cycle=3, fault_ids=[13], recovery=recovery, n_global=2, eta=2.0,
+              faults=[(6, I.subcube_macros(sub, 1, 1, 1))])
+    M = hhg.Mesh(sub, R)
+    M.set_problem(f, I.initial_guess(sub, R))
+    hist, cyc, _ = M.solve(**kw)
+    m = O.Mesh(sub, R)
+    uo = O.pad(I.initial_guess(sub, R))
+    ref = O.solve(m, uo, O.pad(f), **kw)
+    assert cyc == ref["cycles"] and len(hist) == len(ref["hist"]) == cyc + 3
+    assert np.abs(hist - ref["hist"]).max() <= ATOL_HIST
+    assert _rel(M.get_solution(), O.interior(uo)) <= RTOL_U
+    with pytest.raises(hhg.HHGError) as e:
+        M.solve(rtol=1e-10, max_cycles=5, faults=[(0, [1])])
+    assert e.value.code == hhg.HHG_ERR_ARG
+    M.close()

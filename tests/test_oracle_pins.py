@@ -434,3 +434,27 @@ def test_dn_beats_do_nothing():
     r = _run(m, f, 1e-10, fault_cycle=5, fault_ids=ids, recovery=O.DN, n_global=2, eta=4.0)
     assert r["n_F"] == 8
     assert O.kappa(r["k_faulty"], free, 5) < O.kappa(dn, free, 5)
+
+
+def test_two_faults_equal_the_sequence_of_single_fault_steps():
+    """A second fault after the first recovery (§5): the listed faults give the
+    iterate of running cycles, fault, recovery, cycles, fault, recovery by
+    hand."""
+    sub, R = (2, 2, 2), 4
+    m = O.Mesh(sub, R)
+    f = O.pad(I.random_load(sub, R, seed=6))
+    u = O.pad(I.initial_guess(sub, R))
+    r = O.solve(m, u, f, rtol=1e-30, max_cycles=8, fault_cycle=3, fault_ids=[13], recovery=O.DD, n_global=1,
+                eta=2.0, faults=[(6, [40, 41])])
+    assert len(r["hist"]) == 8 + 1 + 2 and r["k_faulty"] == 8 + 2
+    v = O.pad(I.initial_guess(sub, R))
+    top = len(m.levels) - 1
+    for k in range(1, 9):
+        O.vcycle(m, m.global_problem, top, v, f)
+        if k in (3, 6):
+            ids = [13] if k == 3 else [40, 41]
+            O.inject_fault(m, v, ids)
+            for _ in range(2):
+                O.vcycle(m, m.local_problem(ids), top, v, f)
+            O.vcycle(m, m.healthy_problem(ids), top, v, f)
+    assert np.abs(O.interior(v) - O.interior(u)).max() == 0.0
