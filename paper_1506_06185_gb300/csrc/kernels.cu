@@ -253,18 +253,26 @@ __device__ __forceinline__ void flat_item(const Tile& t, int N, int c, bool colo
   }
 
 // Work units of a fused launch: units [0, n_if_units) are chunks of 256
-// interface list entries, the rest are (tile, active macro) pairs.  CTAs walk
-// the units with a grid stride, so a launch has a few CTAs per SM whatever the
-// level size.
+// interface list entries, the rest (tile, active macro) pairs.  CTAs walk the
+// units with a grid stride, so a launch has a few CTAs per SM whatever the
+// level size.  (Spreading the interface chunks among the volume units was
+// measured slower.)
 #define HHG_UNITS(n_if_units, n_tiles, n_act)                                                     \
   for (int unit = blockIdx.x, n_units_ = (n_if_units) + (n_tiles) * (n_act); unit < n_units_;     \
        unit += gridDim.x)
 
-__device__ __forceinline__ void vol_unit(int unit, int n_if_units, int n_tiles, const Tile* __restrict__ tiles,
+// Interface chunk at position u of the walk (-1: a volume unit).
+__device__ __forceinline__ int if_chunk(int u, int n_if_units) { return u < n_if_units ? u : -1; }
+// Index of the volume unit at position u (not an interface chunk).
+__device__ __forceinline__ int vol_index(int u, int n_if_units) { return u - n_if_units; }
+
+// Volume unit -> (tile, macro).  The macro index runs fastest and the tile
+// lists are sorted by decreasing work, so the last units of a grid-stride walk
+// are the smallest tiles of all macros (a short tail).
+__device__ __forceinline__ void vol_unit(int b, int n_act, const Tile* __restrict__ tiles,
                                          const int* __restrict__ act, Tile& t, int& macro) {
-  const int b = unit - n_if_units;
-  t = tiles[b % n_tiles];
-  macro = act[b / n_tiles];
+  t = tiles[b / n_act];
+  macro = act[b % n_act];
 }
 
 // Off-diagonal part of an interface node's stencil applied to u, and the sum
@@ -419,8 +427,8 @@ __global__ void __launch_bounds__(CTA, 5) k_gs(int N, const int* __restrict__ rs
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
   HHG_UNITS(n_if_units, n_tiles, n_act) {
-    if (unit < n_if_units) {
-      const int q = unit * CTA + tid256();
+    if (const int ic_ = if_chunk(unit, n_if_units); ic_ >= 0) {
+      const int q = ic_ * CTA + tid256();
       if (q < n_list) {
         const int node = list[q];
         const int c0 = cptr[node], c1 = cptr[node + 1];
@@ -434,7 +442,7 @@ __global__ void __launch_bounds__(CTA, 5) k_gs(int N, const int* __restrict__ rs
     }
     Tile t;
     int macro;
-    vol_unit(unit, n_if_units, n_tiles, tiles, act, t, macro);
+    vol_unit(vol_index(unit, n_if_units), n_act, tiles, act, t, macro);
     T* ub = u + (size_t)macro * block;
     const T* fb = f + (size_t)macro * block;
     const T* w = W + (size_t)macro * 16 * NDIR;
@@ -498,8 +506,8 @@ __global__ void __launch_bounds__(CTA, sizeof(T) == 8 ? 6 : 5) k_res(int N, cons
   __shared__ double sh[32];
   double ss = 0.0;
   HHG_UNITS(n_if_units, n_tiles, n_act) {
-    if (unit < n_if_units) {
-      const int q = unit * CTA + tid256();
+    if (const int ic_ = if_chunk(unit, n_if_units); ic_ >= 0) {
+      const int q = ic_ * CTA + tid256();
       if (q < n_list) {
         const int node = list[q];
         const int c0 = cptr[node], c1 = cptr[node + 1];
@@ -515,7 +523,7 @@ __global__ void __launch_bounds__(CTA, sizeof(T) == 8 ? 6 : 5) k_res(int N, cons
     }
     Tile t;
     int macro;
-    vol_unit(unit, n_if_units, n_tiles, tiles, act, t, macro);
+    vol_unit(vol_index(unit, n_if_units), n_act, tiles, act, t, macro);
     const T* ub = u + (size_t)macro * block;
     const T* fb = f + (size_t)macro * block;
     T* rb = r + (size_t)macro * block;
@@ -569,8 +577,8 @@ __global__ void __launch_bounds__(CTA) k_restrict(int Nc, const int* __restrict_
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
   HHG_UNITS(n_if_units, n_tiles, n_act) {
-    if (unit < n_if_units) {
-      const int q = unit * CTA + tid256();
+    if (const int ic_ = if_chunk(unit, n_if_units); ic_ >= 0) {
+      const int q = ic_ * CTA + tid256();
       if (q < n_list) {
         const int node = list[q];
         const int64_t* g = gather + (size_t)q * NDIR;
@@ -589,7 +597,7 @@ __global__ void __launch_bounds__(CTA) k_restrict(int Nc, const int* __restrict_
     }
     Tile t;
     int macro;
-    vol_unit(unit, n_if_units, n_tiles, tiles, act, t, macro);
+    vol_unit(vol_index(unit, n_if_units), n_act, tiles, act, t, macro);
     const T* rb = rf + (size_t)macro * bf;
     T* fb = fc + (size_t)macro * bc;
     T* ub = uc + (size_t)macro * bc;
@@ -644,8 +652,8 @@ __global__ void __launch_bounds__(CTA) k_prolong(int Nf, const int* __restrict__
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
   HHG_UNITS(n_if_units, n_tiles, n_act) {
-    if (unit < n_if_units) {
-      const int q = unit * CTA + tid256();
+    if (const int ic_ = if_chunk(unit, n_if_units); ic_ >= 0) {
+      const int q = ic_ * CTA + tid256();
       if (q < n_list) {
         const int node = list[q];
         const int c0 = cptr[node], c1 = cptr[node + 1];
@@ -658,7 +666,7 @@ __global__ void __launch_bounds__(CTA) k_prolong(int Nf, const int* __restrict__
     }
     Tile t;
     int macro;
-    vol_unit(unit, n_if_units, n_tiles, tiles, act, t, macro);
+    vol_unit(vol_index(unit, n_if_units), n_act, tiles, act, t, macro);
     T* fb = uf + (size_t)macro * bf;
     const T* cb = uc + (size_t)macro * bc;
     HHG_TILE_NODES(Nf, rsf, t, s_pre, { fb[lidx32(rsf, Nf, i, j, k)] += interp(cb, Nc, rsc, i, j, k); })
@@ -685,8 +693,8 @@ __global__ void __launch_bounds__(CTA) k_res_f32(int N, const int* __restrict__ 
   __shared__ double sh[32];
   double ss = 0.0;
   HHG_UNITS(n_if_units, n_tiles, n_act) {
-    if (unit < n_if_units) {
-      const int q = unit * CTA + tid256();
+    if (const int ic_ = if_chunk(unit, n_if_units); ic_ >= 0) {
+      const int q = ic_ * CTA + tid256();
       if (q < n_list) {
         const int node = list[q];
         double off = 0.0, diag = 0.0;
@@ -699,7 +707,7 @@ __global__ void __launch_bounds__(CTA) k_res_f32(int N, const int* __restrict__ 
     }
     Tile t;
     int macro;
-    vol_unit(unit, n_if_units, n_tiles, tiles, act, t, macro);
+    vol_unit(vol_index(unit, n_if_units), n_act, tiles, act, t, macro);
     const double* ub = u + (size_t)macro * block;
     const double* fb = f + (size_t)macro * block;
     float* ob = f32 + (size_t)macro * block;
@@ -745,8 +753,8 @@ __global__ void __launch_bounds__(CTA) k_add_corr(int N, const int* __restrict__
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
   HHG_UNITS(n_if_units, n_tiles, n_act) {
-    if (unit < n_if_units) {
-      const int q = unit * CTA + tid256();
+    if (const int ic_ = if_chunk(unit, n_if_units); ic_ >= 0) {
+      const int q = ic_ * CTA + tid256();
       if (q < n_list) {
         const int node = list[q];
         const double val = uI[node] + (double)eI[node];
@@ -757,7 +765,7 @@ __global__ void __launch_bounds__(CTA) k_add_corr(int N, const int* __restrict__
     }
     Tile t;
     int macro;
-    vol_unit(unit, n_if_units, n_tiles, tiles, act, t, macro);
+    vol_unit(vol_index(unit, n_if_units), n_act, tiles, act, t, macro);
     double* ub = u + (size_t)macro * block;
     const float* eb = e + (size_t)macro * block;
     HHG_TILE_NODES(N, rs, t, s_pre, {

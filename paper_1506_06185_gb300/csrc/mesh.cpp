@@ -192,6 +192,18 @@ void build_pair_tiles(int N, std::vector<Tile>& out, int target, int slabs) {
     const int np = std::min(32, std::max(1, (target + per_pair - 1) / per_pair));
     for (int p0 = 0; p0 < pairs; p0 += np) out.push_back(Tile{k0, p0, std::min(np, pairs - p0), nk});
   }
+  // largest tiles first (interior nodes of the tile's pairs in its slices)
+  auto work = [N](const Tile& t) {
+    int64_t w = 0;
+    for (int k = t.k; k < t.k + t.pad; ++k)
+      for (int q = 0; q < t.m0; ++q) {
+        const int j1 = 1 + t.j0 + q, j2 = N - 2 - k - t.j0 - q;
+        if (j1 < j2) w += N - 1 - k;
+        else if (j1 == j2) w += N - 1 - j1 - k;
+      }
+    return w;
+  };
+  std::stable_sort(out.begin(), out.end(), [&](const Tile& a, const Tile& b) { return work(a) > work(b); });
 }
 
 void set_coefficients(HostMesh& m, const double* coeff) {
