@@ -550,6 +550,29 @@ def run_kappa(args):
     return 0
 
 
+def run_profile_case(args):
+    """A short run for kernel captures: two global cycles (FP64, or FP32 inside
+    FP64 refinement with --mixed) of the cube refined --levels times, random
+    load seed 0.  Not a benchmark line."""
+    import torch
+
+    import hhg_inputs as I
+    from paper_1506_06185_gb300 import build
+    from paper_1506_06185_gb300 import hhg
+
+    build()
+    torch.cuda.set_device(0)
+    M = hhg.Mesh(SUB, args.levels, precision=32 if args.mixed else 64)
+    f = torch.from_numpy(I.random_load(SUB, args.levels, SEED)).cuda()
+    M.set_problem(f, torch.zeros_like(f))
+    hist, cyc, _ = M.solve(rtol=1e-30, max_cycles=2, mixed_precision=args.mixed, allow_not_converged=True)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": "profile", "levels": args.levels, "mixed": bool(args.mixed), "cycles": cyc,
+                      "rel_residual": float(hist[-1])}), flush=True)
+    M.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -559,6 +582,10 @@ def main():
     ap.add_argument("--quick", action="store_true", help="skip the variant timings")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--batch", action="store_true", help="run the batched-recovery workload instead")
+    ap.add_argument("--profile-case", action="store_true",
+                    help="two cycles of the cube refined --levels times (for kernel captures)")
+    ap.add_argument("--levels", type=int, default=7)
+    ap.add_argument("--mixed", action="store_true")
     ap.add_argument("--kappa", action="store_true",
                     help="run the cycle-advantage study of the recovery strategies instead")
     ap.add_argument("--precision", action="store_true",
@@ -574,6 +601,8 @@ def main():
         return run_precision(args)
     if args.kappa:
         return run_kappa(args)
+    if args.profile_case:
+        return run_profile_case(args)
     return run_ours(args)
 
 

@@ -415,6 +415,67 @@ __device__ __forceinline__ void gs_group7(const Slice& sc, int N, int j, int g, 
   }
 }
 
+// 7-point residual r = f - A u of the colour-c nodes in slots m0 .. m0 + VW - 1
+// of interior row j of slice k (same vectors as gs_group7 plus the centre);
+// writes the interior nodes among them to rb and/or adds their squares to ss.
+template <class T, bool WRITE, bool NORM>
+__device__ __forceinline__ void res_group7(const Slice& sc, int N, int j, int g, int c, const T* __restrict__ ub,
+                                           const T* __restrict__ fb, T* __restrict__ rb, const T* __restrict__ w,
+                                           double& ss) {
+  constexpr int VW = Vec<T>::n;
+  int ic, mlo, n;
+  colour_row(N, j, sc.k, c, ic, mlo, n);
+  const int m0 = g * VW;
+  const int X = slot_prefix(sc.M - j);
+  const int L = sc.M - j;
+  const int r0 = sc.SL0 + sc.SM0 - X;
+  const int rjp = r0 + row_slots(L);
+  const int rjm = r0 - row_slots(L + 1);
+  const int rkp = sc.SLp + sc.SMm - X;
+  const int rkm = sc.SLm + sc.SMp - X;
+  const int cc = c * sc.CS, cp = ((c + 1) & 3) * sc.CS, cm = ((c + 3) & 3) * sc.CS;
+  const bool e1 = ic == 3, e0 = ic == 0;
+  T acc[VW], a[VW];
+  Vec<T>::load(fb + cc + r0 + m0, acc);
+  Vec<T>::load(ub + cc + r0 + m0, a);               // centre
+#pragma unroll
+  for (int t = 0; t < VW; ++t) acc[t] -= w[0] * a[t];
+  load_shifted(ub + cp + r0 + m0, e1, false, a);    // ( 1,  0,  0)
+#pragma unroll
+  for (int t = 0; t < VW; ++t) acc[t] -= w[1] * a[t];
+  load_shifted(ub + cp + rjp + m0, false, e0, a);   // (-1,  1,  0)
+#pragma unroll
+  for (int t = 0; t < VW; ++t) acc[t] -= w[2] * a[t];
+  Vec<T>::load(ub + cp + rkp + m0, a);              // ( 0, -1,  1)
+#pragma unroll
+  for (int t = 0; t < VW; ++t) acc[t] -= w[3] * a[t];
+  load_shifted(ub + cm + r0 + m0, false, e0, a);    // (-1,  0,  0)
+#pragma unroll
+  for (int t = 0; t < VW; ++t) acc[t] -= w[8] * a[t];
+  load_shifted(ub + cm + rjm + m0, e1, false, a);   // ( 1, -1,  0)
+#pragma unroll
+  for (int t = 0; t < VW; ++t) acc[t] -= w[9] * a[t];
+  Vec<T>::load(ub + cm + rkm + m0, a);              // ( 0,  1, -1)
+#pragma unroll
+  for (int t = 0; t < VW; ++t) acc[t] -= w[10] * a[t];
+  const int lo = max(mlo - m0, 0), hi = min(mlo + n - m0, VW);
+  if (NORM) {
+#pragma unroll
+    for (int t = 0; t < VW; ++t)
+      if (t >= lo && t < hi) ss += (double)acc[t] * (double)acc[t];
+  }
+  if (WRITE) {
+    T* out = rb + cc + r0 + m0;
+    if (lo == 0 && hi == VW) {
+      Vec<T>::store(out, acc);
+    } else {
+#pragma unroll
+      for (int t = 0; t < VW; ++t)
+        if (t >= lo && t < hi) out[t] = acc[t];
+    }
+  }
+}
+
 template <class T, bool S7>
 __global__ void __launch_bounds__(CTA, 5) k_gs(int N, const int* __restrict__ rs, int64_t block, T* __restrict__ u, T* __restrict__ uI,
                                             const T* __restrict__ f, const T* __restrict__ fI,
@@ -528,6 +589,25 @@ __global__ void __launch_bounds__(CTA, sizeof(T) == 8 ? 6 : 5) k_res(int N, cons
     const T* fb = f + (size_t)macro * block;
     T* rb = r + (size_t)macro * block;
     const T* w = W + (size_t)macro * 16 * NDIR;
+    if (S7) {
+      // one colour after another, groups of VW same-colour slots per thread
+      constexpr int VW = Vec<T>::n;
+      const T wr[11] = {w[0], w[1], w[2], w[3], T(0), T(0), T(0), T(0), w[8], w[9], w[10]};
+      for (int c = 0; c < 4; ++c) {
+        const int total = flat_setup_slabs(t, N, c, true, VW, s_pre2, s_pre_tot);
+        int sl = 0;
+        for (int tt = tid256(); tt < total; tt += CTA) {
+          while (tt >= s_pre_tot[sl + 1]) ++sl;
+          const int k = t.k + sl;
+          const Tile ts{k, t.j0, t.m0, 1};
+          int j, g;
+          flat_item(ts, N, c, true, s_pre2[sl], tt - s_pre_tot[sl], j, g, VW);
+          res_group7<T, WRITE, NORM>(slice_consts(rs, N, k), N, j, g, c, ub, fb, rb, wr, ss);
+        }
+        __syncthreads();
+      }
+      continue;
+    }
     HHG_TILE_NODES(N, rs, t, s_pre, {
       int me;
       T acc;
