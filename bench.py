@@ -132,14 +132,18 @@ def _kernel_hash():
 
 
 def _traffic(kind):
-    """DRAM bytes per launch of the dominant kernel from a committed ncu
-    summary, if it was taken on the current kernel source."""
+    """DRAM bytes per launch of the dominant kernel from the committed ncu
+    summary, if it was taken on the current kernel source (else None)."""
+    files = {"gs_vol_f64": "traffic_gs_fp64_config2.md"}
     try:
-        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
-            d = json.load(fh)
-        e = d.get(kind)
-        if e and e.get("kernel_hash") == _kernel_hash():
-            return e.get("bytes_per_launch_full_size")
+        vals = {}
+        with open(os.path.join(ROOT, "profiles", files[kind])) as fh:
+            for line in fh:
+                if ":" in line and not line.startswith(("#", "|", " ")):
+                    key, val = line.split(":", 1)
+                    vals[key.strip()] = val.strip()
+        if vals.get("kernel_hash") == _kernel_hash():
+            return float(vals["bytes_per_launch_full_size"])
     except Exception:
         pass
     return None
