@@ -192,6 +192,7 @@ ProbArgs pargs(const DevProblem& p, int l) {
   a.zero_off = q.zero_off;
   a.n_zero = q.n_zero;
   a.gather = q.gather;
+  a.sched = p.sched;
   return a;
 }
 
@@ -227,6 +228,8 @@ int upload_problem(hhg_mesh* m, const HostProblem& h, DevProblem& d) {
   HHG_TRY(dalloc(m, &d.partial, (size_t)d.n_partial));
   HHG_TRY(dalloc(m, &d.scalar, 8));
   HHG_TRY(dalloc(m, &d.cg_iters, 4));
+  HHG_TRY(dalloc(m, &d.sched, 2));
+  HHG_CUDA(cudaMemset(d.sched, 0, 2 * sizeof(int)));
   return HHG_OK;
 }
 

@@ -239,6 +239,7 @@ struct DevProblemLevel {
 
 struct DevProblem {
   int kind = 0;
+  int* sched = nullptr;               // 2 unit counters of the dynamic walks (kernels.cu)
   int* act = nullptr;
   int n_act = 0;
   std::vector<int> act_host;

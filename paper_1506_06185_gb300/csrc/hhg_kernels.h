@@ -28,6 +28,7 @@ struct ProbArgs {
   const int64_t* zero_off;
   int n_zero;
   const int64_t* gather;
+  int* sched;      // unit counters of the problem's dynamic walks (2 ints, zero between launches)
 };
 
 // One colour of multicolour Gauss-Seidel on the volume interiors and the free

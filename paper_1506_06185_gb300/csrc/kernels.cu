@@ -266,6 +266,31 @@ __device__ __forceinline__ int if_chunk(int u, int n_if_units) { return u < n_if
 // Index of the volume unit at position u (not an interface chunk).
 __device__ __forceinline__ int vol_index(int u, int n_if_units) { return u - n_if_units; }
 
+// Dynamic walk over the same units: each CTA takes the next unit from the
+// problem's counter sched[0], so the units (interface chunks, then tiles by
+// decreasing work) are handed out greedily and the launch ends with the
+// smallest tiles.  The CTA that finishes last (counted in sched[1]) puts both
+// counters back to zero for the problem's next launch; a problem's kernels
+// run one after another on one stream, so launches never share a counter.
+__device__ __forceinline__ int next_unit(int* sched, int* s_unit) {
+  __syncthreads();                              // every thread has read the last unit
+  if (threadIdx.x == 0 && threadIdx.y == 0) *s_unit = atomicAdd(sched, 1);
+  __syncthreads();
+  return *s_unit;
+}
+__device__ __forceinline__ void finish_units(int* sched) {
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    __threadfence();
+    if (atomicAdd(sched + 1, 1) == (int)gridDim.x - 1) {
+      atomicExch(sched, 0);
+      atomicExch(sched + 1, 0);
+    }
+  }
+}
+#define HHG_UNITS_DYN(n_if_units, n_tiles, n_act, sched, s_unit)                                      \
+  for (int n_units_ = (n_if_units) + (n_tiles) * (n_act), unit = next_unit((sched), (s_unit));         \
+       unit < n_units_; unit = next_unit((sched), (s_unit)))
+
 // Volume unit -> (tile, macro).  The macro index runs fastest and the tile
 // lists are sorted by decreasing work, so the last units of a grid-stride walk
 // are the smallest tiles of all macros (a short tail).
@@ -483,11 +508,12 @@ __global__ void __launch_bounds__(CTA, 5) k_gs(int N, const int* __restrict__ rs
                                             const Tile* __restrict__ tiles, int n_tiles, const int* __restrict__ act,
                                             int n_act, int colour, const int* __restrict__ cptr,
                                             const Copy* __restrict__ cps, const int* __restrict__ list, int n_list,
-                                            int n_if_units) {
+                                            int n_if_units, int* __restrict__ sched) {
   __shared__ int s_pre[33];
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
-  HHG_UNITS(n_if_units, n_tiles, n_act) {
+  __shared__ int s_unit;
+  HHG_UNITS_DYN(n_if_units, n_tiles, n_act, sched, &s_unit) {
     if (const int ic_ = if_chunk(unit, n_if_units); ic_ >= 0) {
       const int q = ic_ * CTA + tid256();
       if (q < n_list) {
@@ -546,6 +572,7 @@ __global__ void __launch_bounds__(CTA, 5) k_gs(int N, const int* __restrict__ rs
     __syncthreads();
     }
   }
+  finish_units(sched);
 }
 
 // ---------------------------------------------------------------------------
@@ -560,13 +587,14 @@ __global__ void __launch_bounds__(CTA, sizeof(T) == 8 ? 6 : 5) k_res(int N, cons
                                              int n_act, const int* __restrict__ cptr, const Copy* __restrict__ cps,
                                              const int* __restrict__ list, int n_list,
                                              const int64_t* __restrict__ zero_off, int n_zero, int n_if_units,
-                                             double* __restrict__ partial) {
+                                             double* __restrict__ partial, int* __restrict__ sched) {
   __shared__ int s_pre[33];
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
   __shared__ double sh[32];
   double ss = 0.0;
-  HHG_UNITS(n_if_units, n_tiles, n_act) {
+  __shared__ int s_unit;
+  HHG_UNITS_DYN(n_if_units, n_tiles, n_act, sched, &s_unit) {
     if (const int ic_ = if_chunk(unit, n_if_units); ic_ >= 0) {
       const int q = ic_ * CTA + tid256();
       if (q < n_list) {
@@ -635,6 +663,7 @@ _Pragma("unroll")
       if (NORM) ss += (double)acc * (double)acc;
     })
   }
+  finish_units(sched);
   if (NORM) {
     const double s = block_sum(ss, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.x] = s;
@@ -652,11 +681,12 @@ __global__ void __launch_bounds__(CTA) k_restrict(int Nc, const int* __restrict_
                                                   const int* __restrict__ cptr, const Copy* __restrict__ cps,
                                                   const int* __restrict__ list, int n_list,
                                                   const int64_t* __restrict__ gather,
-                                                  const int64_t* __restrict__ zero_off, int n_zero, int n_if_units) {
+                                                  const int64_t* __restrict__ zero_off, int n_zero, int n_if_units, int* __restrict__ sched) {
   __shared__ int s_pre[33];
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
-  HHG_UNITS(n_if_units, n_tiles, n_act) {
+  __shared__ int s_unit;
+  HHG_UNITS_DYN(n_if_units, n_tiles, n_act, sched, &s_unit) {
     if (const int ic_ = if_chunk(unit, n_if_units); ic_ >= 0) {
       const int q = ic_ * CTA + tid256();
       if (q < n_list) {
@@ -695,6 +725,7 @@ _Pragma("unroll")
       ub[me] = T(0);
     })
   }
+  finish_units(sched);
 }
 
 // ---------------------------------------------------------------------------
@@ -727,11 +758,12 @@ __global__ void __launch_bounds__(CTA) k_prolong(int Nf, const int* __restrict__
                                                  const Tile* __restrict__ tiles, int n_tiles,
                                                  const int* __restrict__ act, int n_act, const int* __restrict__ cptr,
                                                  const Copy* __restrict__ cps, const int* __restrict__ list,
-                                                 int n_list, int n_if_units) {
+                                                 int n_list, int n_if_units, int* __restrict__ sched) {
   __shared__ int s_pre[33];
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
-  HHG_UNITS(n_if_units, n_tiles, n_act) {
+  __shared__ int s_unit;
+  HHG_UNITS_DYN(n_if_units, n_tiles, n_act, sched, &s_unit) {
     if (const int ic_ = if_chunk(unit, n_if_units); ic_ >= 0) {
       const int q = ic_ * CTA + tid256();
       if (q < n_list) {
@@ -751,6 +783,7 @@ __global__ void __launch_bounds__(CTA) k_prolong(int Nf, const int* __restrict__
     const T* cb = uc + (size_t)macro * bc;
     HHG_TILE_NODES(Nf, rsf, t, s_pre, { fb[lidx32(rsf, Nf, i, j, k)] += interp(cb, Nc, rsc, i, j, k); })
   }
+  finish_units(sched);
 }
 
 // ---------------------------------------------------------------------------
@@ -766,13 +799,14 @@ __global__ void __launch_bounds__(CTA) k_res_f32(int N, const int* __restrict__ 
                                                  const int* __restrict__ act, int n_act,
                                                  const int* __restrict__ cptr, const Copy* __restrict__ cps,
                                                  const int* __restrict__ list, int n_list, int n_if_units,
-                                                 double* __restrict__ partial) {
+                                                 double* __restrict__ partial, int* __restrict__ sched) {
   __shared__ int s_pre[33];
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
   __shared__ double sh[32];
   double ss = 0.0;
-  HHG_UNITS(n_if_units, n_tiles, n_act) {
+  __shared__ int s_unit;
+  HHG_UNITS_DYN(n_if_units, n_tiles, n_act, sched, &s_unit) {
     if (const int ic_ = if_chunk(unit, n_if_units); ic_ >= 0) {
       const int q = ic_ * CTA + tid256();
       if (q < n_list) {
@@ -819,6 +853,7 @@ _Pragma("unroll")
       ss += acc * acc;
     })
   }
+  finish_units(sched);
   const double s = block_sum(ss, sh);
   if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.x] = s;
 }
@@ -828,11 +863,12 @@ __global__ void __launch_bounds__(CTA) k_add_corr(int N, const int* __restrict__
                                                   const float* __restrict__ eI, const Tile* __restrict__ tiles,
                                                   int n_tiles, const int* __restrict__ act, int n_act,
                                                   const int* __restrict__ cptr, const Copy* __restrict__ cps,
-                                                  const int* __restrict__ list, int n_list, int n_if_units) {
+                                                  const int* __restrict__ list, int n_list, int n_if_units, int* __restrict__ sched) {
   __shared__ int s_pre[33];
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
-  HHG_UNITS(n_if_units, n_tiles, n_act) {
+  __shared__ int s_unit;
+  HHG_UNITS_DYN(n_if_units, n_tiles, n_act, sched, &s_unit) {
     if (const int ic_ = if_chunk(unit, n_if_units); ic_ >= 0) {
       const int q = ic_ * CTA + tid256();
       if (q < n_list) {
@@ -853,6 +889,7 @@ __global__ void __launch_bounds__(CTA) k_add_corr(int N, const int* __restrict__
       ub[me] += (double)eb[me];
     })
   }
+  finish_units(sched);
 }
 
 // ---------------------------------------------------------------------------
@@ -1152,7 +1189,8 @@ cudaError_t gs_colour(const LevelArgs& L, const ProbArgs& p, T* u, T* uI, const 
   if (ev_begin) cudaEventRecord(ev_begin, s);
   ++g_kernel_launches;
   kern<<<grid, cta_shape(), 0, s>>>(L.N, L.rs, L.block, u, uI, f, fI, W, Winv, L.tiles_int, L.n_tiles_int, p.act,
-                                    p.n_act, colour, L.cptr, L.cps, p.free_if + p.col_off[colour], n, g.n_if_units);
+                                    p.n_act, colour, L.cptr, L.cps, p.free_if + p.col_off[colour], n, g.n_if_units,
+                                    p.sched);
   if (ev_end) cudaEventRecord(ev_end, s);
   return cudaGetLastError();
 }
@@ -1167,7 +1205,7 @@ cudaError_t residual(const LevelArgs& L, const ProbArgs& p, const T* u, const T*
   if (n_part) *n_part = 0;
   if (g.total == 0) return cudaSuccess;
   void (*kern)(int, const int*, int64_t, const T*, const T*, const T*, const T*, T*, const T*, const Tile*, int, const int*,
-               int, const int*, const Copy*, const int*, int, const int64_t*, int, int, double*);
+               int, const int*, const Copy*, const int*, int, const int64_t*, int, int, double*, int*);
   if (seven_point)
     kern = write_r ? (norm ? k_res<T, true, true, true> : k_res<T, true, true, false>) : k_res<T, true, false, true>;
   else
@@ -1176,7 +1214,8 @@ cudaError_t residual(const LevelArgs& L, const ProbArgs& p, const T* u, const T*
   if (n_part && norm) *n_part = (int)grid;
   ++g_kernel_launches;
   kern<<<grid, cta_shape(), 0, s>>>(L.N, L.rs, L.block, u, uI, f, fI, r, W, L.tiles_int, L.n_tiles_int, p.act,
-                                    p.n_act, L.cptr, L.cps, p.free_if, n, p.zero_off, n_zero, g.n_if_units, partial);
+                                    p.n_act, L.cptr, L.cps, p.free_if, n, p.zero_off, n_zero, g.n_if_units, partial,
+                                    p.sched);
   return cudaGetLastError();
 }
 
@@ -1190,7 +1229,7 @@ cudaError_t restrict_to(const LevelArgs& C, const LevelArgs& F, const ProbArgs& 
   ++g_kernel_launches;
   k_restrict<T><<<grid, cta_shape(), 0, s>>>(C.N, C.rs, C.block, fc, fIc, uc, uIc, F.N, F.rs, F.block, rf, C.tiles_int,
                                              C.n_tiles_int, pc.act, pc.n_act, C.cptr, C.cps, pc.free_if, n, pc.gather,
-                                             pc.zero_off, pc.n_zero, g.n_if_units);
+                                             pc.zero_off, pc.n_zero, g.n_if_units, pc.sched);
   return cudaGetLastError();
 }
 
@@ -1204,7 +1243,7 @@ cudaError_t prolong_add(const LevelArgs& F, const LevelArgs& C, const ProbArgs& 
   ++g_kernel_launches;
   k_prolong<T><<<grid, cta_shape(), 0, s>>>(F.N, F.rs, F.block, uf, uIf, C.N, C.rs, C.block, uc, F.tiles_int,
                                             F.n_tiles_int, pf.act, pf.n_act, F.cptr, F.cps, pf.free_if, n,
-                                            g.n_if_units);
+                                            g.n_if_units, pf.sched);
   return cudaGetLastError();
 }
 
@@ -1334,7 +1373,7 @@ cudaError_t residual_to_f32(const LevelArgs& L, const ProbArgs& p, const double*
   if (n_part) *n_part = (int)grid;
   ++g_kernel_launches;
   kern<<<grid, cta_shape(), 0, s>>>(L.N, L.rs, L.block, u, uI, f, fI, f32, fI32, W, L.tiles_int, L.n_tiles_int, p.act,
-                                    p.n_act, L.cptr, L.cps, p.free_if, n, g.n_if_units, partial);
+                                    p.n_act, L.cptr, L.cps, p.free_if, n, g.n_if_units, partial, p.sched);
   return cudaGetLastError();
 }
 
@@ -1346,7 +1385,7 @@ cudaError_t add_correction(const LevelArgs& L, const ProbArgs& p, double* u, dou
   const unsigned grid = resident_grid((const void*)k_add_corr, g.total);
   ++g_kernel_launches;
   k_add_corr<<<grid, cta_shape(), 0, s>>>(L.N, L.rs, L.block, u, uI, e, eI, L.tiles_int, L.n_tiles_int, p.act,
-                                          p.n_act, L.cptr, L.cps, p.free_if, n, g.n_if_units);
+                                          p.n_act, L.cptr, L.cps, p.free_if, n, g.n_if_units, p.sched);
   return cudaGetLastError();
 }
 
