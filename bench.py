@@ -167,6 +167,23 @@ def cpu_oracle_sample(steps=1):
     return dof, times
 
 
+def max_over_ranks(x, dist=None, device=None):
+    """The largest of the ranks' x (the job's time is its slowest replica's);
+    x itself when there is no process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world, dof, cycles, seconds):
+    """Whole-job throughput of `world` identical replicas: fine DoF x V-cycles
+    of every replica over the slowest replica's time."""
+    return world * dof * cycles / seconds
+
+
 def _dist():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -252,14 +269,11 @@ def run_ours(args):
     n_prof, prof_ms = hhg.hhg_profile_read(M.h)
     hhg.hhg_profile_enable(M.h, False)
     clocks = sampler.stop()
-    ms = e0.elapsed_time(e1)
+    ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     if dist:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
         dist.barrier()
     dof = M.n_dof
-    value = world * dof * sum(cyc_list) / (ms * 1e-3)
+    value = job_value(world, dof, sum(cyc_list), ms * 1e-3)
 
     # dominant kernel: finest-level FP64 Gauss-Seidel volume kernel (one colour per launch)
     n_vol, seven = hhg.hhg_profile_info(M.h)
@@ -294,13 +308,9 @@ def run_ours(args):
         M.get_solution(u_pin.numpy())
         e2e_cycles += cyc_e
     torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([t_e2e], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
+    t_e2e = max_over_ranks(time.perf_counter() - t0, dist, dev)
     nbytes = f_np.nbytes
-    e2e = {"value": world * dof * e2e_cycles / t_e2e, "unit": UNIT, "h2d_bytes_per_step": 2 * nbytes,
+    e2e = {"value": job_value(world, dof, e2e_cycles, t_e2e), "unit": UNIT, "h2d_bytes_per_step": 2 * nbytes,
            "d2h_bytes_per_step": nbytes, "ms_per_step": 1e3 * t_e2e / k_e2e}
     M.set_problem(f_dev, None)
 

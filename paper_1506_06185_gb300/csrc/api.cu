@@ -643,6 +643,9 @@ int update_coefficients(hhg_mesh* m, const double* coeff) {
       HHG_CUDA(cudaMemcpy(m->d32.Winv[l], wi32.data(), wi32.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
   }
+  // the Neumann-side problem of DN recovery (operator A_I, coarse matrix,
+  // interface flux) is rebuilt from the new coefficients on its next use
+  m->has_dn = false;
   std::vector<DevProblem*> probs = {&m->global};
   if (m->has_fault) {
     probs.push_back(&m->faulty);

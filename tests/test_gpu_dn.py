@@ -151,3 +151,32 @@ def test_two_faults_match_oracle(hhg, recovery):
         M.solve(rtol=1e-10, max_cycles=5, faults=[(0, [1])])
     assert e.value.code == hhg.HHG_ERR_ARG
     M.close()
+
+
+def test_dn_after_new_coefficients(hhg):
+    """The Neumann-side operator A_I follows hhg_set_coefficients: a DN recovery
+    after a coefficient change matches the oracle built with the new ones."""
+    sub, R = (2, 2, 2), 4
+    ids = [13, 14]
+    k1 = np.exp(np.random.default_rng(1).standard_normal(48))
+    k2 = np.exp(np.random.default_rng(2).standard_normal(48))
+    f = I.random_load(sub, R, seed=9)
+    M = hhg.Mesh(sub, R, coeff=k1)
+    M.set_problem(f, I.initial_guess(sub, R))
+    M.vcycle()
+    M.inject_fault(ids)
+    M.recover_dn(ids, 2, 2.0)
+    M.set_coefficients(k2)
+    M.set_problem(f, I.initial_guess(sub, R))
+    m = O.Mesh(sub, R, coeff=k2)
+    uo, fo = O.pad(I.initial_guess(sub, R)), O.pad(f)
+    top = len(m.levels) - 1
+    for _ in range(2):
+        M.vcycle()
+        O.vcycle(m, m.global_problem, top, uo, fo)
+    M.inject_fault(ids)
+    O.inject_fault(m, uo, ids)
+    M.recover_dn(ids, 2, 2.0)
+    O.dn_recover(m, uo, fo, ids, 2, 2.0)
+    assert _rel(M.get_solution(), O.interior(uo)) <= RTOL_U
+    M.close()
