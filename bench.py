@@ -333,7 +333,16 @@ def run_ours(args):
         ms_dnr, h_dnr, c_dnr = timed(recovery=hhg.HHG_RECOVERY_DN)
         u_fp64 = torch.zeros_like(f_dev)
         M.get_solution(u_fp64)
+        hhg.hhg_profile_enable(M.h, True)
         ms_mx, h_mx, c_mx = timed(mixed_precision=True)
+        n32, ms32 = hhg.hhg_profile_read(M.h)
+        hhg.hhg_profile_enable(M.h, False)
+        avg32 = ms32 / max(n32, 1) * 1e-3
+        gs32 = {"kernel": "k_gs<float> finest level, one colour (inner FP32 cycles)", "launches": n32,
+                "avg_launch_ms": avg32 * 1e3, "bound": "hbm",
+                "achieved_gbs": 12.0 * n_vol / 4.0 / avg32 / 1e9, "peak_gbs": hbm_peak,
+                "frac": 12.0 * n_vol / 4.0 / avg32 / 1e9 / hbm_peak,
+                "bytes_per_node_update": "12 (read u, f; write u, FP32)"}
         u_mx = torch.zeros_like(f_dev)
         M.get_solution(u_mx)
         ms_mx_free, h_mx_free, c_mx_free = timed(mixed_precision=True, fault_cycle=0)
@@ -347,7 +356,8 @@ def run_ours(args):
             "dd_fp64_eta4_nI3": {"ms": ms_dd, "cycles": c_dd, "kappa": kappa(c_dd, N_I)},
             "dn_fp64_eta4_nI3": {"ms": ms_dnr, "cycles": c_dnr, "kappa": kappa(c_dnr, N_I)},
             "dd_mixed_fp32_in_fp64_ir": {"ms": ms_mx, "cycles": c_mx, "final_rel_res": float(h_mx[-1]),
-                                         "max_abs_diff_vs_fp64_solution": diff, "fp64_solution_max": scale},
+                                         "max_abs_diff_vs_fp64_solution": diff, "fp64_solution_max": scale,
+                                         "gs_fp32_roofline": gs32},
             "fault_free_mixed": {"ms": ms_mx_free, "cycles": c_mx_free},
         }
 

@@ -266,19 +266,43 @@ __device__ __forceinline__ int if_chunk(int u, int n_if_units) { return u < n_if
 // Index of the volume unit at position u (not an interface chunk).
 __device__ __forceinline__ int vol_index(int u, int n_if_units) { return u - n_if_units; }
 
-// Dynamic walk over the same units: each CTA takes the next unit from the
-// problem's counter sched[0], so the units (interface chunks, then tiles by
-// decreasing work) are handed out greedily and the launch ends with the
-// smallest tiles.  The CTA that finishes last (counted in sched[1]) puts both
-// counters back to zero for the problem's next launch; a problem's kernels
-// run one after another on one stream, so launches never share a counter.
-__device__ __forceinline__ int next_unit(int* sched, int* s_unit) {
-  __syncthreads();                              // every thread has read the last unit
-  if (threadIdx.x == 0 && threadIdx.y == 0) *s_unit = atomicAdd(sched, 1);
+// Walk over the same units, dynamic for large launches: CTA b starts with
+// unit b; with at least DYN_UNITS_PER_CTA units per CTA, later units come from
+// the problem's counter sched[0] (unit = gridDim.x + counter), so the units
+// (interface chunks, then tiles by decreasing work) are handed out greedily
+// and the launch ends with the smallest tiles; smaller launches keep the grid
+// stride (measured faster there, e.g. the local recovery cycles of a few
+// macros).  Thread 0 takes the next unit one unit ahead, so the atomic's
+// latency hides behind the work.  The CTA that finishes last (counted in
+// sched[1]) puts both counters back to zero for the problem's next launch; a
+// problem's kernels run one after another on one stream, so launches never
+// share a counter.
+constexpr int DYN_UNITS_PER_CTA = 4;
+__device__ __forceinline__ bool walk_dynamic(int n_units) { return n_units >= DYN_UNITS_PER_CTA * (int)gridDim.x; }
+__device__ __forceinline__ int walk_after(int cur, int n_units, int* sched) {
+  if (cur >= n_units) return n_units;
+  return walk_dynamic(n_units) ? (int)gridDim.x + atomicAdd(sched, 1) : cur + (int)gridDim.x;
+}
+__device__ __forceinline__ int walk_first(int n_units, int* sched, int* s_unit, int& nxt) {
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    nxt = walk_after((int)blockIdx.x, n_units, sched);
+    *s_unit = blockIdx.x;
+  }
   __syncthreads();
   return *s_unit;
 }
-__device__ __forceinline__ void finish_units(int* sched) {
+__device__ __forceinline__ int walk_next(int n_units, int* sched, int* s_unit, int& nxt) {
+  __syncthreads();                              // every thread has read the last unit
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+    const int cur = nxt;
+    nxt = walk_after(cur, n_units, sched);
+    *s_unit = cur;
+  }
+  __syncthreads();
+  return *s_unit;
+}
+__device__ __forceinline__ void finish_units(int* sched, int n_units) {
+  if (!walk_dynamic(n_units)) return;
   if (threadIdx.x == 0 && threadIdx.y == 0) {
     __threadfence();
     if (atomicAdd(sched + 1, 1) == (int)gridDim.x - 1) {
@@ -288,8 +312,9 @@ __device__ __forceinline__ void finish_units(int* sched) {
   }
 }
 #define HHG_UNITS_DYN(n_if_units, n_tiles, n_act, sched, s_unit)                                      \
-  for (int n_units_ = (n_if_units) + (n_tiles) * (n_act), unit = next_unit((sched), (s_unit));         \
-       unit < n_units_; unit = next_unit((sched), (s_unit)))
+  for (int n_units_ = (n_if_units) + (n_tiles) * (n_act), nxt_ = 0,                                    \
+           unit = walk_first(n_units_, (sched), (s_unit), nxt_);                                       \
+       unit < n_units_; unit = walk_next(n_units_, (sched), (s_unit), nxt_))
 
 // Volume unit -> (tile, macro).  The macro index runs fastest and the tile
 // lists are sorted by decreasing work, so the last units of a grid-stride walk
@@ -572,7 +597,7 @@ __global__ void __launch_bounds__(CTA, 5) k_gs(int N, const int* __restrict__ rs
     __syncthreads();
     }
   }
-  finish_units(sched);
+  finish_units(sched, n_if_units + n_tiles * n_act);
 }
 
 // ---------------------------------------------------------------------------
@@ -663,7 +688,7 @@ _Pragma("unroll")
       if (NORM) ss += (double)acc * (double)acc;
     })
   }
-  finish_units(sched);
+  finish_units(sched, n_if_units + n_tiles * n_act);
   if (NORM) {
     const double s = block_sum(ss, sh);
     if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.x] = s;
@@ -725,7 +750,7 @@ _Pragma("unroll")
       ub[me] = T(0);
     })
   }
-  finish_units(sched);
+  finish_units(sched, n_if_units + n_tiles * n_act);
 }
 
 // ---------------------------------------------------------------------------
@@ -783,7 +808,7 @@ __global__ void __launch_bounds__(CTA) k_prolong(int Nf, const int* __restrict__
     const T* cb = uc + (size_t)macro * bc;
     HHG_TILE_NODES(Nf, rsf, t, s_pre, { fb[lidx32(rsf, Nf, i, j, k)] += interp(cb, Nc, rsc, i, j, k); })
   }
-  finish_units(sched);
+  finish_units(sched, n_if_units + n_tiles * n_act);
 }
 
 // ---------------------------------------------------------------------------
@@ -853,7 +878,7 @@ _Pragma("unroll")
       ss += acc * acc;
     })
   }
-  finish_units(sched);
+  finish_units(sched, n_if_units + n_tiles * n_act);
   const double s = block_sum(ss, sh);
   if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.x] = s;
 }
@@ -889,7 +914,7 @@ __global__ void __launch_bounds__(CTA) k_add_corr(int N, const int* __restrict__
       ub[me] += (double)eb[me];
     })
   }
-  finish_units(sched);
+  finish_units(sched, n_if_units + n_tiles * n_act);
 }
 
 // ---------------------------------------------------------------------------
