@@ -11,6 +11,7 @@
 #include <new>
 #include <stdexcept>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/hhg.h"
@@ -86,6 +87,12 @@ struct hhg_mesh {
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::vector<void*> allocs;
+  std::unordered_map<void*, int64_t> alloc_bytes;
+  // allocations of the current fault set (its sub-problems and lists), freed
+  // when another set replaces it; `collect`, when set, receives new ones
+  std::vector<void*> fault_allocs, dn_allocs;
+  std::vector<void*>* collect = nullptr;
+  int batch_refs = 0;              // batch graphs that hold this mesh's buffers
   int64_t bytes = 0;
   double* host_scalar = nullptr;   // pinned
   double* grad_partial = nullptr;  // coefficient-gradient partial sums
@@ -126,10 +133,38 @@ int dalloc(hhg_mesh* m, T** p, size_t n) {
                                  cudaGetErrorString(e));
   }
   m->allocs.push_back(q);
+  m->alloc_bytes[q] = (int64_t)(n * sizeof(T));
+  if (m->collect) m->collect->push_back(q);
   m->bytes += (int64_t)(n * sizeof(T));
   *p = static_cast<T*>(q);
   return HHG_OK;
 }
+
+// Free the allocations in `list` (cudaFree waits for the device), unless a
+// batch graph still refers to the mesh's buffers (then they stay until the
+// mesh is destroyed).
+void release(hhg_mesh* m, std::vector<void*>& list) {
+  if (m->batch_refs > 0) {
+    list.clear();
+    return;
+  }
+  if (!list.empty()) cudaDeviceSynchronize();   // nothing in flight may still use them
+  for (void* q : list) {
+    cudaFree(q);
+    m->bytes -= m->alloc_bytes[q];
+    m->alloc_bytes.erase(q);
+    m->allocs.erase(std::find(m->allocs.begin(), m->allocs.end(), q));
+  }
+  list.clear();
+}
+
+// Collect the allocations made while this object lives into `list`.
+struct Collect {
+  hhg_mesh* m;
+  std::vector<void*>* prev;
+  Collect(hhg_mesh* mm, std::vector<void*>& list) : m(mm), prev(mm->collect) { m->collect = &list; }
+  ~Collect() { m->collect = prev; }
+};
 
 template <class T>
 int upload(hhg_mesh* m, T** p, const std::vector<T>& v) {
@@ -141,6 +176,7 @@ int upload(hhg_mesh* m, T** p, const std::vector<T>& v) {
 void free_all(hhg_mesh* m) {
   for (void* p : m->allocs) cudaFree(p);
   m->allocs.clear();
+  m->alloc_bytes.clear();
 }
 
 LevelArgs largs(const hhg_mesh* m, int l) {
@@ -420,6 +456,12 @@ int setup_fault(hhg_mesh* m, const std::vector<unsigned char>& set) {
   } catch (const std::exception& e) {
     return fail(HHG_ERR_ARG, std::string("fault set: ") + e.what());
   }
+  // the previous set's sub-problems and lists (and the DN problem built on
+  // them) are replaced
+  release(m, m->dn_allocs);
+  m->has_dn = false;
+  release(m, m->fault_allocs);
+  Collect keep(m, m->fault_allocs);
   HHG_TRY(upload_problem(m, hf, m->faulty));
   HHG_TRY(upload_problem(m, hh, m->healthy));
   // finest-level fault bookkeeping: masters inside Omega_F are erased; every
@@ -514,6 +556,11 @@ int setup_dn(hhg_mesh* m, const std::vector<unsigned char>& set) {
   } catch (const std::exception& e) {
     return fail(HHG_ERR_ARG, std::string("fault set: ") + e.what());
   }
+  const size_t nI = (size_t)std::max(1, m->host.lv.back().n_if);
+  for (int b = 0; b < 2; ++b)       // the snapshots live as long as the mesh
+    if (!m->dn_snap[b]) HHG_TRY(dalloc(m, &m->dn_snap[b], nI));
+  release(m, m->dn_allocs);
+  Collect keep(m, m->dn_allocs);
   m->dn = DevProblem();
   HHG_TRY(upload_problem(m, hd, m->dn));
   const int L = (int)m->host.lv.size() - 1;
@@ -537,10 +584,7 @@ int setup_dn(hhg_mesh* m, const std::vector<unsigned char>& set) {
   HHG_TRY(upload(m, &m->dn_off, off));
   HHG_TRY(upload(m, &m->dn_master, mst));
   m->n_dn_copy = (int)off.size();
-  const size_t nI = (size_t)std::max(1, H.n_if);
   HHG_TRY(dalloc(m, &m->dn.fI_top, nI));
-  for (int b = 0; b < 2; ++b)
-    if (!m->dn_snap[b]) HHG_TRY(dalloc(m, &m->dn_snap[b], nI));
   if (!m->ev_dn_e) {
     HHG_CUDA(cudaEventCreateWithFlags(&m->ev_dn_e, cudaEventDisableTiming));
     for (int b = 0; b < 2; ++b) HHG_CUDA(cudaEventCreateWithFlags(&m->ev_dn_r[b], cudaEventDisableTiming));
@@ -1104,6 +1148,8 @@ int hhg_batch_create(hhg_mesh* global, int global_cycles, hhg_mesh* const* meshe
   b->graph = g;
   if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)
     return cleanup(fail(HHG_ERR_CUDA, "cudaGraphInstantiate failed"));
+  // the graph holds the meshes' buffers: a new fault set may not free them
+  for (auto& t : b->tasks) ++t.mesh->batch_refs;
   *out = b.release();
   return HHG_OK;
 }
@@ -1129,6 +1175,7 @@ int hhg_batch_destroy(hhg_batch* b) {
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   for (auto& t : b->tasks) {
+    --t.mesh->batch_refs;
     if (t.stream) cudaStreamDestroy(t.stream);
     if (t.done) cudaEventDestroy(t.done);
     if (t.done_time) cudaEventDestroy(t.done_time);

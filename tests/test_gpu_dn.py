@@ -180,3 +180,20 @@ def test_dn_after_new_coefficients(hhg):
     O.dn_recover(m, uo, fo, ids, 2, 2.0)
     assert _rel(M.get_solution(), O.interior(uo)) <= RTOL_U
     M.close()
+
+
+def test_fault_sets_replace_each_other_without_growing_memory(hhg):
+    """Arming the mesh for another fault set frees the previous set's
+    sub-problems: device memory returns to the same size for the same set."""
+    sub, R = (2, 2, 2), 4
+    M = hhg.Mesh(sub, R)
+    M.set_problem(I.random_load(sub, R, seed=1), I.initial_guess(sub, R))
+    sizes = []
+    for ids in ([13], I.subcube_macros(sub, 1, 1, 1), [3, 4, 40], [13]):
+        M.vcycle()
+        M.inject_fault(ids)
+        M.recover_local(ids, 2, 1)
+        M.recover_dn(ids, 1, 2.0)
+        sizes.append(M.bytes())
+    assert sizes[3] == sizes[0], sizes
+    M.close()
