@@ -116,7 +116,10 @@ int hhg_residual_norm(hhg_mesh* mesh, double* out, void* stream);
  * their union Omega_F is re-initialised with zero.  The interface values on
  * Gamma survive in the face/edge/vertex containers and are written back into
  * the ghost shells of the lost blocks (Eq. (4), row 4; Algorithm 1 step 4).
- * Ids must be distinct and in [0, n_macro). */
+ * Ids must be distinct and in [0, n_macro).  The first call for a set builds
+ * the set's recovery sub-problems on the device; a call with another set
+ * replaces them and frees the previous ones (after synchronising the
+ * device), except while a batch (hhg_batch_create) refers to the mesh. */
 int hhg_inject_fault(hhg_mesh* mesh, const int* macro_ids, int n_ids, void* stream);
 
 /* Recovery after hhg_inject_fault on the same ids.  n_local V-cycles of the
