@@ -136,39 +136,15 @@ __device__ __forceinline__ int row_items(int N, int j, int k, int c, bool colour
   return ((N - 1 - j - k) >> 2) + 1;
 }
 
-// An interior tile holds row pairs p = t.j0 .. t.j0 + t.m0 - 1 of slice t.k,
-// pair p being rows 1 + p and J - p (J = N - 2 - k).  The CTA flattens the
-// items of all its pairs into one range so that every lane has work:
-// s_pre[q] = items of pairs t.j0 .. t.j0 + q - 1 (warp 0 computes it with a
-// warp scan).  Returns the tile's item count.  All threads must call it.
-__device__ __forceinline__ int flat_setup(const Tile& t, int N, int c, bool colour, int* s_pre, int vw = 1) {
-  const int k = t.k, J = N - 2 - k;
-  if (threadIdx.y == 0) {
-    const int q = threadIdx.x;
-    int len = 0;
-    if (q < t.m0) {
-      const int j1 = 1 + t.j0 + q, j2 = J - t.j0 - q;
-      if (j1 <= j2) {
-        len = row_items(N, j1, k, c, colour, vw);
-        if (j2 > j1) len += row_items(N, j2, k, c, colour, vw);
-      }
-    }
-    for (int o = 1; o < 32; o <<= 1) {
-      const int y = __shfl_up_sync(0xffffffffu, len, o);
-      if (q >= o) len += y;
-    }
-    s_pre[q + 1] = len;
-    if (q == 0) s_pre[0] = 0;
-  }
-  __syncthreads();
-  return s_pre[t.m0];
-}
-
-// All slices of a tile at once: s_pre[s] is the pair prefix of slice t.k + s
-// (as flat_setup), s_tot[s] the items of slices t.k .. t.k + s - 1.  One CTA
-// barrier for the whole tile, so that the threads stream through the items
-// of all its slices without waiting for each other.  Returns the tile's item
-// count.  All threads must call it.
+// An interior tile holds row pairs p = t.j0 .. t.j0 + t.m0 - 1 of slices t.k ..
+// t.k + t.pad - 1, pair p being rows 1 + p and J - p of a slice (J = N - 2 -
+// k).  The CTA flattens the items of all its pairs and slices into one range
+// so that every lane has work: s_pre[s][q] = items of pairs t.j0 .. t.j0 + q -
+// 1 in slice t.k + s (one warp per slice computes it with a warp scan), and
+// s_tot[s] the items of slices t.k .. t.k + s - 1.  One CTA barrier for the
+// whole tile, so that the threads stream through the items of all its slices
+// without waiting for each other.  Returns the tile's item count.  All
+// threads must call it.
 constexpr int MAX_SLABS = 16;
 __device__ __forceinline__ int flat_setup_slabs(const Tile& t, int N, int c, bool colour, int vw,
                                                 int (*s_pre)[33], int* s_tot) {
@@ -534,7 +510,6 @@ __global__ void __launch_bounds__(CTA, 5) k_gs(int N, const int* __restrict__ rs
                                             int n_act, int colour, const int* __restrict__ cptr,
                                             const Copy* __restrict__ cps, const int* __restrict__ list, int n_list,
                                             int n_if_units, int* __restrict__ sched) {
-  __shared__ int s_pre[33];
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
   __shared__ int s_unit;
@@ -573,29 +548,30 @@ __global__ void __launch_bounds__(CTA, 5) k_gs(int N, const int* __restrict__ rs
         flat_item(ts, N, colour, true, s_pre2[sl], tt - s_pre_tot[sl], j, g, VW);
         gs_group7<T>(slice_consts(rs, N, k), N, j, g, colour, ub, fb, wr, inv);
       }
-      __syncthreads();
-      continue;
-    }
-    for (int k = t.k; k < t.k + t.pad; ++k) {
-    const Tile ts{k, t.j0, t.m0, 1};
-    const int total = flat_setup(ts, N, colour, true, s_pre);
-    for (int tt = tid256(); tt < total; tt += CTA) {
-      int j, v, ic, mlo, n;
-      flat_item(ts, N, colour, true, s_pre, tt, j, v);
-      colour_row(N, j, k, colour, ic, mlo, n);
-      const int i = 4 * (mlo + v) + ic;
-      const int me = lidx32(rs, N, i, j, k);
-      T acc = fb[me];
+    } else {
+      // 15-point: one colour-c node per item
+      const int total = flat_setup_slabs(t, N, colour, true, 1, s_pre2, s_pre_tot);
+      int sl = 0;
+      for (int tt = tid256(); tt < total; tt += CTA) {
+        while (tt >= s_pre_tot[sl + 1]) ++sl;
+        const int k = t.k + sl;
+        const Tile ts{k, t.j0, t.m0, 1};
+        int j, v, ic, mlo, n;
+        flat_item(ts, N, colour, true, s_pre2[sl], tt - s_pre_tot[sl], j, v);
+        colour_row(N, j, k, colour, ic, mlo, n);
+        const int i = 4 * (mlo + v) + ic;
+        const int me = lidx32(rs, N, i, j, k);
+        T acc = fb[me];
 #pragma unroll
-      for (int d = 1; d < NDIR; ++d) {
-        int di, dj, dk;
-        dir_ijk(d, di, dj, dk);
-        acc -= w[d] * ub[lidx32(rs, N, i + di, j + dj, k + dk)];
+        for (int d = 1; d < NDIR; ++d) {
+          int di, dj, dk;
+          dir_ijk(d, di, dj, dk);
+          acc -= w[d] * ub[lidx32(rs, N, i + di, j + dj, k + dk)];
+        }
+        ub[me] = acc * inv;
       }
-      ub[me] = acc * inv;
     }
     __syncthreads();
-    }
   }
   finish_units(sched, n_if_units + n_tiles * n_act);
 }
@@ -613,7 +589,6 @@ __global__ void __launch_bounds__(CTA, sizeof(T) == 8 ? 6 : 5) k_res(int N, cons
                                              const int* __restrict__ list, int n_list,
                                              const int64_t* __restrict__ zero_off, int n_zero, int n_if_units,
                                              double* __restrict__ partial, int* __restrict__ sched) {
-  __shared__ int s_pre[33];
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
   __shared__ double sh[32];
@@ -661,28 +636,15 @@ __global__ void __launch_bounds__(CTA, sizeof(T) == 8 ? 6 : 5) k_res(int N, cons
       }
       continue;
     }
+    // 15-point: four nodes of one slot per item
     HHG_TILE_NODES(N, rs, t, s_pre, {
-      int me;
-      T acc;
-      if (S7) {
-        const Nb7 q = nb7(sc, i, j);
-        me = q.me;
-        acc = fb[me] - w[0] * ub[me];
-        acc -= w[1] * ub[q.nb1];
-        acc -= w[2] * ub[q.nb2];
-        acc -= w[3] * ub[q.nb3];
-        acc -= w[8] * ub[q.nb8];
-        acc -= w[9] * ub[q.nb9];
-        acc -= w[10] * ub[q.nb10];
-      } else {
-        me = lidx32(rs, N, i, j, k);
-        acc = fb[me] - w[0] * ub[me];
+      const int me = lidx32(rs, N, i, j, k);
+      T acc = fb[me] - w[0] * ub[me];
 _Pragma("unroll")
-        for (int d = 1; d < NDIR; ++d) {
-          int di, dj, dk;
-          dir_ijk(d, di, dj, dk);
-          acc -= w[d] * ub[lidx32(rs, N, i + di, j + dj, k + dk)];
-        }
+      for (int d = 1; d < NDIR; ++d) {
+        int di, dj, dk;
+        dir_ijk(d, di, dj, dk);
+        acc -= w[d] * ub[lidx32(rs, N, i + di, j + dj, k + dk)];
       }
       if (WRITE) rb[me] = acc;
       if (NORM) ss += (double)acc * (double)acc;
@@ -707,7 +669,6 @@ __global__ void __launch_bounds__(CTA) k_restrict(int Nc, const int* __restrict_
                                                   const int* __restrict__ list, int n_list,
                                                   const int64_t* __restrict__ gather,
                                                   const int64_t* __restrict__ zero_off, int n_zero, int n_if_units, int* __restrict__ sched) {
-  __shared__ int s_pre[33];
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
   __shared__ int s_unit;
@@ -784,7 +745,6 @@ __global__ void __launch_bounds__(CTA) k_prolong(int Nf, const int* __restrict__
                                                  const int* __restrict__ act, int n_act, const int* __restrict__ cptr,
                                                  const Copy* __restrict__ cps, const int* __restrict__ list,
                                                  int n_list, int n_if_units, int* __restrict__ sched) {
-  __shared__ int s_pre[33];
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
   __shared__ int s_unit;
@@ -825,7 +785,6 @@ __global__ void __launch_bounds__(CTA) k_res_f32(int N, const int* __restrict__ 
                                                  const int* __restrict__ cptr, const Copy* __restrict__ cps,
                                                  const int* __restrict__ list, int n_list, int n_if_units,
                                                  double* __restrict__ partial, int* __restrict__ sched) {
-  __shared__ int s_pre[33];
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
   __shared__ double sh[32];
@@ -889,7 +848,6 @@ __global__ void __launch_bounds__(CTA) k_add_corr(int N, const int* __restrict__
                                                   int n_tiles, const int* __restrict__ act, int n_act,
                                                   const int* __restrict__ cptr, const Copy* __restrict__ cps,
                                                   const int* __restrict__ list, int n_list, int n_if_units, int* __restrict__ sched) {
-  __shared__ int s_pre[33];
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
   __shared__ int s_unit;
