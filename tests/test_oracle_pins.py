@@ -458,3 +458,34 @@ def test_two_faults_equal_the_sequence_of_single_fault_steps():
                 O.vcycle(m, m.local_problem(ids), top, v, f)
             O.vcycle(m, m.healthy_problem(ids), top, v, f)
     assert np.abs(O.interior(v) - O.interior(u)).max() == 0.0
+
+
+def test_strategy_ordering_of_the_cycle_advantage():
+    """§4.4 and Tab. 1: for every superman factor and n_I, DN is at least as
+    good as DD and DD at least as good as LR, none is worse than do-nothing
+    (n_I = 0), and with n_I >= 1 each beats do-nothing; scenarios I (refined
+    5 times) and II (refined 4 times), fault after 5 cycles."""
+    import math
+    for si, (name, sub, ids) in enumerate(I.kappa_scenarios()[:2]):
+        R = 5 if si == 0 else 4
+        m = O.Mesh(sub, R)
+        f = O.pad(I.random_load(sub, R, seed=0))
+        u0 = O.pad(I.initial_guess(sub, R))
+        free = O.solve(m, u0.copy(), f, rtol=1e-10, max_cycles=60)["cycles"]
+        for eta in (2.0, 5.0):
+            nothing = None
+            for n_I in range(4):
+                kap = []
+                for rec in (O.LR, O.DD, O.DN):
+                    kw = dict(fault_cycle=5, fault_ids=ids, recovery=rec)
+                    if rec == O.LR:
+                        kw["n_local"] = int(math.ceil(eta * n_I))
+                    else:
+                        kw.update(n_global=n_I, eta=eta)
+                    r = O.solve(m, u0.copy(), f, rtol=1e-10, max_cycles=60, **kw)
+                    kap.append(O.kappa(r["cycles"] + n_I, free, 5))
+                if n_I == 0:
+                    nothing = kap[0]
+                    assert kap == [nothing] * 3
+                else:
+                    assert kap[2] <= kap[1] <= kap[0] < nothing, (name, eta, n_I, kap)
