@@ -86,6 +86,15 @@ struct hhg_mesh {
   double* staging = nullptr;
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // one recovery cycle of the faulty problem captured as a CUDA graph and
+  // replayed for the later cycles of a recovery (few macros, many small
+  // launches); valid for the current fault set and cycle parameters
+  cudaStream_t cap = nullptr;
+  cudaGraphExec_t local_exec = nullptr;
+  bool local_failed = false;
+  bool local_mixed = false;
+  int local_pre = 0, local_post = 0, local_maxit = 0;
+  double local_rtol = 0.0;
   std::vector<void*> allocs;
   std::unordered_map<void*, int64_t> alloc_bytes;
   // allocations of the current fault set (its sub-problems and lists), freed
@@ -417,6 +426,56 @@ int cycle(hhg_mesh* m, DevProblem& p, bool mixed, int pre, int post, double cg_r
   return vcycle_T<double>(m, m->d64, p, pre, post, cg_rtol, cg_maxit, s);
 }
 
+void drop_local_graph(hhg_mesh* m) {
+  if (m->local_exec) cudaGraphExecDestroy(m->local_exec);
+  m->local_exec = nullptr;
+  m->local_failed = false;
+}
+
+// n cycles of the faulty problem on stream ls: the first one directly (it
+// also fills the launch-shape caches), the others as replays of one captured
+// cycle (captured on the mesh's own stream, so ls may be the legacy stream).
+// Where capture is not possible the cycles run directly.
+int local_cycles(hhg_mesh* m, int n, bool mixed, int pre, int post, double cg_rtol, int cg_maxit, cudaStream_t ls) {
+  if (n <= 0) return HHG_OK;
+  HHG_TRY(cycle(m, m->faulty, mixed, pre, post, cg_rtol, cg_maxit, ls));
+  if (n == 1) return HHG_OK;
+  const bool same = m->local_mixed == mixed && m->local_pre == pre && m->local_post == post &&
+                    m->local_rtol == cg_rtol && m->local_maxit == cg_maxit;
+  if (!same) drop_local_graph(m);
+  // inside a caller's own stream capture the cycles are recorded directly
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  HHG_CUDA(cudaStreamIsCapturing(ls, &cs));
+  if (cs != cudaStreamCaptureStatusNone) {
+    for (int c = 1; c < n; ++c) HHG_TRY(cycle(m, m->faulty, mixed, pre, post, cg_rtol, cg_maxit, ls));
+    return HHG_OK;
+  }
+  if (!m->local_exec && !m->local_failed) {
+    cudaGraph_t g = nullptr;
+    bool ok = cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    int rc = HHG_OK;
+    if (ok) rc = cycle(m, m->faulty, mixed, pre, post, cg_rtol, cg_maxit, m->cap);
+    if (ok) ok = cudaStreamEndCapture(m->cap, &g) == cudaSuccess && rc == HHG_OK && g;
+    if (ok) ok = cudaGraphInstantiate(&m->local_exec, g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+    if (!ok) {
+      cudaGetLastError();
+      m->local_exec = nullptr;
+      m->local_failed = true;
+    }
+    m->local_mixed = mixed;
+    m->local_pre = pre;
+    m->local_post = post;
+    m->local_rtol = cg_rtol;
+    m->local_maxit = cg_maxit;
+  }
+  for (int c = 1; c < n; ++c) {
+    if (m->local_exec) HHG_CUDA(cudaGraphLaunch(m->local_exec, ls));
+    else HHG_TRY(cycle(m, m->faulty, mixed, pre, post, cg_rtol, cg_maxit, ls));
+  }
+  return HHG_OK;
+}
+
 const double* stage_in(hhg_mesh* m, const double* g, cudaStream_t s, int* rc) {
   *rc = HHG_OK;
   cudaPointerAttributes at;
@@ -458,6 +517,7 @@ int setup_fault(hhg_mesh* m, const std::vector<unsigned char>& set) {
   }
   // the previous set's sub-problems and lists (and the DN problem built on
   // them) are replaced
+  drop_local_graph(m);
   release(m, m->dn_allocs);
   m->has_dn = false;
   release(m, m->fault_allocs);
@@ -513,7 +573,7 @@ int recover(hhg_mesh* m, int n_local, int n_global, bool mixed, int pre, int pos
     HHG_CUDA(cudaStreamWaitEvent(m->side, m->ev_fork, 0));
   }
   if (timed) HHG_CUDA(cudaEventRecord(a0, s));
-  for (int c = 0; c < n_local; ++c) HHG_TRY(cycle(m, m->faulty, mixed, pre, post, cg_rtol, cg_maxit, s));
+  HHG_TRY(local_cycles(m, n_local, mixed, pre, post, cg_rtol, cg_maxit, s));
   if (timed) HHG_CUDA(cudaEventRecord(a1, s));
   if (n_global > 0) {
     if (timed) HHG_CUDA(cudaEventRecord(b0, m->side));
@@ -629,7 +689,7 @@ int recover_dn(hhg_mesh* m, int n_global, double eta, bool mixed, int pre, int p
     if (j >= 2)
       HHG_CUDA(restore_copies(D.u, m->dn_snap[(j - 1) & 1], m->dn_off, m->dn_master, m->n_dn_copy, m->side));
     HHG_CUDA(cudaEventRecord(m->ev_dn_r[j & 1], m->side));
-    for (int c = 0; c < cyc; ++c) HHG_TRY(cycle(m, m->faulty, mixed, pre, post, cg_rtol, cg_maxit, m->side));
+    HHG_TRY(local_cycles(m, cyc, mixed, pre, post, cg_rtol, cg_maxit, m->side));
     total += cyc;
     // Omega_I, cycle j; its snapshot overwrites the one block j - 1 read
     HHG_TRY(cycle(m, m->dn, mixed, pre, post, cg_rtol, cg_maxit, s));
@@ -884,6 +944,7 @@ int hhg_mesh_create(const hhg_mesh_desc* desc, hhg_mesh** out) {
   }
   if (rc != HHG_OK) return cleanup(rc);
   if (cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaMallocHost(&m->host_scalar, sizeof(double) * 8) != cudaSuccess) {
@@ -899,7 +960,9 @@ int hhg_mesh_destroy(hhg_mesh* m) {
   if (!m) return HHG_OK;
   cudaDeviceSynchronize();
   free_all(m);
+  if (m->local_exec) cudaGraphExecDestroy(m->local_exec);
   if (m->side) cudaStreamDestroy(m->side);
+  if (m->cap) cudaStreamDestroy(m->cap);
   if (m->ev_fork) cudaEventDestroy(m->ev_fork);
   if (m->ev_join) cudaEventDestroy(m->ev_join);
   if (m->ev_dn_e) cudaEventDestroy(m->ev_dn_e);
@@ -1053,6 +1116,7 @@ int hhg_autotune(hhg_mesh* m, int reps, int* chosen, void* stream) {
   if (!m || reps < 1) return fail(HHG_ERR_ARG, "invalid argument");
   cudaStream_t s = (cudaStream_t)stream;
   const int nl = (int)m->host.lv.size();
+  drop_local_graph(m);
   for (int l = 1; l < nl; ++l) {
     int best = 0;
     if (m->precision == 32) HHG_TRY(tune_level<float>(m, m->d32, l, reps, s, &best));
