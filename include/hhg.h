@@ -270,7 +270,10 @@ int hhg_vcycle_noalloc(hhg_mesh* mesh, int pre, int post, void* stream);
  * hhg_profile_info: volume-interior nodes of the finest level (the nodes one
  * sweep of all four colours of that kernel updates) and whether the stencil
  * has the 7-point structure (only the six axis neighbours non-zero).
- * hhg_launch_count: kernel launches issued by the library in this process. */
+ * hhg_launch_count: kernel launches issued by the library in this process;
+ * each kernel of a CUDA graph the library replays (batched recovery, the
+ * later cycles of a local recovery) counts as one launch per replay, kernels
+ * recorded while capturing such a graph do not count. */
 int hhg_profile_enable(hhg_mesh* mesh, int enable);
 int hhg_profile_read(hhg_mesh* mesh, int64_t* launches, double* total_ms);
 int hhg_profile_info(const hhg_mesh* mesh, int64_t* volume_nodes, int* seven_point);

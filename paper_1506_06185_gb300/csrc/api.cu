@@ -91,6 +91,7 @@ struct hhg_mesh {
   // launches); valid for the current fault set and cycle parameters
   cudaStream_t cap = nullptr;
   cudaGraphExec_t local_exec = nullptr;
+  long long local_kernels = 0;  // kernels in the captured cycle
   bool local_failed = false;
   bool local_mixed = false;
   int local_pre = 0, local_post = 0, local_maxit = 0;
@@ -126,6 +127,7 @@ struct hhg_batch {
   cudaEvent_t start = nullptr, fork = nullptr;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  long long kernels = 0;  // kernels in the graph
 };
 
 namespace {
@@ -454,7 +456,11 @@ int local_cycles(hhg_mesh* m, int n, bool mixed, int pre, int post, double cg_rt
     cudaGraph_t g = nullptr;
     bool ok = cudaStreamBeginCapture(m->cap, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
     int rc = HHG_OK;
+    // captured kernels are counted as launches when the graph replays them
+    const long long k0 = g_kernel_launches.load();
     if (ok) rc = cycle(m, m->faulty, mixed, pre, post, cg_rtol, cg_maxit, m->cap);
+    m->local_kernels = g_kernel_launches.load() - k0;
+    g_kernel_launches -= m->local_kernels;
     if (ok) ok = cudaStreamEndCapture(m->cap, &g) == cudaSuccess && rc == HHG_OK && g;
     if (ok) ok = cudaGraphInstantiate(&m->local_exec, g, 0) == cudaSuccess;
     if (g) cudaGraphDestroy(g);
@@ -470,8 +476,10 @@ int local_cycles(hhg_mesh* m, int n, bool mixed, int pre, int post, double cg_rt
     m->local_maxit = cg_maxit;
   }
   for (int c = 1; c < n; ++c) {
-    if (m->local_exec) HHG_CUDA(cudaGraphLaunch(m->local_exec, ls));
-    else HHG_TRY(cycle(m, m->faulty, mixed, pre, post, cg_rtol, cg_maxit, ls));
+    if (m->local_exec) {
+      HHG_CUDA(cudaGraphLaunch(m->local_exec, ls));
+      g_kernel_launches += m->local_kernels;
+    } else HHG_TRY(cycle(m, m->faulty, mixed, pre, post, cg_rtol, cg_maxit, ls));
   }
   return HHG_OK;
 }
@@ -1185,6 +1193,7 @@ int hhg_batch_create(hhg_mesh* global, int global_cycles, hhg_mesh* const* meshe
   if (cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     return cleanup(fail(HHG_ERR_CUDA, "cudaStreamBeginCapture failed"));
   int rc = HHG_OK;
+  const long long k0 = g_kernel_launches.load();
   // timing events are captured as event-record nodes (External); fork and
   // join events only order the branches
   if (cudaEventRecordWithFlags(b->start, b->origin, cudaEventRecordExternal) != cudaSuccess ||
@@ -1202,6 +1211,9 @@ int hhg_batch_create(hhg_mesh* global, int global_cycles, hhg_mesh* const* meshe
                          cudaStreamWaitEvent(b->origin, task.done, 0) != cudaSuccess))
       rc = fail(HHG_ERR_CUDA, "join in capture failed");
   }
+  // captured kernels are counted as launches when the graph runs
+  b->kernels = g_kernel_launches.load() - k0;
+  g_kernel_launches -= b->kernels;
   cudaGraph_t g = nullptr;
   const cudaError_t ec = cudaStreamEndCapture(b->origin, &g);
   if (rc != HHG_OK) {
@@ -1222,6 +1234,7 @@ int hhg_batch_launch(hhg_batch* b, double* task_ms, void* stream) {
   if (!b) return fail(HHG_ERR_ARG, "null batch");
   cudaStream_t s = (cudaStream_t)stream;
   HHG_CUDA(cudaGraphLaunch(b->exec, s));
+  g_kernel_launches += b->kernels;
   if (task_ms) {
     HHG_CUDA(cudaStreamSynchronize(s));
     for (size_t t = 0; t < b->tasks.size(); ++t) {

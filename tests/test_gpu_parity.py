@@ -184,6 +184,39 @@ def test_recover_local_matches_oracle_and_reports_times(hhg):
     M.close()
 
 
+def test_replayed_local_cycles_match_oracle_and_count_launches(hhg):
+    # the later local cycles of a recovery replay one captured cycle; a second
+    # recovery on the same fault set reuses it, and every replayed kernel
+    # counts as a launch
+    sub, R = (2, 2, 2), 5
+    f = I.random_load(sub, R, seed=6)
+    M = hhg.Mesh(sub, R)
+    M.set_problem(f, I.initial_guess(sub, R))
+    m = O.Mesh(sub, R)
+    uo, fo = O.pad(I.initial_guess(sub, R)), O.pad(f)
+    top = len(m.levels) - 1
+    M.vcycle()
+    O.vcycle(m, m.global_problem, top, uo, fo)
+    ids = I.subcube_macros(sub, 0, 1, 1)
+    M.inject_fault(ids)
+    O.inject_fault(m, uo, ids)
+    lp = m.local_problem(ids)
+    deltas = []
+    for n in (1, 3, 5, 3):
+        l0 = hhg.hhg_launch_count()
+        M.recover_local(ids, n, 0)
+        deltas.append(hhg.hhg_launch_count() - l0)
+        for _ in range(n):
+            O.vcycle(m, lp, top, uo, fo)
+        assert _rel(M.get_solution(), O.interior(uo)) <= RTOL_U
+    per_cycle = (deltas[1] - deltas[0]) // 2
+    assert per_cycle > 0
+    assert deltas[1] - deltas[0] == 2 * per_cycle
+    assert deltas[2] - deltas[1] == 2 * per_cycle
+    assert deltas[3] == deltas[1]
+    M.close()
+
+
 @pytest.mark.slow
 def test_full_size_config2_sampled_residual(hhg):
     """2x2x2x6 macros refined 8 times (1.3e8 unknowns): converge on the GPU,
