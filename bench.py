@@ -278,8 +278,9 @@ def run_ours(args):
     # dominant kernel: finest-level FP64 Gauss-Seidel volume kernel (one colour per launch)
     n_vol, seven = hhg.hhg_profile_info(M.h)
     avg_s = prof_ms / max(n_prof, 1) * 1e-3
-    ops = 6 if seven else 14
-    flops_per_node = 2 * ops + 1          # DFMA per neighbour + one DMUL
+    # 7-point: f and the weights come divided by the centre weight, one DFMA
+    # per neighbour; 15-point: one DFMA per neighbour and the scaling DMUL
+    flops_per_node = 12 if seven else 2 * 14 + 1
     flops = flops_per_node * n_vol / 4.0
     achieved_tflops = flops / avg_s / 1e12
     hbm_peak, hbm_src = _peaks()

@@ -11,6 +11,7 @@
 #include <new>
 #include <stdexcept>
 #include <string>
+#include <type_traits>
 #include <unordered_map>
 #include <vector>
 
@@ -58,6 +59,10 @@ struct hhg_mesh {
   int precision = 64;
   std::vector<DevLevelTables> tab;
   Prec<double> d64;
+  // 7-point stencils: the finest level's f and interior weights divided by
+  // each macro's centre weight (the FP64 volume Gauss-Seidel reads these)
+  double* fs_top = nullptr;
+  double* wsc_top = nullptr;
   Prec<float> d32;
   MacroGeo* geo = nullptr;
   DevProblem global, faulty, healthy;
@@ -311,6 +316,34 @@ int alloc_levels(hhg_mesh* m, Prec<T>& P, bool with_r_on_finest) {
   return HHG_OK;
 }
 
+// The finest level's interior weights divided by the centre weight, per macro
+// (same table layout as W, other node classes zero), uploaded to wsc_top, and
+// fs_top = f scaled the same way (on the legacy stream, after the copies).
+int refresh_scaled(hhg_mesh* m) {
+  if (!m->wsc_top) return HHG_OK;
+  const int L = (int)m->host.lv.size() - 1;
+  const HostLevel& H = m->host.lv[L];
+  std::vector<double> w(H.W.size(), 0.0);
+  for (int t = 0; t < m->host.n_macro; ++t) {
+    const size_t o = (size_t)t * 16 * NDIR;
+    const double inv = 1.0 / H.W[o];
+    for (int d = 0; d < NDIR; ++d) w[o + d] = H.W[o + d] * inv;
+  }
+  HHG_CUDA(cudaMemcpy(m->wsc_top, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+  HHG_CUDA(scale_blocks(m->d64.lv[L].f, m->d64.Winv[L], m->fs_top, m->host.n_macro, H.block, 0));
+  HHG_CUDA(cudaStreamSynchronize(0));
+  return HHG_OK;
+}
+
+int alloc_scaled(hhg_mesh* m) {
+  if (!m->host.seven_point) return HHG_OK;
+  const int L = (int)m->host.lv.size() - 1;
+  const HostLevel& H = m->host.lv[L];
+  HHG_TRY(dalloc(m, &m->fs_top, (size_t)m->host.n_macro * H.block));
+  HHG_TRY(dalloc(m, &m->wsc_top, H.W.size()));
+  return refresh_scaled(m);
+}
+
 // One V(pre, post) cycle of problem p on the arrays of precision T.
 // A pair of events bracketing the next profiled launch (none when profiling
 // is off).
@@ -336,11 +369,18 @@ int smooth(hhg_mesh* m, Prec<T>& P, DevProblem& p, int l, int steps, cudaStream_
   const ProbArgs q = pargs(p, l);
   const T* fI = level_fI<T>(D, p, l == L);
   const bool prof = l == L && p.kind == 0;
+  const T* fs = nullptr;
+  const T* wsc = nullptr;
+  if constexpr (std::is_same<T, double>::value)
+    if (l == L) {
+      fs = m->fs_top;
+      wsc = m->wsc_top;
+    }
   for (int it = 0; it < steps; ++it)
     for (int c = 0; c < 4; ++c) {
       cudaEvent_t b = nullptr, e = nullptr;
       if (prof) HHG_TRY(prof_pair(m, &b, &e));
-      HHG_CUDA(gs_colour<T>(a, q, D.u, D.uI, D.f, fI, D.W, P.Winv[l], c, m->host.seven_point, s, b, e));
+      HHG_CUDA(gs_colour<T>(a, q, D.u, D.uI, D.f, fI, D.W, P.Winv[l], c, m->host.seven_point, s, b, e, fs, wsc));
     }
   return HHG_OK;
 }
@@ -755,6 +795,7 @@ int update_coefficients(hhg_mesh* m, const double* coeff) {
       HHG_CUDA(cudaMemcpy(m->d32.Winv[l], wi32.data(), wi32.size() * sizeof(float), cudaMemcpyHostToDevice));
     }
   }
+  HHG_TRY(refresh_scaled(m));
   // the Neumann-side problem of DN recovery (operator A_I, coarse matrix,
   // interface flux) is rebuilt from the new coefficients on its next use
   m->has_dn = false;
@@ -940,6 +981,7 @@ int hhg_mesh_create(const hhg_mesh_desc* desc, hhg_mesh** out) {
   }
   if (rc == HHG_OK) rc = upload(m.get(), &m->geo, m->host.geo);
   if (rc == HHG_OK) rc = alloc_levels<double>(m.get(), m->d64, true);
+  if (rc == HHG_OK) rc = alloc_scaled(m.get());
   if (rc == HHG_OK && m->precision == 32) rc = alloc_levels<float>(m.get(), m->d32, true);
   if (rc == HHG_OK) {
     HostProblem hg;
@@ -1008,6 +1050,8 @@ int hhg_set_problem(hhg_mesh* m, const double* f, const double* u0, void* stream
     if (!g) return rc;
     HHG_CUDA(import_vec<double>(a, m->geo, m->host.n_macro, m->host.nx, m->host.ny, g, D.f, D.fI, false, s));
     HHG_CUDA(import_masters<double>(a.if_gid, m->host.lv[L].n_if, g, D.fI, s));
+    if (m->fs_top)
+      HHG_CUDA(scale_blocks(D.f, m->d64.Winv[L], m->fs_top, m->host.n_macro, m->host.lv[L].block, s));
   }
   if (u0) {
     const double* g = stage_in(m, u0, s, &rc);

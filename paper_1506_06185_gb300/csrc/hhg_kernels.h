@@ -34,11 +34,19 @@ struct ProbArgs {
 // One colour of multicolour Gauss-Seidel on the volume interiors and the free
 // interface nodes of a problem.
 // If ev_begin / ev_end are not null they are recorded on s right before and
-// after the volume kernel (profiling of the dominant kernel).
+// after the volume kernel (profiling of the dominant kernel).  With the
+// 7-point stencil, fs and Wsc (both non-null) are f and the interior weights
+// divided by each macro's centre weight: the volume nodes are then updated as
+// u = fs - sum Wsc u (no final scaling); the interface nodes always use fI, W.
 template <class T>
 cudaError_t gs_colour(const LevelArgs& L, const ProbArgs& p, T* u, T* uI, const T* f, const T* fI,
                       const T* W, const T* Winv, int colour, bool seven_point, cudaStream_t s,
-                      cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr);
+                      cudaEvent_t ev_begin = nullptr, cudaEvent_t ev_end = nullptr, const T* fs = nullptr,
+                      const T* Wsc = nullptr);
+
+// out[t * block + o] = f[t * block + o] * winv[t] for the n_macro blocks.
+cudaError_t scale_blocks(const double* f, const double* winv, double* out, int n_macro, int64_t block,
+                         cudaStream_t s);
 
 // r = f - A u on the free nodes (written to the blocks' r), zero at the
 // problem's frozen copies.  If partial != NULL each CTA also writes its

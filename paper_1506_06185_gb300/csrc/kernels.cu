@@ -393,8 +393,10 @@ __device__ __forceinline__ void load_shifted(const T* __restrict__ p, bool up, b
 // 7-point update of the colour-c nodes in slots m0 .. m0 + VW - 1 of interior
 // row j of slice k (one aligned vector per stencil direction, plus one element
 // where the neighbour's slot is shifted by one); only the interior nodes among
-// them are written.
-template <class T>
+// them are written.  SCALED: the weights w and the load fb are already divided
+// by the centre weight (u = f~ - sum w~ u, six FMAs per node), else the sum is
+// multiplied by inv, the inverse centre weight.
+template <class T, bool SCALED>
 __device__ __forceinline__ void gs_group7(const Slice& sc, int N, int j, int g, int c, T* __restrict__ ub,
                                           const T* __restrict__ fb, const T* __restrict__ w, T inv) {
   constexpr int VW = Vec<T>::n;
@@ -429,7 +431,10 @@ __device__ __forceinline__ void gs_group7(const Slice& sc, int N, int j, int g, 
   for (int t = 0; t < VW; ++t) acc[t] -= w[9] * a[t];
   Vec<T>::load(ub + cm + rkm + m0, a);              // ( 0,  1, -1)
 #pragma unroll
-  for (int t = 0; t < VW; ++t) acc[t] = (acc[t] - w[10] * a[t]) * inv;
+  for (int t = 0; t < VW; ++t) {
+    if (SCALED) acc[t] -= w[10] * a[t];         // weights and f already divided by the centre weight
+    else acc[t] = (acc[t] - w[10] * a[t]) * inv;
+  }
   T* out = ub + cc + r0 + m0;
   const int lo = max(mlo - m0, 0), hi = min(mlo + n - m0, VW);
   if (lo == 0 && hi == VW) {
@@ -502,10 +507,33 @@ __device__ __forceinline__ void res_group7(const Slice& sc, int N, int j, int g,
   }
 }
 
+// The 7-point colour-c items of one tile: groups of VW consecutive same-colour
+// slots per thread, the items of all the tile's slices streamed in one pass.
+template <class T, bool SCALED>
+__device__ __forceinline__ void gs_tile7(const Tile& t, int N, const int* __restrict__ rs, int colour,
+                                         T* __restrict__ ub, const T* __restrict__ fb, const T* __restrict__ w, T inv,
+                                         int (*s_pre2)[33], int* s_pre_tot) {
+  constexpr int VW = Vec<T>::n;
+  const T wr[11] = {T(0), w[1], w[2], w[3], T(0), T(0), T(0), T(0), w[8], w[9], w[10]};
+  const int total = flat_setup_slabs(t, N, colour, true, VW, s_pre2, s_pre_tot);
+  int sl = 0;
+  for (int tt = tid256(); tt < total; tt += CTA) {
+    while (tt >= s_pre_tot[sl + 1]) ++sl;    // items only grow: the slice only advances
+    const int k = t.k + sl;
+    const Tile ts{k, t.j0, t.m0, 1};
+    int j, g;
+    flat_item(ts, N, colour, true, s_pre2[sl], tt - s_pre_tot[sl], j, g, VW);
+    gs_group7<T, SCALED>(slice_consts(rs, N, k), N, j, g, colour, ub, fb, wr, inv);
+  }
+}
+
+// fs / Wsc (7-point only, may be null): the volume nodes read f and the
+// interior weights already divided by their macro's centre weight.
 template <class T, bool S7>
 __global__ void __launch_bounds__(CTA, 5) k_gs(int N, const int* __restrict__ rs, int64_t block, T* __restrict__ u, T* __restrict__ uI,
                                             const T* __restrict__ f, const T* __restrict__ fI,
                                             const T* __restrict__ W, const T* __restrict__ Winv,
+                                            const T* __restrict__ fs, const T* __restrict__ Wsc,
                                             const Tile* __restrict__ tiles, int n_tiles, const int* __restrict__ act,
                                             int n_act, int colour, const int* __restrict__ cptr,
                                             const Copy* __restrict__ cps, const int* __restrict__ list, int n_list,
@@ -535,19 +563,11 @@ __global__ void __launch_bounds__(CTA, 5) k_gs(int N, const int* __restrict__ rs
     const T* w = W + (size_t)macro * 16 * NDIR;
     const T inv = Winv[macro];
     if (S7) {
-      // groups of VW consecutive same-colour slots per thread
-      constexpr int VW = Vec<T>::n;
-      const T wr[11] = {T(0), w[1], w[2], w[3], T(0), T(0), T(0), T(0), w[8], w[9], w[10]};
-      const int total = flat_setup_slabs(t, N, colour, true, VW, s_pre2, s_pre_tot);
-      int sl = 0;
-      for (int tt = tid256(); tt < total; tt += CTA) {
-        while (tt >= s_pre_tot[sl + 1]) ++sl;    // items only grow: the slice only advances
-        const int k = t.k + sl;
-        const Tile ts{k, t.j0, t.m0, 1};
-        int j, g;
-        flat_item(ts, N, colour, true, s_pre2[sl], tt - s_pre_tot[sl], j, g, VW);
-        gs_group7<T>(slice_consts(rs, N, k), N, j, g, colour, ub, fb, wr, inv);
-      }
+      if (Wsc)
+        gs_tile7<T, true>(t, N, rs, colour, ub, fs + (size_t)macro * block, Wsc + (size_t)macro * 16 * NDIR, T(1),
+                          s_pre2, s_pre_tot);
+      else
+        gs_tile7<T, false>(t, N, rs, colour, ub, fb, w, inv, s_pre2, s_pre_tot);
     } else {
       // 15-point: one colour-c node per item
       const int total = flat_setup_slabs(t, N, colour, true, 1, s_pre2, s_pre_tot);
@@ -1092,6 +1112,13 @@ __global__ void k_copy_listed(const double* __restrict__ src, double* __restrict
   if (q < n) dst[idx[q]] = src[idx[q]];
 }
 
+__global__ void k_scale_blocks(const double* __restrict__ f, const double* __restrict__ winv,
+                               double* __restrict__ out, int n_macro, int64_t block) {
+  const int64_t total = (int64_t)n_macro * block;
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < total; q += (int64_t)gridDim.x * blockDim.x)
+    out[q] = f[q] * winv[q / block];
+}
+
 __global__ void k_set_masters_zero(double* __restrict__ uI, const int* __restrict__ ids, int n) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q < n) uI[ids[q]] = 0.0;
@@ -1163,7 +1190,9 @@ inline unsigned resident_grid(const void* kernel, int total) {
 template <class T>
 cudaError_t gs_colour(const LevelArgs& L, const ProbArgs& p, T* u, T* uI, const T* f, const T* fI, const T* W,
                       const T* Winv, int colour, bool seven_point, cudaStream_t s, cudaEvent_t ev_begin,
-                      cudaEvent_t ev_end) {
+                      cudaEvent_t ev_end, const T* fs, const T* Wsc) {
+  if (!seven_point) fs = Wsc = nullptr;
+  if (!fs || !Wsc) fs = Wsc = nullptr;
   const int n = p.col_off[colour + 1] - p.col_off[colour];
   const Units g = units(n, L.n_tiles_int, p.n_act);
   if (g.total == 0) return cudaSuccess;
@@ -1171,7 +1200,7 @@ cudaError_t gs_colour(const LevelArgs& L, const ProbArgs& p, T* u, T* uI, const 
   const unsigned grid = resident_grid((const void*)kern, g.total);
   if (ev_begin) cudaEventRecord(ev_begin, s);
   ++g_kernel_launches;
-  kern<<<grid, cta_shape(), 0, s>>>(L.N, L.rs, L.block, u, uI, f, fI, W, Winv, L.tiles_int, L.n_tiles_int, p.act,
+  kern<<<grid, cta_shape(), 0, s>>>(L.N, L.rs, L.block, u, uI, f, fI, W, Winv, fs, Wsc, L.tiles_int, L.n_tiles_int, p.act,
                                     p.n_act, colour, L.cptr, L.cps, p.free_if + p.col_off[colour], n, g.n_if_units,
                                     p.sched);
   if (ev_end) cudaEventRecord(ev_end, s);
@@ -1336,6 +1365,17 @@ cudaError_t set_masters_zero(double* uI, const int* ids, int n, cudaStream_t s) 
   return cudaGetLastError();
 }
 
+cudaError_t scale_blocks(const double* f, const double* winv, double* out, int n_macro, int64_t block,
+                         cudaStream_t s) {
+  const int64_t total = (int64_t)n_macro * block;
+  if (total > 0) {
+    ++g_kernel_launches;
+    k_scale_blocks<<<(unsigned)std::min<int64_t>(lin_grid(total, 256), 152 * 16), 256, 0, s>>>(f, winv, out, n_macro,
+                                                                                               block);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t restore_copies(double* u, const double* uI, const int64_t* off, const int* master, int n, cudaStream_t s) {
   if (n > 0) {
     ++g_kernel_launches;
@@ -1390,7 +1430,8 @@ cudaError_t zero_problem_blocks(const LevelArgs& L, const ProbArgs& p, T* u, T* 
 
 #define HHG_INSTANTIATE(T)                                                                                        \
   template cudaError_t gs_colour<T>(const LevelArgs&, const ProbArgs&, T*, T*, const T*, const T*, const T*,   \
-                                    const T*, int, bool, cudaStream_t, cudaEvent_t, cudaEvent_t);               \
+                                    const T*, int, bool, cudaStream_t, cudaEvent_t, cudaEvent_t, const T*,      \
+                                    const T*);                                                                  \
   template cudaError_t residual<T>(const LevelArgs&, const ProbArgs&, const T*, const T*, const T*, const T*, T*, \
                                    const T*, bool, bool, double*, int*, cudaStream_t);                         \
   template cudaError_t restrict_to<T>(const LevelArgs&, const LevelArgs&, const ProbArgs&, const T*, T*, T*, T*, \
