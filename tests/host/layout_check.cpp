@@ -1,0 +1,133 @@
+// Host-side check of the blocked colour-split layout (hhg_internal.h) and of
+// the row-pair work tiles of the volume kernels (csrc/mesh.cpp), driven by
+// tests/test_host_layout.py.  Runs on the CPU; makes no CUDA call.
+//
+// usage: layout_check N_max
+// Checks every refinement N = 2 .. N_max and N = 256, 512, and prints one
+// line per failed property (exit status 1), else "ok".
+#include <cstdio>
+#include <cstdlib>
+#include <vector>
+
+#include "../../paper_1506_06185_gb300/csrc/hhg_internal.h"
+
+using namespace hhg;
+
+static int failures = 0;
+
+#define CHECK(cond, ...)                    \
+  do {                                      \
+    if (!(cond)) {                          \
+      if (failures < 20) {                  \
+        std::printf("N=%d: ", N);           \
+        std::printf(__VA_ARGS__);           \
+        std::printf("\n");                  \
+      }                                     \
+      ++failures;                           \
+    }                                       \
+  } while (0)
+
+// S(m) by its definition: the slots of rows of 1 .. m nodes, 4 ceil(l / 16) each.
+static int64_t slots_by_definition(int m) {
+  int64_t s = 0;
+  for (int l = 1; l <= m; ++l) s += 4 * ((l + 15) / 16);
+  return s;
+}
+
+static void check_layout(int N) {
+  std::vector<int> SL;
+  const int64_t block = build_slice_starts(N, SL);
+  const int CS = SL[N + 2];
+  CHECK(block == 4 * (int64_t)CS, "block %lld != 4 CS", (long long)block);
+  CHECK(CS % 64 == 0, "CS %d not a multiple of 64", CS);
+  // every lattice node gets its own slot, inside its colour's array; rows
+  // start on a multiple of four slots (16 bytes in FP32, two FP64 vectors)
+  std::vector<unsigned char> used((size_t)block, 0);
+  for (int k = 0; k <= N; ++k)
+    for (int j = 0; j + k <= N; ++j) {
+      const int M = N + 1 - k;
+      const int row = SL[k] + slot_prefix(M) - slot_prefix(M - j);
+      CHECK(row % 4 == 0, "row (%d, %d) starts at slot %d", j, k, row);
+      const int L = M - j;
+      CHECK(row + row_slots(L) <= CS, "row (%d, %d) ends past CS", j, k);
+      for (int i = 0; i + j + k <= N; ++i) {
+        const int c = (i + 2 * j + 3 * k) & 3;
+        const int o = lidx(SL.data(), N, i, j, k);
+        CHECK(o >= c * CS && o < (c + 1) * CS, "node (%d, %d, %d) outside colour array %d", i, j, k, c);
+        CHECK(o == c * CS + row + (i >> 2), "node (%d, %d, %d) not in slot i >> 2 of its row", i, j, k);
+        if (o >= 0 && o < block) {
+          CHECK(!used[o], "node (%d, %d, %d) shares slot %d", i, j, k, o);
+          used[o] = 1;
+        }
+      }
+      // the neighbour rows the vector kernels address from row (j, k):
+      // (j + 1, k) follows after row_slots(L), (j - 1, k) precedes by row_slots(L + 1)
+      if (j + k < N) CHECK(SL[k] + slot_prefix(M) - slot_prefix(M - j - 1) == row + row_slots(L), "row (%d+1, %d)", j, k);
+      if (j > 0) CHECK(SL[k] + slot_prefix(M) - slot_prefix(M - j + 1) == row - row_slots(L + 1), "row (%d-1, %d)", j, k);
+    }
+  // slice starts: slice k + 1 begins where slice k's S(N + 1 - k) slots end
+  for (int k = 0; k <= N; ++k) CHECK(SL[k + 1] - SL[k] == slot_prefix(N + 1 - k), "slice %d length", k);
+}
+
+static void check_pair_tiles(int N, int target, int slabs) {
+  if (N < 4) return;
+  std::vector<Tile> tiles;
+  build_pair_tiles(N, tiles, target, slabs);
+  // cover[k][j]: how often interior row j of slice k is covered
+  std::vector<std::vector<int>> cover(N + 1, std::vector<int>(N + 1, 0));
+  int64_t prev_work = -1;
+  for (size_t q = 0; q < tiles.size(); ++q) {
+    const Tile& t = tiles[q];
+    // the kernels' shared tables hold 16 slices of 32 pairs per tile
+    CHECK(t.pad >= 1 && t.pad <= 16, "tile %zu: %d slices (target %d, slabs %d)", q, t.pad, target, slabs);
+    CHECK(t.m0 >= 1 && t.m0 <= 32, "tile %zu: %d pairs", q, t.m0);
+    CHECK(t.k >= 1 && t.k + t.pad - 1 <= N - 3, "tile %zu: slices %d .. %d", q, t.k, t.k + t.pad - 1);
+    int64_t work = 0;
+    for (int k = t.k; k < t.k + t.pad && k <= N; ++k)
+      for (int p = t.j0; p < t.j0 + t.m0; ++p) {
+        const int j1 = 1 + p, j2 = N - 2 - k - p;
+        if (j1 > j2) continue;                      // beyond this slice's pairs: empty
+        ++cover[k][j1];
+        work += N - 1 - j1 - k;
+        if (j2 != j1) {
+          ++cover[k][j2];
+          work += N - 1 - j2 - k;
+        }
+      }
+    // largest tiles first
+    if (prev_work >= 0) CHECK(work <= prev_work, "tile %zu: work %lld after %lld", q, (long long)work, (long long)prev_work);
+    prev_work = work;
+  }
+  for (int k = 1; k <= N - 3; ++k)
+    for (int j = 1; j + k <= N - 2; ++j)
+      CHECK(cover[k][j] == 1, "interior row (%d, %d) covered %d times (target %d, slabs %d)", j, k, cover[k][j],
+            target, slabs);
+}
+
+int main(int argc, char** argv) {
+  if (argc < 2) return 2;
+  const int n_max = std::atoi(argv[1]);
+  // S(m) in closed form against its definition
+  for (int m = 0; m <= 1100; ++m) {
+    const int N = m;
+    CHECK(slot_prefix(m) == slots_by_definition(m), "S(%d) = %d, definition %lld", m, slot_prefix(m),
+          (long long)slots_by_definition(m));
+    if (m > 0) CHECK(slot_prefix(m) - slot_prefix(m - 1) == row_slots(m), "row_slots(%d)", m);
+  }
+  std::vector<int> ns;
+  for (int N = 2; N <= n_max; ++N) ns.push_back(N);
+  if (n_max < 256) ns.push_back(256);
+  if (n_max < 512) ns.push_back(512);
+  // default tiles and the autotuner's candidates (target nodes, slices)
+  const int cand[][2] = {{TILE_TARGET_DEFAULT, TILE_SLABS}, {256, 4}, {512, 8}, {1024, 8}, {2048, 16}};
+  for (int N : ns) {
+    check_layout(N);
+    for (const auto& c : cand) check_pair_tiles(N, c[0], c[1]);
+  }
+  if (failures) {
+    std::printf("%d failures\n", failures);
+    return 1;
+  }
+  std::printf("ok\n");
+  return 0;
+}
