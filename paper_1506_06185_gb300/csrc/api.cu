@@ -829,6 +829,7 @@ template <class T>
 int tune_level(hhg_mesh* m, Prec<T>& P, int l, int reps, cudaStream_t s, int* best_out) {
   const HostLevel& H = m->host.lv[l];
   DevLevelTables& tb = m->tab[l];
+  Tile* const before = tb.tiles_int;
   double best_ms = 1e30;
   int best = -1;
   std::vector<Tile*> dev(N_TUNE_CAND, nullptr);
@@ -860,6 +861,12 @@ int tune_level(hhg_mesh* m, Prec<T>& P, int l, int reps, cudaStream_t s, int* be
   tb.tiles_int = dev[best];
   tb.n_tiles_int = ndev[best];
   *best_out = best;
+  // the other candidates' tiles and the level's previous tiles are unused now
+  std::vector<void*> unused;
+  for (int c = 0; c < N_TUNE_CAND; ++c)
+    if (c != best && dev[c]) unused.push_back(dev[c]);
+  if (before && before != dev[best]) unused.push_back(before);
+  release(m, unused);
   return HHG_OK;
 }
 
