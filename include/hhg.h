@@ -17,7 +17,9 @@
  * ----------------------------------------
  * - Every call returns an int status (HHG_OK on success).  Nothing throws
  *   across the ABI.  hhg_last_error() gives a message for the last failure
- *   of the calling thread.
+ *   of the calling thread.  A NULL handle or a NULL required pointer is
+ *   rejected with HHG_ERR_ARG before any device use; destroying a NULL
+ *   handle is a no-op that returns HHG_OK.
  * - A mesh handle owns all device storage it allocates; the caller owns the
  *   vectors it passes in.  Handles are not thread-safe: one thread at a time.
  * - Global vectors (right-hand side, solution) are laid out over the global

@@ -47,3 +47,25 @@ def test_invalid_arguments_are_rejected_before_device_use():
         with pytest.raises(hhg.HHGError) as e:
             hhg.hhg_mesh_create(**kw)
         assert e.value.code == hhg.HHG_ERR_ARG
+
+
+def test_null_handles_are_rejected_without_device_use():
+    # every entry point called with NULL handles / pointers and zero sizes:
+    # HHG_ERR_ARG with a message, destroying NULL is a no-op (no GPU needed)
+    import ctypes as C
+    from paper_1506_06185_gb300 import hhg
+    lib = hhg.lib()
+    buf = C.create_string_buffer(256)
+    for name in hhg.EXPORTS:
+        if name == "hhg_last_error":
+            continue
+        fn = getattr(lib, name)
+        args = [0.0 if t is C.c_double else 0 if t in (C.c_int, C.c_size_t, C.c_int64) else None
+                for t in fn.argtypes]
+        rc = fn(*args)
+        if name.endswith("_destroy"):
+            assert rc == hhg.HHG_OK, name
+            continue
+        assert rc == hhg.HHG_ERR_ARG, (name, rc)
+        assert lib.hhg_last_error(buf, 256) == hhg.HHG_ERR_ARG
+        assert buf.value, name
