@@ -45,6 +45,25 @@ int fail(int code, const std::string& msg) {
     if (rc_ != HHG_OK) return rc_; \
   } while (0)
 
+// Timing events of one call, destroyed on every return path.
+struct CallEvents {
+  cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+  CallEvents() = default;
+  CallEvents(const CallEvents&) = delete;
+  CallEvents& operator=(const CallEvents&) = delete;
+  ~CallEvents() {
+    for (cudaEvent_t x : e)
+      if (x) cudaEventDestroy(x);
+  }
+  cudaError_t create(int n) {
+    for (int i = 0; i < n; ++i) {
+      const cudaError_t r = cudaEventCreate(&e[i]);
+      if (r != cudaSuccess) return r;
+    }
+    return cudaSuccess;
+  }
+};
+
 template <class T>
 struct Prec {
   std::vector<DevLevel<T>> lv;
@@ -608,14 +627,10 @@ int inject(hhg_mesh* m, cudaStream_t s) {
 
 int recover(hhg_mesh* m, int n_local, int n_global, bool mixed, int pre, int post, double cg_rtol, int cg_maxit,
             double* t_local, double* t_global, cudaStream_t s) {
-  cudaEvent_t a0, a1, b0, b1;
   const bool timed = t_local || t_global;
-  if (timed) {
-    HHG_CUDA(cudaEventCreate(&a0));
-    HHG_CUDA(cudaEventCreate(&a1));
-    HHG_CUDA(cudaEventCreate(&b0));
-    HHG_CUDA(cudaEventCreate(&b1));
-  }
+  CallEvents ev;
+  if (timed) HHG_CUDA(ev.create(4));
+  cudaEvent_t a0 = ev.e[0], a1 = ev.e[1], b0 = ev.e[2], b1 = ev.e[3];
   if (n_global > 0) {
     HHG_CUDA(cudaEventRecord(m->ev_fork, s));
     HHG_CUDA(cudaStreamWaitEvent(m->side, m->ev_fork, 0));
@@ -642,15 +657,10 @@ int recover(hhg_mesh* m, int n_local, int n_global, bool mixed, int pre, int pos
         *t_global = ms * 1e-3;
       }
     }
-    cudaEventDestroy(a0);
-    cudaEventDestroy(a1);
-    cudaEventDestroy(b0);
-    cudaEventDestroy(b1);
   }
   return HHG_OK;
 }
 
-// Stencils of all levels and the coarse CG matrices for new coefficients.
 // Dirichlet-Neumann recovery (§4.3, Algorithm 2).  Omega_I (kind 3) frees
 // every node with a healthy copy, Gamma included, under A_I; Omega_F (kind 1)
 // is the Dirichlet problem of the lost nodes.  Gamma is the set of free
@@ -716,13 +726,9 @@ int recover_dn(hhg_mesh* m, int n_global, double eta, bool mixed, int pre, int p
   DevLevel<double>& D = m->d64.lv[L];
   const size_t nI = (size_t)std::max(1, D.n_if) * sizeof(double);
   const bool timed = t_local || t_global;
-  cudaEvent_t a0 = nullptr, a1 = nullptr, b0 = nullptr, b1 = nullptr;
-  if (timed) {
-    HHG_CUDA(cudaEventCreate(&a0));
-    HHG_CUDA(cudaEventCreate(&a1));
-    HHG_CUDA(cudaEventCreate(&b0));
-    HHG_CUDA(cudaEventCreate(&b1));
-  }
+  CallEvents ev;
+  if (timed) HHG_CUDA(ev.create(4));
+  cudaEvent_t a0 = ev.e[0], a1 = ev.e[1], b0 = ev.e[2], b1 = ev.e[3];
   HHG_CUDA(cudaMemcpyAsync(m->dn.fI_top, D.fI, nI, cudaMemcpyDeviceToDevice, s));
   HHG_CUDA(apply_if_nodes(plargs(m, m->dn, L), D.u, D.uI, D.W, m->host.seven_point, m->dn_gamma, m->n_dn_gamma,
                           m->dn.fI_top, s));
@@ -768,14 +774,12 @@ int recover_dn(hhg_mesh* m, int n_global, double eta, bool mixed, int pre, int p
       HHG_CUDA(cudaEventElapsedTime(&ms, b0, b1));
       *t_global = ms * 1e-3;
     }
-    cudaEventDestroy(a0);
-    cudaEventDestroy(a1);
-    cudaEventDestroy(b0);
-    cudaEventDestroy(b1);
   }
   return HHG_OK;
 }
 
+// Stencils of all levels, the coarse CG matrices and the pre-divided finest
+// level arrays for new coefficients.
 int update_coefficients(hhg_mesh* m, const double* coeff) {
   try {
     set_coefficients(m->host, coeff);
@@ -834,9 +838,9 @@ int tune_level(hhg_mesh* m, Prec<T>& P, int l, int reps, cudaStream_t s, int* be
   int best = -1;
   std::vector<Tile*> dev(N_TUNE_CAND, nullptr);
   std::vector<int> ndev(N_TUNE_CAND, 0);
-  cudaEvent_t a, b;
-  HHG_CUDA(cudaEventCreate(&a));
-  HHG_CUDA(cudaEventCreate(&b));
+  CallEvents ev;
+  HHG_CUDA(ev.create(2));
+  cudaEvent_t a = ev.e[0], b = ev.e[1];
   for (int c = 0; c < N_TUNE_CAND; ++c) {
     std::vector<Tile> tiles;
     build_pair_tiles(H.N, tiles, TUNE_CAND[c][0], TUNE_CAND[c][1]);
@@ -856,8 +860,6 @@ int tune_level(hhg_mesh* m, Prec<T>& P, int l, int reps, cudaStream_t s, int* be
       best = c;
     }
   }
-  cudaEventDestroy(a);
-  cudaEventDestroy(b);
   tb.tiles_int = dev[best];
   tb.n_tiles_int = ndev[best];
   *best_out = best;
