@@ -99,7 +99,10 @@ int hhg_mesh_bytes(const hhg_mesh* mesh, int64_t* bytes);
 
 /* Load the right-hand side f (may be NULL: keep the current one, initially
  * zero) and the initial guess u0 including Dirichlet values (may be NULL:
- * keep the current iterate, initially zero) from global vectors. */
+ * keep the current iterate, initially zero) from global vectors.  With the
+ * 7-point stencil the mesh also keeps f divided by each macro's centre weight
+ * for the finest level's FP64 Gauss-Seidel; it is refreshed here and by
+ * hhg_set_coefficients. */
 int hhg_set_problem(hhg_mesh* mesh, const double* f, const double* u0, void* stream);
 
 /* Write the current fine-level iterate into the global vector u. */
@@ -130,7 +133,11 @@ int hhg_inject_fault(hhg_mesh* mesh, const int* macro_ids, int n_ids, void* stre
  * Dirichlet-Dirichlet recovery, n_global V-cycles of A_II u_I = f_I -
  * A_IG u_G on Omega_I with the interface frozen (step b) run concurrently on
  * a second stream.  If seconds_local / seconds_global are not NULL they
- * receive the device time of the two cycle sequences (synchronises). */
+ * receive the device time of the two cycle sequences (synchronises).  With
+ * n_local >= 2 the first Omega_F cycle runs directly and the others replay a
+ * CUDA graph of one cycle, captured on the first such call for the fault set
+ * and kept until the set, the cycle parameters or the tile shapes change
+ * (inside a caller's stream capture the cycles are recorded directly). */
 int hhg_recover_local(hhg_mesh* mesh, const int* macro_ids, int n_ids, int n_local,
                       int n_global, double* seconds_local, double* seconds_global,
                       void* stream);
@@ -145,9 +152,11 @@ int hhg_recover_local(hhg_mesh* mesh, const int* macro_ids, int n_ids, int n_loc
  * before Omega_I cycle j, ceil(j eta) - ceil((j - 1) eta) of them start on a
  * second stream from the values after Omega_I cycle j - 1, so the two sides
  * run concurrently.  On return the ghost copies of Gamma in the lost blocks
- * hold the final Gamma values.  *n_local_run (may be NULL) receives the
- * Omega_F cycles run, ceil(n_global eta).  seconds_local / seconds_global (may
- * be NULL) receive the device time spans of the two sides (synchronises).
+ * hold the final Gamma values (blocks of two or more Omega_F cycles replay
+ * the captured cycle graph described at hhg_recover_local).  *n_local_run
+ * (may be NULL) receives the Omega_F cycles run, ceil(n_global eta).
+ * seconds_local / seconds_global (may be NULL) receive the device time spans
+ * of the two sides (synchronises).
  * Errors: HHG_ERR_ARG for a NULL mesh, n_global < 0, eta < 0 or NaN, or an
  * invalid id list; CUDA errors as HHG_ERR_CUDA. */
 int hhg_recover_dn(hhg_mesh* mesh, const int* macro_ids, int n_ids, int n_global, double eta,
@@ -219,7 +228,9 @@ int hhg_grad_coeff(hhg_mesh* mesh, const double* u, const double* lam, double* g
  * precision (FP32 arrays for precision-32 meshes, otherwise the FP64
  * iterate, which the sweeps smooth) and keeps the fastest for that level.
  * chosen (may be NULL, one int per level, coarsest first) receives the index
- * of the chosen candidate (-1 for the coarsest level, which is not smoothed). */
+ * of the chosen candidate (-1 for the coarsest level, which is not smoothed).
+ * The tiles not kept are freed (after synchronising the device), except while
+ * a batch refers to the mesh. */
 int hhg_autotune(hhg_mesh* mesh, int reps, int* chosen, void* stream);
 
 /* Batched recovery in one CUDA-graph launch (the concurrency of §4.1's
