@@ -112,6 +112,26 @@ def macro_vertices(sub):
     return out
 
 
+def jittered_vertices(sub, seed=4, amp=0.12, move_boundary=True):
+    """Physical positions of the sub-cube corners, shape (sz+1, sy+1, sx+1, 3):
+    the unit cube's corner grid with every corner moved by a seeded uniform
+    offset of up to ``amp`` sub-cube edges per axis (Philox).  With
+    ``move_boundary`` false the corners on the cube's boundary stay put, so the
+    domain remains the unit cube; otherwise it becomes a general polyhedron.
+    The macro-tetrahedra then have general shapes (not congruent Kuhn
+    simplices)."""
+    sx, sy, sz = (int(s) for s in sub)
+    rng = np.random.Generator(np.random.Philox(int(seed)))
+    k, j, i = np.meshgrid(np.arange(sz + 1), np.arange(sy + 1), np.arange(sx + 1), indexing="ij")
+    base = np.stack([i / sx, j / sy, k / sz], axis=-1)
+    step = np.array([1.0 / sx, 1.0 / sy, 1.0 / sz])
+    off = rng.uniform(-amp, amp, size=base.shape) * step
+    if not move_boundary:
+        bnd = (i == 0) | (i == sx) | (j == 0) | (j == sy) | (k == 0) | (k == sz)
+        off[bnd] = 0.0
+    return base + off
+
+
 def grow_fault_set(sub, size, seed):
     """A connected set of ``size`` macros grown breadth-first (through shared
     faces) from a random seed macro, with a random visiting order."""

@@ -81,6 +81,17 @@ typedef struct {
                              NULL = all ones */
   const double* affine;   /* host, 3x3 row-major linear map applied to the
                              unit cube's node positions; NULL = identity */
+  const double* vertex_pos; /* host, physical positions of the
+                             (sx+1)(sy+1)(sz+1) sub-cube corners, 3 doubles
+                             each, corner (a, b, c) at index
+                             (c (sy+1) + b)(sx+1) + a; NULL = the unit cube's
+                             corners (mapped by affine).  Moved corners make
+                             every macro a general tetrahedron of a polyhedral
+                             domain with the cube family's connectivity (§2.1:
+                             unstructured base mesh, uniform refinement per
+                             macro); each macro must keep its Kuhn simplex's
+                             orientation (else HHG_ERR_ARG).  Not together
+                             with affine. */
 } hhg_mesh_desc;
 
 /* Build the macro mesh, all levels coarsest..levels, the per-macro stencils

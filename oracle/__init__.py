@@ -21,7 +21,10 @@ Multigrid Software at the Extreme Scale":
 
 Every function works on the global structured node grid of the cube family:
 the fine mesh of a cube split into Kuhn macro-tetrahedra and refined
-uniformly is the Freudenthal triangulation of that grid.  Per-macro blocked
+uniformly is the Freudenthal triangulation of that grid.  The macro vertices
+may also sit at arbitrary physical positions (general tetrahedral shapes of a
+polyhedral domain with the same connectivity, §2.1): each macro is then the
+image of its reference lattice under its own affine map.  Per-macro blocked
 storage is a GPU concern and is deliberately absent here.
 
 Parity status of each function is listed in ``oracle/hhg_oracle.py``.

@@ -45,7 +45,7 @@ __all__ = [
     "element_stiffness", "assemble_coo", "dia_to_csr", "apply_A",
     "gs_step", "residual", "restrict", "prolong", "cg", "vcycle",
     "resnorm", "inject_fault", "solve", "kappa", "grad_coeff",
-    "interior", "pad", "node_coords", "NONE", "LR", "DD", "DN", "local_residual", "dn_recover",
+    "interior", "pad", "node_coords", "macro_maps", "NONE", "LR", "DD", "DN", "local_residual", "dn_recover",
 ]
 
 # Lexicographic permutations of the axes (x=0, y=1, z=2).  Kuhn tetrahedron
@@ -99,15 +99,54 @@ def element_stiffness(X):
     return vol * (D @ D.T)
 
 
+def macro_maps(sub, affine=None, vertex_pos=None):
+    """Affine map of every macro-tetrahedron from sub-cube units to physical
+    space (§2.1: the base mesh is a tetrahedral mesh of a polyhedral domain and
+    every refinement is uniform inside a macro, so each macro's fine nodes are
+    the image of its reference lattice under that macro's affine map).
+
+    Macro t = 6 * sub-cube + Kuhn type has integer corner coordinates
+    V_0..V_3 (0, e_pi0, e_pi0 + e_pi1, (1,1,1) shifted to its sub-cube).
+    ``vertex_pos`` (shape (sz+1, sy+1, sx+1, 3), or None) gives the physical
+    position of every sub-cube corner; without it the corners sit at
+    G (V / sub), G = ``affine`` (identity if None).  Returns (V0, P0, M) with
+    x(s) = P0[t] + M[t] (s - V0[t]) for a point s in sub-cube units.
+    """
+    sx, sy, sz = (int(q) for q in sub)
+    G = np.eye(3) if affine is None else np.asarray(affine, dtype=np.float64)[:3, :3]
+    n = 6 * sx * sy * sz
+    V0 = np.zeros((n, 3))
+    P0 = np.zeros((n, 3))
+    M = np.zeros((n, 3, 3))
+    scale = np.array([sx, sy, sz], dtype=np.float64)
+    for c in range(sz):
+        for b in range(sy):
+            for a in range(sx):
+                for p, sigma in enumerate(PERMS):
+                    t = ((c * sy + b) * sx + a) * 6 + p
+                    corners = [np.array((a, b, c)) + np.array(o) for o in _kuhn_offsets(sigma)]
+                    if vertex_pos is None:
+                        P = [G @ (v / scale) for v in corners]
+                    else:
+                        P = [np.asarray(vertex_pos[v[2], v[1], v[0]], dtype=np.float64) for v in corners]
+                    EV = np.stack([corners[q] - corners[0] for q in (1, 2, 3)], axis=1).astype(np.float64)
+                    EP = np.stack([P[q] - P[0] for q in (1, 2, 3)], axis=1)
+                    V0[t], P0[t] = corners[0], P[0]
+                    M[t] = EP @ np.linalg.inv(EV)
+    return V0, P0, M
+
+
 class Level:
     """One refinement level of the cube macro mesh (§2.1, uniform refinement).
 
     Attributes: ``A`` (dict offset -> padded coefficient array), ``boundary``,
     ``colour`` ((x+y+z) mod 4), ``emacro`` (macro id of every fine tetrahedron,
-    per Kuhn type), ``Kel`` (unit-coefficient element stiffness per Kuhn type).
+    per Kuhn type), ``Kel`` (unit-coefficient element stiffness per Kuhn type:
+    one 4x4 matrix when the mesh is an affine image of the uniform grid, else
+    an array (n_macro, 4, 4), one per macro, from ``vertex_pos``).
     """
 
-    def __init__(self, sub, r, coeff, affine=None):
+    def __init__(self, sub, r, coeff, affine=None, vertex_pos=None):
         sx, sy, sz = (int(s) for s in sub)
         self.sub = (sx, sy, sz)
         self.n_macro = 6 * sx * sy * sz
@@ -141,13 +180,23 @@ class Level:
             self.emacro.append((slin * 6 + np.tile(pidx, (sz, sy, sx))).astype(np.int32))
         del lz, ly, lx, cz, cy, cx, slin
 
-        # Unit-coefficient element stiffness of the six Kuhn types: the mesh is
-        # an affine image of the uniform grid, so it does not depend on the cell.
+        # Unit-coefficient element stiffness of the six Kuhn types: for an
+        # affine image of the uniform grid it does not depend on the cell; with
+        # moved macro vertices it depends on the macro (its affine map).
         h = np.array([1.0 / nx, 1.0 / ny, 1.0 / nz])
+        self.vertex_pos = vertex_pos
         self.Kel = []
-        for sigma in PERMS:
-            X = np.array([G @ (np.array(o) * h) for o in _kuhn_offsets(sigma)])
-            self.Kel.append(element_stiffness(X))
+        if vertex_pos is None:
+            for sigma in PERMS:
+                X = np.array([G @ (np.array(o) * h) for o in _kuhn_offsets(sigma)])
+                self.Kel.append(element_stiffness(X))
+        else:
+            self.maps = macro_maps(self.sub, None, vertex_pos)
+            M = self.maps[2]
+            for sigma in PERMS:
+                offs = [np.array(o, dtype=np.float64) / N for o in _kuhn_offsets(sigma)]
+                self.Kel.append(np.stack([element_stiffness(np.array([M[t] @ o for o in offs]))
+                                          for t in range(self.n_macro)]))
 
         self.A = self._assemble_dia(np.asarray(coeff, dtype=np.float64))
         self.off = {d: d[2] * self.Py * self.Px + d[1] * self.Px + d[0] for d in self.A}
@@ -176,7 +225,8 @@ class Level:
                     arr = A.get(d)
                     if arr is None:
                         arr = A[d] = np.zeros(self.pshape)
-                    arr[sl] += kmap * K[a, b]
+                    kab = K[a, b] if K.ndim == 2 else K[:, a, b][self.emacro[s]]
+                    arr[sl] += kmap * kab
         # drop offsets whose coefficients are all exactly zero
         return {d: a for d, a in A.items() if d == (0, 0, 0) or np.any(a != 0.0)}
 
@@ -199,13 +249,36 @@ class Level:
         return interior(cnt), interior(cntf)
 
 
+def _node_macro(lv, x, y, z):
+    """A macro containing each grid node (x, y, z): the Kuhn simplex of its
+    sub-cube whose axis order sorts the node's sub-cube-local coordinates in
+    decreasing order (on shared faces any containing macro gives the same
+    position, as neighbouring macro maps agree there)."""
+    N = lv.N
+    sx, sy, sz = lv.sub
+    sc = [np.minimum(q // N, s - 1) for q, s in ((x, sx), (y, sy), (z, sz))]
+    loc = np.stack([x - sc[0] * N, y - sc[1] * N, z - sc[2] * N], axis=-1)
+    order = np.argsort(-loc, axis=-1, kind="stable")
+    lut = np.zeros(27, dtype=np.int64)
+    for i, p in enumerate(PERMS):
+        lut[p[0] * 9 + p[1] * 3 + p[2]] = i
+    pidx = lut[order[..., 0] * 9 + order[..., 1] * 3 + order[..., 2]]
+    return ((sc[2] * sy + sc[1]) * sx + sc[0]) * 6 + pidx
+
+
 def node_coords(lv):
     """Physical coordinates (x, y, z) of every node of a level."""
     x, y, z = lv.xyz
     nx, ny, nz = lv.n
-    p = np.stack([x / nx, y / ny, z / nz], axis=0)
-    X = np.tensordot(lv.G, p, axes=(1, 0))
-    return X[0], X[1], X[2]
+    if lv.vertex_pos is None:
+        p = np.stack([x / nx, y / ny, z / nz], axis=0)
+        X = np.tensordot(lv.G, p, axes=(1, 0))
+        return X[0], X[1], X[2]
+    V0, P0, M = lv.maps
+    t = _node_macro(lv, x, y, z)
+    s = np.stack([x, y, z], axis=-1) / lv.N - V0[t]
+    X = P0[t] + np.einsum("...ab,...b->...a", M[t], s)
+    return X[..., 0], X[..., 1], X[..., 2]
 
 
 def assemble_coo(lv, coeff):
@@ -228,8 +301,13 @@ def assemble_coo(lv, coeff):
             for cx in range(nx):
                 for s, sigma in enumerate(PERMS):
                     verts = [(cx + o[0], cy + o[1], cz + o[2]) for o in _kuhn_offsets(sigma)]
-                    X = np.array([lv.G @ (np.array(v) * h) for v in verts])
-                    K = element_stiffness(X) * coeff[lv.emacro[s][cz, cy, cx]]
+                    t = lv.emacro[s][cz, cy, cx]
+                    if lv.vertex_pos is None:
+                        X = np.array([lv.G @ (np.array(v) * h) for v in verts])
+                    else:
+                        V0, P0, M = lv.maps
+                        X = np.array([P0[t] + M[t] @ (np.array(v) / lv.N - V0[t]) for v in verts])
+                    K = element_stiffness(X) * coeff[t]
                     ids = [gid(v) for v in verts]
                     for a in range(4):
                         for b in range(4):
@@ -294,9 +372,11 @@ class Problem:
 
 
 class Mesh:
-    """The level hierarchy r0..R of the cube macro mesh (§2.1)."""
+    """The level hierarchy r0..R of the cube macro mesh (§2.1); with
+    ``vertex_pos`` the sub-cube corners sit at the given physical positions
+    (general macro shapes, a polyhedral domain of the same connectivity)."""
 
-    def __init__(self, sub, R, r0=2, coeff=None, affine=None):
+    def __init__(self, sub, R, r0=2, coeff=None, affine=None, vertex_pos=None):
         self.sub = tuple(int(s) for s in sub)
         self.n_macro = 6 * self.sub[0] * self.sub[1] * self.sub[2]
         if R <= r0:
@@ -305,8 +385,12 @@ class Mesh:
             coeff = np.ones(self.n_macro)
         self.coeff = np.asarray(coeff, dtype=np.float64)
         self.affine = affine
+        self.vertex_pos = None if vertex_pos is None else np.asarray(vertex_pos, dtype=np.float64)
+        if self.vertex_pos is not None and self.vertex_pos.shape != (self.sub[2] + 1, self.sub[1] + 1,
+                                                                     self.sub[0] + 1, 3):
+            raise ValueError("vertex_pos must have shape (sz+1, sy+1, sx+1, 3)")
         self.R, self.r0 = int(R), int(r0)
-        self.levels = [Level(self.sub, r, self.coeff, affine) for r in range(self.r0, self.R + 1)]
+        self.levels = [Level(self.sub, r, self.coeff, affine, self.vertex_pos) for r in range(self.r0, self.R + 1)]
         self.global_problem = Problem(self, [~lv.boundary for lv in self.levels])
 
     @property
@@ -345,7 +429,7 @@ def healthy_mesh(mesh, ids):
     which is the sum of the healthy sub-stencils at interface nodes (§3.2)."""
     coeff = mesh.coeff.copy()
     coeff[np.asarray(list(ids), dtype=np.int64)] = 0.0
-    return Mesh(mesh.sub, mesh.R, mesh.r0, coeff=coeff, affine=mesh.affine)
+    return Mesh(mesh.sub, mesh.R, mesh.r0, coeff=coeff, affine=mesh.affine, vertex_pos=mesh.vertex_pos)
 
 
 def dn_recover(mesh, u, f, ids, n_global, eta, pre=3, post=3, cg_rtol=1e-12, cg_maxit=1000, hmesh=None):
@@ -597,7 +681,8 @@ def grad_coeff(mesh, u, lam):
         for a in range(4):
             la = lam[lv._cell_slice(offs[a])]
             for b in range(4):
-                acc += K[a, b] * la * u[lv._cell_slice(offs[b])]
+                kab = K[a, b] if K.ndim == 2 else K[:, a, b][lv.emacro[s]]
+                acc += kab * la * u[lv._cell_slice(offs[b])]
         g += np.bincount(lv.emacro[s].ravel(), weights=acc.ravel(), minlength=mesh.n_macro)
     return -g
 
@@ -610,6 +695,7 @@ def local_residual(sub, R, coeff, affine, u, f, nodes):
     sx, sy, sz = sub
     N = 1 << R
     nx, ny, nz = sx * N, sy * N, sz * N
+    # (affine images of the uniform grid only)
     G = np.eye(3) if affine is None else np.asarray(affine, dtype=np.float64)[:, :3]
     h = np.array([1.0 / nx, 1.0 / ny, 1.0 / nz])
     Kel = [element_stiffness(np.array([G @ (np.array(o) * h) for o in _kuhn_offsets(s)])) for s in PERMS]

@@ -955,10 +955,11 @@ int hhg_mesh_create(const hhg_mesh_desc* desc, hhg_mesh** out) {
   if (desc->coeff)
     for (int t = 0; t < 6 * desc->subcubes[0] * desc->subcubes[1] * desc->subcubes[2]; ++t)
       if (!(desc->coeff[t] > 0.0)) return fail(HHG_ERR_ARG, "coefficients must be positive");
+  if (desc->affine && desc->vertex_pos) return fail(HHG_ERR_ARG, "give affine or vertex_pos, not both");
   std::unique_ptr<hhg_mesh> m(new (std::nothrow) hhg_mesh());
   if (!m) return fail(HHG_ERR_OOM, "host allocation failed");
   try {
-    build_host_mesh(m->host, desc->subcubes, desc->levels, r0, desc->coeff, desc->affine);
+    build_host_mesh(m->host, desc->subcubes, desc->levels, r0, desc->coeff, desc->affine, desc->vertex_pos);
   } catch (const std::bad_alloc&) {
     return fail(HHG_ERR_OOM, "host allocation failed while building the mesh");
   } catch (const std::exception& e) {

@@ -148,6 +148,11 @@ struct HostMesh {
   std::vector<MacroGeo> geo;
   std::vector<double> coeff;
   double G[9];
+  // Physical positions of the sub-cube corners ((sx+1)(sy+1)(sz+1) x 3, x
+  // fastest); empty = the corners of the unit cube mapped by G.  With moved
+  // corners every macro is a general tetrahedron, refined through its own
+  // affine map.
+  std::vector<double> vpos;
   std::vector<HostLevel> lv;          // index 0 = coarsest (r0)
   std::vector<std::vector<int>> node_macros;   // not used on device
   bool seven_point = false;           // all volume stencils have only the 6
@@ -187,7 +192,7 @@ struct HostProblem {
 };
 
 void build_host_mesh(HostMesh& m, const int sub[3], int R, int r0, const double* coeff,
-                     const double* affine);
+                     const double* affine, const double* vertex_pos = nullptr);
 // open: all adjacent macros faulty (and not Dirichlet); closed: any faulty.
 void build_problem(const HostMesh& m, int kind, const std::vector<unsigned char>& faulty,
                    HostProblem& p);

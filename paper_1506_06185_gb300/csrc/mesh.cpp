@@ -43,8 +43,32 @@ int64_t node_gid(const HostMesh& m, int macro, int N, int i, int j, int k) {
   return grid_gid(m, N, X[0], X[1], X[2]);
 }
 
-// Physical position of a local lattice node of a macro at refinement N.
+// Physical position of the sub-cube corner c (integer corner coordinates).
+const double* corner_pos(const HostMesh& m, const int c[3]) {
+  return &m.vpos[(((size_t)c[2] * (m.sub[1] + 1) + c[1]) * (m.sub[0] + 1) + c[0]) * 3];
+}
+
+// Physical position of a local lattice node of a macro at refinement N: the
+// macro's corners P0..P3 (moved corners), P0 + (i (P1-P0) + j (P2-P0) +
+// k (P3-P0)) / N; else the unit-cube grid position mapped by G.
 void position(const HostMesh& m, int macro, int N, int i, int j, int k, double out[3]) {
+  if (!m.vpos.empty()) {
+    const MacroGeo& g = m.geo[macro];
+    int c[4][3];
+    for (int a = 0; a < 3; ++a) {
+      c[0][a] = g.v0[a];
+      c[1][a] = g.v0[a] + g.e1[a];
+      c[2][a] = g.v0[a] + g.e2[a];
+      c[3][a] = g.v0[a] + g.e3[a];
+    }
+    const double* P0 = corner_pos(m, c[0]);
+    const double* P1 = corner_pos(m, c[1]);
+    const double* P2 = corner_pos(m, c[2]);
+    const double* P3 = corner_pos(m, c[3]);
+    for (int a = 0; a < 3; ++a)
+      out[a] = P0[a] + (i * (P1[a] - P0[a]) + j * (P2[a] - P0[a]) + k * (P3[a] - P0[a])) / N;
+    return;
+  }
   int64_t X[3];
   local_to_fine(m.geo[macro], N, i, j, k, X);
   double p[3] = {double(X[0]) / (double(m.sub[0]) * N), double(X[1]) / (double(m.sub[1]) * N),
@@ -214,7 +238,7 @@ void set_coefficients(HostMesh& m, const double* coeff) {
 bool macro_in_set(const std::vector<unsigned char>& s, int m) { return m >= 0 && m < (int)s.size() && s[m]; }
 
 void build_host_mesh(HostMesh& m, const int sub[3], int R, int r0, const double* coeff,
-                     const double* affine) {
+                     const double* affine, const double* vertex_pos) {
   for (int a = 0; a < 3; ++a) m.sub[a] = sub[a];
   m.R = R;
   m.r0 = r0;
@@ -249,6 +273,34 @@ void build_host_mesh(HostMesh& m, const int sub[3], int R, int r0, const double*
           }
         }
   auto vid = [&](const std::array<int, 3>& x) { return (x[2] * (sub[1] + 1) + x[1]) * (sub[0] + 1) + x[0]; };
+
+  // moved corners: every macro must keep the orientation of its Kuhn simplex
+  // and a volume bounded away from zero
+  m.vpos.clear();
+  if (vertex_pos) {
+    const size_t nv = (size_t)(sub[0] + 1) * (sub[1] + 1) * (sub[2] + 1);
+    m.vpos.assign(vertex_pos, vertex_pos + 3 * nv);
+    for (double x : m.vpos)
+      if (!std::isfinite(x)) throw std::invalid_argument("vertex positions must be finite");
+    for (int t = 0; t < m.n_macro; ++t) {
+      double E[3][3], R3[3][3];
+      for (int q = 0; q < 3; ++q) {
+        const double* P = &m.vpos[3 * (size_t)vid(V[t][q + 1])];
+        const double* P0 = &m.vpos[3 * (size_t)vid(V[t][0])];
+        for (int a = 0; a < 3; ++a) {
+          E[a][q] = P[a] - P0[a];
+          R3[a][q] = (double)(V[t][q + 1][a] - V[t][0][a]) / sub[a];
+        }
+      }
+      auto det3 = [](const double A[3][3]) {
+        return A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1]) - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0]) +
+               A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+      };
+      const double d = det3(E), ref = det3(R3);
+      if (!(d * ref > 0.0) || std::fabs(d) < 1e-6 * std::fabs(ref))
+        throw std::invalid_argument("macro " + std::to_string(t) + " is inverted or degenerate");
+    }
+  }
 
   // interface primitives (faces, edges, vertices) with their adjacent macros
   std::map<std::vector<int>, int> key;

@@ -32,7 +32,8 @@ EXPORTS = ["hhg_mesh_create", "hhg_mesh_destroy", "hhg_mesh_info", "hhg_mesh_byt
 
 class hhg_mesh_desc(C.Structure):
     _fields_ = [("subcubes", C.c_int * 3), ("levels", C.c_int), ("coarsest", C.c_int), ("precision", C.c_int),
-                ("coeff", C.POINTER(C.c_double)), ("affine", C.POINTER(C.c_double))]
+                ("coeff", C.POINTER(C.c_double)), ("affine", C.POINTER(C.c_double)),
+                ("vertex_pos", C.POINTER(C.c_double))]
 
 
 class hhg_fault(C.Structure):
@@ -151,7 +152,7 @@ def _ids(ids):
 
 # --- C-named wrappers -------------------------------------------------------
 
-def hhg_mesh_create(subcubes, levels, coarsest=2, precision=64, coeff=None, affine=None):
+def hhg_mesh_create(subcubes, levels, coarsest=2, precision=64, coeff=None, affine=None, vertex_pos=None):
     d = hhg_mesh_desc()
     d.subcubes[:] = [int(s) for s in subcubes]
     d.levels, d.coarsest, d.precision = int(levels), int(coarsest), int(precision)
@@ -164,6 +165,13 @@ def hhg_mesh_create(subcubes, levels, coarsest=2, precision=64, coeff=None, affi
         a = np.ascontiguousarray(np.asarray(affine, dtype=np.float64)[:3, :3])
         keep.append(a)
         d.affine = a.ctypes.data_as(C.POINTER(C.c_double))
+    if vertex_pos is not None:
+        sx, sy, sz = (int(s) for s in subcubes)
+        v = np.ascontiguousarray(vertex_pos, dtype=np.float64)
+        if v.shape != (sz + 1, sy + 1, sx + 1, 3):
+            raise ValueError("vertex_pos must have shape (sz+1, sy+1, sx+1, 3)")
+        keep.append(v)
+        d.vertex_pos = v.ctypes.data_as(C.POINTER(C.c_double))
     h = C.c_void_p()
     _check(lib().hhg_mesh_create(C.byref(d), C.byref(h)))
     return h
@@ -342,10 +350,10 @@ def hhg_launch_count():
 class Mesh:
     """Owning wrapper of an ``hhg_mesh`` handle."""
 
-    def __init__(self, subcubes, levels, coarsest=2, precision=64, coeff=None, affine=None):
+    def __init__(self, subcubes, levels, coarsest=2, precision=64, coeff=None, affine=None, vertex_pos=None):
         self.subcubes = tuple(int(s) for s in subcubes)
         self.levels = int(levels)
-        self.h = hhg_mesh_create(subcubes, levels, coarsest, precision, coeff, affine)
+        self.h = hhg_mesh_create(subcubes, levels, coarsest, precision, coeff, affine, vertex_pos)
         self.n_nodes, self.n_dof, self.n_macro = hhg_mesh_info(self.h)
         N = 1 << self.levels
         self.shape = (self.subcubes[2] * N + 1, self.subcubes[1] * N + 1, self.subcubes[0] * N + 1)

@@ -5,7 +5,9 @@
 // problem kind it applies the restriction gathers and dumps the coarse CG
 // matrix.  Runs on the CPU; makes no CUDA call.
 //
-// usage: mesh_check sx sy sz R shear dir n_faulty id...
+// usage: mesh_check sx sy sz R geometry dir n_faulty id...
+// geometry: 0 = unit cube, 1 = sheared cube, 2 = moved sub-cube corners read
+// from dir/vpos.bin ((sx+1)(sy+1)(sz+1) x 3 doubles, x fastest).
 // dir holds coeff.bin (n_macro doubles), in_<l>.bin (level-l grid vectors) and
 // r_<kind>_<l>.bin (fine residual of problem kind on level l); the checker
 // writes Ag_<l>.bin, rc_<kind>_<l>.bin (pairs grid id, value) and
@@ -61,7 +63,7 @@ int main(int argc, char** argv) {
   if (argc < 8) return 1;
   const int sub[3] = {atoi(argv[1]), atoi(argv[2]), atoi(argv[3])};
   const int R = atoi(argv[4]);
-  const bool shear = atoi(argv[5]) != 0;
+  const int geometry = atoi(argv[5]);
   const std::string dir = argv[6];
   const int nf = atoi(argv[7]);
   const int n_macro = 6 * sub[0] * sub[1] * sub[2];
@@ -69,8 +71,10 @@ int main(int argc, char** argv) {
   for (int q = 0; q < nf; ++q) faulty[atoi(argv[8 + q])] = 1;
   const double G[9] = {1.0, 0.3, -0.2, 0.1, 0.9, 0.25, -0.15, 0.2, 1.1};
   const std::vector<double> coeff = readv(dir + "/coeff.bin", n_macro);
+  std::vector<double> vpos;
+  if (geometry == 2) vpos = readv(dir + "/vpos.bin", (size_t)3 * (sub[0] + 1) * (sub[1] + 1) * (sub[2] + 1));
   HostMesh m;
-  build_host_mesh(m, sub, R, 2, coeff.data(), shear ? G : nullptr);
+  build_host_mesh(m, sub, R, 2, coeff.data(), geometry == 1 ? G : nullptr, geometry == 2 ? vpos.data() : nullptr);
   // A g on every level: volume nodes with their macro's interior stencil,
   // interface nodes with the sum of the sub-stencils of their copies
   for (size_t l = 0; l < m.lv.size(); ++l) {

@@ -69,3 +69,34 @@ def test_null_handles_are_rejected_without_device_use():
         assert rc == hhg.HHG_ERR_ARG, (name, rc)
         assert lib.hhg_last_error(buf, 256) == hhg.HHG_ERR_ARG
         assert buf.value, name
+
+
+def test_moved_corners_are_validated_before_device_use():
+    # inverted or degenerate macros, and affine together with vertex_pos, are
+    # argument errors found while building the host mesh (no GPU needed)
+    import numpy as np
+    import torch
+    import hhg_inputs as I
+    from paper_1506_06185_gb300 import hhg
+    sub = (2, 1, 1)
+    vp = I.jittered_vertices(sub, seed=4)
+    bad = vp.copy()
+    bad[0, 0, 1] = bad[1, 1, 1]            # a corner onto another: degenerate macros
+    with pytest.raises(hhg.HHGError) as e:
+        hhg.hhg_mesh_create(sub, 3, vertex_pos=bad)
+    assert e.value.code == hhg.HHG_ERR_ARG and "macro" in str(e.value)
+    flipped = vp.copy()
+    flipped[..., 0] *= -1.0                # a mirror image: every macro inverted
+    with pytest.raises(hhg.HHGError) as e:
+        hhg.hhg_mesh_create(sub, 3, vertex_pos=flipped)
+    assert e.value.code == hhg.HHG_ERR_ARG
+    with pytest.raises(hhg.HHGError) as e:
+        hhg.hhg_mesh_create(sub, 3, affine=np.eye(3), vertex_pos=vp)
+    assert e.value.code == hhg.HHG_ERR_ARG
+    with pytest.raises(ValueError):
+        hhg.hhg_mesh_create(sub, 3, vertex_pos=vp[:, :, :2])
+    if not torch.cuda.is_available():
+        # accepted corners get past the host checks to the device step
+        with pytest.raises(hhg.HHGError) as e:
+            hhg.hhg_mesh_create(sub, 3, vertex_pos=vp)
+        assert e.value.code == hhg.HHG_ERR_CUDA

@@ -2,8 +2,9 @@
 stencils, interface copies, restriction gathers and coarse CG matrices
 (paper_1506_06185_gb300/csrc/mesh.cpp, compiled with the checker in
 tests/host/) against the oracle's element-by-element assembly (§2.1, §3.2
-Fig. 4), on the cube and on a sheared cube with per-macro coefficients, for
-the global problem and the three recovery problem kinds."""
+Fig. 4), on the cube, on a sheared cube with per-macro coefficients and on
+meshes with moved sub-cube corners (general macro shapes), for the global
+problem and the three recovery problem kinds."""
 
 import os
 import shutil
@@ -41,17 +42,22 @@ def _problems(m, faulty):
     return probs
 
 
-@pytest.mark.parametrize("sub,R,shear,faulty", [
-    ((2, 2, 2), 4, False, [13]),
-    ((2, 1, 2), 4, True, [0, 1, 2, 3, 4, 5]),
-    ((3, 2, 2), 4, True, [13, 14, 30]),
+@pytest.mark.parametrize("sub,R,geometry,faulty", [
+    ((2, 2, 2), 4, 0, [13]),
+    ((2, 1, 2), 4, 1, [0, 1, 2, 3, 4, 5]),
+    ((3, 2, 2), 4, 1, [13, 14, 30]),
+    ((2, 2, 1), 4, 2, [6, 7, 8, 9, 10, 11]),
+    ((2, 2, 2), 3, 2, [13, 20]),
 ])
-def test_mesh_builder_matches_oracle(checker, tmp_path, sub, R, shear, faulty):
+def test_mesh_builder_matches_oracle(checker, tmp_path, sub, R, geometry, faulty):
     n_macro = 6 * sub[0] * sub[1] * sub[2]
     coeff = np.exp(np.random.default_rng(3).standard_normal(n_macro))
     coeff.tofile(tmp_path / "coeff.bin")
-    aff = SHEAR if shear else None
-    m = O.Mesh(sub, R, coeff=coeff, affine=aff)
+    aff = SHEAR if geometry == 1 else None
+    vp = I.jittered_vertices(sub, seed=4) if geometry == 2 else None
+    if vp is not None:
+        vp.tofile(tmp_path / "vpos.bin")
+    m = O.Mesh(sub, R, coeff=coeff, affine=aff, vertex_pos=vp)
     rng = np.random.default_rng(0)
     ins = []
     for l, lv in enumerate(m.levels):
@@ -64,7 +70,7 @@ def test_mesh_builder_matches_oracle(checker, tmp_path, sub, R, shear, faulty):
             r = rng.standard_normal(m.levels[l].shape)
             r[~pr.free[l]] = 0.0
             r.tofile(tmp_path / f"r_{kind}_{l}.bin")
-    subprocess.check_call([checker, *map(str, sub), str(R), str(int(shear)), str(tmp_path), str(len(faulty)),
+    subprocess.check_call([checker, *map(str, sub), str(R), str(geometry), str(tmp_path), str(len(faulty)),
                            *map(str, faulty)])
     # stencils: A g through blocks and copy lists = the assembled operator
     for l, lv in enumerate(m.levels):

@@ -109,6 +109,120 @@ def test_colouring_is_proper():
 
 
 # --------------------------------------------------------------------------
+# general macro shapes: moved macro vertices (§2.1, unstructured base mesh of a
+# polyhedral domain; each macro refined uniformly through its own affine map)
+# --------------------------------------------------------------------------
+
+JSUB = (2, 2, 1)
+
+
+def _jittered(sub=JSUB, move_boundary=True):
+    return I.jittered_vertices(sub, seed=4, amp=0.12, move_boundary=move_boundary)
+
+
+def _domain_volume(sub, vp):
+    """Sum of the macro volumes from the corner positions (determinants)."""
+    vol = 0.0
+    for v in I.macro_vertices(sub):
+        P = [np.asarray(vp[c[2], c[1], c[0]]) for c in v]
+        vol += abs(np.linalg.det(np.stack([P[1] - P[0], P[2] - P[0], P[3] - P[0]]))) / 6.0
+    return vol
+
+
+def test_moved_vertices_keep_every_macro_proper():
+    for sub in [JSUB, (1, 1, 1), (3, 2, 2)]:
+        vp = _jittered(sub)
+        for v in I.macro_vertices(sub):
+            P = [np.asarray(vp[c[2], c[1], c[0]]) for c in v]
+            ref = np.linalg.det(np.stack([np.subtract(v[q], v[0]) for q in (1, 2, 3)]).astype(float))
+            det = np.linalg.det(np.stack([P[1] - P[0], P[2] - P[0], P[3] - P[0]]))
+            assert np.sign(det) == np.sign(ref) and abs(det) > 0.2 * abs(ref) / np.prod(sub)
+
+
+def test_corner_positions_of_the_cube_reproduce_the_cube_operator():
+    sub = (2, 1, 2)
+    k, j, i = np.meshgrid(np.arange(3), np.arange(2), np.arange(3), indexing="ij")
+    vp = np.stack([i / 2, j / 1, k / 2], axis=-1)
+    coeff = _rand_coeff(24, 8)
+    a, b = O.Level(sub, 3, coeff), O.Level(sub, 3, coeff, vertex_pos=vp)
+    assert abs(O.dia_to_csr(a) - O.dia_to_csr(b)).max() <= 1e-15 * abs(O.dia_to_csr(a)).max()
+
+
+def test_moved_vertices_dia_equals_per_element_assembly():
+    coeff = _rand_coeff(6 * 4)
+    lv = O.Level(JSUB, 2, coeff, vertex_pos=_jittered())
+    A_dia, A_coo = O.dia_to_csr(lv), O.assemble_coo(lv, coeff)
+    assert abs(A_dia - A_coo).max() <= 1e-14 * abs(A_coo).max()
+
+
+def test_moved_vertices_linear_kernel_and_energy_equal_the_volume():
+    """For u linear in the physical coordinates, (A u)_i = 0 at every interior
+    node and u^T A u = |grad u|^2 |Omega| (unit coefficient): pins the node
+    positions and the element geometry against the corner positions alone."""
+    vp = _jittered()
+    lv = O.Level(JSUB, 3, np.ones(24), vertex_pos=vp)
+    X, Y, Z = O.node_coords(lv)
+    c = np.array([1.1, -0.7, 0.4])
+    u = 0.3 + c[0] * X + c[1] * Y + c[2] * Z
+    Au = O.apply_A(lv, O.pad(u))
+    assert np.abs(Au[~lv.boundary]).max() <= 1e-13 * np.abs(lv.A[(0, 0, 0)]).max() * np.abs(u).max()
+    energy = float(np.sum(u * Au))
+    assert abs(energy - c @ c * _domain_volume(JSUB, vp)) <= 1e-12 * energy
+    # the boundary nodes lie on the moved boundary: the cube's corners moved
+    assert abs(_domain_volume(JSUB, vp) - 1.0) > 1e-3
+
+
+def test_moved_vertices_general_shapes():
+    lv = O.Level(JSUB, 3, np.ones(24), vertex_pos=_jittered())
+    assert len(lv.A) == 15                                    # all 15 offsets
+    K = lv.Kel[0]
+    assert K.shape == (24, 4, 4) and np.abs(K[1:] - K[:1]).max() > 1e-3 * np.abs(K).max()
+    rng = np.random.default_rng(1)
+    u, v = rng.standard_normal(lv.shape), rng.standard_normal(lv.shape)
+    uAv, vAu = np.sum(u * O.apply_A(lv, O.pad(v))), np.sum(v * O.apply_A(lv, O.pad(u)))
+    assert abs(uAv - vAu) <= 1e-12 * abs(uAv)
+
+
+def test_moved_vertices_galerkin_identity():
+    coeff = _rand_coeff(24, 9)
+    vp = _jittered()
+    lc = O.Level(JSUB, 2, coeff, vertex_pos=vp)
+    lf = O.Level(JSUB, 3, coeff, vertex_pos=vp)
+    P = _prolong_matrix(lc)
+    G = (P.T @ O.dia_to_csr(lf) @ P).toarray()
+    Ac = O.dia_to_csr(lc).toarray()
+    assert np.abs(G - Ac).max() <= 1e-13 * np.abs(Ac).max()
+
+
+def test_moved_vertices_second_order_on_a_polyhedral_domain():
+    """Harmonic u* = exp(pi x) sin(pi y) with Dirichlet data at the moved
+    boundary nodes: the discrete L2 nodal error drops ~4x per refinement."""
+    sub, errs = (1, 1, 1), []
+    vp = _jittered(sub)
+    for R in (4, 5, 6):
+        m = O.Mesh(sub, R, vertex_pos=vp)
+        X, Y, _ = O.node_coords(m.fine)
+        ex = np.exp(np.pi * X) * np.sin(np.pi * Y)
+        u = O.pad(I.initial_guess(sub, R, ex))
+        O.solve(m, u, np.zeros(m.fine.pshape), rtol=1e-12, max_cycles=60)
+        errs.append(np.sqrt(np.mean((O.interior(u) - ex) ** 2)))
+    ratios = [errs[i] / errs[i + 1] for i in range(2)]
+    assert all(3.5 < q < 4.3 for q in ratios), ratios
+
+
+def test_moved_vertices_vcycles_converge_to_direct_solve():
+    R = 4
+    m = O.Mesh(JSUB, R, coeff=_rand_coeff(24, 10), vertex_pos=_jittered(move_boundary=False))
+    g = I.harmonic_boundary(JSUB, R)
+    u = O.pad(I.initial_guess(JSUB, R, g))
+    f = O.pad(I.random_load(JSUB, R, seed=0) * 1e-3)
+    res = O.solve(m, u, f, rtol=1e-13, max_cycles=40)
+    ref = _direct(m.fine, I.initial_guess(JSUB, R, g), O.interior(f), ~m.fine.boundary)
+    assert np.abs(O.interior(u) - ref).max() <= 1e-10 * np.abs(ref).max()
+    assert res["hist"][-1] <= 1e-13
+
+
+# --------------------------------------------------------------------------
 # transfers (§2.1)
 # --------------------------------------------------------------------------
 
