@@ -371,12 +371,14 @@ def _local_direct(m, u, f, ids, healthy=False):
     return _direct(m.fine, O.interior(u).copy(), O.interior(f), free), free
 
 
-@pytest.mark.parametrize("healthy", [False, True])
-def test_recovery_subproblems_converge_to_direct_solve(healthy):
+@pytest.mark.parametrize("healthy,moved", [(False, False), (True, False), (False, True), (True, True)])
+def test_recovery_subproblems_converge_to_direct_solve(healthy, moved):
     """Algorithm 1: step a solves A_FF u_F = f_F - A_FG u_G, step b solves
-    A_II u_I = f_I - A_IG u_G with the interface G frozen."""
+    A_II u_I = f_I - A_IG u_G with the interface G frozen (also with moved
+    sub-cube corners)."""
     sub, R = (2, 2, 2), 4
-    m = O.Mesh(sub, R, coeff=_rand_coeff(48, 9))
+    vp = _jittered(sub) if moved else None
+    m = O.Mesh(sub, R, coeff=_rand_coeff(48, 9), vertex_pos=vp)
     rng = np.random.default_rng(4)
     u = O.pad(I.initial_guess(sub, R))
     O.interior(u)[~m.fine.boundary] = rng.standard_normal((~m.fine.boundary).sum())
@@ -499,12 +501,14 @@ def test_local_residual_equals_assembled_residual():
 # Dirichlet-Neumann recovery (§4.3, Algorithm 2)
 # --------------------------------------------------------------------------
 
-def test_dn_neumann_subproblem_converges_to_direct_solve():
+@pytest.mark.parametrize("moved", [False, True])
+def test_dn_neumann_subproblem_converges_to_direct_solve(moved):
     """With many cycles, Omega_I solves A_I [u_I; u_G] = [f_I; b_G] (A_I from
     the healthy macros' elements, b_G = (A_I u)_G at the fault) and Omega_F
-    the Dirichlet problem with the final interface values."""
+    the Dirichlet problem with the final interface values (also with moved
+    sub-cube corners)."""
     sub, R = (2, 2, 2), 4
-    m = O.Mesh(sub, R, coeff=_rand_coeff(48, 12))
+    m = O.Mesh(sub, R, coeff=_rand_coeff(48, 12), vertex_pos=_jittered(sub) if moved else None)
     rng = np.random.default_rng(5)
     u = O.pad(I.initial_guess(sub, R))
     O.interior(u)[~m.fine.boundary] = rng.standard_normal((~m.fine.boundary).sum())
