@@ -132,6 +132,63 @@ def jittered_vertices(sub, seed=4, amp=0.12, move_boundary=True):
     return base + off
 
 
+def corner_grid(sub):
+    """Unit-cube positions of the sub-cube corners, (n_corner, 3), corner
+    (a, b, c) at index (c (sy+1) + b)(sx+1) + a."""
+    sx, sy, sz = (int(s) for s in sub)
+    k, j, i = np.meshgrid(np.arange(sz + 1), np.arange(sy + 1), np.arange(sx + 1), indexing="ij")
+    return np.stack([i / sx, j / sy, k / sz], axis=-1).reshape(-1, 3)
+
+
+def _corner_id(sub, v):
+    return (int(v[2]) * (int(sub[1]) + 1) + int(v[1])) * (int(sub[0]) + 1) + int(v[0])
+
+
+def kuhn_macro_mesh(sub):
+    """The cube family's macro mesh as a general one: (verts, tets), the six
+    Kuhn tetrahedra of every sub-cube with their vertices in the order 0,
+    e_pi0, e_pi0 + e_pi1, (1,1,1) (macro ids as in ``macro_vertices``)."""
+    tets = [[_corner_id(sub, v) for v in m] for m in macro_vertices(sub)]
+    return corner_grid(sub), np.array(tets, dtype=np.int64)
+
+
+def five_tet_macro_mesh(sub, seed=None, amp=0.0):
+    """A macro mesh of another connectivity: every sub-cube split into five
+    tetrahedra (a central one and four corner ones), the split mirrored on
+    alternate sub-cubes so that neighbouring splits share their face
+    diagonals.  Vertices ordered for a positive orientation.  With ``seed``
+    the interior corners move by seeded uniform offsets of up to ``amp``
+    sub-cube edges per axis."""
+    sx, sy, sz = (int(s) for s in sub)
+    verts = corner_grid(sub)
+    if seed is not None:
+        rng = np.random.Generator(np.random.Philox(int(seed)))
+        off = rng.uniform(-amp, amp, size=verts.shape) * np.array([1.0 / sx, 1.0 / sy, 1.0 / sz])
+        b = (np.isclose(verts, 0.0) | np.isclose(verts, 1.0)).any(axis=1)
+        off[b] = 0.0
+        verts = verts + off
+    tets = []
+    for c in range(sz):
+        for b in range(sy):
+            for a in range(sx):
+                cid = lambda d: _corner_id(sub, (a + d[0], b + d[1], c + d[2]))
+                even = [(0, 0, 0), (1, 1, 0), (1, 0, 1), (0, 1, 1)]
+                odd = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 1)]
+                inner, apex = (even, odd) if (a + b + c) % 2 == 0 else (odd, even)
+                parts = [[cid(d) for d in inner]]
+                # each remaining corner with its three axis neighbours (the
+                # central tetrahedron's vertices)
+                for d in apex:
+                    nb = [tuple(d[q] ^ (q == ax) for q in range(3)) for ax in range(3)]
+                    parts.append([cid(d)] + [cid(n) for n in nb])
+                for tet in parts:
+                    X = verts[tet]
+                    if np.linalg.det((X[1:] - X[0]).T) < 0:
+                        tet = [tet[0], tet[2], tet[1], tet[3]]
+                    tets.append(tet)
+    return verts, np.array(tets, dtype=np.int64)
+
+
 def grow_fault_set(sub, size, seed):
     """A connected set of ``size`` macros grown breadth-first (through shared
     faces) from a random seed macro, with a random visiting order."""

@@ -27,7 +27,12 @@ polyhedral domain with the same connectivity, §2.1): each macro is then the
 image of its reference lattice under its own affine map.  Per-macro blocked
 storage is a GPU concern and is deliberately absent here.
 
-Parity status of each function is listed in ``oracle/hhg_oracle.py``.
+``oracle/unstructured.py`` (imported as ``oracle.unstructured``) is the same
+method on a macro mesh of general connectivity (vertex and tetrahedron
+arrays), with its own smoother reading for that case.
+
+Parity status of each function is listed in ``oracle/hhg_oracle.py`` and
+``oracle/unstructured.py``.
 """
 
 from .hhg_oracle import *  # noqa: F401,F403

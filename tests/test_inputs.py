@@ -134,3 +134,24 @@ def test_fault_scenarios_touch_the_boundary_as_in_section_4_4():
             P = np.array(tri)
             faces += any(np.all(P[:, a] == 0) or np.all(P[:, a] == s2[a]) for a in range(3))
         assert faces == I.boundary_contact(s2, t)[0]
+
+
+def test_five_tetrahedra_meshes_are_conforming_and_oriented():
+    for sub, seed in [((2, 2, 2), None), ((3, 2, 1), 3)]:
+        v, t = I.five_tet_macro_mesh(sub, seed=seed, amp=0.12)
+        assert len(t) == 5 * int(np.prod(sub))
+        dets = [np.linalg.det((v[tt[1:]] - v[tt[0]]).T) for tt in t]
+        assert min(dets) > 0.0                                    # positive orientation
+        faces = {}
+        for tt in t:
+            for f in itertools.combinations(sorted(tt), 3):
+                faces[f] = faces.get(f, 0) + 1
+        assert max(faces.values()) == 2                           # a face joins at most two
+        for f, c in faces.items():                                # outer faces on the cube
+            P = v[list(f)]
+            on = any(np.allclose(P[:, a], 0.0) or np.allclose(P[:, a], 1.0) for a in range(3))
+            assert on == (c == 1)
+        assert abs(sum(abs(d) for d in dets) / 6.0 - 1.0) < 1e-12
+    # the cube family as a general mesh: six Kuhn tetrahedra per sub-cube
+    v, t = I.kuhn_macro_mesh((2, 1, 1))
+    assert len(t) == 12 and np.allclose(v[t[0]], np.array(I.macro_vertices((2, 1, 1))[0]) / [2, 1, 1])
