@@ -9,7 +9,7 @@
 // geometry: 0 = unit cube, 1 = sheared cube, 2 = moved sub-cube corners read
 // from dir/vpos.bin ((sx+1)(sy+1)(sz+1) x 3 doubles, x fastest).
 // dir holds coeff.bin (n_macro doubles), in_<l>.bin (level-l grid vectors) and
-// r_<kind>_<l>.bin (fine residual of problem kind on level l); the checker
+// r_<kind>_<l>.bin (fine residual of problem kind on level l); the program
 // writes Ag_<l>.bin, rc_<kind>_<l>.bin (pairs grid id, value) and
 // csr_<kind>.bin (n, then per row: grid id, nnz, (column grid id, value)...).
 #include <cstdio>

@@ -16,7 +16,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
 @pytest.fixture(scope="module")
-def checker(tmp_path_factory):
+def check_prog(tmp_path_factory):
     cxx = shutil.which("g++") or shutil.which("c++")
     cuda_inc = "/usr/local/cuda/include"
     if not cxx or not os.path.isdir(cuda_inc):
@@ -28,7 +28,7 @@ def checker(tmp_path_factory):
     return str(out)
 
 
-def test_layout_and_tiles(checker):
-    r = subprocess.run([checker, "130"], capture_output=True, text=True, timeout=600)
+def test_layout_and_tiles(check_prog):
+    r = subprocess.run([check_prog, "130"], capture_output=True, text=True, timeout=600)
     assert r.returncode == 0, r.stdout + r.stderr
     assert r.stdout.strip().endswith("ok")

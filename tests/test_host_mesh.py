@@ -1,6 +1,6 @@
 """Host logic of the CUDA path on the CPU: the mesh builder's per-macro
 stencils, interface copies, restriction gathers and coarse CG matrices
-(paper_1506_06185_gb300/csrc/mesh.cpp, compiled with the checker in
+(paper_1506_06185_gb300/csrc/mesh.cpp, compiled with the check program in
 tests/host/) against the oracle's element-by-element assembly (§2.1, §3.2
 Fig. 4), on the cube, on a sheared cube with per-macro coefficients and on
 meshes with moved sub-cube corners (general macro shapes), for the global
@@ -21,7 +21,7 @@ SHEAR = np.array([[1.0, 0.3, -0.2], [0.1, 0.9, 0.25], [-0.15, 0.2, 1.1]])
 
 
 @pytest.fixture(scope="module")
-def checker(tmp_path_factory):
+def check_prog(tmp_path_factory):
     cxx = shutil.which("g++") or shutil.which("c++")
     cuda_inc = "/usr/local/cuda/include"
     if not cxx or not os.path.isdir(cuda_inc):
@@ -49,7 +49,7 @@ def _problems(m, faulty):
     ((2, 2, 1), 4, 2, [6, 7, 8, 9, 10, 11]),
     ((2, 2, 2), 3, 2, [13, 20]),
 ])
-def test_mesh_builder_matches_oracle(checker, tmp_path, sub, R, geometry, faulty):
+def test_mesh_builder_matches_oracle(check_prog, tmp_path, sub, R, geometry, faulty):
     n_macro = 6 * sub[0] * sub[1] * sub[2]
     coeff = np.exp(np.random.default_rng(3).standard_normal(n_macro))
     coeff.tofile(tmp_path / "coeff.bin")
@@ -70,7 +70,7 @@ def test_mesh_builder_matches_oracle(checker, tmp_path, sub, R, geometry, faulty
             r = rng.standard_normal(m.levels[l].shape)
             r[~pr.free[l]] = 0.0
             r.tofile(tmp_path / f"r_{kind}_{l}.bin")
-    subprocess.check_call([checker, *map(str, sub), str(R), str(geometry), str(tmp_path), str(len(faulty)),
+    subprocess.check_call([check_prog, *map(str, sub), str(R), str(geometry), str(tmp_path), str(len(faulty)),
                            *map(str, faulty)])
     # stencils: A g through blocks and copy lists = the assembled operator
     for l, lv in enumerate(m.levels):
