@@ -33,11 +33,15 @@ Gauss-Seidel step visits
     interface node), classes in increasing order.
 Within a class no two nodes are coupled, so each class is one vector update.
 
+Faults (§2.2) and their recovery (LR / DD of Algorithm 1, DN of Algorithm 2)
+follow the structured oracle's readings on these meshes.
+
 Parity status: every function is pinned by ``tests/test_oracle_unstructured.py``
 (the cube family given as a general mesh reproduces the structured oracle's
-operator, transfers and boundary; node counts of the macro mesh's primitives;
-linear-function kernel and energy = volume; Galerkin identity; proper smoother
-classes; V-cycles = direct solve; second-order error).
+operator, transfers, boundary and fault sets; node counts of the macro mesh's
+primitives; linear-function kernel and energy = volume; Galerkin identity;
+proper smoother classes; V-cycles and recovery sub-problems = direct solves;
+second-order error; recovery beats do-nothing).
 """
 
 from __future__ import annotations
@@ -47,7 +51,10 @@ import itertools
 import numpy as np
 import scipy.sparse as sp
 
-__all__ = ["UMesh", "ULevel", "gs_step", "vcycle", "solve", "resnorm", "cg", "element_stiffness"]
+__all__ = ["UMesh", "ULevel", "gs_step", "vcycle", "solve", "resnorm", "cg", "element_stiffness",
+           "inject_fault", "dn_recover", "NONE", "LR", "DD", "DN"]
+
+NONE, LR, DD, DN = 0, 1, 2, 3
 
 PERMS = list(itertools.permutations((0, 1, 2)))
 
@@ -195,6 +202,42 @@ class UMesh:
         self.levels = [ULevel(self, r) for r in range(self.r0, self.R + 1)]
         self.P = [self._prolongation(l) for l in range(1, len(self.levels))]
 
+    def fault_masks(self, ids):
+        """Per level: (open faulty set, closed faulty set) of nodes (§2.2): a
+        node is inside the open union of the faulty macros when every macro
+        containing it is faulty (and it is not a Dirichlet node), in its
+        closure when at least one is."""
+        faulty = np.zeros(self.nt, dtype=bool)
+        faulty[np.asarray(list(ids), dtype=np.int64)] = True
+        out = []
+        for lv in self.levels:
+            cnt = np.zeros(lv.n, dtype=np.int64)
+            cntf = np.zeros(lv.n, dtype=np.int64)
+            for t in range(self.nt):
+                cnt[lv.l2g[t]] += 1
+                if faulty[t]:
+                    cntf[lv.l2g[t]] += 1
+            out.append(((cntf == cnt) & ~lv.boundary, cntf > 0))
+        return out
+
+    def global_masks(self):
+        return [~lv.boundary for lv in self.levels]
+
+    def local_masks(self, ids):
+        """Free nodes of the Dirichlet problem on Omega_F (Algorithm 1, step a)."""
+        return [o for o, _ in self.fault_masks(ids)]
+
+    def healthy_masks(self, ids):
+        """Free nodes of Omega_I with the interface frozen (Algorithm 1, step b)."""
+        return [~lv.boundary & ~c for lv, (_, c) in zip(self.levels, self.fault_masks(ids))]
+
+    def healthy(self, ids):
+        """The hierarchy of A_I: only the healthy macros' elements (faulty
+        coefficients zero), the sum of healthy sub-stencils at the interface."""
+        coeff = self.coeff.copy()
+        coeff[np.asarray(list(ids), dtype=np.int64)] = 0.0
+        return UMesh(self.verts, self.tets, self.R, self.r0, coeff)
+
     def _prolongation(self, l):
         """Linear interpolation from level l - 1 to level l (§2.1): a fine
         lattice point p (chain coordinates) lies on the coarse edge from
@@ -290,15 +333,73 @@ def vcycle(mesh, lvl, u, f, free_masks, pre=3, post=3, cg_rtol=1e-12, cg_maxit=1
         gs_step(lv, u, f, free)
 
 
-def solve(mesh, u, f, rtol=1e-8, max_cycles=50, pre=3, post=3):
-    """V-cycles until ||f - A u|| <= rtol ||f - A u_0|| (free nodes).  Returns
-    the relative residual history."""
-    masks = [~lv.boundary for lv in mesh.levels]
+def inject_fault(mesh, u, ids):
+    """Fault model of §2.2: the unknowns strictly inside the faulty macros
+    are lost and re-initialised with zero; the interface values survive."""
+    u[mesh.local_masks(ids)[-1]] = 0.0
+
+
+def dn_recover(mesh, u, f, ids, n_global, eta, pre=3, post=3):
+    """Dirichlet-Neumann recovery, Algorithm 2 (§4.3), with the same reading
+    as the structured oracle: Omega_I and the interface G iterate on A_I with
+    right-hand side f on Omega_I and b_G = (A_I u)_G at the fault on G; block
+    j of ceil(j eta) - ceil((j - 1) eta) Omega_F Dirichlet cycles uses the G
+    values after Omega_I cycle j - 1.  Returns the Omega_F cycles run."""
+    import math
+    hm = mesh.healthy(ids)
+    masks = mesh.fault_masks(ids)
+    lv = mesh.levels[-1]
+    open_f, closed_f = masks[-1]
+    gamma = closed_f & ~open_f & ~lv.boundary
+    i_masks = [~l.boundary & ~o for l, (o, _) in zip(mesh.levels, masks)]
+    f_masks = [o for o, _ in masks]
+    top = len(mesh.levels) - 1
+    fI = f.copy()
+    fI[gamma] = (hm.levels[-1].A @ u)[gamma]
+    snap = u[gamma].copy()
+    n_F = 0
+    for j in range(1, n_global + 1):
+        cyc = int(math.ceil(j * eta)) - int(math.ceil((j - 1) * eta))
+        uf = u.copy()
+        uf[gamma] = snap
+        for _ in range(cyc):
+            vcycle(mesh, top, uf, f, f_masks, pre, post)
+        n_F += cyc
+        u[open_f] = uf[open_f]
+        vcycle(hm, top, u, fI, i_masks, pre, post)
+        snap = u[gamma].copy()
+    return n_F
+
+
+def solve(mesh, u, f, rtol=1e-8, max_cycles=50, pre=3, post=3, fault_cycle=-1, fault_ids=(),
+          recovery=NONE, n_local=0, n_global=0, eta=1.0):
+    """V-cycles until ||f - A u|| <= rtol ||f - A u_0|| (free nodes), with an
+    optional fault after global cycle ``fault_cycle`` and its recovery (NONE,
+    LR, DD as Algorithm 1, DN as Algorithm 2; n_F = n_local if positive, else
+    ceil(eta n_I)).  Returns the relative residual history: 1, one entry per
+    global cycle, and one extra entry right after the fault and recovery."""
+    import math
+    top = len(mesh.levels) - 1
+    masks = mesh.global_masks()
     r0 = resnorm(mesh, u, f)
     hist = [1.0]
-    for _ in range(max_cycles):
-        if hist[-1] <= rtol:
-            break
-        vcycle(mesh, len(mesh.levels) - 1, u, f, masks, pre, post)
+    k = 0
+    while k < max_cycles and hist[-1] > rtol:
+        vcycle(mesh, top, u, f, masks, pre, post)
+        k += 1
         hist.append(resnorm(mesh, u, f) / r0)
+        if k == fault_cycle:
+            inject_fault(mesh, u, fault_ids)
+            if recovery == DN:
+                dn_recover(mesh, u, f, fault_ids, n_global, eta, pre, post)
+            elif recovery in (LR, DD):
+                n_F = n_local if n_local > 0 else int(math.ceil(eta * n_global))
+                lm = mesh.local_masks(fault_ids)
+                for _ in range(n_F):
+                    vcycle(mesh, top, u, f, lm, pre, post)
+                if recovery == DD:
+                    hm = mesh.healthy_masks(fault_ids)
+                    for _ in range(n_global):
+                        vcycle(mesh, top, u, f, hm, pre, post)
+            hist.append(resnorm(mesh, u, f) / r0)
     return np.array(hist)

@@ -3,7 +3,10 @@ mathematics fixes: the cube family given as a general mesh reproduces the
 structured oracle; node counts of the macro mesh's primitives; linear
 functions and the energy-volume identity; the Galerkin identity; proper
 smoother classes and a brute-force Gauss-Seidel sweep; V-cycles = direct
-solve; second-order discretisation error (§2.1)."""
+solve; second-order discretisation error (§2.1); fault sets equal to the
+structured ones on the cube family, a faulty macro losing exactly its volume
+nodes, LR / DD / DN sub-problems = direct solves, recovery beating
+do-nothing (§2.2, Algorithms 1 and 2)."""
 
 import itertools
 
@@ -146,3 +149,84 @@ def test_second_order_error_on_a_general_mesh():
         errs.append(np.sqrt(np.mean((u - ex) ** 2)))
     ratios = [errs[i] / errs[i + 1] for i in range(2)]
     assert all(3.4 < q < 4.4 for q in ratios), ratios
+
+
+# --------------------------------------------------------------------------
+# faults and recovery (§2.2, Algorithms 1 and 2) on general meshes
+# --------------------------------------------------------------------------
+
+def test_fault_sets_on_the_cube_family_equal_the_structured_ones():
+    sub, R = (2, 2, 1), 3
+    v, t = I.kuhn_macro_mesh(sub)
+    um, sm = U.UMesh(v, t, R), O.Mesh(sub, R)
+    ids = [3, 4, 5, 9]
+    for lu, ls, (ou, cu), (os_, cs) in zip(um.levels, sm.levels, um.fault_masks(ids), sm.fault_masks(ids)):
+        nx, ny, nz = ls.n
+        g = np.rint(lu.X * np.array([nx, ny, nz])).astype(np.int64)
+        gid = (g[:, 2] * (ny + 1) + g[:, 1]) * (nx + 1) + g[:, 0]
+        assert np.array_equal(ou, os_.ravel()[gid]) and np.array_equal(cu, cs.ravel()[gid])
+
+
+def test_one_faulty_macro_loses_exactly_its_volume_nodes(five):
+    for lv, (o, c) in zip(five.levels, five.fault_masks([7])):
+        N = lv.N
+        assert o.sum() == (N - 1) * (N - 2) * (N - 3) // 6
+        assert c.sum() == (N + 1) * (N + 2) * (N + 3) // 6      # its closed lattice
+        assert np.all(lv.dim[o] == 4)
+
+
+def _direct_sub(lv, u, f, free):
+    ref = u.copy()
+    ref[free] = spla.spsolve(lv.A[free][:, free].tocsc(), f[free] - lv.A[free][:, ~free] @ u[~free])
+    return ref
+
+
+@pytest.mark.parametrize("which", ["local", "healthy"])
+def test_recovery_subproblems_converge_to_direct_solves(five, which):
+    lv = five.levels[-1]
+    rng = np.random.default_rng(11)
+    u = np.where(lv.boundary, 0.0, rng.standard_normal(lv.n))
+    f = rng.uniform(-1, 1, lv.n)
+    ids = [0, 1, 2, 3, 4]                                  # one sub-cube's five macros
+    masks = five.local_masks(ids) if which == "local" else five.healthy_masks(ids)
+    ref = _direct_sub(lv, u, f, masks[-1])
+    for _ in range(30):
+        U.vcycle(five, len(five.levels) - 1, u, f, masks)
+    assert np.abs(u - ref).max() <= 1e-10 * np.abs(ref).max()
+    assert np.array_equal(u[~masks[-1]], ref[~masks[-1]])    # frozen nodes untouched
+
+
+def test_dn_neumann_subproblem_converges_to_its_direct_solve(five):
+    lv = five.levels[-1]
+    rng = np.random.default_rng(12)
+    u = np.where(lv.boundary, 0.0, rng.standard_normal(lv.n))
+    f = rng.uniform(-1, 1, lv.n)
+    ids = [5, 6, 7, 8, 9]
+    hm = five.healthy(ids)
+    o, c = five.fault_masks(ids)[-1]
+    gamma = c & ~o & ~lv.boundary
+    b = f.copy()
+    b[gamma] = (hm.levels[-1].A @ u)[gamma]
+    free_i = ~lv.boundary & ~o
+    U.inject_fault(five, u, ids)
+    ref_i = _direct_sub(hm.levels[-1], u, b, free_i)
+    U.dn_recover(five, u, f, ids, n_global=30, eta=1.0)
+    assert np.abs(u[free_i] - ref_i[free_i]).max() <= 1e-10 * np.abs(ref_i).max()
+    ref_f = _direct_sub(lv, u, f, o)
+    assert np.abs(u[o] - ref_f[o]).max() <= 1e-9 * np.abs(ref_f).max()
+
+
+def test_recovery_beats_do_nothing_on_a_general_mesh(five):
+    lv = five.levels[-1]
+    f = np.where(lv.boundary, 0.0, np.random.default_rng(13).uniform(-1, 1, lv.n))
+    ids = [10, 11, 12, 13, 14]
+    runs = {}
+    for name, kw in [("free", {}), ("none", dict(recovery=U.NONE)), ("lr", dict(recovery=U.LR, n_local=4)),
+                     ("dd", dict(recovery=U.DD, n_global=2, eta=3.0)), ("dn", dict(recovery=U.DN, n_global=2, eta=3.0))]:
+        u = np.zeros(lv.n)
+        fk = dict(fault_cycle=4, fault_ids=ids) if name != "free" else {}
+        h = U.solve(five, u, f, rtol=1e-10, max_cycles=40, **fk, **kw)
+        runs[name] = len(h) - 1 - (1 if fk else 0)          # global cycles
+    assert runs["none"] > runs["free"]
+    assert runs["dd"] <= runs["lr"] <= runs["none"] and runs["dn"] <= runs["none"]
+    assert runs["dd"] < runs["none"]
