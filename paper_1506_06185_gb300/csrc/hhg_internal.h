@@ -5,6 +5,7 @@
 
 #include <cuda_runtime.h>
 
+#include <array>
 #include <atomic>
 #include <cstdint>
 #include <string>
@@ -131,10 +132,14 @@ struct HostLevel {
   int64_t block = 0;
   std::vector<int> SL;                // slice-start table of the block layout
   int n_if = 0;
-  std::vector<int64_t> if_gid;        // global grid id of each interface node
+  std::vector<int64_t> if_gid;        // global id of each interface node (grid id
+                                      // on the cube family; general meshes: its
+                                      // rank, interface nodes coming first)
   std::vector<int> if_cptr;           // copies CSR
   std::vector<Copy> if_copy;
-  std::vector<unsigned char> if_colour, if_dirichlet;
+  std::vector<unsigned char> if_colour, if_dirichlet;   // general meshes: if_colour
+                                      // holds the interface smoother class
+  int n_if_classes = 0;               // general meshes: number of interface classes
   std::vector<double> W;              // [n_macro][16][15] stencil weights
   std::vector<Tile> tiles_int;        // row-pair tiles of the volume interior
   std::vector<Tile> tiles_all;        // tiles covering the closed lattice
@@ -148,6 +153,11 @@ struct HostMesh {
   std::vector<MacroGeo> geo;
   std::vector<double> coeff;
   double G[9];
+  // General connectivity (build_general_mesh): the four vertex ids of every
+  // macro, positions in vpos; global node order = interface nodes by key,
+  // then the volume nodes macro by macro in local (k, j, i) order.
+  bool general = false;
+  std::vector<std::array<int, 4>> mverts;
   // Physical positions of the sub-cube corners ((sx+1)(sy+1)(sz+1) x 3, x
   // fastest); empty = the corners of the unit cube mapped by G.  With moved
   // corners every macro is a general tetrahedron, refined through its own
@@ -174,6 +184,14 @@ struct HostProblemLevel {
   // interface nodes of the level.
   std::vector<int> cptr;
   std::vector<Copy> copies;
+  // General meshes: free_if grouped by interface class (class_off, one entry
+  // per class + 1; col_off then only holds the total in col_off[4]) and the
+  // restriction gathers as CSR (gptr over free_if, block offsets goff of the
+  // distinct fine nodes, the coarse node itself first with weight 1, the
+  // others weight 1/2) instead of the 15-entry rows of gather.
+  std::vector<int> class_off;
+  std::vector<int> gptr;
+  std::vector<int64_t> goff;
 };
 
 struct HostProblem {
@@ -201,6 +219,20 @@ bool macro_in_set(const std::vector<unsigned char>& s, int m);
 void build_pair_tiles(int N, std::vector<Tile>& out, int target, int slabs);
 // Recompute every level's stencils for new per-macro coefficients.
 void set_coefficients(HostMesh& m, const double* coeff);
+// A macro mesh of general connectivity: nv vertex positions (3 doubles each),
+// nt macros (4 vertex ids each, any order), refinement levels r0..R, one
+// coefficient per macro (NULL = ones).  Throws std::invalid_argument for a
+// degenerate macro, an id out of range or a face shared by more than two
+// macros.
+void build_general_mesh(HostMesh& m, const double* verts, int nv, const int* tets, int nt, int R, int r0,
+                        const double* coeff);
+// The global problem (kind 0) of a general mesh: free interface nodes by
+// class, frozen copies, variable-length restriction gathers, coarse CSR.
+void build_general_problem(const HostMesh& m, HostProblem& p);
+// Global id of the volume node (i, j, k) (all positive, i + j + k < N) of a
+// macro of a general mesh at level L: n_if + macro * (N-1)(N-2)(N-3)/6 + its
+// index in the local (k, j, i) order.
+int64_t general_volume_id(const HostLevel& L, int macro, int i, int j, int k);
 // (Re)assemble a problem's coarse-level CG system from the current stencils
 // (needs p.act, p.macro_active and p.lv[0].free_if).
 void assemble_coarse(const HostMesh& m, HostProblem& p);

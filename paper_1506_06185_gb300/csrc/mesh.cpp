@@ -27,6 +27,36 @@ struct Prim {
   bool boundary = false;
 };
 
+// Key of a lattice node of a general mesh, the same from every macro that
+// contains it: the number of positive barycentric weights, then the values
+// vertex id * (N + 1) + weight of the positive weights in ascending order,
+// -1 padding first.  Sorting nodes by key orders them by primitive dimension
+// (vertex, edge, face, volume) and then by their vertices and weights.
+using NodeKey = std::array<int64_t, 5>;
+
+struct KeyHash {
+  size_t operator()(const NodeKey& k) const {
+    uint64_t h = 1469598103934665603ull;
+    for (int64_t x : k) {
+      h ^= (uint64_t)x;
+      h *= 1099511628211ull;
+    }
+    return (size_t)h;
+  }
+};
+
+NodeKey node_key(const HostMesh& m, int macro, int N, int i, int j, int k) {
+  const int w[4] = {N - i - j - k, i, j, k};
+  int64_t v[4];
+  int64_t nz = 0;
+  for (int q = 0; q < 4; ++q) {
+    v[q] = w[q] > 0 ? (int64_t)m.mverts[macro][q] * (N + 1) + w[q] : -1;
+    nz += w[q] > 0;
+  }
+  std::sort(v, v + 4);
+  return NodeKey{nz, v[0], v[1], v[2], v[3]};
+}
+
 int64_t grid_gid(const HostMesh& m, int N, int64_t x, int64_t y, int64_t z) {
   int64_t nx = (int64_t)m.sub[0] * N, ny = (int64_t)m.sub[1] * N;
   return (z * (ny + 1) + y) * (nx + 1) + x;
@@ -52,6 +82,13 @@ const double* corner_pos(const HostMesh& m, const int c[3]) {
 // macro's corners P0..P3 (moved corners), P0 + (i (P1-P0) + j (P2-P0) +
 // k (P3-P0)) / N; else the unit-cube grid position mapped by G.
 void position(const HostMesh& m, int macro, int N, int i, int j, int k, double out[3]) {
+  if (!m.mverts.empty()) {
+    const double* P[4];
+    for (int q = 0; q < 4; ++q) P[q] = &m.vpos[3 * (size_t)m.mverts[macro][q]];
+    for (int a = 0; a < 3; ++a)
+      out[a] = P[0][a] + (i * (P[1][a] - P[0][a]) + j * (P[2][a] - P[0][a]) + k * (P[3][a] - P[0][a])) / N;
+    return;
+  }
   if (!m.vpos.empty()) {
     const MacroGeo& g = m.geo[macro];
     int c[4][3];
@@ -409,7 +446,8 @@ void build_host_mesh(HostMesh& m, const int sub[3], int R, int r0, const double*
 // free nodes (volume interiors of the active macros, then free interface
 // nodes), the matrix assembled from the per-macro sub-stencils, and the maps
 // that gather the right-hand side and scatter the solution.
-void assemble_coarse(const HostMesh& m, HostProblem& p) {
+template <class IdFn>
+void assemble_coarse_ids(const HostMesh& m, HostProblem& p, IdFn node_id) {
   p.n_cg = 0;
   p.rowptr.clear();
   p.col.clear();
@@ -428,7 +466,7 @@ void assemble_coarse(const HostMesh& m, HostProblem& p) {
       for (int k = 1; k <= N - 3; ++k)
         for (int j = 1; j + k <= N - 2; ++j)
           for (int i = 1; i + j + k <= N - 1; ++i) {
-            cidx[node_gid(m, t, N, i, j, k)] = (int)dofs.size();
+            cidx[node_id(t, i, j, k)] = (int)dofs.size();
             dofs.push_back(Dof{{Copy{t, i, j, k}}, -1});
           }
     for (int n : p.lv[0].free_if) {
@@ -453,7 +491,7 @@ void assemble_coarse(const HostMesh& m, HostProblem& p) {
           dir_ijk(e, di, dj, dk);
           int ni = cp.i + di, nj = cp.j + dj, nk = cp.k + dk;
           if (!in_lattice(ni, nj, nk, N)) continue;
-          auto it = cidx.find(node_gid(m, cp.macro, N, ni, nj, nk));
+          auto it = cidx.find(node_id(cp.macro, ni, nj, nk));
           if (it == cidx.end()) continue;
           row[it->second] += w[e];
         }
@@ -470,6 +508,38 @@ void assemble_coarse(const HostMesh& m, HostProblem& p) {
       else p.fsrc.push_back(p.udst.back());
     }
   }
+
+int64_t general_volume_id(const HostLevel& L, int macro, int i, int j, int k) {
+  const int64_t N = L.N;
+  // interior slices k' < k hold T(N - 2 - k') nodes, T(m) = m (m + 1) / 2;
+  // rows j' < j of slice k hold N - 1 - j' - k nodes each
+  int64_t before = 0;
+  for (int64_t kk = 1; kk < k; ++kk) {
+    const int64_t M = N - 2 - kk;
+    before += M * (M + 1) / 2;
+  }
+  before += (int64_t)(j - 1) * (N - 1 - k) - (int64_t)(j - 1) * j / 2;
+  const int64_t nvol = (N - 1) * (N - 2) * (N - 3) / 6;
+  return (int64_t)L.n_if + (int64_t)macro * nvol + before + (i - 1);
+}
+
+void assemble_coarse(const HostMesh& m, HostProblem& p) {
+  if (m.general) {
+    const HostLevel& L = m.lv[0];
+    std::unordered_map<NodeKey, int64_t, KeyHash> if_id;
+    for (int n = 0; n < L.n_if; ++n) {
+      const Copy& cp = L.if_copy[L.if_cptr[n]];
+      if_id[node_key(m, cp.macro, L.N, cp.i, cp.j, cp.k)] = L.if_gid[n];
+    }
+    assemble_coarse_ids(m, p, [&](int t, int i, int j, int k) -> int64_t {
+      if (node_class(i, j, k, L.N) == 0) return general_volume_id(L, t, i, j, k);
+      return if_id.at(node_key(m, t, L.N, i, j, k));
+    });
+    return;
+  }
+  const int N = m.lv[0].N;
+  assemble_coarse_ids(m, p, [&](int t, int i, int j, int k) { return node_gid(m, t, N, i, j, k); });
+}
 
 void build_problem(const HostMesh& m, int kind, const std::vector<unsigned char>& faulty, HostProblem& p) {
   p = HostProblem();
@@ -560,6 +630,242 @@ void build_problem(const HostMesh& m, int kind, const std::vector<unsigned char>
       // with the interface free next to inactive macros (kind 3) the fine
       // points inside those macros are not reachable; their residual is zero
       if (cnt != NDIR && !(kind == 3 && cnt > 0)) throw std::runtime_error("restriction stencil incomplete");
+    }
+  }
+  assemble_coarse(m, p);
+}
+
+
+// ---------------------------------------------------------------------------
+// Macro meshes of general connectivity (§2.1: an unstructured base mesh of a
+// polyhedral domain, refined uniformly).  The per-macro blocks, stencils and
+// copy lists are the cube family's; what differs is how nodes are named (keys
+// from the macro vertices instead of grid coordinates), which nodes are
+// Dirichlet (those on faces of a single macro), and the smoother order of the
+// interface nodes: neighbouring macros' local colourings need not agree, so
+// the interface nodes get classes of their own (a greedy colouring of their
+// coupling graph in key order), visited after the four volume colours.
+// ---------------------------------------------------------------------------
+void build_general_mesh(HostMesh& m, const double* verts, int nv, const int* tets, int nt, int R, int r0,
+                        const double* coeff) {
+  if (nv < 4 || nt < 1 || !verts || !tets) throw std::invalid_argument("need vertices and macros");
+  m = HostMesh();
+  m.general = true;
+  m.R = R;
+  m.r0 = r0;
+  m.n_macro = nt;
+  for (int a = 0; a < 9; ++a) m.G[a] = a % 4 == 0 ? 1.0 : 0.0;
+  m.vpos.assign(verts, verts + 3 * (size_t)nv);
+  for (double x : m.vpos)
+    if (!std::isfinite(x)) throw std::invalid_argument("vertex positions must be finite");
+  m.coeff.assign(nt, 1.0);
+  if (coeff)
+    for (int t = 0; t < nt; ++t) m.coeff[t] = coeff[t];
+  m.mverts.resize(nt);
+  double scale = 0.0;
+  for (double x : m.vpos) scale = std::max(scale, std::fabs(x));
+  for (int t = 0; t < nt; ++t) {
+    for (int q = 0; q < 4; ++q) {
+      const int g = tets[4 * (size_t)t + q];
+      if (g < 0 || g >= nv) throw std::invalid_argument("macro " + std::to_string(t) + ": vertex id out of range");
+      m.mverts[t][q] = g;
+    }
+    double E[3][3];
+    for (int q = 0; q < 3; ++q)
+      for (int a = 0; a < 3; ++a) E[a][q] = m.vpos[3 * (size_t)m.mverts[t][q + 1] + a] - m.vpos[3 * (size_t)m.mverts[t][0] + a];
+    const double det = E[0][0] * (E[1][1] * E[2][2] - E[1][2] * E[2][1]) -
+                       E[0][1] * (E[1][0] * E[2][2] - E[1][2] * E[2][0]) +
+                       E[0][2] * (E[1][0] * E[2][1] - E[1][1] * E[2][0]);
+    if (!(std::fabs(det) > 1e-12 * scale * scale * scale))
+      throw std::invalid_argument("macro " + std::to_string(t) + " is degenerate");
+  }
+
+  // primitives keyed by their sorted vertex ids, with the adjacent macros
+  std::map<std::vector<int>, int> key;
+  std::vector<Prim> prims;
+  auto add = [&](int t, const std::vector<int>& loc) {
+    std::vector<std::pair<int, int>> gl;
+    for (int l : loc) gl.push_back({m.mverts[t][l], l});
+    std::sort(gl.begin(), gl.end());
+    std::vector<int> g;
+    for (auto& x : gl) g.push_back(x.first);
+    for (size_t q = 1; q < g.size(); ++q)
+      if (g[q] == g[q - 1]) throw std::invalid_argument("macro " + std::to_string(t) + " repeats a vertex");
+    auto it = key.find(g);
+    int id;
+    if (it == key.end()) {
+      id = (int)prims.size();
+      key[g] = id;
+      Prim pr;
+      pr.type = (int)loc.size() - 1;
+      pr.gv = g;
+      prims.push_back(pr);
+    } else {
+      id = it->second;
+    }
+    std::array<int, 3> lv = {-1, -1, -1};
+    for (size_t q = 0; q < gl.size(); ++q) lv[q] = gl[q].second;
+    prims[id].adj.push_back({t, lv});
+  };
+  for (int t = 0; t < nt; ++t) {
+    for (int q = 0; q < 4; ++q) add(t, {q});
+    for (int q = 0; q < 4; ++q)
+      for (int r = q + 1; r < 4; ++r) add(t, {q, r});
+    for (int o = 0; o < 4; ++o) {
+      std::vector<int> loc;
+      for (int q = 0; q < 4; ++q)
+        if (q != o) loc.push_back(q);
+      add(t, loc);
+    }
+  }
+  // Dirichlet boundary: the faces of a single macro, their edges and vertices
+  for (auto& pr : prims) {
+    if (pr.type != 2) continue;
+    if (pr.adj.size() > 2) throw std::invalid_argument("a face is shared by more than two macros");
+    if (pr.adj.size() != 1) continue;
+    pr.boundary = true;
+    for (int a = 0; a < 3; ++a) {
+      prims[key.at({pr.gv[a]})].boundary = true;
+      for (int b = a + 1; b < 3; ++b) prims[key.at({pr.gv[a], pr.gv[b]})].boundary = true;
+    }
+  }
+
+  m.lv.clear();
+  m.seven_point = false;
+  for (int r = r0; r <= R; ++r) {
+    HostLevel L;
+    L.r = r;
+    L.N = 1 << r;
+    L.block = build_slice_starts(L.N, L.SL);
+    const int N = L.N;
+    compute_level_weights(m, L);
+    // interface nodes in key order
+    struct INode { NodeKey k; int prim; std::array<int, 3> al; };
+    std::vector<INode> nodes;
+    for (int id = 0; id < (int)prims.size(); ++id) {
+      const Prim& pr = prims[id];
+      const int nvp = (int)pr.gv.size();
+      std::vector<std::array<int, 3>> alphas;
+      if (nvp == 1) alphas.push_back({N, 0, 0});
+      if (nvp == 2)
+        for (int a = 1; a <= N - 1; ++a) alphas.push_back({a, N - a, 0});
+      if (nvp == 3)
+        for (int a = 1; a <= N - 2; ++a)
+          for (int b = 1; a + b <= N - 1; ++b) alphas.push_back({a, b, N - a - b});
+      for (auto& al : alphas) {
+        int64_t v[4] = {-1, -1, -1, -1};
+        for (int q = 0; q < nvp; ++q) v[4 - nvp + q] = (int64_t)pr.gv[q] * (N + 1) + al[q];
+        nodes.push_back({NodeKey{nvp, v[0], v[1], v[2], v[3]}, id, al});
+      }
+    }
+    std::sort(nodes.begin(), nodes.end(), [](const INode& a, const INode& b) { return a.k < b.k; });
+    L.if_cptr.push_back(0);
+    for (size_t n = 0; n < nodes.size(); ++n) {
+      const Prim& pr = prims[nodes[n].prim];
+      L.if_gid.push_back((int64_t)n);
+      L.if_dirichlet.push_back(pr.boundary ? 1 : 0);
+      for (auto& ad : pr.adj) {
+        int lam[4] = {0, 0, 0, 0};
+        for (size_t q = 0; q < pr.gv.size(); ++q) lam[ad.second[q]] = nodes[n].al[q];
+        L.if_copy.push_back(Copy{ad.first, lam[1], lam[2], lam[3]});
+      }
+      L.if_cptr.push_back((int)L.if_copy.size());
+    }
+    L.n_if = (int)nodes.size();
+    // interface classes: greedy colouring of the coupling graph of the free
+    // interface nodes (lattice neighbours inside some macro), in key order
+    std::unordered_map<int64_t, int> at;               // macro * block + slot -> interface node
+    for (int n = 0; n < L.n_if; ++n)
+      for (int c = L.if_cptr[n]; c < L.if_cptr[n + 1]; ++c) {
+        const Copy& cp = L.if_copy[c];
+        at[(int64_t)cp.macro * L.block + lidx(L.SL.data(), N, cp.i, cp.j, cp.k)] = n;
+      }
+    std::vector<int> cls(L.n_if, -1);
+    int n_cls = 0;
+    for (int n = 0; n < L.n_if; ++n) {
+      if (L.if_dirichlet[n]) continue;
+      std::vector<char> used(64, 0);
+      for (int c = L.if_cptr[n]; c < L.if_cptr[n + 1]; ++c) {
+        const Copy& cp = L.if_copy[c];
+        for (int d = 1; d < NDIR; ++d) {
+          int di, dj, dk;
+          dir_ijk(d, di, dj, dk);
+          const int ni = cp.i + di, nj = cp.j + dj, nk = cp.k + dk;
+          if (!in_lattice(ni, nj, nk, N) || node_class(ni, nj, nk, N) == 0) continue;
+          auto it = at.find((int64_t)cp.macro * L.block + lidx(L.SL.data(), N, ni, nj, nk));
+          if (it != at.end() && cls[it->second] >= 0) {
+            if (cls[it->second] >= (int)used.size()) used.resize(cls[it->second] + 1, 0);
+            used[cls[it->second]] = 1;
+          }
+        }
+      }
+      int c = 0;
+      while (c < (int)used.size() && used[c]) ++c;
+      if (c > 250) throw std::invalid_argument("too many interface classes");
+      cls[n] = c;
+      n_cls = std::max(n_cls, c + 1);
+    }
+    L.if_colour.resize(L.n_if);
+    for (int n = 0; n < L.n_if; ++n) L.if_colour[n] = (unsigned char)(cls[n] < 0 ? 0 : cls[n]);
+    L.n_if_classes = n_cls;
+    build_pair_tiles(N, L.tiles_int, TILE_TARGET_DEFAULT, TILE_SLABS);
+    build_tiles(N, false, L.tiles_all);
+    m.lv.push_back(std::move(L));
+  }
+}
+
+void build_general_problem(const HostMesh& m, HostProblem& p) {
+  p = HostProblem();
+  p.kind = 0;
+  p.macro_active.assign(m.n_macro, 1);
+  for (int t = 0; t < m.n_macro; ++t) p.act.push_back(t);
+  const int nl = (int)m.lv.size();
+  p.lv.resize(nl);
+  for (int l = 0; l < nl; ++l) {
+    const HostLevel& L = m.lv[l];
+    HostProblemLevel& P = p.lv[l];
+    std::vector<std::vector<int>> bycls(std::max(1, L.n_if_classes));
+    for (int n = 0; n < L.n_if; ++n) {
+      if (!L.if_dirichlet[n]) {
+        bycls[L.if_colour[n]].push_back(n);
+      } else {
+        for (int c = L.if_cptr[n]; c < L.if_cptr[n + 1]; ++c) {
+          const Copy& cp = L.if_copy[c];
+          P.zero_off.push_back((int64_t)cp.macro * L.block + lidx(L.SL.data(), L.N, cp.i, cp.j, cp.k));
+        }
+      }
+    }
+    P.class_off.assign(1, 0);
+    for (auto& b : bycls) {
+      P.free_if.insert(P.free_if.end(), b.begin(), b.end());
+      P.class_off.push_back((int)P.free_if.size());
+    }
+    P.col_off[4] = (int)P.free_if.size();
+  }
+  // restriction gathers: the distinct fine nodes 2 (i, j, k) + d over all
+  // copies of each free coarse interface node, the node itself first
+  for (int l = 0; l + 1 < nl; ++l) {
+    const HostLevel& F = m.lv[l + 1];
+    const HostLevel& C = m.lv[l];
+    HostProblemLevel& P = p.lv[l];
+    P.gptr.assign(1, 0);
+    for (int n : P.free_if) {
+      std::vector<NodeKey> seen;
+      for (int pass = 0; pass < 2; ++pass)
+        for (int c = C.if_cptr[n]; c < C.if_cptr[n + 1]; ++c) {
+          const Copy& cp = C.if_copy[c];
+          for (int d = (pass == 0 ? 0 : 1); d < (pass == 0 ? 1 : NDIR); ++d) {
+            int di, dj, dk;
+            dir_ijk(d, di, dj, dk);
+            const int fi = 2 * cp.i + di, fj = 2 * cp.j + dj, fk = 2 * cp.k + dk;
+            if (!in_lattice(fi, fj, fk, F.N)) continue;
+            const NodeKey kf = node_key(m, cp.macro, F.N, fi, fj, fk);
+            if (std::find(seen.begin(), seen.end(), kf) != seen.end()) continue;
+            seen.push_back(kf);
+            P.goff.push_back((int64_t)cp.macro * F.block + lidx(F.SL.data(), F.N, fi, fj, fk));
+          }
+        }
+      P.gptr.push_back((int)P.goff.size());
     }
   }
   assemble_coarse(m, p);

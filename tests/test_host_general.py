@@ -1,0 +1,104 @@
+"""Host logic of the general-connectivity mesh builder on the CPU
+(paper_1506_06185_gb300/csrc/mesh.cpp, build_general_mesh and
+build_general_problem, compiled with the check program in tests/host/)
+against the general-mesh oracle (oracle/unstructured.py): node keys, the
+operator applied through macro blocks and copy lists, the interface smoother
+classes, the restriction gathers and the coarse CG matrix (§2.1, §3.1, §3.2
+Fig. 4), on meshes of another connectivity than the cube family."""
+
+import os
+import shutil
+import subprocess
+
+import numpy as np
+import pytest
+
+import hhg_inputs as I
+from oracle import unstructured as U
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def check_prog(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    cuda_inc = "/usr/local/cuda/include"
+    if not cxx or not os.path.isdir(cuda_inc):
+        pytest.skip("needs a C++ compiler and the CUDA headers")
+    out = tmp_path_factory.mktemp("generalcheck") / "general_check"
+    subprocess.check_call([cxx, "-O1", "-std=c++17", "-I" + cuda_inc, "-o", str(out),
+                           os.path.join(ROOT, "tests", "host", "general_check.cpp"),
+                           os.path.join(ROOT, "paper_1506_06185_gb300", "csrc", "mesh.cpp")])
+    return str(out)
+
+
+def _perm(path, lv):
+    """Library node order -> oracle node id, matched by node keys."""
+    keys = np.fromfile(path, dtype=np.int64).reshape(-1, 5)
+    assert len(keys) == lv.n
+    okeys = {tuple(k): q for q, k in enumerate(lv.keys.tolist())}
+    return np.array([okeys[tuple(k)] for k in keys.tolist()])
+
+
+@pytest.mark.parametrize("mesh,R", [("five", 4), ("five-moved", 4), ("kuhn", 3)])
+def test_general_builder_matches_oracle(check_prog, tmp_path, mesh, R):
+    if mesh == "kuhn":
+        v, t = I.kuhn_macro_mesh((2, 1, 2))
+    else:
+        v, t = I.five_tet_macro_mesh((2, 2, 1), seed=3 if mesh == "five-moved" else None, amp=0.12)
+    coeff = np.exp(np.random.default_rng(6).standard_normal(len(t)))
+    np.ascontiguousarray(v, dtype=np.float64).tofile(tmp_path / "verts.bin")
+    np.ascontiguousarray(t, dtype=np.int32).tofile(tmp_path / "tets.bin")
+    coeff.tofile(tmp_path / "coeff.bin")
+    subprocess.check_call([check_prog, str(len(v)), str(len(t)), str(R), str(tmp_path)])
+    om = U.UMesh(v, t, R, coeff=coeff)
+    perms = []
+    for l, lv in enumerate(om.levels):
+        perm = _perm(tmp_path / f"keys_{l}.bin", lv)
+        assert np.array_equal(np.sort(perm), np.arange(lv.n))       # a bijection
+        perms.append(perm)
+        # A g through blocks and copy lists = the oracle's assembled operator
+        g = np.fromfile(tmp_path / f"g_{l}.bin")
+        Ag = np.fromfile(tmp_path / f"Ag_{l}.bin")
+        go = np.zeros(lv.n)
+        go[perm] = g
+        ref = (lv.A @ go)[perm]
+        assert np.abs(Ag - ref).max() <= 1e-13 * np.abs(ref).max()
+        # interface classes = the oracle's, Dirichlet nodes marked
+        cls = np.fromfile(tmp_path / f"cls_{l}.bin", dtype=np.int32)
+        n_if = len(cls)
+        ocls = np.full(lv.n, -1)
+        for c, members in enumerate(lv.classes[4:]):
+            ocls[members] = c
+        assert np.array_equal(cls, ocls[perm[:n_if]])
+        assert np.all(lv.dim[perm[:n_if]] < 4) and np.all(lv.dim[perm[n_if:]] == 4)
+    # restriction gathers = P^T on the free coarse interface nodes
+    for l in range(len(om.levels) - 1):
+        r = np.fromfile(tmp_path / f"r_{l + 1}.bin")
+        ro = np.zeros(om.levels[l + 1].n)
+        ro[perms[l + 1]] = r
+        rc = om.P[l].T @ ro
+        d = np.fromfile(tmp_path / f"rc_{l}.bin").reshape(-1, 2)
+        ids = perms[l][d[:, 0].astype(np.int64)]
+        assert len(ids) == (~om.levels[l].boundary & (om.levels[l].dim < 4)).sum()
+        assert np.abs(rc[ids] - d[:, 1]).max() <= 1e-13 * max(1.0, np.abs(rc).max())
+    # coarse CG matrix = level-0 operator on the free nodes
+    lv0 = om.levels[0]
+    dump = np.fromfile(tmp_path / "csr.bin")
+    n, pos = int(dump[0]), 1
+    A = lv0.A.tocsr()
+    free = ~lv0.boundary
+    rows = []
+    for _ in range(n):
+        gid, nnz = int(dump[pos]), int(dump[pos + 1])
+        pos += 2
+        o = perms[0][gid]
+        rows.append(o)
+        refr = A.getrow(o).toarray().ravel()
+        refr[~free] = 0.0
+        mine = np.zeros_like(refr)
+        for _ in range(nnz):
+            mine[perms[0][int(dump[pos])]] += dump[pos + 1]
+            pos += 2
+        assert np.abs(mine - refr).max() <= 1e-13 * np.abs(refr).max()
+    assert sorted(rows) == sorted(np.nonzero(free)[0].tolist())
