@@ -101,6 +101,38 @@ typedef struct {
 int hhg_mesh_create(const hhg_mesh_desc* desc, hhg_mesh** out);
 int hhg_mesh_destroy(hhg_mesh* mesh);
 
+/* A macro mesh of general connectivity (§2.1: an unstructured tetrahedral
+ * base mesh of a polyhedral domain, refined uniformly inside every macro).
+ * vertices: host, n_vertices x 3 doubles; macros: host, n_macros x 4 vertex
+ * ids (any order, a conforming mesh: a face belongs to at most two macros);
+ * coeff: host, one positive coefficient per macro or NULL.  The Dirichlet
+ * boundary is every face of a single macro.  Global vectors of such a mesh
+ * list first the interface nodes (vertex, edge and face nodes of the macro
+ * mesh) sorted by key - the number of macro vertices with a positive
+ * barycentric weight, then the values vertex id * (2^levels + 1) + weight of
+ * those vertices in ascending order - and then the volume nodes macro by
+ * macro, node (i, j, k) of a macro (weights (N-i-j-k, i, j, k) on its
+ * vertices in the given order) in the order k, then j, then i; hhg_mesh_info
+ * gives their count.  One Gauss-Seidel step visits the volume nodes by their
+ * macro's colour (i + 2j + 3k) mod 4 and then the interface nodes in the
+ * classes of a greedy colouring of their couplings in key order.
+ * V-cycles and fault-free solves (FP64) are available; fault injection,
+ * recovery, mixed precision, coefficient changes and gradients, batching,
+ * autotuning and the allocation-free cycle return HHG_ERR_STATE for these
+ * meshes.  Errors: HHG_ERR_ARG for invalid sizes, ids, degenerate macros or
+ * a non-conforming mesh (found before any device use). */
+typedef struct {
+  int n_vertices;
+  const double* vertices;
+  int n_macros;
+  const int* macros;
+  int levels;             /* finest refinement R: 2^R intervals per macro edge */
+  int coarsest;           /* coarsest refinement r0 (>= 2, < levels; 0 = 2) */
+  int precision;          /* 64 or 32, as for hhg_mesh_desc */
+  const double* coeff;
+} hhg_general_desc;
+int hhg_mesh_create_general(const hhg_general_desc* desc, hhg_mesh** out);
+
 /* n_nodes: entries of a global vector; n_dof: non-Dirichlet fine nodes;
  * n_macro: macro-tetrahedra.  Any output pointer may be NULL. */
 int hhg_mesh_info(const hhg_mesh* mesh, int64_t* n_nodes, int64_t* n_dof, int* n_macro);

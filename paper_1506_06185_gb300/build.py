@@ -20,7 +20,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libhhg.so")
-SOURCES = ["mesh.cpp", "kernels.cu", "api.cu"]
+SOURCES = ["mesh.cpp", "kernels.cu", "general.cu", "api.cu"]
 HEADERS = ["hhg_internal.h", "hhg_kernels.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC,-O3", "--expt-relaxed-constexpr",

@@ -82,6 +82,11 @@ struct hhg_mesh {
   // each macro's centre weight (the FP64 volume Gauss-Seidel reads these)
   double* fs_top = nullptr;
   double* wsc_top = nullptr;
+  // general connectivity: every interface copy of the finest level (block
+  // offset, master), to fill the ghost shells after an import
+  int64_t* gen_copy_off = nullptr;
+  int* gen_copy_master = nullptr;
+  int n_gen_copy = 0;
   Prec<float> d32;
   MacroGeo* geo = nullptr;
   DevProblem global, faulty, healthy;
@@ -283,6 +288,9 @@ int upload_problem(hhg_mesh* m, const HostProblem& h, DevProblem& d) {
     HHG_TRY(upload(m, &d.lv[l].gather, h.lv[l].gather));
     HHG_TRY(upload(m, &d.lv[l].cptr, h.lv[l].cptr));
     HHG_TRY(upload(m, &d.lv[l].cps, h.lv[l].copies));
+    HHG_TRY(upload(m, &d.lv[l].gptr, h.lv[l].gptr));
+    HHG_TRY(upload(m, &d.lv[l].goff, h.lv[l].goff));
+    d.lv[l].class_off = h.lv[l].class_off;
   }
   d.n_cg = h.n_cg;
   d.nnz = (int64_t)h.val.size();
@@ -395,6 +403,26 @@ int smooth(hhg_mesh* m, Prec<T>& P, DevProblem& p, int l, int steps, cudaStream_
       fs = m->fs_top;
       wsc = m->wsc_top;
     }
+  if (m->host.general) {
+    // general connectivity: the four volume colours without interface nodes,
+    // then the interface classes, each an interface-only launch
+    ProbArgs qv = q;
+    qv.col_off[4] = 0;
+    ProbArgs qi = q;
+    qi.n_act = 0;
+    const std::vector<int>& co = p.lv[l].class_off;
+    for (int it = 0; it < steps; ++it) {
+      for (int c = 0; c < 4; ++c)
+        HHG_CUDA(gs_colour<T>(a, qv, D.u, D.uI, D.f, fI, D.W, P.Winv[l], c, false, s));
+      for (size_t c = 0; c + 1 < co.size(); ++c) {
+        if (co[c + 1] == co[c]) continue;
+        qi.col_off[0] = co[c];
+        qi.col_off[1] = co[c + 1];
+        HHG_CUDA(gs_colour<T>(a, qi, D.u, D.uI, D.f, fI, D.W, P.Winv[l], 0, false, s));
+      }
+    }
+    return HHG_OK;
+  }
   for (int it = 0; it < steps; ++it)
     for (int c = 0; c < 4; ++c) {
       cudaEvent_t b = nullptr, e = nullptr;
@@ -416,6 +444,17 @@ int vcycle_T(hhg_mesh* m, Prec<T>& P, DevProblem& p, int pre, int post, double c
     HHG_TRY(smooth<T>(m, P, p, l, pre, s));
     HHG_CUDA(residual<T>(a, q, D.u, D.uI, D.f, level_fI<T>(D, p, l == L), D.r, D.W, s7, true, nullptr, nullptr, s));
     DevLevel<T>& C = P.lv[l - 1];
+    if (m->host.general) {
+      // volume part as usual, interface part through the variable-length gathers
+      ProbArgs qc = pargs(p, l - 1);
+      ProbArgs qv = qc;
+      qv.col_off[4] = 0;
+      qv.n_zero = 0;
+      HHG_CUDA(restrict_to<T>(plargs(m, p, l - 1), a, qv, D.r, C.f, C.fI, C.u, C.uI, s));
+      HHG_CUDA(general_restrict_if<T>(plargs(m, p, l - 1), qc, p.lv[l - 1].gptr, p.lv[l - 1].goff, D.r, C.fI, C.u,
+                                      C.uI, s));
+      continue;
+    }
     HHG_CUDA(restrict_to<T>(plargs(m, p, l - 1), a, pargs(p, l - 1), D.r, C.f, C.fI, C.u, C.uI, s));
   }
   HHG_CUDA(coarse_cg<T>(p, P.lv[0].f, P.lv[0].fI, P.lv[0].u, P.lv[0].uI, cg_rtol, cg_maxit, s));
@@ -543,13 +582,39 @@ int local_cycles(hhg_mesh* m, int n, bool mixed, int pre, int post, double cg_rt
   return HHG_OK;
 }
 
+// Entries of a global vector: the grid nodes of the cube family; for general
+// connectivity the interface nodes plus every macro's volume nodes.
+int64_t global_nodes(const hhg_mesh* m) {
+  if (m->host.general) {
+    const HostLevel& L = m->host.lv.back();
+    return (int64_t)L.n_if + (int64_t)m->host.n_macro * (L.N - 1) * (L.N - 2) * (L.N - 3) / 6;
+  }
+  return (m->host.nx + 1) * (m->host.ny + 1) * (m->host.nz + 1);
+}
+
+int64_t global_dof(const hhg_mesh* m) {
+  if (m->host.general) {
+    const HostLevel& L = m->host.lv.back();
+    int64_t dir = 0;
+    for (unsigned char d : L.if_dirichlet) dir += d;
+    return global_nodes(m) - dir;
+  }
+  return (m->host.nx - 1) * (m->host.ny - 1) * (m->host.nz - 1);
+}
+
+int refuse_general(const hhg_mesh* m, const char* what) {
+  if (m && m->host.general)
+    return fail(HHG_ERR_STATE, std::string(what) + " is not available for meshes of general connectivity");
+  return HHG_OK;
+}
+
 const double* stage_in(hhg_mesh* m, const double* g, cudaStream_t s, int* rc) {
   *rc = HHG_OK;
   cudaPointerAttributes at;
   cudaError_t e = cudaPointerGetAttributes(&at, g);
   if (e != cudaSuccess) cudaGetLastError();
   if (e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged)) return g;
-  const int64_t n = (m->host.nx + 1) * (m->host.ny + 1) * (m->host.nz + 1);
+  const int64_t n = global_nodes(m);
   if (!m->staging) {
     *rc = dalloc(m, &m->staging, (size_t)n);
     if (*rc != HHG_OK) return nullptr;
@@ -916,6 +981,7 @@ extern "C" {
 
 int hhg_vcycle_noalloc(hhg_mesh* m, int pre, int post, void* stream) {
   if (!m || pre < 0 || post < 0) return fail(HHG_ERR_ARG, "invalid argument");
+  HHG_TRY(refuse_general(m, "the allocation-free cycle"));
   if (m->global.n_cg > NOALLOC_MAX_COARSE)
     return fail(HHG_ERR_ARG, "coarse problem has " + std::to_string(m->global.n_cg) +
                                  " unknowns; the allocation-free V-cycle holds at most " +
@@ -943,6 +1009,74 @@ int hhg_last_error(char* buf, size_t len) {
   return g_err_code;
 }
 
+// Device side of a new mesh (after its host mesh is built): level tables,
+// arrays of both precisions, the global problem, streams and events.  On
+// failure everything allocated is freed.
+int setup_device(hhg_mesh* m) {
+  int rc = HHG_OK;
+  auto cleanup = [&](int code) {
+    free_all(m);
+    return code;
+  };
+  if (cudaGetDevice(&m->device) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(HHG_ERR_CUDA, "no CUDA device");
+  }
+  const int nl = (int)m->host.lv.size();
+  m->tab.assign(nl, DevLevelTables());
+  for (int l = 0; l < nl && rc == HHG_OK; ++l) {
+    const HostLevel& H = m->host.lv[l];
+    DevLevelTables& t = m->tab[l];
+    if ((rc = upload(m, &t.SL, H.SL)) != HHG_OK) break;
+    if ((rc = upload(m, &t.if_gid, H.if_gid)) != HHG_OK) break;
+    if ((rc = upload(m, &t.if_cptr, H.if_cptr)) != HHG_OK) break;
+    if ((rc = upload(m, &t.if_copy, H.if_copy)) != HHG_OK) break;
+    if ((rc = upload(m, &t.tiles_int, H.tiles_int)) != HHG_OK) break;
+    if ((rc = upload(m, &t.tiles_all, H.tiles_all)) != HHG_OK) break;
+    t.n_tiles_int = (int)H.tiles_int.size();
+    t.n_tiles_all = (int)H.tiles_all.size();
+  }
+  if (rc == HHG_OK) rc = upload(m, &m->geo, m->host.geo);
+  if (rc == HHG_OK) rc = alloc_levels<double>(m, m->d64, true);
+  if (rc == HHG_OK) rc = alloc_scaled(m);
+  if (rc == HHG_OK && m->precision == 32) rc = alloc_levels<float>(m, m->d32, true);
+  if (rc == HHG_OK) {
+    HostProblem hg;
+    try {
+      if (m->host.general) build_general_problem(m->host, hg);
+      else build_problem(m->host, 0, std::vector<unsigned char>(m->host.n_macro, 0), hg);
+    } catch (const std::exception& e) {
+      rc = fail(HHG_ERR_ARG, std::string("problem: ") + e.what());
+    }
+    if (rc == HHG_OK) rc = upload_problem(m, hg, m->global);
+  }
+  if (rc == HHG_OK && m->host.general) {
+    const HostLevel& H = m->host.lv.back();
+    std::vector<int64_t> off;
+    std::vector<int> master;
+    for (int n = 0; n < H.n_if; ++n)
+      for (int c = H.if_cptr[n]; c < H.if_cptr[n + 1]; ++c) {
+        const Copy& cp = H.if_copy[c];
+        off.push_back((int64_t)cp.macro * H.block + lidx(H.SL.data(), H.N, cp.i, cp.j, cp.k));
+        master.push_back(n);
+      }
+    m->n_gen_copy = (int)off.size();
+    rc = upload(m, &m->gen_copy_off, off);
+    if (rc == HHG_OK) rc = upload(m, &m->gen_copy_master, master);
+  }
+  if (rc != HHG_OK) return cleanup(rc);
+  if (cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+      cudaMallocHost(&m->host_scalar, sizeof(double) * 8) != cudaSuccess) {
+    cudaGetLastError();
+    return cleanup(fail(HHG_ERR_CUDA, "stream / event creation failed"));
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) return cleanup(fail(HHG_ERR_CUDA, "device error during setup"));
+  return HHG_OK;
+}
+
 int hhg_mesh_create(const hhg_mesh_desc* desc, hhg_mesh** out) {
   if (!desc || !out) return fail(HHG_ERR_ARG, "null argument");
   *out = nullptr;
@@ -966,52 +1100,35 @@ int hhg_mesh_create(const hhg_mesh_desc* desc, hhg_mesh** out) {
     return fail(HHG_ERR_ARG, std::string("mesh: ") + e.what());
   }
   m->precision = desc->precision;
-  int rc = HHG_OK;
-  auto cleanup = [&](int code) {
-    free_all(m.get());
-    return code;
-  };
-  if (cudaGetDevice(&m->device) != cudaSuccess) {
-    cudaGetLastError();
-    return fail(HHG_ERR_CUDA, "no CUDA device");
+  HHG_TRY(setup_device(m.get()));
+  *out = m.release();
+  return HHG_OK;
+}
+
+int hhg_mesh_create_general(const hhg_general_desc* desc, hhg_mesh** out) {
+  if (!desc || !out) return fail(HHG_ERR_ARG, "null argument");
+  *out = nullptr;
+  const int r0 = desc->coarsest > 0 ? desc->coarsest : 2;
+  if (!desc->vertices || !desc->macros || desc->n_vertices < 4 || desc->n_macros < 1)
+    return fail(HHG_ERR_ARG, "need vertices and macros");
+  if (r0 < 2) return fail(HHG_ERR_ARG, "coarsest refinement must be >= 2");
+  if (desc->levels <= r0 || desc->levels > 10) return fail(HHG_ERR_ARG, "levels must be in (coarsest, 10]");
+  if (desc->precision != 64 && desc->precision != 32) return fail(HHG_ERR_ARG, "precision must be 64 or 32");
+  if (desc->coeff)
+    for (int t = 0; t < desc->n_macros; ++t)
+      if (!(desc->coeff[t] > 0.0)) return fail(HHG_ERR_ARG, "coefficients must be positive");
+  std::unique_ptr<hhg_mesh> m(new (std::nothrow) hhg_mesh());
+  if (!m) return fail(HHG_ERR_OOM, "host allocation failed");
+  try {
+    build_general_mesh(m->host, desc->vertices, desc->n_vertices, desc->macros, desc->n_macros, desc->levels, r0,
+                       desc->coeff);
+  } catch (const std::bad_alloc&) {
+    return fail(HHG_ERR_OOM, "host allocation failed while building the mesh");
+  } catch (const std::exception& e) {
+    return fail(HHG_ERR_ARG, std::string("mesh: ") + e.what());
   }
-  const int nl = (int)m->host.lv.size();
-  m->tab.assign(nl, DevLevelTables());
-  for (int l = 0; l < nl && rc == HHG_OK; ++l) {
-    const HostLevel& H = m->host.lv[l];
-    DevLevelTables& t = m->tab[l];
-    if ((rc = upload(m.get(), &t.SL, H.SL)) != HHG_OK) break;
-    if ((rc = upload(m.get(), &t.if_gid, H.if_gid)) != HHG_OK) break;
-    if ((rc = upload(m.get(), &t.if_cptr, H.if_cptr)) != HHG_OK) break;
-    if ((rc = upload(m.get(), &t.if_copy, H.if_copy)) != HHG_OK) break;
-    if ((rc = upload(m.get(), &t.tiles_int, H.tiles_int)) != HHG_OK) break;
-    if ((rc = upload(m.get(), &t.tiles_all, H.tiles_all)) != HHG_OK) break;
-    t.n_tiles_int = (int)H.tiles_int.size();
-    t.n_tiles_all = (int)H.tiles_all.size();
-  }
-  if (rc == HHG_OK) rc = upload(m.get(), &m->geo, m->host.geo);
-  if (rc == HHG_OK) rc = alloc_levels<double>(m.get(), m->d64, true);
-  if (rc == HHG_OK) rc = alloc_scaled(m.get());
-  if (rc == HHG_OK && m->precision == 32) rc = alloc_levels<float>(m.get(), m->d32, true);
-  if (rc == HHG_OK) {
-    HostProblem hg;
-    try {
-      build_problem(m->host, 0, std::vector<unsigned char>(m->host.n_macro, 0), hg);
-    } catch (const std::exception& e) {
-      rc = fail(HHG_ERR_ARG, std::string("problem: ") + e.what());
-    }
-    if (rc == HHG_OK) rc = upload_problem(m.get(), hg, m->global);
-  }
-  if (rc != HHG_OK) return cleanup(rc);
-  if (cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaMallocHost(&m->host_scalar, sizeof(double) * 8) != cudaSuccess) {
-    cudaGetLastError();
-    return cleanup(fail(HHG_ERR_CUDA, "stream / event creation failed"));
-  }
-  if (cudaDeviceSynchronize() != cudaSuccess) return cleanup(fail(HHG_ERR_CUDA, "device error during setup"));
+  m->precision = desc->precision;
+  HHG_TRY(setup_device(m.get()));
   *out = m.release();
   return HHG_OK;
 }
@@ -1036,8 +1153,8 @@ int hhg_mesh_destroy(hhg_mesh* m) {
 
 int hhg_mesh_info(const hhg_mesh* m, int64_t* n_nodes, int64_t* n_dof, int* n_macro) {
   if (!m) return fail(HHG_ERR_ARG, "null mesh");
-  if (n_nodes) *n_nodes = (m->host.nx + 1) * (m->host.ny + 1) * (m->host.nz + 1);
-  if (n_dof) *n_dof = (m->host.nx - 1) * (m->host.ny - 1) * (m->host.nz - 1);
+  if (n_nodes) *n_nodes = global_nodes(m);
+  if (n_dof) *n_dof = global_dof(m);
   if (n_macro) *n_macro = m->host.n_macro;
   return HHG_OK;
 }
@@ -1055,10 +1172,13 @@ int hhg_set_problem(hhg_mesh* m, const double* f, const double* u0, void* stream
   const LevelArgs a = largs(m, L);
   DevLevel<double>& D = m->d64.lv[L];
   int rc;
+  const bool gen = m->host.general;
+  const int64_t n_if = m->host.lv[L].n_if;
   if (f) {
     const double* g = stage_in(m, f, s, &rc);
     if (!g) return rc;
-    HHG_CUDA(import_vec<double>(a, m->geo, m->host.n_macro, m->host.nx, m->host.ny, g, D.f, D.fI, false, s));
+    if (gen) HHG_CUDA(general_import_vol<double>(a, m->host.n_macro, n_if, g, D.f, s));
+    else HHG_CUDA(import_vec<double>(a, m->geo, m->host.n_macro, m->host.nx, m->host.ny, g, D.f, D.fI, false, s));
     HHG_CUDA(import_masters<double>(a.if_gid, m->host.lv[L].n_if, g, D.fI, s));
     if (m->fs_top)
       HHG_CUDA(scale_blocks(D.f, m->d64.Winv[L], m->fs_top, m->host.n_macro, m->host.lv[L].block, s));
@@ -1066,8 +1186,14 @@ int hhg_set_problem(hhg_mesh* m, const double* f, const double* u0, void* stream
   if (u0) {
     const double* g = stage_in(m, u0, s, &rc);
     if (!g) return rc;
-    HHG_CUDA(import_vec<double>(a, m->geo, m->host.n_macro, m->host.nx, m->host.ny, g, D.u, D.uI, true, s));
-    HHG_CUDA(import_masters<double>(a.if_gid, m->host.lv[L].n_if, g, D.uI, s));
+    if (gen) {
+      HHG_CUDA(general_import_vol<double>(a, m->host.n_macro, n_if, g, D.u, s));
+      HHG_CUDA(import_masters<double>(a.if_gid, m->host.lv[L].n_if, g, D.uI, s));
+      HHG_CUDA(restore_copies(D.u, D.uI, m->gen_copy_off, m->gen_copy_master, m->n_gen_copy, s));
+    } else {
+      HHG_CUDA(import_vec<double>(a, m->geo, m->host.n_macro, m->host.nx, m->host.ny, g, D.u, D.uI, true, s));
+      HHG_CUDA(import_masters<double>(a.if_gid, m->host.lv[L].n_if, g, D.uI, s));
+    }
   }
   return HHG_OK;
 }
@@ -1083,12 +1209,15 @@ int hhg_get_solution(hhg_mesh* m, double* u, void* stream) {
   if (e != cudaSuccess) cudaGetLastError();
   const bool dev = e == cudaSuccess && (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
   double* g = u;
-  const int64_t n = (m->host.nx + 1) * (m->host.ny + 1) * (m->host.nz + 1);
+  const int64_t n = global_nodes(m);
   if (!dev) {
     if (!m->staging) HHG_TRY(dalloc(m, &m->staging, (size_t)n));
     g = m->staging;
   }
-  HHG_CUDA(export_vec<double>(a, m->geo, m->host.n_macro, m->host.nx, m->host.ny, D.u, D.uI, g, s));
+  if (m->host.general)
+    HHG_CUDA(general_export_vol<double>(a, m->host.n_macro, m->host.lv[L].n_if, D.u, g, s));
+  else
+    HHG_CUDA(export_vec<double>(a, m->geo, m->host.n_macro, m->host.nx, m->host.ny, D.u, D.uI, g, s));
   HHG_CUDA(export_masters<double>(a.if_gid, m->host.lv[L].n_if, D.uI, g, s));
   if (!dev) {
     HHG_CUDA(cudaMemcpyAsync(u, g, (size_t)n * sizeof(double), cudaMemcpyDefault, s));
@@ -1112,6 +1241,7 @@ int hhg_residual_norm(hhg_mesh* m, double* out, void* stream) {
 
 int hhg_inject_fault(hhg_mesh* m, const int* ids, int n, void* stream) {
   if (!m) return fail(HHG_ERR_ARG, "null mesh");
+  HHG_TRY(refuse_general(m, "fault injection"));
   std::vector<unsigned char> set;
   HHG_TRY(check_ids(m, ids, n, set));
   HHG_TRY(setup_fault(m, set));
@@ -1121,6 +1251,7 @@ int hhg_inject_fault(hhg_mesh* m, const int* ids, int n, void* stream) {
 int hhg_recover_local(hhg_mesh* m, const int* ids, int n, int n_local, int n_global, double* seconds_local,
                       double* seconds_global, void* stream) {
   if (!m || n_local < 0 || n_global < 0) return fail(HHG_ERR_ARG, "invalid argument");
+  HHG_TRY(refuse_general(m, "recovery"));
   std::vector<unsigned char> set;
   HHG_TRY(check_ids(m, ids, n, set));
   HHG_TRY(setup_fault(m, set));
@@ -1131,6 +1262,7 @@ int hhg_recover_local(hhg_mesh* m, const int* ids, int n, int n_local, int n_glo
 int hhg_recover_dn(hhg_mesh* m, const int* ids, int n, int n_global, double eta, int* n_local_run,
                    double* seconds_local, double* seconds_global, void* stream) {
   if (!m || n_global < 0 || !(eta >= 0.0)) return fail(HHG_ERR_ARG, "invalid argument");
+  HHG_TRY(refuse_general(m, "recovery"));
   std::vector<unsigned char> set;
   HHG_TRY(check_ids(m, ids, n, set));
   HHG_TRY(setup_dn(m, set));
@@ -1140,6 +1272,7 @@ int hhg_recover_dn(hhg_mesh* m, const int* ids, int n, int n_global, double eta,
 
 int hhg_set_coefficients(hhg_mesh* m, const double* coeff, void* stream) {
   if (!m || !coeff) return fail(HHG_ERR_ARG, "null argument");
+  HHG_TRY(refuse_general(m, "changing coefficients"));
   for (int t = 0; t < m->host.n_macro; ++t)
     if (!(coeff[t] > 0.0)) return fail(HHG_ERR_ARG, "coefficients must be positive");
   HHG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
@@ -1148,6 +1281,7 @@ int hhg_set_coefficients(hhg_mesh* m, const double* coeff, void* stream) {
 
 int hhg_grad_coeff(hhg_mesh* m, const double* u, const double* lam, double* grad, void* stream) {
   if (!m || !u || !lam || !grad) return fail(HHG_ERR_ARG, "null argument");
+  HHG_TRY(refuse_general(m, "the coefficient gradient"));
   cudaStream_t s = (cudaStream_t)stream;
   const int L = (int)m->host.lv.size() - 1;
   const LevelArgs a = largs(m, L);
@@ -1176,6 +1310,7 @@ int hhg_grad_coeff(hhg_mesh* m, const double* u, const double* lam, double* grad
 
 int hhg_autotune(hhg_mesh* m, int reps, int* chosen, void* stream) {
   if (!m || reps < 1) return fail(HHG_ERR_ARG, "invalid argument");
+  HHG_TRY(refuse_general(m, "autotuning"));
   cudaStream_t s = (cudaStream_t)stream;
   const int nl = (int)m->host.lv.size();
   drop_local_graph(m);
@@ -1198,9 +1333,11 @@ int hhg_batch_create(hhg_mesh* global, int global_cycles, hhg_mesh* const* meshe
   std::unique_ptr<hhg_batch> b(new (std::nothrow) hhg_batch());
   if (!b) return fail(HHG_ERR_OOM, "host allocation failed");
   b->mixed = mixed != 0;
+  if (global) HHG_TRY(refuse_general(global, "batched recovery"));
   for (int t = 0; t < n_tasks; ++t) {
     hhg_mesh* m = meshes[t];
     if (!m || cycles[t] < 0) return fail(HHG_ERR_ARG, "invalid task");
+    HHG_TRY(refuse_general(m, "batched recovery"));
     if (b->mixed && m->precision != 32) return fail(HHG_ERR_STATE, "mixed precision needs precision-32 meshes");
     for (int q = 0; q < t; ++q)
       if (meshes[q] == m) return fail(HHG_ERR_ARG, "a mesh may appear in one task only");
@@ -1357,6 +1494,8 @@ int hhg_launch_count(int64_t* count) {
 int hhg_solve(hhg_mesh* m, const hhg_solve_opts* o, double* hist, int* n_hist, int* cycles, void* stream) {
   if (!m || !o) return fail(HHG_ERR_ARG, "null argument");
   if (o->max_cycles < 0 || !(o->rtol >= 0.0)) return fail(HHG_ERR_ARG, "invalid rtol / max_cycles");
+  if (o->fault_cycle > 0 || o->n_faults > 0) HHG_TRY(refuse_general(m, "fault injection"));
+  if (o->mixed_precision) HHG_TRY(refuse_general(m, "mixed precision"));
   const bool mixed = o->mixed_precision != 0;
   if (mixed && m->precision != 32) return fail(HHG_ERR_STATE, "mixed precision needs a precision-32 mesh");
   const int pre = o->pre > 0 ? o->pre : 3, post = o->post > 0 ? o->post : 3;

@@ -265,6 +265,9 @@ struct DevLevelTables {
 };
 
 struct DevProblemLevel {
+  int* gptr = nullptr;                // general meshes: restriction gathers (CSR)
+  int64_t* goff = nullptr;
+  std::vector<int> class_off;         // general meshes: interface classes in free_if
   int* free_if = nullptr;
   int col_off[5] = {0, 0, 0, 0, 0};
   int64_t* zero_off = nullptr;

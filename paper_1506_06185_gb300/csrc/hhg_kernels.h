@@ -118,4 +118,22 @@ cudaError_t add_correction(const LevelArgs& L, const ProbArgs& p, double* u, dou
 template <class T>
 cudaError_t zero_problem_blocks(const LevelArgs& L, const ProbArgs& p, T* u, T* uI, cudaStream_t s);
 
+// Macro meshes of general connectivity (general.cu).  Global vectors list
+// the interface nodes first (their masters move with import_masters /
+// export_masters) and then the volume nodes macro by macro in local
+// (k, j, i) order, which these two move into / out of the blocks.
+template <class T>
+cudaError_t general_import_vol(const LevelArgs& L, int n_macro, int64_t n_if, const double* g, T* blocks,
+                               cudaStream_t s);
+template <class T>
+cudaError_t general_export_vol(const LevelArgs& L, int n_macro, int64_t n_if, const T* blocks, double* g,
+                               cudaStream_t s);
+// Restriction onto the free coarse interface nodes through variable-length
+// gathers (gptr over pc.free_if, fine block offsets goff, the node itself
+// first) and zeroing of the coarse correction there, on their copies and at
+// the frozen copies pc.zero_off; the volume part is restrict_to's.
+template <class T>
+cudaError_t general_restrict_if(const LevelArgs& C, const ProbArgs& pc, const int* gptr, const int64_t* goff,
+                                const T* rf, T* fIc, T* uc, T* uIc, cudaStream_t s);
+
 }  // namespace hhg

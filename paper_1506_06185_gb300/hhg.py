@@ -27,13 +27,20 @@ EXPORTS = ["hhg_mesh_create", "hhg_mesh_destroy", "hhg_mesh_info", "hhg_mesh_byt
            "hhg_get_solution", "hhg_vcycle", "hhg_residual_norm", "hhg_inject_fault", "hhg_recover_local",
            "hhg_solve", "hhg_last_error", "hhg_profile_enable", "hhg_profile_read", "hhg_profile_info",
            "hhg_launch_count", "hhg_vcycle_noalloc", "hhg_set_coefficients", "hhg_grad_coeff",
-           "hhg_autotune", "hhg_batch_create", "hhg_batch_launch", "hhg_batch_destroy", "hhg_recover_dn"]
+           "hhg_autotune", "hhg_batch_create", "hhg_batch_launch", "hhg_batch_destroy", "hhg_recover_dn",
+           "hhg_mesh_create_general"]
 
 
 class hhg_mesh_desc(C.Structure):
     _fields_ = [("subcubes", C.c_int * 3), ("levels", C.c_int), ("coarsest", C.c_int), ("precision", C.c_int),
                 ("coeff", C.POINTER(C.c_double)), ("affine", C.POINTER(C.c_double)),
                 ("vertex_pos", C.POINTER(C.c_double))]
+
+
+class hhg_general_desc(C.Structure):
+    _fields_ = [("n_vertices", C.c_int), ("vertices", C.POINTER(C.c_double)), ("n_macros", C.c_int),
+                ("macros", C.POINTER(C.c_int)), ("levels", C.c_int), ("coarsest", C.c_int),
+                ("precision", C.c_int), ("coeff", C.POINTER(C.c_double))]
 
 
 class hhg_fault(C.Structure):
@@ -63,6 +70,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
     sig = {
         "hhg_mesh_create": ([C.POINTER(hhg_mesh_desc), C.POINTER(P)], C.c_int),
         "hhg_mesh_destroy": ([P], C.c_int),
+        "hhg_mesh_create_general": ([C.POINTER(hhg_general_desc), C.POINTER(P)], C.c_int),
         "hhg_mesh_info": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int)], C.c_int),
         "hhg_mesh_bytes": ([P, C.POINTER(C.c_int64)], C.c_int),
         "hhg_set_problem": ([P, P, P, P], C.c_int),
@@ -174,6 +182,26 @@ def hhg_mesh_create(subcubes, levels, coarsest=2, precision=64, coeff=None, affi
         d.vertex_pos = v.ctypes.data_as(C.POINTER(C.c_double))
     h = C.c_void_p()
     _check(lib().hhg_mesh_create(C.byref(d), C.byref(h)))
+    return h
+
+
+def hhg_mesh_create_general(vertices, macros, levels, coarsest=2, precision=64, coeff=None):
+    v = np.ascontiguousarray(vertices, dtype=np.float64)
+    t = np.ascontiguousarray(macros, dtype=np.int32)
+    if v.ndim != 2 or v.shape[1] != 3 or t.ndim != 2 or t.shape[1] != 4:
+        raise ValueError("vertices must be (nv, 3) and macros (nt, 4)")
+    d = hhg_general_desc()
+    d.n_vertices, d.n_macros = v.shape[0], t.shape[0]
+    d.vertices = v.ctypes.data_as(C.POINTER(C.c_double))
+    d.macros = t.ctypes.data_as(C.POINTER(C.c_int))
+    d.levels, d.coarsest, d.precision = int(levels), int(coarsest), int(precision)
+    keep = [v, t]
+    if coeff is not None:
+        c = np.ascontiguousarray(coeff, dtype=np.float64)
+        keep.append(c)
+        d.coeff = c.ctypes.data_as(C.POINTER(C.c_double))
+    h = C.c_void_p()
+    _check(lib().hhg_mesh_create_general(C.byref(d), C.byref(h)))
     return h
 
 
@@ -357,6 +385,20 @@ class Mesh:
         self.n_nodes, self.n_dof, self.n_macro = hhg_mesh_info(self.h)
         N = 1 << self.levels
         self.shape = (self.subcubes[2] * N + 1, self.subcubes[1] * N + 1, self.subcubes[0] * N + 1)
+
+    @classmethod
+    def general(cls, vertices, macros, levels, coarsest=2, precision=64, coeff=None):
+        """A macro mesh of general connectivity (vertex positions and the four
+        vertex ids of every macro); vectors are flat, in the library's node
+        order (see ``hhg_mesh_create_general`` in include/hhg.h)."""
+        self = cls.__new__(cls)
+        self.h = None
+        self.subcubes = None
+        self.levels = int(levels)
+        self.h = hhg_mesh_create_general(vertices, macros, levels, coarsest, precision, coeff)
+        self.n_nodes, self.n_dof, self.n_macro = hhg_mesh_info(self.h)
+        self.shape = (self.n_nodes,)
+        return self
 
     def close(self):
         if self.h is not None:

@@ -100,3 +100,36 @@ def test_moved_corners_are_validated_before_device_use():
         with pytest.raises(hhg.HHGError) as e:
             hhg.hhg_mesh_create(sub, 3, vertex_pos=vp)
         assert e.value.code == hhg.HHG_ERR_CUDA
+
+
+def test_general_meshes_are_validated_before_device_use():
+    import numpy as np
+    import torch
+    import hhg_inputs as I
+    from paper_1506_06185_gb300 import hhg
+    v, t = I.five_tet_macro_mesh((2, 1, 1))
+    bad = t.copy()
+    bad[0, 0] = len(v)                                    # id out of range
+    with pytest.raises(hhg.HHGError) as e:
+        hhg.hhg_mesh_create_general(v, bad, 3)
+    assert e.value.code == hhg.HHG_ERR_ARG
+    flat = v.copy()
+    flat[:, 2] = 0.0                                      # every macro flattened
+    with pytest.raises(hhg.HHGError) as e:
+        hhg.hhg_mesh_create_general(flat, t, 3)
+    assert e.value.code == hhg.HHG_ERR_ARG and "degenerate" in str(e.value)
+    rep = t.copy()
+    rep[0, 1] = rep[0, 0]                                 # a repeated vertex
+    with pytest.raises(hhg.HHGError) as e:
+        hhg.hhg_mesh_create_general(v, rep, 3)
+    assert e.value.code == hhg.HHG_ERR_ARG
+    tri = np.vstack([t, t[:1]])                           # one face shared by three macros
+    with pytest.raises(hhg.HHGError) as e:
+        hhg.hhg_mesh_create_general(v, tri, 3)
+    assert e.value.code == hhg.HHG_ERR_ARG
+    with pytest.raises(ValueError):
+        hhg.hhg_mesh_create_general(v, t[:, :3], 3)
+    if not torch.cuda.is_available():
+        with pytest.raises(hhg.HHGError) as e:
+            hhg.hhg_mesh_create_general(v, t, 3)
+        assert e.value.code == hhg.HHG_ERR_CUDA
