@@ -16,19 +16,10 @@ namespace {
 
 constexpr int GCTA = 256;
 
-// S3(m) = sum_{x=1..m} x (x + 1) / 2
-__device__ __forceinline__ int64_t tet_sum(int64_t m) { return m <= 0 ? 0 : m * (m + 1) * (m + 2) / 6; }
-
-// Index of volume node (i, j, k) of a macro in the local (k, j, i) order of
-// its interior: slices k' < k hold T(N - 2 - k') nodes, rows j' < j of slice
-// k hold N - 1 - j' - k nodes each.
-__device__ __forceinline__ int64_t vol_local(int N, int i, int j, int k) {
-  return tet_sum(N - 3) - tet_sum(N - 2 - k) + (int64_t)(j - 1) * (N - 1 - k) - (int64_t)(j - 1) * j / 2 + (i - 1);
-}
-
-// One thread per volume node of every macro: t = q / nvol, local index q % nvol
-// mapped back to (i, j, k) by walking slices and rows (N is small enough
-// that the walk costs less than the memory traffic it feeds).
+// One thread per volume node of every macro: t = q / nvol, and the local
+// index q % nvol (order k, then j, then i; slice k holds T(N - 2 - k) nodes,
+// T(m) = m (m + 1) / 2, row j of it N - 1 - j - k) mapped back to (i, j, k)
+// by walking slices and rows.
 __device__ __forceinline__ void vol_ijk(int N, int64_t l, int& i, int& j, int& k) {
   k = 1;
   for (;;) {
