@@ -1043,7 +1043,7 @@ int setup_device(hhg_mesh* m) {
   if (rc == HHG_OK) {
     HostProblem hg;
     try {
-      if (m->host.general) build_general_problem(m->host, hg);
+      if (m->host.general) build_general_problem(m->host, 0, std::vector<unsigned char>(m->host.n_macro, 0), hg);
       else build_problem(m->host, 0, std::vector<unsigned char>(m->host.n_macro, 0), hg);
     } catch (const std::exception& e) {
       rc = fail(HHG_ERR_ARG, std::string("problem: ") + e.what());

@@ -226,9 +226,12 @@ void set_coefficients(HostMesh& m, const double* coeff);
 // macros.
 void build_general_mesh(HostMesh& m, const double* verts, int nv, const int* tets, int nt, int R, int r0,
                         const double* coeff);
-// The global problem (kind 0) of a general mesh: free interface nodes by
-// class, frozen copies, variable-length restriction gathers, coarse CSR.
-void build_general_problem(const HostMesh& m, HostProblem& p);
+// A problem of a general mesh (kinds as for build_problem: 0 global, 1
+// faulty sub-domain, 2 healthy with the interface frozen, 3 healthy with the
+// interface free under A_I): free interface nodes by class, frozen copies,
+// variable-length restriction gathers, coarse CSR.
+void build_general_problem(const HostMesh& m, int kind, const std::vector<unsigned char>& faulty,
+                           HostProblem& p);
 // Global id of the volume node (i, j, k) (all positive, i + j + k < N) of a
 // macro of a general mesh at level L: n_if + macro * (N-1)(N-2)(N-3)/6 + its
 // index in the local (k, j, i) order.

@@ -814,11 +814,17 @@ void build_general_mesh(HostMesh& m, const double* verts, int nv, const int* tet
   }
 }
 
-void build_general_problem(const HostMesh& m, HostProblem& p) {
+void build_general_problem(const HostMesh& m, int kind, const std::vector<unsigned char>& faulty,
+                           HostProblem& p) {
   p = HostProblem();
-  p.kind = 0;
-  p.macro_active.assign(m.n_macro, 1);
-  for (int t = 0; t < m.n_macro; ++t) p.act.push_back(t);
+  p.kind = kind;
+  p.macro_active.assign(m.n_macro, 0);
+  for (int t = 0; t < m.n_macro; ++t) {
+    const bool f = macro_in_set(faulty, t);
+    const bool a = kind == 0 ? true : (kind == 1 ? f : !f);
+    p.macro_active[t] = a;
+    if (a) p.act.push_back(t);
+  }
   const int nl = (int)m.lv.size();
   p.lv.resize(nl);
   for (int l = 0; l < nl; ++l) {
@@ -826,12 +832,25 @@ void build_general_problem(const HostMesh& m, HostProblem& p) {
     HostProblemLevel& P = p.lv[l];
     std::vector<std::vector<int>> bycls(std::max(1, L.n_if_classes));
     for (int n = 0; n < L.n_if; ++n) {
-      if (!L.if_dirichlet[n]) {
+      // free as for the cube family: all copies faulty (kind 1), none (kind
+      // 2), not all (kind 3, the Neumann side with its interface free)
+      bool any_f = false, all_f = true;
+      for (int c = L.if_cptr[n]; c < L.if_cptr[n + 1]; ++c) {
+        const bool f = macro_in_set(faulty, L.if_copy[c].macro);
+        any_f = any_f || f;
+        all_f = all_f && f;
+      }
+      bool fr = !L.if_dirichlet[n];
+      if (kind == 1) fr = fr && all_f;
+      if (kind == 2) fr = fr && !any_f;
+      if (kind == 3) fr = fr && !all_f;
+      if (fr) {
         bycls[L.if_colour[n]].push_back(n);
       } else {
         for (int c = L.if_cptr[n]; c < L.if_cptr[n + 1]; ++c) {
           const Copy& cp = L.if_copy[c];
-          P.zero_off.push_back((int64_t)cp.macro * L.block + lidx(L.SL.data(), L.N, cp.i, cp.j, cp.k));
+          if (p.macro_active[cp.macro])
+            P.zero_off.push_back((int64_t)cp.macro * L.block + lidx(L.SL.data(), L.N, cp.i, cp.j, cp.k));
         }
       }
     }
@@ -841,9 +860,17 @@ void build_general_problem(const HostMesh& m, HostProblem& p) {
       P.class_off.push_back((int)P.free_if.size());
     }
     P.col_off[4] = (int)P.free_if.size();
+    if (kind == 3) {
+      P.cptr.assign(1, 0);
+      for (int n = 0; n < L.n_if; ++n) {
+        for (int c = L.if_cptr[n]; c < L.if_cptr[n + 1]; ++c)
+          if (p.macro_active[L.if_copy[c].macro]) P.copies.push_back(L.if_copy[c]);
+        P.cptr.push_back((int)P.copies.size());
+      }
+    }
   }
-  // restriction gathers: the distinct fine nodes 2 (i, j, k) + d over all
-  // copies of each free coarse interface node, the node itself first
+  // restriction gathers: the distinct fine nodes 2 (i, j, k) + d over the
+  // active copies of each free coarse interface node, the node itself first
   for (int l = 0; l + 1 < nl; ++l) {
     const HostLevel& F = m.lv[l + 1];
     const HostLevel& C = m.lv[l];
@@ -854,6 +881,7 @@ void build_general_problem(const HostMesh& m, HostProblem& p) {
       for (int pass = 0; pass < 2; ++pass)
         for (int c = C.if_cptr[n]; c < C.if_cptr[n + 1]; ++c) {
           const Copy& cp = C.if_copy[c];
+          if (!p.macro_active[cp.macro]) continue;
           for (int d = (pass == 0 ? 0 : 1); d < (pass == 0 ? 1 : NDIR); ++d) {
             int di, dj, dk;
             dir_ijk(d, di, dj, dk);

@@ -2,15 +2,18 @@
 // build_general_mesh / build_general_problem), driven by
 // tests/test_host_general.py.  Runs on the CPU; makes no CUDA call.
 //
-// usage: general_check nv nt R dir
+// usage: general_check nv nt R dir [n_faulty id...]
 // dir holds verts.bin (nv x 3 doubles) and tets.bin (nt x 4 int32), and
 // receives per level l: keys_<l>.bin (node keys, 5 int64 per node, in the
 // library's node order), g_<l>.bin and Ag_<l>.bin (a test vector and A g
 // applied through the macro blocks and copy lists as the kernels do),
-// cls_<l>.bin (interface class per interface node, -1 = Dirichlet); per level
-// l below the finest r_<l+1>.bin and rc_<l>.bin (a fine residual and its
-// restriction through the gathers, pairs node id / value); csr.bin (the
-// coarse CG matrix: n, then per row id, nnz, (column id, value)...).
+// cls_<l>.bin (interface class per interface node, -1 = Dirichlet); and per
+// problem kind (0 global; with faulty macros also 1 faulty, 2 healthy with
+// the interface frozen, 3 healthy under A_I) and level l below the finest
+// r_<kind>_<l+1>.bin and rc_<kind>_<l>.bin (a fine residual, zero off the
+// problem's free nodes, and its restriction through the gathers, pairs node
+// id / value), and csr_<kind>.bin (the coarse CG matrix: n, then per row id,
+// nnz, (column id, value)...).
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -105,10 +108,11 @@ int main(int argc, char** argv) {
   const std::vector<double> verts = readv<double>(dir + "/verts.bin", 3 * (size_t)nv);
   const std::vector<int> tets = readv<int>(dir + "/tets.bin", 4 * (size_t)nt);
   const std::vector<double> coeff = readv<double>(dir + "/coeff.bin", (size_t)nt);
+  std::vector<unsigned char> faulty(nt, 0);
+  const int nf = argc > 5 ? atoi(argv[5]) : 0;
+  for (int q = 0; q < nf; ++q) faulty[atoi(argv[6 + q])] = 1;
   HostMesh m;
   build_general_mesh(m, verts.data(), nv, tets.data(), nt, R, 2, coeff.data());
-  HostProblem p;
-  build_general_problem(m, p);
   std::vector<LevelIds> all;
   for (size_t l = 0; l < m.lv.size(); ++l) all.push_back(level_ids(m, m.lv[l]));
   for (size_t l = 0; l < m.lv.size(); ++l) {
@@ -171,31 +175,42 @@ int main(int argc, char** argv) {
     for (int n = 0; n < L.n_if; ++n) cls[L.if_gid[n]] = L.if_dirichlet[n] ? -1 : (int)L.if_colour[n];
     writev(dir + "/cls_" + std::to_string(l) + ".bin", cls);
   }
-  // restriction through the gathers
-  for (size_t l = 0; l + 1 < m.lv.size(); ++l) {
-    const HostLevel& C = m.lv[l];
-    const HostLevel& F = m.lv[l + 1];
-    const LevelIds& fids = all[l + 1];
-    std::vector<double> r(fids.n_nodes);
-    for (int64_t q = 0; q < fids.n_nodes; ++q) r[q] = testval(q, 101 + l);
-    for (int n = 0; n < F.n_if; ++n)
-      if (F.if_dirichlet[n]) r[F.if_gid[n]] = 0.0;
-    writev(dir + "/r_" + std::to_string(l + 1) + ".bin", r);
-    const std::vector<double> blk = to_blocks(m, F, fids, r);
-    const HostProblemLevel& P = p.lv[l];
-    std::vector<double> res;
-    for (size_t q = 0; q < P.free_if.size(); ++q) {
-      double b = 0.0;
-      for (int e = P.gptr[q] + 1; e < P.gptr[q + 1]; ++e) b += blk[P.goff[e]];
-      res.push_back((double)C.if_gid[P.free_if[q]]);
-      res.push_back(blk[P.goff[P.gptr[q]]] + 0.5 * b);
+  for (int kind = 0; kind < 4; ++kind) {
+    if (kind > 0 && nf == 0) break;
+    HostProblem p;
+    build_general_problem(m, kind, faulty, p);
+    const std::string ks = std::to_string(kind);
+    // restriction through the gathers
+    for (size_t l = 0; l + 1 < m.lv.size(); ++l) {
+      const HostLevel& C = m.lv[l];
+      const HostLevel& F = m.lv[l + 1];
+      const LevelIds& fids = all[l + 1];
+      std::vector<double> r(fids.n_nodes);
+      for (int64_t q = 0; q < fids.n_nodes; ++q) r[q] = testval(q, 101 + l + 7 * kind);
+      // zero off the free nodes: interface nodes not in the problem's lists,
+      // volume nodes of inactive macros
+      std::vector<unsigned char> fr(F.n_if, 0);
+      for (int n : p.lv[l + 1].free_if) fr[n] = 1;
+      for (int n = 0; n < F.n_if; ++n)
+        if (!fr[n]) r[F.if_gid[n]] = 0.0;
+      const int64_t nvol = (int64_t)(F.N - 1) * (F.N - 2) * (F.N - 3) / 6;
+      for (int t = 0; t < m.n_macro; ++t)
+        if (!p.macro_active[t])
+          for (int64_t q = 0; q < nvol; ++q) r[F.n_if + (int64_t)t * nvol + q] = 0.0;
+      writev(dir + "/r_" + ks + "_" + std::to_string(l + 1) + ".bin", r);
+      const std::vector<double> blk = to_blocks(m, F, fids, r);
+      const HostProblemLevel& P = p.lv[l];
+      std::vector<double> res;
+      for (size_t q = 0; q < P.free_if.size(); ++q) {
+        double b = 0.0;
+        for (int e = P.gptr[q] + 1; e < P.gptr[q + 1]; ++e) b += blk[P.goff[e]];
+        res.push_back((double)C.if_gid[P.free_if[q]]);
+        res.push_back(blk[P.goff[P.gptr[q]]] + 0.5 * b);
+      }
+      writev(dir + "/rc_" + ks + "_" + std::to_string(l) + ".bin", res);
     }
-    writev(dir + "/rc_" + std::to_string(l) + ".bin", res);
-  }
-  // coarse CG matrix with node ids
-  {
+    // coarse CG matrix with node ids
     const HostLevel& L0 = m.lv[0];
-    const LevelIds& ids = all[0];
     std::unordered_map<int64_t, int64_t> off_id;
     for (int t = 0; t < m.n_macro; ++t)
       for (int k = 1; k <= L0.N; ++k)
@@ -204,10 +219,9 @@ int main(int argc, char** argv) {
             off_id[(int64_t)t * L0.block + lidx(L0.SL.data(), L0.N, i, j, k)] = general_volume_id(L0, t, i, j, k);
     std::vector<int64_t> did(p.n_cg);
     for (int q = 0; q < p.n_cg; ++q) {
-      const int64_t s = p.fsrc[q];
-      did[q] = s < 0 ? L0.if_gid[-1 - s] : off_id.at(s);
+      const int64_t sidx = p.fsrc[q];
+      did[q] = sidx < 0 ? L0.if_gid[-1 - sidx] : off_id.at(sidx);
     }
-    (void)ids;
     std::vector<double> dump;
     dump.push_back(p.n_cg);
     for (int q = 0; q < p.n_cg; ++q) {
@@ -218,7 +232,7 @@ int main(int argc, char** argv) {
         dump.push_back(p.val[e]);
       }
     }
-    writev(dir + "/csr.bin", dump);
+    writev(dir + "/csr_" + ks + ".bin", dump);
   }
   return 0;
 }

@@ -3,8 +3,10 @@
 build_general_problem, compiled with the check program in tests/host/)
 against the general-mesh oracle (oracle/unstructured.py): node keys, the
 operator applied through macro blocks and copy lists, the interface smoother
-classes, the restriction gathers and the coarse CG matrix (§2.1, §3.1, §3.2
-Fig. 4), on meshes of another connectivity than the cube family."""
+classes, and for the global problem and the three recovery problem kinds
+(§4.2 Algorithm 1, §4.3 Algorithm 2) the restriction gathers and the coarse
+CG matrix (§2.1, §3.1, §3.2 Fig. 4), on meshes of another connectivity than
+the cube family."""
 
 import os
 import shutil
@@ -40,8 +42,9 @@ def _perm(path, lv):
     return np.array([okeys[tuple(k)] for k in keys.tolist()])
 
 
-@pytest.mark.parametrize("mesh,R", [("five", 4), ("five-moved", 4), ("kuhn", 3)])
-def test_general_builder_matches_oracle(check_prog, tmp_path, mesh, R):
+@pytest.mark.parametrize("mesh,R,faulty", [("five", 4, [0, 1, 2, 3, 4]), ("five-moved", 4, [7, 12]),
+                                           ("kuhn", 3, [3, 4, 5])])
+def test_general_builder_matches_oracle(check_prog, tmp_path, mesh, R, faulty):
     if mesh == "kuhn":
         v, t = I.kuhn_macro_mesh((2, 1, 2))
     else:
@@ -50,7 +53,8 @@ def test_general_builder_matches_oracle(check_prog, tmp_path, mesh, R):
     np.ascontiguousarray(v, dtype=np.float64).tofile(tmp_path / "verts.bin")
     np.ascontiguousarray(t, dtype=np.int32).tofile(tmp_path / "tets.bin")
     coeff.tofile(tmp_path / "coeff.bin")
-    subprocess.check_call([check_prog, str(len(v)), str(len(t)), str(R), str(tmp_path)])
+    subprocess.check_call([check_prog, str(len(v)), str(len(t)), str(R), str(tmp_path), str(len(faulty)),
+                           *map(str, faulty)])
     om = U.UMesh(v, t, R, coeff=coeff)
     perms = []
     for l, lv in enumerate(om.levels):
@@ -72,33 +76,40 @@ def test_general_builder_matches_oracle(check_prog, tmp_path, mesh, R):
             ocls[members] = c
         assert np.array_equal(cls, ocls[perm[:n_if]])
         assert np.all(lv.dim[perm[:n_if]] < 4) and np.all(lv.dim[perm[n_if:]] == 4)
-    # restriction gathers = P^T on the free coarse interface nodes
-    for l in range(len(om.levels) - 1):
-        r = np.fromfile(tmp_path / f"r_{l + 1}.bin")
-        ro = np.zeros(om.levels[l + 1].n)
-        ro[perms[l + 1]] = r
-        rc = om.P[l].T @ ro
-        d = np.fromfile(tmp_path / f"rc_{l}.bin").reshape(-1, 2)
-        ids = perms[l][d[:, 0].astype(np.int64)]
-        assert len(ids) == (~om.levels[l].boundary & (om.levels[l].dim < 4)).sum()
-        assert np.abs(rc[ids] - d[:, 1]).max() <= 1e-13 * max(1.0, np.abs(rc).max())
-    # coarse CG matrix = level-0 operator on the free nodes
-    lv0 = om.levels[0]
-    dump = np.fromfile(tmp_path / "csr.bin")
-    n, pos = int(dump[0]), 1
-    A = lv0.A.tocsr()
-    free = ~lv0.boundary
-    rows = []
-    for _ in range(n):
-        gid, nnz = int(dump[pos]), int(dump[pos + 1])
-        pos += 2
-        o = perms[0][gid]
-        rows.append(o)
-        refr = A.getrow(o).toarray().ravel()
-        refr[~free] = 0.0
-        mine = np.zeros_like(refr)
-        for _ in range(nnz):
-            mine[perms[0][int(dump[pos])]] += dump[pos + 1]
+    # per problem kind: restriction gathers = P^T on the free coarse interface
+    # nodes, coarse CG matrix = the level-0 operator (A_I for kind 3) on the
+    # free nodes
+    hm = om.healthy(faulty)
+    fmasks = om.fault_masks(faulty)
+    kinds = [om.global_masks(), om.local_masks(faulty), om.healthy_masks(faulty),
+             [~lv.boundary & ~o for lv, (o, _) in zip(om.levels, fmasks)]]
+    for kind, free in enumerate(kinds):
+        for l in range(len(om.levels) - 1):
+            r = np.fromfile(tmp_path / f"r_{kind}_{l + 1}.bin")
+            ro = np.zeros(om.levels[l + 1].n)
+            ro[perms[l + 1]] = r
+            ro[~free[l + 1]] = 0.0
+            rc = om.P[l].T @ ro
+            d = np.fromfile(tmp_path / f"rc_{kind}_{l}.bin").reshape(-1, 2)
+            ids = perms[l][d[:, 0].astype(np.int64)]
+            want = np.nonzero(free[l] & (om.levels[l].dim < 4))[0]
+            assert sorted(ids.tolist()) == want.tolist()
+            assert np.abs(rc[ids] - d[:, 1]).max(initial=0.0) <= 1e-13 * max(1.0, np.abs(rc).max())
+        lv0 = (hm if kind == 3 else om).levels[0]
+        dump = np.fromfile(tmp_path / f"csr_{kind}.bin")
+        n, pos = int(dump[0]), 1
+        A = lv0.A.tocsr()
+        rows = []
+        for _ in range(n):
+            gid, nnz = int(dump[pos]), int(dump[pos + 1])
             pos += 2
-        assert np.abs(mine - refr).max() <= 1e-13 * np.abs(refr).max()
-    assert sorted(rows) == sorted(np.nonzero(free)[0].tolist())
+            o = perms[0][gid]
+            rows.append(o)
+            refr = A.getrow(o).toarray().ravel()
+            refr[~free[0]] = 0.0
+            mine = np.zeros_like(refr)
+            for _ in range(nnz):
+                mine[perms[0][int(dump[pos])]] += dump[pos + 1]
+                pos += 2
+            assert np.abs(mine - refr).max() <= 1e-13 * max(np.abs(refr).max(), 1e-300)
+        assert sorted(rows) == np.nonzero(free[0])[0].tolist()
