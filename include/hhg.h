@@ -116,8 +116,8 @@ int hhg_mesh_destroy(hhg_mesh* mesh);
  * gives their count.  One Gauss-Seidel step visits the volume nodes by their
  * macro's colour (i + 2j + 3k) mod 4 and then the interface nodes in the
  * classes of a greedy colouring of their couplings in key order.
- * V-cycles and fault-free solves (FP64) are available; fault injection,
- * recovery, mixed precision, coefficient changes and gradients, batching,
+ * V-cycles, solves, fault injection and LR / DD / DN recovery (FP64) are
+ * available; mixed precision, coefficient changes and gradients, batching,
  * autotuning and the allocation-free cycle return HHG_ERR_STATE for these
  * meshes.  Errors: HHG_ERR_ARG for invalid sizes, ids, degenerate macros or
  * a non-conforming mesh (found before any device use). */

@@ -638,12 +638,18 @@ int check_ids(const hhg_mesh* m, const int* ids, int n, std::vector<unsigned cha
   return HHG_OK;
 }
 
+// A problem of either mesh family (kinds as for build_problem).
+void build_any_problem(const HostMesh& h, int kind, const std::vector<unsigned char>& set, HostProblem& p) {
+  if (h.general) build_general_problem(h, kind, set, p);
+  else build_problem(h, kind, set, p);
+}
+
 int setup_fault(hhg_mesh* m, const std::vector<unsigned char>& set) {
   if (m->has_fault && set == m->fault_set) return HHG_OK;
   HostProblem hf, hh;
   try {
-    build_problem(m->host, 1, set, hf);
-    build_problem(m->host, 2, set, hh);
+    build_any_problem(m->host, 1, set, hf);
+    build_any_problem(m->host, 2, set, hh);
   } catch (const std::exception& e) {
     return fail(HHG_ERR_ARG, std::string("fault set: ") + e.what());
   }
@@ -735,7 +741,7 @@ int setup_dn(hhg_mesh* m, const std::vector<unsigned char>& set) {
   if (m->has_dn && set == m->dn_set) return HHG_OK;
   HostProblem hd;
   try {
-    build_problem(m->host, 3, set, hd);
+    build_any_problem(m->host, 3, set, hd);
   } catch (const std::exception& e) {
     return fail(HHG_ERR_ARG, std::string("fault set: ") + e.what());
   }
@@ -1241,7 +1247,6 @@ int hhg_residual_norm(hhg_mesh* m, double* out, void* stream) {
 
 int hhg_inject_fault(hhg_mesh* m, const int* ids, int n, void* stream) {
   if (!m) return fail(HHG_ERR_ARG, "null mesh");
-  HHG_TRY(refuse_general(m, "fault injection"));
   std::vector<unsigned char> set;
   HHG_TRY(check_ids(m, ids, n, set));
   HHG_TRY(setup_fault(m, set));
@@ -1251,7 +1256,6 @@ int hhg_inject_fault(hhg_mesh* m, const int* ids, int n, void* stream) {
 int hhg_recover_local(hhg_mesh* m, const int* ids, int n, int n_local, int n_global, double* seconds_local,
                       double* seconds_global, void* stream) {
   if (!m || n_local < 0 || n_global < 0) return fail(HHG_ERR_ARG, "invalid argument");
-  HHG_TRY(refuse_general(m, "recovery"));
   std::vector<unsigned char> set;
   HHG_TRY(check_ids(m, ids, n, set));
   HHG_TRY(setup_fault(m, set));
@@ -1262,7 +1266,6 @@ int hhg_recover_local(hhg_mesh* m, const int* ids, int n, int n_local, int n_glo
 int hhg_recover_dn(hhg_mesh* m, const int* ids, int n, int n_global, double eta, int* n_local_run,
                    double* seconds_local, double* seconds_global, void* stream) {
   if (!m || n_global < 0 || !(eta >= 0.0)) return fail(HHG_ERR_ARG, "invalid argument");
-  HHG_TRY(refuse_general(m, "recovery"));
   std::vector<unsigned char> set;
   HHG_TRY(check_ids(m, ids, n, set));
   HHG_TRY(setup_dn(m, set));
@@ -1494,7 +1497,6 @@ int hhg_launch_count(int64_t* count) {
 int hhg_solve(hhg_mesh* m, const hhg_solve_opts* o, double* hist, int* n_hist, int* cycles, void* stream) {
   if (!m || !o) return fail(HHG_ERR_ARG, "null argument");
   if (o->max_cycles < 0 || !(o->rtol >= 0.0)) return fail(HHG_ERR_ARG, "invalid rtol / max_cycles");
-  if (o->fault_cycle > 0 || o->n_faults > 0) HHG_TRY(refuse_general(m, "fault injection"));
   if (o->mixed_precision) HHG_TRY(refuse_general(m, "mixed precision"));
   const bool mixed = o->mixed_precision != 0;
   if (mixed && m->precision != 32) return fail(HHG_ERR_STATE, "mixed precision needs a precision-32 mesh");
