@@ -6,7 +6,9 @@ operator applied through macro blocks and copy lists, the interface smoother
 classes, and for the global problem and the three recovery problem kinds
 (§4.2 Algorithm 1, §4.3 Algorithm 2) the restriction gathers and the coarse
 CG matrix (§2.1, §3.1, §3.2 Fig. 4), on meshes of another connectivity than
-the cube family."""
+the cube family; and a host model of the device V-cycle (those tables driven
+with the kernels' per-node arithmetic and order, tests/host/general_vcycle.cpp)
+against the oracle's V-cycle iterates."""
 
 import os
 import shutil
@@ -113,3 +115,61 @@ def test_general_builder_matches_oracle(check_prog, tmp_path, mesh, R, faulty):
                 pos += 2
             assert np.abs(mine - refr).max() <= 1e-13 * max(np.abs(refr).max(), 1e-300)
         assert sorted(rows) == np.nonzero(free[0])[0].tolist()
+
+
+def _lib_to_oracle(om, tets):
+    """Library node order -> oracle node id: the interface nodes in the same
+    key order, then the volume nodes macro by macro, local order k, j, i."""
+    lv = om.levels[-1]
+    N = lv.N
+    n_if = int((lv.dim < 4).sum())
+    okeys = {tuple(k): q for q, k in enumerate(lv.keys.tolist())}
+    perm = list(range(n_if))
+    for t in tets:
+        for k in range(1, N):
+            for j in range(1, N - k):
+                for i in range(1, N - j - k):
+                    w = [N - i - j - k, i, j, k]
+                    perm.append(okeys[(4, *sorted(int(g) * (N + 1) + ww for g, ww in zip(t, w)))])
+    return np.array(perm)
+
+
+@pytest.fixture(scope="module")
+def vcycle_prog(tmp_path_factory):
+    cxx = shutil.which("g++") or shutil.which("c++")
+    cuda_inc = "/usr/local/cuda/include"
+    if not cxx or not os.path.isdir(cuda_inc):
+        pytest.skip("needs a C++ compiler and the CUDA headers")
+    out = tmp_path_factory.mktemp("generalvcycle") / "general_vcycle"
+    subprocess.check_call([cxx, "-O2", "-std=c++17", "-I" + cuda_inc, "-o", str(out),
+                           os.path.join(ROOT, "tests", "host", "general_vcycle.cpp"),
+                           os.path.join(ROOT, "paper_1506_06185_gb300", "csrc", "mesh.cpp")])
+    return str(out)
+
+
+@pytest.mark.parametrize("moved", [False, True])
+def test_host_model_of_the_device_vcycle_matches_oracle(vcycle_prog, tmp_path, moved):
+    """The library's tables driven with its kernels' per-node arithmetic and
+    order (a host model of the device V-cycle) give the oracle's iterates."""
+    v, t = I.five_tet_macro_mesh((2, 2, 1), seed=3 if moved else None, amp=0.12)
+    R = 4
+    coeff = np.exp(np.random.default_rng(9).standard_normal(len(t)))
+    om = U.UMesh(v, t, R, coeff=coeff)
+    lv = om.levels[-1]
+    perm = _lib_to_oracle(om, t)
+    assert np.array_equal(np.sort(perm), np.arange(lv.n))
+    rng = np.random.default_rng(4)
+    fo = np.where(lv.boundary, 0.0, rng.uniform(-1, 1, lv.n))
+    uo = np.where(lv.boundary, np.exp(np.pi * lv.X[:, 0]) * np.sin(np.pi * lv.X[:, 1]), 0.0)
+    np.ascontiguousarray(v, dtype=np.float64).tofile(tmp_path / "verts.bin")
+    np.ascontiguousarray(t, dtype=np.int32).tofile(tmp_path / "tets.bin")
+    coeff.tofile(tmp_path / "coeff.bin")
+    fo[perm].tofile(tmp_path / "f.bin")
+    uo[perm].tofile(tmp_path / "u0.bin")
+    cycles = 4
+    subprocess.check_call([vcycle_prog, str(len(v)), str(len(t)), str(R), str(cycles), str(tmp_path)])
+    masks = om.global_masks()
+    for c in range(cycles):
+        U.vcycle(om, len(om.levels) - 1, uo, fo, masks)
+        ul = np.fromfile(tmp_path / f"u_{c}.bin")
+        assert np.linalg.norm(ul - uo[perm]) <= 1e-11 * np.linalg.norm(uo), c
