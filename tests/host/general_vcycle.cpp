@@ -7,9 +7,13 @@
 // coarse CG; interpolation along the coarse edge through each fine node),
 // executed one node at a time.  Runs on the CPU; makes no CUDA call.
 //
-// usage: general_vcycle nv nt R cycles dir
+// usage: general_vcycle nv nt R cycles dir [fault_cycle recovery n_local n_global n_faulty id...]
 // dir holds verts.bin, tets.bin (int32), coeff.bin, f.bin and u0.bin (global
-// vectors in the library's node order); writes u_<c>.bin after every cycle.
+// vectors in the library's node order); writes u_<c>.bin after every global
+// cycle and hist.bin (relative residual after every global cycle and, with a
+// fault, one entry right after the fault and its recovery: recovery 1 = LR,
+// n_local cycles on the faulty sub-domain; 2 = DD, also n_global cycles on
+// the healthy one with the interface frozen).
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -40,7 +44,7 @@ struct Lev {
 
 struct Model {
   HostMesh m;
-  HostProblem p;
+  HostProblem glob, loc, heal;                // global, faulty sub-domain, healthy (interface frozen)
   std::vector<Lev> lv;
 
   size_t at(const HostLevel& L, int t, int i, int j, int k) const {
@@ -69,14 +73,14 @@ struct Model {
     }
   }
 
-  void smooth(int l, int steps) {
+  void smooth(const HostProblem& p, int l, int steps) {
     const HostLevel& L = m.lv[l];
     Lev& D = lv[l];
     const HostProblemLevel& P = p.lv[l];
     const int N = L.N;
     for (int it = 0; it < steps; ++it) {
       for (int c = 0; c < 4; ++c)
-        for (int t = 0; t < m.n_macro; ++t) {
+        for (int t : p.act) {
           const double* w = &L.W[(size_t)t * 16 * NDIR];
           for (int k = 1; k <= N; ++k)
             for (int j = 1; j + k <= N - 1; ++j)
@@ -103,12 +107,12 @@ struct Model {
     }
   }
 
-  void residual(int l) {
+  void residual(const HostProblem& p, int l) {
     const HostLevel& L = m.lv[l];
     Lev& D = lv[l];
     const HostProblemLevel& P = p.lv[l];
     const int N = L.N;
-    for (int t = 0; t < m.n_macro; ++t) {
+    for (int t : p.act) {
       const double* w = &L.W[(size_t)t * 16 * NDIR];
       for (int k = 1; k <= N; ++k)
         for (int j = 1; j + k <= N - 1; ++j)
@@ -130,14 +134,14 @@ struct Model {
     for (int64_t o : P.zero_off) D.r[o] = 0.0;
   }
 
-  void restrict_to(int l) {   // level l -> l - 1
+  void restrict_to(const HostProblem& p, int l) {   // level l -> l - 1
     const HostLevel& F = m.lv[l];
     const HostLevel& C = m.lv[l - 1];
     Lev& Df = lv[l];
     Lev& Dc = lv[l - 1];
     const HostProblemLevel& P = p.lv[l - 1];
     const int Nc = C.N;
-    for (int t = 0; t < m.n_macro; ++t)
+    for (int t : p.act)
       for (int k = 1; k <= Nc; ++k)
         for (int j = 1; j + k <= Nc - 1; ++j)
           for (int i = 1; i + j + k <= Nc - 1; ++i) {
@@ -171,13 +175,13 @@ struct Model {
     return 0.5 * (uc[at(C, t, la - lb, lb - lc, lc)] + uc[at(C, t, ha - hb, hb - hc, hc)]);
   }
 
-  void prolong(int l) {   // level l - 1 -> l
+  void prolong(const HostProblem& p, int l) {   // level l - 1 -> l
     const HostLevel& F = m.lv[l];
     const HostLevel& C = m.lv[l - 1];
     Lev& Df = lv[l];
     const Lev& Dc = lv[l - 1];
     const int N = F.N;
-    for (int t = 0; t < m.n_macro; ++t)
+    for (int t : p.act)
       for (int k = 1; k <= N; ++k)
         for (int j = 1; j + k <= N - 1; ++j)
           for (int i = 1; i + j + k <= N - 1; ++i) Df.u[at(F, t, i, j, k)] += interp(C, Dc.u, t, i, j, k);
@@ -189,7 +193,7 @@ struct Model {
     }
   }
 
-  void coarse_solve() {
+  void coarse_solve(const HostProblem& p) {
     // CG on the compact free nodes of level 0, from zero, to 1e-12 relative
     Lev& D = lv[0];
     const int n = p.n_cg;
@@ -230,18 +234,54 @@ struct Model {
     }
   }
 
-  void vcycle() {
+  void vcycle(const HostProblem& p) {
     const int top = (int)m.lv.size() - 1;
     for (int l = top; l >= 1; --l) {
-      smooth(l, 3);
-      residual(l);
-      restrict_to(l);
+      smooth(p, l, 3);
+      residual(p, l);
+      restrict_to(p, l);
     }
-    coarse_solve();
+    coarse_solve(p);
     for (int l = 1; l <= top; ++l) {
-      prolong(l);
-      smooth(l, 3);
+      prolong(p, l);
+      smooth(p, l, 3);
     }
+  }
+
+  // ||f - A u|| over the free nodes of the global problem (finest level)
+  double resnorm() {
+    const int top = (int)m.lv.size() - 1;
+    residual(glob, top);
+    const HostLevel& L = m.lv[top];
+    const Lev& D = lv[top];
+    double ss = 0.0;
+    for (int t = 0; t < m.n_macro; ++t)
+      for (int k = 1; k <= L.N; ++k)
+        for (int j = 1; j + k <= L.N - 1; ++j)
+          for (int i = 1; i + j + k <= L.N - 1; ++i) ss += D.r[at(L, t, i, j, k)] * D.r[at(L, t, i, j, k)];
+    for (int n : glob.lv[top].free_if) {
+      const Copy& cp = L.if_copy[L.if_cptr[n]];
+      const double v = D.r[at(L, cp.macro, cp.i, cp.j, cp.k)];
+      ss += v * v;
+    }
+    return std::sqrt(ss);
+  }
+
+  // fault (§2.2): the faulty blocks lose everything, the masters inside
+  // Omega_F are erased, the copies in the lost blocks come back from masters
+  void inject(const std::vector<unsigned char>& faulty) {
+    const int top = (int)m.lv.size() - 1;
+    const HostLevel& L = m.lv[top];
+    Lev& D = lv[top];
+    for (int t = 0; t < m.n_macro; ++t)
+      if (faulty[t]) std::fill(D.u.begin() + (size_t)t * L.block, D.u.begin() + (size_t)(t + 1) * L.block, 0.0);
+    for (int n : loc.lv[top].free_if) D.uI[n] = 0.0;
+    for (int n = 0; n < L.n_if; ++n)
+      for (int c = L.if_cptr[n]; c < L.if_cptr[n + 1]; ++c)
+        if (faulty[L.if_copy[c].macro]) {
+          const Copy& cp = L.if_copy[c];
+          D.u[at(L, cp.macro, cp.i, cp.j, cp.k)] = D.uI[n];
+        }
   }
 };
 
@@ -254,7 +294,18 @@ int main(int argc, char** argv) {
   const auto coeff = readv<double>(dir + "/coeff.bin", (size_t)nt);
   Model M;
   build_general_mesh(M.m, verts.data(), nv, tets.data(), nt, R, 2, coeff.data());
-  build_general_problem(M.m, 0, std::vector<unsigned char>(nt, 0), M.p);
+  std::vector<unsigned char> faulty(nt, 0);
+  const int fault_cycle = argc > 6 ? atoi(argv[6]) : -1;
+  const int recovery = argc > 7 ? atoi(argv[7]) : 0;
+  const int n_local = argc > 8 ? atoi(argv[8]) : 0;
+  const int n_global = argc > 9 ? atoi(argv[9]) : 0;
+  const int nf = argc > 10 ? atoi(argv[10]) : 0;
+  for (int q = 0; q < nf; ++q) faulty[atoi(argv[11 + q])] = 1;
+  build_general_problem(M.m, 0, std::vector<unsigned char>(nt, 0), M.glob);
+  if (nf > 0) {
+    build_general_problem(M.m, 1, faulty, M.loc);
+    build_general_problem(M.m, 2, faulty, M.heal);
+  }
   M.lv.resize(M.m.lv.size());
   for (size_t l = 0; l < M.m.lv.size(); ++l) {
     const HostLevel& L = M.m.lv[l];
@@ -286,8 +337,19 @@ int main(int argc, char** argv) {
     D.uI[n] = u0[T.if_gid[n]];
     M.write_copies(T, D.u, n, D.uI[n]);
   }
+  std::vector<double> hist = {1.0};
+  const double r0 = M.resnorm();
   for (int c = 0; c < cycles; ++c) {
-    M.vcycle();
+    M.vcycle(M.glob);
+    hist.push_back(M.resnorm() / r0);
+    if (c + 1 == fault_cycle) {
+      M.inject(faulty);
+      if (recovery == 1 || recovery == 2)
+        for (int q = 0; q < n_local; ++q) M.vcycle(M.loc);
+      if (recovery == 2)
+        for (int q = 0; q < n_global; ++q) M.vcycle(M.heal);
+      hist.push_back(M.resnorm() / r0);
+    }
     std::vector<double> out(nn);
     for (int t = 0; t < nt; ++t)
       for (int k = 1; k <= N; ++k)
@@ -298,5 +360,8 @@ int main(int argc, char** argv) {
     fwrite(out.data(), 8, out.size(), fo);
     fclose(fo);
   }
+  FILE* fh = fopen((dir + "/hist.bin").c_str(), "wb");
+  fwrite(hist.data(), 8, hist.size(), fh);
+  fclose(fh);
   return 0;
 }

@@ -8,7 +8,8 @@ classes, and for the global problem and the three recovery problem kinds
 CG matrix (§2.1, §3.1, §3.2 Fig. 4), on meshes of another connectivity than
 the cube family; and a host model of the device V-cycle (those tables driven
 with the kernels' per-node arithmetic and order, tests/host/general_vcycle.cpp)
-against the oracle's V-cycle iterates."""
+against the oracle's V-cycle iterates and, with a fault, its LR / DD recovery
+(§2.2, §4.2 Algorithm 1)."""
 
 import os
 import shutil
@@ -173,3 +174,35 @@ def test_host_model_of_the_device_vcycle_matches_oracle(vcycle_prog, tmp_path, m
         U.vcycle(om, len(om.levels) - 1, uo, fo, masks)
         ul = np.fromfile(tmp_path / f"u_{c}.bin")
         assert np.linalg.norm(ul - uo[perm]) <= 1e-11 * np.linalg.norm(uo), c
+
+
+@pytest.mark.parametrize("recovery", ["LR", "DD"])
+def test_host_model_of_the_device_fault_recovery_matches_oracle(vcycle_prog, tmp_path, recovery):
+    """Fault after cycle 2 on one sub-cube's five macros and its LR / DD
+    recovery through the library's tables and the kernels' arithmetic: the
+    residual history and the iterates equal the oracle's."""
+    v, t = I.five_tet_macro_mesh((2, 2, 1), seed=3, amp=0.12)
+    R = 4
+    om = U.UMesh(v, t, R)
+    lv = om.levels[-1]
+    perm = _lib_to_oracle(om, t)
+    fo = np.where(lv.boundary, 0.0, np.random.default_rng(8).uniform(-1, 1, lv.n))
+    uo = np.zeros(lv.n)
+    np.ascontiguousarray(v, dtype=np.float64).tofile(tmp_path / "verts.bin")
+    np.ascontiguousarray(t, dtype=np.int32).tofile(tmp_path / "tets.bin")
+    np.ones(len(t)).tofile(tmp_path / "coeff.bin")
+    fo[perm].tofile(tmp_path / "f.bin")
+    uo[perm].tofile(tmp_path / "u0.bin")
+    ids = [5, 6, 7, 8, 9]
+    cycles, n_local, n_global = 5, 3, 2
+    rec = {"LR": 1, "DD": 2}[recovery]
+    subprocess.check_call([vcycle_prog, str(len(v)), str(len(t)), str(R), str(cycles), str(tmp_path), "2", str(rec),
+                           str(n_local), str(n_global), str(len(ids)), *map(str, ids)])
+    kw = dict(recovery=U.LR, n_local=n_local) if recovery == "LR" else \
+        dict(recovery=U.DD, n_local=n_local, n_global=n_global)
+    hist_o = U.solve(om, uo, fo, rtol=0.0, max_cycles=cycles, fault_cycle=2, fault_ids=ids, **kw)
+    hist = np.fromfile(tmp_path / "hist.bin")
+    assert len(hist) == len(hist_o) == cycles + 2
+    assert np.abs(hist - hist_o).max() <= 1e-11
+    ul = np.fromfile(tmp_path / f"u_{cycles - 1}.bin")
+    assert np.linalg.norm(ul - uo[perm]) <= 1e-11 * np.linalg.norm(uo)
