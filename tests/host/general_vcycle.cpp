@@ -7,13 +7,14 @@
 // coarse CG; interpolation along the coarse edge through each fine node),
 // executed one node at a time.  Runs on the CPU; makes no CUDA call.
 //
-// usage: general_vcycle nv nt R cycles dir [fault_cycle recovery n_local n_global n_faulty id...]
+// usage: general_vcycle nv nt R cycles dir [fault_cycle recovery n_local n_global n_faulty id... [eta]]
 // dir holds verts.bin, tets.bin (int32), coeff.bin, f.bin and u0.bin (global
 // vectors in the library's node order); writes u_<c>.bin after every global
 // cycle and hist.bin (relative residual after every global cycle and, with a
 // fault, one entry right after the fault and its recovery: recovery 1 = LR,
 // n_local cycles on the faulty sub-domain; 2 = DD, also n_global cycles on
-// the healthy one with the interface frozen).
+// the healthy one with the interface frozen; 3 = DN, n_global Neumann-side
+// cycles with Omega_F blocks of ceil(j eta) - ceil((j - 1) eta) cycles).
 #include <algorithm>
 #include <array>
 #include <cmath>
@@ -44,24 +45,38 @@ struct Lev {
 
 struct Model {
   HostMesh m;
-  HostProblem glob, loc, heal;                // global, faulty sub-domain, healthy (interface frozen)
+  HostProblem glob, loc, heal, neum;          // global, faulty sub-domain, healthy (interface
+                                              // frozen), healthy under A_I (interface free)
   std::vector<Lev> lv;
 
   size_t at(const HostLevel& L, int t, int i, int j, int k) const {
     return (size_t)t * L.block + lidx(L.SL.data(), L.N, i, j, k);
   }
 
-  void write_copies(const HostLevel& L, std::vector<double>& b, int n, double v) const {
-    for (int c = L.if_cptr[n]; c < L.if_cptr[n + 1]; ++c) {
-      const Copy& cp = L.if_copy[c];
+  // the copy lists a problem works with: its own (the Neumann side keeps
+  // only the healthy copies) or the level's
+  struct Cps {
+    const int* ptr;
+    const Copy* cps;
+  };
+  Cps copies(const HostProblem& p, int l) const {
+    const HostProblemLevel& P = p.lv[l];
+    if (!P.cptr.empty()) return {P.cptr.data(), P.copies.data()};
+    return {m.lv[l].if_cptr.data(), m.lv[l].if_copy.data()};
+  }
+  Cps all_copies(int l) const { return {m.lv[l].if_cptr.data(), m.lv[l].if_copy.data()}; }
+
+  void write_copies(const HostLevel& L, Cps cl, std::vector<double>& b, int n, double v) const {
+    for (int c = cl.ptr[n]; c < cl.ptr[n + 1]; ++c) {
+      const Copy& cp = cl.cps[c];
       b[at(L, cp.macro, cp.i, cp.j, cp.k)] = v;
     }
   }
   // sum over the copies of the sub-stencils: off-diagonal part and diagonal
-  void if_stencil(const HostLevel& L, const std::vector<double>& u, int n, double& off, double& diag) const {
+  void if_stencil(const HostLevel& L, Cps cl, const std::vector<double>& u, int n, double& off, double& diag) const {
     off = diag = 0.0;
-    for (int c = L.if_cptr[n]; c < L.if_cptr[n + 1]; ++c) {
-      const Copy& cp = L.if_copy[c];
+    for (int c = cl.ptr[n]; c < cl.ptr[n + 1]; ++c) {
+      const Copy& cp = cl.cps[c];
       const double* w = &L.W[((size_t)cp.macro * 16 + node_class(cp.i, cp.j, cp.k, L.N)) * NDIR];
       diag += w[0];
       for (int d = 1; d < NDIR; ++d) {
@@ -73,10 +88,11 @@ struct Model {
     }
   }
 
-  void smooth(const HostProblem& p, int l, int steps) {
+  void smooth(const HostProblem& p, int l, int steps, const std::vector<double>& fI) {
     const HostLevel& L = m.lv[l];
     Lev& D = lv[l];
     const HostProblemLevel& P = p.lv[l];
+    const Cps cl = copies(p, l);
     const int N = L.N;
     for (int it = 0; it < steps; ++it) {
       for (int c = 0; c < 4; ++c)
@@ -99,18 +115,19 @@ struct Model {
         for (int q = P.class_off[c]; q < P.class_off[c + 1]; ++q) {
           const int n = P.free_if[q];
           double off, diag;
-          if_stencil(L, D.u, n, off, diag);
-          const double v = (D.fI[n] - off) / diag;
+          if_stencil(L, cl, D.u, n, off, diag);
+          const double v = (fI[n] - off) / diag;
           D.uI[n] = v;
-          write_copies(L, D.u, n, v);
+          write_copies(L, cl, D.u, n, v);
         }
     }
   }
 
-  void residual(const HostProblem& p, int l) {
+  void residual(const HostProblem& p, int l, const std::vector<double>& fI) {
     const HostLevel& L = m.lv[l];
     Lev& D = lv[l];
     const HostProblemLevel& P = p.lv[l];
+    const Cps cl = copies(p, l);
     const int N = L.N;
     for (int t : p.act) {
       const double* w = &L.W[(size_t)t * 16 * NDIR];
@@ -128,8 +145,8 @@ struct Model {
     }
     for (int n : P.free_if) {
       double off, diag;
-      if_stencil(L, D.u, n, off, diag);
-      write_copies(L, D.r, n, D.fI[n] - diag * D.uI[n] - off);
+      if_stencil(L, cl, D.u, n, off, diag);
+      write_copies(L, cl, D.r, n, fI[n] - diag * D.uI[n] - off);
     }
     for (int64_t o : P.zero_off) D.r[o] = 0.0;
   }
@@ -160,7 +177,7 @@ struct Model {
       for (int e = P.gptr[q] + 1; e < P.gptr[q + 1]; ++e) acc += Df.r[P.goff[e]];
       Dc.fI[n] = Df.r[P.goff[P.gptr[q]]] + 0.5 * acc;
       Dc.uI[n] = 0.0;
-      write_copies(C, Dc.u, n, 0.0);
+      write_copies(C, copies(p, l - 1), Dc.u, n, 0.0);
     }
     for (int64_t o : P.zero_off) Dc.u[o] = 0.0;
   }
@@ -185,11 +202,12 @@ struct Model {
       for (int k = 1; k <= N; ++k)
         for (int j = 1; j + k <= N - 1; ++j)
           for (int i = 1; i + j + k <= N - 1; ++i) Df.u[at(F, t, i, j, k)] += interp(C, Dc.u, t, i, j, k);
+    const Cps cl = copies(p, l);
     for (int n : p.lv[l].free_if) {
-      const Copy& cp = F.if_copy[F.if_cptr[n]];
+      const Copy& cp = cl.cps[cl.ptr[n]];
       const double v = Df.uI[n] + interp(C, Dc.u, cp.macro, cp.i, cp.j, cp.k);
       Df.uI[n] = v;
-      write_copies(F, Df.u, n, v);
+      write_copies(F, cl, Df.u, n, v);
     }
   }
 
@@ -234,24 +252,27 @@ struct Model {
     }
   }
 
-  void vcycle(const HostProblem& p) {
+  // fI_top: the interface right-hand side of the finest level (the Neumann
+  // side's, with the flux on Gamma), else the level's own
+  void vcycle(const HostProblem& p, const std::vector<double>* fI_top = nullptr) {
     const int top = (int)m.lv.size() - 1;
+    auto fI = [&](int l) -> const std::vector<double>& { return l == top && fI_top ? *fI_top : lv[l].fI; };
     for (int l = top; l >= 1; --l) {
-      smooth(p, l, 3);
-      residual(p, l);
+      smooth(p, l, 3, fI(l));
+      residual(p, l, fI(l));
       restrict_to(p, l);
     }
     coarse_solve(p);
     for (int l = 1; l <= top; ++l) {
       prolong(p, l);
-      smooth(p, l, 3);
+      smooth(p, l, 3, fI(l));
     }
   }
 
   // ||f - A u|| over the free nodes of the global problem (finest level)
   double resnorm() {
     const int top = (int)m.lv.size() - 1;
-    residual(glob, top);
+    residual(glob, top, lv[top].fI);
     const HostLevel& L = m.lv[top];
     const Lev& D = lv[top];
     double ss = 0.0;
@@ -265,6 +286,49 @@ struct Model {
       ss += v * v;
     }
     return std::sqrt(ss);
+  }
+
+  // Dirichlet-Neumann recovery as the device schedules it (Algorithm 2): the
+  // Neumann side's interface right-hand side takes the flux (A_I u) on Gamma
+  // (the interface nodes free on the Neumann side with a faulty copy); block j
+  // of ceil(j eta) - ceil((j - 1) eta) Omega_F cycles starts from the Gamma
+  // values after Omega_I cycle j - 1 (copied into the faulty blocks), Omega_I
+  // cycle j follows (the two touch disjoint data, so the device runs them
+  // concurrently); at the end the faulty blocks take the final Gamma values.
+  void recover_dn(const std::vector<unsigned char>& faulty, int n_global, double eta) {
+    const int top = (int)m.lv.size() - 1;
+    const HostLevel& L = m.lv[top];
+    Lev& D = lv[top];
+    const Cps cn = copies(neum, top);
+    std::vector<int> gamma;
+    for (int n : neum.lv[top].free_if) {
+      bool any_f = false;
+      for (int c = L.if_cptr[n]; c < L.if_cptr[n + 1]; ++c) any_f = any_f || faulty[L.if_copy[c].macro];
+      if (any_f) gamma.push_back(n);
+    }
+    std::vector<double> fI_dn = D.fI;
+    for (int n : gamma) {
+      double off, diag;
+      if_stencil(L, cn, D.u, n, off, diag);
+      fI_dn[n] = diag * D.uI[n] + off;
+    }
+    auto to_faulty_blocks = [&](const std::vector<double>& val) {
+      for (size_t q = 0; q < gamma.size(); ++q)
+        for (int c = L.if_cptr[gamma[q]]; c < L.if_cptr[gamma[q] + 1]; ++c) {
+          const Copy& cp = L.if_copy[c];
+          if (faulty[cp.macro]) D.u[at(L, cp.macro, cp.i, cp.j, cp.k)] = val[q];
+        }
+    };
+    std::vector<double> snap(gamma.size());
+    for (size_t q = 0; q < gamma.size(); ++q) snap[q] = D.uI[gamma[q]];
+    for (int j = 1; j <= n_global; ++j) {
+      const int cyc = (int)std::ceil(j * eta) - (int)std::ceil((j - 1) * eta);
+      if (j >= 2) to_faulty_blocks(snap);
+      for (int c = 0; c < cyc; ++c) vcycle(loc);
+      vcycle(neum, &fI_dn);
+      for (size_t q = 0; q < gamma.size(); ++q) snap[q] = D.uI[gamma[q]];
+    }
+    to_faulty_blocks(snap);
   }
 
   // fault (§2.2): the faulty blocks lose everything, the masters inside
@@ -305,7 +369,9 @@ int main(int argc, char** argv) {
   if (nf > 0) {
     build_general_problem(M.m, 1, faulty, M.loc);
     build_general_problem(M.m, 2, faulty, M.heal);
+    build_general_problem(M.m, 3, faulty, M.neum);
   }
+  const double eta = argc > 11 + nf ? atof(argv[11 + nf]) : 1.0;
   M.lv.resize(M.m.lv.size());
   for (size_t l = 0; l < M.m.lv.size(); ++l) {
     const HostLevel& L = M.m.lv[l];
@@ -335,7 +401,7 @@ int main(int argc, char** argv) {
   for (int n = 0; n < T.n_if; ++n) {
     D.fI[n] = f[T.if_gid[n]];
     D.uI[n] = u0[T.if_gid[n]];
-    M.write_copies(T, D.u, n, D.uI[n]);
+    M.write_copies(T, M.all_copies((int)M.m.lv.size() - 1), D.u, n, D.uI[n]);
   }
   std::vector<double> hist = {1.0};
   const double r0 = M.resnorm();
@@ -348,6 +414,7 @@ int main(int argc, char** argv) {
         for (int q = 0; q < n_local; ++q) M.vcycle(M.loc);
       if (recovery == 2)
         for (int q = 0; q < n_global; ++q) M.vcycle(M.heal);
+      if (recovery == 3) M.recover_dn(faulty, n_global, eta);
       hist.push_back(M.resnorm() / r0);
     }
     std::vector<double> out(nn);

@@ -8,8 +8,8 @@ classes, and for the global problem and the three recovery problem kinds
 CG matrix (§2.1, §3.1, §3.2 Fig. 4), on meshes of another connectivity than
 the cube family; and a host model of the device V-cycle (those tables driven
 with the kernels' per-node arithmetic and order, tests/host/general_vcycle.cpp)
-against the oracle's V-cycle iterates and, with a fault, its LR / DD recovery
-(§2.2, §4.2 Algorithm 1)."""
+against the oracle's V-cycle iterates and, with a fault, its LR / DD / DN
+recovery (§2.2, §4.2 Algorithm 1, §4.3 Algorithm 2)."""
 
 import os
 import shutil
@@ -176,11 +176,12 @@ def test_host_model_of_the_device_vcycle_matches_oracle(vcycle_prog, tmp_path, m
         assert np.linalg.norm(ul - uo[perm]) <= 1e-11 * np.linalg.norm(uo), c
 
 
-@pytest.mark.parametrize("recovery", ["LR", "DD"])
+@pytest.mark.parametrize("recovery", ["LR", "DD", "DN"])
 def test_host_model_of_the_device_fault_recovery_matches_oracle(vcycle_prog, tmp_path, recovery):
-    """Fault after cycle 2 on one sub-cube's five macros and its LR / DD
-    recovery through the library's tables and the kernels' arithmetic: the
-    residual history and the iterates equal the oracle's."""
+    """Fault after cycle 2 on one sub-cube's five macros and its LR / DD / DN
+    recovery through the library's tables and the kernels' arithmetic (DN in
+    the device's block schedule): the residual history and the iterates
+    equal the oracle's."""
     v, t = I.five_tet_macro_mesh((2, 2, 1), seed=3, amp=0.12)
     R = 4
     om = U.UMesh(v, t, R)
@@ -195,11 +196,13 @@ def test_host_model_of_the_device_fault_recovery_matches_oracle(vcycle_prog, tmp
     uo[perm].tofile(tmp_path / "u0.bin")
     ids = [5, 6, 7, 8, 9]
     cycles, n_local, n_global = 5, 3, 2
-    rec = {"LR": 1, "DD": 2}[recovery]
+    rec = {"LR": 1, "DD": 2, "DN": 3}[recovery]
+    eta = 2.5
     subprocess.check_call([vcycle_prog, str(len(v)), str(len(t)), str(R), str(cycles), str(tmp_path), "2", str(rec),
-                           str(n_local), str(n_global), str(len(ids)), *map(str, ids)])
-    kw = dict(recovery=U.LR, n_local=n_local) if recovery == "LR" else \
-        dict(recovery=U.DD, n_local=n_local, n_global=n_global)
+                           str(n_local), str(n_global), str(len(ids)), *map(str, ids), str(eta)])
+    kw = {"LR": dict(recovery=U.LR, n_local=n_local),
+          "DD": dict(recovery=U.DD, n_local=n_local, n_global=n_global),
+          "DN": dict(recovery=U.DN, n_global=n_global, eta=eta)}[recovery]
     hist_o = U.solve(om, uo, fo, rtol=0.0, max_cycles=cycles, fault_cycle=2, fault_ids=ids, **kw)
     hist = np.fromfile(tmp_path / "hist.bin")
     assert len(hist) == len(hist_o) == cycles + 2
