@@ -22,6 +22,10 @@
  *   handle is a no-op that returns HHG_OK.
  * - A mesh handle owns all device storage it allocates; the caller owns the
  *   vectors it passes in.  Handles are not thread-safe: one thread at a time.
+ * - A mesh lives on the device that was current when it was created.  Every
+ *   call that takes a mesh (or a batch) needs that device current and
+ *   returns HHG_ERR_STATE otherwise; hhg_mesh_destroy makes the mesh's device
+ *   current by itself for the release and restores the caller's device.
  * - Global vectors (right-hand side, solution) are laid out over the global
  *   node grid, x fastest: node (x, y, z) of a grid with nx, ny, nz intervals
  *   has index (z * (ny + 1) + y) * (nx + 1) + x, nx = subcubes[0] * 2^levels
@@ -116,9 +120,9 @@ int hhg_mesh_destroy(hhg_mesh* mesh);
  * gives their count.  One Gauss-Seidel step visits the volume nodes by their
  * macro's colour (i + 2j + 3k) mod 4 and then the interface nodes in the
  * classes of a greedy colouring of their couplings in key order.
- * V-cycles, solves, fault injection and LR / DD / DN recovery (FP64) are
- * available; mixed precision, coefficient changes and gradients, batching,
- * autotuning and the allocation-free cycle return HHG_ERR_STATE for these
+ * V-cycles (also the allocation-free one), solves, fault injection and LR /
+ * DD / DN recovery (FP64) are available; mixed precision, coefficient changes
+ * and gradients, batching and autotuning return HHG_ERR_STATE for these
  * meshes.  Errors: HHG_ERR_ARG for invalid sizes, ids, degenerate macros or
  * a non-conforming mesh (found before any device use). */
 typedef struct {
@@ -307,12 +311,15 @@ int hhg_batch_destroy(hhg_batch* batch);
  * until the process exits) instead of in memory obtained from cudaMalloc; the
  * call itself makes no cudaMalloc, cudaFree or other allocating call.
  * Limit: the coarsest level may have at most 16384 unknowns; larger meshes
- * get HHG_ERR_ARG.  The first call on a device looks up the array's device
- * address (cudaGetSymbolAddress) with that device current; make that first
- * call before any stream capture.  All calls share the array and it keeps
- * the last call's contents; the CG kernel writes every work value before it
- * reads it, so nothing has to start at zero, but calls whose work overlaps on
- * the GPU (other streams, other threads, other meshes) race on the array. */
+ * get HHG_ERR_ARG.  Meshes of general connectivity are accepted.  The mesh's
+ * device must be current (HHG_ERR_STATE otherwise); the first call on a
+ * device looks up that device's copy of the array (cudaGetSymbolAddress) with
+ * the device current, so make that first call before any stream capture.
+ * The cycle's Gauss-Seidel launches are not timed by hhg_profile_enable.
+ * All calls share the array and it keeps the last call's contents; the CG
+ * kernel writes every work value before it reads it, so nothing has to start
+ * at zero, but calls whose work overlaps on the GPU (other streams, other
+ * threads, other meshes) race on the array. */
 int hhg_vcycle_noalloc(hhg_mesh* mesh, int pre, int post, void* stream);
 
 /* Measurement support (not part of the method).
@@ -329,11 +336,25 @@ int hhg_vcycle_noalloc(hhg_mesh* mesh, int pre, int post, void* stream);
  * hhg_launch_count: kernel launches issued by the library in this process;
  * each kernel of a CUDA graph the library replays (batched recovery, the
  * later cycles of a local recovery) counts as one launch per replay, kernels
- * recorded while capturing such a graph do not count. */
+ * recorded while capturing such a graph do not count.
+ * hhg_set_launch_limit: at most max_ctas CTAs per level-wide launch (0, the
+ * default: as many as the GPU holds at once).  A level-wide launch walks its
+ * work units (interface chunks, then volume tiles) with a grid stride when
+ * it has fewer than 4 units per CTA, and otherwise hands the units out
+ * through a per-problem counter (the dynamic walk of large launches); a small
+ * limit makes small meshes take the dynamic walk.  The result does not
+ * depend on the limit.  Drops the captured recovery-cycle graph.
+ * hhg_walk_counts: counts[0..3] = level-wide launches that completed the
+ * dynamic walk, for the global problem, the faulty sub-problem (Omega_F),
+ * the healthy sub-problem with Gamma frozen and the Neumann problem of DN
+ * recovery (0 where a problem does not exist; counts restart when a fault set
+ * replaces the sub-problems).  Synchronises the device. */
 int hhg_profile_enable(hhg_mesh* mesh, int enable);
 int hhg_profile_read(hhg_mesh* mesh, int64_t* launches, double* total_ms);
 int hhg_profile_info(const hhg_mesh* mesh, int64_t* volume_nodes, int* seven_point);
 int hhg_launch_count(int64_t* count);
+int hhg_set_launch_limit(hhg_mesh* mesh, int max_ctas);
+int hhg_walk_counts(hhg_mesh* mesh, int64_t* counts);
 
 /* Copy the message of the calling thread's last failure into buf (always
  * NUL-terminated if len > 0).  Returns the status of that failure. */

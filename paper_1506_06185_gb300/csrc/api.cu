@@ -136,6 +136,8 @@ struct hhg_mesh {
   double* host_scalar = nullptr;   // pinned
   double* grad_partial = nullptr;  // coefficient-gradient partial sums
   double* grad_out = nullptr;
+  // CTAs per fused launch at most (0: as many as are resident; hhg_set_launch_limit)
+  int grid_cap = 0;
   // profiling of the finest-level Gauss-Seidel volume kernel of the global problem
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_ev;
@@ -269,6 +271,7 @@ ProbArgs pargs(const DevProblem& p, int l) {
   a.n_zero = q.n_zero;
   a.gather = q.gather;
   a.sched = p.sched;
+  a.grid_cap = p.grid_cap;
   return a;
 }
 
@@ -307,8 +310,9 @@ int upload_problem(hhg_mesh* m, const HostProblem& h, DevProblem& d) {
   HHG_TRY(dalloc(m, &d.partial, (size_t)d.n_partial));
   HHG_TRY(dalloc(m, &d.scalar, 8));
   HHG_TRY(dalloc(m, &d.cg_iters, 4));
-  HHG_TRY(dalloc(m, &d.sched, 2));
-  HHG_CUDA(cudaMemset(d.sched, 0, 2 * sizeof(int)));
+  HHG_TRY(dalloc(m, &d.sched, 4));
+  HHG_CUDA(cudaMemset(d.sched, 0, 4 * sizeof(int)));
+  d.grid_cap = m->grid_cap;
   return HHG_OK;
 }
 
@@ -388,14 +392,15 @@ int prof_pair(hhg_mesh* m, cudaEvent_t* b, cudaEvent_t* e) {
   return HHG_OK;
 }
 
+// profile = false keeps the profiling hook (which creates events) out.
 template <class T>
-int smooth(hhg_mesh* m, Prec<T>& P, DevProblem& p, int l, int steps, cudaStream_t s) {
+int smooth(hhg_mesh* m, Prec<T>& P, DevProblem& p, int l, int steps, cudaStream_t s, bool profile = true) {
   const int L = (int)P.lv.size() - 1;
   DevLevel<T>& D = P.lv[l];
   const LevelArgs a = plargs(m, p, l);
   const ProbArgs q = pargs(p, l);
   const T* fI = level_fI<T>(D, p, l == L);
-  const bool prof = l == L && p.kind == 0;
+  const bool prof = profile && l == L && p.kind == 0;
   const T* fs = nullptr;
   const T* wsc = nullptr;
   if constexpr (std::is_same<T, double>::value)
@@ -432,16 +437,25 @@ int smooth(hhg_mesh* m, Prec<T>& P, DevProblem& p, int l, int steps, cudaStream_
   return HHG_OK;
 }
 
+// Options of one cycle beyond the problem's own state: cg_work (not null)
+// replaces the problem's coarse CG work vectors (4 n_cg doubles); profile =
+// false leaves the cycle's Gauss-Seidel launches out of hhg_profile_enable's
+// record.
+struct CycleOpts {
+  double* cg_work = nullptr;
+  bool profile = true;
+};
+
 template <class T>
 int vcycle_T(hhg_mesh* m, Prec<T>& P, DevProblem& p, int pre, int post, double cg_rtol, int cg_maxit,
-             cudaStream_t s) {
+             cudaStream_t s, const CycleOpts& co = CycleOpts()) {
   const int L = (int)P.lv.size() - 1;
   const bool s7 = m->host.seven_point;
   for (int l = L; l >= 1; --l) {
     DevLevel<T>& D = P.lv[l];
     const LevelArgs a = plargs(m, p, l);
     const ProbArgs q = pargs(p, l);
-    HHG_TRY(smooth<T>(m, P, p, l, pre, s));
+    HHG_TRY(smooth<T>(m, P, p, l, pre, s, co.profile));
     HHG_CUDA(residual<T>(a, q, D.u, D.uI, D.f, level_fI<T>(D, p, l == L), D.r, D.W, s7, true, nullptr, nullptr, s));
     DevLevel<T>& C = P.lv[l - 1];
     if (m->host.general) {
@@ -457,13 +471,13 @@ int vcycle_T(hhg_mesh* m, Prec<T>& P, DevProblem& p, int pre, int post, double c
     }
     HHG_CUDA(restrict_to<T>(plargs(m, p, l - 1), a, pargs(p, l - 1), D.r, C.f, C.fI, C.u, C.uI, s));
   }
-  HHG_CUDA(coarse_cg<T>(p, P.lv[0].f, P.lv[0].fI, P.lv[0].u, P.lv[0].uI, cg_rtol, cg_maxit, s));
+  HHG_CUDA(coarse_cg<T>(p, P.lv[0].f, P.lv[0].fI, P.lv[0].u, P.lv[0].uI, cg_rtol, cg_maxit, s, co.cg_work));
   for (int l = 1; l <= L; ++l) {
     DevLevel<T>& D = P.lv[l];
     const LevelArgs a = plargs(m, p, l);
     const ProbArgs q = pargs(p, l);
     HHG_CUDA(prolong_add<T>(a, plargs(m, p, l - 1), q, D.u, D.uI, P.lv[l - 1].u, s));
-    HHG_TRY(smooth<T>(m, P, p, l, post, s));
+    HHG_TRY(smooth<T>(m, P, p, l, post, s, co.profile));
   }
   return HHG_OK;
 }
@@ -605,6 +619,21 @@ int64_t global_dof(const hhg_mesh* m) {
 int refuse_general(const hhg_mesh* m, const char* what) {
   if (m && m->host.general)
     return fail(HHG_ERR_STATE, std::string(what) + " is not available for meshes of general connectivity");
+  return HHG_OK;
+}
+
+// Every call on a mesh runs on the device the mesh was created on: that
+// device must be current (the mesh's buffers, streams and the static scratch
+// address of the allocation-free cycle belong to it).
+int check_device(const hhg_mesh* m) {
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(HHG_ERR_CUDA, "cudaGetDevice failed");
+  }
+  if (dev != m->device)
+    return fail(HHG_ERR_STATE, "the current device (" + std::to_string(dev) + ") is not the mesh's device (" +
+                                   std::to_string(m->device) + ")");
   return HHG_OK;
 }
 
@@ -987,23 +1016,20 @@ extern "C" {
 
 int hhg_vcycle_noalloc(hhg_mesh* m, int pre, int post, void* stream) {
   if (!m || pre < 0 || post < 0) return fail(HHG_ERR_ARG, "invalid argument");
-  HHG_TRY(refuse_general(m, "the allocation-free cycle"));
+  HHG_TRY(check_device(m));
   if (m->global.n_cg > NOALLOC_MAX_COARSE)
     return fail(HHG_ERR_ARG, "coarse problem has " + std::to_string(m->global.n_cg) +
                                  " unknowns; the allocation-free V-cycle holds at most " +
                                  std::to_string(NOALLOC_MAX_COARSE));
+  // the mesh's device is current (checked above), so this is its copy
   double* scratch = nullptr;
   HHG_TRY(noalloc_scratch(&scratch));
-  // run the ordinary cycle with the coarse CG pointed at the static array; the
-  // pointer is passed by value at launch, so restoring it right away is safe
-  double* own = m->global.cg_work;
-  const int kind = m->global.kind;
-  m->global.cg_work = scratch;
-  m->global.kind = -1;   // keeps the profiling hook (which creates events) out
-  const int rc = vcycle_T<double>(m, m->d64, m->global, pre, post, 1e-12, 1000, (cudaStream_t)stream);
-  m->global.cg_work = own;
-  m->global.kind = kind;
-  return rc;
+  // the ordinary cycle with the coarse CG's work vectors in the static array
+  // and without the profiling hook (which creates events)
+  CycleOpts co;
+  co.cg_work = scratch;
+  co.profile = false;
+  return vcycle_T<double>(m, m->d64, m->global, pre, post, 1e-12, 1000, (cudaStream_t)stream, co);
 }
 
 int hhg_last_error(char* buf, size_t len) {
@@ -1141,6 +1167,14 @@ int hhg_mesh_create_general(const hhg_general_desc* desc, hhg_mesh** out) {
 
 int hhg_mesh_destroy(hhg_mesh* m) {
   if (!m) return HHG_OK;
+  // the mesh's device is made current for the release and the caller's
+  // current device is put back afterwards
+  int cur = -1;
+  if (cudaGetDevice(&cur) != cudaSuccess) {
+    cudaGetLastError();
+    cur = -1;
+  }
+  if (cur != m->device) cudaSetDevice(m->device);
   cudaDeviceSynchronize();
   free_all(m);
   if (m->local_exec) cudaGraphExecDestroy(m->local_exec);
@@ -1153,7 +1187,9 @@ int hhg_mesh_destroy(hhg_mesh* m) {
     if (m->ev_dn_r[b]) cudaEventDestroy(m->ev_dn_r[b]);
   if (m->host_scalar) cudaFreeHost(m->host_scalar);
   for (cudaEvent_t ev : m->prof_ev) cudaEventDestroy(ev);
+  const int dev = m->device;
   delete m;
+  if (cur >= 0 && cur != dev) cudaSetDevice(cur);
   return HHG_OK;
 }
 
@@ -1173,6 +1209,7 @@ int hhg_mesh_bytes(const hhg_mesh* m, int64_t* bytes) {
 
 int hhg_set_problem(hhg_mesh* m, const double* f, const double* u0, void* stream) {
   if (!m) return fail(HHG_ERR_ARG, "null mesh");
+  HHG_TRY(check_device(m));
   cudaStream_t s = (cudaStream_t)stream;
   const int L = (int)m->host.lv.size() - 1;
   const LevelArgs a = largs(m, L);
@@ -1206,6 +1243,7 @@ int hhg_set_problem(hhg_mesh* m, const double* f, const double* u0, void* stream
 
 int hhg_get_solution(hhg_mesh* m, double* u, void* stream) {
   if (!m || !u) return fail(HHG_ERR_ARG, "null argument");
+  HHG_TRY(check_device(m));
   cudaStream_t s = (cudaStream_t)stream;
   const int L = (int)m->host.lv.size() - 1;
   const LevelArgs a = largs(m, L);
@@ -1234,6 +1272,7 @@ int hhg_get_solution(hhg_mesh* m, double* u, void* stream) {
 
 int hhg_vcycle(hhg_mesh* m, int pre, int post, double* resid_out, void* stream) {
   if (!m || pre < 0 || post < 0) return fail(HHG_ERR_ARG, "invalid argument");
+  HHG_TRY(check_device(m));
   cudaStream_t s = (cudaStream_t)stream;
   HHG_TRY(vcycle_T<double>(m, m->d64, m->global, pre, post, 1e-12, 1000, s));
   if (resid_out) HHG_TRY(resnorm(m, resid_out, s));
@@ -1242,11 +1281,13 @@ int hhg_vcycle(hhg_mesh* m, int pre, int post, double* resid_out, void* stream) 
 
 int hhg_residual_norm(hhg_mesh* m, double* out, void* stream) {
   if (!m || !out) return fail(HHG_ERR_ARG, "null argument");
+  HHG_TRY(check_device(m));
   return resnorm(m, out, (cudaStream_t)stream);
 }
 
 int hhg_inject_fault(hhg_mesh* m, const int* ids, int n, void* stream) {
   if (!m) return fail(HHG_ERR_ARG, "null mesh");
+  HHG_TRY(check_device(m));
   std::vector<unsigned char> set;
   HHG_TRY(check_ids(m, ids, n, set));
   HHG_TRY(setup_fault(m, set));
@@ -1256,6 +1297,7 @@ int hhg_inject_fault(hhg_mesh* m, const int* ids, int n, void* stream) {
 int hhg_recover_local(hhg_mesh* m, const int* ids, int n, int n_local, int n_global, double* seconds_local,
                       double* seconds_global, void* stream) {
   if (!m || n_local < 0 || n_global < 0) return fail(HHG_ERR_ARG, "invalid argument");
+  HHG_TRY(check_device(m));
   std::vector<unsigned char> set;
   HHG_TRY(check_ids(m, ids, n, set));
   HHG_TRY(setup_fault(m, set));
@@ -1266,6 +1308,7 @@ int hhg_recover_local(hhg_mesh* m, const int* ids, int n, int n_local, int n_glo
 int hhg_recover_dn(hhg_mesh* m, const int* ids, int n, int n_global, double eta, int* n_local_run,
                    double* seconds_local, double* seconds_global, void* stream) {
   if (!m || n_global < 0 || !(eta >= 0.0)) return fail(HHG_ERR_ARG, "invalid argument");
+  HHG_TRY(check_device(m));
   std::vector<unsigned char> set;
   HHG_TRY(check_ids(m, ids, n, set));
   HHG_TRY(setup_dn(m, set));
@@ -1275,6 +1318,7 @@ int hhg_recover_dn(hhg_mesh* m, const int* ids, int n, int n_global, double eta,
 
 int hhg_set_coefficients(hhg_mesh* m, const double* coeff, void* stream) {
   if (!m || !coeff) return fail(HHG_ERR_ARG, "null argument");
+  HHG_TRY(check_device(m));
   HHG_TRY(refuse_general(m, "changing coefficients"));
   for (int t = 0; t < m->host.n_macro; ++t)
     if (!(coeff[t] > 0.0)) return fail(HHG_ERR_ARG, "coefficients must be positive");
@@ -1284,6 +1328,7 @@ int hhg_set_coefficients(hhg_mesh* m, const double* coeff, void* stream) {
 
 int hhg_grad_coeff(hhg_mesh* m, const double* u, const double* lam, double* grad, void* stream) {
   if (!m || !u || !lam || !grad) return fail(HHG_ERR_ARG, "null argument");
+  HHG_TRY(check_device(m));
   HHG_TRY(refuse_general(m, "the coefficient gradient"));
   cudaStream_t s = (cudaStream_t)stream;
   const int L = (int)m->host.lv.size() - 1;
@@ -1313,6 +1358,7 @@ int hhg_grad_coeff(hhg_mesh* m, const double* u, const double* lam, double* grad
 
 int hhg_autotune(hhg_mesh* m, int reps, int* chosen, void* stream) {
   if (!m || reps < 1) return fail(HHG_ERR_ARG, "invalid argument");
+  HHG_TRY(check_device(m));
   HHG_TRY(refuse_general(m, "autotuning"));
   cudaStream_t s = (cudaStream_t)stream;
   const int nl = (int)m->host.lv.size();
@@ -1337,9 +1383,11 @@ int hhg_batch_create(hhg_mesh* global, int global_cycles, hhg_mesh* const* meshe
   if (!b) return fail(HHG_ERR_OOM, "host allocation failed");
   b->mixed = mixed != 0;
   if (global) HHG_TRY(refuse_general(global, "batched recovery"));
+  if (global) HHG_TRY(check_device(global));
   for (int t = 0; t < n_tasks; ++t) {
     hhg_mesh* m = meshes[t];
     if (!m || cycles[t] < 0) return fail(HHG_ERR_ARG, "invalid task");
+    HHG_TRY(check_device(m));
     HHG_TRY(refuse_general(m, "batched recovery"));
     if (b->mixed && m->precision != 32) return fail(HHG_ERR_STATE, "mixed precision needs precision-32 meshes");
     for (int q = 0; q < t; ++q)
@@ -1426,6 +1474,7 @@ int hhg_batch_create(hhg_mesh* global, int global_cycles, hhg_mesh* const* meshe
 
 int hhg_batch_launch(hhg_batch* b, double* task_ms, void* stream) {
   if (!b) return fail(HHG_ERR_ARG, "null batch");
+  if (!b->tasks.empty()) HHG_TRY(check_device(b->tasks[0].mesh));
   cudaStream_t s = (cudaStream_t)stream;
   HHG_CUDA(cudaGraphLaunch(b->exec, s));
   g_kernel_launches += b->kernels;
@@ -1467,6 +1516,7 @@ int hhg_profile_enable(hhg_mesh* m, int enable) {
 
 int hhg_profile_read(hhg_mesh* m, int64_t* launches, double* total_ms) {
   if (!m) return fail(HHG_ERR_ARG, "null mesh");
+  HHG_TRY(check_device(m));
   HHG_CUDA(cudaDeviceSynchronize());
   double t = 0.0;
   for (size_t q = 0; q + 1 < m->prof_used; q += 2) {
@@ -1488,6 +1538,28 @@ int hhg_profile_info(const hhg_mesh* m, int64_t* volume_nodes, int* seven_point)
   return HHG_OK;
 }
 
+int hhg_set_launch_limit(hhg_mesh* m, int max_ctas) {
+  if (!m || max_ctas < 0) return fail(HHG_ERR_ARG, "invalid argument");
+  HHG_TRY(check_device(m));
+  m->grid_cap = max_ctas;
+  for (DevProblem* p : {&m->global, &m->faulty, &m->healthy, &m->dn}) p->grid_cap = max_ctas;
+  // captured recovery cycles hold the old launch shapes
+  drop_local_graph(m);
+  return HHG_OK;
+}
+
+int hhg_walk_counts(hhg_mesh* m, int64_t* counts) {
+  if (!m || !counts) return fail(HHG_ERR_ARG, "null argument");
+  HHG_TRY(check_device(m));
+  const DevProblem* probs[4] = {&m->global, &m->faulty, &m->healthy, &m->dn};
+  int v[4] = {0, 0, 0, 0};
+  HHG_CUDA(cudaDeviceSynchronize());
+  for (int q = 0; q < 4; ++q)
+    if (probs[q]->sched) HHG_CUDA(cudaMemcpy(&v[q], probs[q]->sched + 2, sizeof(int), cudaMemcpyDeviceToHost));
+  for (int q = 0; q < 4; ++q) counts[q] = v[q];
+  return HHG_OK;
+}
+
 int hhg_launch_count(int64_t* count) {
   if (!count) return fail(HHG_ERR_ARG, "null argument");
   *count = (int64_t)g_kernel_launches.load();
@@ -1496,6 +1568,7 @@ int hhg_launch_count(int64_t* count) {
 
 int hhg_solve(hhg_mesh* m, const hhg_solve_opts* o, double* hist, int* n_hist, int* cycles, void* stream) {
   if (!m || !o) return fail(HHG_ERR_ARG, "null argument");
+  HHG_TRY(check_device(m));
   if (o->max_cycles < 0 || !(o->rtol >= 0.0)) return fail(HHG_ERR_ARG, "invalid rtol / max_cycles");
   if (o->mixed_precision) HHG_TRY(refuse_general(m, "mixed precision"));
   const bool mixed = o->mixed_precision != 0;

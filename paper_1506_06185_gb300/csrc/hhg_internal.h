@@ -282,7 +282,9 @@ struct DevProblemLevel {
 
 struct DevProblem {
   int kind = 0;
-  int* sched = nullptr;               // 2 unit counters of the dynamic walks (kernels.cu)
+  int* sched = nullptr;               // counters of the dynamic walks (kernels.cu): next unit,
+                                      // finished CTAs, completed dynamic launches
+  int grid_cap = 0;                   // CTAs per fused launch at most (0: resident CTAs)
   int* act = nullptr;
   int n_act = 0;
   std::vector<int> act_host;

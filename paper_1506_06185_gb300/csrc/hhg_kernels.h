@@ -28,7 +28,9 @@ struct ProbArgs {
   const int64_t* zero_off;
   int n_zero;
   const int64_t* gather;
-  int* sched;      // unit counters of the problem's dynamic walks (2 ints, zero between launches)
+  int* sched;      // the problem's dynamic-walk counters: [0] next unit, [1] finished CTAs (both
+                   // zero between launches), [2] dynamic launches completed
+  int grid_cap;    // > 0: at most this many CTAs per fused launch (0: as many as are resident)
 };
 
 // One colour of multicolour Gauss-Seidel on the volume interiors and the free
@@ -69,10 +71,11 @@ cudaError_t prolong_add(const LevelArgs& F, const LevelArgs& C, const ProbArgs& 
                         const T* uc, cudaStream_t s);
 
 // Coarse CG (FP64) on the compact free nodes of level 0; reads the level's
-// right-hand side (type T), writes the solution into u / uI.
+// right-hand side (type T), writes the solution into u / uI.  work (4 n_cg
+// doubles) replaces the problem's own work vectors when not null.
 template <class T>
 cudaError_t coarse_cg(const DevProblem& p, const T* f, const T* fI, T* u, T* uI, double rtol, int maxit,
-                      cudaStream_t s);
+                      cudaStream_t s, double* work = nullptr);
 
 cudaError_t reduce_partials(const double* partial, int n, double* out, cudaStream_t s);
 

@@ -250,9 +250,10 @@ __device__ __forceinline__ int vol_index(int u, int n_if_units) { return u - n_i
 // stride (measured faster there, e.g. the local recovery cycles of a few
 // macros).  Thread 0 takes the next unit one unit ahead, so the atomic's
 // latency hides behind the work.  The CTA that finishes last (counted in
-// sched[1]) puts both counters back to zero for the problem's next launch; a
-// problem's kernels run one after another on one stream, so launches never
-// share a counter.
+// sched[1]) puts both counters back to zero for the problem's next launch and
+// counts the completed dynamic launch in sched[2] (read back by tests to show
+// that the dynamic branch ran); a problem's kernels run one after another on
+// one stream, so launches never share a counter.
 constexpr int DYN_UNITS_PER_CTA = 4;
 __device__ __forceinline__ bool walk_dynamic(int n_units) { return n_units >= DYN_UNITS_PER_CTA * (int)gridDim.x; }
 __device__ __forceinline__ int walk_after(int cur, int n_units, int* sched) {
@@ -284,6 +285,7 @@ __device__ __forceinline__ void finish_units(int* sched, int n_units) {
     if (atomicAdd(sched + 1, 1) == (int)gridDim.x - 1) {
       atomicExch(sched, 0);
       atomicExch(sched + 1, 0);
+      atomicAdd(sched + 2, 1);
     }
   }
 }
@@ -1162,7 +1164,9 @@ inline Units units(int n_if_items, int n_tiles, int n_act) {
 std::mutex g_occ_mu;
 std::map<std::pair<const void*, int>, int> g_occ;   // (kernel, device) -> resident CTAs
 
-inline unsigned resident_grid(const void* kernel, int total) {
+// cap > 0 limits the grid further (a smaller grid makes a launch take the
+// dynamic walk at smaller sizes).
+inline unsigned resident_grid(const void* kernel, int total, int cap_limit = 0) {
   int dev = 0;
   cudaGetDevice(&dev);
   int cap = 0;
@@ -1179,6 +1183,7 @@ inline unsigned resident_grid(const void* kernel, int total) {
       g_occ[{kernel, dev}] = cap;
     }
   }
+  if (cap_limit > 0) cap = std::min(cap, cap_limit);
   return (unsigned)std::min(total, cap);
 }
 
@@ -1197,7 +1202,7 @@ cudaError_t gs_colour(const LevelArgs& L, const ProbArgs& p, T* u, T* uI, const 
   const Units g = units(n, L.n_tiles_int, p.n_act);
   if (g.total == 0) return cudaSuccess;
   auto kern = seven_point ? k_gs<T, true> : k_gs<T, false>;
-  const unsigned grid = resident_grid((const void*)kern, g.total);
+  const unsigned grid = resident_grid((const void*)kern, g.total, p.grid_cap);
   if (ev_begin) cudaEventRecord(ev_begin, s);
   ++g_kernel_launches;
   kern<<<grid, cta_shape(), 0, s>>>(L.N, L.rs, L.block, u, uI, f, fI, W, Winv, fs, Wsc, L.tiles_int, L.n_tiles_int, p.act,
@@ -1222,7 +1227,7 @@ cudaError_t residual(const LevelArgs& L, const ProbArgs& p, const T* u, const T*
     kern = write_r ? (norm ? k_res<T, true, true, true> : k_res<T, true, true, false>) : k_res<T, true, false, true>;
   else
     kern = write_r ? (norm ? k_res<T, false, true, true> : k_res<T, false, true, false>) : k_res<T, false, false, true>;
-  const unsigned grid = resident_grid((const void*)kern, g.total);
+  const unsigned grid = resident_grid((const void*)kern, g.total, p.grid_cap);
   if (n_part && norm) *n_part = (int)grid;
   ++g_kernel_launches;
   kern<<<grid, cta_shape(), 0, s>>>(L.N, L.rs, L.block, u, uI, f, fI, r, W, L.tiles_int, L.n_tiles_int, p.act,
@@ -1237,7 +1242,7 @@ cudaError_t restrict_to(const LevelArgs& C, const LevelArgs& F, const ProbArgs& 
   const int n = pc.col_off[4];
   const Units g = units(n + pc.n_zero, C.n_tiles_int, pc.n_act);
   if (g.total == 0) return cudaSuccess;
-  const unsigned grid = resident_grid((const void*)k_restrict<T>, g.total);
+  const unsigned grid = resident_grid((const void*)k_restrict<T>, g.total, pc.grid_cap);
   ++g_kernel_launches;
   k_restrict<T><<<grid, cta_shape(), 0, s>>>(C.N, C.rs, C.block, fc, fIc, uc, uIc, F.N, F.rs, F.block, rf, C.tiles_int,
                                              C.n_tiles_int, pc.act, pc.n_act, C.cptr, C.cps, pc.free_if, n, pc.gather,
@@ -1251,7 +1256,7 @@ cudaError_t prolong_add(const LevelArgs& F, const LevelArgs& C, const ProbArgs& 
   const int n = pf.col_off[4];
   const Units g = units(n, F.n_tiles_int, pf.n_act);
   if (g.total == 0) return cudaSuccess;
-  const unsigned grid = resident_grid((const void*)k_prolong<T>, g.total);
+  const unsigned grid = resident_grid((const void*)k_prolong<T>, g.total, pf.grid_cap);
   ++g_kernel_launches;
   k_prolong<T><<<grid, cta_shape(), 0, s>>>(F.N, F.rs, F.block, uf, uIf, C.N, C.rs, C.block, uc, F.tiles_int,
                                             F.n_tiles_int, pf.act, pf.n_act, F.cptr, F.cps, pf.free_if, n,
@@ -1261,11 +1266,11 @@ cudaError_t prolong_add(const LevelArgs& F, const LevelArgs& C, const ProbArgs& 
 
 template <class T>
 cudaError_t coarse_cg(const DevProblem& p, const T* f, const T* fI, T* u, T* uI, double rtol, int maxit,
-                      cudaStream_t s) {
+                      cudaStream_t s, double* work) {
   if (p.n_cg == 0) return cudaSuccess;
   ++g_kernel_launches;
   k_cg<T><<<1, CG_THREADS, 0, s>>>(p.n_cg, p.rowptr, p.col, p.val, p.fsrc, f, fI, p.uptr, p.udst, p.umaster, u, uI,
-                                   p.cg_work, rtol, maxit, p.cg_iters);
+                                   work ? work : p.cg_work, rtol, maxit, p.cg_iters);
   return cudaGetLastError();
 }
 
@@ -1392,7 +1397,7 @@ cudaError_t residual_to_f32(const LevelArgs& L, const ProbArgs& p, const double*
   if (n_part) *n_part = 0;
   if (g.total == 0) return cudaSuccess;
   auto kern = seven_point ? k_res_f32<true> : k_res_f32<false>;
-  const unsigned grid = resident_grid((const void*)kern, g.total);
+  const unsigned grid = resident_grid((const void*)kern, g.total, p.grid_cap);
   if (n_part) *n_part = (int)grid;
   ++g_kernel_launches;
   kern<<<grid, cta_shape(), 0, s>>>(L.N, L.rs, L.block, u, uI, f, fI, f32, fI32, W, L.tiles_int, L.n_tiles_int, p.act,
@@ -1405,7 +1410,7 @@ cudaError_t add_correction(const LevelArgs& L, const ProbArgs& p, double* u, dou
   const int n = p.col_off[4];
   const Units g = units(n, L.n_tiles_int, p.n_act);
   if (g.total == 0) return cudaSuccess;
-  const unsigned grid = resident_grid((const void*)k_add_corr, g.total);
+  const unsigned grid = resident_grid((const void*)k_add_corr, g.total, p.grid_cap);
   ++g_kernel_launches;
   k_add_corr<<<grid, cta_shape(), 0, s>>>(L.N, L.rs, L.block, u, uI, e, eI, L.tiles_int, L.n_tiles_int, p.act,
                                           p.n_act, L.cptr, L.cps, p.free_if, n, g.n_if_units, p.sched);
@@ -1438,7 +1443,8 @@ cudaError_t zero_problem_blocks(const LevelArgs& L, const ProbArgs& p, T* u, T* 
                                       T*, cudaStream_t);                                                       \
   template cudaError_t prolong_add<T>(const LevelArgs&, const LevelArgs&, const ProbArgs&, T*, T*, const T*,     \
                                       cudaStream_t);                                                           \
-  template cudaError_t coarse_cg<T>(const DevProblem&, const T*, const T*, T*, T*, double, int, cudaStream_t);   \
+  template cudaError_t coarse_cg<T>(const DevProblem&, const T*, const T*, T*, T*, double, int, cudaStream_t,     \
+                                    double*);                                                                  \
   template cudaError_t import_vec<T>(const LevelArgs&, const MacroGeo*, int, int64_t, int64_t, const double*,    \
                                      T*, T*, bool, cudaStream_t);                                              \
   template cudaError_t export_vec<T>(const LevelArgs&, const MacroGeo*, int, int64_t, int64_t, const T*,         \

@@ -28,7 +28,7 @@ EXPORTS = ["hhg_mesh_create", "hhg_mesh_destroy", "hhg_mesh_info", "hhg_mesh_byt
            "hhg_solve", "hhg_last_error", "hhg_profile_enable", "hhg_profile_read", "hhg_profile_info",
            "hhg_launch_count", "hhg_vcycle_noalloc", "hhg_set_coefficients", "hhg_grad_coeff",
            "hhg_autotune", "hhg_batch_create", "hhg_batch_launch", "hhg_batch_destroy", "hhg_recover_dn",
-           "hhg_mesh_create_general"]
+           "hhg_mesh_create_general", "hhg_set_launch_limit", "hhg_walk_counts"]
 
 
 class hhg_mesh_desc(C.Structure):
@@ -89,6 +89,8 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "hhg_profile_read": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_double)], C.c_int),
         "hhg_profile_info": ([P, C.POINTER(C.c_int64), C.POINTER(C.c_int)], C.c_int),
         "hhg_launch_count": ([C.POINTER(C.c_int64)], C.c_int),
+        "hhg_set_launch_limit": ([P, C.c_int], C.c_int),
+        "hhg_walk_counts": ([P, C.POINTER(C.c_int64)], C.c_int),
         "hhg_vcycle_noalloc": ([P, C.c_int, C.c_int, P], C.c_int),
         "hhg_set_coefficients": ([P, C.POINTER(C.c_double), P], C.c_int),
         "hhg_grad_coeff": ([P, P, P, C.POINTER(C.c_double), P], C.c_int),
@@ -367,6 +369,18 @@ def hhg_profile_info(h):
     n, s = C.c_int64(), C.c_int()
     _check(lib().hhg_profile_info(h, C.byref(n), C.byref(s)))
     return n.value, bool(s.value)
+
+
+def hhg_set_launch_limit(h, max_ctas):
+    return _check(lib().hhg_set_launch_limit(h, int(max_ctas)))
+
+
+def hhg_walk_counts(h):
+    """Dynamic-walk launches completed by the global, faulty, healthy
+    (Gamma frozen) and DN Neumann problems."""
+    c = (C.c_int64 * 4)()
+    _check(lib().hhg_walk_counts(h, c))
+    return list(c)
 
 
 def hhg_launch_count():

@@ -88,3 +88,38 @@ def test_coefficient_gradient_central_differences(mods):
         fd = (L(k0 + h * d) - L(k0 - h * d)) / (2 * h)
         assert abs(fd - g @ d) <= 1e-5 * max(abs(fd), 1e-12) + 1e-9, (fd, g @ d)
     M.close()
+
+
+def test_coefficient_gradient_sixteen_directions_384_macros(mods):
+    """The differentiation workload's shape at a size the test affords: 4x4x4
+    sub-cubes x 6 = 384 macros (refined 4 times), k ~ lognormal(0, 1) (seed
+    1), loss 1/2 ||u - u_target||^2 with the smooth target; the adjoint
+    gradient against central differences (h = 1e-6) on 16 random coefficient
+    directions (seed 2)."""
+    torch, H, AG = mods
+    sub, R = (4, 4, 4), 4
+    n = 384
+    k0 = I.lognormal_coeff(n, seed=1)
+    f = torch.from_numpy(I.random_load(sub, R, seed=0)).cuda()
+    ut = torch.from_numpy(I.smooth_target(sub, R)).cuda()
+    mask = torch.from_numpy(I.boundary_mask(sub, R)).cuda()
+    M = H.Mesh(sub, R, coeff=k0)
+    opts = dict(rtol=1e-13, max_cycles=100)
+
+    def L(k):
+        with torch.no_grad():
+            return float(_loss(torch, AG.solve(M, f, torch.from_numpy(k).cuda(), **opts), ut, mask))
+
+    kt = torch.from_numpy(k0.copy()).cuda().requires_grad_(True)
+    loss = _loss(torch, AG.solve(M, f, kt, **opts), ut, mask)
+    loss.backward()
+    g = kt.grad.cpu().numpy()
+    h = 1e-6
+    worst = 0.0
+    for d in I.random_directions(n, 16, seed=2):
+        fd = (L(k0 + h * d) - L(k0 - h * d)) / (2 * h)
+        err = abs(fd - g @ d) / max(abs(fd), 1e-12)
+        worst = max(worst, err)
+        assert abs(fd - g @ d) <= 1e-5 * max(abs(fd), 1e-12) + 1e-9, (fd, g @ d)
+    print(f"384 macros, 16 directions: largest relative gap to central differences {worst:.2e}")
+    M.close()

@@ -9,6 +9,7 @@ import pytest
 
 import hhg_inputs as I
 import oracle as O
+from parity import assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -46,13 +47,11 @@ def _recover(hhg, sub, R, ids, n_global, eta, coeff=None, affine=None, seed=5, b
     nf, tl, tg = M.recover_dn(ids, n_global, eta, timed=True)
     nf_o = O.dn_recover(m, uo, fo, ids, n_global, eta)
     assert nf == nf_o
-    err = _rel(M.get_solution(), O.interior(uo))
-    assert err <= RTOL_U, err
+    assert_close(M.get_solution(), O.interior(uo), RTOL_U, what="after DN recovery")
     # the global iteration resumes from consistent ghost copies
     M.vcycle()
     O.vcycle(m, m.global_problem, top, uo, fo)
-    err = _rel(M.get_solution(), O.interior(uo))
-    assert err <= RTOL_U, err
+    assert_close(M.get_solution(), O.interior(uo), RTOL_U, what="next global cycle")
     M.close()
     return nf, tl, tg
 
@@ -104,7 +103,7 @@ def test_solve_dn_history_matches_oracle(hhg):
     ref = O.solve(m, uo, O.pad(f), **kw)
     assert cyc == ref["cycles"] and len(hist) == len(ref["hist"])
     assert np.abs(hist - ref["hist"]).max() <= ATOL_HIST
-    assert _rel(M.get_solution(), O.interior(uo)) <= RTOL_U
+    assert_close(M.get_solution(), O.interior(uo), RTOL_U, what="DN solve")
     M.close()
 
 
@@ -126,7 +125,7 @@ def test_mixed_precision_dn(hhg):
     # a few per cent of the FP64 one
     k = kw["fault_cycle"] + 1
     assert abs(hist[k] / ref["hist"][k] - 1.0) < 0.05, (hist[k], ref["hist"][k])
-    assert _rel(M.get_solution(), O.interior(uo)) <= 1e-8
+    assert_close(M.get_solution(), O.interior(uo), 1e-8, what="mixed DN solve")
     M.close()
 
 
@@ -146,7 +145,7 @@ def test_two_faults_match_oracle(hhg, recovery):
     ref = O.solve(m, uo, O.pad(f), **kw)
     assert cyc == ref["cycles"] and len(hist) == len(ref["hist"]) == cyc + 3
     assert np.abs(hist - ref["hist"]).max() <= ATOL_HIST
-    assert _rel(M.get_solution(), O.interior(uo)) <= RTOL_U
+    assert_close(M.get_solution(), O.interior(uo), RTOL_U, what="two faults")
     with pytest.raises(hhg.HHGError) as e:
         M.solve(rtol=1e-10, max_cycles=5, faults=[(0, [1])])
     assert e.value.code == hhg.HHG_ERR_ARG
@@ -178,7 +177,7 @@ def test_dn_after_new_coefficients(hhg):
     O.inject_fault(m, uo, ids)
     M.recover_dn(ids, 2, 2.0)
     O.dn_recover(m, uo, fo, ids, 2, 2.0)
-    assert _rel(M.get_solution(), O.interior(uo)) <= RTOL_U
+    assert_close(M.get_solution(), O.interior(uo), RTOL_U, what="DN after new coefficients")
     M.close()
 
 

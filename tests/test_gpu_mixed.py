@@ -8,6 +8,7 @@ import pytest
 
 import hhg_inputs as I
 import oracle as O
+from parity import assert_close, errors
 
 pytestmark = pytest.mark.gpu
 
@@ -32,14 +33,16 @@ def _check(hhg, sub, R, f, u0, coeff=None, **kw):
     okw = {k: v for k, v in kw.items() if k in ("rtol", "max_cycles", "fault_cycle", "fault_ids", "recovery",
                                                   "n_local", "n_global", "eta")}
     ref = O.solve(m, uo, O.pad(f), **okw)
-    err = np.linalg.norm(ug - O.interior(uo)) / np.linalg.norm(O.interior(uo))
+    err, err_max = errors(ug, O.interior(uo))
     print(f"mixed: {cyc} cycles (FP64 oracle {ref['cycles']}), final rel. residual {hist[-1]:.2e}, "
-          f"|u - u_oracle| / |u_oracle| = {err:.2e}")
+          f"|u - u_oracle| / |u_oracle| = {err:.2e}, max-norm {err_max:.2e}")
     assert hist[-1] <= kw["rtol"]
     assert abs(cyc - ref["cycles"]) <= 1
-    # the stopping test bounds the algebraic error by cond(A) * rtol; both
-    # solutions sit within that of the exact discrete solution
-    assert err <= 100 * kw["rtol"] * 1e2
+    # both solutions satisfy the same stopping test ||r|| <= rtol ||r_0||, so
+    # each is within cond(A) rtol (relative) of the discrete solution; on
+    # meshes refined 4-5 times cond(A) ~ 4^R <= 1e3, which bounds the two
+    # solutions' difference node by node
+    assert_close(ug, O.interior(uo), 1e3 * kw["rtol"], what="mixed vs FP64 oracle")
     M.close()
     return err
 

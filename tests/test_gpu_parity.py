@@ -13,6 +13,7 @@ import pytest
 
 import hhg_inputs as I
 import oracle as O
+from parity import assert_close
 
 pytestmark = pytest.mark.gpu
 
@@ -60,7 +61,7 @@ def _compare_cycles(hhg, sub, R, f, u0, coeff=None, affine=None, cycles=6, devic
             ug = ug.cpu().numpy()
         else:
             ug = M.get_solution()
-        assert _rel(ug, O.interior(uo)) <= RTOL_U, (k, _rel(ug, O.interior(uo)))
+        assert_close(ug, O.interior(uo), RTOL_U, what=f"cycle {k}")
         assert abs(rg - O.resnorm(m, uo, fo)) <= ATOL_HIST * r0, k
     M.close()
 
@@ -106,7 +107,7 @@ def _compare_solve(hhg, sub, R, f, u0, coeff=None, affine=None, **kw):
     assert len(hist) == len(ref["hist"])
     assert np.abs(hist - ref["hist"]).max() <= ATOL_HIST, np.abs(hist - ref["hist"]).max()
     ug = M.get_solution()
-    assert _rel(ug, O.interior(uo)) <= RTOL_U, _rel(ug, O.interior(uo))
+    assert_close(ug, O.interior(uo), RTOL_U, what="solve")
     M.close()
     return hist, ref
 
@@ -172,7 +173,7 @@ def test_recover_local_matches_oracle_and_reports_times(hhg):
     ids = I.subcube_macros(sub, 1, 0, 1)
     M.inject_fault(ids)
     O.inject_fault(m, uo, ids)
-    assert _rel(M.get_solution(), O.interior(uo)) <= RTOL_U
+    assert_close(M.get_solution(), O.interior(uo), RTOL_U, what="after the fault")
     tl, tg = M.recover_local(ids, 4, 2, timed=True)
     assert tl > 0 and tg > 0
     lp, hp = m.local_problem(ids), m.healthy_problem(ids)
@@ -180,7 +181,7 @@ def test_recover_local_matches_oracle_and_reports_times(hhg):
         O.vcycle(m, lp, top, uo, fo)
     for _ in range(2):
         O.vcycle(m, hp, top, uo, fo)
-    assert _rel(M.get_solution(), O.interior(uo)) <= RTOL_U
+    assert_close(M.get_solution(), O.interior(uo), RTOL_U, what="after DD recovery")
     M.close()
 
 
@@ -208,7 +209,7 @@ def test_replayed_local_cycles_match_oracle_and_count_launches(hhg):
         deltas.append(hhg.hhg_launch_count() - l0)
         for _ in range(n):
             O.vcycle(m, lp, top, uo, fo)
-        assert _rel(M.get_solution(), O.interior(uo)) <= RTOL_U
+        assert_close(M.get_solution(), O.interior(uo), RTOL_U, what=f"{n} local cycles")
     per_cycle = (deltas[1] - deltas[0]) // 2
     assert per_cycle > 0
     assert deltas[1] - deltas[0] == 2 * per_cycle
