@@ -231,6 +231,7 @@ LevelArgs largs(const hhg_mesh* m, int l) {
   a.if_gid = t.if_gid;
   a.cptr = t.if_cptr;
   a.cps = t.if_copy;
+  a.cp_off = t.cp_off;
   a.tiles_int = t.tiles_int;
   a.n_tiles_int = t.n_tiles_int;
   a.tiles_all = t.tiles_all;
@@ -245,6 +246,7 @@ LevelArgs plargs(const hhg_mesh* m, const DevProblem& p, int l) {
   if (p.lv[l].cptr) {
     a.cptr = p.lv[l].cptr;
     a.cps = p.lv[l].cps;
+    a.cp_off = p.lv[l].cp_off;
   }
   return a;
 }
@@ -272,7 +274,61 @@ ProbArgs pargs(const DevProblem& p, int l) {
   a.gather = q.gather;
   a.sched = p.sched;
   a.grid_cap = p.grid_cap;
+  a.tnb = q.tnb;
+  a.tw64 = q.tw64;
+  a.td64 = q.td64;
+  a.ti64 = q.ti64;
+  a.tw32 = q.tw32;
+  a.td32 = q.td32;
+  a.ti32 = q.ti32;
+  a.tn = q.tn;
   return a;
+}
+
+// Interface stencil tables (weights, diagonal, inverse diagonal) of problem
+// level l from the current stencils; allocates on the first call (device
+// pointers null), else overwrites the weights in place (new coefficients).
+// Levels of general meshes, the coarsest level and meshes whose offsets need
+// more than 32 bits keep the per-copy path (tables null).
+int upload_if_tables(hhg_mesh* m, DevProblemLevel& q, int l, int kind, const std::vector<int>& free_if,
+                     const std::vector<int>& pcptr, const std::vector<Copy>& pcopies) {
+  if (l == 0 || free_if.empty()) return HHG_OK;
+  const HostLevel& H = m->host.lv[l];
+  const std::vector<int>& cptr = kind == 3 ? pcptr : H.if_cptr;
+  const std::vector<Copy>& copies = kind == 3 ? pcopies : H.if_copy;
+  const int K = m->host.seven_point ? 6 : 14;
+  std::vector<uint32_t> nb;
+  std::vector<double> w, dg;
+  if (!build_if_tables(m->host, l, free_if, cptr, copies, K, nb, w, dg)) return HHG_OK;
+  const size_t n = free_if.size();
+  std::vector<double> di(n);
+  for (size_t i = 0; i < n; ++i) di[i] = 1.0 / dg[i];
+  const bool fresh = q.tnb == nullptr;
+  if (fresh) {
+    HHG_TRY(upload(m, &q.tnb, nb));
+    HHG_TRY(dalloc(m, &q.tw64, w.size()));
+    HHG_TRY(dalloc(m, &q.td64, n));
+    HHG_TRY(dalloc(m, &q.ti64, n));
+    if (m->precision == 32) {
+      HHG_TRY(dalloc(m, &q.tw32, w.size()));
+      HHG_TRY(dalloc(m, &q.td32, n));
+      HHG_TRY(dalloc(m, &q.ti32, n));
+    }
+    q.tn = (int)n;
+  } else if ((size_t)q.tn != n) {
+    return fail(HHG_ERR_STATE, "interface table changed shape");
+  }
+  HHG_CUDA(cudaMemcpy(q.tw64, w.data(), w.size() * sizeof(double), cudaMemcpyHostToDevice));
+  HHG_CUDA(cudaMemcpy(q.td64, dg.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+  HHG_CUDA(cudaMemcpy(q.ti64, di.data(), n * sizeof(double), cudaMemcpyHostToDevice));
+  if (q.tw32) {
+    std::vector<float> w32(w.begin(), w.end()), d32(dg.begin(), dg.end()), i32(n);
+    for (size_t i = 0; i < n; ++i) i32[i] = (float)(1.0 / (double)d32[i]);
+    HHG_CUDA(cudaMemcpy(q.tw32, w32.data(), w32.size() * sizeof(float), cudaMemcpyHostToDevice));
+    HHG_CUDA(cudaMemcpy(q.td32, d32.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+    HHG_CUDA(cudaMemcpy(q.ti32, i32.data(), n * sizeof(float), cudaMemcpyHostToDevice));
+  }
+  return HHG_OK;
 }
 
 int upload_problem(hhg_mesh* m, const HostProblem& h, DevProblem& d) {
@@ -280,6 +336,8 @@ int upload_problem(hhg_mesh* m, const HostProblem& h, DevProblem& d) {
   d.act_host = h.act;
   d.macro_active_host = h.macro_active;
   d.free0_host = h.lv.empty() ? std::vector<int>() : h.lv[0].free_if;
+  d.free_host.clear();
+  for (const HostProblemLevel& q : h.lv) d.free_host.push_back(q.free_if);
   d.n_act = (int)h.act.size();
   HHG_TRY(upload(m, &d.act, h.act));
   d.lv.assign(h.lv.size(), DevProblemLevel());
@@ -291,6 +349,11 @@ int upload_problem(hhg_mesh* m, const HostProblem& h, DevProblem& d) {
     HHG_TRY(upload(m, &d.lv[l].gather, h.lv[l].gather));
     HHG_TRY(upload(m, &d.lv[l].cptr, h.lv[l].cptr));
     HHG_TRY(upload(m, &d.lv[l].cps, h.lv[l].copies));
+    if (!h.lv[l].copies.empty()) {
+      std::vector<uint32_t> off;
+      if (copy_offsets(m->host, (int)l, h.lv[l].copies, off)) HHG_TRY(upload(m, &d.lv[l].cp_off, off));
+    }
+    HHG_TRY(upload_if_tables(m, d.lv[l], (int)l, h.kind, h.lv[l].free_if, h.lv[l].cptr, h.lv[l].copies));
     HHG_TRY(upload(m, &d.lv[l].gptr, h.lv[l].gptr));
     HHG_TRY(upload(m, &d.lv[l].goff, h.lv[l].goff));
     d.lv[l].class_off = h.lv[l].class_off;
@@ -456,7 +519,11 @@ int vcycle_T(hhg_mesh* m, Prec<T>& P, DevProblem& p, int pre, int post, double c
     const LevelArgs a = plargs(m, p, l);
     const ProbArgs q = pargs(p, l);
     HHG_TRY(smooth<T>(m, P, p, l, pre, s, co.profile));
-    HHG_CUDA(residual<T>(a, q, D.u, D.uI, D.f, level_fI<T>(D, p, l == L), D.r, D.W, s7, true, nullptr, nullptr, s));
+    // after a smoothing step the last colour's residual vanishes (cube family:
+    // colour 3 is smoothed last, interface nodes included)
+    const int skip = pre > 0 && !m->host.general ? 3 : -1;
+    HHG_CUDA(residual<T>(a, q, D.u, D.uI, D.f, level_fI<T>(D, p, l == L), D.r, D.W, s7, true, nullptr, nullptr, s,
+                         skip));
     DevLevel<T>& C = P.lv[l - 1];
     if (m->host.general) {
       // volume part as usual, interface part through the variable-length gathers
@@ -483,12 +550,15 @@ int vcycle_T(hhg_mesh* m, Prec<T>& P, DevProblem& p, int pre, int post, double c
 }
 
 // ||f - A u||^2 of problem p on the finest FP64 level, left in p.scalar[0].
-int norm2_async(hhg_mesh* m, DevProblem& p, cudaStream_t s) {
+// after_smoothing: the iterate comes straight from an FP64 cycle with post-
+// smoothing, so the last colour's residual vanishes and is skipped.
+int norm2_async(hhg_mesh* m, DevProblem& p, cudaStream_t s, bool after_smoothing = false) {
   const int L = (int)m->d64.lv.size() - 1;
   DevLevel<double>& D = m->d64.lv[L];
   int np = 0;
+  const int skip = after_smoothing && !m->host.general ? 3 : -1;
   HHG_CUDA(residual<double>(plargs(m, p, L), pargs(p, L), D.u, D.uI, D.f, level_fI<double>(D, p, true), nullptr, D.W,
-                            m->host.seven_point, false, p.partial, &np, s));
+                            m->host.seven_point, false, p.partial, &np, s, skip));
   HHG_CUDA(reduce_partials(p.partial, np, p.scalar, s));
   return HHG_OK;
 }
@@ -920,6 +990,12 @@ int update_coefficients(hhg_mesh* m, const double* coeff) {
       return fail(HHG_ERR_STATE, "coarse system changed shape");
     if (!h.val.empty())
       HHG_CUDA(cudaMemcpy(d->val, h.val.data(), h.val.size() * sizeof(double), cudaMemcpyHostToDevice));
+    // the interface tables hold summed stencil weights (kinds 0-2 use the
+    // level's own copy lists)
+    for (size_t l = 1; l < d->lv.size() && l < d->free_host.size(); ++l)
+      if (d->lv[l].tnb)
+        HHG_TRY(upload_if_tables(m, d->lv[l], (int)l, d->kind, d->free_host[l], std::vector<int>(),
+                                 std::vector<Copy>()));
   }
   return HHG_OK;
 }
@@ -1063,6 +1139,10 @@ int setup_device(hhg_mesh* m) {
     if ((rc = upload(m, &t.if_gid, H.if_gid)) != HHG_OK) break;
     if ((rc = upload(m, &t.if_cptr, H.if_cptr)) != HHG_OK) break;
     if ((rc = upload(m, &t.if_copy, H.if_copy)) != HHG_OK) break;
+    {
+      std::vector<uint32_t> off;
+      if (copy_offsets(m->host, l, H.if_copy, off) && (rc = upload(m, &t.cp_off, off)) != HHG_OK) break;
+    }
     if ((rc = upload(m, &t.tiles_int, H.tiles_int)) != HHG_OK) break;
     if ((rc = upload(m, &t.tiles_all, H.tiles_all)) != HHG_OK) break;
     t.n_tiles_int = (int)H.tiles_int.size();
@@ -1635,7 +1715,7 @@ int hhg_solve(hhg_mesh* m, const hhg_solve_opts* o, double* hist, int* n_hist, i
       HHG_TRY(read_scalar(m, m->global.scalar, &v, s));
     } else {
       HHG_TRY(vcycle_T<double>(m, m->d64, m->global, pre, post, cg_rtol, cg_maxit, s));
-      HHG_TRY(norm2_async(m, m->global, s));
+      HHG_TRY(norm2_async(m, m->global, s, post > 0));
       HHG_TRY(read_scalar(m, m->global.scalar, &v, s));
     }
     ++k;

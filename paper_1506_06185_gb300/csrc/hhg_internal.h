@@ -240,6 +240,24 @@ int64_t general_volume_id(const HostLevel& L, int macro, int i, int j, int k);
 // (needs p.act, p.macro_active and p.lv[0].free_if).
 void assemble_coarse(const HostMesh& m, HostProblem& p);
 
+// Block offsets (macro * block + local offset) of the copies of level l,
+// or of a given copy list; false if an offset does not fit 32 bits.
+bool copy_offsets(const HostMesh& m, int l, const std::vector<Copy>& copies, std::vector<uint32_t>& out);
+
+// Interface stencil tables of one problem level of a cube-family mesh.  For
+// the interface nodes free_if[q] (in that order) the stencil - the sum of the
+// sub-stencils of the node's copies listed in cptr / copies (§3.2, Fig. 4) -
+// is stored per distinct neighbour: its summed weight w and the block offset
+// nb of a copy of it inside the block of a macro whose sub-stencil reaches
+// it, K entries per node direction-major (entry e of node q at e * n + q,
+// n = free_if.size()), padded with weight 0 and the node's own first copy;
+// diag[q] is the summed centre weight.  Returns false (tables empty) for
+// general connectivity, for a node with more than K neighbours or for an
+// offset beyond 32 bits.
+bool build_if_tables(const HostMesh& m, int l, const std::vector<int>& free_if, const std::vector<int>& cptr,
+                     const std::vector<Copy>& copies, int K, std::vector<uint32_t>& nb, std::vector<double>& w,
+                     std::vector<double>& diag);
+
 // ---------------------------------------------------------------------------
 // Device-side structures.
 // ---------------------------------------------------------------------------
@@ -261,6 +279,7 @@ struct DevLevelTables {
   int64_t* if_gid = nullptr;
   int* if_cptr = nullptr;
   Copy* if_copy = nullptr;
+  uint32_t* cp_off = nullptr;         // block offset of every copy (null: computed from if_copy)
   Tile* tiles_int = nullptr;
   int n_tiles_int = 0;
   Tile* tiles_all = nullptr;
@@ -278,6 +297,19 @@ struct DevProblemLevel {
   int64_t* gather = nullptr;
   int* cptr = nullptr;                // active copies (kind 3), else null
   Copy* cps = nullptr;
+  uint32_t* cp_off = nullptr;         // block offsets of those copies (kind 3)
+  // interface stencil tables of the free interface nodes (build_if_tables;
+  // null for general meshes and on level 0): tK entries per node,
+  // direction-major with stride tn = free_if size; weights, diagonal and its
+  // inverse in both precisions (FP32 only on precision-32 meshes)
+  uint32_t* tnb = nullptr;
+  double* tw64 = nullptr;
+  double* td64 = nullptr;
+  double* ti64 = nullptr;
+  float* tw32 = nullptr;
+  float* td32 = nullptr;
+  float* ti32 = nullptr;
+  int tn = 0;
 };
 
 struct DevProblem {
@@ -290,6 +322,9 @@ struct DevProblem {
   std::vector<int> act_host;
   std::vector<unsigned char> macro_active_host;
   std::vector<int> free0_host;        // free interface nodes of level 0
+  std::vector<std::vector<int>> free_host;  // free interface nodes of every level
+                                      // (rebuilding the interface tables for new
+                                      // coefficients)
   std::vector<DevProblemLevel> lv;
   int n_cg = 0;
   int64_t nnz = 0;

@@ -14,6 +14,7 @@ struct LevelArgs {
   const int64_t* if_gid;
   const int* cptr;
   const Copy* cps;
+  const uint32_t* cp_off;   // block offsets of the copies cps (null: computed)
   const Tile* tiles_int;
   int n_tiles_int;
   const Tile* tiles_all;
@@ -31,6 +32,15 @@ struct ProbArgs {
   int* sched;      // the problem's dynamic-walk counters: [0] next unit, [1] finished CTAs (both
                    // zero between launches), [2] dynamic launches completed
   int grid_cap;    // > 0: at most this many CTAs per fused launch (0: as many as are resident)
+  // interface stencil tables of free_if (DevProblemLevel; tnb null: none)
+  const uint32_t* tnb;
+  const double* tw64;
+  const double* td64;
+  const double* ti64;
+  const float* tw32;
+  const float* td32;
+  const float* ti32;
+  int tn;
 };
 
 // One colour of multicolour Gauss-Seidel on the volume interiors and the free
@@ -54,10 +64,13 @@ cudaError_t scale_blocks(const double* f, const double* winv, double* out, int n
 // problem's frozen copies.  If partial != NULL each CTA also writes its
 // partial sum of r^2 (volume CTAs first, then interface CTAs) and write_r may
 // be false (norm only).  Returns the number of partials written in *n_part.
+// skip (0..3, cube-family meshes only): the colour smoothed last, whose
+// nodes' residual vanishes (all their neighbours have other colours and were
+// updated before them); it is written as zero without evaluating the stencil.
 template <class T>
 cudaError_t residual(const LevelArgs& L, const ProbArgs& p, const T* u, const T* uI, const T* f,
                      const T* fI, T* r, const T* W, bool seven_point, bool write_r, double* partial,
-                     int* n_part, cudaStream_t s);
+                     int* n_part, cudaStream_t s, int skip = -1);
 
 // Coarse right-hand side f_c = P^T r_f on the free coarse nodes; the coarse
 // correction u_c is set to zero on the problem's nodes of the coarse level.

@@ -329,13 +329,43 @@ __device__ __forceinline__ void if_stencil(int N, const int* __restrict__ rs, in
   }
 }
 
+// Writes val into the copies c0 .. c1 - 1 of an interface node: at their
+// precomputed block offsets cpo when given, else at the offsets computed from
+// (macro, i, j, k).
 template <class T>
 __device__ __forceinline__ void write_copies(int N, const int* __restrict__ rs, int64_t block, T* __restrict__ u,
-                                             const Copy* __restrict__ cps, int c0, int c1, T val) {
+                                             const Copy* __restrict__ cps, const uint32_t* __restrict__ cpo, int c0,
+                                             int c1, T val) {
+  if (cpo) {
+    for (int c = c0; c < c1; ++c) u[cpo[c]] = val;
+    return;
+  }
   for (int c = c0; c < c1; ++c) {
     const Copy cp = cps[c];
     u[(size_t)cp.macro * block + lidx32(rs, N, cp.i, cp.j, cp.k)] = val;
   }
+}
+
+// Interface stencil table of a problem level (build_if_tables): for list
+// entry q the K distinct neighbours of the node's summed stencil, entry e at
+// e * n + q (block offset nb, weight w), its diagonal and inverse diagonal.
+template <class T>
+struct IfTab {
+  const uint32_t* nb;
+  const T* w;
+  const T* diag;
+  const T* dinv;
+  int n;
+};
+constexpr int if_tab_k(bool s7) { return s7 ? 6 : 14; }
+
+// Off-diagonal part of the stencil of list entry q applied to u.
+template <class T, int K>
+__device__ __forceinline__ T if_offdiag(const IfTab<T>& t, const T* __restrict__ u, int q) {
+  T s = T(0);
+#pragma unroll
+  for (int e = 0; e < K; ++e) s += t.w[(size_t)e * t.n + q] * u[t.nb[(size_t)e * t.n + q]];
+  return s;
 }
 
 // ---------------------------------------------------------------------------
@@ -451,7 +481,9 @@ __device__ __forceinline__ void gs_group7(const Slice& sc, int N, int j, int g, 
 // 7-point residual r = f - A u of the colour-c nodes in slots m0 .. m0 + VW - 1
 // of interior row j of slice k (same vectors as gs_group7 plus the centre);
 // writes the interior nodes among them to rb and/or adds their squares to ss.
-template <class T, bool WRITE, bool NORM>
+// ZERO: the residual of these nodes is known to vanish (their colour was the
+// last one smoothed); zeros are written and nothing is read.
+template <class T, bool WRITE, bool NORM, bool ZERO = false>
 __device__ __forceinline__ void res_group7(const Slice& sc, int N, int j, int g, int c, const T* __restrict__ ub,
                                            const T* __restrict__ fb, T* __restrict__ rb, const T* __restrict__ w,
                                            double& ss) {
@@ -469,6 +501,22 @@ __device__ __forceinline__ void res_group7(const Slice& sc, int N, int j, int g,
   const int cc = c * sc.CS, cp = ((c + 1) & 3) * sc.CS, cm = ((c + 3) & 3) * sc.CS;
   const bool e1 = ic == 3, e0 = ic == 0;
   T acc[VW], a[VW];
+  if (ZERO) {
+#pragma unroll
+    for (int t = 0; t < VW; ++t) acc[t] = T(0);
+    if (WRITE) {
+      const int lo = max(mlo - m0, 0), hi = min(mlo + n - m0, VW);
+      T* out = rb + cc + r0 + m0;
+      if (lo == 0 && hi == VW) {
+        Vec<T>::store(out, acc);
+      } else {
+#pragma unroll
+        for (int t = 0; t < VW; ++t)
+          if (t >= lo && t < hi) out[t] = acc[t];
+      }
+    }
+    return;
+  }
   Vec<T>::load(fb + cc + r0 + m0, acc);
   Vec<T>::load(ub + cc + r0 + m0, a);               // centre
 #pragma unroll
@@ -538,7 +586,8 @@ __global__ void __launch_bounds__(CTA, 5) k_gs(int N, const int* __restrict__ rs
                                             const T* __restrict__ fs, const T* __restrict__ Wsc,
                                             const Tile* __restrict__ tiles, int n_tiles, const int* __restrict__ act,
                                             int n_act, int colour, const int* __restrict__ cptr,
-                                            const Copy* __restrict__ cps, const int* __restrict__ list, int n_list,
+                                            const Copy* __restrict__ cps, const uint32_t* __restrict__ cpo,
+                                            const int* __restrict__ list, int n_list, IfTab<T> tab,
                                             int n_if_units, int* __restrict__ sched) {
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
@@ -549,11 +598,16 @@ __global__ void __launch_bounds__(CTA, 5) k_gs(int N, const int* __restrict__ rs
       if (q < n_list) {
         const int node = list[q];
         const int c0 = cptr[node], c1 = cptr[node + 1];
-        T off = T(0), diag = T(0);
-        if_stencil<T, S7>(N, rs, block, u, W, cps, c0, c1, off, diag);
-        const T val = (fI[node] - off) / diag;
+        T val;
+        if (tab.nb) {
+          val = (fI[node] - if_offdiag<T, if_tab_k(S7)>(tab, u, q)) * tab.dinv[q];
+        } else {
+          T off = T(0), diag = T(0);
+          if_stencil<T, S7>(N, rs, block, u, W, cps, c0, c1, off, diag);
+          val = (fI[node] - off) / diag;
+        }
         uI[node] = val;
-        write_copies(N, rs, block, u, cps, c0, c1, val);
+        write_copies(N, rs, block, u, cps, cpo, c0, c1, val);
       }
       continue;
     }
@@ -608,9 +662,11 @@ __global__ void __launch_bounds__(CTA, sizeof(T) == 8 ? 6 : 5) k_res(int N, cons
                                              const T* __restrict__ fI, T* __restrict__ r, const T* __restrict__ W,
                                              const Tile* __restrict__ tiles, int n_tiles, const int* __restrict__ act,
                                              int n_act, const int* __restrict__ cptr, const Copy* __restrict__ cps,
-                                             const int* __restrict__ list, int n_list,
+                                             const uint32_t* __restrict__ cpo, const int* __restrict__ list,
+                                             int n_list, IfTab<T> tab,
                                              const int64_t* __restrict__ zero_off, int n_zero, int n_if_units,
-                                             double* __restrict__ partial, int* __restrict__ sched) {
+                                             double* __restrict__ partial, int* __restrict__ sched, int skip,
+                                             int skip_lo, int skip_hi) {
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
   __shared__ double sh[32];
@@ -622,10 +678,17 @@ __global__ void __launch_bounds__(CTA, sizeof(T) == 8 ? 6 : 5) k_res(int N, cons
       if (q < n_list) {
         const int node = list[q];
         const int c0 = cptr[node], c1 = cptr[node + 1];
-        T off = T(0), diag = T(0);
-        if_stencil<T, S7>(N, rs, block, u, W, cps, c0, c1, off, diag);
-        const T res = fI[node] - diag * uI[node] - off;
-        if (WRITE) write_copies(N, rs, block, r, cps, c0, c1, res);
+        T res;
+        if (q >= skip_lo && q < skip_hi) {
+          res = T(0);                              // the colour smoothed last
+        } else if (tab.nb) {
+          res = fI[node] - tab.diag[q] * uI[node] - if_offdiag<T, if_tab_k(S7)>(tab, u, q);
+        } else {
+          T off = T(0), diag = T(0);
+          if_stencil<T, S7>(N, rs, block, u, W, cps, c0, c1, off, diag);
+          res = fI[node] - diag * uI[node] - off;
+        }
+        if (WRITE) write_copies(N, rs, block, r, cps, cpo, c0, c1, res);
         if (NORM) ss += (double)res * (double)res;
       } else if (WRITE && q < n_list + n_zero) {
         r[zero_off[q - n_list]] = T(0);
@@ -644,6 +707,7 @@ __global__ void __launch_bounds__(CTA, sizeof(T) == 8 ? 6 : 5) k_res(int N, cons
       constexpr int VW = Vec<T>::n;
       const T wr[11] = {w[0], w[1], w[2], w[3], T(0), T(0), T(0), T(0), w[8], w[9], w[10]};
       for (int c = 0; c < 4; ++c) {
+        if (!WRITE && c == skip) continue;         // norm only: the skipped colour adds nothing
         const int total = flat_setup_slabs(t, N, c, true, VW, s_pre2, s_pre_tot);
         int sl = 0;
         for (int tt = tid256(); tt < total; tt += CTA) {
@@ -652,7 +716,10 @@ __global__ void __launch_bounds__(CTA, sizeof(T) == 8 ? 6 : 5) k_res(int N, cons
           const Tile ts{k, t.j0, t.m0, 1};
           int j, g;
           flat_item(ts, N, c, true, s_pre2[sl], tt - s_pre_tot[sl], j, g, VW);
-          res_group7<T, WRITE, NORM>(slice_consts(rs, N, k), N, j, g, c, ub, fb, rb, wr, ss);
+          if (c == skip)
+            res_group7<T, WRITE, NORM, true>(slice_consts(rs, N, k), N, j, g, c, ub, fb, rb, wr, ss);
+          else
+            res_group7<T, WRITE, NORM>(slice_consts(rs, N, k), N, j, g, c, ub, fb, rb, wr, ss);
         }
         __syncthreads();
       }
@@ -661,12 +728,15 @@ __global__ void __launch_bounds__(CTA, sizeof(T) == 8 ? 6 : 5) k_res(int N, cons
     // 15-point: four nodes of one slot per item
     HHG_TILE_NODES(N, rs, t, s_pre, {
       const int me = lidx32(rs, N, i, j, k);
-      T acc = fb[me] - w[0] * ub[me];
+      T acc = T(0);
+      if (((i + 2 * j + 3 * k) & 3) != skip) {
+        acc = fb[me] - w[0] * ub[me];
 _Pragma("unroll")
-      for (int d = 1; d < NDIR; ++d) {
-        int di, dj, dk;
-        dir_ijk(d, di, dj, dk);
-        acc -= w[d] * ub[lidx32(rs, N, i + di, j + dj, k + dk)];
+        for (int d = 1; d < NDIR; ++d) {
+          int di, dj, dk;
+          dir_ijk(d, di, dj, dk);
+          acc -= w[d] * ub[lidx32(rs, N, i + di, j + dj, k + dk)];
+        }
       }
       if (WRITE) rb[me] = acc;
       if (NORM) ss += (double)acc * (double)acc;
@@ -688,6 +758,7 @@ __global__ void __launch_bounds__(CTA) k_restrict(int Nc, const int* __restrict_
                                                   const T* __restrict__ rf, const Tile* __restrict__ tiles, int n_tiles,
                                                   const int* __restrict__ act, int n_act,
                                                   const int* __restrict__ cptr, const Copy* __restrict__ cps,
+                                                  const uint32_t* __restrict__ cpo,
                                                   const int* __restrict__ list, int n_list,
                                                   const int64_t* __restrict__ gather,
                                                   const int64_t* __restrict__ zero_off, int n_zero, int n_if_units, int* __restrict__ sched) {
@@ -707,7 +778,7 @@ __global__ void __launch_bounds__(CTA) k_restrict(int Nc, const int* __restrict_
         }
         fIc[node] = rf[g[0]] + T(0.5) * acc;
         uIc[node] = T(0);
-        write_copies(Nc, rsc, bc, uc, cps, cptr[node], cptr[node + 1], T(0));
+        write_copies(Nc, rsc, bc, uc, cps, cpo, cptr[node], cptr[node + 1], T(0));
       } else if (q < n_list + n_zero) {
         uc[zero_off[q - n_list]] = T(0);
       }
@@ -765,7 +836,8 @@ __global__ void __launch_bounds__(CTA) k_prolong(int Nf, const int* __restrict__
                                                  int Nc, const int* __restrict__ rsc, int64_t bc, const T* __restrict__ uc,
                                                  const Tile* __restrict__ tiles, int n_tiles,
                                                  const int* __restrict__ act, int n_act, const int* __restrict__ cptr,
-                                                 const Copy* __restrict__ cps, const int* __restrict__ list,
+                                                 const Copy* __restrict__ cps, const uint32_t* __restrict__ cpo,
+                                                 const int* __restrict__ list,
                                                  int n_list, int n_if_units, int* __restrict__ sched) {
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
@@ -779,7 +851,7 @@ __global__ void __launch_bounds__(CTA) k_prolong(int Nf, const int* __restrict__
         const Copy cp = cps[c0];
         const T val = uIf[node] + interp(uc + (size_t)cp.macro * bc, Nc, rsc, cp.i, cp.j, cp.k);
         uIf[node] = val;
-        write_copies(Nf, rsf, bf, uf, cps, c0, c1, val);
+        write_copies(Nf, rsf, bf, uf, cps, cpo, c0, c1, val);
       }
       continue;
     }
@@ -805,8 +877,9 @@ __global__ void __launch_bounds__(CTA) k_res_f32(int N, const int* __restrict__ 
                                                  const Tile* __restrict__ tiles, int n_tiles,
                                                  const int* __restrict__ act, int n_act,
                                                  const int* __restrict__ cptr, const Copy* __restrict__ cps,
-                                                 const int* __restrict__ list, int n_list, int n_if_units,
-                                                 double* __restrict__ partial, int* __restrict__ sched) {
+                                                 const int* __restrict__ list, int n_list, IfTab<double> tab,
+                                                 int n_if_units, double* __restrict__ partial,
+                                                 int* __restrict__ sched) {
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
   __shared__ double sh[32];
@@ -817,9 +890,14 @@ __global__ void __launch_bounds__(CTA) k_res_f32(int N, const int* __restrict__ 
       const int q = ic_ * CTA + tid256();
       if (q < n_list) {
         const int node = list[q];
-        double off = 0.0, diag = 0.0;
-        if_stencil<double, S7>(N, rs, block, u, W, cps, cptr[node], cptr[node + 1], off, diag);
-        const double res = fI[node] - diag * uI[node] - off;
+        double res;
+        if (tab.nb) {
+          res = fI[node] - tab.diag[q] * uI[node] - if_offdiag<double, if_tab_k(S7)>(tab, u, q);
+        } else {
+          double off = 0.0, diag = 0.0;
+          if_stencil<double, S7>(N, rs, block, u, W, cps, cptr[node], cptr[node + 1], off, diag);
+          res = fI[node] - diag * uI[node] - off;
+        }
         fI32[node] = (float)res;
         ss += res * res;
       }
@@ -869,7 +947,8 @@ __global__ void __launch_bounds__(CTA) k_add_corr(int N, const int* __restrict__
                                                   const float* __restrict__ eI, const Tile* __restrict__ tiles,
                                                   int n_tiles, const int* __restrict__ act, int n_act,
                                                   const int* __restrict__ cptr, const Copy* __restrict__ cps,
-                                                  const int* __restrict__ list, int n_list, int n_if_units, int* __restrict__ sched) {
+                                                  const uint32_t* __restrict__ cpo, const int* __restrict__ list,
+                                                  int n_list, int n_if_units, int* __restrict__ sched) {
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
   __shared__ int s_unit;
@@ -880,7 +959,7 @@ __global__ void __launch_bounds__(CTA) k_add_corr(int N, const int* __restrict__
         const int node = list[q];
         const double val = uI[node] + (double)eI[node];
         uI[node] = val;
-        write_copies(N, rs, block, u, cps, cptr[node], cptr[node + 1], val);
+        write_copies(N, rs, block, u, cps, cpo, cptr[node], cptr[node + 1], val);
       }
       continue;
     }
@@ -1146,6 +1225,22 @@ __global__ void k_zero_list(T* __restrict__ uI, const int* __restrict__ list, in
 }
 
 inline unsigned lin_grid(int64_t n, int b) { return (unsigned)((n + b - 1) / b); }
+
+// The problem's interface table in precision T, starting at list entry off.
+template <class T>
+IfTab<T> if_tab(const ProbArgs& p, int off);
+template <>
+IfTab<double> if_tab<double>(const ProbArgs& p, int off) {
+  IfTab<double> t{nullptr, nullptr, nullptr, nullptr, 0};
+  if (p.tnb && p.tw64) t = IfTab<double>{p.tnb + off, p.tw64 + off, p.td64 + off, p.ti64 + off, p.tn};
+  return t;
+}
+template <>
+IfTab<float> if_tab<float>(const ProbArgs& p, int off) {
+  IfTab<float> t{nullptr, nullptr, nullptr, nullptr, 0};
+  if (p.tnb && p.tw32) t = IfTab<float>{p.tnb + off, p.tw32 + off, p.td32 + off, p.ti32 + off, p.tn};
+  return t;
+}
 inline dim3 cta_shape() { return dim3(TILE_SLOTS, TILE_ROWS); }
 
 // Grid of a fused launch: interface units first, then tiles x active macros;
@@ -1206,15 +1301,16 @@ cudaError_t gs_colour(const LevelArgs& L, const ProbArgs& p, T* u, T* uI, const 
   if (ev_begin) cudaEventRecord(ev_begin, s);
   ++g_kernel_launches;
   kern<<<grid, cta_shape(), 0, s>>>(L.N, L.rs, L.block, u, uI, f, fI, W, Winv, fs, Wsc, L.tiles_int, L.n_tiles_int, p.act,
-                                    p.n_act, colour, L.cptr, L.cps, p.free_if + p.col_off[colour], n, g.n_if_units,
-                                    p.sched);
+                                    p.n_act, colour, L.cptr, L.cps, L.cp_off, p.free_if + p.col_off[colour], n,
+                                    if_tab<T>(p, p.col_off[colour]), g.n_if_units, p.sched);
   if (ev_end) cudaEventRecord(ev_end, s);
   return cudaGetLastError();
 }
 
 template <class T>
 cudaError_t residual(const LevelArgs& L, const ProbArgs& p, const T* u, const T* uI, const T* f, const T* fI, T* r,
-                     const T* W, bool seven_point, bool write_r, double* partial, int* n_part, cudaStream_t s) {
+                     const T* W, bool seven_point, bool write_r, double* partial, int* n_part, cudaStream_t s,
+                     int skip) {
   const bool norm = partial != nullptr;
   const int n = p.col_off[4];
   const int n_zero = write_r ? p.n_zero : 0;
@@ -1222,7 +1318,10 @@ cudaError_t residual(const LevelArgs& L, const ProbArgs& p, const T* u, const T*
   if (n_part) *n_part = 0;
   if (g.total == 0) return cudaSuccess;
   void (*kern)(int, const int*, int64_t, const T*, const T*, const T*, const T*, T*, const T*, const Tile*, int, const int*,
-               int, const int*, const Copy*, const int*, int, const int64_t*, int, int, double*, int*);
+               int, const int*, const Copy*, const uint32_t*, const int*, int, IfTab<T>, const int64_t*, int, int,
+               double*, int*, int, int, int);
+  const int skip_lo = skip >= 0 && skip < 4 ? p.col_off[skip] : 0;
+  const int skip_hi = skip >= 0 && skip < 4 ? p.col_off[skip + 1] : 0;
   if (seven_point)
     kern = write_r ? (norm ? k_res<T, true, true, true> : k_res<T, true, true, false>) : k_res<T, true, false, true>;
   else
@@ -1231,8 +1330,8 @@ cudaError_t residual(const LevelArgs& L, const ProbArgs& p, const T* u, const T*
   if (n_part && norm) *n_part = (int)grid;
   ++g_kernel_launches;
   kern<<<grid, cta_shape(), 0, s>>>(L.N, L.rs, L.block, u, uI, f, fI, r, W, L.tiles_int, L.n_tiles_int, p.act,
-                                    p.n_act, L.cptr, L.cps, p.free_if, n, p.zero_off, n_zero, g.n_if_units, partial,
-                                    p.sched);
+                                    p.n_act, L.cptr, L.cps, L.cp_off, p.free_if, n, if_tab<T>(p, 0), p.zero_off, n_zero,
+                                    g.n_if_units, partial, p.sched, skip >= 0 && skip < 4 ? skip : -1, skip_lo, skip_hi);
   return cudaGetLastError();
 }
 
@@ -1245,8 +1344,8 @@ cudaError_t restrict_to(const LevelArgs& C, const LevelArgs& F, const ProbArgs& 
   const unsigned grid = resident_grid((const void*)k_restrict<T>, g.total, pc.grid_cap);
   ++g_kernel_launches;
   k_restrict<T><<<grid, cta_shape(), 0, s>>>(C.N, C.rs, C.block, fc, fIc, uc, uIc, F.N, F.rs, F.block, rf, C.tiles_int,
-                                             C.n_tiles_int, pc.act, pc.n_act, C.cptr, C.cps, pc.free_if, n, pc.gather,
-                                             pc.zero_off, pc.n_zero, g.n_if_units, pc.sched);
+                                             C.n_tiles_int, pc.act, pc.n_act, C.cptr, C.cps, C.cp_off, pc.free_if, n,
+                                             pc.gather, pc.zero_off, pc.n_zero, g.n_if_units, pc.sched);
   return cudaGetLastError();
 }
 
@@ -1259,7 +1358,7 @@ cudaError_t prolong_add(const LevelArgs& F, const LevelArgs& C, const ProbArgs& 
   const unsigned grid = resident_grid((const void*)k_prolong<T>, g.total, pf.grid_cap);
   ++g_kernel_launches;
   k_prolong<T><<<grid, cta_shape(), 0, s>>>(F.N, F.rs, F.block, uf, uIf, C.N, C.rs, C.block, uc, F.tiles_int,
-                                            F.n_tiles_int, pf.act, pf.n_act, F.cptr, F.cps, pf.free_if, n,
+                                            F.n_tiles_int, pf.act, pf.n_act, F.cptr, F.cps, F.cp_off, pf.free_if, n,
                                             g.n_if_units, pf.sched);
   return cudaGetLastError();
 }
@@ -1401,7 +1500,8 @@ cudaError_t residual_to_f32(const LevelArgs& L, const ProbArgs& p, const double*
   if (n_part) *n_part = (int)grid;
   ++g_kernel_launches;
   kern<<<grid, cta_shape(), 0, s>>>(L.N, L.rs, L.block, u, uI, f, fI, f32, fI32, W, L.tiles_int, L.n_tiles_int, p.act,
-                                    p.n_act, L.cptr, L.cps, p.free_if, n, g.n_if_units, partial, p.sched);
+                                    p.n_act, L.cptr, L.cps, p.free_if, n, if_tab<double>(p, 0), g.n_if_units, partial,
+                                    p.sched);
   return cudaGetLastError();
 }
 
@@ -1413,7 +1513,7 @@ cudaError_t add_correction(const LevelArgs& L, const ProbArgs& p, double* u, dou
   const unsigned grid = resident_grid((const void*)k_add_corr, g.total, p.grid_cap);
   ++g_kernel_launches;
   k_add_corr<<<grid, cta_shape(), 0, s>>>(L.N, L.rs, L.block, u, uI, e, eI, L.tiles_int, L.n_tiles_int, p.act,
-                                          p.n_act, L.cptr, L.cps, p.free_if, n, g.n_if_units, p.sched);
+                                          p.n_act, L.cptr, L.cps, L.cp_off, p.free_if, n, g.n_if_units, p.sched);
   return cudaGetLastError();
 }
 
@@ -1438,7 +1538,7 @@ cudaError_t zero_problem_blocks(const LevelArgs& L, const ProbArgs& p, T* u, T* 
                                     const T*, int, bool, cudaStream_t, cudaEvent_t, cudaEvent_t, const T*,      \
                                     const T*);                                                                  \
   template cudaError_t residual<T>(const LevelArgs&, const ProbArgs&, const T*, const T*, const T*, const T*, T*, \
-                                   const T*, bool, bool, double*, int*, cudaStream_t);                         \
+                                   const T*, bool, bool, double*, int*, cudaStream_t, int);                    \
   template cudaError_t restrict_to<T>(const LevelArgs&, const LevelArgs&, const ProbArgs&, const T*, T*, T*, T*, \
                                       T*, cudaStream_t);                                                       \
   template cudaError_t prolong_add<T>(const LevelArgs&, const LevelArgs&, const ProbArgs&, T*, T*, const T*,     \

@@ -541,6 +541,78 @@ void assemble_coarse(const HostMesh& m, HostProblem& p) {
   assemble_coarse_ids(m, p, [&](int t, int i, int j, int k) { return node_gid(m, t, N, i, j, k); });
 }
 
+bool copy_offsets(const HostMesh& m, int l, const std::vector<Copy>& copies, std::vector<uint32_t>& out) {
+  const HostLevel& L = m.lv[l];
+  out.clear();
+  if ((uint64_t)m.n_macro * (uint64_t)L.block > 0xffffffffull) return false;
+  out.reserve(copies.size());
+  for (const Copy& cp : copies)
+    out.push_back((uint32_t)((int64_t)cp.macro * L.block + lidx(L.SL.data(), L.N, cp.i, cp.j, cp.k)));
+  return true;
+}
+
+bool build_if_tables(const HostMesh& m, int l, const std::vector<int>& free_if, const std::vector<int>& cptr,
+                     const std::vector<Copy>& copies, int K, std::vector<uint32_t>& nb, std::vector<double>& w,
+                     std::vector<double>& diag) {
+  nb.clear();
+  w.clear();
+  diag.clear();
+  const HostLevel& L = m.lv[l];
+  const int N = L.N;
+  const size_t n = free_if.size();
+  if (m.general || (uint64_t)m.n_macro * (uint64_t)L.block > 0xffffffffull) return false;
+  nb.assign((size_t)K * n, 0);
+  w.assign((size_t)K * n, 0.0);
+  diag.assign(n, 0.0);
+  struct Ent {
+    int64_t gid;
+    double w;
+    uint32_t off;
+  };
+  std::vector<Ent> ent;
+  for (size_t q = 0; q < n; ++q) {
+    const int node = free_if[q];
+    ent.clear();
+    double dg = 0.0;
+    uint32_t self = 0;
+    for (int c = cptr[node]; c < cptr[node + 1]; ++c) {
+      const Copy& cp = copies[c];
+      const double* wm = &L.W[((size_t)cp.macro * 16 + node_class(cp.i, cp.j, cp.k, N)) * NDIR];
+      if (c == cptr[node]) self = (uint32_t)((int64_t)cp.macro * L.block + lidx(L.SL.data(), N, cp.i, cp.j, cp.k));
+      dg += wm[0];
+      for (int d = 1; d < NDIR; ++d) {
+        if (wm[d] == 0.0) continue;
+        int di, dj, dk;
+        dir_ijk(d, di, dj, dk);
+        const int ni = cp.i + di, nj = cp.j + dj, nk = cp.k + dk;
+        if (!in_lattice(ni, nj, nk, N)) continue;
+        const int64_t g = node_gid(m, cp.macro, N, ni, nj, nk);
+        bool found = false;
+        for (Ent& e : ent)
+          if (e.gid == g) {
+            e.w += wm[d];
+            found = true;
+            break;
+          }
+        if (!found)
+          ent.push_back(Ent{g, wm[d], (uint32_t)((int64_t)cp.macro * L.block + lidx(L.SL.data(), N, ni, nj, nk))});
+      }
+    }
+    if ((int)ent.size() > K) {
+      nb.clear();
+      w.clear();
+      diag.clear();
+      return false;
+    }
+    diag[q] = dg;
+    for (int e = 0; e < K; ++e) {
+      nb[(size_t)e * n + q] = e < (int)ent.size() ? ent[e].off : self;
+      w[(size_t)e * n + q] = e < (int)ent.size() ? ent[e].w : 0.0;
+    }
+  }
+  return true;
+}
+
 void build_problem(const HostMesh& m, int kind, const std::vector<unsigned char>& faulty, HostProblem& p) {
   p = HostProblem();
   p.kind = kind;

@@ -10,8 +10,13 @@
 // from dir/vpos.bin ((sx+1)(sy+1)(sz+1) x 3 doubles, x fastest).
 // dir holds coeff.bin (n_macro doubles), in_<l>.bin (level-l grid vectors) and
 // r_<kind>_<l>.bin (fine residual of problem kind on level l); the program
-// writes Ag_<l>.bin, rc_<kind>_<l>.bin (pairs grid id, value) and
-// csr_<kind>.bin (n, then per row: grid id, nnz, (column grid id, value)...).
+// writes Ag_<l>.bin, rc_<kind>_<l>.bin (pairs grid id, value),
+// csr_<kind>.bin (n, then per row: grid id, nnz, (column grid id, value)...)
+// and, where the interface stencil tables exist, At_<kind>_<l>.bin (pairs
+// grid id, (A in_l) at the problem's free interface nodes through the tables:
+// diagonal times the node's value plus the summed weights times the values
+// at the tables' block offsets).  Exit code 4: a copy offset differs from
+// the one computed from (macro, i, j, k).
 #include <cstdio>
 #include <cstdlib>
 #include <string>
@@ -166,6 +171,36 @@ int main(int argc, char** argv) {
       }
     }
     writev(dir + "/csr_" + std::to_string(kind) + ".bin", dump);
+    // interface stencil tables (levels above the coarsest) applied to in_l
+    for (size_t l = 1; l < m.lv.size(); ++l) {
+      const HostLevel& L = m.lv[l];
+      const HostProblemLevel& P = p.lv[l];
+      const std::vector<int>& cptr = kind == 3 ? P.cptr : L.if_cptr;
+      const std::vector<Copy>& copies = kind == 3 ? P.copies : L.if_copy;
+      std::vector<uint32_t> off;
+      if (copy_offsets(m, (int)l, copies, off))
+        for (size_t c = 0; c < copies.size(); ++c)
+          if (off[c] != (uint32_t)((int64_t)copies[c].macro * L.block +
+                                   lidx(L.SL.data(), L.N, copies[c].i, copies[c].j, copies[c].k)))
+            return 4;
+      const int K = m.seven_point ? 6 : 14;
+      std::vector<uint32_t> nb;
+      std::vector<double> w, dg;
+      if (!build_if_tables(m, (int)l, P.free_if, cptr, copies, K, nb, w, dg)) continue;
+      const size_t nn = (size_t)(m.sub[0] * L.N + 1) * (m.sub[1] * L.N + 1) * (m.sub[2] * L.N + 1);
+      const std::vector<double> g = readv(dir + "/in_" + std::to_string(l) + ".bin", nn);
+      const std::vector<double> blk = to_blocks(m, L, g);
+      const size_t n = P.free_if.size();
+      std::vector<double> res;
+      for (size_t q = 0; q < n; ++q) {
+        const int node = P.free_if[q];
+        double a = dg[q] * g[L.if_gid[node]];
+        for (int e = 0; e < K; ++e) a += w[(size_t)e * n + q] * blk[nb[(size_t)e * n + q]];
+        res.push_back((double)L.if_gid[node]);
+        res.push_back(a);
+      }
+      writev(dir + "/At_" + std::to_string(kind) + "_" + std::to_string(l) + ".bin", res);
+    }
   }
   return 0;
 }

@@ -106,3 +106,15 @@ def test_mesh_builder_matches_oracle(check_prog, tmp_path, sub, R, geometry, fau
                 pos += 2
             assert np.abs(mine - ref).max() <= 1e-13 * np.abs(ref).max()
         assert sorted(rows) == sorted(np.nonzero(free)[0].tolist())
+        # interface stencil tables (summed weights per distinct neighbour) =
+        # the level's operator (A_I for the Neumann side) at the free
+        # interface nodes; every level above the coarsest has them
+        opm = hm if kind == 3 else m
+        for l in range(1, len(m.levels)):
+            fn = tmp_path / f"At_{kind}_{l}.bin"
+            assert fn.exists(), fn
+            d = np.fromfile(fn).reshape(-1, 2)
+            ref = O.apply_A(opm.levels[l], O.pad(ins[l])).ravel()
+            g = d[:, 0].astype(np.int64)
+            assert len(g) == len(np.unique(g))
+            assert np.abs(ref[g] - d[:, 1]).max(initial=0.0) <= 1e-13 * np.abs(ref).max()
