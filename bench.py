@@ -16,9 +16,17 @@ fault injection, interface restore, local and healthy-side recovery cycles,
 recoupling).  value = fine-grid DoF x global V-cycles / second.  Inputs are
 resident in HBM before the timed region and larger than L2.
 
---impl reference runs the CPU oracle (FP64 numpy) on the host cores on a
-bounded sample of the same workload: one V-cycle of the same cube refined 7
-times per step.
+--impl reference runs the CPU oracle (FP64 numpy) on all host cores, one
+worker process per core, on a bounded sample of the same workload: each step
+one V-cycle in every worker, each on its own copy of the same cube refined 6
+times.
+
+The default line also carries, under "variants", the other forms of the
+same workload (fault-free, do-nothing, LR, DN, mixed precision), the eta the
+concurrent recoveries achieve, a per-phase breakdown of the cycles, and three
+separate workloads: the cube refined 9 levels in FP64 and in mixed precision
+(time to 1e-8 with a fault), the batched recovery of 64 sub-domains next to a
+global solve, and a forward + adjoint solve of 384 macros refined 7 levels.
 """
 
 from __future__ import annotations
@@ -174,6 +182,85 @@ def cpu_oracle_sample(steps=1):
     return dof, times
 
 
+def cpu_info():
+    """Host cores and CPU model (lscpu), for the CPU baseline's record."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                if line.startswith("Model name"):
+                    break
+    except Exception:
+        pass
+    return os.cpu_count() or 1, model
+
+
+# --- the oracle on all host cores: one worker process per core, each with its
+# own copy of the problem (cube refined R_POOL times), timing V-cycles
+R_POOL = 6
+_POOL_STATE = {}
+
+
+def _pool_init(r):
+    import numpy as np
+    import hhg_inputs as I
+    import oracle as O
+    m = O.Mesh(SUB, r)
+    _POOL_STATE.update(m=m, O=O, f=O.pad(I.random_load(SUB, r, SEED)), u=O.pad(np.zeros(m.fine.shape)),
+                       dof=(2 ** (r + 1) - 1) ** 3)
+
+
+def _pool_cycle(_):
+    st = _POOL_STATE
+    t = time.perf_counter()
+    st["O"].vcycle(st["m"], st["m"].global_problem, len(st["m"].levels) - 1, st["u"], st["f"])
+    return st["dof"], time.perf_counter() - t
+
+
+class OraclePool:
+    """`procs` spawned workers (spawn: the parent may hold a CUDA context);
+    round() runs one V-cycle in every worker at once and returns the DoF
+    processed and the wall time."""
+
+    def __init__(self, procs, r=R_POOL):
+        import multiprocessing as mp
+        self.procs, self.r = procs, r
+        self.pool = mp.get_context("spawn").Pool(procs, initializer=_pool_init, initargs=(r,))
+        self.round()   # every worker has built its mesh
+
+    def round(self):
+        t = time.perf_counter()
+        res = self.pool.map(_pool_cycle, range(self.procs), chunksize=1)
+        return sum(d for d, _ in res), time.perf_counter() - t
+
+    def close(self):
+        self.pool.close()
+        self.pool.join()
+
+
+def cpu_baseline_record(rounds=3):
+    """The oracle on one core (one V-cycle of the cube refined R_CPU times)
+    and on all host cores (R_POOL, one worker per core, `rounds` V-cycles in
+    every worker), with the core count and model."""
+    cores, model = cpu_info()
+    cdof, ctimes = cpu_oracle_sample(1)
+    pool = OraclePool(cores)
+    dofs, walls = zip(*[pool.round() for _ in range(rounds)])
+    pool.close()
+    allcore = sum(dofs) / sum(walls)
+    return {"value": allcore, "unit": UNIT, "cores": cores, "kind": "oracle", "cpu_model": model,
+            "sample": (f"{rounds} rounds of one V-cycle in each of {cores} worker processes (one per host core), "
+                       f"each on its own copy of the cube refined {R_POOL} levels "
+                       f"({(2 ** (R_POOL + 1) - 1) ** 3} DoF), FP64 numpy; value = DoF x V-cycles of all "
+                       f"workers / wall time.  Per-DoF cost of the oracle's V-cycle is linear in the DoF, so "
+                       f"the rate stands for the benchmark's refinement-8 cube as well"),
+            "single_thread": {"value": cdof / ctimes[0], "unit": UNIT, "cores": 1,
+                              "sample": f"1 V-cycle on the cube refined {R_CPU} levels ({cdof} DoF), "
+                                        f"{ctimes[0]:.1f} s"}}
+
+
 def max_over_ranks(x, dist=None, device=None):
     """The largest of the ranks' x (the job's time is its slowest replica's);
     x itself when there is no process group."""
@@ -199,24 +286,43 @@ def _dist():
 
 
 def run_reference(args):
+    """The CPU oracle as it stands on all host cores: one worker process per
+    core, each step one V-cycle in every worker (cube refined R_POOL levels,
+    its own copy of the problem per worker)."""
     rank, world, _ = _dist()
     if rank != 0:
         return 0
-    import numpy as np  # noqa: F401
-    dof, times = cpu_oracle_sample(args.warmup + args.steps)
-    timed = times[args.warmup:]
-    t = sum(timed)
-    value = dof * len(timed) / t
-    sample = (f"{len(timed)} V-cycles (one per step) of the CPU oracle on the same cube refined {R_CPU} levels "
-              f"({dof} DoF), FP64 numpy, single thread")
+    cores, model = cpu_info()
+    pool = OraclePool(cores)
+    for _ in range(args.warmup):
+        pool.round()
+    dofs, walls = zip(*[pool.round() for _ in range(args.steps)])
+    pool.close()
+    t = sum(walls)
+    value = sum(dofs) / t
+    sample = (f"{args.steps} steps, each one V-cycle in each of {cores} worker processes (one per host core) on "
+              f"its own copy of the same cube refined {R_POOL} levels ({(2 ** (R_POOL + 1) - 1) ** 3} DoF), "
+              f"FP64 numpy")
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1e3 * t / len(timed), "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / len(walls), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": {"workload": WORKLOAD, "sample": sample, "parallelism": "none (host)"},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "config": {"workload": WORKLOAD, "sample": sample, "parallelism": f"{cores} host processes"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample,
+                             "cpu_model": model},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def _events_ms(torch, stream, fn):
+    """Device time of fn() on `stream` (CUDA events, synchronised)."""
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    out = fn()
+    b.record(stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b), out
 
 
 def run_ours(args):
@@ -235,6 +341,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     build()
     dev = torch.device("cuda", local)
+    fp64_peak = hhg.hhg_measure_fp64_peak()
     M = hhg.Mesh(SUB, R, precision=32)
     fault = I.subcube_macros(SUB, 0, 0, 0)
     f_np = I.random_load(SUB, R, SEED)
@@ -262,7 +369,7 @@ def run_ours(args):
     visible = os.environ.get("CUDA_VISIBLE_DEVICES")
     sampler = ClockSampler(visible.split(",")[local] if visible else local)
     sampler.start()
-    hhg.hhg_profile_enable(M.h, True)
+    hhg.hhg_profile_enable(M.h, 1)
     l0 = hhg.hhg_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -274,7 +381,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     l1 = hhg.hhg_launch_count()
     n_prof, prof_ms = hhg.hhg_profile_read(M.h)
-    hhg.hhg_profile_enable(M.h, False)
+    hhg.hhg_profile_enable(M.h, 0)
     clocks = sampler.stop()
     ms = max_over_ranks(e0.elapsed_time(e1), dist, dev)
     if dist:
@@ -282,7 +389,8 @@ def run_ours(args):
     dof = M.n_dof
     value = job_value(world, dof, sum(cyc_list), ms * 1e-3)
 
-    # dominant kernel: finest-level FP64 Gauss-Seidel volume kernel (one colour per launch)
+    # dominant kernel: finest-level FP64 Gauss-Seidel (one colour per launch,
+    # volume and interface nodes)
     n_vol, seven = hhg.hhg_profile_info(M.h)
     avg_s = prof_ms / max(n_prof, 1) * 1e-3
     # 7-point: f and the weights come divided by the centre weight, one DFMA
@@ -292,11 +400,13 @@ def run_ours(args):
     achieved_tflops = flops / avg_s / 1e12
     hbm_peak, hbm_src = _peaks()
     alg_bytes = 24.0 * n_vol / 4.0        # read u, read f, write u per node update
-    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved_tflops / FP64_PEAK_TFLOPS, "traffic": _traffic("gs_vol_f64"),
-                "kernel": "k_gs_vol<double> finest level, one colour", "launches": n_prof,
+    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved_tflops / fp64_peak, "traffic": _traffic("gs_vol_f64"),
+                "kernel": "k_gs<double, 7-point> finest level, one colour", "launches": n_prof,
                 "avg_launch_ms": avg_s * 1e3,
-                "peak_source": "derived: 152 SMs x 2 DFMA/clk x 2 flop x 2.07 GHz (FP64)",
+                "peak_source": "measured in this run: FP64 FMA probe (hhg_measure_fp64_peak, 8 x 256-thread "
+                               "CTAs per SM, 8 independent FMA chains per thread)",
+                "peak_derived": FP64_PEAK_TFLOPS,
                 "hbm_achieved_gbs": alg_bytes / avg_s / 1e9, "hbm_peak_gbs": hbm_peak,
                 "hbm_frac": alg_bytes / avg_s / 1e9 / hbm_peak, "hbm_peak_source": hbm_src}
 
@@ -322,52 +432,24 @@ def run_ours(args):
            "d2h_bytes_per_step": nbytes, "ms_per_step": 1e3 * t_e2e / k_e2e}
     M.set_problem(f_dev, None)
 
-    # variants on the same GPU: fault-free, do-nothing, LR, DN, and mixed precision
     variants = {}
     if not args.quick:
-        def timed(**over):
-            torch.cuda.synchronize()
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            h, c = step(**over)
-            b.record(stream)
-            torch.cuda.synchronize()
-            return a.elapsed_time(b), h, c
-        ms_free, h_free, c_free = timed(fault_cycle=0)
-        ms_dn, h_dn, c_dn = timed(recovery=hhg.HHG_RECOVERY_NONE)
-        ms_lr, h_lr, c_lr = timed(recovery=hhg.HHG_RECOVERY_LR, n_local=3)
-        ms_dd, h_dd, c_dd = timed()
-        step(recovery=hhg.HHG_RECOVERY_DN)   # builds the Neumann-side problem once
-        ms_dnr, h_dnr, c_dnr = timed(recovery=hhg.HHG_RECOVERY_DN)
-        u_fp64 = torch.zeros_like(f_dev)
-        M.get_solution(u_fp64)
-        hhg.hhg_profile_enable(M.h, True)
-        ms_mx, h_mx, c_mx = timed(mixed_precision=True)
-        n32, ms32 = hhg.hhg_profile_read(M.h)
-        hhg.hhg_profile_enable(M.h, False)
-        avg32 = ms32 / max(n32, 1) * 1e-3
-        gs32 = {"kernel": "k_gs<float> finest level, one colour (inner FP32 cycles)", "launches": n32,
-                "avg_launch_ms": avg32 * 1e3, "bound": "hbm",
-                "achieved_gbs": 12.0 * n_vol / 4.0 / avg32 / 1e9, "peak_gbs": hbm_peak,
-                "frac": 12.0 * n_vol / 4.0 / avg32 / 1e9 / hbm_peak,
-                "bytes_per_node_update": "12 (read u, f; write u, FP32)"}
-        u_mx = torch.zeros_like(f_dev)
-        M.get_solution(u_mx)
-        ms_mx_free, h_mx_free, c_mx_free = timed(mixed_precision=True, fault_cycle=0)
-        diff = float((u_mx - u_fp64).abs().max().item())
-        scale = float(u_fp64.abs().max().item())
-        kappa = lambda kf, n_extra=0: (kf + n_extra - c_free) / FAULT_CYCLE
-        variants = {
-            "fault_free_fp64": {"ms": ms_free, "cycles": c_free, "final_rel_res": float(h_free[-1])},
-            "do_nothing_fp64": {"ms": ms_dn, "cycles": c_dn, "kappa": kappa(c_dn)},
-            "local_recovery_fp64_nF3": {"ms": ms_lr, "cycles": c_lr, "kappa": kappa(c_lr)},
-            "dd_fp64_eta4_nI3": {"ms": ms_dd, "cycles": c_dd, "kappa": kappa(c_dd, N_I)},
-            "dn_fp64_eta4_nI3": {"ms": ms_dnr, "cycles": c_dnr, "kappa": kappa(c_dnr, N_I)},
-            "dd_mixed_fp32_in_fp64_ir": {"ms": ms_mx, "cycles": c_mx, "final_rel_res": float(h_mx[-1]),
-                                         "max_abs_diff_vs_fp64_solution": diff, "fp64_solution_max": scale,
-                                         "gs_fp32_roofline": gs32},
-            "fault_free_mixed": {"ms": ms_mx_free, "cycles": c_mx_free},
-        }
+        variants = bench_variants(torch, hhg, M, step, stream, f_dev, u0_dev, fault, n_vol, hbm_peak)
+    if rank == 0 and world == 1 and not args.quick and not args.no_extras:
+        M.close()
+        del f_dev, u0_dev, f_pin, u0_pin, u_pin
+        torch.cuda.empty_cache()
+        for name, fn in (("precision_r9", extra_precision_r9), ("batch", extra_batch),
+                         ("differentiation", extra_grad)):
+            t = time.perf_counter()
+            try:
+                variants[name] = fn(torch, hhg, I)
+            except Exception as exc:      # reported, not hidden
+                variants[name] = {"error": f"{type(exc).__name__}: {exc}"}
+            variants[name]["wall_s"] = time.perf_counter() - t
+            torch.cuda.empty_cache()
+    else:
+        M.close()
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -378,11 +460,7 @@ def run_ours(args):
             "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": l1 - l0,
             "final_rel_residual": float(hist[-1]), "variants": variants}
     if rank == 0 and world == 1 and not args.no_cpu:
-        cdof, ctimes = cpu_oracle_sample(1)
-        line["cpu_baseline"] = {"value": cdof / ctimes[0], "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": f"1 V-cycle of the CPU oracle (FP64 numpy, one thread) on the same cube "
-                                          f"refined {R_CPU} levels ({cdof} DoF), {ctimes[0]:.1f} s"}
-    M.close()
+        line["cpu_baseline"] = cpu_baseline_record()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:
@@ -390,20 +468,121 @@ def run_ours(args):
     return 0
 
 
-def run_batch(args):
-    """Batched recovery workload: one global mixed-precision solve on 4x4x4x6
-    macros refined 7 levels plus 64 recovery problems of uneven size (1..27
-    macros grown from seeded seeds, refinement 5..7, seed 3), FP32 cycles in
-    FP64 refinement, all in one CUDA-graph launch."""
+def bench_variants(torch, hhg, M, step, stream, f_dev, u0_dev, fault, n_vol, hbm_peak):
+    """The same workload's other forms on the same GPU (one solve each, CUDA
+    events): fault-free, do-nothing, LR, DD, DN, mixed precision; the eta the
+    concurrent recoveries achieve; and the per-phase breakdown of the cycles."""
+    def timed(**over):
+        return _events_ms(torch, stream, lambda: step(**over))
+
+    ms_free, (h_free, c_free) = timed(fault_cycle=0)
+    ms_dn, (h_dn, c_dn) = timed(recovery=hhg.HHG_RECOVERY_NONE)
+    ms_lr, (h_lr, c_lr) = timed(recovery=hhg.HHG_RECOVERY_LR, n_local=3)
+    ms_dd, (h_dd, c_dd) = timed()
+    step(recovery=hhg.HHG_RECOVERY_DN)   # builds the Neumann-side problem once
+    ms_dnr, (h_dnr, c_dnr) = timed(recovery=hhg.HHG_RECOVERY_DN)
+    u_fp64 = torch.zeros_like(f_dev)
+    M.get_solution(u_fp64)
+    hhg.hhg_profile_enable(M.h, 1)
+    ms_mx, (h_mx, c_mx) = timed(mixed_precision=True)
+    n32, ms32 = hhg.hhg_profile_read(M.h)
+    hhg.hhg_profile_enable(M.h, 0)
+    avg32 = ms32 / max(n32, 1) * 1e-3
+    gs32 = {"kernel": "k_gs<float, 7-point> finest level, one colour (inner FP32 cycles)", "launches": n32,
+            "avg_launch_ms": avg32 * 1e3, "bound": "hbm",
+            "achieved_gbs": 12.0 * n_vol / 4.0 / avg32 / 1e9, "peak_gbs": hbm_peak,
+            "frac": 12.0 * n_vol / 4.0 / avg32 / 1e9 / hbm_peak,
+            "bytes_per_node_update": "12 (read u, f; write u, FP32)"}
+    u_mx = torch.zeros_like(f_dev)
+    M.get_solution(u_mx)
+    ms_mx_free, (h_mx_free, c_mx_free) = timed(mixed_precision=True, fault_cycle=0)
+    diff = float((u_mx - u_fp64).abs().max().item())
+    scale = float(u_fp64.abs().max().item())
+    kappa = lambda kf, n_extra=0: (kf + n_extra - c_free) / FAULT_CYCLE
+    out = {
+        "fault_free_fp64": {"ms": ms_free, "cycles": c_free, "final_rel_res": float(h_free[-1])},
+        "do_nothing_fp64": {"ms": ms_dn, "cycles": c_dn, "kappa": kappa(c_dn)},
+        "local_recovery_fp64_nF3": {"ms": ms_lr, "cycles": c_lr, "kappa": kappa(c_lr)},
+        "dd_fp64_eta4_nI3": {"ms": ms_dd, "cycles": c_dd, "kappa": kappa(c_dd, N_I)},
+        "dn_fp64_eta4_nI3": {"ms": ms_dnr, "cycles": c_dnr, "kappa": kappa(c_dnr, N_I)},
+        "dd_mixed_fp32_in_fp64_ir": {"ms": ms_mx, "cycles": c_mx, "final_rel_res": float(h_mx[-1]),
+                                     "max_abs_diff_vs_fp64_solution": diff, "fp64_solution_max": scale,
+                                     "gs_fp32_roofline": gs32},
+        "fault_free_mixed": {"ms": ms_mx_free, "cycles": c_mx_free},
+    }
+    # eta achieved: the two sides of DD (12 local cycles on Omega_F, 3 on
+    # Omega_I, concurrent streams) and DN, timed on the device after the fault
+    n_f = int(math.ceil(ETA * N_I))
+    eta = {}
+    for name in ("dd", "dn"):
+        M.set_problem(None, u0_dev)
+        M.solve(rtol=1e-30, max_cycles=FAULT_CYCLE, allow_not_converged=True)
+        M.inject_fault(fault)
+        if name == "dd":
+            tl, tg = M.recover_local(fault, n_f, N_I, timed=True)
+            nf_run = n_f
+        else:
+            nf_run, tl, tg = M.recover_dn(fault, N_I, ETA, timed=True)
+        eta[name] = {"omega_f_cycles": nf_run, "omega_f_s": tl, "omega_i_cycles": N_I, "omega_i_s": tg,
+                     "eta_target": ETA, "eta_achieved": (nf_run / tl) / (N_I / tg)}
+    out["eta_achieved"] = eta
+    # per-phase breakdown of one fault-free solve in each precision
+    bd = {}
+    for name, mixed in (("fp64", False), ("mixed", True)):
+        hhg.hhg_profile_enable(M.h, 2)
+        M.set_problem(None, u0_dev)
+        _, c = M.solve(rtol=RTOL, max_cycles=MAX_CYCLES, mixed_precision=mixed)[:2]
+        parts = hhg.hhg_profile_breakdown(M.h)
+        hhg.hhg_profile_enable(M.h, 0)
+        bd[name] = {"cycles": c, "ms_per_cycle": {k: v / c for k, v in parts.items()},
+                    "ms_per_cycle_total": sum(parts.values()) / c}
+    out["cycle_breakdown_fault_free"] = bd
+    return out
+
+
+def extra_precision_r9(torch, hhg, I):
+    """FP64 against FP32-in-FP64 refinement on the cube refined 9 levels
+    (1.07e9 DoF): fault after cycle 4 on sub-cube (0,0,0), DD recovery
+    (eta = 4, n_I = 3), time to 1e-8 (one warm-up and one timed solve each)
+    and the two solutions' difference."""
+    r = 9
+    t0 = time.perf_counter()
+    M = hhg.Mesh(SUB, r, precision=32)
+    setup_s = time.perf_counter() - t0
+    f = torch.from_numpy(I.random_load(SUB, r, SEED)).cuda()
+    u0 = torch.zeros_like(f)
+    M.set_problem(f, u0)
+    kw = dict(rtol=RTOL, max_cycles=MAX_CYCLES, fault_cycle=4, fault_ids=I.subcube_macros(SUB),
+              recovery=hhg.HHG_RECOVERY_DD, n_global=N_I, eta=ETA)
+    out, sols = {}, {}
+    stream = torch.cuda.current_stream()
+    for name, mixed in (("fp64", False), ("mixed_fp32_in_fp64_ir", True)):
+        for it in range(2):
+            M.set_problem(None, u0)
+            ms, (hist, cyc, _) = _events_ms(torch, stream, lambda: M.solve(mixed_precision=mixed, **kw))
+        u = torch.zeros_like(f)
+        M.get_solution(u)
+        sols[name] = u
+        out[name] = {"ms": ms, "cycles": cyc, "final_rel_res": float(hist[-1])}
+    d = sols["mixed_fp32_in_fp64_ir"] - sols["fp64"]
+    res = {"workload": "cube 2x2x2x6 macro-tets refined 9 levels, random load seed 0, fault after cycle 4 erases "
+                       "sub-cube (0,0,0), DD eta=4 n_I=3, rtol 1e-8",
+           "dof": M.n_dof, "mesh_setup_s": setup_s, "device_bytes": M.bytes(), "forms": out,
+           "speedup_mixed": out["fp64"]["ms"] / out["mixed_fp32_in_fp64_ir"]["ms"],
+           "rel_l2_diff_mixed_vs_fp64": float(d.norm() / sols["fp64"].norm()),
+           "max_abs_diff_mixed_vs_fp64": float(d.abs().max()),
+           "max_abs_fp64_solution": float(sols["fp64"].abs().max())}
+    M.close()
+    return res
+
+
+def batch_workload(torch, hhg, I, warmup, steps):
+    """Batched recovery: one global mixed-precision solve on 4x4x4x6 macros
+    refined 7 levels plus 64 recovery problems of uneven size (1..27 macros
+    grown from seeded seeds, refinement 5..7, seed 3), FP32 cycles in FP64
+    refinement, all in one CUDA-graph launch; and the plain FP64 form of the
+    same work, one call after the other."""
     import numpy as np
-    import torch
-
-    import hhg_inputs as I
-    from paper_1506_06185_gb300 import build
-    from paper_1506_06185_gb300 import hhg
-
-    build()
-    torch.cuda.set_device(0)
     gsub, gR = (4, 4, 4), 7
     G = hhg.Mesh(gsub, gR, precision=32)
     gf = torch.from_numpy(I.random_load(gsub, gR, SEED)).cuda()
@@ -424,20 +603,17 @@ def run_batch(args):
     setup_s = time.perf_counter() - t0
     G.set_problem(None, gu0)
     batch = hhg.Batch(tasks, G, g_cycles, mixed=True)
-    runs = []
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         batch.launch()
-    for _ in range(args.steps):
+    runs = []
+    for _ in range(steps):
         G.set_problem(None, gu0)
         torch.cuda.synchronize()
         runs.append(batch.launch())
     ms = np.array(runs)
     lat = ms[:, :-1].ravel()
-    total = ms[:, -1].max(axis=0) if ms.ndim == 1 else ms.max(axis=1)
+    total = ms.max(axis=1)
 
-    # the plain FP64 form of the same work, one call after the other on one
-    # stream: the global FP64 solve to 1e-8, then every recovery (fault
-    # injection + 4 local FP64 cycles)
     def plain():
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -451,19 +627,83 @@ def run_batch(args):
         torch.cuda.synchronize()
         return a.elapsed_time(b), c
     plain()
-    plain_runs = [plain() for _ in range(max(1, min(args.steps, 3)))]
-    plain_ms = float(np.median([r[0] for r in plain_runs]))
-    line = {"metric": "batched recovery: total time to 1e-8 (global) and per-problem latency", "impl": "ours",
-            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "f32-in-f64-ir", "data": "synthetic",
-            "config": {"workload": "global 4x4x4x6 macros refined 7 levels (1.33e8 DoF) to 1e-8 + 64 recovery "
-                                   "problems (1..27 macros, refinement 5..7, 4 local FP32-IR cycles each), one "
-                                   "CUDA-graph launch", "global_cycles": g_cycles,
-                       "task_dof": [int(t[0].n_dof) for t in tasks]},
-            "total_ms_median": float(np.median(total)), "latency_ms_p50": float(np.percentile(lat, 50)),
-            "latency_ms_p99": float(np.percentile(lat, 99)), "setup_s": setup_s,
-            "plain_fp64_sequential_ms": plain_ms, "plain_fp64_global_cycles": plain_runs[0][1]}
-    print(json.dumps(line), flush=True)
+    plain_runs = [plain() for _ in range(max(1, min(steps, 2)))]
+    res = {"workload": "global 4x4x4x6 macros refined 7 levels (1.33e8 DoF) to 1e-8 + 64 recovery problems "
+                       "(1..27 macros, refinement 5..7, 4 local FP32-IR cycles each), one CUDA-graph launch",
+           "global_cycles": g_cycles, "task_dof": [int(t[0].n_dof) for t in tasks],
+           "total_ms_median": float(np.median(total)), "latency_ms_p50": float(np.percentile(lat, 50)),
+           "latency_ms_p99": float(np.percentile(lat, 99)), "setup_s": setup_s,
+           "plain_fp64_sequential_ms": float(np.median([r[0] for r in plain_runs])),
+           "plain_fp64_global_cycles": plain_runs[0][1]}
+    res["speedup_vs_plain_fp64"] = res["plain_fp64_sequential_ms"] / res["total_ms_median"]
     batch.close()
+    for M, _, _ in tasks:
+        M.close()
+    G.close()
+    return res
+
+
+def extra_batch(torch, hhg, I):
+    return batch_workload(torch, hhg, I, warmup=1, steps=3)
+
+
+def extra_grad(torch, hhg, I):
+    """Differentiation at scale: 4x4x4 sub-cubes x 6 = 384 macros refined 7
+    levels (1.33e8 DoF), per-macro k ~ lognormal(0, 1) (seed 1), FP64 forward
+    and adjoint solves to 1e-10, loss 1/2 ||u - u_target||^2 (smooth target):
+    device time of one forward + backward (one warm-up first), and of the
+    coefficient set-up inside it."""
+    from paper_1506_06185_gb300 import autograd as AG
+    sub, r = (4, 4, 4), 7
+    k0 = I.lognormal_coeff(384, seed=1)
+    t0 = time.perf_counter()
+    M = hhg.Mesh(sub, r, coeff=k0)
+    setup_s = time.perf_counter() - t0
+    f = torch.from_numpy(I.random_load(sub, r, SEED)).cuda()
+    ut = torch.from_numpy(I.smooth_target(sub, r)).cuda()
+    mask = torch.from_numpy(I.boundary_mask(sub, r)).cuda()
+    opts = dict(rtol=1e-10, max_cycles=60)
+
+    def fwd_bwd():
+        ft = f.clone().requires_grad_(True)
+        kt = torch.from_numpy(k0.copy()).cuda().requires_grad_(True)
+        u = AG.solve(M, ft, kt, **opts)
+        loss = 0.5 * ((u - ut)[~mask] ** 2).sum()
+        loss.backward()
+        return float(loss), kt.grad, ft.grad
+    fwd_bwd()
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    loss, gk, gf = fwd_bwd()
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t
+    t = time.perf_counter()
+    M.set_coefficients(k0)
+    coeff_s = time.perf_counter() - t
+    res = {"workload": "4x4x4x6 = 384 macros refined 7 levels, k ~ lognormal(0,1) seed 1, forward and adjoint "
+                       "FP64 solves to 1e-10, loss 1/2||u - u_target||^2",
+           "dof": M.n_dof, "mesh_setup_s": setup_s, "forward_backward_s": wall,
+           "set_coefficients_s": coeff_s, "loss": loss, "grad_k_norm": float(gk.norm()),
+           "grad_f_norm": float(gf.norm())}
+    M.close()
+    return res
+
+
+def run_batch(args):
+    """The batched-recovery workload alone (batch_workload)."""
+    import torch
+
+    import hhg_inputs as I
+    from paper_1506_06185_gb300 import build
+    from paper_1506_06185_gb300 import hhg
+
+    build()
+    torch.cuda.set_device(0)
+    res = batch_workload(torch, hhg, I, args.warmup, args.steps)
+    line = {"metric": "batched recovery: total time to 1e-8 (global) and per-problem latency", "impl": "ours",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "f32-in-f64-ir", "data": "synthetic"}
+    line.update(res)
+    print(json.dumps(line), flush=True)
     return 0
 
 
@@ -613,6 +853,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="skip the variant timings")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the refined-9 precision, batched-recovery and differentiation workloads")
     ap.add_argument("--batch", action="store_true", help="run the batched-recovery workload instead")
     ap.add_argument("--profile-case", action="store_true",
                     help="two cycles of the cube refined --levels times (for kernel captures)")

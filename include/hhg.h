@@ -53,7 +53,8 @@ enum {
   HHG_ERR_ARG = 1,            /* invalid argument (sizes, ids, null pointer) */
   HHG_ERR_CUDA = 2,           /* a CUDA runtime call failed */
   HHG_ERR_OOM = 3,            /* device or host allocation failed */
-  HHG_ERR_TIMEOUT = 4,        /* a bounded device-side wait ran out */
+  HHG_ERR_TIMEOUT = 4,        /* a bounded device-side wait ran out
+                                 (hhg_set_wait_limit) */
   HHG_ERR_NOT_CONVERGED = 5,  /* hhg_solve stopped at max_cycles above rtol */
   HHG_ERR_STATE = 6           /* call not valid in the mesh's current state */
 };
@@ -323,10 +324,20 @@ int hhg_batch_destroy(hhg_batch* batch);
 int hhg_vcycle_noalloc(hhg_mesh* mesh, int pre, int post, void* stream);
 
 /* Measurement support (not part of the method).
- * hhg_profile_enable: while enabled, every launch of the dominant kernel -- the
+ * hhg_profile_enable: enable bit 0: every launch of the dominant kernel -- the
  * finest-level Gauss-Seidel volume kernel of the global problem (one colour of
  * the smoother of §2.1 on all macro interiors) -- is bracketed by CUDA events on
- * the stream it runs on.  Enabling clears the record.
+ * the stream it runs on.  Bit 1: the global cycles of hhg_solve / hhg_vcycle
+ * record an event at every phase boundary (not inside a stream capture).
+ * Enabling clears both records.
+ * hhg_profile_breakdown: synchronises the device and sums, per phase, the
+ * time from each recorded boundary to the next, into ms[0..9]: fine-level
+ * smoothing, fine residual, restriction from the fine level, prolongation to
+ * it, the levels below (smoothing, residuals, transfers), coarse CG, the
+ * stopping test (residual and norm; FP64 residual of iterative refinement),
+ * host turnaround (read-back of the norm until the next cycle's first work),
+ * fault injection and recovery, and the FP32 correction's zeroing and
+ * addition (mixed precision); n >= 10.  Clears the record.
  * hhg_profile_read: synchronises the device and returns the number of
  * recorded launches and their summed device time in milliseconds; clears the
  * record.
@@ -350,11 +361,39 @@ int hhg_vcycle_noalloc(hhg_mesh* mesh, int pre, int post, void* stream);
  * recovery (0 where a problem does not exist; counts restart when a fault set
  * replaces the sub-problems).  Synchronises the device. */
 int hhg_profile_enable(hhg_mesh* mesh, int enable);
+int hhg_profile_breakdown(hhg_mesh* mesh, double* ms, int n);
 int hhg_profile_read(hhg_mesh* mesh, int64_t* launches, double* total_ms);
 int hhg_profile_info(const hhg_mesh* mesh, int64_t* volume_nodes, int* seven_point);
 int hhg_launch_count(int64_t* count);
 int hhg_set_launch_limit(hhg_mesh* mesh, int max_ctas);
+
+/* FP64 FMA throughput of the current device in TFLOP/s (measurement support:
+ * the ALU roofline of the FP64 kernels): 8 CTAs of 256 threads per SM, each
+ * thread running 8 independent FMA chains of 16384 steps, timed with CUDA
+ * events on the legacy stream, best of three after a warm-up launch.
+ * Allocates and frees a small device buffer; synchronises. */
+int hhg_measure_fp64_peak(double* tflops);
 int hhg_walk_counts(hhg_mesh* mesh, int64_t* counts);
+
+/* Kernel options (implementation knobs, not part of the method).
+ * hhg_set_streaming: enable or disable (default) the streaming Gauss-Seidel
+ * kernel on meshes with the 7-point structure: on levels with at least 64
+ * intervals per macro edge it sweeps bands of rows slice by slice, a
+ * producer warp staging the two neighbour colours and the right-hand side of
+ * each slice in shared memory with bulk asynchronous copies on mbarriers for
+ * eight consumer warps; disabled, every level uses the row-pair tile kernel.
+ * Both give the same iterate bit for bit (the tile kernel is the faster one
+ * on GB300).  Drops the captured recovery-cycle graph.
+ * hhg_set_wait_limit: the streaming kernel's waits on its mbarriers are bounded
+ * (default tries < 0: about one second per wait).  When a wait runs out the
+ * CTA records it in the mesh's device error flag, waits (bounded) for its
+ * copies in flight and stops; the next call that reads a result back
+ * (hhg_vcycle with resid_out, hhg_residual_norm, hhg_solve) clears the flag
+ * and returns HHG_ERR_TIMEOUT, and the iterate is then incomplete (reload it
+ * with hhg_set_problem).  tries = 0 makes every wait run out at once, which
+ * exercises that path without any fault. */
+int hhg_set_streaming(hhg_mesh* mesh, int enable);
+int hhg_set_wait_limit(hhg_mesh* mesh, int tries);
 
 /* Copy the message of the calling thread's last failure into buf (always
  * NUL-terminated if len > 0).  Returns the status of that failure. */

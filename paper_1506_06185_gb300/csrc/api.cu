@@ -138,6 +138,18 @@ struct hhg_mesh {
   double* grad_out = nullptr;
   // CTAs per fused launch at most (0: as many as are resident; hhg_set_launch_limit)
   int grid_cap = 0;
+  // streaming 7-point Gauss-Seidel (hhg_set_streaming) and the bounded device
+  // waits: their error flag (device) and tries (hhg_set_wait_limit)
+  int stream_gs = 0;
+  int* dev_err = nullptr;
+  int wait_limit = 1 << 24;
+  int* host_flag = nullptr;        // pinned
+  // phase breakdown of the global cycles (hhg_profile_enable bit 1): an event
+  // at every phase boundary and the phase that starts there
+  bool bd_on = false;
+  std::vector<cudaEvent_t> bd_ev;
+  std::vector<int> bd_cat;
+  size_t bd_used = 0;
   // profiling of the finest-level Gauss-Seidel volume kernel of the global problem
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_ev;
@@ -236,6 +248,12 @@ LevelArgs largs(const hhg_mesh* m, int l) {
   a.n_tiles_int = t.n_tiles_int;
   a.tiles_all = t.tiles_all;
   a.n_tiles_all = t.n_tiles_all;
+  a.tiles_stream = t.tiles_stream;
+  a.n_tiles_stream = t.n_tiles_stream;
+  a.stream_band = H.stream_band;
+  a.tiles_stream32 = t.tiles_stream32;
+  a.n_tiles_stream32 = t.n_tiles_stream32;
+  a.stream_band32 = H.stream_band32;
   return a;
 }
 
@@ -282,6 +300,9 @@ ProbArgs pargs(const DevProblem& p, int l) {
   a.td32 = q.td32;
   a.ti32 = q.ti32;
   a.tn = q.tn;
+  a.stream_gs = p.stream_gs;
+  a.err = p.err;
+  a.wait_limit = p.wait_limit;
   return a;
 }
 
@@ -376,6 +397,9 @@ int upload_problem(hhg_mesh* m, const HostProblem& h, DevProblem& d) {
   HHG_TRY(dalloc(m, &d.sched, 4));
   HHG_CUDA(cudaMemset(d.sched, 0, 4 * sizeof(int)));
   d.grid_cap = m->grid_cap;
+  d.stream_gs = m->stream_gs;
+  d.err = m->dev_err;
+  d.wait_limit = m->wait_limit;
   return HHG_OK;
 }
 
@@ -456,6 +480,33 @@ int prof_pair(hhg_mesh* m, cudaEvent_t* b, cudaEvent_t* e) {
 }
 
 // profile = false keeps the profiling hook (which creates events) out.
+// Phases of the breakdown: fine-level smoothing, fine residual, restriction
+// from and prolongation to the fine level, the levels below (smoothing,
+// residuals, transfers), coarse CG, the stopping test's residual and norm
+// (with iterative refinement: the FP64 residual), the time until the host
+// issues the next work (read-back of the norm, launch), fault injection and
+// recovery, and the FP32 correction's zeroing and addition (mixed precision).
+enum { BD_FINE_SMOOTH, BD_FINE_RES, BD_RESTRICT, BD_PROLONG, BD_COARSE, BD_CG, BD_NORM, BD_HOST, BD_RECOVERY,
+       BD_IR, BD_N };
+
+// Start of phase `cat` on stream s (breakdown enabled, global problem only).
+int bd_mark(hhg_mesh* m, cudaStream_t s, int cat) {
+  if (!m->bd_on) return HHG_OK;
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  HHG_CUDA(cudaStreamIsCapturing(s, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return HHG_OK;
+  if (m->bd_ev.size() <= m->bd_used) {
+    cudaEvent_t ev;
+    HHG_CUDA(cudaEventCreate(&ev));
+    m->bd_ev.push_back(ev);
+    m->bd_cat.push_back(0);
+  }
+  HHG_CUDA(cudaEventRecord(m->bd_ev[m->bd_used], s));
+  m->bd_cat[m->bd_used] = cat;
+  ++m->bd_used;
+  return HHG_OK;
+}
+
 template <class T>
 int smooth(hhg_mesh* m, Prec<T>& P, DevProblem& p, int l, int steps, cudaStream_t s, bool profile = true) {
   const int L = (int)P.lv.size() - 1;
@@ -514,17 +565,22 @@ int vcycle_T(hhg_mesh* m, Prec<T>& P, DevProblem& p, int pre, int post, double c
              cudaStream_t s, const CycleOpts& co = CycleOpts()) {
   const int L = (int)P.lv.size() - 1;
   const bool s7 = m->host.seven_point;
+  const bool bd = co.profile && p.kind == 0;
+  auto mark = [&](int cat) { return bd ? bd_mark(m, s, cat) : HHG_OK; };
   for (int l = L; l >= 1; --l) {
     DevLevel<T>& D = P.lv[l];
     const LevelArgs a = plargs(m, p, l);
     const ProbArgs q = pargs(p, l);
+    HHG_TRY(mark(l == L ? BD_FINE_SMOOTH : BD_COARSE));
     HHG_TRY(smooth<T>(m, P, p, l, pre, s, co.profile));
+    if (l == L) HHG_TRY(mark(BD_FINE_RES));
     // after a smoothing step the last colour's residual vanishes (cube family:
     // colour 3 is smoothed last, interface nodes included)
     const int skip = pre > 0 && !m->host.general ? 3 : -1;
     HHG_CUDA(residual<T>(a, q, D.u, D.uI, D.f, level_fI<T>(D, p, l == L), D.r, D.W, s7, true, nullptr, nullptr, s,
                          skip));
     DevLevel<T>& C = P.lv[l - 1];
+    if (l == L) HHG_TRY(mark(BD_RESTRICT));
     if (m->host.general) {
       // volume part as usual, interface part through the variable-length gathers
       ProbArgs qc = pargs(p, l - 1);
@@ -538,12 +594,16 @@ int vcycle_T(hhg_mesh* m, Prec<T>& P, DevProblem& p, int pre, int post, double c
     }
     HHG_CUDA(restrict_to<T>(plargs(m, p, l - 1), a, pargs(p, l - 1), D.r, C.f, C.fI, C.u, C.uI, s));
   }
+  HHG_TRY(mark(BD_CG));
   HHG_CUDA(coarse_cg<T>(p, P.lv[0].f, P.lv[0].fI, P.lv[0].u, P.lv[0].uI, cg_rtol, cg_maxit, s, co.cg_work));
+  HHG_TRY(mark(BD_COARSE));
   for (int l = 1; l <= L; ++l) {
     DevLevel<T>& D = P.lv[l];
     const LevelArgs a = plargs(m, p, l);
     const ProbArgs q = pargs(p, l);
+    if (l == L) HHG_TRY(mark(BD_PROLONG));
     HHG_CUDA(prolong_add<T>(a, plargs(m, p, l - 1), q, D.u, D.uI, P.lv[l - 1].u, s));
+    if (l == L) HHG_TRY(mark(BD_FINE_SMOOTH));
     HHG_TRY(smooth<T>(m, P, p, l, post, s, co.profile));
   }
   return HHG_OK;
@@ -563,10 +623,21 @@ int norm2_async(hhg_mesh* m, DevProblem& p, cudaStream_t s, bool after_smoothing
   return HHG_OK;
 }
 
+// Reads a device scalar (synchronising s) together with the mesh's error
+// flag; a set flag (a bounded device wait ran out in an earlier kernel) is
+// cleared and reported as HHG_ERR_TIMEOUT.
 int read_scalar(hhg_mesh* m, const double* dev, double* out, cudaStream_t s) {
   HHG_CUDA(cudaMemcpyAsync(m->host_scalar, dev, sizeof(double), cudaMemcpyDeviceToHost, s));
+  HHG_CUDA(cudaMemcpyAsync(m->host_flag, m->dev_err, sizeof(int), cudaMemcpyDeviceToHost, s));
   HHG_CUDA(cudaStreamSynchronize(s));
   *out = *m->host_scalar;
+  if (*m->host_flag != 0) {
+    const int code = *m->host_flag;
+    HHG_CUDA(cudaMemsetAsync(m->dev_err, 0, sizeof(int), s));
+    HHG_CUDA(cudaStreamSynchronize(s));
+    return fail(HHG_ERR_TIMEOUT, code == 1 ? "a bounded device wait ran out (the iterate is incomplete)"
+                                           : "a staging range exceeded its shared-memory slot");
+  }
   return HHG_OK;
 }
 
@@ -1145,10 +1216,17 @@ int setup_device(hhg_mesh* m) {
     }
     if ((rc = upload(m, &t.tiles_int, H.tiles_int)) != HHG_OK) break;
     if ((rc = upload(m, &t.tiles_all, H.tiles_all)) != HHG_OK) break;
+    if ((rc = upload(m, &t.tiles_stream, H.tiles_stream)) != HHG_OK) break;
+    if ((rc = upload(m, &t.tiles_stream32, H.tiles_stream32)) != HHG_OK) break;
     t.n_tiles_int = (int)H.tiles_int.size();
     t.n_tiles_all = (int)H.tiles_all.size();
+    t.n_tiles_stream = (int)H.tiles_stream.size();
+    t.n_tiles_stream32 = (int)H.tiles_stream32.size();
   }
   if (rc == HHG_OK) rc = upload(m, &m->geo, m->host.geo);
+  if (rc == HHG_OK) rc = dalloc(m, &m->dev_err, 4);
+  if (rc == HHG_OK && cudaMemset(m->dev_err, 0, 4 * sizeof(int)) != cudaSuccess)
+    rc = fail(HHG_ERR_CUDA, "cudaMemset failed");
   if (rc == HHG_OK) rc = alloc_levels<double>(m, m->d64, true);
   if (rc == HHG_OK) rc = alloc_scaled(m);
   if (rc == HHG_OK && m->precision == 32) rc = alloc_levels<float>(m, m->d32, true);
@@ -1181,7 +1259,8 @@ int setup_device(hhg_mesh* m) {
       cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming) != cudaSuccess ||
-      cudaMallocHost(&m->host_scalar, sizeof(double) * 8) != cudaSuccess) {
+      cudaMallocHost(&m->host_scalar, sizeof(double) * 8) != cudaSuccess ||
+      cudaMallocHost(&m->host_flag, sizeof(int) * 4) != cudaSuccess) {
     cudaGetLastError();
     return cleanup(fail(HHG_ERR_CUDA, "stream / event creation failed"));
   }
@@ -1266,7 +1345,9 @@ int hhg_mesh_destroy(hhg_mesh* m) {
   for (int b = 0; b < 2; ++b)
     if (m->ev_dn_r[b]) cudaEventDestroy(m->ev_dn_r[b]);
   if (m->host_scalar) cudaFreeHost(m->host_scalar);
+  if (m->host_flag) cudaFreeHost(m->host_flag);
   for (cudaEvent_t ev : m->prof_ev) cudaEventDestroy(ev);
+  for (cudaEvent_t ev : m->bd_ev) cudaEventDestroy(ev);
   const int dev = m->device;
   delete m;
   if (cur >= 0 && cur != dev) cudaSetDevice(cur);
@@ -1589,8 +1670,24 @@ int hhg_batch_destroy(hhg_batch* b) {
 
 int hhg_profile_enable(hhg_mesh* m, int enable) {
   if (!m) return fail(HHG_ERR_ARG, "null mesh");
-  m->prof_on = enable != 0;
+  m->prof_on = (enable & 1) != 0;
   m->prof_used = 0;
+  m->bd_on = (enable & 2) != 0;
+  m->bd_used = 0;
+  return HHG_OK;
+}
+
+int hhg_profile_breakdown(hhg_mesh* m, double* ms, int n) {
+  if (!m || !ms || n < BD_N) return fail(HHG_ERR_ARG, "invalid argument");
+  HHG_TRY(check_device(m));
+  HHG_CUDA(cudaDeviceSynchronize());
+  for (int c = 0; c < n; ++c) ms[c] = 0.0;
+  for (size_t q = 0; q + 1 < m->bd_used; ++q) {
+    float t = 0.f;
+    HHG_CUDA(cudaEventElapsedTime(&t, m->bd_ev[q], m->bd_ev[q + 1]));
+    ms[m->bd_cat[q]] += t;
+  }
+  m->bd_used = 0;
   return HHG_OK;
 }
 
@@ -1628,6 +1725,24 @@ int hhg_set_launch_limit(hhg_mesh* m, int max_ctas) {
   return HHG_OK;
 }
 
+int hhg_set_streaming(hhg_mesh* m, int enable) {
+  if (!m) return fail(HHG_ERR_ARG, "null mesh");
+  HHG_TRY(check_device(m));
+  m->stream_gs = enable ? 1 : 0;
+  for (DevProblem* p : {&m->global, &m->faulty, &m->healthy, &m->dn}) p->stream_gs = m->stream_gs;
+  drop_local_graph(m);
+  return HHG_OK;
+}
+
+int hhg_set_wait_limit(hhg_mesh* m, int tries) {
+  if (!m) return fail(HHG_ERR_ARG, "null mesh");
+  HHG_TRY(check_device(m));
+  m->wait_limit = tries >= 0 ? tries : (1 << 24);
+  for (DevProblem* p : {&m->global, &m->faulty, &m->healthy, &m->dn}) p->wait_limit = m->wait_limit;
+  drop_local_graph(m);
+  return HHG_OK;
+}
+
 int hhg_walk_counts(hhg_mesh* m, int64_t* counts) {
   if (!m || !counts) return fail(HHG_ERR_ARG, "null argument");
   HHG_TRY(check_device(m));
@@ -1637,6 +1752,33 @@ int hhg_walk_counts(hhg_mesh* m, int64_t* counts) {
   for (int q = 0; q < 4; ++q)
     if (probs[q]->sched) HHG_CUDA(cudaMemcpy(&v[q], probs[q]->sched + 2, sizeof(int), cudaMemcpyDeviceToHost));
   for (int q = 0; q < 4; ++q) counts[q] = v[q];
+  return HHG_OK;
+}
+
+int hhg_measure_fp64_peak(double* tflops) {
+  if (!tflops) return fail(HHG_ERR_ARG, "null argument");
+  int dev = 0, sms = 0;
+  HHG_CUDA(cudaGetDevice(&dev));
+  HHG_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  const int blocks = 8 * sms, iters = 1 << 14;
+  double* out = nullptr;
+  HHG_CUDA(cudaMalloc(&out, sizeof(double) * 256 * (size_t)blocks));
+  CallEvents ev;
+  cudaError_t e = ev.create(2);
+  double best = 0.0;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {
+    e = cudaEventRecord(ev.e[0], 0);
+    if (e == cudaSuccess) e = fma_probe(out, blocks, iters, 0);
+    if (e == cudaSuccess) e = cudaEventRecord(ev.e[1], 0);
+    if (e == cudaSuccess) e = cudaEventSynchronize(ev.e[1]);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, ev.e[0], ev.e[1]);
+    if (e == cudaSuccess && rep > 0 && ms > 0.f)   // the first launch is a warm-up
+      best = std::max(best, 2.0 * 8.0 * iters * 256.0 * blocks / (ms * 1e-3) / 1e12);
+  }
+  cudaFree(out);
+  if (e != cudaSuccess) return fail(HHG_ERR_CUDA, std::string("FP64 probe: ") + cudaGetErrorString(e));
+  *tflops = best;
   return HHG_OK;
 }
 
@@ -1707,15 +1849,21 @@ int hhg_solve(hhg_mesh* m, const hhg_solve_opts* o, double* hist, int* n_hist, i
       // the residual of the current iterate is already the FP32 right-hand side
       const int L = (int)m->d64.lv.size() - 1;
       DevLevel<float>& E = m->d32.lv[L];
+      HHG_TRY(bd_mark(m, s, BD_IR));
       HHG_CUDA(zero_problem_blocks<float>(largs(m, L), pargs(m->global, L), E.u, E.uI, s));
       HHG_TRY(vcycle_T<float>(m, m->d32, m->global, pre, post, cg_rtol, cg_maxit, s));
       DevLevel<double>& D = m->d64.lv[L];
+      HHG_TRY(bd_mark(m, s, BD_IR));
       HHG_CUDA(add_correction(largs(m, L), pargs(m->global, L), D.u, D.uI, E.u, E.uI, s));
+      HHG_TRY(bd_mark(m, s, BD_NORM));
       HHG_TRY(ir_residual(m, m->global, s));
+      HHG_TRY(bd_mark(m, s, BD_HOST));
       HHG_TRY(read_scalar(m, m->global.scalar, &v, s));
     } else {
       HHG_TRY(vcycle_T<double>(m, m->d64, m->global, pre, post, cg_rtol, cg_maxit, s));
+      HHG_TRY(bd_mark(m, s, BD_NORM));
       HHG_TRY(norm2_async(m, m->global, s, post > 0));
+      HHG_TRY(bd_mark(m, s, BD_HOST));
       HHG_TRY(read_scalar(m, m->global.scalar, &v, s));
     }
     ++k;
@@ -1725,6 +1873,7 @@ int hhg_solve(hhg_mesh* m, const hhg_solve_opts* o, double* hist, int* n_hist, i
       if (ev.cycle != k) continue;
       if (o->recovery == HHG_RECOVERY_DN) HHG_TRY(setup_dn(m, ev.set));
       else HHG_TRY(setup_fault(m, ev.set));
+      HHG_TRY(bd_mark(m, s, BD_RECOVERY));
       HHG_TRY(inject(m, s));
       if (o->recovery == HHG_RECOVERY_DN) {
         HHG_TRY(recover_dn(m, o->n_global, o->eta, mixed, pre, post, cg_rtol, cg_maxit, nullptr, nullptr, nullptr, s));
@@ -1734,8 +1883,10 @@ int hhg_solve(hhg_mesh* m, const hhg_solve_opts* o, double* hist, int* n_hist, i
         if (n_local <= 0 && o->recovery == HHG_RECOVERY_DD) n_local = (int)std::ceil(o->eta * o->n_global);
         HHG_TRY(recover(m, n_local, n_global, mixed, pre, post, cg_rtol, cg_maxit, nullptr, nullptr, s));
       }
+      HHG_TRY(bd_mark(m, s, BD_NORM));
       if (mixed) HHG_TRY(ir_residual(m, m->global, s));
       else HHG_TRY(norm2_async(m, m->global, s));
+      HHG_TRY(bd_mark(m, s, BD_HOST));
       HHG_TRY(read_scalar(m, m->global.scalar, &v, s));
       rel = r0 > 0 ? std::sqrt(v) / r0 : 0.0;
       push(rel);

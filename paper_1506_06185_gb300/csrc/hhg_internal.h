@@ -113,6 +113,17 @@ constexpr int TILE_SLABS = 8;
 constexpr int TILE_TARGET_DEFAULT = 512;
 constexpr int TILE_SLOTS = 32;
 
+// Work unit of the streaming Gauss-Seidel kernel (7-point structure): the
+// interior rows j0..j1 of slices ka..kb of one macro, swept slice by slice
+// with the neighbour colours staged in shared memory (kernels.cu).
+struct StreamTile {
+  int j0, j1, ka, kb;
+};
+constexpr int STREAM_BAND = 16;      // rows per band of the FP64 units (8 from 512 intervals on)
+constexpr int STREAM_BAND32 = 32;    // rows per band of the FP32 units (16 from 512 intervals on)
+constexpr int STREAM_SLICES = 16;    // slices per unit at most
+constexpr int STREAM_MIN_N = 64;     // levels with at least this many intervals stream
+
 // A copy of an interface node inside one macro block.
 struct Copy {
   int macro, i, j, k;
@@ -143,6 +154,10 @@ struct HostLevel {
   std::vector<double> W;              // [n_macro][16][15] stencil weights
   std::vector<Tile> tiles_int;        // row-pair tiles of the volume interior
   std::vector<Tile> tiles_all;        // tiles covering the closed lattice
+  std::vector<StreamTile> tiles_stream;  // streaming units (N >= STREAM_MIN_N), FP64 cycles
+  int stream_band = 0;                // their rows per band
+  std::vector<StreamTile> tiles_stream32;  // the same for the FP32 cycles (wider bands)
+  int stream_band32 = 0;
 };
 
 struct HostMesh {
@@ -217,6 +232,9 @@ void build_problem(const HostMesh& m, int kind, const std::vector<unsigned char>
 bool macro_in_set(const std::vector<unsigned char>& s, int m);
 // Interior row-pair tiles of refinement N (see mesh.cpp).
 void build_pair_tiles(int N, std::vector<Tile>& out, int target, int slabs);
+// Streaming units of refinement N: bands of `band` interior rows, each split
+// into runs of at most `slices` slices, largest first.
+void build_stream_tiles(int N, int band, int slices, std::vector<StreamTile>& out);
 // Recompute every level's stencils for new per-macro coefficients.
 void set_coefficients(HostMesh& m, const double* coeff);
 // A macro mesh of general connectivity: nv vertex positions (3 doubles each),
@@ -284,6 +302,10 @@ struct DevLevelTables {
   int n_tiles_int = 0;
   Tile* tiles_all = nullptr;
   int n_tiles_all = 0;
+  StreamTile* tiles_stream = nullptr;
+  int n_tiles_stream = 0;
+  StreamTile* tiles_stream32 = nullptr;
+  int n_tiles_stream32 = 0;
 };
 
 struct DevProblemLevel {
@@ -317,6 +339,9 @@ struct DevProblem {
   int* sched = nullptr;               // counters of the dynamic walks (kernels.cu): next unit,
                                       // finished CTAs, completed dynamic launches
   int grid_cap = 0;                   // CTAs per fused launch at most (0: resident CTAs)
+  int stream_gs = 0;                  // streaming 7-point Gauss-Seidel where a level has units
+  int* err = nullptr;                 // the mesh's device error flag (bounded waits)
+  int wait_limit = 1 << 24;           // tries of a bounded device wait
   int* act = nullptr;
   int n_act = 0;
   std::vector<int> act_host;

@@ -19,6 +19,12 @@ struct LevelArgs {
   int n_tiles_int;
   const Tile* tiles_all;
   int n_tiles_all;
+  const StreamTile* tiles_stream;   // streaming Gauss-Seidel units of the FP64 cycles (none below
+  int n_tiles_stream;               // STREAM_MIN_N) and their rows per band
+  int stream_band;
+  const StreamTile* tiles_stream32; // the same for the FP32 cycles
+  int n_tiles_stream32;
+  int stream_band32;
 };
 
 struct ProbArgs {
@@ -41,6 +47,9 @@ struct ProbArgs {
   const float* td32;
   const float* ti32;
   int tn;
+  int stream_gs;   // 1: 7-point Gauss-Seidel uses the streaming kernel where the level has units
+  int* err;        // device flag: set to 1 when a bounded wait of a kernel runs out
+  int wait_limit;  // tries of such a wait (about 64 ns apart)
 };
 
 // One colour of multicolour Gauss-Seidel on the volume interiors and the free
@@ -91,6 +100,10 @@ cudaError_t coarse_cg(const DevProblem& p, const T* f, const T* fI, T* u, T* uI,
                       cudaStream_t s, double* work = nullptr);
 
 cudaError_t reduce_partials(const double* partial, int n, double* out, cudaStream_t s);
+
+// FP64 FMA throughput probe: `blocks` CTAs of 256 threads, 8 x iters FMAs per
+// thread; out holds blocks * 256 doubles.
+cudaError_t fma_probe(double* out, int blocks, int iters, cudaStream_t s);
 
 // Global vector <-> blocked storage of one level.
 template <class T>

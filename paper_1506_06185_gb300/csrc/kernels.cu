@@ -653,6 +653,346 @@ __global__ void __launch_bounds__(CTA, 5) k_gs(int N, const int* __restrict__ rs
 }
 
 // ---------------------------------------------------------------------------
+// Streaming Gauss-Seidel, one colour, 7-point structure (levels with at least
+// STREAM_MIN_N intervals).  In the colour-split layout the rows of a slice
+// follow each other, so a band of rows of one slice and colour is one
+// contiguous range of memory.  A unit (StreamTile) sweeps the band j0..j1 of
+// one macro through the slices ka..kb.  The colour-c update of slice k reads
+// colour c+1 in slices k and k+1, colour c-1 in slices k-1 and k, and f of
+// colour c in slice k.  A producer warp copies these ranges into shared
+// memory with bulk asynchronous copies (rings of three slices per neighbour
+// colour, two for f) that complete on a "full" mbarrier per step; eight
+// consumer warps wait on it, update their share of the slice's colour-c
+// nodes straight into global memory and arrive on the step's "empty"
+// mbarrier, which frees the slots the producer refills two steps later.  No
+// CTA-wide barrier separates the steps of a unit, so warps and copies
+// overlap; each neighbour value crosses HBM about once per launch (plus one
+// row on either side of the band and one slice at either end of the unit).
+// Interface chunks are updated by the consumer threads as in k_gs.  Every
+// wait on an mbarrier is bounded: when one runs out the CTA sets *err, lets
+// its copies in flight land (bounded) and stops taking units.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+__device__ __forceinline__ void fence_async_shared() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// Wait for the phase of bar with the given parity; false after `limit`
+// unsuccessful tries (the first 32 back to back, then about 64 ns apart).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int limit) {
+  for (int it = 0; it < limit; ++it) {
+    if (mbar_test(bar, parity)) return true;
+    if (it >= 32) __nanosleep(64);
+  }
+  return false;
+}
+constexpr int DRAIN_LIMIT = 1 << 24;
+
+// First slot and slot count, inside one colour array, of rows ja..jb of
+// slice k (clipped to the slice's closed lattice, rows 0..N-k).
+__device__ __forceinline__ void band_range(const int* __restrict__ rs, int N, int k, int ja, int jb, int& off,
+                                           int& len) {
+  const int M = N + 1 - k;
+  jb = min(jb, N - k);
+  off = __ldg(rs + k) + slot_prefix(M) - slot_prefix(M - ja);
+  len = jb >= ja ? slot_prefix(M - ja) - slot_prefix(M - jb - 1) : 0;
+}
+
+// 16-byte vector of a staged row in shared memory (16-byte aligned), shifted
+// by one slot as in load_shifted.
+template <class T>
+struct SVec;
+template <>
+struct SVec<float> {
+  __device__ static void load(const float* p, float* v) {
+    const float4 q = *reinterpret_cast<const float4*>(p);
+    v[0] = q.x;
+    v[1] = q.y;
+    v[2] = q.z;
+    v[3] = q.w;
+  }
+};
+template <>
+struct SVec<double> {
+  __device__ static void load(const double* p, double* v) {
+    const double2 q = *reinterpret_cast<const double2*>(p);
+    v[0] = q.x;
+    v[1] = q.y;
+  }
+};
+template <class T>
+__device__ __forceinline__ void lds_shifted(const T* p, bool up, bool dn, T* v) {
+  constexpr int VW = Vec<T>::n;
+  SVec<T>::load(p, v);
+  if (up) {
+    const T e = p[VW];
+#pragma unroll
+    for (int t = 0; t < VW - 1; ++t) v[t] = v[t + 1];
+    v[VW - 1] = e;
+  } else if (dn) {
+    const T e = p[-1];
+#pragma unroll
+    for (int t = VW - 1; t > 0; --t) v[t] = v[t - 1];
+    v[0] = e;
+  }
+}
+
+// The update of gs_group7 with its operands read from the staged rows: a0 /
+// a0p = colour c+1 rows j and j+1 of slice k, a1m = colour c+1 row j-1 of
+// slice k+1, b0 / b0m = colour c-1 rows j and j-1 of slice k, bmp = colour
+// c-1 row j+1 of slice k-1, fr = row j of f (all pointing at slot m0); out
+// is row j of colour c in global memory at slot m0.  Same operations in the
+// same order as gs_group7.
+template <class T, bool SCALED>
+__device__ __forceinline__ void gs_group7_staged(const T* a0, const T* a0p, const T* a1m, const T* b0, const T* b0m,
+                                                 const T* bmp, const T* fr, T* __restrict__ out, bool e0, bool e1,
+                                                 int lo, int hi, const T* w, T inv) {
+  constexpr int VW = Vec<T>::n;
+  T acc[VW], a[VW];
+  SVec<T>::load(fr, acc);
+  lds_shifted(a0, e1, false, a);    // ( 1,  0,  0)
+#pragma unroll
+  for (int t = 0; t < VW; ++t) acc[t] -= w[1] * a[t];
+  lds_shifted(a0p, false, e0, a);   // (-1,  1,  0)
+#pragma unroll
+  for (int t = 0; t < VW; ++t) acc[t] -= w[2] * a[t];
+  SVec<T>::load(a1m, a);            // ( 0, -1,  1)
+#pragma unroll
+  for (int t = 0; t < VW; ++t) acc[t] -= w[3] * a[t];
+  lds_shifted(b0, false, e0, a);    // (-1,  0,  0)
+#pragma unroll
+  for (int t = 0; t < VW; ++t) acc[t] -= w[8] * a[t];
+  lds_shifted(b0m, e1, false, a);   // ( 1, -1,  0)
+#pragma unroll
+  for (int t = 0; t < VW; ++t) acc[t] -= w[9] * a[t];
+  SVec<T>::load(bmp, a);            // ( 0,  1, -1)
+#pragma unroll
+  for (int t = 0; t < VW; ++t) {
+    if (SCALED) acc[t] -= w[10] * a[t];
+    else acc[t] = (acc[t] - w[10] * a[t]) * inv;
+  }
+  if (lo == 0 && hi == VW) {
+    Vec<T>::store(out, acc);
+  } else {
+#pragma unroll
+    for (int t = 0; t < VW; ++t)
+      if (t >= lo && t < hi) out[t] = acc[t];
+  }
+}
+
+// Shared memory of the streaming kernel: 8 staging slots of `slot` elements
+// (3 for colour c+1, 3 for colour c-1, 2 for f) between pads of STREAM_PAD
+// elements, so that the one-slot shifts of lanes outside the interior stay
+// inside the allocation.  The CTA is 8 consumer warps and 1 producer warp.
+constexpr int STREAM_PAD = 32;
+constexpr int STREAM_NSLOT = 8;
+constexpr int STREAM_CONSUMERS = 8;
+constexpr int STREAM_CTA = 32 * (STREAM_CONSUMERS + 1);
+
+template <class T, bool SCALED>
+__global__ void __launch_bounds__(STREAM_CTA) k_gs_stream(
+    int N, const int* __restrict__ rs, int64_t block, T* __restrict__ u, T* __restrict__ uI,
+    const T* __restrict__ fI, const T* __restrict__ W, const T* __restrict__ Winv, const T* __restrict__ fv,
+    const T* __restrict__ Wv, const StreamTile* __restrict__ tiles, int n_tiles, const int* __restrict__ act,
+    int n_act, int colour, const int* __restrict__ cptr, const Copy* __restrict__ cps,
+    const uint32_t* __restrict__ cpo, const int* __restrict__ list, int n_list, IfTab<T> tab, int n_if_units,
+    int* __restrict__ sched, int slot, int wait_limit, int* __restrict__ err) {
+  extern __shared__ __align__(128) unsigned char s_dyn[];
+  T* const buf = reinterpret_cast<T*>(s_dyn) + STREAM_PAD;
+  __shared__ __align__(8) uint64_t full[3], empty[3];
+  __shared__ int s_pre[STREAM_SLICES][STREAM_BAND32 + 1];
+  __shared__ int s_unit;
+  __shared__ int s_fail;
+  const int tid = tid256();
+  const int warp = threadIdx.y, lane = threadIdx.x;
+  const bool producer = warp == STREAM_CONSUMERS;
+  if (tid == 0) s_fail = 0;
+  constexpr int VW = Vec<T>::n;
+  const int CS = __ldg(rs + N + 2);
+  const int c = colour, cA = (c + 1) & 3, cB = (c + 3) & 3;
+  bool failed = false;
+  HHG_UNITS_DYN(n_if_units, n_tiles, n_act, sched, &s_unit) {
+    if (const int ic_ = if_chunk(unit, n_if_units); ic_ >= 0) {
+      const int q = ic_ * CTA + tid;
+      if (!producer && q < n_list) {
+        const int node = list[q];
+        const int c0 = cptr[node], c1 = cptr[node + 1];
+        T val;
+        if (tab.nb) {
+          val = (fI[node] - if_offdiag<T, 6>(tab, u, q)) * tab.dinv[q];
+        } else {
+          T off = T(0), diag = T(0);
+          if_stencil<T, true>(N, rs, block, u, W, cps, c0, c1, off, diag);
+          val = (fI[node] - off) / diag;
+        }
+        uI[node] = val;
+        write_copies(N, rs, block, u, cps, cpo, c0, c1, val);
+      }
+      continue;
+    }
+    const int vb = vol_index(unit, n_if_units);
+    const StreamTile st = tiles[vb / n_act];
+    const int macro = act[vb % n_act];
+    const int nst = st.kb - st.ka + 1;
+    // fresh barriers per unit (every phase of the previous unit completed:
+    // its steps were all consumed and released), and the items per row of
+    // every step of the unit
+    if (tid == 0)
+      for (int b = 0; b < 3; ++b) {
+        mbar_init(&full[b], 1);
+        mbar_init(&empty[b], STREAM_CONSUMERS);
+      }
+    for (int sidx = warp; sidx < nst; sidx += STREAM_CONSUMERS + 1) {
+      const int k = st.ka + sidx;
+      const int nr = min(st.j1, N - 2 - k) - st.j0 + 1;
+      int len = lane < nr ? row_items(N, st.j0 + lane, k, c, true, VW) : 0;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, len, o);
+        if (lane >= o) len += y;
+      }
+      if (lane < nr) s_pre[sidx][lane + 1] = len;
+      if (lane == 0) s_pre[sidx][0] = 0;
+    }
+    __syncthreads();
+    T* ub = u + (size_t)macro * block;
+    const int ja = st.j0 - 1, jbA = st.j1 + 1;
+    if (producer) {
+      if (lane == 0) {
+        const T* gA = ub + (size_t)cA * CS;
+        const T* gB = ub + (size_t)cB * CS;
+        const T* gF = fv + (size_t)macro * block + (size_t)c * CS;
+        int issued = 0;
+        for (int sidx = 0; sidx < nst; ++sidx) {
+          // step sidx refills the slots of step sidx - 2 (released on its empty barrier)
+          if (sidx >= 2 && !mbar_wait(&empty[(sidx - 2) % 3], ((sidx - 2) / 3) & 1, wait_limit)) {
+            atomicExch(err, 1);
+            atomicExch(&s_fail, 1);
+          }
+          if (*(volatile int*)&s_fail) break;
+          const int k = st.ka + sidx;
+          int oA1, lA1, oB0, lB0, oF, lF, oA0 = 0, lA0 = 0, oBm = 0, lBm = 0;
+          band_range(rs, N, k + 1, ja, jbA, oA1, lA1);
+          band_range(rs, N, k, ja, jbA, oB0, lB0);
+          band_range(rs, N, k, st.j0, min(st.j1, N - 2 - k), oF, lF);
+          if (sidx == 0) {
+            band_range(rs, N, k, ja, jbA, oA0, lA0);
+            band_range(rs, N, k - 1, ja, jbA, oBm, lBm);
+          }
+          if (max(max(max(lA1, lB0), max(lF, lA0)), lBm) > slot) {   // never for the host's slot size
+            atomicExch(err, 2);
+            lA1 = min(lA1, slot);
+            lB0 = min(lB0, slot);
+            lF = min(lF, slot);
+            lA0 = min(lA0, slot);
+            lBm = min(lBm, slot);
+          }
+          fence_async_shared();
+          uint64_t* b = &full[sidx % 3];
+          mbar_expect(b, (uint32_t)(lA1 + lB0 + lF + lA0 + lBm) * (uint32_t)sizeof(T));
+          if (lA1) bulk_load(buf + ((k + 1) % 3) * slot, gA + oA1, lA1 * (uint32_t)sizeof(T), b);
+          if (lB0) bulk_load(buf + (3 + k % 3) * slot, gB + oB0, lB0 * (uint32_t)sizeof(T), b);
+          if (lF) bulk_load(buf + (6 + k % 2) * slot, gF + oF, lF * (uint32_t)sizeof(T), b);
+          if (lA0) bulk_load(buf + (k % 3) * slot, gA + oA0, lA0 * (uint32_t)sizeof(T), b);
+          if (lBm) bulk_load(buf + (3 + (k + 2) % 3) * slot, gB + oBm, lBm * (uint32_t)sizeof(T), b);
+          issued = sidx + 1;
+        }
+        if (*(volatile int*)&s_fail) {
+          // the copies of the last step issued on each barrier may still be in flight
+          for (int b = 0; b < 3; ++b) {
+            int last = -1;
+            for (int q = 0; q < issued; ++q)
+              if (q % 3 == b) last = q;
+            if (last >= 0) mbar_wait(&full[b], (last / 3) & 1, DRAIN_LIMIT);
+          }
+        }
+      }
+    } else {
+      T* gU = ub + (size_t)c * CS;
+      const T* wm = Wv + (size_t)macro * 16 * NDIR;
+      const T w[11] = {T(0), wm[1], wm[2], wm[3], T(0), T(0), T(0), T(0), wm[8], wm[9], wm[10]};
+      const T inv = SCALED ? T(1) : Winv[macro];
+      for (int sidx = 0; sidx < nst; ++sidx) {
+        if (!mbar_wait(&full[sidx % 3], (sidx / 3) & 1, wait_limit)) {
+          if (lane == 0) {
+            atomicExch(err, 1);
+            atomicExch(&s_fail, 1);
+          }
+          break;   // no arrival on empty: the producer stops at its next wait
+        }
+        const int k = st.ka + sidx;
+        const int nr = min(st.j1, N - 2 - k) - st.j0 + 1;
+        const int* pre = s_pre[sidx];
+        const int total = pre[nr];
+        const int M = N + 1 - k, M1 = N - k, Mm = N + 2 - k;
+        const T* sA0 = buf + (k % 3) * slot;
+        const T* sA1 = buf + ((k + 1) % 3) * slot;
+        const T* sB0 = buf + (3 + k % 3) * slot;
+        const T* sBm = buf + (3 + (k + 2) % 3) * slot;
+        const T* sF = buf + (6 + k % 2) * slot;
+        const int PA = slot_prefix(M - ja), PA1 = slot_prefix(M1 - ja), PAm = slot_prefix(Mm - ja);
+        const int PF = slot_prefix(M - st.j0);
+        const int gbase = __ldg(rs + k) + slot_prefix(M);
+        for (int tt = tid; tt < total; tt += CTA) {
+          int lo_r = 0, hi_r = nr;
+          while (hi_r - lo_r > 1) {
+            const int mid = (lo_r + hi_r) >> 1;
+            if (pre[mid] <= tt) lo_r = mid;
+            else hi_r = mid;
+          }
+          const int j = st.j0 + lo_r;
+          const int g = tt - pre[lo_r];
+          int ic, mlo, n;
+          colour_row(N, j, k, c, ic, mlo, n);
+          const int m0 = g * VW;
+          const int X = slot_prefix(M - j);
+          const T* a0 = sA0 + (PA - X) + m0;
+          const T* a0p = sA0 + (PA - slot_prefix(M - j - 1)) + m0;
+          const T* a1m = sA1 + (PA1 - slot_prefix(M1 - j + 1)) + m0;
+          const T* b0 = sB0 + (PA - X) + m0;
+          const T* b0m = sB0 + (PA - slot_prefix(M - j + 1)) + m0;
+          const T* bmp = sBm + (PAm - slot_prefix(Mm - j - 1)) + m0;
+          const T* fr = sF + (PF - X) + m0;
+          const int lo = max(mlo - m0, 0), hi = min(mlo + n - m0, VW);
+          gs_group7_staged<T, SCALED>(a0, a0p, a1m, b0, b0m, bmp, fr, gU + (gbase - X) + m0, ic == 0, ic == 3,
+                                      lo, hi, w, inv);
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[sidx % 3]);
+      }
+    }
+    __syncthreads();
+    if (*(volatile int*)&s_fail) {
+      failed = true;
+      break;
+    }
+  }
+  (void)failed;
+  finish_units(sched, n_if_units + n_tiles * n_act);
+}
+
+// ---------------------------------------------------------------------------
 // Residual r = f - A u on the free nodes (all colours); optional write of r
 // (zero at the problem's frozen ghost copies) and per-CTA partial sums of r^2
 // ---------------------------------------------------------------------------
@@ -1110,6 +1450,22 @@ __global__ void k_reduce(const double* __restrict__ partial, int n, double* __re
   if (threadIdx.x == 0) out[0] = s;
 }
 
+// FP64 FMA throughput probe (measurement support): every thread runs eight
+// independent FMA chains of `iters` steps and writes their sum.
+__global__ void __launch_bounds__(256) k_fma_probe(double* __restrict__ out, int iters, double a, double b) {
+  double x[8];
+#pragma unroll
+  for (int q = 0; q < 8; ++q) x[q] = threadIdx.x * 1e-3 + q;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = fma(x[q], a, b);
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) s += x[q];
+  out[(size_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
 // ---------------------------------------------------------------------------
 // Global vector <-> blocks (closed-lattice tiles: 8 rows x 32 slots)
 // ---------------------------------------------------------------------------
@@ -1287,6 +1643,60 @@ inline unsigned resident_grid(const void* kernel, int total, int cap_limit = 0) 
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+// Elements of one staging slot of the streaming kernel on a level: the
+// largest band range, rows 0..band+1 of slice 0, rounded up to 32 elements.
+inline int stream_slot(int N, int band) {
+  const int M = N + 1;
+  const int len = slot_prefix(M) - slot_prefix(std::max(0, M - (band + 2)));
+  return (len + 31) & ~31;
+}
+
+template <class T, bool SCALED>
+cudaError_t launch_gs_stream(const LevelArgs& L, const ProbArgs& p, T* u, T* uI, const T* fI, const T* W,
+                             const T* Winv, const T* fv, const T* Wv, int colour, int n, cudaStream_t s) {
+  const bool wide = sizeof(T) == 4;   // FP32 cycles: wider bands
+  const StreamTile* tiles = wide ? L.tiles_stream32 : L.tiles_stream;
+  const int n_tiles = wide ? L.n_tiles_stream32 : L.n_tiles_stream;
+  const Units g = units(n, n_tiles, p.n_act);
+  if (g.total == 0) return cudaSuccess;
+  const int slot = stream_slot(L.N, wide ? L.stream_band32 : L.stream_band);
+  const size_t smem = (size_t)(STREAM_NSLOT * slot + 2 * STREAM_PAD) * sizeof(T);
+  auto kern = k_gs_stream<T, SCALED>;
+  // the kernel may use up to the device's opt-in shared memory per CTA (set
+  // once per device; a smaller setting would refuse later, larger launches)
+  static std::mutex mu;
+  static std::map<int, int> attr_max;   // device -> bytes allowed
+  int dev = 0;
+  cudaGetDevice(&dev);
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = attr_max.find(dev);
+    if (it == attr_max.end()) {
+      int optin = 0;
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      const int static_bytes = 4096;   // the kernel's own shared arrays, with room
+      const int allow = std::max(0, optin - static_bytes);
+      const cudaError_t e =
+          cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, allow);
+      if (e != cudaSuccess) return e;
+      it = attr_max.emplace(dev, allow).first;
+    }
+    if ((size_t)it->second < smem) return cudaErrorInvalidConfiguration;
+  }
+  int per_sm = 0, sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)kern, STREAM_CTA, smem);
+  int cap = std::max(1, sms * std::max(1, per_sm));
+  if (p.grid_cap > 0) cap = std::min(cap, p.grid_cap);
+  const unsigned grid = (unsigned)std::min(g.total, cap);
+  ++g_kernel_launches;
+  kern<<<grid, dim3(32, STREAM_CONSUMERS + 1), smem, s>>>(L.N, L.rs, L.block, u, uI, fI, W, Winv, fv, Wv, tiles,
+                                                         n_tiles, p.act, p.n_act, colour, L.cptr, L.cps, L.cp_off,
+                                       p.free_if + p.col_off[colour], n, if_tab<T>(p, p.col_off[colour]),
+                                       g.n_if_units, p.sched, slot, p.wait_limit, p.err);
+  return cudaGetLastError();
+}
+
 template <class T>
 cudaError_t gs_colour(const LevelArgs& L, const ProbArgs& p, T* u, T* uI, const T* f, const T* fI, const T* W,
                       const T* Winv, int colour, bool seven_point, cudaStream_t s, cudaEvent_t ev_begin,
@@ -1294,6 +1704,13 @@ cudaError_t gs_colour(const LevelArgs& L, const ProbArgs& p, T* u, T* uI, const 
   if (!seven_point) fs = Wsc = nullptr;
   if (!fs || !Wsc) fs = Wsc = nullptr;
   const int n = p.col_off[colour + 1] - p.col_off[colour];
+  if (seven_point && p.stream_gs && L.n_tiles_stream > 0 && p.err) {
+    if (ev_begin) cudaEventRecord(ev_begin, s);
+    const cudaError_t e = fs ? launch_gs_stream<T, true>(L, p, u, uI, fI, W, Winv, fs, Wsc, colour, n, s)
+                             : launch_gs_stream<T, false>(L, p, u, uI, fI, W, Winv, f, W, colour, n, s);
+    if (ev_end) cudaEventRecord(ev_end, s);
+    return e;
+  }
   const Units g = units(n, L.n_tiles_int, p.n_act);
   if (g.total == 0) return cudaSuccess;
   auto kern = seven_point ? k_gs<T, true> : k_gs<T, false>;
@@ -1370,6 +1787,12 @@ cudaError_t coarse_cg(const DevProblem& p, const T* f, const T* fI, T* u, T* uI,
   ++g_kernel_launches;
   k_cg<T><<<1, CG_THREADS, 0, s>>>(p.n_cg, p.rowptr, p.col, p.val, p.fsrc, f, fI, p.uptr, p.udst, p.umaster, u, uI,
                                    work ? work : p.cg_work, rtol, maxit, p.cg_iters);
+  return cudaGetLastError();
+}
+
+cudaError_t fma_probe(double* out, int blocks, int iters, cudaStream_t s) {
+  ++g_kernel_launches;
+  k_fma_probe<<<blocks, 256, 0, s>>>(out, iters, 0.999999, 1e-7);
   return cudaGetLastError();
 }
 

@@ -267,6 +267,25 @@ void build_pair_tiles(int N, std::vector<Tile>& out, int target, int slabs) {
   std::stable_sort(out.begin(), out.end(), [&](const Tile& a, const Tile& b) { return work(a) > work(b); });
 }
 
+void build_stream_tiles(int N, int band, int slices, std::vector<StreamTile>& out) {
+  out.clear();
+  // interior rows j = 1..N-2-k of slice k = 1..N-3; band [j0, j1] has
+  // interior rows in slices k <= N - 2 - j0
+  for (int j0 = 1; j0 <= N - 3; j0 += band) {
+    const int j1 = std::min(j0 + band - 1, N - 3);
+    for (int ka = 1; ka <= N - 2 - j0; ka += slices)
+      out.push_back(StreamTile{j0, j1, ka, std::min(ka + slices - 1, N - 2 - j0)});
+  }
+  auto work = [N](const StreamTile& t) {
+    int64_t w = 0;
+    for (int k = t.ka; k <= t.kb; ++k)
+      for (int j = t.j0; j <= std::min(t.j1, N - 2 - k); ++j) w += N - 1 - j - k;
+    return w;
+  };
+  std::stable_sort(out.begin(), out.end(),
+                   [&](const StreamTile& a, const StreamTile& b) { return work(a) > work(b); });
+}
+
 void set_coefficients(HostMesh& m, const double* coeff) {
   for (int t = 0; t < m.n_macro; ++t) m.coeff[t] = coeff[t];
   for (auto& L : m.lv) compute_level_weights(m, L);
@@ -438,6 +457,12 @@ void build_host_mesh(HostMesh& m, const int sub[3], int R, int r0, const double*
     L.n_if = (int)L.if_gid.size();
     build_pair_tiles(N, L.tiles_int, TILE_TARGET_DEFAULT, TILE_SLABS);
     build_tiles(N, false, L.tiles_all);
+    if (N >= STREAM_MIN_N) {
+      L.stream_band = N >= 512 ? STREAM_BAND / 2 : STREAM_BAND;
+      build_stream_tiles(N, L.stream_band, STREAM_SLICES, L.tiles_stream);
+      L.stream_band32 = N >= 512 ? STREAM_BAND32 / 2 : STREAM_BAND32;
+      build_stream_tiles(N, L.stream_band32, STREAM_SLICES, L.tiles_stream32);
+    }
     m.lv.push_back(std::move(L));
   }
 }
@@ -882,6 +907,12 @@ void build_general_mesh(HostMesh& m, const double* verts, int nv, const int* tet
     L.n_if_classes = n_cls;
     build_pair_tiles(N, L.tiles_int, TILE_TARGET_DEFAULT, TILE_SLABS);
     build_tiles(N, false, L.tiles_all);
+    if (N >= STREAM_MIN_N) {
+      L.stream_band = N >= 512 ? STREAM_BAND / 2 : STREAM_BAND;
+      build_stream_tiles(N, L.stream_band, STREAM_SLICES, L.tiles_stream);
+      L.stream_band32 = N >= 512 ? STREAM_BAND32 / 2 : STREAM_BAND32;
+      build_stream_tiles(N, L.stream_band32, STREAM_SLICES, L.tiles_stream32);
+    }
     m.lv.push_back(std::move(L));
   }
 }

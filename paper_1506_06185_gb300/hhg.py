@@ -28,7 +28,8 @@ EXPORTS = ["hhg_mesh_create", "hhg_mesh_destroy", "hhg_mesh_info", "hhg_mesh_byt
            "hhg_solve", "hhg_last_error", "hhg_profile_enable", "hhg_profile_read", "hhg_profile_info",
            "hhg_launch_count", "hhg_vcycle_noalloc", "hhg_set_coefficients", "hhg_grad_coeff",
            "hhg_autotune", "hhg_batch_create", "hhg_batch_launch", "hhg_batch_destroy", "hhg_recover_dn",
-           "hhg_mesh_create_general", "hhg_set_launch_limit", "hhg_walk_counts"]
+           "hhg_mesh_create_general", "hhg_set_launch_limit", "hhg_walk_counts", "hhg_set_streaming",
+           "hhg_set_wait_limit", "hhg_measure_fp64_peak", "hhg_profile_breakdown"]
 
 
 class hhg_mesh_desc(C.Structure):
@@ -91,6 +92,10 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "hhg_launch_count": ([C.POINTER(C.c_int64)], C.c_int),
         "hhg_set_launch_limit": ([P, C.c_int], C.c_int),
         "hhg_walk_counts": ([P, C.POINTER(C.c_int64)], C.c_int),
+        "hhg_set_streaming": ([P, C.c_int], C.c_int),
+        "hhg_set_wait_limit": ([P, C.c_int], C.c_int),
+        "hhg_measure_fp64_peak": ([C.POINTER(C.c_double)], C.c_int),
+        "hhg_profile_breakdown": ([P, C.POINTER(C.c_double), C.c_int], C.c_int),
         "hhg_vcycle_noalloc": ([P, C.c_int, C.c_int, P], C.c_int),
         "hhg_set_coefficients": ([P, C.POINTER(C.c_double), P], C.c_int),
         "hhg_grad_coeff": ([P, P, P, C.POINTER(C.c_double), P], C.c_int),
@@ -356,7 +361,21 @@ class Batch:
 
 
 def hhg_profile_enable(h, enable=True):
-    return _check(lib().hhg_profile_enable(h, 1 if enable else 0))
+    """enable: True/1 times the dominant kernel's launches, 2 records the
+    phase breakdown, 3 both; False/0 stops."""
+    return _check(lib().hhg_profile_enable(h, int(enable)))
+
+
+BREAKDOWN_PHASES = ["fine_smoothing", "fine_residual", "restriction", "prolongation", "coarse_levels", "coarse_cg",
+                    "stopping_test", "host_turnaround", "fault_recovery", "ir_correction"]
+
+
+def hhg_profile_breakdown(h):
+    """Per-phase device time (ms) of the global cycles since profiling bit 1
+    was enabled, as a dict keyed by BREAKDOWN_PHASES."""
+    ms = (C.c_double * len(BREAKDOWN_PHASES))()
+    _check(lib().hhg_profile_breakdown(h, ms, len(BREAKDOWN_PHASES)))
+    return dict(zip(BREAKDOWN_PHASES, list(ms)))
 
 
 def hhg_profile_read(h):
@@ -375,12 +394,29 @@ def hhg_set_launch_limit(h, max_ctas):
     return _check(lib().hhg_set_launch_limit(h, int(max_ctas)))
 
 
+def hhg_set_streaming(h, enable=True):
+    return _check(lib().hhg_set_streaming(h, 1 if enable else 0))
+
+
+def hhg_set_wait_limit(h, tries):
+    """tries >= 0: at most that many tries per bounded device wait (0: every
+    wait runs out at once); tries < 0: the default."""
+    return _check(lib().hhg_set_wait_limit(h, int(tries)))
+
+
 def hhg_walk_counts(h):
     """Dynamic-walk launches completed by the global, faulty, healthy
     (Gamma frozen) and DN Neumann problems."""
     c = (C.c_int64 * 4)()
     _check(lib().hhg_walk_counts(h, c))
     return list(c)
+
+
+def hhg_measure_fp64_peak():
+    """FP64 FMA throughput of the current device, TFLOP/s."""
+    t = C.c_double()
+    _check(lib().hhg_measure_fp64_peak(C.byref(t)))
+    return t.value
 
 
 def hhg_launch_count():
