@@ -348,6 +348,9 @@ def run_ours(args):
     f_dev = torch.from_numpy(f_np).to(dev)
     u0_dev = torch.zeros_like(f_dev)
     M.set_problem(f_dev, u0_dev)
+    # tile shapes of every smoothed level picked by the library's autotuner
+    # (before the timed region; the steps reload the initial guess)
+    tiles = None if args.no_autotune else hhg.hhg_autotune(M.h, R - 1, reps=3)
     torch.cuda.synchronize()
     solve_kw = dict(rtol=RTOL, max_cycles=MAX_CYCLES, fault_cycle=FAULT_CYCLE, fault_ids=fault,
                     recovery=hhg.HHG_RECOVERY_DD, n_global=N_I, eta=ETA)
@@ -456,7 +459,8 @@ def run_ours(args):
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "dof": dof, "cycles_per_step": cyc_list,
                        "time_to_1e-8_with_fault_ms": ms / args.steps, "l2": "inputs larger than L2 (no flush)",
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": "replicas" if world > 1 else "single GPU",
+                       "autotuned_tile_shapes": tiles},
             "roofline": roofline, "e2e": e2e, "clocks": clocks, "gpu_launches": l1 - l0,
             "final_rel_residual": float(hist[-1]), "variants": variants}
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -853,6 +857,7 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--quick", action="store_true", help="skip the variant timings")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default tile shapes")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the refined-9 precision, batched-recovery and differentiation workloads")
     ap.add_argument("--batch", action="store_true", help="run the batched-recovery workload instead")

@@ -272,9 +272,9 @@ int hhg_grad_coeff(hhg_mesh* mesh, const double* u, const double* lam, double* g
 /* Autotuning of the volume tile shape (an implementation knob, not part of
  * the method).  For every smoothed level, times `reps` Gauss-Seidel steps of
  * the global problem with each candidate tile shape (nodes per tile and
- * slices per tile: 256/4, 512/8, 1024/8, 2048/16) in the mesh's working
- * precision (FP32 arrays for precision-32 meshes, otherwise the FP64
- * iterate, which the sweeps smooth) and keeps the fastest for that level.
+ * slices per tile: 256/4, 512/8, 1024/8, 2048/16) on the FP64 iterate (which
+ * the sweeps smooth) and, on precision-32 meshes, also on the FP32 arrays,
+ * and keeps for that level the shape with the least total time.
  * chosen (may be NULL, one int per level, coarsest first) receives the index
  * of the chosen candidate (-1 for the coarsest level, which is not smoothed).
  * The tiles not kept are freed (after synchronising the device), except while

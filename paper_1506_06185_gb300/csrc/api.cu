@@ -1076,8 +1076,20 @@ int update_coefficients(hhg_mesh* m, const double* coeff) {
 const int TUNE_CAND[][2] = {{256, 4}, {512, 8}, {1024, 8}, {2048, 16}};
 constexpr int N_TUNE_CAND = 4;
 
+// Device time of `reps` Gauss-Seidel steps of the global problem on level l
+// in precision T (after one warm-up step).
 template <class T>
-int tune_level(hhg_mesh* m, Prec<T>& P, int l, int reps, cudaStream_t s, int* best_out) {
+int time_smooth(hhg_mesh* m, Prec<T>& P, int l, int reps, cudaStream_t s, cudaEvent_t a, cudaEvent_t b, float* ms) {
+  HHG_TRY(smooth<T>(m, P, m->global, l, 1, s, false));
+  HHG_CUDA(cudaEventRecord(a, s));
+  HHG_TRY(smooth<T>(m, P, m->global, l, reps, s, false));
+  HHG_CUDA(cudaEventRecord(b, s));
+  HHG_CUDA(cudaEventSynchronize(b));
+  HHG_CUDA(cudaEventElapsedTime(ms, a, b));
+  return HHG_OK;
+}
+
+int tune_level(hhg_mesh* m, int l, int reps, cudaStream_t s, int* best_out) {
   const HostLevel& H = m->host.lv[l];
   DevLevelTables& tb = m->tab[l];
   Tile* const before = tb.tiles_int;
@@ -1095,13 +1107,12 @@ int tune_level(hhg_mesh* m, Prec<T>& P, int l, int reps, cudaStream_t s, int* be
     ndev[c] = (int)tiles.size();
     tb.tiles_int = dev[c];
     tb.n_tiles_int = ndev[c];
-    HHG_TRY(smooth<T>(m, P, m->global, l, 1, s));   // warm-up
-    HHG_CUDA(cudaEventRecord(a, s));
-    HHG_TRY(smooth<T>(m, P, m->global, l, reps, s));
-    HHG_CUDA(cudaEventRecord(b, s));
-    HHG_CUDA(cudaEventSynchronize(b));
-    float ms = 0.f;
-    HHG_CUDA(cudaEventElapsedTime(&ms, a, b));
+    // both precisions' sweeps use the level's tiles: the FP64 one always,
+    // the FP32 one on precision-32 meshes
+    float ms = 0.f, ms32 = 0.f;
+    HHG_TRY(time_smooth<double>(m, m->d64, l, reps, s, a, b, &ms));
+    if (m->precision == 32) HHG_TRY(time_smooth<float>(m, m->d32, l, reps, s, a, b, &ms32));
+    ms += ms32;
     if (ms < best_ms) {
       best_ms = ms;
       best = c;
@@ -1526,8 +1537,7 @@ int hhg_autotune(hhg_mesh* m, int reps, int* chosen, void* stream) {
   drop_local_graph(m);
   for (int l = 1; l < nl; ++l) {
     int best = 0;
-    if (m->precision == 32) HHG_TRY(tune_level<float>(m, m->d32, l, reps, s, &best));
-    else HHG_TRY(tune_level<double>(m, m->d64, l, reps, s, &best));
+    HHG_TRY(tune_level(m, l, reps, s, &best));
     if (chosen) chosen[l] = best;
   }
   if (chosen) chosen[0] = -1;

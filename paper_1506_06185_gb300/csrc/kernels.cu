@@ -483,6 +483,20 @@ __device__ __forceinline__ void gs_group7(const Slice& sc, int N, int j, int g, 
 // writes the interior nodes among them to rb and/or adds their squares to ss.
 // ZERO: the residual of these nodes is known to vanish (their colour was the
 // last one smoothed); zeros are written and nothing is read.
+// Stores the lanes lo .. hi - 1 of a VW-vector (all lanes at once when the
+// vector is complete).
+template <class T>
+__device__ __forceinline__ void store_lanes(T* __restrict__ out, const T* acc, int lo, int hi) {
+  constexpr int VW = Vec<T>::n;
+  if (lo == 0 && hi == VW) {
+    Vec<T>::store(out, acc);
+  } else {
+#pragma unroll
+    for (int t = 0; t < VW; ++t)
+      if (t >= lo && t < hi) out[t] = acc[t];
+  }
+}
+
 template <class T, bool WRITE, bool NORM, bool ZERO = false>
 __device__ __forceinline__ void res_group7(const Slice& sc, int N, int j, int g, int c, const T* __restrict__ ub,
                                            const T* __restrict__ fb, T* __restrict__ rb, const T* __restrict__ w,
@@ -504,17 +518,7 @@ __device__ __forceinline__ void res_group7(const Slice& sc, int N, int j, int g,
   if (ZERO) {
 #pragma unroll
     for (int t = 0; t < VW; ++t) acc[t] = T(0);
-    if (WRITE) {
-      const int lo = max(mlo - m0, 0), hi = min(mlo + n - m0, VW);
-      T* out = rb + cc + r0 + m0;
-      if (lo == 0 && hi == VW) {
-        Vec<T>::store(out, acc);
-      } else {
-#pragma unroll
-        for (int t = 0; t < VW; ++t)
-          if (t >= lo && t < hi) out[t] = acc[t];
-      }
-    }
+    if (WRITE) store_lanes(rb + cc + r0 + m0, acc, max(mlo - m0, 0), min(mlo + n - m0, VW));
     return;
   }
   Vec<T>::load(fb + cc + r0 + m0, acc);
@@ -545,16 +549,7 @@ __device__ __forceinline__ void res_group7(const Slice& sc, int N, int j, int g,
     for (int t = 0; t < VW; ++t)
       if (t >= lo && t < hi) ss += (double)acc[t] * (double)acc[t];
   }
-  if (WRITE) {
-    T* out = rb + cc + r0 + m0;
-    if (lo == 0 && hi == VW) {
-      Vec<T>::store(out, acc);
-    } else {
-#pragma unroll
-      for (int t = 0; t < VW; ++t)
-        if (t >= lo && t < hi) out[t] = acc[t];
-    }
-  }
+  if (WRITE) store_lanes(rb + cc + r0 + m0, acc, lo, hi);
 }
 
 // The 7-point colour-c items of one tile: groups of VW consecutive same-colour
@@ -997,7 +992,7 @@ __global__ void __launch_bounds__(STREAM_CTA) k_gs_stream(
 // (zero at the problem's frozen ghost copies) and per-CTA partial sums of r^2
 // ---------------------------------------------------------------------------
 template <class T, bool S7, bool WRITE, bool NORM>
-__global__ void __launch_bounds__(CTA, sizeof(T) == 8 ? 6 : 5) k_res(int N, const int* __restrict__ rs, int64_t block, const T* __restrict__ u,
+__global__ void __launch_bounds__(CTA, 4) k_res(int N, const int* __restrict__ rs, int64_t block, const T* __restrict__ u,
                                              const T* __restrict__ uI, const T* __restrict__ f,
                                              const T* __restrict__ fI, T* __restrict__ r, const T* __restrict__ W,
                                              const Tile* __restrict__ tiles, int n_tiles, const int* __restrict__ act,
@@ -1282,45 +1277,38 @@ _Pragma("unroll")
   if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.x] = s;
 }
 
-__global__ void __launch_bounds__(CTA) k_add_corr(int N, const int* __restrict__ rs, int64_t block, double* __restrict__ u,
-                                                  double* __restrict__ uI, const float* __restrict__ e,
-                                                  const float* __restrict__ eI, const Tile* __restrict__ tiles,
-                                                  int n_tiles, const int* __restrict__ act, int n_act,
-                                                  const int* __restrict__ cptr, const Copy* __restrict__ cps,
-                                                  const uint32_t* __restrict__ cpo, const int* __restrict__ list,
-                                                  int n_list, int n_if_units, int* __restrict__ sched) {
-  __shared__ int s_pre2[MAX_SLABS][33];
-  __shared__ int s_pre_tot[MAX_SLABS + 1];
-  __shared__ int s_unit;
-  HHG_UNITS_DYN(n_if_units, n_tiles, n_act, sched, &s_unit) {
-    if (const int ic_ = if_chunk(unit, n_if_units); ic_ >= 0) {
-      const int q = ic_ * CTA + tid256();
-      if (q < n_list) {
-        const int node = list[q];
-        const double val = uI[node] + (double)eI[node];
-        uI[node] = val;
-        write_copies(N, rs, block, u, cps, cpo, cptr[node], cptr[node + 1], val);
-      }
-      continue;
-    }
-    Tile t;
-    int macro;
-    vol_unit(vol_index(unit, n_if_units), n_act, tiles, act, t, macro);
-    double* ub = u + (size_t)macro * block;
-    const float* eb = e + (size_t)macro * block;
-    HHG_TILE_NODES(N, rs, t, s_pre, {
-      const int me = lidx32(rs, N, i, j, k);
-      ub[me] += (double)eb[me];
-    })
+// u64 += e32 over whole active blocks, two slots per thread and step: the
+// FP32 correction is zero at every slot the cycle does not own (Dirichlet and
+// frozen copies, padding; the blocks are cleared before the cycle), and each
+// ghost copy of a free interface node holds the master's correction, so the
+// copies stay equal to their masters.  Blocks are multiples of 256 slots.
+__global__ void __launch_bounds__(256) k_add_corr_blocks(double* __restrict__ u, const float* __restrict__ e,
+                                                        int64_t block, const int* __restrict__ act) {
+  const size_t base = (size_t)act[blockIdx.y] * block;
+  double2* ub = reinterpret_cast<double2*>(u + base);
+  const float2* eb = reinterpret_cast<const float2*>(e + base);
+  for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < block / 2; q += (int64_t)gridDim.x * blockDim.x) {
+    double2 x = ub[q];
+    const float2 d = __ldg(eb + q);
+    x.x += (double)d.x;
+    x.y += (double)d.y;
+    ub[q] = x;
   }
-  finish_units(sched, n_if_units + n_tiles * n_act);
+}
+
+// uI[list[q]] += eI[list[q]] for the free interface masters.
+__global__ void k_add_corr_masters(double* __restrict__ uI, const float* __restrict__ eI, const int* __restrict__ list,
+                                   int n) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) {
+    const int node = list[q];
+    uI[node] += (double)eI[node];
+  }
 }
 
 // ---------------------------------------------------------------------------
 // Coarse-level CG, one CTA (FP64; §2.1 coarse solver)
 // ---------------------------------------------------------------------------
-constexpr int CG_THREADS = 1024;
-
 __device__ __forceinline__ double cta_sum(double v, double* sh) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   __syncthreads();
@@ -1336,6 +1324,27 @@ __device__ __forceinline__ double cta_sum(double v, double* sh) {
   return sh[32];
 }
 
+constexpr int CG_THREADS = 256;
+
+// Sum of v over the CTA (CG_THREADS threads), returned to every thread in the
+// same order (warp partials 0..7); buf holds the warp partials.  Consecutive
+// reductions alternate between two buffers.
+__device__ __forceinline__ double cg_allreduce(double v, double* buf) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) buf[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double s = 0.0;
+#pragma unroll
+  for (int w = 0; w < CG_THREADS / 32; ++w) s += buf[w];
+  return s;
+}
+
+// CG on the compact free nodes of the coarsest level from x = 0 until
+// ||r|| <= rtol ||b|| or maxit iterations.  x, r, p and A p live in shared
+// memory (smem != 0) or in the global work array (4 n doubles).  Each
+// iteration: A p and p.Ap (one reduction), the updates of x and r and r.r
+// (one reduction), the new direction; row q belongs to thread q mod
+// CG_THREADS throughout.
 template <class T>
 __global__ void __launch_bounds__(CG_THREADS) k_cg(int n, const int* __restrict__ rowptr, const int* __restrict__ col,
                                                    const double* __restrict__ val, const int64_t* __restrict__ fsrc,
@@ -1343,14 +1352,15 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg(int n, const int* __restrict_
                                                    const int* __restrict__ uptr, const int64_t* __restrict__ udst,
                                                    const int* __restrict__ umaster, T* __restrict__ u,
                                                    T* __restrict__ uI, double* __restrict__ work, double rtol,
-                                                   int maxit, int* __restrict__ iters) {
-  __shared__ double sh[33];
-  double* x = work;
-  double* r = work + n;
-  double* p = work + 2 * (size_t)n;
-  double* Ap = work + 3 * (size_t)n;
+                                                   int maxit, int* __restrict__ iters, int smem) {
+  extern __shared__ double s_cg[];
+  __shared__ double red[2][CG_THREADS / 32];
+  double* x = smem ? s_cg : work;
+  double* r = x + n;
+  double* p = r + n;
+  double* Ap = p + n;
   double part = 0.0;
-  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+  for (int q = threadIdx.x; q < n; q += CG_THREADS) {
     const int64_t s = fsrc[q];
     const double b = s >= 0 ? (double)f[s] : (double)fI[-1 - s];
     x[q] = 0.0;
@@ -1358,34 +1368,37 @@ __global__ void __launch_bounds__(CG_THREADS) k_cg(int n, const int* __restrict_
     p[q] = b;
     part += b * b;
   }
-  double rr = cta_sum(part, sh);
+  double rr = cg_allreduce(part, red[0]);
+  int rb = 1;
   const double bnorm = sqrt(rr);
   int it = 0;
   while (bnorm > 0.0 && sqrt(rr) > rtol * bnorm && it < maxit) {
+    __syncthreads();   // every p entry written before A p reads it
     part = 0.0;
-    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    for (int q = threadIdx.x; q < n; q += CG_THREADS) {
       double a = 0.0;
-      for (int e = rowptr[q]; e < rowptr[q + 1]; ++e) a += val[e] * p[col[e]];
+      for (int e = __ldg(rowptr + q); e < __ldg(rowptr + q + 1); ++e) a += __ldg(val + e) * p[__ldg(col + e)];
       Ap[q] = a;
       part += p[q] * a;
     }
-    const double pAp = cta_sum(part, sh);
+    const double pAp = cg_allreduce(part, red[rb]);
+    rb ^= 1;
     const double alpha = rr / pAp;
     part = 0.0;
-    for (int q = threadIdx.x; q < n; q += blockDim.x) {
+    for (int q = threadIdx.x; q < n; q += CG_THREADS) {
       x[q] += alpha * p[q];
       const double rq = r[q] - alpha * Ap[q];
       r[q] = rq;
       part += rq * rq;
     }
-    const double rr_new = cta_sum(part, sh);
+    const double rr_new = cg_allreduce(part, red[rb]);
+    rb ^= 1;
     const double beta = rr_new / rr;
-    for (int q = threadIdx.x; q < n; q += blockDim.x) p[q] = r[q] + beta * p[q];
+    for (int q = threadIdx.x; q < n; q += CG_THREADS) p[q] = r[q] + beta * p[q];
     rr = rr_new;
     ++it;
-    __syncthreads();
   }
-  for (int q = threadIdx.x; q < n; q += blockDim.x) {
+  for (int q = threadIdx.x; q < n; q += CG_THREADS) {
     const T v = (T)x[q];
     for (int e = uptr[q]; e < uptr[q + 1]; ++e) u[udst[e]] = v;
     if (umaster[q] >= 0) uI[umaster[q]] = v;
@@ -1784,9 +1797,32 @@ template <class T>
 cudaError_t coarse_cg(const DevProblem& p, const T* f, const T* fI, T* u, T* uI, double rtol, int maxit,
                       cudaStream_t s, double* work) {
   if (p.n_cg == 0) return cudaSuccess;
+  // the vectors live in shared memory when they fit and no work array is
+  // imposed (the allocation-free cycle passes its static array)
+  static std::mutex mu;
+  static std::map<int, int> allow;   // device -> dynamic shared bytes allowed
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int lim = 0;
+  {
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = allow.find(dev);
+    if (it == allow.end()) {
+      int optin = 0;
+      cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+      const int a = std::max(0, optin - 4096);
+      const cudaError_t e = cudaFuncSetAttribute((const void*)k_cg<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, a);
+      if (e != cudaSuccess) return e;
+      it = allow.emplace(dev, a).first;
+    }
+    lim = it->second;
+  }
+  const size_t bytes = (size_t)4 * p.n_cg * sizeof(double);
+  const bool in_smem = !work && bytes <= (size_t)lim;
   ++g_kernel_launches;
-  k_cg<T><<<1, CG_THREADS, 0, s>>>(p.n_cg, p.rowptr, p.col, p.val, p.fsrc, f, fI, p.uptr, p.udst, p.umaster, u, uI,
-                                   work ? work : p.cg_work, rtol, maxit, p.cg_iters);
+  k_cg<T><<<1, CG_THREADS, in_smem ? bytes : 0, s>>>(p.n_cg, p.rowptr, p.col, p.val, p.fsrc, f, fI, p.uptr, p.udst,
+                                                     p.umaster, u, uI, work ? work : p.cg_work, rtol, maxit,
+                                                     p.cg_iters, in_smem ? 1 : 0);
   return cudaGetLastError();
 }
 
@@ -1930,13 +1966,17 @@ cudaError_t residual_to_f32(const LevelArgs& L, const ProbArgs& p, const double*
 
 cudaError_t add_correction(const LevelArgs& L, const ProbArgs& p, double* u, double* uI, const float* e,
                            const float* eI, cudaStream_t s) {
+  if (p.n_act > 0) {
+    const int64_t per = 256 * 8;
+    const unsigned gx = (unsigned)std::min<int64_t>((L.block / 2 + per - 1) / per, 4096);
+    ++g_kernel_launches;
+    k_add_corr_blocks<<<dim3(gx, (unsigned)p.n_act), 256, 0, s>>>(u, e, L.block, p.act);
+  }
   const int n = p.col_off[4];
-  const Units g = units(n, L.n_tiles_int, p.n_act);
-  if (g.total == 0) return cudaSuccess;
-  const unsigned grid = resident_grid((const void*)k_add_corr, g.total, p.grid_cap);
-  ++g_kernel_launches;
-  k_add_corr<<<grid, cta_shape(), 0, s>>>(L.N, L.rs, L.block, u, uI, e, eI, L.tiles_int, L.n_tiles_int, p.act,
-                                          p.n_act, L.cptr, L.cps, L.cp_off, p.free_if, n, g.n_if_units, p.sched);
+  if (n > 0) {
+    ++g_kernel_launches;
+    k_add_corr_masters<<<lin_grid(n, 256), 256, 0, s>>>(uI, eI, p.free_if, n);
+  }
   return cudaGetLastError();
 }
 
