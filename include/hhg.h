@@ -179,8 +179,9 @@ int hhg_inject_fault(hhg_mesh* mesh, const int* macro_ids, int n_ids, void* stre
  * Dirichlet problem A_FF u_F = f_F - A_FG u_G on Omega_F (Algorithm 1 step
  * a).  n_global = 0: local recovery (LR), Omega_I idles.  n_global > 0:
  * Dirichlet-Dirichlet recovery, n_global V-cycles of A_II u_I = f_I -
- * A_IG u_G on Omega_I with the interface frozen (step b) run concurrently on
- * a second stream.  If seconds_local / seconds_global are not NULL they
+ * A_IG u_G on Omega_I with the interface frozen (step b) run on the caller's
+ * stream concurrently with the Omega_F cycles, which run on a stream of the
+ * device's highest priority (forked from and joined back into `stream`).  If seconds_local / seconds_global are not NULL they
  * receive the device time of the two cycle sequences (synchronises).  With
  * n_local >= 2 the first Omega_F cycle runs directly and the others replay a
  * CUDA graph of one cycle, captured on the first such call for the fault set

@@ -113,7 +113,8 @@ struct hhg_mesh {
   double* dn_snap[2] = {nullptr, nullptr};
   cudaEvent_t ev_dn_e = nullptr, ev_dn_r[2] = {nullptr, nullptr};
   double* staging = nullptr;
-  cudaStream_t side = nullptr;
+  cudaStream_t side = nullptr;       // highest priority: the Omega_F side of a recovery
+  int prio_hi = 0;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   // one recovery cycle of the faulty problem captured as a CUDA graph and
   // replayed for the later cycles of a recovery (few macros, many small
@@ -681,6 +682,29 @@ int cycle(hhg_mesh* m, DevProblem& p, bool mixed, int pre, int post, double cg_r
   return vcycle_T<double>(m, m->d64, p, pre, post, cg_rtol, cg_maxit, s);
 }
 
+// Every kernel node of g runs at stream priority prio (the replayed local
+// cycles keep the high priority of the stream they were captured on).
+cudaError_t set_kernel_priority(cudaGraph_t g, int prio) {
+  size_t n = 0;
+  cudaError_t e = cudaGraphGetNodes(g, nullptr, &n);
+  if (e != cudaSuccess || n == 0) return e;
+  std::vector<cudaGraphNode_t> nodes(n);
+  e = cudaGraphGetNodes(g, nodes.data(), &n);
+  if (e != cudaSuccess) return e;
+  for (cudaGraphNode_t nd : nodes) {
+    cudaGraphNodeType t;
+    e = cudaGraphNodeGetType(nd, &t);
+    if (e != cudaSuccess) return e;
+    if (t != cudaGraphNodeTypeKernel) continue;
+    cudaKernelNodeAttrValue v;
+    std::memset(&v, 0, sizeof(v));
+    v.priority = prio;
+    e = cudaGraphKernelNodeSetAttribute(nd, cudaKernelNodeAttributePriority, &v);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
 void drop_local_graph(hhg_mesh* m) {
   if (m->local_exec) cudaGraphExecDestroy(m->local_exec);
   m->local_exec = nullptr;
@@ -715,6 +739,7 @@ int local_cycles(hhg_mesh* m, int n, bool mixed, int pre, int post, double cg_rt
     m->local_kernels = g_kernel_launches.load() - k0;
     g_kernel_launches -= m->local_kernels;
     if (ok) ok = cudaStreamEndCapture(m->cap, &g) == cudaSuccess && rc == HHG_OK && g;
+    if (ok) ok = set_kernel_priority(g, m->prio_hi) == cudaSuccess;
     if (ok) ok = cudaGraphInstantiate(&m->local_exec, g, 0) == cudaSuccess;
     if (g) cudaGraphDestroy(g);
     if (!ok) {
@@ -866,24 +891,30 @@ int inject(hhg_mesh* m, cudaStream_t s) {
   return HHG_OK;
 }
 
+// LR (n_global = 0): the Omega_F cycles on s.  DD: the Omega_F cycles on the
+// mesh's high-priority stream, forked from s, and the Omega_I cycles on s;
+// the block scheduler serves the small local kernels first, so Omega_F runs
+// ahead (the superman of §4.1) while Omega_I fills the rest of the GPU.
 int recover(hhg_mesh* m, int n_local, int n_global, bool mixed, int pre, int post, double cg_rtol, int cg_maxit,
             double* t_local, double* t_global, cudaStream_t s) {
   const bool timed = t_local || t_global;
   CallEvents ev;
   if (timed) HHG_CUDA(ev.create(4));
   cudaEvent_t a0 = ev.e[0], a1 = ev.e[1], b0 = ev.e[2], b1 = ev.e[3];
+  cudaStream_t ls = s;
   if (n_global > 0) {
+    ls = m->side;
     HHG_CUDA(cudaEventRecord(m->ev_fork, s));
-    HHG_CUDA(cudaStreamWaitEvent(m->side, m->ev_fork, 0));
+    HHG_CUDA(cudaStreamWaitEvent(ls, m->ev_fork, 0));
   }
-  if (timed) HHG_CUDA(cudaEventRecord(a0, s));
-  HHG_TRY(local_cycles(m, n_local, mixed, pre, post, cg_rtol, cg_maxit, s));
-  if (timed) HHG_CUDA(cudaEventRecord(a1, s));
+  if (timed) HHG_CUDA(cudaEventRecord(a0, ls));
+  HHG_TRY(local_cycles(m, n_local, mixed, pre, post, cg_rtol, cg_maxit, ls));
+  if (timed) HHG_CUDA(cudaEventRecord(a1, ls));
   if (n_global > 0) {
-    if (timed) HHG_CUDA(cudaEventRecord(b0, m->side));
-    for (int c = 0; c < n_global; ++c) HHG_TRY(cycle(m, m->healthy, mixed, pre, post, cg_rtol, cg_maxit, m->side));
-    if (timed) HHG_CUDA(cudaEventRecord(b1, m->side));
-    HHG_CUDA(cudaEventRecord(m->ev_join, m->side));
+    if (timed) HHG_CUDA(cudaEventRecord(b0, s));
+    for (int c = 0; c < n_global; ++c) HHG_TRY(cycle(m, m->healthy, mixed, pre, post, cg_rtol, cg_maxit, s));
+    if (timed) HHG_CUDA(cudaEventRecord(b1, s));
+    HHG_CUDA(cudaEventRecord(m->ev_join, ls));
     HHG_CUDA(cudaStreamWaitEvent(s, m->ev_join, 0));
   }
   if (timed) {
@@ -1266,8 +1297,16 @@ int setup_device(hhg_mesh* m) {
     if (rc == HHG_OK) rc = upload(m, &m->gen_copy_master, master);
   }
   if (rc != HHG_OK) return cleanup(rc);
-  if (cudaStreamCreateWithFlags(&m->side, cudaStreamNonBlocking) != cudaSuccess ||
-      cudaStreamCreateWithFlags(&m->cap, cudaStreamNonBlocking) != cudaSuccess ||
+  // the recovery's Omega_F side (and the capture of its cycle) run at the
+  // device's highest stream priority
+  int prio_lo = 0, prio_hi = 0;
+  if (cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi) != cudaSuccess) {
+    cudaGetLastError();
+    prio_hi = 0;
+  }
+  m->prio_hi = prio_hi;
+  if (cudaStreamCreateWithPriority(&m->side, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
+      cudaStreamCreateWithPriority(&m->cap, cudaStreamNonBlocking, prio_hi) != cudaSuccess ||
       cudaEventCreateWithFlags(&m->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
       cudaEventCreateWithFlags(&m->ev_join, cudaEventDisableTiming) != cudaSuccess ||
       cudaMallocHost(&m->host_scalar, sizeof(double) * 8) != cudaSuccess ||
