@@ -5,6 +5,7 @@
 // usage: layout_check N_max
 // Checks every refinement N = 2 .. N_max and N = 256, 512, and prints one
 // line per failed property (exit status 1), else "ok".
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -104,6 +105,98 @@ static void check_pair_tiles(int N, int target, int slabs) {
             target, slabs);
 }
 
+// The streaming Gauss-Seidel kernel (k_gs_stream) on refinement N with bands
+// of `band` rows and vectors of VW slots: every staged range (colour c+1
+// rows j0-1 .. j1+1 of slices k and k+1, colour c-1 of slices k-1 and k, f
+// rows j0 .. of slice k) fits one slot of the shared-memory ring and starts
+// and ends on 16 bytes; every neighbour read of every interior colour-c node
+// a unit updates lands, inside its staged range, on the right lattice node;
+// the one-slot shifts of the other lanes stay inside the padded buffer; and
+// the units update every interior node of every colour exactly once.  The
+// offset expressions are the kernel's.
+static int colour_first(int j, int k, int c) { return (c - 2 * j - 3 * k) & 3; }
+
+static void check_stream_tiles(int N, int band, int VW) {
+  std::vector<int> SL;
+  const int64_t block = build_slice_starts(N, SL);
+  (void)block;
+  std::vector<StreamTile> tiles;
+  build_stream_tiles(N, band, STREAM_SLICES, tiles);
+  const int M0 = N + 1;
+  const int slot = ((slot_prefix(M0) - slot_prefix(std::max(0, M0 - (band + 2)))) + 31) & ~31;
+  const int PAD = 32;
+  auto S = [](int m) { return slot_prefix(m); };
+  auto range = [&](int k, int ja, int jb, int& off, int& len) {
+    const int M = N + 1 - k;
+    jb = std::min(jb, N - k);
+    off = SL[k] + S(M) - S(M - ja);
+    len = jb >= ja ? S(M - ja) - S(M - jb - 1) : 0;
+  };
+  auto inner = [&](int i, int j, int k) { return lidx(SL.data(), N, i, j, k) - ((i + 2 * j + 3 * k) & 3) * SL[N + 2]; };
+  std::vector<unsigned char> hits((size_t)(N + 1) * (N + 1) * (N + 1), 0);
+  for (int c = 0; c < 4; ++c) {
+    std::fill(hits.begin(), hits.end(), 0);
+    for (const StreamTile& t : tiles) {
+      CHECK(t.ka >= 1 && t.kb <= N - 2 - t.j0 && t.kb - t.ka < STREAM_SLICES && t.j1 - t.j0 < band,
+            "unit (%d..%d, %d..%d)", t.j0, t.j1, t.ka, t.kb);
+      const int ja = t.j0 - 1, jbA = t.j1 + 1;
+      for (int k = t.ka; k <= t.kb; ++k) {
+        int oA0, lA0, oA1, lA1, oB0, lB0, oBm, lBm, oF, lF;
+        range(k, ja, jbA, oA0, lA0);
+        range(k + 1, ja, jbA, oA1, lA1);
+        range(k, ja, jbA, oB0, lB0);
+        range(k - 1, ja, jbA, oBm, lBm);
+        const int je = std::min(t.j1, N - 2 - k);
+        range(k, t.j0, je, oF, lF);
+        for (int len : {lA0, lA1, lBm, lF}) CHECK(len <= slot && len % 4 == 0, "staged range %d, slot %d", len, slot);
+        for (int off : {oA0, oA1, oBm, oF}) CHECK(off % 4 == 0, "staged range starts at %d", off);
+        const int M = N + 1 - k, M1 = N - k, Mm = N + 2 - k;
+        const int PA = S(M - ja), PA1 = S(M1 - ja), PAm = S(Mm - ja), PF = S(M - t.j0);
+        for (int j = t.j0; j <= je; ++j) {
+          const int ic = colour_first(j, k, c);
+          const int L = N - 1 - j - k;
+          const int mlo = ic == 0;
+          const int n = L >= ic ? ((L - ic) >> 2) - mlo + 1 : 0;
+          const int X = S(M - j);
+          const int groups = n > 0 ? (mlo + n - 1) / VW + 1 : 0;
+          for (int g = 0; g < groups; ++g) {
+            const int m0 = g * VW;
+            struct Rd { int off0, lo, len, shift_lo, shift_hi; } rd[7] = {
+                {PA - X, oA0, lA0, 0, ic == 3},               {PA - S(M - j - 1), oA0, lA0, -(ic == 0), 0},
+                {PA1 - S(M1 - j + 1), oA1, lA1, 0, 0},        {PA - X, oB0, lB0, -(ic == 0), 0},
+                {PA - S(M - j + 1), oB0, lB0, 0, ic == 3},    {PAm - S(Mm - j - 1), oBm, lBm, 0, 0},
+                {PF - X, oF, lF, 0, 0}};
+            for (const Rd& r : rd)
+              CHECK(r.off0 + m0 - 1 >= -PAD && r.off0 + m0 + VW < slot + PAD, "vector read outside the buffer");
+            const int lo = std::max(mlo - m0, 0), hi = std::min(mlo + n - m0, VW);
+            for (int q = lo; q < hi; ++q) {
+              const int m = m0 + q, i = 4 * m + ic;
+              CHECK(i >= 1 && i + j + k <= N - 1, "lane outside the interior");
+              CHECK(SL[k] + S(M) - X + m == inner(i, j, k), "store slot of (%d, %d, %d)", i, j, k);
+              const int nb[7][3] = {{i + 1, j, k}, {i - 1, j + 1, k}, {i, j - 1, k + 1}, {i - 1, j, k},
+                                    {i + 1, j - 1, k}, {i, j + 1, k - 1}, {i, j, k}};
+              const int sh[7] = {ic == 3, -(ic == 0), 0, -(ic == 0), ic == 3, 0, 0};
+              for (int d = 0; d < 7; ++d) {
+                const int e = rd[d].off0 + m + sh[d];
+                CHECK(e >= 0 && e < rd[d].len, "read %d of (%d, %d, %d) outside its range", d, i, j, k);
+                CHECK(rd[d].lo + e == inner(nb[d][0], nb[d][1], nb[d][2]), "read %d of (%d, %d, %d)", d, i, j, k);
+              }
+              unsigned char& h = hits[((size_t)k * (N + 1) + j) * (N + 1) + i];
+              CHECK(h == 0, "(%d, %d, %d) updated twice", i, j, k);
+              h = 1;
+            }
+          }
+        }
+      }
+    }
+    for (int k = 1; k <= N; ++k)
+      for (int j = 1; j + k <= N - 1; ++j)
+        for (int i = 1; i + j + k <= N - 1; ++i)
+          if (((i + 2 * j + 3 * k) & 3) == c)
+            CHECK(hits[((size_t)k * (N + 1) + j) * (N + 1) + i], "(%d, %d, %d) of colour %d not updated", i, j, k, c);
+  }
+}
+
 int main(int argc, char** argv) {
   if (argc < 2) return 2;
   const int n_max = std::atoi(argv[1]);
@@ -123,6 +216,12 @@ int main(int argc, char** argv) {
   for (int N : ns) {
     check_layout(N);
     for (const auto& c : cand) check_pair_tiles(N, c[0], c[1]);
+  }
+  // streaming units on the levels that have them (64 intervals and more),
+  // FP64 (two slots per vector) and FP32 (four) bands
+  for (int N : {64, 128, 256, 512}) {
+    check_stream_tiles(N, N >= 512 ? STREAM_BAND / 2 : STREAM_BAND, 2);
+    check_stream_tiles(N, N >= 512 ? STREAM_BAND32 / 2 : STREAM_BAND32, 4);
   }
   if (failures) {
     std::printf("%d failures\n", failures);

@@ -4,7 +4,11 @@ its colour's array, rows start on 16-byte boundaries and the neighbour-row
 offsets the vector kernels use hold; the slot-prefix closed form equals its
 definition; the row-pair tiles of the volume kernels (default and autotuner
 candidates) cover every interior row of every slice exactly once, within the
-kernels' per-tile table sizes, largest first.  Refinements 2..130, 256, 512."""
+kernels' per-tile table sizes, largest first.  Refinements 2..130, 256, 512.
+The streaming Gauss-Seidel units (refinements 64..512, FP64 and FP32 bands):
+staged ranges fit the shared-memory slots, every neighbour read of every
+updated node lands on the right lattice node inside its staged range, and
+every interior node of every colour is updated exactly once."""
 
 import os
 import shutil
