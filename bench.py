@@ -26,7 +26,8 @@ same workload (fault-free, do-nothing, LR, DN, mixed precision), the eta the
 concurrent recoveries achieve, a per-phase breakdown of the cycles, and three
 separate workloads: the cube refined 9 levels in FP64 and in mixed precision
 (time to 1e-8 with a fault), the batched recovery of 64 sub-domains next to a
-global solve, and a forward + adjoint solve of 384 macros refined 7 levels.
+global solve, a forward + adjoint solve of 384 macros refined 7 levels, and a
+sheared cube (15-point stencils) refined 8 levels.
 """
 
 from __future__ import annotations
@@ -443,7 +444,7 @@ def run_ours(args):
         del f_dev, u0_dev, f_pin, u0_pin, u_pin
         torch.cuda.empty_cache()
         for name, fn in (("precision_r9", extra_precision_r9), ("batch", extra_batch),
-                         ("differentiation", extra_grad)):
+                         ("differentiation", extra_grad), ("fifteen_point", extra_fifteen_point)):
             t = time.perf_counter()
             try:
                 variants[name] = fn(torch, hhg, I)
@@ -618,6 +619,48 @@ def batch_workload(torch, hhg, I, warmup, steps):
     lat = ms[:, :-1].ravel()
     total = ms.max(axis=1)
 
+    def event_ms(launch):
+        G.set_problem(None, gu0)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        launch(timed=False, stream=torch.cuda.current_stream())
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    graph_event = [event_ms(batch.launch) for _ in range(steps)]
+    # the same work as one launch of the persistent scheduler kernel
+    for _ in range(warmup):
+        batch.launch_persistent()
+    pruns = []
+    for _ in range(steps):
+        G.set_problem(None, gu0)
+        torch.cuda.synchronize()
+        pruns.append(batch.launch_persistent())
+    pm = np.array(pruns)
+    pers_event = [event_ms(batch.launch_persistent) for _ in range(steps)]
+    n_tasks, n_ops, n_units, n_kernels = batch.info()
+
+    def persistent_with(prio):
+        batch.set_priority(prio)
+        batch.launch_persistent()
+        r = []
+        for _ in range(steps):
+            G.set_problem(None, gu0)
+            torch.cuda.synchronize()
+            r.append(batch.launch_persistent())
+        batch.set_priority(None)
+        r = np.array(r)
+        return {"total_ms_median": float(np.median(r.max(axis=1))),
+                "latency_ms_p50": float(np.percentile(r[:, :-1].ravel(), 50)),
+                "latency_ms_p99": float(np.percentile(r[:, :-1].ravel(), 99))}
+
+    # the global task (the longest) in the higher class, then the recovery
+    # tasks in the higher class (superman-style)
+    pers_global_first = persistent_with([0] * (n_tasks - 1) + [1])
+    pers_recovery_first = persistent_with([1] * (n_tasks - 1) + [0])
+
     def plain():
         torch.cuda.synchronize()
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -640,6 +683,14 @@ def batch_workload(torch, hhg, I, warmup, steps):
            "plain_fp64_sequential_ms": float(np.median([r[0] for r in plain_runs])),
            "plain_fp64_global_cycles": plain_runs[0][1]}
     res["speedup_vs_plain_fp64"] = res["plain_fp64_sequential_ms"] / res["total_ms_median"]
+    res["graph_launch_event_ms"] = float(np.median(graph_event))
+    res["graph_kernels"] = n_kernels
+    res["persistent"] = {"launch_event_ms": float(np.median(pers_event)),
+                         "total_ms_median": float(np.median(pm.max(axis=1))),
+                         "latency_ms_p50": float(np.percentile(pm[:, :-1].ravel(), 50)),
+                         "latency_ms_p99": float(np.percentile(pm[:, :-1].ravel(), 99)),
+                         "operations": n_ops, "work_units": n_units, "kernel_launches": 1,
+                         "global_task_first": pers_global_first, "recovery_tasks_first": pers_recovery_first}
     batch.close()
     for M, _, _ in tasks:
         M.close()
@@ -649,6 +700,40 @@ def batch_workload(torch, hhg, I, warmup, steps):
 
 def extra_batch(torch, hhg, I):
     return batch_workload(torch, hhg, I, warmup=1, steps=3)
+
+
+SHEAR = [[1.0, 0.3, -0.2], [0.1, 0.9, 0.25], [-0.15, 0.2, 1.1]]
+
+
+def extra_fifteen_point(torch, hhg, I):
+    """The 15-point kernels: the same cube refined 8 levels under a shear
+    (every macro a general tetrahedron, all 15 stencil weights non-zero),
+    fault-free FP64 solve to 1e-8; the finest-level Gauss-Seidel launch timed
+    with CUDA events (29 flop per node update: 14 FMA and the scaling)."""
+    M = hhg.Mesh(SUB, R, affine=SHEAR)
+    f = torch.from_numpy(I.random_load(SUB, R, SEED)).cuda()
+    u0 = torch.zeros_like(f)
+    M.set_problem(f, u0)
+    n_vol, seven = hhg.hhg_profile_info(M.h)
+    stream = torch.cuda.current_stream()
+    M.solve(rtol=RTOL, max_cycles=MAX_CYCLES)
+    M.set_problem(None, u0)
+    hhg.hhg_profile_enable(M.h, 1)
+    ms, (hist, cyc, _) = _events_ms(torch, stream, lambda: M.solve(rtol=RTOL, max_cycles=MAX_CYCLES))
+    n, gs_ms = hhg.hhg_profile_read(M.h)
+    hhg.hhg_profile_enable(M.h, 0)
+    avg = gs_ms / max(n, 1) * 1e-3
+    peak = hhg.hhg_measure_fp64_peak()
+    tflops = (2 * 14 + 1) * n_vol / 4.0 / avg / 1e12
+    res = {"workload": "cube 2x2x2x6 macro-tets refined 8 levels under a shear (15-point stencils), random load "
+                       "seed 0, fault-free FP64 solve to 1e-8",
+           "seven_point": bool(seven), "ms": ms, "cycles": cyc, "final_rel_res": float(hist[-1]),
+           "gs_roofline": {"kernel": "k_gs<double, 15-point> finest level, one colour", "launches": n,
+                           "avg_launch_ms": avg * 1e3, "bound": "alu", "achieved_tflops": tflops,
+                           "peak_tflops": peak, "frac": tflops / peak,
+                           "hbm_gbs": 24.0 * n_vol / 4.0 / avg / 1e9}}
+    M.close()
+    return res
 
 
 def extra_grad(torch, hhg, I):

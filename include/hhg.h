@@ -261,8 +261,9 @@ int hhg_solve(hhg_mesh* mesh, const hhg_solve_opts* opts, double* hist, int* n_h
 /* Differentiation support (an extension of the method of §2.1 to a
  * per-macro diffusion coefficient k_T, A = sum_T k_T A_T).
  * hhg_set_coefficients: replace the coefficients (host, n_macro positive
- * values) and rebuild every level's stencils and the coarse CG matrices; the
- * iterate and right-hand side are kept.  Synchronises the stream.
+ * values) and rebuild every level's stencils, interface tables and the coarse
+ * CG matrices (nothing to rebuild when the values equal the current ones);
+ * the iterate and right-hand side are kept.  Synchronises the stream.
  * hhg_grad_coeff: with u a solution (global vector with its Dirichlet
  * values) and lam the adjoint solution of A_FF lam = dL/du_F (zero on the
  * Dirichlet nodes), write dL/dk_T = -lam^T A_T u for every macro into grad
@@ -301,6 +302,39 @@ int hhg_batch_create(hhg_mesh* global, int global_cycles, hhg_mesh* const* meshe
                      const int* n_ids, const int* cycles, int n_tasks, int mixed, hhg_batch** out);
 int hhg_batch_launch(hhg_batch* batch, double* task_ms, void* stream);
 int hhg_batch_destroy(hhg_batch* batch);
+
+/* The same batch as ONE kernel launch: a persistent scheduler kernel (as
+ * many CTAs as the GPU holds at once) runs every task's operations in their
+ * stream order.  Creation records each task's program -- every launch the
+ * graph makes (Gauss-Seidel colours, residuals, transfers, the coarse CG, the
+ * fault's zeroing and restoring, the FP32/FP64 hand-over), with its work
+ * units -- and uploads it.  The launch resets the scheduler's counters (two
+ * memsets on stream) and starts the kernel.  A CTA takes the next unit of
+ * the current operation of some task; a task advances to its next operation
+ * when all units of the current one are done, so the tasks share the GPU
+ * unit by unit instead of by stream.  The results are bit for bit those of
+ * hhg_batch_launch (the per-unit arithmetic is the same).  task_ms (may be
+ * NULL; n_tasks + 1 doubles as in hhg_batch_launch) synchronises stream and
+ * receives each task's completion time in ms after the first CTA started
+ * (device global timer).  A kernel that found no work to take for longer than
+ * the first task mesh's wait limit (hhg_set_wait_limit) stops and the timed
+ * launch returns HHG_ERR_TIMEOUT; an untimed launch reports it on the next
+ * timed one.  Needs the batch's device current. */
+int hhg_batch_launch_persistent(hhg_batch* batch, double* task_ms, void* stream);
+
+/* Priorities of the persistent launch's tasks: prio[t] for t < n_tasks (the
+ * global task last, when present), or NULL for all equal (the default).  A
+ * CTA looking for work takes it from the highest class that has some; within
+ * a class it stays with the task it served last.  Giving the recovery tasks
+ * the higher class lets them run ahead, as with §4.1's superman (shorter
+ * latency per recovered sub-domain); giving the longest task the higher
+ * class shortens the whole batch.  Results do not depend on the priorities.
+ * Synchronises the device. */
+int hhg_batch_set_priority(hhg_batch* batch, const int* prio);
+
+/* info[0..4): tasks, recorded operations, work units over all operations,
+ * kernels in the graph of hhg_batch_launch. */
+int hhg_batch_info(hhg_batch* batch, int64_t* info);
 
 /* Allocation-free V-cycle (an interface addition; the paper has no
  * counterpart).  Some callers cannot call cudaMalloc at all once they are

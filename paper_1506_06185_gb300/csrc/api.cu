@@ -151,6 +151,7 @@ struct hhg_mesh {
   std::vector<cudaEvent_t> bd_ev;
   std::vector<int> bd_cat;
   size_t bd_used = 0;
+  bool coeff_dirty = false;   // host coefficients changed, device stencils not yet
   // profiling of the finest-level Gauss-Seidel volume kernel of the global problem
   bool prof_on = false;
   std::vector<cudaEvent_t> prof_ev;
@@ -172,6 +173,20 @@ struct hhg_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   long long kernels = 0;  // kernels in the graph
+  // persistent executor (hhg_batch_launch_persistent): every task's
+  // operations in order, run by one launch of the scheduler kernel
+  std::vector<BOp> ops;
+  std::vector<int> op_off;               // task t: ops [op_off[t], op_off[t + 1])
+  BOp* d_ops = nullptr;
+  int* d_op_off = nullptr;
+  int* d_state = nullptr;                // phase[n] | issued[n_ops] | done[n_ops] | tasks_done
+  size_t state_bytes = 0;
+  unsigned long long* d_ns = nullptr;    // start | completion of task t (globaltimer ns)
+  int* d_err = nullptr;
+  int* d_order = nullptr;                // tasks by priority class, highest first
+  int* d_seg = nullptr;                  // class c: d_order[d_seg[c] .. d_seg[c + 1])
+  int n_seg = 1;
+  int wait_limit = 1 << 24;
 };
 
 namespace {
@@ -885,7 +900,7 @@ int inject(hhg_mesh* m, cudaStream_t s) {
   const int L = (int)m->host.lv.size() - 1;
   DevLevel<double>& D = m->d64.lv[L];
   for (int t = 0; t < m->host.n_macro; ++t)
-    if (m->fault_set[t]) HHG_CUDA(cudaMemsetAsync(D.u + (size_t)t * D.block, 0, D.block * sizeof(double), s));
+    if (m->fault_set[t]) HHG_CUDA(memset16(D.u + (size_t)t * D.block, D.block * sizeof(double), s));
   HHG_CUDA(set_masters_zero(D.uI, m->fault_zero_ids, m->n_fault_zero, s));
   HHG_CUDA(restore_copies(D.u, D.uI, m->fault_restore_off, m->fault_restore_master, m->n_fault_restore, s));
   return HHG_OK;
@@ -1169,6 +1184,78 @@ int capture_task(hhg_mesh* m, int cycles, bool recovery, bool mixed, cudaStream_
     for (int c = 0; c < cycles; ++c) HHG_TRY(cycle(m, m->global, mixed, 3, 3, 1e-12, 1000, s));
   }
   return HHG_OK;
+}
+
+// The operations of one task as the persistent executor runs them: while
+// recording, the launchers append the launch they would make (its kind,
+// arguments and number of work units) to `out` and launch nothing.  The
+// profiling hooks are off meanwhile (they would record events).
+int record_task(hhg_mesh* m, int cycles, bool recovery, bool mixed, std::vector<BOp>& out) {
+  const bool prof = m->prof_on, bd = m->bd_on;
+  m->prof_on = m->bd_on = false;
+  record_ops(&out);
+  const int rc = capture_task(m, cycles, recovery, mixed, nullptr);
+  record_ops(nullptr);
+  m->prof_on = prof;
+  m->bd_on = bd;
+  return rc;
+}
+
+void free_persistent(hhg_batch* b) {
+  for (void* q : {(void*)b->d_ops, (void*)b->d_op_off, (void*)b->d_state, (void*)b->d_ns, (void*)b->d_err,
+                  (void*)b->d_order, (void*)b->d_seg})
+    if (q) cudaFree(q);
+  b->d_order = nullptr;
+  b->d_seg = nullptr;
+  b->d_ops = nullptr;
+  b->d_op_off = nullptr;
+  b->d_state = nullptr;
+  b->d_ns = nullptr;
+  b->d_err = nullptr;
+}
+
+// Priority classes of the persistent executor: the tasks ordered by
+// decreasing priority (ties in task order), one class per distinct value.
+int upload_priorities(hhg_batch* b, const std::vector<int>& prio) {
+  const int n = (int)prio.size();
+  std::vector<int> order(n), seg;
+  for (int t = 0; t < n; ++t) order[t] = t;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int c) { return prio[a] > prio[c]; });
+  for (int q = 0; q < n; ++q)
+    if (q == 0 || prio[order[q]] != prio[order[q - 1]]) seg.push_back(q);
+  seg.push_back(n);
+  b->n_seg = (int)seg.size() - 1;
+  if (n > 0) HHG_CUDA(cudaMemcpy(b->d_order, order.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+  HHG_CUDA(cudaMemcpy(b->d_seg, seg.data(), seg.size() * sizeof(int), cudaMemcpyHostToDevice));
+  return HHG_OK;
+}
+
+// Records every task's program and uploads it with the scheduler's counters.
+int setup_persistent(hhg_batch* b, size_t n_rec) {
+  b->op_off.assign(1, 0);
+  for (size_t t = 0; t < b->tasks.size(); ++t) {
+    HHG_TRY(record_task(b->tasks[t].mesh, b->tasks[t].cycles, t < n_rec, b->mixed, b->ops));
+    b->op_off.push_back((int)b->ops.size());
+  }
+  const size_t n = b->tasks.size(), n_ops = b->ops.size();
+  b->state_bytes = (n + 2 * n_ops + 1) * sizeof(int);
+  auto alloc = [&](void** q, size_t bytes) {
+    const cudaError_t e = cudaMalloc(q, std::max<size_t>(bytes, 16));
+    if (e != cudaSuccess) cudaGetLastError();
+    return e;
+  };
+  if (alloc((void**)&b->d_ops, n_ops * sizeof(BOp)) != cudaSuccess ||
+      alloc((void**)&b->d_op_off, (n + 1) * sizeof(int)) != cudaSuccess ||
+      alloc((void**)&b->d_state, b->state_bytes) != cudaSuccess ||
+      alloc((void**)&b->d_ns, (n + 1) * sizeof(unsigned long long)) != cudaSuccess ||
+      alloc((void**)&b->d_err, sizeof(int)) != cudaSuccess || alloc((void**)&b->d_order, n * sizeof(int)) != cudaSuccess ||
+      alloc((void**)&b->d_seg, (n + 1) * sizeof(int)) != cudaSuccess)
+    return fail(HHG_ERR_OOM, "allocation of the persistent executor's program failed");
+  if (n_ops) HHG_CUDA(cudaMemcpy(b->d_ops, b->ops.data(), n_ops * sizeof(BOp), cudaMemcpyHostToDevice));
+  HHG_CUDA(cudaMemcpy(b->d_op_off, b->op_off.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice));
+  HHG_CUDA(cudaMemset(b->d_err, 0, sizeof(int)));
+  if (!b->tasks.empty()) b->wait_limit = b->tasks[0].mesh->global.wait_limit;
+  return upload_priorities(b, std::vector<int>(n, 0));
 }
 
 // ---------------------------------------------------------------------------
@@ -1534,7 +1621,13 @@ int hhg_set_coefficients(hhg_mesh* m, const double* coeff, void* stream) {
   for (int t = 0; t < m->host.n_macro; ++t)
     if (!(coeff[t] > 0.0)) return fail(HHG_ERR_ARG, "coefficients must be positive");
   HHG_CUDA(cudaStreamSynchronize((cudaStream_t)stream));
-  return update_coefficients(m, coeff);
+  // the same coefficients again (an adjoint solve after its forward solve):
+  // the stencils, tables and coarse matrices already hold them
+  if (!m->coeff_dirty && std::equal(coeff, coeff + m->host.n_macro, m->host.coeff.begin())) return HHG_OK;
+  m->coeff_dirty = true;   // until the device holds them (a failed update is redone)
+  HHG_TRY(update_coefficients(m, coeff));
+  m->coeff_dirty = false;
+  return HHG_OK;
 }
 
 int hhg_grad_coeff(hhg_mesh* m, const double* u, const double* lam, double* grad, void* stream) {
@@ -1623,6 +1716,7 @@ int hhg_batch_create(hhg_mesh* global, int global_cycles, hhg_mesh* const* meshe
     if (b->start) cudaEventDestroy(b->start);
     if (b->fork) cudaEventDestroy(b->fork);
     if (b->graph) cudaGraphDestroy(b->graph);
+    free_persistent(b.get());
     return rc;
   };
   if (cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking) != cudaSuccess ||
@@ -1676,6 +1770,11 @@ int hhg_batch_create(hhg_mesh* global, int global_cycles, hhg_mesh* const* meshe
   b->graph = g;
   if (cudaGraphInstantiate(&b->exec, b->graph, 0) != cudaSuccess)
     return cleanup(fail(HHG_ERR_CUDA, "cudaGraphInstantiate failed"));
+  rc = setup_persistent(b.get(), n_rec);
+  if (rc != HHG_OK) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    return cleanup(rc);
+  }
   // the graph holds the meshes' buffers: a new fault set may not free them
   for (auto& t : b->tasks) ++t.mesh->batch_refs;
   *out = b.release();
@@ -1699,9 +1798,67 @@ int hhg_batch_launch(hhg_batch* b, double* task_ms, void* stream) {
   return HHG_OK;
 }
 
+int hhg_batch_launch_persistent(hhg_batch* b, double* task_ms, void* stream) {
+  if (!b) return fail(HHG_ERR_ARG, "null batch");
+  if (b->tasks.empty()) return HHG_OK;
+  HHG_TRY(check_device(b->tasks[0].mesh));
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = (int)b->tasks.size();
+  const int n_ops = (int)b->ops.size();
+  HHG_CUDA(cudaMemsetAsync(b->d_state, 0, b->state_bytes, s));
+  HHG_CUDA(cudaMemsetAsync(b->d_ns, 0xff, sizeof(unsigned long long), s));   // start: atomicMin over the CTAs
+  BatchState st;
+  st.phase = b->d_state;
+  st.issued = b->d_state + n;
+  st.done = b->d_state + n + n_ops;
+  st.tasks_done = b->d_state + n + 2 * n_ops;
+  st.start_ns = b->d_ns;
+  st.task_ns = b->d_ns + 1;
+  int n_live = 0;
+  for (int t = 0; t < n; ++t) n_live += b->op_off[t + 1] > b->op_off[t] ? 1 : 0;
+  HHG_CUDA(run_batch(b->d_ops, b->d_op_off, b->d_order, b->d_seg, b->n_seg, n_live, st, b->wait_limit, b->d_err, s));
+  if (task_ms) {
+    std::vector<unsigned long long> ns(n + 1);
+    int err = 0;
+    HHG_CUDA(cudaMemcpyAsync(ns.data(), b->d_ns, (n + 1) * sizeof(unsigned long long), cudaMemcpyDeviceToHost, s));
+    HHG_CUDA(cudaMemcpyAsync(&err, b->d_err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    HHG_CUDA(cudaStreamSynchronize(s));
+    if (err != 0) {
+      HHG_CUDA(cudaMemsetAsync(b->d_err, 0, sizeof(int), s));
+      HHG_CUDA(cudaStreamSynchronize(s));
+      return fail(HHG_ERR_TIMEOUT, "the persistent batch found no work for longer than its wait limit");
+    }
+    for (int t = 0; t < n; ++t)
+      task_ms[t] = b->op_off[t + 1] > b->op_off[t] ? (double)(ns[t + 1] - ns[0]) * 1e-6 : 0.0;
+  }
+  return HHG_OK;
+}
+
+int hhg_batch_set_priority(hhg_batch* b, const int* prio) {
+  if (!b) return fail(HHG_ERR_ARG, "null batch");
+  if (b->tasks.empty()) return HHG_OK;
+  HHG_TRY(check_device(b->tasks[0].mesh));
+  std::vector<int> p(b->tasks.size(), 0);
+  if (prio) p.assign(prio, prio + b->tasks.size());
+  HHG_CUDA(cudaDeviceSynchronize());   // no launch may still read the old order
+  return upload_priorities(b, p);
+}
+
+int hhg_batch_info(hhg_batch* b, int64_t* info) {
+  if (!b || !info) return fail(HHG_ERR_ARG, "invalid argument");
+  int64_t units = 0;
+  for (const BOp& op : b->ops) units += op.n_units;
+  info[0] = (int64_t)b->tasks.size();
+  info[1] = (int64_t)b->ops.size();
+  info[2] = units;
+  info[3] = b->kernels;
+  return HHG_OK;
+}
+
 int hhg_batch_destroy(hhg_batch* b) {
   if (!b) return HHG_OK;
   cudaDeviceSynchronize();
+  free_persistent(b);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   for (auto& t : b->tasks) {

@@ -3,6 +3,8 @@
 // iterative refinement).
 #pragma once
 
+#include <vector>
+
 #include "hhg_internal.h"
 
 namespace hhg {
@@ -146,6 +148,88 @@ cudaError_t add_correction(const LevelArgs& L, const ProbArgs& p, double* u, dou
                            const float* eI, cudaStream_t s);
 template <class T>
 cudaError_t zero_problem_blocks(const LevelArgs& L, const ProbArgs& p, T* u, T* uI, cudaStream_t s);
+
+// ---------------------------------------------------------------------------
+// Persistent batch executor (kernels.cu).  A program is the list of the
+// level-wide operations one task issues (fault injection, Gauss-Seidel
+// colours, residuals, transfers, coarse CG, the FP64/FP32 hand-over of
+// iterative refinement), each split into the work units its kernel would
+// walk.  While a recording is open, the launchers of this header append an
+// operation instead of launching; run_batch then executes the programs of
+// many tasks in one launch.
+// ---------------------------------------------------------------------------
+enum BOpKind : int {
+  BOP_GS, BOP_RES, BOP_RESTRICT, BOP_PROLONG, BOP_CG, BOP_ZERO_BLOCKS, BOP_ZERO_LIST, BOP_RES_F32,
+  BOP_ADD_BLOCKS, BOP_ADD_MASTERS, BOP_MEMSET, BOP_SET_ZERO, BOP_RESTORE
+};
+
+struct BOp {
+  int kind;            // BOpKind
+  int fp32;            // arithmetic type of the arrays: 1 float, 0 double
+  int n_units;
+  int n_if_units;      // interface chunks, first (GS, RES, RESTRICT, PROLONG, RES_F32)
+  int seven_point, scaled, colour, skip, skip_lo, skip_hi;
+  LevelArgs L;         // the level (the fine one of a transfer)
+  LevelArgs C;         // the coarse level of a transfer
+  ProbArgs P;          // the problem on L (on C for a restriction)
+  int list_off;        // first entry of P.free_if the operation walks
+  int n_list;
+  int n_zero;          // frozen copies zeroed after the list (RES, RESTRICT)
+  // arrays (float or double by fp32; FP64 + FP32 for the hand-over)
+  void* u;
+  void* uI;
+  const void* f;
+  const void* fI;
+  void* r;
+  const void* W;       // stencil weights (interface sub-stencils)
+  const void* Wv;      // the volume's weights (GS: divided by the centre weight when scaled)
+  const void* Winv;
+  void* fc;
+  void* fIc;
+  void* uc;
+  void* uIc;
+  void* o32;           // RES_F32 output, ADD_* correction (FP32)
+  void* oI32;
+  int64_t n;           // element count (ZERO_LIST, MEMSET in 16-byte words, SET_ZERO, RESTORE, ADD_MASTERS)
+  const int* ids;      // ZERO_LIST, SET_ZERO, ADD_MASTERS: index list; RESTORE: master per copy
+  const int64_t* offs; // RESTORE: block offsets
+  // coarse CG (level 0 of the problem)
+  int n_cg;
+  const int* rowptr;
+  const int* col;
+  const double* val;
+  const int64_t* fsrc;
+  const int* uptr;
+  const int64_t* udst;
+  const int* umaster;
+  double* work;
+  int* iters;
+  double rtol;
+  int maxit;
+};
+
+// While rec != null the launchers append to *rec instead of launching.
+void record_ops(std::vector<BOp>* rec);
+bool recording();
+// Zero `bytes` bytes at p (a multiple of 16; recorded as BOP_MEMSET).
+cudaError_t memset16(void* p, size_t bytes, cudaStream_t s);
+// Runs the programs ops[op_off[t] .. op_off[t + 1]) of the tasks in one
+// launch (grid = resident CTAs).  order[seg[c] .. seg[c + 1]) lists the
+// tasks of priority class c (n_seg classes, highest first; every task in
+// exactly one class); n_live tasks have at least one operation.  The
+// counters (phase per task, issued and done per operation, tasks done) must
+// be zero and *start_ns ~0 before the launch.  task_ns[t] receives the
+// global timer when task t finished, *start_ns the earliest start.
+struct BatchState {
+  int* phase;
+  int* issued;
+  int* done;
+  int* tasks_done;
+  unsigned long long* start_ns;
+  unsigned long long* task_ns;
+};
+cudaError_t run_batch(const BOp* ops, const int* op_off, const int* order, const int* seg, int n_seg, int n_live,
+                      const BatchState& st, int wait_limit, int* err, cudaStream_t s);
 
 // Macro meshes of general connectivity (general.cu).  Global vectors list
 // the interface nodes first (their masters move with import_masters /

@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstring>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -374,13 +375,16 @@ __device__ __forceinline__ T if_offdiag(const IfTab<T>& t, const T* __restrict__
 // 16-byte vectors of a row: 4 FP32 or 2 FP64 consecutive slots.
 template <class T>
 struct Vec;
-// load() goes through the read-only path: a Gauss-Seidel colour kernel reads
-// only arrays it does not write (the other colours and f).
+// load<true>() goes through the read-only path: a Gauss-Seidel colour
+// kernel reads only arrays it does not write (the other colours and f).
+// load<false>() is a plain coherent load, for code that reads data written
+// earlier in the same launch (the persistent batch executor).
 template <>
 struct Vec<float> {
   static constexpr int n = 4;
+  template <bool NC = true>
   __device__ static void load(const float* p, float* v) {
-    const float4 q = __ldg(reinterpret_cast<const float4*>(p));
+    const float4 q = NC ? __ldg(reinterpret_cast<const float4*>(p)) : *reinterpret_cast<const float4*>(p);
     v[0] = q.x;
     v[1] = q.y;
     v[2] = q.z;
@@ -393,8 +397,9 @@ struct Vec<float> {
 template <>
 struct Vec<double> {
   static constexpr int n = 2;
+  template <bool NC = true>
   __device__ static void load(const double* p, double* v) {
-    const double2 q = __ldg(reinterpret_cast<const double2*>(p));
+    const double2 q = NC ? __ldg(reinterpret_cast<const double2*>(p)) : *reinterpret_cast<const double2*>(p);
     v[0] = q.x;
     v[1] = q.y;
   }
@@ -405,17 +410,17 @@ struct Vec<double> {
 
 // Slots m0 + s .. m0 + s + VW - 1 (s = +1 when up, -1 when dn, else 0) of a
 // row, from the aligned vector at p = &row[m0] and one extra element.
-template <class T>
+template <class T, bool NC = true>
 __device__ __forceinline__ void load_shifted(const T* __restrict__ p, bool up, bool dn, T* v) {
   constexpr int VW = Vec<T>::n;
-  Vec<T>::load(p, v);
+  Vec<T>::template load<NC>(p, v);
   if (up) {
-    const T e = __ldg(p + VW);
+    const T e = NC ? __ldg(p + VW) : p[VW];
 #pragma unroll
     for (int t = 0; t < VW - 1; ++t) v[t] = v[t + 1];
     v[VW - 1] = e;
   } else if (dn) {
-    const T e = __ldg(p - 1);
+    const T e = NC ? __ldg(p - 1) : p[-1];
 #pragma unroll
     for (int t = VW - 1; t > 0; --t) v[t] = v[t - 1];
     v[0] = e;
@@ -428,7 +433,7 @@ __device__ __forceinline__ void load_shifted(const T* __restrict__ p, bool up, b
 // them are written.  SCALED: the weights w and the load fb are already divided
 // by the centre weight (u = f~ - sum w~ u, six FMAs per node), else the sum is
 // multiplied by inv, the inverse centre weight.
-template <class T, bool SCALED>
+template <class T, bool SCALED, bool NC = true>
 __device__ __forceinline__ void gs_group7(const Slice& sc, int N, int j, int g, int c, T* __restrict__ ub,
                                           const T* __restrict__ fb, const T* __restrict__ w, T inv) {
   constexpr int VW = Vec<T>::n;
@@ -445,23 +450,23 @@ __device__ __forceinline__ void gs_group7(const Slice& sc, int N, int j, int g, 
   const int cc = c * sc.CS, cp = ((c + 1) & 3) * sc.CS, cm = ((c + 3) & 3) * sc.CS;
   const bool e1 = ic == 3, e0 = ic == 0;         // slot of i + 1 is m + e1, of i - 1 is m - e0
   T acc[VW], a[VW];
-  Vec<T>::load(fb + cc + r0 + m0, acc);
-  load_shifted(ub + cp + r0 + m0, e1, false, a);    // ( 1,  0,  0)
+  Vec<T>::template load<NC>(fb + cc + r0 + m0, acc);
+  load_shifted<T, NC>(ub + cp + r0 + m0, e1, false, a);    // ( 1,  0,  0)
 #pragma unroll
   for (int t = 0; t < VW; ++t) acc[t] -= w[1] * a[t];
-  load_shifted(ub + cp + rjp + m0, false, e0, a);   // (-1,  1,  0)
+  load_shifted<T, NC>(ub + cp + rjp + m0, false, e0, a);   // (-1,  1,  0)
 #pragma unroll
   for (int t = 0; t < VW; ++t) acc[t] -= w[2] * a[t];
-  Vec<T>::load(ub + cp + rkp + m0, a);              // ( 0, -1,  1)
+  Vec<T>::template load<NC>(ub + cp + rkp + m0, a);              // ( 0, -1,  1)
 #pragma unroll
   for (int t = 0; t < VW; ++t) acc[t] -= w[3] * a[t];
-  load_shifted(ub + cm + r0 + m0, false, e0, a);    // (-1,  0,  0)
+  load_shifted<T, NC>(ub + cm + r0 + m0, false, e0, a);    // (-1,  0,  0)
 #pragma unroll
   for (int t = 0; t < VW; ++t) acc[t] -= w[8] * a[t];
-  load_shifted(ub + cm + rjm + m0, e1, false, a);   // ( 1, -1,  0)
+  load_shifted<T, NC>(ub + cm + rjm + m0, e1, false, a);   // ( 1, -1,  0)
 #pragma unroll
   for (int t = 0; t < VW; ++t) acc[t] -= w[9] * a[t];
-  Vec<T>::load(ub + cm + rkm + m0, a);              // ( 0,  1, -1)
+  Vec<T>::template load<NC>(ub + cm + rkm + m0, a);              // ( 0,  1, -1)
 #pragma unroll
   for (int t = 0; t < VW; ++t) {
     if (SCALED) acc[t] -= w[10] * a[t];         // weights and f already divided by the centre weight
@@ -497,7 +502,7 @@ __device__ __forceinline__ void store_lanes(T* __restrict__ out, const T* acc, i
   }
 }
 
-template <class T, bool WRITE, bool NORM, bool ZERO = false>
+template <class T, bool WRITE, bool NORM, bool ZERO = false, bool NC = true>
 __device__ __forceinline__ void res_group7(const Slice& sc, int N, int j, int g, int c, const T* __restrict__ ub,
                                            const T* __restrict__ fb, T* __restrict__ rb, const T* __restrict__ w,
                                            double& ss) {
@@ -521,26 +526,26 @@ __device__ __forceinline__ void res_group7(const Slice& sc, int N, int j, int g,
     if (WRITE) store_lanes(rb + cc + r0 + m0, acc, max(mlo - m0, 0), min(mlo + n - m0, VW));
     return;
   }
-  Vec<T>::load(fb + cc + r0 + m0, acc);
-  Vec<T>::load(ub + cc + r0 + m0, a);               // centre
+  Vec<T>::template load<NC>(fb + cc + r0 + m0, acc);
+  Vec<T>::template load<NC>(ub + cc + r0 + m0, a);               // centre
 #pragma unroll
   for (int t = 0; t < VW; ++t) acc[t] -= w[0] * a[t];
-  load_shifted(ub + cp + r0 + m0, e1, false, a);    // ( 1,  0,  0)
+  load_shifted<T, NC>(ub + cp + r0 + m0, e1, false, a);    // ( 1,  0,  0)
 #pragma unroll
   for (int t = 0; t < VW; ++t) acc[t] -= w[1] * a[t];
-  load_shifted(ub + cp + rjp + m0, false, e0, a);   // (-1,  1,  0)
+  load_shifted<T, NC>(ub + cp + rjp + m0, false, e0, a);   // (-1,  1,  0)
 #pragma unroll
   for (int t = 0; t < VW; ++t) acc[t] -= w[2] * a[t];
-  Vec<T>::load(ub + cp + rkp + m0, a);              // ( 0, -1,  1)
+  Vec<T>::template load<NC>(ub + cp + rkp + m0, a);              // ( 0, -1,  1)
 #pragma unroll
   for (int t = 0; t < VW; ++t) acc[t] -= w[3] * a[t];
-  load_shifted(ub + cm + r0 + m0, false, e0, a);    // (-1,  0,  0)
+  load_shifted<T, NC>(ub + cm + r0 + m0, false, e0, a);    // (-1,  0,  0)
 #pragma unroll
   for (int t = 0; t < VW; ++t) acc[t] -= w[8] * a[t];
-  load_shifted(ub + cm + rjm + m0, e1, false, a);   // ( 1, -1,  0)
+  load_shifted<T, NC>(ub + cm + rjm + m0, e1, false, a);   // ( 1, -1,  0)
 #pragma unroll
   for (int t = 0; t < VW; ++t) acc[t] -= w[9] * a[t];
-  Vec<T>::load(ub + cm + rkm + m0, a);              // ( 0,  1, -1)
+  Vec<T>::template load<NC>(ub + cm + rkm + m0, a);              // ( 0,  1, -1)
 #pragma unroll
   for (int t = 0; t < VW; ++t) acc[t] -= w[10] * a[t];
   const int lo = max(mlo - m0, 0), hi = min(mlo + n - m0, VW);
@@ -554,7 +559,7 @@ __device__ __forceinline__ void res_group7(const Slice& sc, int N, int j, int g,
 
 // The 7-point colour-c items of one tile: groups of VW consecutive same-colour
 // slots per thread, the items of all the tile's slices streamed in one pass.
-template <class T, bool SCALED>
+template <class T, bool SCALED, bool NC = true>
 __device__ __forceinline__ void gs_tile7(const Tile& t, int N, const int* __restrict__ rs, int colour,
                                          T* __restrict__ ub, const T* __restrict__ fb, const T* __restrict__ w, T inv,
                                          int (*s_pre2)[33], int* s_pre_tot) {
@@ -568,7 +573,7 @@ __device__ __forceinline__ void gs_tile7(const Tile& t, int N, const int* __rest
     const Tile ts{k, t.j0, t.m0, 1};
     int j, g;
     flat_item(ts, N, colour, true, s_pre2[sl], tt - s_pre_tot[sl], j, g, VW);
-    gs_group7<T, SCALED>(slice_consts(rs, N, k), N, j, g, colour, ub, fb, wr, inv);
+    gs_group7<T, SCALED, NC>(slice_consts(rs, N, k), N, j, g, colour, ub, fb, wr, inv);
   }
 }
 
@@ -1330,8 +1335,9 @@ constexpr int CG_THREADS = 256;
 // same order (warp partials 0..7); buf holds the warp partials.  Consecutive
 // reductions alternate between two buffers.
 __device__ __forceinline__ double cg_allreduce(double v, double* buf) {
+  const int t = threadIdx.y * blockDim.x + threadIdx.x;   // 1-D or (32, 8) CTAs
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((threadIdx.x & 31) == 0) buf[threadIdx.x >> 5] = v;
+  if ((t & 31) == 0) buf[t >> 5] = v;
   __syncthreads();
   double s = 0.0;
 #pragma unroll
@@ -1651,11 +1657,736 @@ inline unsigned resident_grid(const void* kernel, int total, int cap_limit = 0) 
   return (unsigned)std::min(total, cap);
 }
 
+// ---------------------------------------------------------------------------
+// Persistent batch executor.  One launch runs the programs of many tasks (a
+// program is the list of level-wide operations one task issues, recorded
+// from the launchers; see hhg_kernels.h).  A CTA takes the next unit of the
+// current operation of some task (per-operation counters of units handed out
+// and finished); the CTA that finishes an operation's last unit publishes the
+// task's next operation.  Units of one operation are independent, as in the
+// level kernels; the publishing thread fences after the CTA's writes, and a
+// CTA fences after reading a task's operation index and before reading its
+// data (no read-only-path loads of data written in the launch), so every
+// operation sees its predecessors' results.  A CTA never waits inside a
+// unit, so some CTA always makes progress; a CTA that finds no work waits
+// (bounded) and retries, and stops when every task has finished.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+template <class T>
+__device__ __forceinline__ IfTab<T> dev_if_tab(const ProbArgs& p, int off);
+template <>
+__device__ __forceinline__ IfTab<double> dev_if_tab<double>(const ProbArgs& p, int off) {
+  IfTab<double> t{nullptr, nullptr, nullptr, nullptr, 0};
+  if (p.tnb && p.tw64) t = IfTab<double>{p.tnb + off, p.tw64 + off, p.td64 + off, p.ti64 + off, p.tn};
+  return t;
+}
+template <>
+__device__ __forceinline__ IfTab<float> dev_if_tab<float>(const ProbArgs& p, int off) {
+  IfTab<float> t{nullptr, nullptr, nullptr, nullptr, 0};
+  if (p.tnb && p.tw32) t = IfTab<float>{p.tnb + off, p.tw32 + off, p.td32 + off, p.ti32 + off, p.tn};
+  return t;
+}
+
+// Unit `unit` of a Gauss-Seidel colour (k_gs).
+template <class T, bool S7>
+__device__ void unit_gs(const BOp& op, int unit, int (*s_pre2)[33], int* s_pre_tot) {
+  const LevelArgs& L = op.L;
+  const ProbArgs& p = op.P;
+  const int N = L.N;
+  const int* rs = L.rs;
+  const int64_t block = L.block;
+  T* u = (T*)op.u;
+  if (unit < op.n_if_units) {
+    const int q = unit * CTA + tid256();
+    if (q < op.n_list) {
+      T* uI = (T*)op.uI;
+      const T* fI = (const T*)op.fI;
+      const int node = p.free_if[op.list_off + q];
+      const int c0 = L.cptr[node], c1 = L.cptr[node + 1];
+      const IfTab<T> tab = dev_if_tab<T>(p, op.list_off);
+      T val;
+      if (tab.nb) {
+        val = (fI[node] - if_offdiag<T, if_tab_k(S7)>(tab, u, q)) * tab.dinv[q];
+      } else {
+        T off = T(0), diag = T(0);
+        if_stencil<T, S7>(N, rs, block, u, (const T*)op.W, L.cps, c0, c1, off, diag);
+        val = (fI[node] - off) / diag;
+      }
+      uI[node] = val;
+      write_copies(N, rs, block, u, L.cps, L.cp_off, c0, c1, val);
+    }
+    return;
+  }
+  const int vb = unit - op.n_if_units;
+  const Tile t = L.tiles_int[vb / p.n_act];
+  const int macro = p.act[vb % p.n_act];
+  T* ub = u + (size_t)macro * block;
+  const T* w = (const T*)op.Wv + (size_t)macro * 16 * NDIR;
+  const T inv = ((const T*)op.Winv)[macro];
+  const T* fb = (const T*)op.f + (size_t)macro * block;
+  if (S7) {
+    if (op.scaled) gs_tile7<T, true, false>(t, N, rs, op.colour, ub, fb, w, T(1), s_pre2, s_pre_tot);
+    else gs_tile7<T, false, false>(t, N, rs, op.colour, ub, fb, w, inv, s_pre2, s_pre_tot);
+    return;
+  }
+  const int total = flat_setup_slabs(t, N, op.colour, true, 1, s_pre2, s_pre_tot);
+  int sl = 0;
+  for (int tt = tid256(); tt < total; tt += CTA) {
+    while (tt >= s_pre_tot[sl + 1]) ++sl;
+    const int k = t.k + sl;
+    const Tile ts{k, t.j0, t.m0, 1};
+    int j, v, ic, mlo, n;
+    flat_item(ts, N, op.colour, true, s_pre2[sl], tt - s_pre_tot[sl], j, v);
+    colour_row(N, j, k, op.colour, ic, mlo, n);
+    const int i = 4 * (mlo + v) + ic;
+    const int me = lidx32(rs, N, i, j, k);
+    T acc = fb[me];
+#pragma unroll
+    for (int d = 1; d < NDIR; ++d) {
+      int di, dj, dk;
+      dir_ijk(d, di, dj, dk);
+      acc -= w[d] * ub[lidx32(rs, N, i + di, j + dj, k + dk)];
+    }
+    ub[me] = acc * inv;
+  }
+}
+
+// Unit of the residual r = f - A u written to r (k_res, no norm).
+template <class T, bool S7>
+__device__ void unit_res(const BOp& op, int unit, int (*s_pre2)[33], int* s_pre_tot) {
+  const LevelArgs& L = op.L;
+  const ProbArgs& p = op.P;
+  const int N = L.N;
+  const int* rs = L.rs;
+  const int64_t block = L.block;
+  const T* u = (const T*)op.u;
+  T* r = (T*)op.r;
+  double ss = 0.0;
+  if (unit < op.n_if_units) {
+    const int q = unit * CTA + tid256();
+    if (q < op.n_list) {
+      const T* uI = (const T*)op.uI;
+      const T* fI = (const T*)op.fI;
+      const int node = p.free_if[q];
+      const int c0 = L.cptr[node], c1 = L.cptr[node + 1];
+      const IfTab<T> tab = dev_if_tab<T>(p, 0);
+      T res;
+      if (q >= op.skip_lo && q < op.skip_hi) {
+        res = T(0);
+      } else if (tab.nb) {
+        res = fI[node] - tab.diag[q] * uI[node] - if_offdiag<T, if_tab_k(S7)>(tab, u, q);
+      } else {
+        T off = T(0), diag = T(0);
+        if_stencil<T, S7>(N, rs, block, u, (const T*)op.W, L.cps, c0, c1, off, diag);
+        res = fI[node] - diag * uI[node] - off;
+      }
+      write_copies(N, rs, block, r, L.cps, L.cp_off, c0, c1, res);
+    } else if (q < op.n_list + op.n_zero) {
+      r[p.zero_off[q - op.n_list]] = T(0);
+    }
+    return;
+  }
+  const int vb = unit - op.n_if_units;
+  const Tile t = L.tiles_int[vb / p.n_act];
+  const int macro = p.act[vb % p.n_act];
+  const T* ub = u + (size_t)macro * block;
+  const T* fb = (const T*)op.f + (size_t)macro * block;
+  T* rb = r + (size_t)macro * block;
+  const T* w = (const T*)op.W + (size_t)macro * 16 * NDIR;
+  if (S7) {
+    constexpr int VW = Vec<T>::n;
+    const T wr[11] = {w[0], w[1], w[2], w[3], T(0), T(0), T(0), T(0), w[8], w[9], w[10]};
+    for (int c = 0; c < 4; ++c) {
+      const int total = flat_setup_slabs(t, N, c, true, VW, s_pre2, s_pre_tot);
+      int sl = 0;
+      for (int tt = tid256(); tt < total; tt += CTA) {
+        while (tt >= s_pre_tot[sl + 1]) ++sl;
+        const int k = t.k + sl;
+        const Tile ts{k, t.j0, t.m0, 1};
+        int j, g;
+        flat_item(ts, N, c, true, s_pre2[sl], tt - s_pre_tot[sl], j, g, VW);
+        if (c == op.skip)
+          res_group7<T, true, false, true, false>(slice_consts(rs, N, k), N, j, g, c, ub, fb, rb, wr, ss);
+        else
+          res_group7<T, true, false, false, false>(slice_consts(rs, N, k), N, j, g, c, ub, fb, rb, wr, ss);
+      }
+      __syncthreads();
+    }
+    return;
+  }
+  HHG_TILE_NODES(N, rs, t, s_pre, {
+    const int me = lidx32(rs, N, i, j, k);
+    T acc = T(0);
+    if (((i + 2 * j + 3 * k) & 3) != op.skip) {
+      acc = fb[me] - w[0] * ub[me];
+_Pragma("unroll")
+      for (int d = 1; d < NDIR; ++d) {
+        int di, dj, dk;
+        dir_ijk(d, di, dj, dk);
+        acc -= w[d] * ub[lidx32(rs, N, i + di, j + dj, k + dk)];
+      }
+    }
+    rb[me] = acc;
+  })
+}
+
+// Unit of the restriction onto the coarse level C (k_restrict).
+template <class T>
+__device__ void unit_restrict(const BOp& op, int unit, int (*s_pre2)[33], int* s_pre_tot) {
+  const LevelArgs& F = op.L;
+  const LevelArgs& C = op.C;
+  const ProbArgs& pc = op.P;
+  const T* rf = (const T*)op.r;
+  T* fc = (T*)op.fc;
+  T* uc = (T*)op.uc;
+  if (unit < op.n_if_units) {
+    const int q = unit * CTA + tid256();
+    if (q < op.n_list) {
+      T* fIc = (T*)op.fIc;
+      T* uIc = (T*)op.uIc;
+      const int node = pc.free_if[q];
+      const int64_t* g = pc.gather + (size_t)q * NDIR;
+      T acc = T(0);
+      for (int e = 1; e < NDIR; ++e) {
+        const int64_t o = g[e];
+        if (o >= 0) acc += rf[o];
+      }
+      fIc[node] = rf[g[0]] + T(0.5) * acc;
+      uIc[node] = T(0);
+      write_copies(C.N, C.rs, C.block, uc, C.cps, C.cp_off, C.cptr[node], C.cptr[node + 1], T(0));
+    } else if (q < op.n_list + op.n_zero) {
+      uc[pc.zero_off[q - op.n_list]] = T(0);
+    }
+    return;
+  }
+  const int vb = unit - op.n_if_units;
+  const Tile t = C.tiles_int[vb / pc.n_act];
+  const int macro = pc.act[vb % pc.n_act];
+  const T* rb = rf + (size_t)macro * F.block;
+  T* fb = fc + (size_t)macro * C.block;
+  T* ub = uc + (size_t)macro * C.block;
+  const int Nc = C.N, Nf = F.N;
+  const int* rsc = C.rs;
+  const int* rsf = F.rs;
+  HHG_TILE_NODES(Nc, rsc, t, s_pre, {
+    const int fi = 2 * i, fj = 2 * j, fk = 2 * k;
+    T acc = T(0);
+_Pragma("unroll")
+    for (int d = 1; d < NDIR; ++d) {
+      int di, dj, dk;
+      dir_ijk(d, di, dj, dk);
+      acc += rb[lidx32(rsf, Nf, fi + di, fj + dj, fk + dk)];
+    }
+    const int me = lidx32(rsc, Nc, i, j, k);
+    fb[me] = rb[lidx32(rsf, Nf, fi, fj, fk)] + T(0.5) * acc;
+    ub[me] = T(0);
+  })
+}
+
+// Unit of the prolongation u_f += P u_c (k_prolong).
+template <class T>
+__device__ void unit_prolong(const BOp& op, int unit, int (*s_pre2)[33], int* s_pre_tot) {
+  const LevelArgs& F = op.L;
+  const LevelArgs& C = op.C;
+  const ProbArgs& pf = op.P;
+  T* uf = (T*)op.u;
+  const T* uc = (const T*)op.uc;
+  if (unit < op.n_if_units) {
+    const int q = unit * CTA + tid256();
+    if (q < op.n_list) {
+      T* uIf = (T*)op.uI;
+      const int node = pf.free_if[q];
+      const int c0 = F.cptr[node], c1 = F.cptr[node + 1];
+      const Copy cp = F.cps[c0];
+      const T val = uIf[node] + interp(uc + (size_t)cp.macro * C.block, C.N, C.rs, cp.i, cp.j, cp.k);
+      uIf[node] = val;
+      write_copies(F.N, F.rs, F.block, uf, F.cps, F.cp_off, c0, c1, val);
+    }
+    return;
+  }
+  const int vb = unit - op.n_if_units;
+  const Tile t = F.tiles_int[vb / pf.n_act];
+  const int macro = pf.act[vb % pf.n_act];
+  T* fb = uf + (size_t)macro * F.block;
+  const T* cb = uc + (size_t)macro * C.block;
+  const int Nf = F.N, Nc = C.N;
+  const int* rsf = F.rs;
+  const int* rsc = C.rs;
+  HHG_TILE_NODES(Nf, rsf, t, s_pre, { fb[lidx32(rsf, Nf, i, j, k)] += interp(cb, Nc, rsc, i, j, k); })
+}
+
+// Unit of the FP64 residual handed to the FP32 cycle (k_res_f32, no norm).
+template <bool S7>
+__device__ void unit_res_f32(const BOp& op, int unit, int (*s_pre2)[33], int* s_pre_tot) {
+  const LevelArgs& L = op.L;
+  const ProbArgs& p = op.P;
+  const int N = L.N;
+  const int* rs = L.rs;
+  const int64_t block = L.block;
+  const double* u = (const double*)op.u;
+  if (unit < op.n_if_units) {
+    const int q = unit * CTA + tid256();
+    if (q < op.n_list) {
+      const double* uI = (const double*)op.uI;
+      const double* fI = (const double*)op.fI;
+      const int node = p.free_if[q];
+      const IfTab<double> tab = dev_if_tab<double>(p, 0);
+      double res;
+      if (tab.nb) {
+        res = fI[node] - tab.diag[q] * uI[node] - if_offdiag<double, if_tab_k(S7)>(tab, u, q);
+      } else {
+        double off = 0.0, diag = 0.0;
+        if_stencil<double, S7>(N, rs, block, u, (const double*)op.W, L.cps, L.cptr[node], L.cptr[node + 1], off,
+                               diag);
+        res = fI[node] - diag * uI[node] - off;
+      }
+      ((float*)op.oI32)[node] = (float)res;
+    }
+    return;
+  }
+  const int vb = unit - op.n_if_units;
+  const Tile t = L.tiles_int[vb / p.n_act];
+  const int macro = p.act[vb % p.n_act];
+  const double* ub = u + (size_t)macro * block;
+  const double* fb = (const double*)op.f + (size_t)macro * block;
+  float* ob = (float*)op.o32 + (size_t)macro * block;
+  const double* w = (const double*)op.W + (size_t)macro * 16 * NDIR;
+  HHG_TILE_NODES(N, rs, t, s_pre, {
+    int me;
+    double acc;
+    if (S7) {
+      const Nb7 q = nb7(sc, i, j);
+      me = q.me;
+      acc = fb[me] - w[0] * ub[me];
+      acc -= w[1] * ub[q.nb1];
+      acc -= w[2] * ub[q.nb2];
+      acc -= w[3] * ub[q.nb3];
+      acc -= w[8] * ub[q.nb8];
+      acc -= w[9] * ub[q.nb9];
+      acc -= w[10] * ub[q.nb10];
+    } else {
+      me = lidx32(rs, N, i, j, k);
+      acc = fb[me] - w[0] * ub[me];
+_Pragma("unroll")
+      for (int d = 1; d < NDIR; ++d) {
+        int di, dj, dk;
+        dir_ijk(d, di, dj, dk);
+        acc -= w[d] * ub[lidx32(rs, N, i + di, j + dj, k + dk)];
+      }
+    }
+    ob[me] = (float)acc;
+  })
+}
+
+// Coarse CG (k_cg with its vectors in the problem's global work array).
+template <class T>
+__device__ void unit_cg(const BOp& op, double* red) {
+  const int n = op.n_cg;
+  const T* f = (const T*)op.f;
+  const T* fI = (const T*)op.fI;
+  T* u = (T*)op.u;
+  T* uI = (T*)op.uI;
+  double* x = op.work;
+  double* r = x + n;
+  double* p = r + n;
+  double* Ap = p + n;
+  const int tid = tid256();
+  double part = 0.0;
+  for (int q = tid; q < n; q += CTA) {
+    const int64_t s = op.fsrc[q];
+    const double b = s >= 0 ? (double)f[s] : (double)fI[-1 - s];
+    x[q] = 0.0;
+    r[q] = b;
+    p[q] = b;
+    part += b * b;
+  }
+  double rr = cg_allreduce(part, red);
+  int rb = 1;
+  const double bnorm = sqrt(rr);
+  int it = 0;
+  while (bnorm > 0.0 && sqrt(rr) > op.rtol * bnorm && it < op.maxit) {
+    __syncthreads();
+    part = 0.0;
+    for (int q = tid; q < n; q += CTA) {
+      double a = 0.0;
+      for (int e = op.rowptr[q]; e < op.rowptr[q + 1]; ++e) a += op.val[e] * p[op.col[e]];
+      Ap[q] = a;
+      part += p[q] * a;
+    }
+    const double pAp = cg_allreduce(part, red + 8 * rb);
+    rb ^= 1;
+    const double alpha = rr / pAp;
+    part = 0.0;
+    for (int q = tid; q < n; q += CTA) {
+      x[q] += alpha * p[q];
+      const double rq = r[q] - alpha * Ap[q];
+      r[q] = rq;
+      part += rq * rq;
+    }
+    const double rr_new = cg_allreduce(part, red + 8 * rb);
+    rb ^= 1;
+    const double beta = rr_new / rr;
+    for (int q = tid; q < n; q += CTA) p[q] = r[q] + beta * p[q];
+    rr = rr_new;
+    ++it;
+  }
+  for (int q = tid; q < n; q += CTA) {
+    const T v = (T)x[q];
+    for (int e = op.uptr[q]; e < op.uptr[q + 1]; ++e) u[op.udst[e]] = v;
+    if (op.umaster[q] >= 0) uI[op.umaster[q]] = v;
+  }
+  if (tid == 0 && op.iters) *op.iters = it;
+}
+
+// 16384 elements per unit of the block-wise operations (zeroing, the FP32
+// correction added in FP64, memsets): tens of microseconds of streaming per
+// unit, like a stencil tile, so that the claims stay cheap by comparison
+constexpr int BATCH_CHUNK = CTA * 64;
+
+__device__ void run_unit(const BOp& op, int unit, int (*s_pre2)[33], int* s_pre_tot, double* red) {
+  const int tid = tid256();
+  switch (op.kind) {
+    case BOP_GS:
+      if (op.fp32) {
+        if (op.seven_point) unit_gs<float, true>(op, unit, s_pre2, s_pre_tot);
+        else unit_gs<float, false>(op, unit, s_pre2, s_pre_tot);
+      } else {
+        if (op.seven_point) unit_gs<double, true>(op, unit, s_pre2, s_pre_tot);
+        else unit_gs<double, false>(op, unit, s_pre2, s_pre_tot);
+      }
+      break;
+    case BOP_RES:
+      if (op.fp32) {
+        if (op.seven_point) unit_res<float, true>(op, unit, s_pre2, s_pre_tot);
+        else unit_res<float, false>(op, unit, s_pre2, s_pre_tot);
+      } else {
+        if (op.seven_point) unit_res<double, true>(op, unit, s_pre2, s_pre_tot);
+        else unit_res<double, false>(op, unit, s_pre2, s_pre_tot);
+      }
+      break;
+    case BOP_RESTRICT:
+      if (op.fp32) unit_restrict<float>(op, unit, s_pre2, s_pre_tot);
+      else unit_restrict<double>(op, unit, s_pre2, s_pre_tot);
+      break;
+    case BOP_PROLONG:
+      if (op.fp32) unit_prolong<float>(op, unit, s_pre2, s_pre_tot);
+      else unit_prolong<double>(op, unit, s_pre2, s_pre_tot);
+      break;
+    case BOP_CG:
+      if (op.fp32) unit_cg<float>(op, red);
+      else unit_cg<double>(op, red);
+      break;
+    case BOP_RES_F32:
+      if (op.seven_point) unit_res_f32<true>(op, unit, s_pre2, s_pre_tot);
+      else unit_res_f32<false>(op, unit, s_pre2, s_pre_tot);
+      break;
+    case BOP_ZERO_BLOCKS: {
+      // unit = (active macro, chunk of BATCH_CHUNK elements)
+      const int64_t chunks = (op.L.block + BATCH_CHUNK - 1) / BATCH_CHUNK;
+      const int macro = op.P.act[unit / chunks];
+      const int64_t c0 = (unit % chunks) * BATCH_CHUNK;
+      const int64_t c1 = min((int64_t)BATCH_CHUNK + c0, op.L.block);
+      for (int64_t q = c0 + tid; q < c1; q += CTA) {
+        if (op.fp32) ((float*)op.u)[(size_t)macro * op.L.block + q] = 0.f;
+        else ((double*)op.u)[(size_t)macro * op.L.block + q] = 0.0;
+      }
+      break;
+    }
+    case BOP_ZERO_LIST: {
+      const int64_t q = (int64_t)unit * CTA + tid;
+      if (q < op.n) {
+        if (op.fp32) ((float*)op.uI)[op.ids[q]] = 0.f;
+        else ((double*)op.uI)[op.ids[q]] = 0.0;
+      }
+      break;
+    }
+    case BOP_ADD_BLOCKS: {
+      // unit = (active macro, chunk of BATCH_CHUNK FP64 slots); u64 += e32
+      const int64_t chunks = (op.L.block + BATCH_CHUNK - 1) / BATCH_CHUNK;
+      const int macro = op.P.act[unit / chunks];
+      const int64_t c0 = (unit % chunks) * BATCH_CHUNK;
+      const int64_t c1 = min((int64_t)BATCH_CHUNK + c0, op.L.block);
+      double* ub = (double*)op.u + (size_t)macro * op.L.block;
+      const float* eb = (const float*)op.o32 + (size_t)macro * op.L.block;
+      for (int64_t q = c0 + 2 * tid; q < c1; q += 2 * CTA) {
+        double2 x = *reinterpret_cast<double2*>(ub + q);
+        const float2 d = *reinterpret_cast<const float2*>(eb + q);
+        x.x += (double)d.x;
+        x.y += (double)d.y;
+        *reinterpret_cast<double2*>(ub + q) = x;
+      }
+      break;
+    }
+    case BOP_ADD_MASTERS: {
+      const int64_t q = (int64_t)unit * CTA + tid;
+      if (q < op.n) {
+        const int node = op.ids[q];
+        ((double*)op.uI)[node] += (double)((const float*)op.oI32)[node];
+      }
+      break;
+    }
+    case BOP_MEMSET: {
+      // 16-byte words [unit * BATCH_CHUNK, ...) of op.u
+      const int64_t c0 = (int64_t)unit * BATCH_CHUNK;
+      const int64_t c1 = min((int64_t)BATCH_CHUNK + c0, op.n);
+      for (int64_t q = c0 + tid; q < c1; q += CTA) reinterpret_cast<double2*>(op.u)[q] = make_double2(0.0, 0.0);
+      break;
+    }
+    case BOP_SET_ZERO: {
+      const int64_t q = (int64_t)unit * CTA + tid;
+      if (q < op.n) ((double*)op.uI)[op.ids[q]] = 0.0;
+      break;
+    }
+    case BOP_RESTORE: {
+      const int64_t q = (int64_t)unit * CTA + tid;
+      if (q < op.n) ((double*)op.u)[op.offs[q]] = ((const double*)op.uI)[op.ids[q]];
+      break;
+    }
+    default:
+      break;
+  }
+}
+
+// Persistent executor of a batch: task t runs ops [op_off[t], op_off[t + 1])
+// in order; n_live tasks have at least one operation.  Every CTA repeatedly
+// claims a unit of the current operation of some task, runs it and counts it
+// done; the CTA that completes an operation's last unit publishes the task's
+// next phase.
+//   * Claims: warp 0 scans the tasks 32 at a time in priority classes (the
+//     tasks order[seg[c] .. seg[c + 1]) form class c, highest first); within
+//     a class it starts at the task it served last, and the first lane that
+//     sees unissued units of its task's current operation takes one with an
+//     atomic.  While the CTA runs a unit, thread 0 already claims the next
+//     unit of the same operation (the atomic's latency hides behind the
+//     work), except near the end of the operation; a unit taken there is
+//     valid because an operation with unissued units is still its task's
+//     current one.
+//   * Memory order: a unit's writes precede its done count (CTA barrier, then
+//     a device fence by the counting thread); a CTA reads a published phase
+//     before the data (device fence by the scanning warp, then a CTA
+//     barrier); the units read that data with plain coherent loads.
+//   * A CTA that finds no unit for wait_limit rounds in a row sets *err = 1
+//     and stops; the CTA that completes an operation always finds the next
+//     one, so the work still finishes.
+//   * Time stamps: st.start_ns (first CTA), st.task_ns[t] (the task's last
+//     unit done).
+// One unit per claim: a large operation gives each CTA only a few units
+// (a Gauss-Seidel tile takes tens of microseconds), so claiming several at
+// once lengthens the operation's tail by more than the claims cost.
+__device__ __forceinline__ int batch_claim_size(int) { return 1; }
+
+// Scheduler state of a CTA, in shared memory so that no register stays live
+// across a unit's body.
+struct BatchCtl {
+  int state, task, gi, unit, cnt;   // the claim to run (written by warp 0)
+  int cur_gi, cur_task;             // operation held in the CTA's op copy
+  int next;                         // first task of the next scan
+  int pf_u, pf_k;                   // chunk claimed ahead on cur_gi (-1: none)
+  int idle;                         // scans in a row that found nothing
+};
+
+__global__ void __launch_bounds__(CTA, 5) k_batch(const BOp* __restrict__ ops, const int* __restrict__ op_off,
+                                                  const int* __restrict__ order, const int* __restrict__ seg, int n_seg,
+                                                  int n_live, BatchState st, int wait_limit, int* __restrict__ err) {
+  __shared__ int s_pre2[MAX_SLABS][33];
+  __shared__ int s_pre_tot[MAX_SLABS + 1];
+  __shared__ double red[16];
+  __shared__ BatchCtl ctl;
+  __shared__ __align__(16) BOp s_op;
+  if (tid256() == 0) {
+    atomicMin(st.start_ns, global_ns());
+    ctl.cur_gi = -1;
+    ctl.cur_task = 0;
+    ctl.next = -1;
+    ctl.pf_u = -1;
+    ctl.pf_k = 0;
+    ctl.idle = 0;
+  }
+  __syncthreads();
+  for (;;) {
+    if (tid256() < 32) {
+      const int lane = tid256();
+      int state = 0, task = 0, gi = 0, u = 0, cnt = 0;
+      if (ctl.pf_u >= 0) {
+        state = 1;
+        task = ctl.cur_task;
+        gi = ctl.cur_gi;
+        u = ctl.pf_u;
+        cnt = ctl.pf_k;
+      } else if (*(volatile int*)st.tasks_done >= n_live) {
+        state = 2;
+      } else {
+        int pos_taken = 0;
+        for (int c = 0; c < n_seg && state == 0; ++c) {
+          const int lo = seg[c], len = seg[c + 1] - lo;
+          const int cur = ctl.next;   // position in order[] of the task served last
+          const int start = cur >= lo && cur < lo + len ? cur - lo : (int)(blockIdx.x % (unsigned)len);
+          for (int base = 0; base < len && state == 0; base += 32) {
+            const int q = base + lane;
+            int pos = start + q;
+            if (pos >= len) pos -= len;
+            bool avail = false;
+            int g = 0, nu = 0, t = 0;
+            if (q < len) {
+              t = order[lo + pos];
+              const int ph = *(volatile int*)(st.phase + t);
+              const int o0 = op_off[t];
+              if (ph < op_off[t + 1] - o0) {
+                g = o0 + ph;
+                nu = ops[g].n_units;
+                avail = *(volatile int*)(st.issued + g) < nu;
+              }
+            }
+            unsigned mask = __ballot_sync(0xffffffffu, avail);
+            while (mask) {
+              const int src = __ffs(mask) - 1;
+              mask &= mask - 1;
+              int claim = -1, k = 0;
+              if (lane == src) {
+                k = batch_claim_size(nu);
+                const int u0 = atomicAdd(st.issued + g, k);
+                if (u0 < nu) {
+                  claim = u0;
+                  k = min(k, nu - u0);
+                }
+              }
+              claim = __shfl_sync(0xffffffffu, claim, src);
+              if (claim >= 0) {
+                state = 1;
+                task = __shfl_sync(0xffffffffu, t, src);
+                gi = __shfl_sync(0xffffffffu, g, src);
+                cnt = __shfl_sync(0xffffffffu, k, src);
+                pos_taken = lo + __shfl_sync(0xffffffffu, pos, src);
+                u = claim;
+                break;
+              }
+            }
+          }
+        }
+        if (state == 1 && lane == 0) ctl.next = pos_taken;
+        __threadfence();   // what the earlier operations wrote is read after this
+      }
+      __syncwarp();
+      if (lane == 0) {
+        ctl.state = state;
+        ctl.task = task;
+        ctl.gi = gi;
+        ctl.unit = u;
+        ctl.cnt = cnt;
+      }
+    }
+    __syncthreads();
+    if (ctl.state == 2) break;
+    if (ctl.state == 0) {
+      __syncthreads();   // every thread has read the state
+      if (tid256() == 0) {
+        if (++ctl.idle > wait_limit) {
+          atomicExch(err, 1);
+          ctl.state = 2;
+        } else {
+          __nanosleep(256);
+        }
+      }
+      __syncthreads();
+      if (ctl.state == 2) break;
+      continue;
+    }
+    if (ctl.gi != ctl.cur_gi) {
+      const int* src = reinterpret_cast<const int*>(ops + ctl.gi);
+      int* dst = reinterpret_cast<int*>(&s_op);
+      for (int q = tid256(); q < (int)(sizeof(BOp) / sizeof(int)); q += CTA) dst[q] = src[q];
+      __syncthreads();
+    }
+    if (tid256() == 0) {
+      ctl.idle = 0;
+      ctl.cur_gi = ctl.gi;
+      ctl.cur_task = ctl.task;
+      // claim the next unit of this operation while this one runs, unless
+      // the operation nears its end (a unit held back there lengthens the
+      // operation's tail)
+      const int nu = s_op.n_units;
+      ctl.pf_k = batch_claim_size(nu);
+      ctl.pf_u = ctl.unit + ctl.cnt + 2 * (int)gridDim.x * ctl.pf_k < nu ? atomicAdd(st.issued + ctl.gi, ctl.pf_k) : nu;
+    }
+    for (int c = 0; c < ctl.cnt; ++c) {
+      run_unit(s_op, ctl.unit + c, s_pre2, s_pre_tot, red);
+      __syncthreads();
+    }
+    if (tid256() == 0) {
+      const int nu = s_op.n_units;
+      if (ctl.pf_u >= nu) ctl.pf_u = -1;
+      else ctl.pf_k = min(ctl.pf_k, nu - ctl.pf_u);
+      const int gi = ctl.gi, cnt = ctl.cnt;
+      __threadfence();   // the CTA's writes before its units count as done
+      const int d = atomicAdd(st.done + gi, cnt);
+      if (d + cnt == nu) {
+        const int t = ctl.task;
+        const int ph = gi - op_off[t] + 1;
+        __threadfence();
+        atomicExch(st.phase + t, ph);
+        if (ph == op_off[t + 1] - op_off[t]) {
+          st.task_ns[t] = global_ns();
+          __threadfence();
+          atomicAdd(st.tasks_done, 1);
+        }
+      }
+    }
+    // the next scan (warp 0) reads ctl after thread 0 wrote it: same warp,
+    // ordered by __syncwarp at the top of the scan
+    __syncwarp();
+  }
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------
 // Launchers
 // ---------------------------------------------------------------------------
+namespace {
+thread_local std::vector<BOp>* g_rec = nullptr;
+
+// A batch operation of kind k in the arithmetic type T.
+template <class T>
+BOp new_op(int kind) {
+  BOp op;
+  std::memset(&op, 0, sizeof(op));
+  op.kind = kind;
+  op.fp32 = sizeof(T) == 4 ? 1 : 0;
+  return op;
+}
+
+int64_t block_chunks(int64_t block) { return (block + BATCH_CHUNK - 1) / BATCH_CHUNK; }
+}  // namespace
+
+void record_ops(std::vector<BOp>* rec) { g_rec = rec; }
+bool recording() { return g_rec != nullptr; }
+
+cudaError_t memset16(void* p, size_t bytes, cudaStream_t s) {
+  if (g_rec) {
+    if (bytes % 16 != 0 || reinterpret_cast<uintptr_t>(p) % 16 != 0) return cudaErrorInvalidValue;
+    BOp op = new_op<double>(BOP_MEMSET);
+    op.u = p;
+    op.n = (int64_t)(bytes / 16);
+    op.n_units = (int)((op.n + BATCH_CHUNK - 1) / BATCH_CHUNK);
+    if (op.n_units > 0) g_rec->push_back(op);
+    return cudaSuccess;
+  }
+  return cudaMemsetAsync(p, 0, bytes, s);
+}
+
+cudaError_t run_batch(const BOp* ops, const int* op_off, const int* order, const int* seg, int n_seg, int n_live,
+                      const BatchState& st, int wait_limit, int* err, cudaStream_t s) {
+  if (n_live <= 0) return cudaSuccess;
+  const unsigned grid = resident_grid((const void*)k_batch, 1 << 30);
+  ++g_kernel_launches;
+  k_batch<<<grid, cta_shape(), 0, s>>>(ops, op_off, order, seg, n_seg, n_live, st, wait_limit, err);
+  return cudaGetLastError();
+}
 // Elements of one staging slot of the streaming kernel on a level: the
 // largest band range, rows 0..band+1 of slice 0, rounded up to 32 elements.
 inline int stream_slot(int N, int band) {
@@ -1714,6 +2445,31 @@ template <class T>
 cudaError_t gs_colour(const LevelArgs& L, const ProbArgs& p, T* u, T* uI, const T* f, const T* fI, const T* W,
                       const T* Winv, int colour, bool seven_point, cudaStream_t s, cudaEvent_t ev_begin,
                       cudaEvent_t ev_end, const T* fs, const T* Wsc) {
+  if (g_rec) {
+    if (!seven_point || !fs || !Wsc) fs = Wsc = nullptr;
+    const int nl = p.col_off[colour + 1] - p.col_off[colour];
+    const Units g = units(nl, L.n_tiles_int, p.n_act);
+    if (g.total == 0) return cudaSuccess;
+    BOp op = new_op<T>(BOP_GS);
+    op.seven_point = seven_point ? 1 : 0;
+    op.scaled = fs ? 1 : 0;
+    op.colour = colour;
+    op.L = L;
+    op.P = p;
+    op.list_off = p.col_off[colour];
+    op.n_list = nl;
+    op.n_if_units = g.n_if_units;
+    op.n_units = g.total;
+    op.u = u;
+    op.uI = uI;
+    op.f = fs ? fs : f;
+    op.fI = fI;
+    op.W = W;
+    op.Wv = Wsc ? Wsc : W;
+    op.Winv = Winv;
+    g_rec->push_back(op);
+    return cudaSuccess;
+  }
   if (!seven_point) fs = Wsc = nullptr;
   if (!fs || !Wsc) fs = Wsc = nullptr;
   const int n = p.col_off[colour + 1] - p.col_off[colour];
@@ -1741,6 +2497,31 @@ template <class T>
 cudaError_t residual(const LevelArgs& L, const ProbArgs& p, const T* u, const T* uI, const T* f, const T* fI, T* r,
                      const T* W, bool seven_point, bool write_r, double* partial, int* n_part, cudaStream_t s,
                      int skip) {
+  if (g_rec) {
+    if (partial || !write_r) return cudaErrorNotSupported;   // norms are not part of a batch
+    const int nl = p.col_off[4];
+    const Units g = units(nl + p.n_zero, L.n_tiles_int, p.n_act);
+    if (g.total == 0) return cudaSuccess;
+    BOp op = new_op<T>(BOP_RES);
+    op.seven_point = seven_point ? 1 : 0;
+    op.skip = skip >= 0 && skip < 4 ? skip : -1;
+    op.skip_lo = op.skip >= 0 ? p.col_off[op.skip] : 0;
+    op.skip_hi = op.skip >= 0 ? p.col_off[op.skip + 1] : 0;
+    op.L = L;
+    op.P = p;
+    op.n_list = nl;
+    op.n_zero = p.n_zero;
+    op.n_if_units = g.n_if_units;
+    op.n_units = g.total;
+    op.u = (void*)u;
+    op.uI = (void*)uI;
+    op.f = f;
+    op.fI = fI;
+    op.r = r;
+    op.W = W;
+    g_rec->push_back(op);
+    return cudaSuccess;
+  }
   const bool norm = partial != nullptr;
   const int n = p.col_off[4];
   const int n_zero = write_r ? p.n_zero : 0;
@@ -1768,6 +2549,26 @@ cudaError_t residual(const LevelArgs& L, const ProbArgs& p, const T* u, const T*
 template <class T>
 cudaError_t restrict_to(const LevelArgs& C, const LevelArgs& F, const ProbArgs& pc, const T* rf, T* fc, T* fIc, T* uc,
                         T* uIc, cudaStream_t s) {
+  if (g_rec) {
+    const int nl = pc.col_off[4];
+    const Units g = units(nl + pc.n_zero, C.n_tiles_int, pc.n_act);
+    if (g.total == 0) return cudaSuccess;
+    BOp op = new_op<T>(BOP_RESTRICT);
+    op.L = F;
+    op.C = C;
+    op.P = pc;
+    op.n_list = nl;
+    op.n_zero = pc.n_zero;
+    op.n_if_units = g.n_if_units;
+    op.n_units = g.total;
+    op.r = (void*)rf;
+    op.fc = fc;
+    op.fIc = fIc;
+    op.uc = uc;
+    op.uIc = uIc;
+    g_rec->push_back(op);
+    return cudaSuccess;
+  }
   const int n = pc.col_off[4];
   const Units g = units(n + pc.n_zero, C.n_tiles_int, pc.n_act);
   if (g.total == 0) return cudaSuccess;
@@ -1782,6 +2583,23 @@ cudaError_t restrict_to(const LevelArgs& C, const LevelArgs& F, const ProbArgs& 
 template <class T>
 cudaError_t prolong_add(const LevelArgs& F, const LevelArgs& C, const ProbArgs& pf, T* uf, T* uIf, const T* uc,
                         cudaStream_t s) {
+  if (g_rec) {
+    const int nl = pf.col_off[4];
+    const Units g = units(nl, F.n_tiles_int, pf.n_act);
+    if (g.total == 0) return cudaSuccess;
+    BOp op = new_op<T>(BOP_PROLONG);
+    op.L = F;
+    op.C = C;
+    op.P = pf;
+    op.n_list = nl;
+    op.n_if_units = g.n_if_units;
+    op.n_units = g.total;
+    op.u = uf;
+    op.uI = uIf;
+    op.uc = (void*)uc;
+    g_rec->push_back(op);
+    return cudaSuccess;
+  }
   const int n = pf.col_off[4];
   const Units g = units(n, F.n_tiles_int, pf.n_act);
   if (g.total == 0) return cudaSuccess;
@@ -1796,6 +2614,29 @@ cudaError_t prolong_add(const LevelArgs& F, const LevelArgs& C, const ProbArgs& 
 template <class T>
 cudaError_t coarse_cg(const DevProblem& p, const T* f, const T* fI, T* u, T* uI, double rtol, int maxit,
                       cudaStream_t s, double* work) {
+  if (g_rec) {
+    if (p.n_cg == 0) return cudaSuccess;
+    BOp op = new_op<T>(BOP_CG);
+    op.n_units = 1;
+    op.n_cg = p.n_cg;
+    op.rowptr = p.rowptr;
+    op.col = p.col;
+    op.val = p.val;
+    op.fsrc = p.fsrc;
+    op.uptr = p.uptr;
+    op.udst = p.udst;
+    op.umaster = p.umaster;
+    op.work = work ? work : p.cg_work;
+    op.iters = p.cg_iters;
+    op.rtol = rtol;
+    op.maxit = maxit;
+    op.f = f;
+    op.fI = fI;
+    op.u = u;
+    op.uI = uI;
+    g_rec->push_back(op);
+    return cudaSuccess;
+  }
   if (p.n_cg == 0) return cudaSuccess;
   // the vectors live in shared memory when they fit and no work array is
   // imposed (the allocation-free cycle passes its static array)
@@ -1833,6 +2674,7 @@ cudaError_t fma_probe(double* out, int blocks, int iters, cudaStream_t s) {
 }
 
 cudaError_t reduce_partials(const double* partial, int n, double* out, cudaStream_t s) {
+  if (g_rec) return cudaSuccess;   // a batch needs no norms
   ++g_kernel_launches;
   k_reduce<<<1, 1024, 0, s>>>(partial, n, out);
   return cudaGetLastError();
@@ -1921,6 +2763,16 @@ cudaError_t copy_listed(const double* src, double* dst, const int* idx, int n, c
 }
 
 cudaError_t set_masters_zero(double* uI, const int* ids, int n, cudaStream_t s) {
+  if (g_rec) {
+    if (n <= 0) return cudaSuccess;
+    BOp op = new_op<double>(BOP_SET_ZERO);
+    op.uI = uI;
+    op.ids = ids;
+    op.n = n;
+    op.n_units = (int)lin_grid(n, CTA);
+    g_rec->push_back(op);
+    return cudaSuccess;
+  }
   if (n > 0) {
     ++g_kernel_launches;
     k_set_masters_zero<<<lin_grid(n, 256), 256, 0, s>>>(uI, ids, n);
@@ -1940,6 +2792,18 @@ cudaError_t scale_blocks(const double* f, const double* winv, double* out, int n
 }
 
 cudaError_t restore_copies(double* u, const double* uI, const int64_t* off, const int* master, int n, cudaStream_t s) {
+  if (g_rec) {
+    if (n <= 0) return cudaSuccess;
+    BOp op = new_op<double>(BOP_RESTORE);
+    op.u = u;
+    op.uI = (void*)uI;
+    op.offs = off;
+    op.ids = master;
+    op.n = n;
+    op.n_units = (int)lin_grid(n, CTA);
+    g_rec->push_back(op);
+    return cudaSuccess;
+  }
   if (n > 0) {
     ++g_kernel_launches;
     k_restore<<<lin_grid(n, 256), 256, 0, s>>>(u, uI, off, master, n);
@@ -1950,6 +2814,28 @@ cudaError_t restore_copies(double* u, const double* uI, const int64_t* off, cons
 cudaError_t residual_to_f32(const LevelArgs& L, const ProbArgs& p, const double* u, const double* uI, const double* f,
                             const double* fI, float* f32, float* fI32, const double* W, bool seven_point,
                             double* partial, int* n_part, cudaStream_t s) {
+  if (g_rec) {
+    const int nl = p.col_off[4];
+    const Units g = units(nl, L.n_tiles_int, p.n_act);
+    if (n_part) *n_part = 0;
+    if (g.total == 0) return cudaSuccess;
+    BOp op = new_op<double>(BOP_RES_F32);
+    op.seven_point = seven_point ? 1 : 0;
+    op.L = L;
+    op.P = p;
+    op.n_list = nl;
+    op.n_if_units = g.n_if_units;
+    op.n_units = g.total;
+    op.u = (void*)u;
+    op.uI = (void*)uI;
+    op.f = f;
+    op.fI = fI;
+    op.o32 = f32;
+    op.oI32 = fI32;
+    op.W = W;
+    g_rec->push_back(op);
+    return cudaSuccess;
+  }
   const int n = p.col_off[4];
   const Units g = units(n, L.n_tiles_int, p.n_act);
   if (n_part) *n_part = 0;
@@ -1966,6 +2852,27 @@ cudaError_t residual_to_f32(const LevelArgs& L, const ProbArgs& p, const double*
 
 cudaError_t add_correction(const LevelArgs& L, const ProbArgs& p, double* u, double* uI, const float* e,
                            const float* eI, cudaStream_t s) {
+  if (g_rec) {
+    if (p.n_act > 0) {
+      BOp op = new_op<double>(BOP_ADD_BLOCKS);
+      op.L = L;
+      op.P = p;
+      op.u = u;
+      op.o32 = (void*)e;
+      op.n_units = (int)(p.n_act * block_chunks(L.block));
+      g_rec->push_back(op);
+    }
+    if (p.col_off[4] > 0) {
+      BOp op = new_op<double>(BOP_ADD_MASTERS);
+      op.uI = uI;
+      op.oI32 = (void*)eI;
+      op.ids = p.free_if;
+      op.n = p.col_off[4];
+      op.n_units = (int)lin_grid(op.n, CTA);
+      g_rec->push_back(op);
+    }
+    return cudaSuccess;
+  }
   if (p.n_act > 0) {
     const int64_t per = 256 * 8;
     const unsigned gx = (unsigned)std::min<int64_t>((L.block / 2 + per - 1) / per, 4096);
@@ -1982,6 +2889,25 @@ cudaError_t add_correction(const LevelArgs& L, const ProbArgs& p, double* u, dou
 
 template <class T>
 cudaError_t zero_problem_blocks(const LevelArgs& L, const ProbArgs& p, T* u, T* uI, cudaStream_t s) {
+  if (g_rec) {
+    if (p.n_act > 0) {
+      BOp op = new_op<T>(BOP_ZERO_BLOCKS);
+      op.L = L;
+      op.P = p;
+      op.u = u;
+      op.n_units = (int)(p.n_act * block_chunks(L.block));
+      g_rec->push_back(op);
+    }
+    if (p.col_off[4] > 0) {
+      BOp op = new_op<T>(BOP_ZERO_LIST);
+      op.uI = uI;
+      op.ids = p.free_if;
+      op.n = p.col_off[4];
+      op.n_units = (int)lin_grid(op.n, CTA);
+      g_rec->push_back(op);
+    }
+    return cudaSuccess;
+  }
   if (p.n_act > 0) {
     const int64_t per = 256 * 8;
     unsigned gx = (unsigned)std::min<int64_t>((L.block + per - 1) / per, 4096);

@@ -27,7 +27,8 @@ EXPORTS = ["hhg_mesh_create", "hhg_mesh_destroy", "hhg_mesh_info", "hhg_mesh_byt
            "hhg_get_solution", "hhg_vcycle", "hhg_residual_norm", "hhg_inject_fault", "hhg_recover_local",
            "hhg_solve", "hhg_last_error", "hhg_profile_enable", "hhg_profile_read", "hhg_profile_info",
            "hhg_launch_count", "hhg_vcycle_noalloc", "hhg_set_coefficients", "hhg_grad_coeff",
-           "hhg_autotune", "hhg_batch_create", "hhg_batch_launch", "hhg_batch_destroy", "hhg_recover_dn",
+           "hhg_autotune", "hhg_batch_create", "hhg_batch_launch", "hhg_batch_destroy",
+           "hhg_batch_launch_persistent", "hhg_batch_info", "hhg_batch_set_priority", "hhg_recover_dn",
            "hhg_mesh_create_general", "hhg_set_launch_limit", "hhg_walk_counts", "hhg_set_streaming",
            "hhg_set_wait_limit", "hhg_measure_fp64_peak", "hhg_profile_breakdown"]
 
@@ -104,6 +105,9 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
                               C.POINTER(C.c_int), C.c_int, C.c_int, C.POINTER(P)], C.c_int),
         "hhg_batch_launch": ([P, C.POINTER(C.c_double), P], C.c_int),
         "hhg_batch_destroy": ([P], C.c_int),
+        "hhg_batch_launch_persistent": ([P, C.POINTER(C.c_double), P], C.c_int),
+        "hhg_batch_info": ([P, C.POINTER(C.c_int64)], C.c_int),
+        "hhg_batch_set_priority": ([P, C.POINTER(C.c_int)], C.c_int),
     }
     for name, (args, res) in sig.items():
         fn = getattr(lib, name)
@@ -347,6 +351,27 @@ class Batch:
         ms = (C.c_double * max(self.n, 1))()
         _check(lib().hhg_batch_launch(self.h, ms if timed else None, _stream(stream)))
         return list(ms)[:self.n] if timed else None
+
+    def launch_persistent(self, timed=True, stream=None):
+        """The same work as one launch of the persistent scheduler kernel."""
+        ms = (C.c_double * max(self.n, 1))()
+        _check(lib().hhg_batch_launch_persistent(self.h, ms if timed else None, _stream(stream)))
+        return list(ms)[:self.n] if timed else None
+
+    def set_priority(self, prio=None):
+        """Priority per task (the global task last) for the persistent
+        launch; None: all equal."""
+        if prio is None:
+            _check(lib().hhg_batch_set_priority(self.h, None))
+            return
+        arr = (C.c_int * self.n)(*[int(x) for x in prio])
+        _check(lib().hhg_batch_set_priority(self.h, arr))
+
+    def info(self):
+        """(tasks, recorded operations, work units, kernels in the graph)."""
+        v = (C.c_int64 * 4)()
+        _check(lib().hhg_batch_info(self.h, v))
+        return tuple(int(x) for x in v)
 
     def close(self):
         if self.h is not None and self.h.value is not None:
