@@ -698,8 +698,52 @@ def batch_workload(torch, hhg, I, warmup, steps):
     return res
 
 
+def small_tasks_workload(torch, hhg, I, n_tasks=256, R=5, cycles=3, steps=5):
+    """Many small recovery problems: n_tasks meshes of 6 or 12 macros refined R
+    times (random load seed 200 + t, zero initial guess), each with a fault of
+    up to two macros (seed 0) and `cycles` local FP64 cycles; the batch as one
+    CUDA-graph launch and as one persistent-kernel launch (CUDA events around
+    each launch, median of `steps`)."""
+    import numpy as np
+    rng = np.random.default_rng(0)
+    tasks = []
+    for q in range(n_tasks):
+        sub = (2, 1, 1) if q % 2 else (1, 1, 1)
+        M = hhg.Mesh(sub, R)
+        f = torch.from_numpy(I.random_load(sub, R, 200 + q)).cuda()
+        M.set_problem(f, torch.zeros_like(f))
+        ids = sorted(set(int(x) for x in rng.integers(0, 6 * int(np.prod(sub)), size=2)))
+        tasks.append((M, ids, cycles))
+    B = hhg.Batch(tasks)
+    stream = torch.cuda.current_stream()
+    out = {"workload": f"{n_tasks} recovery problems of 6 or 12 macros refined {R} levels, a fault of up to "
+                       f"two macros and {cycles} local FP64 cycles each"}
+    for name, launch in (("graph_ms", B.launch), ("persistent_ms", B.launch_persistent)):
+        for _ in range(3):
+            launch(timed=False)
+        ev = []
+        for _ in range(steps):
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            launch(timed=False, stream=stream)
+            b.record()
+            torch.cuda.synchronize()
+            ev.append(a.elapsed_time(b))
+        out[name] = float(np.median(ev))
+    n, n_ops, n_units, n_kernels = B.info()
+    out.update({"graph_kernels": n_kernels, "operations": n_ops, "work_units": n_units,
+                "speedup_persistent_vs_graph": out["graph_ms"] / out["persistent_ms"]})
+    B.close()
+    for M, _, _ in tasks:
+        M.close()
+    return out
+
+
 def extra_batch(torch, hhg, I):
-    return batch_workload(torch, hhg, I, warmup=1, steps=3)
+    res = batch_workload(torch, hhg, I, warmup=1, steps=3)
+    res["many_small_problems"] = small_tasks_workload(torch, hhg, I)
+    return res
 
 
 SHEAR = [[1.0, 0.3, -0.2], [0.1, 0.9, 0.25], [-0.15, 0.2, 1.1]]
@@ -779,7 +823,7 @@ def extra_grad(torch, hhg, I):
 
 
 def run_batch(args):
-    """The batched-recovery workload alone (batch_workload)."""
+    """The batched-recovery workloads alone (batch_workload, small_tasks_workload)."""
     import torch
 
     import hhg_inputs as I
@@ -789,6 +833,7 @@ def run_batch(args):
     build()
     torch.cuda.set_device(0)
     res = batch_workload(torch, hhg, I, args.warmup, args.steps)
+    res["many_small_problems"] = small_tasks_workload(torch, hhg, I, steps=max(args.steps, 3))
     line = {"metric": "batched recovery: total time to 1e-8 (global) and per-problem latency", "impl": "ours",
             "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "dtype": "f32-in-f64-ir", "data": "synthetic"}
     line.update(res)
@@ -926,8 +971,16 @@ def run_profile_case(args):
     M = hhg.Mesh(SUB, args.levels, precision=32 if args.mixed else 64)
     f = torch.from_numpy(I.random_load(SUB, args.levels, SEED)).cuda()
     M.set_problem(f, torch.zeros_like(f))
+    if args.autotune_profile:
+        # the tile shapes the benchmark uses; captures then start at the solve
+        # (ncu --profile-from-start off)
+        hhg.hhg_autotune(M.h, args.levels - 1, reps=2)
+        M.set_problem(f, torch.zeros_like(f))
+    torch.cuda.synchronize()
+    torch.cuda.profiler.start()
     hist, cyc, _ = M.solve(rtol=1e-30, max_cycles=2, mixed_precision=args.mixed, allow_not_converged=True)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     print(json.dumps({"case": "profile", "levels": args.levels, "mixed": bool(args.mixed), "cycles": cyc,
                       "rel_residual": float(hist[-1])}), flush=True)
     M.close()
@@ -950,6 +1003,9 @@ def main():
                     help="two cycles of the cube refined --levels times (for kernel captures)")
     ap.add_argument("--levels", type=int, default=7)
     ap.add_argument("--mixed", action="store_true")
+    ap.add_argument("--autotune-profile", action="store_true",
+                    help="with --profile-case: autotune the tiles first; the solve is bracketed by "
+                         "cudaProfilerStart/Stop")
     ap.add_argument("--kappa", action="store_true",
                     help="run the cycle-advantage study of the recovery strategies instead")
     ap.add_argument("--precision", action="store_true",
