@@ -618,7 +618,12 @@ int vcycle_T(hhg_mesh* m, Prec<T>& P, DevProblem& p, int pre, int post, double c
     const LevelArgs a = plargs(m, p, l);
     const ProbArgs q = pargs(p, l);
     if (l == L) HHG_TRY(mark(BD_PROLONG));
-    HHG_CUDA(prolong_add<T>(a, plargs(m, p, l - 1), q, D.u, D.uI, P.lv[l - 1].u, s));
+    // the first post-smoothing colour (0) overwrites its nodes without
+    // reading them: their correction is not formed (interface entries of
+    // colour 0 too, where the list is sorted by colour: the cube family)
+    const int pskip = post > 0 ? 0 : -1;
+    const int if_hi = post > 0 && !m->host.general ? q.col_off[1] : 0;
+    HHG_CUDA(prolong_add<T>(a, plargs(m, p, l - 1), q, D.u, D.uI, P.lv[l - 1].u, s, pskip, q.col_off[0], if_hi));
     if (l == L) HHG_TRY(mark(BD_FINE_SMOOTH));
     HHG_TRY(smooth<T>(m, P, p, l, post, s, co.profile));
   }

@@ -89,10 +89,12 @@ template <class T>
 cudaError_t restrict_to(const LevelArgs& C, const LevelArgs& F, const ProbArgs& pc, const T* rf, T* fc,
                         T* fIc, T* uc, T* uIc, cudaStream_t s);
 
-// u_f += P u_c on the free fine nodes.
+// u_f += P u_c on the free fine nodes.  skip (0..3): the volume nodes of that
+// colour are left out, and the interface list entries [if_lo, if_hi) too --
+// for nodes the next Gauss-Seidel colour overwrites without reading them.
 template <class T>
 cudaError_t prolong_add(const LevelArgs& F, const LevelArgs& C, const ProbArgs& pf, T* uf, T* uIf,
-                        const T* uc, cudaStream_t s);
+                        const T* uc, cudaStream_t s, int skip = -1, int if_lo = 0, int if_hi = 0);
 
 // Coarse CG (FP64) on the compact free nodes of level 0; reads the level's
 // right-hand side (type T), writes the solution into u / uI.  work (4 n_cg

@@ -26,6 +26,7 @@
 
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 #include <map>
 #include <mutex>
 #include <utility>
@@ -51,6 +52,12 @@ __device__ __forceinline__ int lidx32(const int* __restrict__ rs, int N, int i, 
   const int M = N + 1 - k;
   return ((i + 2 * j + 3 * k) & 3) * __ldg(rs + N + 2) + __ldg(rs + k) + slot_prefix(M) - slot_prefix(M - j) +
          (i >> 2);
+}
+
+// Base slot of row j of slice k of a level (colour array 0).
+__device__ __forceinline__ int row_base(const int* __restrict__ rs, int N, int j, int k) {
+  const int M = N + 1 - k;
+  return __ldg(rs + k) + slot_prefix(M) - slot_prefix(M - j);
 }
 
 // Offsets of the 7-point neighbourhood of node (i, j, k), colour c, in one
@@ -302,6 +309,24 @@ __device__ __forceinline__ void vol_unit(int b, int n_act, const Tile* __restric
                                          const int* __restrict__ act, Tile& t, int& macro) {
   t = tiles[b / n_act];
   macro = act[b % n_act];
+}
+
+// The restriction walks each coarse tile as RESTRICT_SPLIT units of
+// consecutive slices: a coarse level has an eighth of the fine level's nodes
+// and its tiles give a few heavy units per CTA, whose tail left SMs idle.
+constexpr int RESTRICT_SPLIT = 4;
+
+// Volume unit b of a walk over split tiles: part (b / n_act) % split of tile
+// (b / n_act) / split, for active macro b % n_act.
+__device__ __forceinline__ void vol_subunit(int b, int n_act, int split, const Tile* __restrict__ tiles,
+                                            const int* __restrict__ act, Tile& t, int& macro) {
+  const int tp = b / n_act;
+  macro = act[b % n_act];
+  t = tiles[tp / split];
+  const int part = tp % split;
+  const int s0 = t.pad * part / split, s1 = t.pad * (part + 1) / split;
+  t.k += s0;
+  t.pad = s1 - s0;
 }
 
 // Off-diagonal part of an interface node's stencil applied to u, and the sum
@@ -1092,8 +1117,85 @@ _Pragma("unroll")
 // ---------------------------------------------------------------------------
 // Restriction R = P^T onto the coarse level (§2.1); zero the coarse correction
 // ---------------------------------------------------------------------------
+// Calls body(j, k, m) for every item of a tile: slot m of interior row j of
+// slice k, i.e. the nodes i = 4m .. 4m + 3 (one per colour array), the items
+// of all the tile's slices in one range (one CTA barrier per tile, as for the
+// stencil kernels); ends with a CTA barrier.  The kernel declares
+// s_pre2[MAX_SLABS][33] and s_pre_tot[MAX_SLABS + 1] in shared memory.
+template <class F>
+__device__ __forceinline__ void for_tile_slots(const Tile& t, int N, int (*s_pre2)[33], int* s_pre_tot, F&& body) {
+  const int total = flat_setup_slabs(t, N, 0, false, 1, s_pre2, s_pre_tot);
+  int sl = 0;
+  for (int tt = tid256(); tt < total; tt += CTA) {
+    while (tt >= s_pre_tot[sl + 1]) ++sl;
+    const int k = t.k + sl;
+    const Tile ts{k, t.j0, t.m0, 1};
+    int j, m;
+    flat_item(ts, N, 0, false, s_pre2[sl], tt - s_pre_tot[sl], j, m);
+    body(j, k, m);
+  }
+  __syncthreads();
+}
+
+// Full-weighting restriction f_c = r(2I) + 1/2 sum_d r(2I + d) (d over the 14
+// stencil directions, summed in their order) of the coarse nodes I = 4M ..
+// 4M + 3 of interior row J of coarse slice K (one per colour array); the
+// coarse correction there is zeroed.  The seven fine rows (2J + dj, 2K + dk)
+// are located once per item; fine node i' = 8M + 2q + di lies in colour
+// array (2q + di + 2 jf + 3 kf) & 3 at slot 2M + ((2q + di) >> 2), so every
+// load is a row base plus constants.  All colours of the item in one pass
+// keep the fine rows in cache for the four coarse nodes.  Plain loads when
+// NC is false (data written in this launch).
+template <class T, bool NC>
+__device__ __forceinline__ void restrict_slot(int Nc, const int* __restrict__ rsc, int Nf,
+                                              const int* __restrict__ rsf, int J, int K, int M,
+                                              const T* __restrict__ rb, T* __restrict__ fcb, T* __restrict__ ucb) {
+  const int Lc = Nc - 1 - J - K;
+  const int CSf = __ldg(rsf + Nf + 2);
+  int base[NDIR], col[NDIR];
+#pragma unroll
+  for (int d = 0; d < NDIR; ++d) {
+    int di, dj, dk;
+    dir_ijk(d, di, dj, dk);
+    const int jf = 2 * J + dj, kf = 2 * K + dk;
+    base[d] = row_base(rsf, Nf, jf, kf) + 2 * M;
+    col[d] = 2 * jf + 3 * kf;
+  }
+  const int CSc = __ldg(rsc + Nc + 2);
+  const int rbc = row_base(rsc, Nc, J, K) + M;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int I = 4 * M + q;
+    if (I < 1 || I > Lc) continue;
+    T cen = T(0), acc = T(0);
+#pragma unroll
+    for (int d = 0; d < NDIR; ++d) {
+      int di, dj, dk;
+      dir_ijk(d, di, dj, dk);
+      const int o = ((2 * q + di + col[d]) & 3) * CSf + base[d] + ((2 * q + di) >> 2);
+      const T x = NC ? __ldg(rb + o) : rb[o];
+      if (d == 0) cen = x;
+      else acc += x;
+    }
+    const int me = ((q + 2 * J + 3 * K) & 3) * CSc + rbc;
+    fcb[me] = fma(T(0.5), acc, cen);   // the halving is exact: same value as a separate multiply
+    ucb[me] = T(0);
+  }
+}
+
+// Volume restriction of a coarse tile.
+template <class T, bool NC>
+__device__ __forceinline__ void restrict_tile(const Tile& t, int Nc, const int* __restrict__ rsc, int Nf,
+                                              const int* __restrict__ rsf, const T* __restrict__ rb,
+                                              T* __restrict__ fcb, T* __restrict__ ucb, int (*s_pre2)[33],
+                                              int* s_pre_tot) {
+  for_tile_slots(t, Nc, s_pre2, s_pre_tot, [&](int J, int K, int M) {
+    restrict_slot<T, NC>(Nc, rsc, Nf, rsf, J, K, M, rb, fcb, ucb);
+  });
+}
+
 template <class T>
-__global__ void __launch_bounds__(CTA) k_restrict(int Nc, const int* __restrict__ rsc, int64_t bc, T* __restrict__ fc, T* __restrict__ fIc,
+__global__ void __launch_bounds__(CTA, 4) k_restrict(int Nc, const int* __restrict__ rsc, int64_t bc, T* __restrict__ fc, T* __restrict__ fIc,
                                                   T* __restrict__ uc, T* __restrict__ uIc, int Nf, const int* __restrict__ rsf, int64_t bf,
                                                   const T* __restrict__ rf, const Tile* __restrict__ tiles, int n_tiles,
                                                   const int* __restrict__ act, int n_act,
@@ -1105,7 +1207,7 @@ __global__ void __launch_bounds__(CTA) k_restrict(int Nc, const int* __restrict_
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
   __shared__ int s_unit;
-  HHG_UNITS_DYN(n_if_units, n_tiles, n_act, sched, &s_unit) {
+  HHG_UNITS_DYN(n_if_units, n_tiles * RESTRICT_SPLIT, n_act, sched, &s_unit) {
     if (const int ic_ = if_chunk(unit, n_if_units); ic_ >= 0) {
       const int q = ic_ * CTA + tid256();
       if (q < n_list) {
@@ -1126,25 +1228,11 @@ __global__ void __launch_bounds__(CTA) k_restrict(int Nc, const int* __restrict_
     }
     Tile t;
     int macro;
-    vol_unit(vol_index(unit, n_if_units), n_act, tiles, act, t, macro);
-    const T* rb = rf + (size_t)macro * bf;
-    T* fb = fc + (size_t)macro * bc;
-    T* ub = uc + (size_t)macro * bc;
-    HHG_TILE_NODES(Nc, rsc, t, s_pre, {
-      const int fi = 2 * i, fj = 2 * j, fk = 2 * k;
-      T acc = T(0);
-_Pragma("unroll")
-      for (int d = 1; d < NDIR; ++d) {
-        int di, dj, dk;
-        dir_ijk(d, di, dj, dk);
-        acc += rb[lidx32(rsf, Nf, fi + di, fj + dj, fk + dk)];
-      }
-      const int me = lidx32(rsc, Nc, i, j, k);
-      fb[me] = rb[lidx32(rsf, Nf, fi, fj, fk)] + T(0.5) * acc;
-      ub[me] = T(0);
-    })
+    vol_subunit(vol_index(unit, n_if_units), n_act, RESTRICT_SPLIT, tiles, act, t, macro);
+    restrict_tile<T, true>(t, Nc, rsc, Nf, rsf, rf + (size_t)macro * bf, fc + (size_t)macro * bc,
+                           uc + (size_t)macro * bc, s_pre2, s_pre_tot);
   }
-  finish_units(sched, n_if_units + n_tiles * n_act);
+  finish_units(sched, n_if_units + n_tiles * RESTRICT_SPLIT * n_act);
 }
 
 // ---------------------------------------------------------------------------
@@ -1171,6 +1259,143 @@ __device__ __forceinline__ T interp(const T* __restrict__ cb, int Nc, const int*
   return T(0.5) * (a + b);
 }
 
+// Coarse edge through a fine node of parities (pi, pj, pk), not all zero: the
+// fine node is the midpoint of coarse nodes (i -+ di, j -+ dj, k -+ dk) / 2.
+__device__ __forceinline__ void edge_dir(int code, int& di, int& dj, int& dk) {
+  switch (code) {
+    case 1: di = 1; dj = 0; dk = 0; break;
+    case 2: di = 0; dj = 1; dk = 0; break;
+    case 4: di = 0; dj = 0; dk = 1; break;
+    case 3: di = -1; dj = 1; dk = 0; break;
+    case 5: di = -1; dj = 0; dk = 1; break;
+    case 6: di = 0; dj = -1; dk = 1; break;
+    default: di = 1; dj = -1; dk = 1; break;
+  }
+}
+
+// Prolongation u_f += P u_c of the fine nodes i = 4m .. 4m + 3 of interior
+// row j of fine slice k (one per colour array; fine block fb, coarse block
+// cb).  The parities of a node are (q & 1, j & 1, k & 1), so an item has two
+// interpolation cases (even and odd i): the coarse node (i/2, j/2, k/2) when
+// all parities are even, else the mean of the coarse edge's two ends.  Their
+// coarse rows are located once per item; coarse node I = 2m + const lies in
+// colour array (I + 2J + 3K) & 3 at slot I >> 2.  Plain loads for the fine
+// values (written by this launch), the read-only path for the coarse ones
+// when NC.  Nodes of colour skip are left out (-1: none).
+template <class T, bool NC>
+__device__ __forceinline__ void prolong_slot(int Nf, const int* __restrict__ rsf, int Nc, const int* __restrict__ rsc,
+                                             int j, int k, int m, T* __restrict__ fb, const T* __restrict__ cb,
+                                             int skip) {
+  const int L = Nf - 1 - j - k;
+  const int CSf = __ldg(rsf + Nf + 2), CSc = __ldg(rsc + Nc + 2);
+  const int rbf = row_base(rsf, Nf, j, k) + m;
+  const int cf = 2 * j + 3 * k;
+  // per parity of i: direction, the two coarse rows and their colour terms
+  int di[2], rba[2], rbb[2], ca[2], cbb[2], code[2];
+#pragma unroll
+  for (int par = 0; par < 2; ++par) {
+    code[par] = par | ((j & 1) << 1) | ((k & 1) << 2);
+    int dj = 0, dk = 0;
+    di[par] = 0;
+    if (code[par]) edge_dir(code[par], di[par], dj, dk);
+    const int JA = (j - dj) >> 1, KA = (k - dk) >> 1, JB = (j + dj) >> 1, KB = (k + dk) >> 1;
+    rba[par] = row_base(rsc, Nc, JA, KA);
+    rbb[par] = row_base(rsc, Nc, JB, KB);
+    ca[par] = 2 * JA + 3 * KA;
+    cbb[par] = 2 * JB + 3 * KB;
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int i = 4 * m + q;
+    if (i < 1 || i > L || ((q + cf) & 3) == skip) continue;
+    const int par = q & 1;
+    T* out = fb + ((q + cf) & 3) * CSf + rbf;
+    const T u = *out;
+    if (code[par] == 0) {
+      const int I = 2 * m + (q >> 1);
+      const int o = ((I + ca[par]) & 3) * CSc + rba[par] + (I >> 2);
+      *out = u + (NC ? __ldg(cb + o) : cb[o]);
+    } else {
+      const int IA = 2 * m + ((q - di[par]) >> 1), IB = 2 * m + ((q + di[par]) >> 1);
+      const int oa = ((IA + ca[par]) & 3) * CSc + rba[par] + (IA >> 2);
+      const int ob = ((IB + cbb[par]) & 3) * CSc + rbb[par] + (IB >> 2);
+      const T a = NC ? __ldg(cb + oa) : cb[oa];
+      const T b = NC ? __ldg(cb + ob) : cb[ob];
+      *out = fma(T(0.5), a + b, u);   // the halving is exact: same value as a separate multiply
+    }
+  }
+}
+
+// The same prolongation for the colour-c nodes in slots m0 .. m0 + VW - 1 of
+// interior row j of fine slice k, one 16-byte vector of fine values: all
+// nodes i = 4m + ic of a colour row share their parities, hence one case.
+template <class T, bool NC>
+__device__ __forceinline__ void prolong_group(int Nf, const int* __restrict__ rsf, int Nc, const int* __restrict__ rsc,
+                                              int j, int k, int g, int c, T* __restrict__ fb,
+                                              const T* __restrict__ cb) {
+  constexpr int VW = Vec<T>::n;
+  int ic, mlo, n;
+  colour_row(Nf, j, k, c, ic, mlo, n);
+  const int m0 = g * VW;
+  const int lo = max(mlo - m0, 0), hi = min(mlo + n - m0, VW);
+  T* out = fb + c * __ldg(rsf + Nf + 2) + row_base(rsf, Nf, j, k) + m0;
+  T v[VW];
+  Vec<T>::template load<false>(out, v);
+  const int CSc = __ldg(rsc + Nc + 2);
+  const int code = (ic & 1) | ((j & 1) << 1) | ((k & 1) << 2);
+  int di = 0, dj = 0, dk = 0;
+  if (code) edge_dir(code, di, dj, dk);
+  const int JA = (j - dj) >> 1, KA = (k - dk) >> 1, ia = (ic - di) >> 1;
+  const int JB = (j + dj) >> 1, KB = (k + dk) >> 1, ib = (ic + di) >> 1;
+  const int rba = row_base(rsc, Nc, JA, KA), rbb = row_base(rsc, Nc, JB, KB);
+  const int ca = ia + 2 * JA + 3 * KA, cbb = ib + 2 * JB + 3 * KB;
+#pragma unroll
+  for (int q = 0; q < VW; ++q) {
+    if (q < lo || q >= hi) continue;
+    const int two_m = 2 * (m0 + q);
+    const int oa = ((ca + two_m) & 3) * CSc + rba + ((two_m + ia) >> 2);
+    const T a = NC ? __ldg(cb + oa) : cb[oa];
+    if (code == 0) {
+      v[q] += a;
+    } else {
+      const int ob = ((cbb + two_m) & 3) * CSc + rbb + ((two_m + ib) >> 2);
+      const T b = NC ? __ldg(cb + ob) : cb[ob];
+      v[q] = fma(T(0.5), a + b, v[q]);   // the halving is exact: same value as a separate multiply
+    }
+  }
+  store_lanes(out, v, lo, hi);
+}
+
+// Volume prolongation of a fine tile: FP64 one item per slot (four nodes,
+// all colours), FP32 colour by colour in 16-byte vectors (measured faster for
+// each precision); colour skip left out (-1: none).
+template <class T, bool NC>
+__device__ __forceinline__ void prolong_tile(const Tile& t, int Nf, const int* __restrict__ rsf, int Nc,
+                                             const int* __restrict__ rsc, T* __restrict__ fb, const T* __restrict__ cb,
+                                             int skip, int (*s_pre2)[33], int* s_pre_tot) {
+  if constexpr (std::is_same<T, float>::value) {
+    constexpr int VW = Vec<T>::n;
+    for (int c = 0; c < 4; ++c) {
+      if (c == skip) continue;
+      const int total = flat_setup_slabs(t, Nf, c, true, VW, s_pre2, s_pre_tot);
+      int sl = 0;
+      for (int tt = tid256(); tt < total; tt += CTA) {
+        while (tt >= s_pre_tot[sl + 1]) ++sl;
+        const int k = t.k + sl;
+        const Tile ts{k, t.j0, t.m0, 1};
+        int j, g;
+        flat_item(ts, Nf, c, true, s_pre2[sl], tt - s_pre_tot[sl], j, g, VW);
+        prolong_group<T, NC>(Nf, rsf, Nc, rsc, j, k, g, c, fb, cb);
+      }
+      __syncthreads();
+    }
+  } else {
+    for_tile_slots(t, Nf, s_pre2, s_pre_tot, [&](int j, int k, int m) {
+      prolong_slot<T, NC>(Nf, rsf, Nc, rsc, j, k, m, fb, cb, skip);
+    });
+  }
+}
+
 template <class T>
 __global__ void __launch_bounds__(CTA) k_prolong(int Nf, const int* __restrict__ rsf, int64_t bf, T* __restrict__ uf, T* __restrict__ uIf,
                                                  int Nc, const int* __restrict__ rsc, int64_t bc, const T* __restrict__ uc,
@@ -1178,14 +1403,15 @@ __global__ void __launch_bounds__(CTA) k_prolong(int Nf, const int* __restrict__
                                                  const int* __restrict__ act, int n_act, const int* __restrict__ cptr,
                                                  const Copy* __restrict__ cps, const uint32_t* __restrict__ cpo,
                                                  const int* __restrict__ list,
-                                                 int n_list, int n_if_units, int* __restrict__ sched) {
+                                                 int n_list, int n_if_units, int* __restrict__ sched, int skip,
+                                                 int if_lo, int if_hi) {
   __shared__ int s_pre2[MAX_SLABS][33];
   __shared__ int s_pre_tot[MAX_SLABS + 1];
   __shared__ int s_unit;
   HHG_UNITS_DYN(n_if_units, n_tiles, n_act, sched, &s_unit) {
     if (const int ic_ = if_chunk(unit, n_if_units); ic_ >= 0) {
       const int q = ic_ * CTA + tid256();
-      if (q < n_list) {
+      if (q < n_list && (q < if_lo || q >= if_hi)) {
         const int node = list[q];
         const int c0 = cptr[node], c1 = cptr[node + 1];
         const Copy cp = cps[c0];
@@ -1198,9 +1424,8 @@ __global__ void __launch_bounds__(CTA) k_prolong(int Nf, const int* __restrict__
     Tile t;
     int macro;
     vol_unit(vol_index(unit, n_if_units), n_act, tiles, act, t, macro);
-    T* fb = uf + (size_t)macro * bf;
-    const T* cb = uc + (size_t)macro * bc;
-    HHG_TILE_NODES(Nf, rsf, t, s_pre, { fb[lidx32(rsf, Nf, i, j, k)] += interp(cb, Nc, rsc, i, j, k); })
+    prolong_tile<T, true>(t, Nf, rsf, Nc, rsc, uf + (size_t)macro * bf, uc + (size_t)macro * bc, skip, s_pre2,
+                          s_pre_tot);
   }
   finish_units(sched, n_if_units + n_tiles * n_act);
 }
@@ -1864,28 +2089,11 @@ __device__ void unit_restrict(const BOp& op, int unit, int (*s_pre2)[33], int* s
     }
     return;
   }
-  const int vb = unit - op.n_if_units;
-  const Tile t = C.tiles_int[vb / pc.n_act];
-  const int macro = pc.act[vb % pc.n_act];
-  const T* rb = rf + (size_t)macro * F.block;
-  T* fb = fc + (size_t)macro * C.block;
-  T* ub = uc + (size_t)macro * C.block;
-  const int Nc = C.N, Nf = F.N;
-  const int* rsc = C.rs;
-  const int* rsf = F.rs;
-  HHG_TILE_NODES(Nc, rsc, t, s_pre, {
-    const int fi = 2 * i, fj = 2 * j, fk = 2 * k;
-    T acc = T(0);
-_Pragma("unroll")
-    for (int d = 1; d < NDIR; ++d) {
-      int di, dj, dk;
-      dir_ijk(d, di, dj, dk);
-      acc += rb[lidx32(rsf, Nf, fi + di, fj + dj, fk + dk)];
-    }
-    const int me = lidx32(rsc, Nc, i, j, k);
-    fb[me] = rb[lidx32(rsf, Nf, fi, fj, fk)] + T(0.5) * acc;
-    ub[me] = T(0);
-  })
+  Tile t;
+  int macro;
+  vol_subunit(unit - op.n_if_units, pc.n_act, RESTRICT_SPLIT, C.tiles_int, pc.act, t, macro);
+  restrict_tile<T, false>(t, C.N, C.rs, F.N, F.rs, rf + (size_t)macro * F.block, fc + (size_t)macro * C.block,
+                          uc + (size_t)macro * C.block, s_pre2, s_pre_tot);
 }
 
 // Unit of the prolongation u_f += P u_c (k_prolong).
@@ -1898,7 +2106,7 @@ __device__ void unit_prolong(const BOp& op, int unit, int (*s_pre2)[33], int* s_
   const T* uc = (const T*)op.uc;
   if (unit < op.n_if_units) {
     const int q = unit * CTA + tid256();
-    if (q < op.n_list) {
+    if (q < op.n_list && (q < op.skip_lo || q >= op.skip_hi)) {
       T* uIf = (T*)op.uI;
       const int node = pf.free_if[q];
       const int c0 = F.cptr[node], c1 = F.cptr[node + 1];
@@ -1912,12 +2120,8 @@ __device__ void unit_prolong(const BOp& op, int unit, int (*s_pre2)[33], int* s_
   const int vb = unit - op.n_if_units;
   const Tile t = F.tiles_int[vb / pf.n_act];
   const int macro = pf.act[vb % pf.n_act];
-  T* fb = uf + (size_t)macro * F.block;
-  const T* cb = uc + (size_t)macro * C.block;
-  const int Nf = F.N, Nc = C.N;
-  const int* rsf = F.rs;
-  const int* rsc = C.rs;
-  HHG_TILE_NODES(Nf, rsf, t, s_pre, { fb[lidx32(rsf, Nf, i, j, k)] += interp(cb, Nc, rsc, i, j, k); })
+  prolong_tile<T, false>(t, F.N, F.rs, C.N, C.rs, uf + (size_t)macro * F.block, uc + (size_t)macro * C.block, op.skip,
+                         s_pre2, s_pre_tot);
 }
 
 // Unit of the FP64 residual handed to the FP32 cycle (k_res_f32, no norm).
@@ -2551,7 +2755,7 @@ cudaError_t restrict_to(const LevelArgs& C, const LevelArgs& F, const ProbArgs& 
                         T* uIc, cudaStream_t s) {
   if (g_rec) {
     const int nl = pc.col_off[4];
-    const Units g = units(nl + pc.n_zero, C.n_tiles_int, pc.n_act);
+    const Units g = units(nl + pc.n_zero, C.n_tiles_int * RESTRICT_SPLIT, pc.n_act);
     if (g.total == 0) return cudaSuccess;
     BOp op = new_op<T>(BOP_RESTRICT);
     op.L = F;
@@ -2570,7 +2774,7 @@ cudaError_t restrict_to(const LevelArgs& C, const LevelArgs& F, const ProbArgs& 
     return cudaSuccess;
   }
   const int n = pc.col_off[4];
-  const Units g = units(n + pc.n_zero, C.n_tiles_int, pc.n_act);
+  const Units g = units(n + pc.n_zero, C.n_tiles_int * RESTRICT_SPLIT, pc.n_act);
   if (g.total == 0) return cudaSuccess;
   const unsigned grid = resident_grid((const void*)k_restrict<T>, g.total, pc.grid_cap);
   ++g_kernel_launches;
@@ -2582,12 +2786,17 @@ cudaError_t restrict_to(const LevelArgs& C, const LevelArgs& F, const ProbArgs& 
 
 template <class T>
 cudaError_t prolong_add(const LevelArgs& F, const LevelArgs& C, const ProbArgs& pf, T* uf, T* uIf, const T* uc,
-                        cudaStream_t s) {
+                        cudaStream_t s, int skip, int if_lo, int if_hi) {
+  skip = skip >= 0 && skip < 4 ? skip : -1;
+  if (if_hi <= if_lo) if_lo = if_hi = 0;
   if (g_rec) {
     const int nl = pf.col_off[4];
     const Units g = units(nl, F.n_tiles_int, pf.n_act);
     if (g.total == 0) return cudaSuccess;
     BOp op = new_op<T>(BOP_PROLONG);
+    op.skip = skip;
+    op.skip_lo = if_lo;
+    op.skip_hi = if_hi;
     op.L = F;
     op.C = C;
     op.P = pf;
@@ -2607,7 +2816,7 @@ cudaError_t prolong_add(const LevelArgs& F, const LevelArgs& C, const ProbArgs& 
   ++g_kernel_launches;
   k_prolong<T><<<grid, cta_shape(), 0, s>>>(F.N, F.rs, F.block, uf, uIf, C.N, C.rs, C.block, uc, F.tiles_int,
                                             F.n_tiles_int, pf.act, pf.n_act, F.cptr, F.cps, F.cp_off, pf.free_if, n,
-                                            g.n_if_units, pf.sched);
+                                            g.n_if_units, pf.sched, skip, if_lo, if_hi);
   return cudaGetLastError();
 }
 
@@ -2931,7 +3140,7 @@ cudaError_t zero_problem_blocks(const LevelArgs& L, const ProbArgs& p, T* u, T* 
   template cudaError_t restrict_to<T>(const LevelArgs&, const LevelArgs&, const ProbArgs&, const T*, T*, T*, T*, \
                                       T*, cudaStream_t);                                                       \
   template cudaError_t prolong_add<T>(const LevelArgs&, const LevelArgs&, const ProbArgs&, T*, T*, const T*,     \
-                                      cudaStream_t);                                                           \
+                                      cudaStream_t, int, int, int);                                            \
   template cudaError_t coarse_cg<T>(const DevProblem&, const T*, const T*, T*, T*, double, int, cudaStream_t,     \
                                     double*);                                                                  \
   template cudaError_t import_vec<T>(const LevelArgs&, const MacroGeo*, int, int64_t, int64_t, const double*,    \
