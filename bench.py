@@ -376,6 +376,9 @@ def run_ours(args):
     hhg.hhg_profile_enable(M.h, 1)
     l0 = hhg.hhg_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    # the timed steps are bracketed by cudaProfilerStart/Stop, so that kernel
+    # captures can start there (ncu --profile-from-start off)
+    torch.cuda.profiler.start()
     e0.record(stream)
     cyc_list = []
     for _ in range(args.steps):
@@ -383,6 +386,7 @@ def run_ours(args):
         cyc_list.append(cycles)
     e1.record(stream)
     torch.cuda.synchronize()
+    torch.cuda.profiler.stop()
     l1 = hhg.hhg_launch_count()
     n_prof, prof_ms = hhg.hhg_profile_read(M.h)
     hhg.hhg_profile_enable(M.h, 0)
