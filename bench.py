@@ -424,6 +424,11 @@ def run_ours(args):
     u_pin = torch.zeros_like(f_pin).pin_memory()
     torch.cuda.synchronize()
     k_e2e = max(1, min(args.steps, 3))
+    # one untimed pass: the first host-pointer call allocates the mesh's
+    # staging buffer (a one-time cost per mesh, like the device path's warm-up)
+    M.set_problem(f_pin.numpy(), u0_pin.numpy())
+    M.get_solution(u_pin.numpy())
+    torch.cuda.synchronize()
     if dist:
         dist.barrier()
     t0 = time.perf_counter()
