@@ -387,9 +387,11 @@ int hhg_vcycle_noalloc(hhg_mesh* mesh, int pre, int post, void* stream);
  * default: as many as the GPU holds at once).  A level-wide launch walks its
  * work units (interface chunks, then volume tiles) with a grid stride when
  * it has fewer than 4 units per CTA, and otherwise hands the units out
- * through a per-problem counter (the dynamic walk of large launches); a small
- * limit makes small meshes take the dynamic walk.  The result does not
- * depend on the limit.  Drops the captured recovery-cycle graph.
+ * through a per-problem counter (the dynamic walk of large launches, where
+ * the Gauss-Seidel and residual launches place the interface chunks evenly
+ * among the volume tiles); a small limit makes small meshes take the dynamic
+ * walk.  The result does not depend on the limit (a residual norm only up to
+ * the order of its summation).  Drops the captured recovery-cycle graph.
  * hhg_walk_counts: counts[0..3] = level-wide launches that completed the
  * dynamic walk, for the global problem, the faulty sub-problem (Omega_F),
  * the healthy sub-problem with Gamma frozen and the Neumann problem of DN

@@ -88,6 +88,32 @@ __host__ __device__ __forceinline__ int lidx(const int* SL, int N, int i, int j,
   return ((i + 2 * j + 3 * k) & 3) * SL[N + 2] + SL[k] + slot_prefix(M) - slot_prefix(M - j) + (i >> 2);
 }
 
+// Walk position u of a launch with n_if interface chunks and n_vol volume
+// units, chunks spread evenly among the volume units: one chunk after every
+// R = n_vol / n_if volume units (chunks left over when n_vol < n_if follow,
+// then the remaining volume units).  Returns the chunk index, or -1 with the
+// volume unit's index in vol.  A bijection of [0, n_if + n_vol) onto the
+// chunks and the volume units, both in their own order.
+__host__ __device__ __forceinline__ int spread_position(int u, int n_if, int n_vol, int& vol) {
+  if (n_if == 0) {
+    vol = u;
+    return -1;
+  }
+  const int R = n_vol / n_if > 1 ? n_vol / n_if : 1;
+  const int m = n_if < n_vol / R ? n_if : n_vol / R;   // chunks placed among the volume units
+  const int span = m * (R + 1);
+  if (u < span) {
+    const int q = u / (R + 1), r = u - q * (R + 1);
+    if (r == R) return q;
+    vol = q * R + r;
+    return -1;
+  }
+  u -= span;
+  if (u < n_if - m) return m + u;
+  vol = m * R + (u - (n_if - m));
+  return -1;
+}
+
 // Slice-start table (N + 3 entries, last = CS) and block size (4 CS, CS a
 // multiple of 64) of refinement N.
 inline int64_t build_slice_starts(int N, std::vector<int>& SL) {

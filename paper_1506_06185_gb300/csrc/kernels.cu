@@ -1,10 +1,10 @@
 // CUDA kernels of the HHG multigrid for sm_103a.
 //
 // Every level-wide operation is one launch of 256-thread CTAs (32 x 8), as many
-// as the GPU holds at once, walking a list of work units with a grid stride:
-// the first units are chunks of free interface (face / edge / vertex) nodes,
-// one node per thread; the rest are row-pair tiles of the volume interiors of
-// the active macros.
+// as the GPU holds at once, walking a list of work units: chunks of free
+// interface (face / edge / vertex) nodes, one node per thread, and row-pair
+// tiles of the volume interiors of the active macros (the chunks first, or in
+// large stencil launches spread evenly among the tiles).
 //
 // Volume work: in slice k of a macro's lattice the interior rows are
 // j = 1..J (J = N - 2 - k) and row j holds N - 1 - j - k nodes.  Rows are
@@ -237,10 +237,10 @@ __device__ __forceinline__ void flat_item(const Tile& t, int N, int c, bool colo
   }
 
 // Work units of a fused launch: units [0, n_if_units) are chunks of 256
-// interface list entries, the rest (tile, active macro) pairs.  CTAs walk the
-// units with a grid stride, so a launch has a few CTAs per SM whatever the
-// level size.  (Spreading the interface chunks among the volume units was
-// measured slower.)
+// interface list entries, the rest (tile, active macro) pairs (large stencil
+// launches map walk positions to units through spread_unit instead).  CTAs
+// walk the units with a grid stride, so a launch has a few CTAs per SM
+// whatever the level size.
 #define HHG_UNITS(n_if_units, n_tiles, n_act)                                                     \
   for (int unit = blockIdx.x, n_units_ = (n_if_units) + (n_tiles) * (n_act); unit < n_units_;     \
        unit += gridDim.x)
@@ -253,8 +253,9 @@ __device__ __forceinline__ int vol_index(int u, int n_if_units) { return u - n_i
 // Walk over the same units, dynamic for large launches: CTA b starts with
 // unit b; with at least DYN_UNITS_PER_CTA units per CTA, later units come from
 // the problem's counter sched[0] (unit = gridDim.x + counter), so the units
-// (interface chunks, then tiles by decreasing work) are handed out greedily
-// and the launch ends with the smallest tiles; smaller launches keep the grid
+// (tiles by decreasing work, the interface chunks spread among them, see
+// spread_unit) are handed out greedily and the launch ends with the smallest
+// tiles; smaller launches keep the grid
 // stride (measured faster there, e.g. the local recovery cycles of a few
 // macros).  Thread 0 takes the next unit one unit ahead, so the atomic's
 // latency hides behind the work.  The CTA that finishes last (counted in
@@ -301,6 +302,25 @@ __device__ __forceinline__ void finish_units(int* sched, int n_units) {
   for (int n_units_ = (n_if_units) + (n_tiles) * (n_act), nxt_ = 0,                                    \
            unit = walk_first(n_units_, (sched), (s_unit), nxt_);                                       \
        unit < n_units_; unit = walk_next(n_units_, (sched), (s_unit), nxt_))
+
+// Position u of a stencil launch's walk -> its interface chunk (returned, or
+// -1 for a volume unit, whose index is written to vol).  Launches that take
+// the dynamic walk interleave the n_if interface chunks with the n_vol volume
+// units (spread_position in hhg_internal.h: one chunk after every
+// R = n_vol / n_if volume units).  An interface chunk gathers scattered
+// neighbours and does little arithmetic, a volume tile streams contiguous
+// rows through the FP64 (or load) pipe, so CTAs of the two kinds side by side
+// on an SM keep the pipe busier than a launch whose first units are all
+// interface chunks (finest FP64 Gauss-Seidel launch at refinement 8: 0.416
+// against 0.442 ms).  Smaller launches keep the chunks first (measured faster
+// on the coarse levels).  Every unit still runs once.
+__device__ __forceinline__ int spread_unit(int u, int n_if, int n_vol, int& vol) {
+  if (!walk_dynamic(n_if + n_vol)) {
+    vol = u - n_if;
+    return u < n_if ? u : -1;
+  }
+  return spread_position(u, n_if, n_vol, vol);
+}
 
 // Volume unit -> (tile, macro).  The macro index runs fastest and the tile
 // lists are sorted by decreasing work, so the last units of a grid-stride walk
@@ -618,7 +638,8 @@ __global__ void __launch_bounds__(CTA, 5) k_gs(int N, const int* __restrict__ rs
   __shared__ int s_pre_tot[MAX_SLABS + 1];
   __shared__ int s_unit;
   HHG_UNITS_DYN(n_if_units, n_tiles, n_act, sched, &s_unit) {
-    if (const int ic_ = if_chunk(unit, n_if_units); ic_ >= 0) {
+    int vol_ = 0;
+    if (const int ic_ = spread_unit(unit, n_if_units, n_tiles * n_act, vol_); ic_ >= 0) {
       const int q = ic_ * CTA + tid256();
       if (q < n_list) {
         const int node = list[q];
@@ -638,7 +659,7 @@ __global__ void __launch_bounds__(CTA, 5) k_gs(int N, const int* __restrict__ rs
     }
     Tile t;
     int macro;
-    vol_unit(vol_index(unit, n_if_units), n_act, tiles, act, t, macro);
+    vol_unit(vol_, n_act, tiles, act, t, macro);
     T* ub = u + (size_t)macro * block;
     const T* fb = f + (size_t)macro * block;
     const T* w = W + (size_t)macro * 16 * NDIR;
@@ -1038,7 +1059,8 @@ __global__ void __launch_bounds__(CTA, 4) k_res(int N, const int* __restrict__ r
   double ss = 0.0;
   __shared__ int s_unit;
   HHG_UNITS_DYN(n_if_units, n_tiles, n_act, sched, &s_unit) {
-    if (const int ic_ = if_chunk(unit, n_if_units); ic_ >= 0) {
+    int vol_ = 0;
+    if (const int ic_ = spread_unit(unit, n_if_units, n_tiles * n_act, vol_); ic_ >= 0) {
       const int q = ic_ * CTA + tid256();
       if (q < n_list) {
         const int node = list[q];
@@ -1062,7 +1084,7 @@ __global__ void __launch_bounds__(CTA, 4) k_res(int N, const int* __restrict__ r
     }
     Tile t;
     int macro;
-    vol_unit(vol_index(unit, n_if_units), n_act, tiles, act, t, macro);
+    vol_unit(vol_, n_act, tiles, act, t, macro);
     const T* ub = u + (size_t)macro * block;
     const T* fb = f + (size_t)macro * block;
     T* rb = r + (size_t)macro * block;
@@ -1451,7 +1473,8 @@ __global__ void __launch_bounds__(CTA) k_res_f32(int N, const int* __restrict__ 
   double ss = 0.0;
   __shared__ int s_unit;
   HHG_UNITS_DYN(n_if_units, n_tiles, n_act, sched, &s_unit) {
-    if (const int ic_ = if_chunk(unit, n_if_units); ic_ >= 0) {
+    int vol_ = 0;
+    if (const int ic_ = spread_unit(unit, n_if_units, n_tiles * n_act, vol_); ic_ >= 0) {
       const int q = ic_ * CTA + tid256();
       if (q < n_list) {
         const int node = list[q];
@@ -1470,7 +1493,7 @@ __global__ void __launch_bounds__(CTA) k_res_f32(int N, const int* __restrict__ 
     }
     Tile t;
     int macro;
-    vol_unit(vol_index(unit, n_if_units), n_act, tiles, act, t, macro);
+    vol_unit(vol_, n_act, tiles, act, t, macro);
     const double* ub = u + (size_t)macro * block;
     const double* fb = f + (size_t)macro * block;
     float* ob = f32 + (size_t)macro * block;

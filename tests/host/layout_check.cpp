@@ -6,6 +6,7 @@
 // Checks every refinement N = 2 .. N_max and N = 256, 512, and prints one
 // line per failed property (exit status 1), else "ok".
 #include <algorithm>
+#include <array>
 #include <cstdio>
 #include <cstdlib>
 #include <vector>
@@ -197,6 +198,41 @@ static void check_stream_tiles(int N, int band, int VW) {
   }
 }
 
+// The walk order of the large stencil launches (spread_position): every
+// interface chunk and every volume unit exactly once, each kind in its own
+// order, and while volume units remain no more than R = n_vol / n_if of them
+// between two chunks.
+static void check_spread(int n_if, int n_vol) {
+  const int N = -1;   // for the CHECK message
+  std::vector<int> seen_if(n_if, 0), seen_vol(n_vol, 0);
+  int last_if = -1, last_vol = -1, run = 0, max_run = 0;
+  for (int u = 0; u < n_if + n_vol; ++u) {
+    int vol = -1;
+    const int c = spread_position(u, n_if, n_vol, vol);
+    if (c >= 0) {
+      CHECK(c < n_if && c == last_if + 1, "spread %d/%d: position %d gives chunk %d after %d", n_if, n_vol, u, c,
+            last_if);
+      if (c < n_if) ++seen_if[c];
+      last_if = c;
+      max_run = std::max(max_run, run);
+      run = 0;
+    } else {
+      CHECK(vol >= 0 && vol < n_vol && vol == last_vol + 1, "spread %d/%d: position %d gives unit %d after %d", n_if,
+            n_vol, u, vol, last_vol);
+      if (vol >= 0 && vol < n_vol) ++seen_vol[vol];
+      last_vol = vol;
+      ++run;
+    }
+  }
+  for (int q = 0; q < n_if; ++q) CHECK(seen_if[q] == 1, "spread %d/%d: chunk %d seen %d times", n_if, n_vol, q, seen_if[q]);
+  for (int b = 0; b < n_vol; ++b)
+    CHECK(seen_vol[b] == 1, "spread %d/%d: unit %d seen %d times", n_if, n_vol, b, seen_vol[b]);
+  if (n_if > 0) {
+    const int R = std::max(1, n_vol / n_if);
+    CHECK(max_run <= R, "spread %d/%d: %d volume units between two chunks (R = %d)", n_if, n_vol, max_run, R);
+  }
+}
+
 int main(int argc, char** argv) {
   if (argc < 2) return 2;
   const int n_max = std::atoi(argv[1]);
@@ -223,6 +259,12 @@ int main(int argc, char** argv) {
     check_stream_tiles(N, N >= 512 ? STREAM_BAND / 2 : STREAM_BAND, 2);
     check_stream_tiles(N, N >= 512 ? STREAM_BAND32 / 2 : STREAM_BAND32, 4);
   }
+  for (int n_if = 0; n_if <= 40; ++n_if)
+    for (int n_vol = 0; n_vol <= 130; ++n_vol) check_spread(n_if, n_vol);
+  // the finest launches of the bench's mesh (refinement 8: about 2300 chunks
+  // per colour, 5000 .. 31000 tiles) and of its residual (four colours)
+  for (const auto& c : {std::array<int, 2>{2284, 5040}, {2284, 8784}, {2284, 30912}, {9136, 8784}, {9136, 5040}})
+    check_spread(c[0], c[1]);
   if (failures) {
     std::printf("%d failures\n", failures);
     return 1;
