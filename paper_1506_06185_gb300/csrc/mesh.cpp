@@ -243,6 +243,59 @@ void build_tiles(int N, bool interior, std::vector<Tile>& out) {
 // `slabs` consecutive slices k .. k + pad - 1, so that the CTA that loads a
 // slice's rows reuses them for the next slice (pairs beyond a slice's count
 // are empty).
+// Renumber the interface nodes of a level colour by colour and, within a
+// colour, by the block offset of a "home" copy: the first copy that lies in
+// the plane j = 0 or k = 0 of its macro (whose rows are contiguous in the
+// block; the planes i = 0 and i + j + k = N cut across the rows), else the
+// first copy.  The home copy is moved to the front of the node's copy list,
+// so the interface stencil tables read shared neighbours from the home block.
+// A colour's Gauss-Seidel launch then touches the masters, loads and copy
+// pointers of consecutive node ids, and on a face lying in a contiguous plane
+// the neighbour gathers and the home copy's write of consecutive nodes land
+// on consecutive slots.
+static void number_if_by_colour(HostLevel& L) {
+  const int n_if = L.n_if;
+  std::vector<int> home(n_if);
+  std::vector<int64_t> home_off(n_if);
+  for (int n = 0; n < n_if; ++n) {
+    int h = L.if_cptr[n];
+    for (int c = L.if_cptr[n]; c < L.if_cptr[n + 1]; ++c)
+      if (L.if_copy[c].j == 0 || L.if_copy[c].k == 0) {
+        h = c;
+        break;
+      }
+    home[n] = h;
+    const Copy& cp = L.if_copy[h];
+    home_off[n] = (int64_t)cp.macro * L.block + lidx(L.SL.data(), L.N, cp.i, cp.j, cp.k);
+  }
+  std::vector<int> order(n_if);
+  for (int n = 0; n < n_if; ++n) order[n] = n;
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    if (L.if_colour[a] != L.if_colour[b]) return L.if_colour[a] < L.if_colour[b];
+    return home_off[a] < home_off[b];
+  });
+  std::vector<int64_t> gid(n_if);
+  std::vector<unsigned char> col(n_if), dir(n_if);
+  std::vector<int> cptr(1, 0);
+  std::vector<Copy> copies;
+  copies.reserve(L.if_copy.size());
+  for (int n = 0; n < n_if; ++n) {
+    const int o = order[n];
+    gid[n] = L.if_gid[o];
+    col[n] = L.if_colour[o];
+    dir[n] = L.if_dirichlet[o];
+    copies.push_back(L.if_copy[home[o]]);
+    for (int c = L.if_cptr[o]; c < L.if_cptr[o + 1]; ++c)
+      if (c != home[o]) copies.push_back(L.if_copy[c]);
+    cptr.push_back((int)copies.size());
+  }
+  L.if_gid.swap(gid);
+  L.if_colour.swap(col);
+  L.if_dirichlet.swap(dir);
+  L.if_cptr.swap(cptr);
+  L.if_copy.swap(copies);
+}
+
 void build_pair_tiles(int N, std::vector<Tile>& out, int target, int slabs) {
   out.clear();
   for (int k0 = 1; k0 <= N - 3; k0 += slabs) {
@@ -455,6 +508,7 @@ void build_host_mesh(HostMesh& m, const int sub[3], int R, int r0, const double*
       }
     }
     L.n_if = (int)L.if_gid.size();
+    number_if_by_colour(L);
     build_pair_tiles(N, L.tiles_int, TILE_TARGET_DEFAULT, TILE_SLABS);
     build_tiles(N, false, L.tiles_all);
     if (N >= STREAM_MIN_N) {
