@@ -276,9 +276,13 @@ int hhg_grad_coeff(hhg_mesh* mesh, const double* u, const double* lam, double* g
  * the global problem with each candidate tile shape (nodes per tile and
  * slices per tile: 256/4, 512/8, 1024/8, 2048/16) on the FP64 iterate (which
  * the sweeps smooth) and, on precision-32 meshes, also on the FP32 arrays,
- * and keeps for that level the shape with the least total time.
+ * and keeps for that level the shape with the least total time; on meshes
+ * with the 7-point structure it then times the flat Gauss-Seidel kernel
+ * (hhg_set_flat_gs) and keeps it for the level's sweeps if it is faster
+ * still (the residual and transfer kernels keep the chosen tiles).
  * chosen (may be NULL, one int per level, coarsest first) receives the index
- * of the chosen candidate (-1 for the coarsest level, which is not smoothed).
+ * c of the chosen tile shape, or c + 4 when the level's Gauss-Seidel sweeps
+ * use the flat kernel (-1 for the coarsest level, which is not smoothed).
  * The tiles not kept are freed (after synchronising the device), except while
  * a batch refers to the mesh. */
 int hhg_autotune(hhg_mesh* mesh, int reps, int* chosen, void* stream);
@@ -430,6 +434,18 @@ int hhg_walk_counts(hhg_mesh* mesh, int64_t* counts);
  * with hhg_set_problem).  tries = 0 makes every wait run out at once, which
  * exercises that path without any fault. */
 int hhg_set_streaming(hhg_mesh* mesh, int enable);
+/* hhg_set_flat_gs: enable or disable (default) the flat Gauss-Seidel kernel on
+ * every smoothed level of a mesh with the 7-point structure (ignored on
+ * meshes without it; general connectivity: HHG_ERR_STATE): one thread per
+ * 16-byte vector of same-colour nodes, indexed through a per-level item
+ * table (4 bytes per item, FP64 and on precision-32 meshes FP32 tables,
+ * allocated on enable and freed on disable), with no tiles and no CTA
+ * barrier, which suits the small coarse levels; hhg_autotune picks it per
+ * level.  Same iterate bit for bit as the tile kernel.  The streaming kernel
+ * (hhg_set_streaming) takes precedence where both are enabled; the
+ * persistent batch executor keeps the tile kernel.  Drops the captured
+ * recovery-cycle graph. */
+int hhg_set_flat_gs(hhg_mesh* mesh, int enable);
 int hhg_set_wait_limit(hhg_mesh* mesh, int tries);
 
 /* Copy the message of the calling thread's last failure into buf (always

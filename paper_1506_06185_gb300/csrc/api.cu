@@ -270,6 +270,13 @@ LevelArgs largs(const hhg_mesh* m, int l) {
   a.tiles_stream32 = t.tiles_stream32;
   a.n_tiles_stream32 = t.n_tiles_stream32;
   a.stream_band32 = H.stream_band32;
+  a.gs_items64 = t.gs_items64;
+  a.gs_items32 = t.gs_items32;
+  for (int c = 0; c < 5; ++c) {
+    a.gs_off64[c] = t.gs_off64[c];
+    a.gs_off32[c] = t.gs_off32[c];
+  }
+  a.gs_flat = t.gs_flat;
   return a;
 }
 
@@ -1127,6 +1134,41 @@ int update_coefficients(hhg_mesh* m, const double* coeff) {
 const int TUNE_CAND[][2] = {{256, 4}, {512, 8}, {1024, 8}, {2048, 16}};
 constexpr int N_TUNE_CAND = 4;
 
+// Flat Gauss-Seidel on level l (7-point meshes of the cube family): build and
+// upload its item tables (FP64, and FP32 on precision-32 meshes) when
+// switching it on, free them when switching it off.
+int set_flat(hhg_mesh* m, int l, bool on) {
+  DevLevelTables& tb = m->tab[l];
+  const HostLevel& H = m->host.lv[l];
+  if (!on) {
+    std::vector<void*> unused;
+    if (tb.gs_items64) unused.push_back(tb.gs_items64);
+    if (tb.gs_items32) unused.push_back(tb.gs_items32);
+    release(m, unused);
+    tb.gs_items64 = tb.gs_items32 = nullptr;
+    for (int c = 0; c < 5; ++c) tb.gs_off64[c] = tb.gs_off32[c] = 0;
+    tb.gs_flat = 0;
+    return HHG_OK;
+  }
+  if (H.N > 1024 || H.N < 4) return fail(HHG_ERR_ARG, "flat Gauss-Seidel needs 4 .. 1024 intervals per macro edge");
+  for (int vw : {2, 4}) {
+    if (vw == 4 && m->precision != 32) continue;
+    uint32_t*& dst = vw == 2 ? tb.gs_items64 : tb.gs_items32;
+    if (dst) continue;
+    std::vector<uint32_t> items;
+    int off[5];
+    build_gs_items(H.N, vw, items, off);
+    int most = 0;
+    for (int c = 0; c < 4; ++c) most = std::max(most, off[c + 1] - off[c]);
+    if ((int64_t)most * m->host.n_macro > (int64_t)INT32_MAX - 1024)
+      return fail(HHG_ERR_ARG, "mesh too large for the flat Gauss-Seidel kernel");
+    HHG_TRY(upload(m, &dst, items));
+    for (int c = 0; c < 5; ++c) (vw == 2 ? tb.gs_off64 : tb.gs_off32)[c] = off[c];
+  }
+  tb.gs_flat = 1;
+  return HHG_OK;
+}
+
 // Device time of `reps` Gauss-Seidel steps of the global problem on level l
 // in precision T (after one warm-up step).
 template <class T>
@@ -1143,6 +1185,7 @@ int time_smooth(hhg_mesh* m, Prec<T>& P, int l, int reps, cudaStream_t s, cudaEv
 int tune_level(hhg_mesh* m, int l, int reps, cudaStream_t s, int* best_out) {
   const HostLevel& H = m->host.lv[l];
   DevLevelTables& tb = m->tab[l];
+  HHG_TRY(set_flat(m, l, false));   // the tile candidates are timed with the tile kernel
   Tile* const before = tb.tiles_int;
   double best_ms = 1e30;
   int best = -1;
@@ -1172,6 +1215,16 @@ int tune_level(hhg_mesh* m, int l, int reps, cudaStream_t s, int* best_out) {
   tb.tiles_int = dev[best];
   tb.n_tiles_int = ndev[best];
   *best_out = best;
+  // the flat Gauss-Seidel kernel against the best tile shape (7-point
+  // levels); the level's other kernels keep the tiles either way
+  if (m->host.seven_point) {
+    HHG_TRY(set_flat(m, l, true));
+    float ms = 0.f, ms32 = 0.f;
+    HHG_TRY(time_smooth<double>(m, m->d64, l, reps, s, a, b, &ms));
+    if (m->precision == 32) HHG_TRY(time_smooth<float>(m, m->d32, l, reps, s, a, b, &ms32));
+    if (ms + ms32 < best_ms) *best_out = best + N_TUNE_CAND;
+    else HHG_TRY(set_flat(m, l, false));
+  }
   // the other candidates' tiles and the level's previous tiles are unused now
   std::vector<void*> unused;
   for (int c = 0; c < N_TUNE_CAND; ++c)
@@ -1942,6 +1995,15 @@ int hhg_set_streaming(hhg_mesh* m, int enable) {
   m->stream_gs = enable ? 1 : 0;
   for (DevProblem* p : {&m->global, &m->faulty, &m->healthy, &m->dn}) p->stream_gs = m->stream_gs;
   drop_local_graph(m);
+  return HHG_OK;
+}
+
+int hhg_set_flat_gs(hhg_mesh* m, int enable) {
+  if (!m) return fail(HHG_ERR_ARG, "null mesh");
+  HHG_TRY(check_device(m));
+  HHG_TRY(refuse_general(m, "the flat Gauss-Seidel kernel"));
+  drop_local_graph(m);
+  for (int l = 1; l < (int)m->host.lv.size(); ++l) HHG_TRY(set_flat(m, l, enable != 0));
   return HHG_OK;
 }
 

@@ -261,6 +261,12 @@ void build_pair_tiles(int N, std::vector<Tile>& out, int target, int slabs);
 // Streaming units of refinement N: bands of `band` interior rows, each split
 // into runs of at most `slices` slices, largest first.
 void build_stream_tiles(int N, int band, int slices, std::vector<StreamTile>& out);
+// Work items of the flat Gauss-Seidel kernel on refinement N (N <= 1024) for
+// vectors of vw same-colour slots: for each colour c, the groups g of every
+// interior row (j, k) of one macro holding colour-c nodes, packed as
+// (j << 20) | (k << 10) | g, slice by slice, row by row, group by group;
+// colour c's items are items[off[c] .. off[c + 1]).
+void build_gs_items(int N, int vw, std::vector<uint32_t>& items, int off[5]);
 // Recompute every level's stencils for new per-macro coefficients.
 void set_coefficients(HostMesh& m, const double* coeff);
 // A macro mesh of general connectivity: nv vertex positions (3 doubles each),
@@ -332,6 +338,13 @@ struct DevLevelTables {
   int n_tiles_stream = 0;
   StreamTile* tiles_stream32 = nullptr;
   int n_tiles_stream32 = 0;
+  // flat Gauss-Seidel (7-point levels, on request): build_gs_items for FP64
+  // (2 slots per item) and FP32 (4), and whether the level uses it
+  uint32_t* gs_items64 = nullptr;
+  int gs_off64[5] = {0, 0, 0, 0, 0};
+  uint32_t* gs_items32 = nullptr;
+  int gs_off32[5] = {0, 0, 0, 0, 0};
+  int gs_flat = 0;
 };
 
 struct DevProblemLevel {

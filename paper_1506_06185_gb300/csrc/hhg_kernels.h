@@ -27,6 +27,11 @@ struct LevelArgs {
   const StreamTile* tiles_stream32; // the same for the FP32 cycles
   int n_tiles_stream32;
   int stream_band32;
+  const uint32_t* gs_items64;       // flat Gauss-Seidel items (build_gs_items), FP64 and FP32,
+  const uint32_t* gs_items32;       // with their per-colour offsets; used when gs_flat is set
+  int gs_off64[5];
+  int gs_off32[5];
+  int gs_flat;
 };
 
 struct ProbArgs {

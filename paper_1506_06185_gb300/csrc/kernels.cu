@@ -698,6 +698,60 @@ __global__ void __launch_bounds__(CTA, 5) k_gs(int N, const int* __restrict__ rs
   finish_units(sched, n_if_units + n_tiles * n_act);
 }
 
+// Flat Gauss-Seidel, one colour, 7-point structure: one work item (one
+// 16-byte vector of same-colour slots of one row) per thread, no tiles, no
+// CTA barrier.  items[it] = (j << 20) | (k << 10) | g lists the colour's
+// items of one macro interior, slice by slice and row by row, so consecutive
+// threads take consecutive vectors of a row; a thread's global index runs
+// over the active macros (item it of macro act[a]).  CTAs of interface nodes
+// (one node per thread, as in k_gs) are spread among the volume CTAs
+// (spread_position over CTAs).  fv / Wv: the volume's load and weights (f and
+// W, or with SCALED both divided by the centre weight).  On a coarse level the tile kernel's launch
+// waits for a few CTAs each walking a whole tile; here every thread has one
+// item and the launch lasts about one item's latency.  Same arithmetic per
+// item as gs_tile7, so the iterate equals the tile kernel's bit for bit.
+template <class T, bool SCALED>
+__global__ void __launch_bounds__(CTA) k_gs_flat(int N, const int* __restrict__ rs, int64_t block, T* __restrict__ u,
+                                                 T* __restrict__ uI, const T* __restrict__ fI,
+                                                 const T* __restrict__ W, const T* __restrict__ Winv,
+                                                 const T* __restrict__ fv, const T* __restrict__ Wv,
+                                                 const uint32_t* __restrict__ items, int n_items,
+                                                 const int* __restrict__ act, int n_act, int colour,
+                                                 const int* __restrict__ cptr, const Copy* __restrict__ cps,
+                                                 const uint32_t* __restrict__ cpo, const int* __restrict__ list,
+                                                 int n_list, IfTab<T> tab, int n_if_ctas, int n_vol_ctas) {
+  int vb = 0;
+  const int ib = spread_position((int)blockIdx.x, n_if_ctas, n_vol_ctas, vb);
+  if (ib >= 0) {
+    const int q = ib * CTA + tid256();
+    if (q < n_list) {
+      const int node = list[q];
+      const int c0 = cptr[node], c1 = cptr[node + 1];
+      T val;
+      if (tab.nb) {
+        val = (fI[node] - if_offdiag<T, 6>(tab, u, q)) * tab.dinv[q];
+      } else {
+        T off = T(0), diag = T(0);
+        if_stencil<T, true>(N, rs, block, u, W, cps, c0, c1, off, diag);
+        val = (fI[node] - off) / diag;
+      }
+      uI[node] = val;
+      write_copies(N, rs, block, u, cps, cpo, c0, c1, val);
+    }
+    return;
+  }
+  const int v = vb * CTA + tid256();
+  if (v >= n_items * n_act) return;
+  const int a = v / n_items, it = v - a * n_items;
+  const int macro = act[a];
+  const uint32_t d = items[it];
+  const int j = (int)(d >> 20), k = (int)((d >> 10) & 1023u), g = (int)(d & 1023u);
+  const T* w = Wv + (size_t)macro * 16 * NDIR;
+  const T wr[11] = {T(0), w[1], w[2], w[3], T(0), T(0), T(0), T(0), w[8], w[9], w[10]};
+  gs_group7<T, SCALED>(slice_consts(rs, N, k), N, j, g, colour, u + (size_t)macro * block,
+                       fv + (size_t)macro * block, wr, SCALED ? T(1) : Winv[macro]);
+}
+
 // ---------------------------------------------------------------------------
 // Streaming Gauss-Seidel, one colour, 7-point structure (levels with at least
 // STREAM_MIN_N intervals).  In the colour-split layout the rows of a slice
@@ -2706,6 +2760,23 @@ cudaError_t gs_colour(const LevelArgs& L, const ProbArgs& p, T* u, T* uI, const 
                              : launch_gs_stream<T, false>(L, p, u, uI, fI, W, Winv, f, W, colour, n, s);
     if (ev_end) cudaEventRecord(ev_end, s);
     return e;
+  }
+  const uint32_t* items = sizeof(T) == 8 ? L.gs_items64 : L.gs_items32;
+  if (seven_point && L.gs_flat && items) {
+    const int* off = sizeof(T) == 8 ? L.gs_off64 : L.gs_off32;
+    const int n_items = off[colour + 1] - off[colour];
+    const int n_if_ctas = (int)lin_grid(n, CTA);
+    const int n_vol_ctas = p.n_act > 0 ? (int)lin_grid((int64_t)n_items * p.n_act, CTA) : 0;
+    if (n_if_ctas + n_vol_ctas == 0) return cudaSuccess;
+    auto kern = fs ? k_gs_flat<T, true> : k_gs_flat<T, false>;
+    if (ev_begin) cudaEventRecord(ev_begin, s);
+    ++g_kernel_launches;
+    kern<<<n_if_ctas + n_vol_ctas, cta_shape(), 0, s>>>(
+        L.N, L.rs, L.block, u, uI, fI, W, Winv, fs ? fs : f, Wsc ? Wsc : W, items + off[colour], n_items, p.act,
+        p.n_act, colour, L.cptr, L.cps, L.cp_off, p.free_if + p.col_off[colour], n, if_tab<T>(p, p.col_off[colour]),
+        n_if_ctas, n_vol_ctas);
+    if (ev_end) cudaEventRecord(ev_end, s);
+    return cudaGetLastError();
   }
   const Units g = units(n, L.n_tiles_int, p.n_act);
   if (g.total == 0) return cudaSuccess;

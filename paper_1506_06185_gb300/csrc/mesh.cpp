@@ -320,6 +320,24 @@ void build_pair_tiles(int N, std::vector<Tile>& out, int target, int slabs) {
   std::stable_sort(out.begin(), out.end(), [&](const Tile& a, const Tile& b) { return work(a) > work(b); });
 }
 
+void build_gs_items(int N, int vw, std::vector<uint32_t>& items, int off[5]) {
+  items.clear();
+  for (int c = 0; c < 4; ++c) {
+    off[c] = (int)items.size();
+    for (int k = 1; k <= N - 3; ++k)
+      for (int j = 1; j <= N - 2 - k; ++j) {
+        // colour-c nodes of the row: i = 4 m + ic for slots m = mlo .. mlo + n - 1
+        const int ic = (c - 2 * j - 3 * k) & 3;
+        const int L = N - 1 - j - k;
+        const int mlo = ic == 0;
+        const int n = L >= ic ? ((L - ic) >> 2) - mlo + 1 : 0;
+        const int groups = n > 0 ? (mlo + n - 1) / vw + 1 : 0;
+        for (int g = 0; g < groups; ++g) items.push_back(((uint32_t)j << 20) | ((uint32_t)k << 10) | (uint32_t)g);
+      }
+  }
+  off[4] = (int)items.size();
+}
+
 void build_stream_tiles(int N, int band, int slices, std::vector<StreamTile>& out) {
   out.clear();
   // interior rows j = 1..N-2-k of slice k = 1..N-3; band [j0, j1] has

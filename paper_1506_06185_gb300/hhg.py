@@ -30,7 +30,7 @@ EXPORTS = ["hhg_mesh_create", "hhg_mesh_destroy", "hhg_mesh_info", "hhg_mesh_byt
            "hhg_autotune", "hhg_batch_create", "hhg_batch_launch", "hhg_batch_destroy",
            "hhg_batch_launch_persistent", "hhg_batch_info", "hhg_batch_set_priority", "hhg_recover_dn",
            "hhg_mesh_create_general", "hhg_set_launch_limit", "hhg_walk_counts", "hhg_set_streaming",
-           "hhg_set_wait_limit", "hhg_measure_fp64_peak", "hhg_profile_breakdown"]
+           "hhg_set_wait_limit", "hhg_measure_fp64_peak", "hhg_profile_breakdown", "hhg_set_flat_gs"]
 
 
 class hhg_mesh_desc(C.Structure):
@@ -95,6 +95,7 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
         "hhg_walk_counts": ([P, C.POINTER(C.c_int64)], C.c_int),
         "hhg_set_streaming": ([P, C.c_int], C.c_int),
         "hhg_set_wait_limit": ([P, C.c_int], C.c_int),
+        "hhg_set_flat_gs": ([P, C.c_int], C.c_int),
         "hhg_measure_fp64_peak": ([C.POINTER(C.c_double)], C.c_int),
         "hhg_profile_breakdown": ([P, C.POINTER(C.c_double), C.c_int], C.c_int),
         "hhg_vcycle_noalloc": ([P, C.c_int, C.c_int, P], C.c_int),
@@ -421,6 +422,10 @@ def hhg_set_launch_limit(h, max_ctas):
 
 def hhg_set_streaming(h, enable=True):
     return _check(lib().hhg_set_streaming(h, 1 if enable else 0))
+
+
+def hhg_set_flat_gs(h, enable=True):
+    _check(lib().hhg_set_flat_gs(h, 1 if enable else 0))
 
 
 def hhg_set_wait_limit(h, tries):

@@ -233,6 +233,44 @@ static void check_spread(int n_if, int n_vol) {
   }
 }
 
+// The flat Gauss-Seidel items (build_gs_items): for each colour, the slots of
+// every item hold at least one colour-c interior node, and every colour-c
+// interior node of every slice lies in exactly one item's slots.
+static void check_gs_items(int N, int vw) {
+  std::vector<uint32_t> items;
+  int off[5];
+  build_gs_items(N, vw, items, off);
+  CHECK(off[0] == 0 && off[4] == (int)items.size(), "gs items: offsets %d .. %d of %zu", off[0], off[4], items.size());
+  std::vector<int> seen;
+  auto at = [&](int i, int j, int k) { return ((size_t)k * (N + 1) + j) * (N + 1) + i; };
+  for (int c = 0; c < 4; ++c) {
+    CHECK(off[c] <= off[c + 1], "gs items: colour %d offsets decrease", c);
+    seen.assign((size_t)(N + 1) * (N + 1) * (N + 1), 0);
+    for (int q = off[c]; q < off[c + 1]; ++q) {
+      const uint32_t d = items[q];
+      const int j = (int)(d >> 20), k = (int)((d >> 10) & 1023u), g = (int)(d & 1023u);
+      CHECK(k >= 1 && k <= N - 3 && j >= 1 && j <= N - 2 - k, "gs items vw %d: row (%d, %d) not interior", vw, j, k);
+      if (!(k >= 1 && k <= N - 3 && j >= 1 && j <= N - 2 - k)) continue;
+      const int L = N - 1 - j - k, ic = (c - 2 * j - 3 * k) & 3;
+      int here = 0;
+      for (int m = g * vw; m < g * vw + vw; ++m) {
+        const int i = 4 * m + ic;
+        if (i >= 1 && i <= L) {
+          ++seen[at(i, j, k)];
+          ++here;
+        }
+      }
+      CHECK(here > 0, "gs items vw %d: item (%d, %d, %d) of colour %d holds no node", vw, j, k, g, c);
+    }
+    for (int k = 1; k <= N - 3; ++k)
+      for (int j = 1; j <= N - 2 - k; ++j)
+        for (int i = 1; i <= N - 1 - j - k; ++i)
+          if (((i + 2 * j + 3 * k) & 3) == c)
+            CHECK(seen[at(i, j, k)] == 1, "gs items vw %d: node (%d, %d, %d) covered %d times", vw, i, j, k,
+                  seen[at(i, j, k)]);
+  }
+}
+
 int main(int argc, char** argv) {
   if (argc < 2) return 2;
   const int n_max = std::atoi(argv[1]);
@@ -259,6 +297,8 @@ int main(int argc, char** argv) {
     check_stream_tiles(N, N >= 512 ? STREAM_BAND / 2 : STREAM_BAND, 2);
     check_stream_tiles(N, N >= 512 ? STREAM_BAND32 / 2 : STREAM_BAND32, 4);
   }
+  for (int N : {4, 5, 8, 13, 16, 32, 64, 128})
+    for (int vw : {2, 4}) check_gs_items(N, vw);
   for (int n_if = 0; n_if <= 40; ++n_if)
     for (int n_vol = 0; n_vol <= 130; ++n_vol) check_spread(n_if, n_vol);
   // the finest launches of the bench's mesh (refinement 8: about 2300 chunks

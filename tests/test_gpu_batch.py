@@ -154,7 +154,7 @@ def test_autotune_keeps_parity(hhg):
     f = I.random_load(sub, R, seed=1)
     M = hhg.Mesh(sub, R, precision=32)
     chosen = hhg.hhg_autotune(M.h, R - 1, reps=2)
-    assert chosen[0] == -1 and all(0 <= c < 4 for c in chosen[1:])
+    assert chosen[0] == -1 and all(0 <= c < 8 for c in chosen[1:])
     M.set_problem(f, I.initial_guess(sub, R))
     m = O.Mesh(sub, R)
     uo, fo = O.pad(I.initial_guess(sub, R)), O.pad(f)

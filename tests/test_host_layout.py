@@ -8,7 +8,9 @@ kernels' per-tile table sizes, largest first.  Refinements 2..130, 256, 512.
 The streaming Gauss-Seidel units (refinements 64..512, FP64 and FP32 bands):
 staged ranges fit the shared-memory slots, every neighbour read of every
 updated node lands on the right lattice node inside its staged range, and
-every interior node of every colour is updated exactly once.  The walk order
+every interior node of every colour is updated exactly once.  The flat
+Gauss-Seidel item tables (FP64 and FP32 vectors) cover every interior node of
+every colour exactly once, each item holding at least one node.  The walk order
 of the large stencil launches (interface chunks spread among the volume
 units) visits every chunk and unit exactly once, each kind in its own order,
 with at most n_vol / n_if volume units between two chunks."""
