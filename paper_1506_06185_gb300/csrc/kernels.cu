@@ -1190,6 +1190,76 @@ _Pragma("unroll")
   }
 }
 
+// Flat residual, 7-point structure: the items of all four colours of the flat
+// Gauss-Seidel tables (colour c's at off[c] .. off[c + 1]) for every active
+// macro, and the interface entries, in chunks of 256 walked with a grid
+// stride (launched with one chunk per CTA), interface chunks spread among the
+// volume chunks; no tiles and no CTA barrier before the final norm
+// reduction.  Same arithmetic per item as k_res (res_group7), so r is the
+// same bit for bit; the norm's partial sums would follow the grid.  n_items:
+// items per macro taken (off[4], or off[3] for a norm-only launch that skips
+// colour 3).
+template <class T, bool WRITE, bool NORM>
+__global__ void __launch_bounds__(CTA) k_res_flat(int N, const int* __restrict__ rs, int64_t block,
+                                                  const T* __restrict__ u, const T* __restrict__ uI,
+                                                  const T* __restrict__ f, const T* __restrict__ fI, T* __restrict__ r,
+                                                  const T* __restrict__ W, const uint32_t* __restrict__ items,
+                                                  int4 off, int n_items, const int* __restrict__ act, int n_act,
+                                                  const int* __restrict__ cptr, const Copy* __restrict__ cps,
+                                                  const uint32_t* __restrict__ cpo, const int* __restrict__ list,
+                                                  int n_list, IfTab<T> tab, const int64_t* __restrict__ zero_off,
+                                                  int n_zero, int n_if_chunks, int n_vol_chunks,
+                                                  double* __restrict__ partial, int skip, int skip_lo, int skip_hi) {
+  __shared__ double sh[32];
+  double ss = 0.0;
+  const int n_vol = n_items * n_act;
+  for (int chunk = blockIdx.x; chunk < n_if_chunks + n_vol_chunks; chunk += gridDim.x) {
+    int vc = 0;
+    const int ic = spread_position(chunk, n_if_chunks, n_vol_chunks, vc);
+    if (ic >= 0) {
+      const int q = ic * CTA + tid256();
+      if (q < n_list) {
+        const int node = list[q];
+        const int c0 = cptr[node], c1 = cptr[node + 1];
+        T res;
+        if (q >= skip_lo && q < skip_hi) {
+          res = T(0);                              // the colour smoothed last
+        } else if (tab.nb) {
+          res = fI[node] - tab.diag[q] * uI[node] - if_offdiag<T, 6>(tab, u, q);
+        } else {
+          T off_ = T(0), diag = T(0);
+          if_stencil<T, true>(N, rs, block, u, W, cps, c0, c1, off_, diag);
+          res = fI[node] - diag * uI[node] - off_;
+        }
+        if (WRITE) write_copies(N, rs, block, r, cps, cpo, c0, c1, res);
+        if (NORM) ss += (double)res * (double)res;
+      } else if (WRITE && q < n_list + n_zero) {
+        r[zero_off[q - n_list]] = T(0);
+      }
+      continue;
+    }
+    const int v = vc * CTA + tid256();
+    if (v >= n_vol) continue;
+    const int a = v / n_items, it = v - a * n_items;
+    const int c = it < off.y ? 0 : it < off.z ? 1 : it < off.w ? 2 : 3;
+    if (!WRITE && c == skip) continue;             // norm only: the skipped colour adds nothing
+    const int macro = act[a];
+    const uint32_t d = items[it];
+    const int j = (int)(d >> 20), k = (int)((d >> 10) & 1023u), g = (int)(d & 1023u);
+    const T* w = W + (size_t)macro * 16 * NDIR;
+    const T wr[11] = {w[0], w[1], w[2], w[3], T(0), T(0), T(0), T(0), w[8], w[9], w[10]};
+    const size_t mb = (size_t)macro * block;
+    if (c == skip)
+      res_group7<T, WRITE, NORM, true>(slice_consts(rs, N, k), N, j, g, c, u + mb, f + mb, r + mb, wr, ss);
+    else
+      res_group7<T, WRITE, NORM>(slice_consts(rs, N, k), N, j, g, c, u + mb, f + mb, r + mb, wr, ss);
+  }
+  if (NORM) {
+    const double s = block_sum(ss, sh);
+    if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.x] = s;
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Restriction R = P^T onto the coarse level (§2.1); zero the coarse correction
 // ---------------------------------------------------------------------------
@@ -2826,6 +2896,23 @@ cudaError_t residual(const LevelArgs& L, const ProbArgs& p, const T* u, const T*
   const Units g = units(n + n_zero, L.n_tiles_int, p.n_act);
   if (n_part) *n_part = 0;
   if (g.total == 0) return cudaSuccess;
+  const uint32_t* items = sizeof(T) == 8 ? L.gs_items64 : L.gs_items32;
+  if (seven_point && L.gs_flat && items && write_r && !norm) {
+    // the residual before a restriction, on levels whose Gauss-Seidel runs
+    // flat: one chunk per CTA (norm launches keep the tile kernel, whose
+    // partial sums per CTA measured faster)
+    const int* off = sizeof(T) == 8 ? L.gs_off64 : L.gs_off32;
+    const int sk = skip >= 0 && skip < 4 ? skip : -1;
+    const int n_items = off[4];
+    const int n_if_chunks = (int)lin_grid(n + n_zero, CTA);
+    const int n_vol_chunks = p.n_act > 0 ? (int)lin_grid((int64_t)n_items * p.n_act, CTA) : 0;
+    ++g_kernel_launches;
+    k_res_flat<T, true, false><<<n_if_chunks + n_vol_chunks, cta_shape(), 0, s>>>(
+        L.N, L.rs, L.block, u, uI, f, fI, r, W, items, make_int4(off[0], off[1], off[2], off[3]), n_items, p.act,
+        p.n_act, L.cptr, L.cps, L.cp_off, p.free_if, n, if_tab<T>(p, 0), p.zero_off, n_zero, n_if_chunks,
+        n_vol_chunks, nullptr, sk, sk >= 0 ? p.col_off[sk] : 0, sk >= 0 ? p.col_off[sk + 1] : 0);
+    return cudaGetLastError();
+  }
   void (*kern)(int, const int*, int64_t, const T*, const T*, const T*, const T*, T*, const T*, const Tile*, int, const int*,
                int, const int*, const Copy*, const uint32_t*, const int*, int, IfTab<T>, const int64_t*, int, int,
                double*, int*, int, int, int);

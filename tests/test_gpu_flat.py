@@ -1,9 +1,10 @@
-"""The flat Gauss-Seidel kernel (hhg_set_flat_gs) against the oracle and the tile kernel.
+"""The flat Gauss-Seidel and residual kernels (hhg_set_flat_gs) against the oracle and the tile kernels.
 
-The flat kernel gives every thread one 16-byte vector of same-colour nodes,
-looked up in a per-level item table, instead of walking row-pair tiles; its
-per-item arithmetic is the tile kernel's, and a colour's nodes read only
-other colours, so the iterate must equal the tile kernel's bit for bit.  Each
+The flat kernels give every thread one 16-byte vector of same-colour nodes,
+looked up in a per-level item table, instead of walking row-pair tiles; their
+per-item arithmetic is the tile kernels', and a colour's nodes read only
+other colours, so the iterate must equal the tile kernels' bit for bit (the
+residual norms only up to the order of their partial sums).  Each
 test runs a mesh with the flat kernel on every smoothed level next to a twin
 on the tile kernel and compares:
   * the iterates with the oracle node by node (parity.assert_close) and the
@@ -66,7 +67,8 @@ def test_flat_vcycles(hhg, sub, R):
         assert_close(uf, O.interior(uo), what=f"cycle {k}")
         assert np.array_equal(uf, ut), f"cycle {k}: flat and tile kernels differ"
         ro = O.resnorm(m, uo, fo)
-        assert abs(rf - ro) <= ATOL_HIST * r0 and rf == rt, k
+        # the norms' partial sums follow each kernel's grid: equal up to rounding
+        assert abs(rf - ro) <= ATOL_HIST * r0 and abs(rf - rt) <= 1e-14 * r0, k
     F.close()
     T.close()
 
