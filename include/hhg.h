@@ -441,9 +441,11 @@ int hhg_set_streaming(hhg_mesh* mesh, int enable);
  * table (4 bytes per item, FP64 and on precision-32 meshes FP32 tables,
  * allocated on enable and freed on disable), with no tiles and no CTA
  * barrier, which suits the small coarse levels; hhg_autotune picks it per
- * level.  On those levels the residual before each restriction runs in the
- * same flat form (the stopping test's norm keeps the tile kernel).  Same
- * iterate bit for bit as the tile kernels.  The streaming kernel
+ * level.  On those levels the residual before each restriction, the
+ * restriction onto the level (one thread per slot of four coarse nodes) and
+ * the prolongation onto it (one thread per 16-byte vector of same-colour fine
+ * nodes) run in the same flat form; the stopping test's norm keeps the tile
+ * kernel.  Same iterate bit for bit as the tile kernels.  The streaming kernel
  * (hhg_set_streaming) takes precedence where both are enabled; the
  * persistent batch executor keeps the tile kernel.  Drops the captured
  * recovery-cycle graph. */

@@ -276,6 +276,8 @@ LevelArgs largs(const hhg_mesh* m, int l) {
     a.gs_off64[c] = t.gs_off64[c];
     a.gs_off32[c] = t.gs_off32[c];
   }
+  a.slot_items = t.slot_items;
+  a.n_slots = t.n_slots;
   a.gs_flat = t.gs_flat;
   return a;
 }
@@ -1142,10 +1144,12 @@ int set_flat(hhg_mesh* m, int l, bool on) {
   const HostLevel& H = m->host.lv[l];
   if (!on) {
     std::vector<void*> unused;
-    if (tb.gs_items64) unused.push_back(tb.gs_items64);
-    if (tb.gs_items32) unused.push_back(tb.gs_items32);
+    for (void* q : {(void*)tb.gs_items64, (void*)tb.gs_items32, (void*)tb.slot_items})
+      if (q) unused.push_back(q);
     release(m, unused);
     tb.gs_items64 = tb.gs_items32 = nullptr;
+    tb.slot_items = nullptr;
+    tb.n_slots = 0;
     for (int c = 0; c < 5; ++c) tb.gs_off64[c] = tb.gs_off32[c] = 0;
     tb.gs_flat = 0;
     return HHG_OK;
@@ -1164,6 +1168,12 @@ int set_flat(hhg_mesh* m, int l, bool on) {
       return fail(HHG_ERR_ARG, "mesh too large for the flat Gauss-Seidel kernel");
     HHG_TRY(upload(m, &dst, items));
     for (int c = 0; c < 5; ++c) (vw == 2 ? tb.gs_off64 : tb.gs_off32)[c] = off[c];
+  }
+  if (!tb.slot_items) {
+    std::vector<uint32_t> slots;
+    build_slot_items(H.N, slots);
+    HHG_TRY(upload(m, &tb.slot_items, slots));
+    tb.n_slots = (int)slots.size();
   }
   tb.gs_flat = 1;
   return HHG_OK;

@@ -267,6 +267,11 @@ void build_stream_tiles(int N, int band, int slices, std::vector<StreamTile>& ou
 // (j << 20) | (k << 10) | g, slice by slice, row by row, group by group;
 // colour c's items are items[off[c] .. off[c + 1]).
 void build_gs_items(int N, int vw, std::vector<uint32_t>& items, int off[5]);
+// Slots of four consecutive nodes (one per colour array) of every interior
+// row (j, k) of one macro, m = 0 .. (N - 1 - j - k) >> 2, packed as
+// (j << 20) | (k << 10) | m, slice by slice, row by row: the flat
+// restriction's items on the coarse level.
+void build_slot_items(int N, std::vector<uint32_t>& items);
 // Recompute every level's stencils for new per-macro coefficients.
 void set_coefficients(HostMesh& m, const double* coeff);
 // A macro mesh of general connectivity: nv vertex positions (3 doubles each),
@@ -344,6 +349,8 @@ struct DevLevelTables {
   int gs_off64[5] = {0, 0, 0, 0, 0};
   uint32_t* gs_items32 = nullptr;
   int gs_off32[5] = {0, 0, 0, 0, 0};
+  uint32_t* slot_items = nullptr;    // build_slot_items
+  int n_slots = 0;
   int gs_flat = 0;
 };
 

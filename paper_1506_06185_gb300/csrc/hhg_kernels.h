@@ -31,6 +31,8 @@ struct LevelArgs {
   const uint32_t* gs_items32;       // with their per-colour offsets; used when gs_flat is set
   int gs_off64[5];
   int gs_off32[5];
+  const uint32_t* slot_items;       // the flat restriction's items on this (coarse) level
+  int n_slots;
   int gs_flat;
 };
 

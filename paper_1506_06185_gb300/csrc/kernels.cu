@@ -710,8 +710,15 @@ __global__ void __launch_bounds__(CTA, 5) k_gs(int N, const int* __restrict__ rs
 // waits for a few CTAs each walking a whole tile; here every thread has one
 // item and the launch lasts about one item's latency.  Same arithmetic per
 // item as gs_tile7, so the iterate equals the tile kernel's bit for bit.
+// Resident CTAs per SM: the FP64 form is held to 8 (32 registers; measured
+// 1.2% faster at refinement 8); the FP32 form is left to the compiler (0: no
+// bound; 3% slower held to 8, 6% slower held to 6).
+template <class T>
+struct FlatMinCtas {
+  static constexpr int value = sizeof(T) == 8 ? 8 : 0;
+};
 template <class T, bool SCALED>
-__global__ void __launch_bounds__(CTA) k_gs_flat(int N, const int* __restrict__ rs, int64_t block, T* __restrict__ u,
+__global__ void __launch_bounds__(CTA, FlatMinCtas<T>::value) k_gs_flat(int N, const int* __restrict__ rs, int64_t block, T* __restrict__ u,
                                                  T* __restrict__ uI, const T* __restrict__ fI,
                                                  const T* __restrict__ W, const T* __restrict__ Winv,
                                                  const T* __restrict__ fv, const T* __restrict__ Wv,
@@ -1574,6 +1581,93 @@ __global__ void __launch_bounds__(CTA) k_prolong(int Nf, const int* __restrict__
                           s_pre_tot);
   }
   finish_units(sched, n_if_units + n_tiles * n_act);
+}
+
+// Flat transfers (levels on the flat kernels): one thread per item, no tiles
+// and no CTA barrier, CTAs of interface nodes spread among the volume CTAs.
+// The restriction takes the coarse level's slot items (four coarse nodes of
+// one row per thread, restrict_slot); the prolongation takes the fine level's
+// Gauss-Seidel items of the colours it updates (one 16-byte vector of
+// same-colour fine nodes per thread, prolong_group).  Same arithmetic per
+// node as k_restrict / k_prolong, so the same values bit for bit.
+template <class T>
+__global__ void __launch_bounds__(CTA) k_restrict_flat(int Nc, const int* __restrict__ rsc, int64_t bc,
+                                                       T* __restrict__ fc, T* __restrict__ fIc, T* __restrict__ uc,
+                                                       T* __restrict__ uIc, int Nf, const int* __restrict__ rsf,
+                                                       int64_t bf, const T* __restrict__ rf,
+                                                       const uint32_t* __restrict__ slots, int n_slots,
+                                                       const int* __restrict__ act, int n_act,
+                                                       const int* __restrict__ cptr, const Copy* __restrict__ cps,
+                                                       const uint32_t* __restrict__ cpo, const int* __restrict__ list,
+                                                       int n_list, const int64_t* __restrict__ gather,
+                                                       const int64_t* __restrict__ zero_off, int n_zero,
+                                                       int n_if_ctas, int n_vol_ctas) {
+  int vb = 0;
+  const int ib = spread_position((int)blockIdx.x, n_if_ctas, n_vol_ctas, vb);
+  if (ib >= 0) {
+    const int q = ib * CTA + tid256();
+    if (q < n_list) {
+      const int node = list[q];
+      const int64_t* g = gather + (size_t)q * NDIR;
+      T acc = T(0);
+      for (int e = 1; e < NDIR; ++e) {
+        const int64_t o = g[e];
+        if (o >= 0) acc += rf[o];
+      }
+      fIc[node] = rf[g[0]] + T(0.5) * acc;
+      uIc[node] = T(0);
+      write_copies(Nc, rsc, bc, uc, cps, cpo, cptr[node], cptr[node + 1], T(0));
+    } else if (q < n_list + n_zero) {
+      uc[zero_off[q - n_list]] = T(0);
+    }
+    return;
+  }
+  const int v = vb * CTA + tid256();
+  if (v >= n_slots * n_act) return;
+  const int a = v / n_slots, it = v - a * n_slots;
+  const int macro = act[a];
+  const uint32_t d = slots[it];
+  restrict_slot<T, true>(Nc, rsc, Nf, rsf, (int)(d >> 20), (int)((d >> 10) & 1023u), (int)(d & 1023u),
+                         rf + (size_t)macro * bf, fc + (size_t)macro * bc, uc + (size_t)macro * bc);
+}
+
+// items / n_items: the fine level's Gauss-Seidel items of colours first_c ..
+// 3 (colour-major, from off[first_c] on); off holds the starts of the later
+// colours relative to that (n_items where there is none), to find an item's
+// colour.
+template <class T>
+__global__ void __launch_bounds__(CTA) k_prolong_flat(int Nf, const int* __restrict__ rsf, int64_t bf,
+                                                      T* __restrict__ uf, T* __restrict__ uIf, int Nc,
+                                                      const int* __restrict__ rsc, int64_t bc,
+                                                      const T* __restrict__ uc, const uint32_t* __restrict__ items,
+                                                      int n_items, int first_c, int3 off,
+                                                      const int* __restrict__ act, int n_act,
+                                                      const int* __restrict__ cptr, const Copy* __restrict__ cps,
+                                                      const uint32_t* __restrict__ cpo,
+                                                      const int* __restrict__ list, int n_list, int if_lo, int if_hi,
+                                                      int n_if_ctas, int n_vol_ctas) {
+  int vb = 0;
+  const int ib = spread_position((int)blockIdx.x, n_if_ctas, n_vol_ctas, vb);
+  if (ib >= 0) {
+    const int q = ib * CTA + tid256();
+    if (q < n_list && (q < if_lo || q >= if_hi)) {
+      const int node = list[q];
+      const int c0 = cptr[node], c1 = cptr[node + 1];
+      const Copy cp = cps[c0];
+      const T val = uIf[node] + interp(uc + (size_t)cp.macro * bc, Nc, rsc, cp.i, cp.j, cp.k);
+      uIf[node] = val;
+      write_copies(Nf, rsf, bf, uf, cps, cpo, c0, c1, val);
+    }
+    return;
+  }
+  const int v = vb * CTA + tid256();
+  if (v >= n_items * n_act) return;
+  const int a = v / n_items, it = v - a * n_items;
+  const int c = first_c + (it >= off.x) + (it >= off.y) + (it >= off.z);
+  const int macro = act[a];
+  const uint32_t d = items[it];
+  prolong_group<T, true>(Nf, rsf, Nc, rsc, (int)(d >> 20), (int)((d >> 10) & 1023u), (int)(d & 1023u), c,
+                         uf + (size_t)macro * bf, uc + (size_t)macro * bc);
 }
 
 // ---------------------------------------------------------------------------
@@ -2957,6 +3051,15 @@ cudaError_t restrict_to(const LevelArgs& C, const LevelArgs& F, const ProbArgs& 
   const int n = pc.col_off[4];
   const Units g = units(n + pc.n_zero, C.n_tiles_int * RESTRICT_SPLIT, pc.n_act);
   if (g.total == 0) return cudaSuccess;
+  if (C.gs_flat && C.slot_items) {
+    const int n_if_ctas = (int)lin_grid(n + pc.n_zero, CTA);
+    const int n_vol_ctas = pc.n_act > 0 ? (int)lin_grid((int64_t)C.n_slots * pc.n_act, CTA) : 0;
+    ++g_kernel_launches;
+    k_restrict_flat<T><<<n_if_ctas + n_vol_ctas, cta_shape(), 0, s>>>(
+        C.N, C.rs, C.block, fc, fIc, uc, uIc, F.N, F.rs, F.block, rf, C.slot_items, C.n_slots, pc.act, pc.n_act,
+        C.cptr, C.cps, C.cp_off, pc.free_if, n, pc.gather, pc.zero_off, pc.n_zero, n_if_ctas, n_vol_ctas);
+    return cudaGetLastError();
+  }
   const unsigned grid = resident_grid((const void*)k_restrict<T>, g.total, pc.grid_cap);
   ++g_kernel_launches;
   k_restrict<T><<<grid, cta_shape(), 0, s>>>(C.N, C.rs, C.block, fc, fIc, uc, uIc, F.N, F.rs, F.block, rf, C.tiles_int,
@@ -2993,6 +3096,27 @@ cudaError_t prolong_add(const LevelArgs& F, const LevelArgs& C, const ProbArgs& 
   const int n = pf.col_off[4];
   const Units g = units(n, F.n_tiles_int, pf.n_act);
   if (g.total == 0) return cudaSuccess;
+  const uint32_t* items = sizeof(T) == 8 ? F.gs_items64 : F.gs_items32;
+  if (F.gs_flat && items && (skip == -1 || skip == 0)) {
+    // the fine level's items of the colours updated: all, or 1..3 when the
+    // first post-smoothing sweep overwrites colour 0
+    const int* off = sizeof(T) == 8 ? F.gs_off64 : F.gs_off32;
+    const int first_c = skip == 0 ? 1 : 0;
+    const int n_items = off[4] - off[first_c];
+    int rel[3];   // starts of the colours after first_c, relative to off[first_c]
+    for (int t = 0; t < 3; ++t) {
+      const int cc = first_c + 1 + t;
+      rel[t] = cc <= 3 ? off[cc] - off[first_c] : n_items;
+    }
+    const int n_if_ctas = (int)lin_grid(n, CTA);
+    const int n_vol_ctas = pf.n_act > 0 ? (int)lin_grid((int64_t)n_items * pf.n_act, CTA) : 0;
+    ++g_kernel_launches;
+    k_prolong_flat<T><<<n_if_ctas + n_vol_ctas, cta_shape(), 0, s>>>(
+        F.N, F.rs, F.block, uf, uIf, C.N, C.rs, C.block, uc, items + off[first_c], n_items, first_c,
+        make_int3(rel[0], rel[1], rel[2]), pf.act,
+        pf.n_act, F.cptr, F.cps, F.cp_off, pf.free_if, n, if_lo, if_hi, n_if_ctas, n_vol_ctas);
+    return cudaGetLastError();
+  }
   const unsigned grid = resident_grid((const void*)k_prolong<T>, g.total, pf.grid_cap);
   ++g_kernel_launches;
   k_prolong<T><<<grid, cta_shape(), 0, s>>>(F.N, F.rs, F.block, uf, uIf, C.N, C.rs, C.block, uc, F.tiles_int,

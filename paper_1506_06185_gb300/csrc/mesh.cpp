@@ -338,6 +338,14 @@ void build_gs_items(int N, int vw, std::vector<uint32_t>& items, int off[5]) {
   off[4] = (int)items.size();
 }
 
+void build_slot_items(int N, std::vector<uint32_t>& items) {
+  items.clear();
+  for (int k = 1; k <= N - 3; ++k)
+    for (int j = 1; j <= N - 2 - k; ++j)
+      for (int m = 0; m <= (N - 1 - j - k) >> 2; ++m)
+        items.push_back(((uint32_t)j << 20) | ((uint32_t)k << 10) | (uint32_t)m);
+}
+
 void build_stream_tiles(int N, int band, int slices, std::vector<StreamTile>& out) {
   out.clear();
   // interior rows j = 1..N-2-k of slice k = 1..N-3; band [j0, j1] has

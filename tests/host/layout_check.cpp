@@ -198,6 +198,34 @@ static void check_stream_tiles(int N, int band, int VW) {
   }
 }
 
+// The flat restriction's slot items (build_slot_items): every interior node
+// of a macro lies in exactly one slot of four (i = 4m .. 4m + 3 of its row),
+// and every slot holds at least one interior node.
+static void check_slot_items(int N) {
+  std::vector<uint32_t> items;
+  build_slot_items(N, items);
+  std::vector<int> seen((size_t)(N + 1) * (N + 1) * (N + 1), 0);
+  auto at = [&](int i, int j, int k) { return ((size_t)k * (N + 1) + j) * (N + 1) + i; };
+  for (uint32_t d : items) {
+    const int j = (int)(d >> 20), k = (int)((d >> 10) & 1023u), m = (int)(d & 1023u);
+    CHECK(k >= 1 && k <= N - 3 && j >= 1 && j <= N - 2 - k, "slot items: row (%d, %d) not interior", j, k);
+    if (!(k >= 1 && k <= N - 3 && j >= 1 && j <= N - 2 - k)) continue;
+    int here = 0;
+    for (int q = 0; q < 4; ++q) {
+      const int i = 4 * m + q;
+      if (i >= 1 && i <= N - 1 - j - k) {
+        ++seen[at(i, j, k)];
+        ++here;
+      }
+    }
+    CHECK(here > 0, "slot items: slot (%d, %d, %d) holds no node", j, k, m);
+  }
+  for (int k = 1; k <= N - 3; ++k)
+    for (int j = 1; j <= N - 2 - k; ++j)
+      for (int i = 1; i <= N - 1 - j - k; ++i)
+        CHECK(seen[at(i, j, k)] == 1, "slot items: node (%d, %d, %d) covered %d times", i, j, k, seen[at(i, j, k)]);
+}
+
 // The walk order of the large stencil launches (spread_position): every
 // interface chunk and every volume unit exactly once, each kind in its own
 // order, and while volume units remain no more than R = n_vol / n_if of them
@@ -299,6 +327,7 @@ int main(int argc, char** argv) {
   }
   for (int N : {4, 5, 8, 13, 16, 32, 64, 128})
     for (int vw : {2, 4}) check_gs_items(N, vw);
+  for (int N : {4, 5, 8, 13, 16, 32, 64, 128}) check_slot_items(N);
   for (int n_if = 0; n_if <= 40; ++n_if)
     for (int n_vol = 0; n_vol <= 130; ++n_vol) check_spread(n_if, n_vol);
   // the finest launches of the bench's mesh (refinement 8: about 2300 chunks

@@ -1,7 +1,9 @@
-"""The flat Gauss-Seidel and residual kernels (hhg_set_flat_gs) against the oracle and the tile kernels.
+"""The flat kernels (hhg_set_flat_gs) against the oracle and the tile kernels.
 
-The flat kernels give every thread one 16-byte vector of same-colour nodes,
-looked up in a per-level item table, instead of walking row-pair tiles; their
+The flat Gauss-Seidel, residual and prolongation kernels give every thread one
+16-byte vector of same-colour nodes, and the flat restriction one slot of four
+coarse nodes, looked up in per-level item tables, instead of walking row-pair
+tiles; their
 per-item arithmetic is the tile kernels', and a colour's nodes read only
 other colours, so the iterate must equal the tile kernels' bit for bit (the
 residual norms only up to the order of their partial sums).  Each

@@ -10,7 +10,8 @@ staged ranges fit the shared-memory slots, every neighbour read of every
 updated node lands on the right lattice node inside its staged range, and
 every interior node of every colour is updated exactly once.  The flat
 Gauss-Seidel item tables (FP64 and FP32 vectors) cover every interior node of
-every colour exactly once, each item holding at least one node.  The walk order
+every colour exactly once, each item holding at least one node, and the flat
+restriction's slot items cover every interior node exactly once.  The walk order
 of the large stencil launches (interface chunks spread among the volume
 units) visits every chunk and unit exactly once, each kind in its own order,
 with at most n_vol / n_if volume units between two chunks."""
