@@ -18,6 +18,13 @@
 // idle lanes cost as much as busy ones.  Consecutive lanes read consecutive
 // slots of one colour segment, so stencil neighbours are contiguous accesses.
 //
+// Flat kernels (k_gs_flat, k_res_flat, k_restrict_flat, k_prolong_flat; the
+// autotuner's choice per level on meshes with the 7-point structure): no
+// tiles, one work item per thread from a per-level table (a 16-byte vector of
+// same-colour slots, or a slot of four nodes), one CTA per 256 items, so a
+// launch has no CTA barrier and no CTA walking a long tile; the per-item
+// arithmetic is the tile kernels', hence the same results bit for bit.
+//
 // Interface work: a node's stencil is the sum of the sub-stencils of the
 // macros around it (§3.2, Fig. 4); the kernel updates the master in the
 // interface container and writes the value into the ghost shell of every
