@@ -422,9 +422,10 @@ int hhg_walk_counts(hhg_mesh* mesh, int64_t* counts);
  * intervals per macro edge it sweeps bands of rows slice by slice, a
  * producer warp staging the two neighbour colours and the right-hand side of
  * each slice in shared memory with bulk asynchronous copies on mbarriers for
- * eight consumer warps; disabled, every level uses the row-pair tile kernel.
- * Both give the same iterate bit for bit (the tile kernel is the faster one
- * on GB300).  Drops the captured recovery-cycle graph.
+ * eight consumer warps; disabled, each level uses the row-pair tile kernel or,
+ * where switched on (hhg_set_flat_gs, hhg_autotune), the flat kernel.  All
+ * give the same iterate bit for bit (the streaming kernel is the slowest of
+ * the three on GB300).  Drops the captured recovery-cycle graph.
  * hhg_set_wait_limit: the streaming kernel's waits on its mbarriers are bounded
  * (default tries < 0: about one second per wait).  When a wait runs out the
  * CTA records it in the mesh's device error flag, waits (bounded) for its
