@@ -387,8 +387,9 @@ int hhg_vcycle_noalloc(hhg_mesh* mesh, int pre, int post, void* stream);
  * each kernel of a CUDA graph the library replays (batched recovery, the
  * later cycles of a local recovery) counts as one launch per replay, kernels
  * recorded while capturing such a graph do not count.
- * hhg_set_launch_limit: at most max_ctas CTAs per level-wide launch (0, the
- * default: as many as the GPU holds at once).  A level-wide launch walks its
+ * hhg_set_launch_limit: at most max_ctas CTAs per level-wide launch of the
+ * tile kernels (0, the default: as many as the GPU holds at once; the flat
+ * kernels launch one CTA per 256 items and are not limited).  A level-wide launch walks its
  * work units (interface chunks, then volume tiles) with a grid stride when
  * it has fewer than 4 units per CTA, and otherwise hands the units out
  * through a per-problem counter (the dynamic walk of large launches, where
@@ -437,7 +438,9 @@ int hhg_walk_counts(hhg_mesh* mesh, int64_t* counts);
 int hhg_set_streaming(hhg_mesh* mesh, int enable);
 /* hhg_set_flat_gs: enable or disable (default) the flat Gauss-Seidel kernel on
  * every smoothed level of a mesh with the 7-point structure (ignored on
- * meshes without it; general connectivity: HHG_ERR_STATE): one thread per
+ * meshes without it; general connectivity: HHG_ERR_STATE; HHG_ERR_ARG, with
+ * nothing changed, when a level has more than 1024 intervals per macro edge
+ * or 2^31 items per launch): one thread per
  * 16-byte vector of same-colour nodes, indexed through a per-level item
  * table (4 bytes per item, FP64 and on precision-32 meshes FP32 tables,
  * allocated on enable and freed on disable), with no tiles and no CTA

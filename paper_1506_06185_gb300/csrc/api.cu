@@ -1139,6 +1139,28 @@ constexpr int N_TUNE_CAND = 4;
 // Flat Gauss-Seidel on level l (7-point meshes of the cube family): build and
 // upload its item tables (FP64, and FP32 on precision-32 meshes) when
 // switching it on, free them when switching it off.
+// Whether the flat kernels can run level l: 4 .. 1024 intervals per macro edge
+// (the packed items hold j, k and the group in 10 bits each) and every item
+// count times the macros below 2^31 (the kernels' thread indices are 32-bit;
+// the largest counts are the slots and the FP64 items of all four colours).
+bool flat_fits(const hhg_mesh* m, int l) {
+  const int N = m->host.lv[l].N;
+  if (N > 1024 || N < 4) return false;
+  int64_t items = 0, slots = 0;
+  for (int k = 1; k <= N - 3; ++k)
+    for (int j = 1; j <= N - 2 - k; ++j) {
+      const int L = N - 1 - j - k;
+      slots += (L >> 2) + 1;
+      for (int c = 0; c < 4; ++c) {
+        const int ic = (c - 2 * j - 3 * k) & 3, mlo = ic == 0;
+        const int n = L >= ic ? ((L - ic) >> 2) - mlo + 1 : 0;
+        items += n > 0 ? (mlo + n - 1) / 2 + 1 : 0;
+      }
+    }
+  const int64_t limit = (int64_t)INT32_MAX - 1024;
+  return std::max(items, slots) * m->host.n_macro <= limit;
+}
+
 int set_flat(hhg_mesh* m, int l, bool on) {
   DevLevelTables& tb = m->tab[l];
   const HostLevel& H = m->host.lv[l];
@@ -1154,7 +1176,9 @@ int set_flat(hhg_mesh* m, int l, bool on) {
     tb.gs_flat = 0;
     return HHG_OK;
   }
-  if (H.N > 1024 || H.N < 4) return fail(HHG_ERR_ARG, "flat Gauss-Seidel needs 4 .. 1024 intervals per macro edge");
+  if (!flat_fits(m, l))
+    return fail(HHG_ERR_ARG, "the flat kernels need 4 .. 1024 intervals per macro edge and fewer than 2^31 "
+                             "items per launch");
   for (int vw : {2, 4}) {
     if (vw == 4 && m->precision != 32) continue;
     uint32_t*& dst = vw == 2 ? tb.gs_items64 : tb.gs_items32;
@@ -1162,10 +1186,6 @@ int set_flat(hhg_mesh* m, int l, bool on) {
     std::vector<uint32_t> items;
     int off[5];
     build_gs_items(H.N, vw, items, off);
-    int most = 0;
-    for (int c = 0; c < 4; ++c) most = std::max(most, off[c + 1] - off[c]);
-    if ((int64_t)most * m->host.n_macro > (int64_t)INT32_MAX - 1024)
-      return fail(HHG_ERR_ARG, "mesh too large for the flat Gauss-Seidel kernel");
     HHG_TRY(upload(m, &dst, items));
     for (int c = 0; c < 5; ++c) (vw == 2 ? tb.gs_off64 : tb.gs_off32)[c] = off[c];
   }
@@ -1227,7 +1247,7 @@ int tune_level(hhg_mesh* m, int l, int reps, cudaStream_t s, int* best_out) {
   *best_out = best;
   // the flat Gauss-Seidel kernel against the best tile shape (7-point
   // levels); the level's other kernels keep the tiles either way
-  if (m->host.seven_point) {
+  if (m->host.seven_point && flat_fits(m, l)) {
     HHG_TRY(set_flat(m, l, true));
     float ms = 0.f, ms32 = 0.f;
     HHG_TRY(time_smooth<double>(m, m->d64, l, reps, s, a, b, &ms));
@@ -2012,8 +2032,15 @@ int hhg_set_flat_gs(hhg_mesh* m, int enable) {
   if (!m) return fail(HHG_ERR_ARG, "null mesh");
   HHG_TRY(check_device(m));
   HHG_TRY(refuse_general(m, "the flat Gauss-Seidel kernel"));
+  if (!m->host.seven_point) return HHG_OK;   // the flat kernels serve the 7-point structure only
+  const int nl = (int)m->host.lv.size();
+  if (enable)
+    for (int l = 1; l < nl; ++l)
+      if (!flat_fits(m, l))
+        return fail(HHG_ERR_ARG, "the flat kernels need 4 .. 1024 intervals per macro edge and fewer than 2^31 "
+                                 "items per launch");
   drop_local_graph(m);
-  for (int l = 1; l < (int)m->host.lv.size(); ++l) HHG_TRY(set_flat(m, l, enable != 0));
+  for (int l = 1; l < nl; ++l) HHG_TRY(set_flat(m, l, enable != 0));
   return HHG_OK;
 }
 
