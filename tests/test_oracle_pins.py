@@ -223,6 +223,73 @@ def test_moved_vertices_vcycles_converge_to_direct_solve():
 
 
 # --------------------------------------------------------------------------
+# smoother (§2.1: Gauss-Seidel, here in the 4-colour order of the reading)
+# --------------------------------------------------------------------------
+
+def _smoother_case(seed=11):
+    """A small sheared mesh with random coefficients (all 15 stencil offsets),
+    the oracle's colour lists of its free nodes, the per-element CSR matrix, and
+    a random iterate (boundary values included) and load."""
+    sub, r = (1, 2, 1), 3
+    coeff = _rand_coeff(6 * 2, seed)
+    m = O.Mesh(sub, r, coeff=coeff, affine=SHEAR)
+    lv = m.fine
+    A = O.assemble_coo(lv, coeff).tocsr()
+    rng = np.random.default_rng(seed)
+    u0 = rng.standard_normal(lv.shape)
+    f = rng.standard_normal(lv.shape)
+    f[lv.boundary] = 0.0
+    return m, lv, A, u0, f
+
+
+def test_gs_step_equals_a_node_by_node_sweep():
+    """One step of the oracle's vectorised colour sweep equals the textbook
+    Gauss-Seidel loop, u_i <- (f_i - sum_{j != i} a_ij u_j) / a_ii node after
+    node, over the same nodes in colour order 0, 1, 2, 3 with the per-element
+    matrix (nodes of one colour are not coupled, so only rounding differs)."""
+    m, lv, A, u0, f = _smoother_case()
+    u_or = O.pad(u0.copy())
+    O.gs_step(lv, u_or, O.pad(f), m.global_problem.lists[-1])
+    u = u0.ravel().copy()
+    fr = f.ravel()
+    free = (~lv.boundary).ravel()
+    col = lv.colour.ravel()
+    for c in range(4):
+        for i in np.nonzero(free & (col == c))[0]:
+            lo, hi = A.indptr[i], A.indptr[i + 1]
+            js, vs = A.indices[lo:hi], A.data[lo:hi]
+            aii = vs[js == i].sum()
+            s = vs.dot(u[js]) - aii * u[i]
+            u[i] = (fr[i] - s) / aii
+    got = O.interior(u_or).ravel()
+    assert np.abs(got - u).max() <= 1e-13 * np.abs(u).max()
+    assert np.array_equal(got[~free], u0.ravel()[~free])      # Dirichlet nodes untouched
+
+
+def test_residual_after_a_step_is_the_later_colours_updates():
+    """After a full step in colour order 0..3, the residual of a colour-c node
+    is -sum over later colours c' > c of a_{c c'} (u_new - u_old)_{c'}: the node
+    was exact when swept, and only colours swept after it moved.  Colour 3's
+    residual vanishes.  A wrong colour order or a stale neighbour value breaks
+    this identity."""
+    m, lv, A, u0, f = _smoother_case(seed=12)
+    u = O.pad(u0.copy())
+    O.gs_step(lv, u, O.pad(f), m.global_problem.lists[-1])
+    un = O.interior(u).ravel()
+    delta = un - u0.ravel()
+    free = (~lv.boundary).ravel()
+    col = lv.colour.ravel()
+    r = f.ravel() - A @ un
+    scale = np.abs(A @ un).max()
+    for c in range(4):
+        later = np.where(col > c, delta, 0.0)
+        expect = -(A @ later)
+        sel = free & (col == c)
+        assert np.abs(r[sel] - expect[sel]).max() <= 1e-12 * scale, c
+    assert np.abs(r[free & (col == 3)]).max() <= 1e-12 * scale
+
+
+# --------------------------------------------------------------------------
 # transfers (§2.1)
 # --------------------------------------------------------------------------
 
@@ -481,6 +548,31 @@ def test_planted_stiffness_mistake_is_caught(monkeypatch):
     monkeypatch.setattr(O.hhg_oracle, "element_stiffness", lambda X: orig(X).T * np.array([1, 1, 1, 1.01]))
     with pytest.raises(AssertionError):
         test_cube_stencil_is_scaled_seven_point()
+
+
+def test_planted_colour_order_mistake_is_caught(monkeypatch):
+    orig = O.gs_step
+    monkeypatch.setattr(O, "gs_step", lambda lv, u, f, lists: orig(lv, u, f, lists[::-1]))   # colours 3..0
+    with pytest.raises(AssertionError):
+        test_residual_after_a_step_is_the_later_colours_updates()
+    with pytest.raises(AssertionError):
+        test_gs_step_equals_a_node_by_node_sweep()
+
+
+def test_planted_dropped_neighbour_is_caught(monkeypatch):
+    orig = O.gs_step
+
+    def dropped(lv, u, f, lists):
+        d = next(k for k in lv.A if k != (0, 0, 0))
+        saved = lv.A.pop(d)                       # the sweep forgets one neighbour
+        try:
+            orig(lv, u, f, lists)
+        finally:
+            lv.A[d] = saved
+
+    monkeypatch.setattr(O, "gs_step", dropped)
+    with pytest.raises(AssertionError):
+        test_gs_step_equals_a_node_by_node_sweep()
 
 
 def test_local_residual_equals_assembled_residual():
